@@ -1,0 +1,191 @@
+/*
+ * fks.h - flexible shifted-Krylov solver for GB300 (sm_103a), C ABI.
+ *
+ * Solves the shifted systems of Section 2, Eq. multipleshifted,
+ *     (K + sigma_j M) x_j = b,   j = 1..n_f,
+ * for a real symmetric positive definite stiffness K and a positive diagonal
+ * storage matrix M (Section 2 allows a lumped, diagonal M), from ONE flexible
+ * Arnoldi basis (Algorithm 3) built with the shifted preconditioners
+ * (K + tau_k M)^{-1}, applied inexactly by a geometric-multigrid inner solve
+ * (Section 4, Eq. zmmoditer), followed by a per-shift least-squares solve
+ * (Algorithm 4, FGMRES) and the assembly x_j = Z_m y_j.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns fks_status; fks_last_error() gives the message of the
+ *    last failing call on the calling thread. No C++ exception crosses the ABI.
+ *  - The caller owns every array it passes. The library owns its contexts,
+ *    operators, device workspaces and streams it creates.
+ *  - Invalid arguments return FKS_ERR_ARG before any device work is queued.
+ *  - Data pointers passed to fks_solve / fks_op_apply may be host or device
+ *    memory (detected with cudaPointerGetAttributes); device pointers are used in
+ *    place on the given stream, host pointers are copied.
+ *  - A context is used by one thread at a time.
+ *  - Complex numbers are fks_c128 (layout of C99 double complex).
+ *  - The grid is cell-centred, x fastest: cell (i, j, k) is at flat index
+ *    (k * ny + j) * nx + i; 2D grids have nz = 1.
+ */
+#ifndef FKS_H
+#define FKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } fks_c128;
+
+typedef enum {
+  FKS_OK = 0,                  /* every shift converged                            */
+  FKS_NOT_CONVERGED = 1,       /* some shift reached m_max without converging      */
+  FKS_BREAKDOWN_EXACT = 2,     /* h_{k+1,k} = 0: the iterate is exact (Section 3)  */
+  FKS_INNER_NOT_CONVERGED = 3, /* an inner solve hit its cycle cap (result valid)  */
+  FKS_ERR_ARG = -1,
+  FKS_ERR_OOM = -2,
+  FKS_ERR_CUDA = -3,
+  FKS_ERR_TIMEOUT = -4,
+  FKS_ERR_CANCELLED = -5
+} fks_status;
+
+typedef struct fks_ctx fks_ctx;
+typedef struct fks_op fks_op;
+
+/* Create a context bound to CUDA device `device`. */
+fks_status fks_create(fks_ctx** out, int device);
+void fks_destroy(fks_ctx* ctx);
+/* Message of the last failing call on this thread ("" if none). */
+const char* fks_last_error(void);
+/* Library version string. */
+const char* fks_version(void);
+
+/*
+ * Structured-grid operator (Section 5.1, Eq. phasor1, discretised by cell-centred
+ * two-point-flux finite volumes):
+ *   interior face between cells c, c' on axis a: t = (A_a / h_a) 2 K_c K_c' / (K_c + K_c')
+ *   zero-head face (bit set in dirichlet_mask):  t = 2 K_c A_a / h_a
+ *   no-flow face (bit clear):                    t = 0
+ *   (K x)_c = sum_faces t (x_c - x_nb) + sum_zero_head_faces t x_c,
+ *   M = diag(S_s,c * hx * hy * hz)   (lumped storage, the cell volume times S_s)
+ * with A_a the face area prod_{b != a} h_b.
+ *  dim            2 or 3
+ *  ncell[3]       (nx, ny, nz); nz ignored (taken as 1) when dim == 2; each >= 1
+ *  h[3]           cell size per axis (> 0)
+ *  cond           [n] hydraulic conductivity per cell, > 0, host memory
+ *  ss             [n] specific storage S_s per cell, > 0, host memory
+ *  dirichlet_mask bit 2a: low face of axis a is zero-head; bit 2a+1: high face
+ *  out            receives the operator (owned by the library; free with fks_op_destroy)
+ * The multigrid hierarchy is built here: axis a is halved while n_a is even and
+ * n_a > 4; the coarsest level must hold at most 1024 cells (else FKS_ERR_ARG).
+ */
+fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const double h[3],
+                       const double* cond, const double* ss, uint32_t dirichlet_mask,
+                       fks_op** out);
+void fks_op_destroy(fks_op* op);
+/* Number of cells n of the operator (0 on a NULL operator). */
+int64_t fks_op_size(const fks_op* op);
+
+enum { FKS_FGMRES = 0, FKS_FFOM = 1 };
+enum { FKS_PREC_FP64 = 0, FKS_PREC_MIXED = 1 };
+
+typedef struct {
+  double tol;            /* relative tolerance on ||b - (K + sigma_j M) x_j|| / ||b||, > 0     */
+  int m_max;             /* maximum Arnoldi steps, 1..128                                     */
+  int variant;           /* FKS_FGMRES (least squares) or FKS_FFOM (square solve)             */
+  int precision;         /* FKS_PREC_FP64: complex128 throughout; FKS_PREC_MIXED: inner
+                            multigrid cycles in complex64, defect correction and everything
+                            else in complex128                                                */
+  double inner_tol;      /* eps: stop the inner solve when ||p_k|| <= eps ||v_k||; <= 0 means
+                            min(1e-6, tol / 100)                                              */
+  int inner_max_cycles;  /* cap on multigrid cycles per inner solve (<= 0 means 50)           */
+  const int32_t* tau_schedule; /* host [sched_len]: index into tau for step k, cycled         */
+  int sched_len;         /* >= 1                                                              */
+  int replay_mode;       /* 1: run exactly replay_inner_cycles / freeze at replay_mj          */
+  const int32_t* replay_inner_cycles; /* host [m_max * n_rhs], step-major per source          */
+  const int32_t* replay_mj;           /* host [n_f * n_rhs]                                   */
+} fks_options;
+
+/* Optional per-solve diagnostics, host arrays owned by the caller (any may be NULL). */
+typedef struct {
+  int32_t* steps;         /* [n_rhs] Arnoldi steps taken                                     */
+  int32_t* inner_cycles;  /* [m_max * n_rhs] multigrid cycles of step k (source-major)       */
+  double* pnorm;          /* [m_max * n_rhs] ||p_k|| = ||v_k - (K + tau_k M) z_k||           */
+  int32_t* breakdown;     /* [n_rhs] 1 if h_{k+1,k} vanished                                 */
+} fks_info;
+
+/*
+ * Solve (K + sigma_j M) x_j = b_r for every shift j and every source r
+ * (Algorithms 3 and 4). The n_rhs sources run as independent Arnoldi processes
+ * advanced together (no block Krylov). Zero initial guess; beta = ||b_r||.
+ *  b          [n * n_rhs] source-major (column r contiguous)
+ *  sigma      [n_f] shifts; tau [n_tau] distinct preconditioner shifts
+ *  X          [n * n_f * n_rhs] out: x_j of source r at ((r * n_f) + j) * n
+ *  res_est    [n_f * n_rhs] out: ||beta e_1 - H_bar(sigma_j; T) y_j|| / beta
+ *  res_bound  [n_f * n_rhs] out: (res_est * beta + sum_i |y_i| ||p_i||) / beta (Eq. trueresidual)
+ *  res_true   [n_f * n_rhs] out: ||b - (K + sigma_j M) x_j|| / beta (computed), may be NULL
+ *  m_j        [n_f * n_rhs] out: steps used by shift j
+ *  shift_status [n_f * n_rhs] out: FKS_OK / FKS_NOT_CONVERGED / FKS_BREAKDOWN_EXACT
+ *  stream     cudaStream_t to run on (NULL: the legacy default stream)
+ * Shift j is converged when the bound of Eq. trueresidual is <= tol * beta; it
+ * is then frozen (Algorithm 4's "if not converged"). Returns FKS_OK when all
+ * shifts of all sources converged, FKS_NOT_CONVERGED or FKS_BREAKDOWN_EXACT
+ * otherwise, or an error. Outputs are complete when the call returns.
+ */
+fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
+                     const fks_c128* tau, int n_tau, const fks_options* opt, fks_c128* X,
+                     double* res_est, double* res_bound, double* res_true, int32_t* m_j,
+                     int32_t* shift_status, fks_info* info, void* stream);
+
+/*
+ * y = (K + s M) x for n_vec vectors (the operator apply of Section 2), x and y
+ * [n * n_vec] vector-major, host or device. Used by the solver's residual check.
+ */
+fks_status fks_op_apply(fks_op* op, fks_c128 s, const fks_c128* x, fks_c128* y, int n_vec, void* stream);
+
+/*
+ * Inexact preconditioner apply (Section 4, Eq. zmmoditer): z ~ (K + tau M)^{-1} v by
+ * multigrid cycles from z = 0 until ||v - (K + tau M) z|| <= eps ||v|| or max_cycles
+ * (cycles >= 0 forces exactly that many). precision as in fks_options.
+ * v, z [n] host or device; out_cycles, out_pnorm host scalars (may be NULL).
+ */
+fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c128* z, double eps,
+                             int max_cycles, int cycles, int precision, int32_t* out_cycles,
+                             double* out_pnorm, void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper). Kernel classes of the solve:
+ */
+enum {
+  FKS_K_SMOOTH = 0,    /* red-black Gauss-Seidel half sweep (any level)           */
+  FKS_K_RESTRICT = 1,  /* residual + restriction to the next coarser level        */
+  FKS_K_PROLONG = 2,   /* interpolation + correction from the coarser level       */
+  FKS_K_COARSE = 3,    /* coarsest-level dense solve                              */
+  FKS_K_DEFECT = 4,    /* complex128 defect r = v - (K + tau M) z of the inner solve */
+  FKS_K_CORRECT = 5,   /* z += e of the inner solve                               */
+  FKS_K_MDOT = 6,      /* CGS projection pass h = V^* w                           */
+  FKS_K_MAXPY = 7,     /* CGS update pass w -= V h                                */
+  FKS_K_GIVENS = 8,    /* per-shift Givens least-squares update                   */
+  FKS_K_ASSEMBLE = 9,  /* x_j = Z y_j                                             */
+  FKS_K_TRES = 10,     /* true residuals                                          */
+  FKS_K_COUNT = 11
+};
+/*
+ * Time every launch of kernel class `kclass` (on level `level`, or every level
+ * when level < 0) with CUDA events recorded on the launching stream, from now
+ * on; kclass < 0 stops timing. Every kernel launch is counted either way.
+ */
+fks_status fks_profile_select(fks_op* op, int kclass, int level);
+/*
+ * Read and reset the counters: launches of the selected class, their summed
+ * event time (ms), their summed algorithmic bytes and flops (the per-launch
+ * models of each class), and the number of all kernel launches since the last
+ * read. Any output pointer may be NULL. Synchronises the recorded events.
+ */
+fks_status fks_profile_read(fks_op* op, int64_t* launches, double* total_ms, double* alg_bytes,
+                            double* alg_flops, int64_t* all_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKS_H */

@@ -1,0 +1,773 @@
+// Host engine and C ABI of the flexible shifted-Krylov solver.
+//
+// fks_solve runs Algorithm 3 (flexible Arnoldi) for every source in lockstep
+// and Algorithm 4 (per-shift FGMRES / FFOM) after every step, with the inner
+// preconditioner solves (Section 4) done by multigrid cycles and a defect
+// correction in complex128. All per-step state lives in device memory; the
+// host only enqueues kernels and reads small flags to decide when a loop ends.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fks.h"
+#include "common.cuh"
+#include "grid.cuh"
+#include "krylov.cuh"
+
+namespace fks {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* get_error() { return g_err.c_str(); }
+
+constexpr int NU1 = 2;  // pre-smoothing red-black sweeps
+constexpr int NU2 = 2;  // post-smoothing sweeps
+constexpr double BREAKDOWN_RTOL = 1e-13;
+
+struct CudaError {
+  cudaError_t e;
+  const char* where;
+};
+
+#define CK(x)                                            \
+  do {                                                   \
+    cudaError_t e_ = (x);                                \
+    if (e_ != cudaSuccess) throw CudaError{e_, #x};      \
+  } while (0)
+
+// One growable device buffer carved into aligned pieces.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  void reserve(size_t bytes) {
+    if (bytes <= cap) return;
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw CudaError{e, "cudaMalloc(workspace)"};
+    }
+    cap = bytes;
+  }
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+  }
+  void reset() { off = 0; }
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = ((count * sizeof(T)) + 255) & ~(size_t)255;
+    T* p = (T*)(base ? base + off : nullptr);
+    off += bytes;
+    return p;
+  }
+};
+
+// Event timing of one selected kernel class plus a count of all launches.
+struct Prof {
+  int cls = -1, level = -1;
+  std::vector<cudaEvent_t> ev;
+  std::vector<double> bytes, flops;
+  size_t used = 0;
+  int64_t launches = 0, all_launches = 0;
+  double ms = 0.0, tot_bytes = 0.0, tot_flops = 0.0;
+  bool open = false;
+  bool match(int c, int l) const { return cls >= 0 && c == cls && (level < 0 || l == level); }
+  void begin(int c, int l, double b, double f, cudaStream_t s) {
+    ++all_launches;
+    open = match(c, l);
+    if (!open) return;
+    if (2 * used + 2 > ev.size()) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      ev.push_back(e0);
+      ev.push_back(e1);
+      bytes.push_back(0);
+      flops.push_back(0);
+    }
+    cudaEventRecord(ev[2 * used], s);
+    bytes[used] = b;
+    flops[used] = f;
+  }
+  void end(cudaStream_t s) {
+    if (!open) return;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+    open = false;
+  }
+  void collect() {
+    for (size_t i = 0; i < used; ++i) {
+      cudaEventSynchronize(ev[2 * i + 1]);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      ms += t;
+      tot_bytes += bytes[i];
+      tot_flops += flops[i];
+      ++launches;
+    }
+    used = 0;
+  }
+  void release() {
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+  }
+};
+
+}  // namespace fks
+
+using namespace fks;
+
+struct fks_ctx {
+  int device;
+};
+
+struct fks_op {
+  fks_ctx* ctx;
+  int dim;
+  int nx, ny, nz;
+  int64_t n;
+  uint32_t mask;
+  std::vector<LevelHost> levels;
+  Arena ws;
+  Prof prof;
+};
+
+namespace fks {
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return;
+  CK(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+static void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0 || !dst) return;
+  CK(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+// Shapes of the multigrid levels: axis a halves while n_a is even and > 4.
+static std::vector<LevelHost> level_shapes(int nx, int ny, int nz, const double h[3]) {
+  std::vector<LevelHost> L;
+  LevelHost l{};
+  l.nx = nx; l.ny = ny; l.nz = nz;
+  l.h[0] = h[0]; l.h[1] = h[1]; l.h[2] = h[2];
+  while (true) {
+    l.n = (int64_t)l.nx * l.ny * l.nz;
+    l.rx = (l.nx % 2 == 0 && l.nx > 4) ? 2 : 1;
+    l.ry = (l.ny % 2 == 0 && l.ny > 4) ? 2 : 1;
+    l.rz = (l.nz % 2 == 0 && l.nz > 4) ? 2 : 1;
+    L.push_back(l);
+    if (l.rx == 1 && l.ry == 1 && l.rz == 1) break;
+    LevelHost c{};
+    c.nx = l.nx / l.rx; c.ny = l.ny / l.ry; c.nz = l.nz / l.rz;
+    c.h[0] = l.h[0] * l.rx; c.h[1] = l.h[1] * l.ry; c.h[2] = l.h[2] * l.rz;
+    l = c;
+    if ((int)L.size() >= MAX_LEVELS) break;
+  }
+  return L;
+}
+
+// ------------------------------------------------------------------ solve state
+struct Solve {
+  fks_op* op;
+  cudaStream_t s;
+  int nslot, n_f, n_tau, m, sched_len, precision, variant;
+  int64_t n;
+  double tol, eps;
+  int max_cycles;
+  bool replay;
+  SlotState* st;
+  SlotState* st_host;  // pinned mirror
+  z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
+  double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
+  int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular;
+  // multigrid, cycle precision
+  std::vector<void*> f, z, invd;
+  void* cinv;      // coarse inverse in cycle precision
+  z64* cwork;      // dense coarse matrices
+  z64* cinv64;
+};
+
+#define PROF(cls, lvl, by, fl, call)                          \
+  do {                                                       \
+    S.op->prof.begin((cls), (lvl), (by), (fl), S.s);         \
+    call;                                                    \
+    S.op->prof.end(S.s);                                     \
+  } while (0)
+
+template <typename VT>
+static void vcycle(Solve& S) {
+  auto& Ls = S.op->levels;
+  int nl = (int)Ls.size();
+  cudaStream_t s = S.s;
+  auto F = [&](int l) { return (cx<VT>*)S.f[l]; };
+  auto Zl = [&](int l) { return (cx<VT>*)S.z[l]; };
+  auto I = [&](int l) { return (const cx<VT>*)S.invd[l]; };
+  const double cv = sizeof(cx<VT>), rv = sizeof(VT), d = S.op->dim, ns = S.nslot;
+  // algorithmic bytes / flops per launch (per level), see the class list in fks.h
+  auto smooth_b = [&](const LevelHost& L, int zs) {
+    return zs ? ns * L.n * 1.5 * cv : ns * L.n * (2 * cv + d * rv);
+  };
+  auto smooth_f = [&](const LevelHost& L, int zs) { return zs ? ns * L.n * 3.0 : ns * L.n * 0.5 * (8 * d + 6); };
+  for (int l = 0; l + 1 < nl; ++l) {
+    const LevelHost& L = Ls[l];
+    for (int r = 0; r < NU1; ++r) {
+      int zs = r == 0 ? 1 : 0;
+      PROF(FKS_K_SMOOTH, l, smooth_b(L, zs), smooth_f(L, zs),
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, zs, s));
+      PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s));
+    }
+    PROF(FKS_K_RESTRICT, l, ns * (L.n * (2 * cv + (d + 1) * rv) + cv * Ls[l + 1].n), ns * L.n * (8 * d + 10),
+         launch_residual_restrict<VT>(L, Ls[l + 1], S.st, S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
+                                      s));
+  }
+  const LevelHost& C = Ls[nl - 1];
+  PROF(FKS_K_COARSE, nl - 1, ns * cv * (C.n * C.n + 2 * C.n), ns * 8.0 * C.n * C.n,
+       launch_coarse_solve<VT>((const cx<VT>*)S.cinv, (int)C.n, S.st, F(nl - 1), Zl(nl - 1), C.n, S.nslot, s));
+  for (int l = nl - 2; l >= 0; --l) {
+    const LevelHost& L = Ls[l];
+    PROF(FKS_K_PROLONG, l, ns * (2 * cv * L.n + cv * Ls[l + 1].n), ns * L.n * (4.0 * (1 << S.op->dim) + 2),
+         launch_prolong_add<VT>(L, Ls[l + 1], S.op->mask, S.st, Zl(l + 1), Ls[l + 1].n, Zl(l), L.n, S.nslot, s));
+    for (int r = 0; r < NU2; ++r) {
+      PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s));
+      PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, 0, s));
+    }
+  }
+}
+
+static bool any_inner_running(Solve& S) {
+  CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * S.nslot, cudaMemcpyDeviceToHost, S.s));
+  CK(cudaStreamSynchronize(S.s));
+  for (int i = 0; i < S.nslot; ++i)
+    if (S.st_host[i].active && !S.st_host[i].inner_done) return true;
+  return false;
+}
+
+static bool any_active(Solve& S) {
+  CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * S.nslot, cudaMemcpyDeviceToHost, S.s));
+  CK(cudaStreamSynchronize(S.s));
+  for (int i = 0; i < S.nslot; ++i)
+    if (S.st_host[i].active) return true;
+  return false;
+}
+
+// Inner solve of the current step: z_k (column k-1 of Z) from v_k (column k-1 of V).
+template <typename VT>
+static void inner_solve(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ) {
+  const LevelHost& L0 = S.op->levels[0];
+  int nbl = defect_blocks(L0.n);
+  cx<VT>* f0 = (cx<VT>*)S.f[0];
+  cx<VT>* e0 = (cx<VT>*)S.z[0];
+  const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
+  const double cv = sizeof(cx<VT>), d = S.op->dim, ns = S.nslot, n = L0.n;
+  const double def_b = ns * n * (32 + 8 * (d + 1) + cv), def_f = ns * n * (8 * d + 14);
+  PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
+       launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 1, f0, L0.n, S.dpart, 1, S.nslot, S.s));
+  PROF(-1, -1, 0, 0, launch_inner_decide(S.st, S.nslot, S.dpart, nbl, 1, S.eps, S.max_cycles, rc, S.m, S.s));
+  int guard = 0;
+  while (any_inner_running(S)) {
+    vcycle<VT>(S);
+    PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
+         launch_correct<VT>(S.st, Z, vsZ, L0.n, e0, L0.n, L0.n, S.nslot, S.s));
+    PROF(FKS_K_DEFECT, 0, def_b, def_f,
+         launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 0, f0, L0.n, S.dpart, 0, S.nslot, S.s));
+    PROF(-1, -1, 0, 0, launch_inner_decide(S.st, S.nslot, S.dpart, nbl, 0, S.eps, S.max_cycles, rc, S.m, S.s));
+    if (++guard > 100000) break;
+  }
+}
+
+template <typename VT>
+static void setup_levels(Solve& S) {
+  auto& Ls = S.op->levels;
+  for (size_t l = 0; l < Ls.size(); ++l)
+    PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
+  const LevelHost& C = Ls.back();
+  int64_t nc = C.n;
+  CK(cudaMemsetAsync(S.singular, 0, sizeof(int), S.s));
+  S.op->prof.all_launches += 2;
+  launch_coarse_inverse(C, S.taus, S.n_tau, S.cwork, S.cinv64, S.singular, S.s);
+  if constexpr (sizeof(VT) == 8) {
+    CK(cudaMemcpyAsync(S.cinv, S.cinv64, sizeof(z64) * S.n_tau * nc * nc, cudaMemcpyDeviceToDevice, S.s));
+  } else {
+    PROF(-1, -1, 0, 0, launch_to_prec<VT>(S.cinv64, (cx<VT>*)S.cinv, (int64_t)S.n_tau * nc * nc, S.s));
+  }
+}
+
+template <typename VT>
+static void carve(Solve& S, Arena& A, bool x_internal) {
+  int64_t n = S.n;
+  int ns = S.nslot, m = S.m, nf = S.n_f;
+  auto& Ls = S.op->levels;
+  A.reset();
+  S.st = A.take<SlotState>(ns);
+  S.b = A.take<z64>((size_t)ns * n);
+  S.sigma = A.take<z64>(nf);
+  S.taus = A.take<z64>(S.n_tau);
+  S.sched = A.take<int32_t>(S.sched_len);
+  S.rep_cyc = A.take<int32_t>((size_t)ns * m);
+  S.rep_mj = A.take<int32_t>((size_t)ns * nf);
+  S.V = A.take<z64>((size_t)ns * (m + 1) * n);
+  S.Z = A.take<z64>((size_t)ns * m * n);
+  S.w = A.take<z64>((size_t)ns * n);
+  S.f.assign(Ls.size(), nullptr);
+  S.z.assign(Ls.size(), nullptr);
+  S.invd.assign(Ls.size(), nullptr);
+  for (size_t l = 0; l < Ls.size(); ++l) {
+    S.f[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
+    S.z[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
+    S.invd[l] = A.take<cx<VT>>((size_t)S.n_tau * Ls[l].n);
+  }
+  int64_t nc = Ls.back().n;
+  S.cwork = A.take<z64>((size_t)S.n_tau * nc * nc);
+  S.cinv64 = A.take<z64>((size_t)S.n_tau * nc * nc);
+  S.cinv = A.take<cx<VT>>((size_t)S.n_tau * nc * nc);
+  S.singular = A.take<int32_t>(1);
+  S.dpart = A.take<double>((size_t)ns * defect_blocks(n) * 2);
+  S.npart = A.take<double>((size_t)ns * norm_blocks(n));
+  S.mpart = A.take<double>((size_t)ns * norm_blocks(n));
+  S.wpart = A.take<double>((size_t)ns * norm_blocks(n));
+  S.mdpart = A.take<z64>((size_t)ns * mdot_blocks(n) * MAX_M);
+  S.h12 = A.take<z64>((size_t)ns * 2 * MAX_M);
+  S.H = A.take<z64>((size_t)ns * (m + 1) * m);
+  S.taus_k = A.take<z64>((size_t)ns * m);
+  S.pn = A.take<double>((size_t)ns * m);
+  S.cyc = A.take<int32_t>((size_t)ns * m);
+  S.g = A.take<z64>((size_t)ns * nf * (m + 1));
+  S.rc = A.take<double>((size_t)ns * nf * m);
+  S.rs = A.take<z64>((size_t)ns * nf * m);
+  S.R = A.take<z64>((size_t)ns * nf * m * m);
+  S.Y = A.take<z64>((size_t)ns * nf * m);
+  S.sst = A.take<int32_t>((size_t)ns * nf);
+  S.mj = A.take<int32_t>((size_t)ns * nf);
+  S.est = A.take<double>((size_t)ns * nf);
+  S.bnd = A.take<double>((size_t)ns * nf);
+  S.tpart = A.take<double>((size_t)ns * nf * tres_blocks(n));
+  S.tres = A.take<double>((size_t)ns * nf);
+  S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
+}
+
+template <typename VT>
+static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
+                             const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X, double* res_est,
+                             double* res_bound, double* res_true, int32_t* m_j, int32_t* shift_status, fks_info* info,
+                             cudaStream_t s) {
+  Solve S{};
+  S.op = op;
+  S.s = s;
+  S.nslot = n_rhs;
+  S.n_f = n_f;
+  S.n_tau = n_tau;
+  S.m = o->m_max;
+  S.sched_len = o->sched_len;
+  S.precision = o->precision;
+  S.variant = o->variant;
+  S.n = op->n;
+  S.tol = o->tol;
+  S.eps = o->inner_tol > 0 ? o->inner_tol : std::min(1e-6, o->tol / 100.0);
+  S.max_cycles = o->inner_max_cycles > 0 ? o->inner_max_cycles : 50;
+  S.replay = o->replay_mode != 0;
+  bool x_dev = is_device_ptr(X);
+  // workspace size: carve once on a null base to measure
+  Arena probe;
+  carve<VT>(S, probe, !x_dev);
+  size_t need = probe.off + 4096;
+  op->ws.reserve(need);
+  carve<VT>(S, op->ws, !x_dev);
+  z64* Xd = x_dev ? (z64*)X : S.X;
+  std::vector<SlotState> st_host(n_rhs);
+  S.st_host = st_host.data();
+  int64_t n = S.n;
+  int m = S.m;
+  // inputs
+  copy_in(S.b, b, sizeof(z64) * n * n_rhs, s);
+  copy_in(S.sigma, sigma, sizeof(z64) * n_f, s);
+  copy_in(S.taus, tau, sizeof(z64) * n_tau, s);
+  CK(cudaMemcpyAsync(S.sched, o->tau_schedule, sizeof(int32_t) * o->sched_len, cudaMemcpyHostToDevice, s));
+  if (S.replay) {
+    CK(cudaMemcpyAsync(S.rep_cyc, o->replay_inner_cycles, sizeof(int32_t) * m * n_rhs, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.rep_mj, o->replay_mj, sizeof(int32_t) * n_f * n_rhs, cudaMemcpyHostToDevice, s));
+  }
+  // preconditioner setup for the distinct taus (inverse diagonals, coarse inverse)
+  setup_levels<VT>(S);
+  // start: beta, v_1
+  int nbn = norm_blocks(n);
+  PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 0, S.b, n, n, S.npart, n_rhs, s));
+  PROF(-1, -1, 0, 0, launch_start(S.st, n_rhs, S.npart, nbn, n_f, s));
+  PROF(-1, -1, 0, 0, launch_init_v1(S.st, S.b, n, S.V, (m + 1) * n, n_rhs, s));
+  PROF(-1, -1, 0, 0, launch_init_shifts(S.st, n_f, m, S.sst, S.mj, S.est, S.bnd, S.Y, n_rhs, s));
+  CK(cudaMemsetAsync(S.pn, 0, sizeof(double) * m * n_rhs, s));
+  CK(cudaMemsetAsync(S.cyc, 0, sizeof(int32_t) * m * n_rhs, s));
+  const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
+  int steps = 0;
+  if (any_active(S)) {
+    for (int step = 1; step <= m; ++step) {
+      steps = step;
+      const double ns = n_rhs, nn = (double)n, kk = step, d = op->dim;
+      PROF(-1, -1, 0, 0, launch_step_begin(S.st, n_rhs, step, S.sched, S.sched_len, S.taus, S.taus_k, m, s));
+      inner_solve<VT>(S, S.V, vsV, S.Z, vsZ);
+      PROF(-1, -1, 0, 0, launch_mass(S.st, op->levels[0].d64[3], S.Z, vsZ, S.w, n, S.mpart, n_rhs, s));
+      // CGS2: two projections; pass p writes its coefficients to h12[slot][p]
+      for (int pass = 0; pass < 2; ++pass) {
+        z64* hp = S.h12 + pass * MAX_M;
+        PROF(FKS_K_MDOT, -1, ns * 16 * nn * (kk + 1), ns * 8 * nn * kk,
+             launch_mdot(S.st, S.V, vsV, S.w, n, S.mdpart, step, n_rhs, s));
+        PROF(-1, -1, 0, 0, launch_hreduce(S.st, S.mdpart, n, hp, 2 * MAX_M, n_rhs, s));
+        PROF(FKS_K_MAXPY, -1, ns * 16 * nn * (kk + 2), ns * 8 * nn * kk,
+             launch_maxpy(S.st, S.V, vsV, hp, 2 * MAX_M, S.w, n, n_rhs, s));
+      }
+      PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 1, S.w, n, n, S.wpart, n_rhs, s));
+      PROF(-1, -1, 0, 0,
+           launch_arnoldi_finish(S.st, n_rhs, S.h12, S.wpart, S.mpart, nbn, S.H, m, S.pn, S.cyc, BREAKDOWN_RTOL, s));
+      PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, s));
+      PROF(FKS_K_GIVENS, -1, ns * n_f * 48.0 * kk, ns * n_f * 26.0 * kk,
+           launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant,
+                         S.replay ? S.rep_mj : nullptr, S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, n_rhs,
+                         s));
+      PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, s));
+      (void)d;
+      if (!any_active(S)) break;
+    }
+  }
+  // assembly and true residual
+  {
+    const double ns = n_rhs, nn = (double)n, ks = steps, d = op->dim;
+    PROF(FKS_K_ASSEMBLE, -1, ns * 16 * nn * (ks + n_f), ns * 8 * nn * ks * n_f,
+         launch_assemble(S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, s));
+    if (res_true)
+      PROF(FKS_K_TRES, -1, ns * nn * (16.0 * n_f + 16 + 8 * (d + 1)), ns * nn * n_f * (8 * d + 14),
+           launch_true_residual(op->levels[0], S.sigma, n_f, S.b, Xd, S.tpart, S.st, S.tres, n_rhs, s));
+    if (res_true) op->prof.all_launches += 1;  // the true residual is two kernels
+  }
+  CK(cudaGetLastError());
+  // outputs
+  if (!x_dev) copy_out(X, Xd, sizeof(z64) * n * n_f * n_rhs, s);
+  copy_out(res_est, S.est, sizeof(double) * n_f * n_rhs, s);
+  copy_out(res_bound, S.bnd, sizeof(double) * n_f * n_rhs, s);
+  if (res_true) copy_out(res_true, S.tres, sizeof(double) * n_f * n_rhs, s);
+  copy_out(m_j, S.mj, sizeof(int32_t) * n_f * n_rhs, s);
+  std::vector<int32_t> sst_h((size_t)n_f * n_rhs);
+  CK(cudaMemcpyAsync(sst_h.data(), S.sst, sizeof(int32_t) * n_f * n_rhs, cudaMemcpyDeviceToHost, s));
+  copy_out(shift_status, S.sst, sizeof(int32_t) * n_f * n_rhs, s);
+  std::vector<int32_t> cyc_h;
+  std::vector<double> pn_h;
+  if (info && info->inner_cycles) cyc_h.resize((size_t)m * n_rhs);
+  if (info && info->pnorm) pn_h.resize((size_t)m * n_rhs);
+  if (!cyc_h.empty()) CK(cudaMemcpyAsync(cyc_h.data(), S.cyc, sizeof(int32_t) * m * n_rhs, cudaMemcpyDeviceToHost, s));
+  if (!pn_h.empty()) CK(cudaMemcpyAsync(pn_h.data(), S.pn, sizeof(double) * m * n_rhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
+  int singular = 0;
+  CK(cudaMemcpyAsync(&singular, S.singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (info) {
+    for (int r = 0; r < n_rhs; ++r) {
+      if (info->steps) info->steps[r] = S.st_host[r].beta > 0 ? S.st_host[r].k : 0;
+      if (info->breakdown) info->breakdown[r] = S.st_host[r].breakdown;
+    }
+    if (info->inner_cycles) std::memcpy(info->inner_cycles, cyc_h.data(), sizeof(int32_t) * m * n_rhs);
+    if (info->pnorm) std::memcpy(info->pnorm, pn_h.data(), sizeof(double) * m * n_rhs);
+  }
+  (void)steps;
+  if (singular) {
+    set_error("coarsest multigrid level is singular for some tau");
+    return FKS_ERR_ARG;
+  }
+  bool nc = false, bd = false, capped = false;
+  for (int32_t v : sst_h) {
+    if (v == 1 || v == -1) nc = true;
+    if (v == 2) bd = true;
+  }
+  for (int r = 0; r < n_rhs; ++r) capped = capped || S.st_host[r].inner_capped;
+  if (nc) return FKS_NOT_CONVERGED;
+  if (bd) return FKS_BREAKDOWN_EXACT;
+  if (capped) return FKS_INNER_NOT_CONVERGED;
+  return FKS_OK;
+}
+
+static bool finite_c(const fks_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
+
+}  // namespace fks
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* fks_last_error(void) { return fks::get_error(); }
+const char* fks_version(void) { return "fks 0.1 (sm_103a)"; }
+
+fks_status fks_create(fks_ctx** out, int device) {
+  if (!out) { set_error("fks_create: out is NULL"); return FKS_ERR_ARG; }
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    set_error("fks_create: no CUDA device");
+    return FKS_ERR_CUDA;
+  }
+  if (device < 0 || device >= count) { set_error("fks_create: bad device index"); return FKS_ERR_ARG; }
+  if (cudaSetDevice(device) != cudaSuccess) { set_error("fks_create: cudaSetDevice failed"); return FKS_ERR_CUDA; }
+  fks_ctx* c = new fks_ctx;
+  c->device = device;
+  *out = c;
+  set_error("");
+  return FKS_OK;
+}
+
+void fks_destroy(fks_ctx* ctx) { delete ctx; }
+
+fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const double h[3], const double* cond,
+                       const double* ss, uint32_t mask, fks_op** out) {
+  if (!out) { set_error("fks_op_grid: out is NULL"); return FKS_ERR_ARG; }
+  *out = nullptr;
+  if (!ctx || !ncell || !h || !cond || !ss) { set_error("fks_op_grid: NULL argument"); return FKS_ERR_ARG; }
+  if (dim != 2 && dim != 3) { set_error("fks_op_grid: dim must be 2 or 3"); return FKS_ERR_ARG; }
+  int64_t nx = ncell[0], ny = ncell[1], nz = dim == 3 ? ncell[2] : 1;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) {
+    set_error("fks_op_grid: cell counts must be >= 1");
+    return FKS_ERR_ARG;
+  }
+  for (int a = 0; a < dim; ++a)
+    if (!(h[a] > 0) || !std::isfinite(h[a])) { set_error("fks_op_grid: h must be positive"); return FKS_ERR_ARG; }
+  if (mask >> (2 * dim)) { set_error("fks_op_grid: dirichlet_mask has bits beyond 2*dim"); return FKS_ERR_ARG; }
+  int64_t n = nx * ny * nz;
+  for (int64_t c = 0; c < n; ++c) {
+    if (!(cond[c] > 0) || !std::isfinite(cond[c])) { set_error("fks_op_grid: cond must be positive and finite"); return FKS_ERR_ARG; }
+    if (!(ss[c] > 0) || !std::isfinite(ss[c])) { set_error("fks_op_grid: ss must be positive and finite"); return FKS_ERR_ARG; }
+  }
+  double hh[3] = {h[0], h[1], dim == 3 ? h[2] : 1.0};
+  // lumped storage: M_cc = S_s,c * cell volume
+  double vol = hh[0] * hh[1] * hh[2];
+  std::vector<double> mass(n);
+  for (int64_t c = 0; c < n; ++c) mass[c] = ss[c] * vol;
+  std::vector<LevelHost> Ls = level_shapes((int)nx, (int)ny, (int)nz, hh);
+  if (Ls.back().n > MAX_COARSE) {
+    set_error("fks_op_grid: coarsest multigrid level has more than 1024 cells (halve sides while even and > 4)");
+    return FKS_ERR_ARG;
+  }
+  fks_op* op = new fks_op;
+  op->ctx = ctx;
+  op->dim = dim;
+  op->nx = (int)nx; op->ny = (int)ny; op->nz = (int)nz;
+  op->n = n;
+  op->mask = mask;
+  double* cond_d = nullptr;
+  try {
+    CK(cudaSetDevice(ctx->device));
+    for (auto& L : Ls) {
+      for (int a = 0; a < 4; ++a) {
+        int64_t cnt = a < 3 ? (a == 2 && L.nz == 1 ? 1 : face_count(L, a)) : L.n;
+        CK(cudaMalloc(&L.d64[a], sizeof(double) * cnt));
+        CK(cudaMalloc(&L.d32[a], sizeof(float) * cnt));
+      }
+    }
+    op->levels = Ls;
+    cudaStream_t s = 0;
+    CK(cudaMalloc(&cond_d, sizeof(double) * n));
+    CK(cudaMemcpy(cond_d, cond, sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(op->levels[0].d64[3], mass.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    launch_faces_from_cond(op->levels[0], hh, mask, cond_d, s);
+    for (size_t l = 0; l + 1 < op->levels.size(); ++l) launch_coarsen(op->levels[l], op->levels[l + 1], s);
+    for (auto& L : op->levels)
+      for (int a = 0; a < 4; ++a) {
+        int64_t cnt = a < 3 ? (a == 2 && L.nz == 1 ? 1 : face_count(L, a)) : L.n;
+        launch_to_f32(L.d64[a], L.d32[a], cnt, s);
+      }
+    CK(cudaDeviceSynchronize());
+    CK(cudaGetLastError());
+    cudaFree(cond_d);
+  } catch (CudaError& e) {
+    if (cond_d) cudaFree(cond_d);
+    set_error(std::string("fks_op_grid: ") + e.where + ": " + cudaGetErrorString(e.e));
+    fks_op_destroy(op);
+    return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+  *out = op;
+  return FKS_OK;
+}
+
+void fks_op_destroy(fks_op* op) {
+  if (!op) return;
+  for (auto& L : op->levels)
+    for (int a = 0; a < 4; ++a) {
+      if (L.d64[a]) cudaFree(L.d64[a]);
+      if (L.d32[a]) cudaFree(L.d32[a]);
+    }
+  op->ws.release();
+  op->prof.release();
+  delete op;
+}
+
+int64_t fks_op_size(const fks_op* op) { return op ? op->n : 0; }
+
+fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f, const fks_c128* tau,
+                     int n_tau, const fks_options* o, fks_c128* X, double* res_est, double* res_bound,
+                     double* res_true, int32_t* m_j, int32_t* shift_status, fks_info* info, void* stream) {
+  if (!op || !b || !sigma || !tau || !o || !X || !res_est || !res_bound || !m_j || !shift_status) {
+    set_error("fks_solve: NULL argument");
+    return FKS_ERR_ARG;
+  }
+  if (n_rhs < 1 || n_f < 1 || n_tau < 1 || n_tau > MAX_TAU) { set_error("fks_solve: bad n_rhs / n_f / n_tau"); return FKS_ERR_ARG; }
+  if (o->m_max < 1 || o->m_max > MAX_M) { set_error("fks_solve: m_max must be in 1..128"); return FKS_ERR_ARG; }
+  if (!(o->tol > 0) || !std::isfinite(o->tol)) { set_error("fks_solve: tol must be positive"); return FKS_ERR_ARG; }
+  if (o->variant != FKS_FGMRES && o->variant != FKS_FFOM) { set_error("fks_solve: bad variant"); return FKS_ERR_ARG; }
+  if (o->precision != FKS_PREC_FP64 && o->precision != FKS_PREC_MIXED) { set_error("fks_solve: bad precision"); return FKS_ERR_ARG; }
+  if (o->sched_len < 1 || !o->tau_schedule) { set_error("fks_solve: empty tau schedule"); return FKS_ERR_ARG; }
+  for (int i = 0; i < o->sched_len; ++i)
+    if (o->tau_schedule[i] < 0 || o->tau_schedule[i] >= n_tau) { set_error("fks_solve: schedule index out of range"); return FKS_ERR_ARG; }
+  if (o->replay_mode && (!o->replay_inner_cycles || !o->replay_mj)) { set_error("fks_solve: replay arrays missing"); return FKS_ERR_ARG; }
+  if (o->replay_mode) {
+    for (int i = 0; i < o->m_max * n_rhs; ++i)
+      if (o->replay_inner_cycles[i] < 0) { set_error("fks_solve: negative replay cycle count"); return FKS_ERR_ARG; }
+    for (int i = 0; i < n_f * n_rhs; ++i)
+      if (o->replay_mj[i] < 1 || o->replay_mj[i] > o->m_max) { set_error("fks_solve: replay m_j out of range"); return FKS_ERR_ARG; }
+  }
+  // small host-side checks of shifts (device pointers are checked after a copy)
+  std::vector<fks_c128> sg(n_f), tu(n_tau);
+  cudaMemcpy(sg.data(), sigma, sizeof(fks_c128) * n_f, cudaMemcpyDefault);
+  cudaMemcpy(tu.data(), tau, sizeof(fks_c128) * n_tau, cudaMemcpyDefault);
+  if (cudaGetLastError() != cudaSuccess) { set_error("fks_solve: cannot read sigma / tau"); return FKS_ERR_ARG; }
+  for (auto& z : sg) if (!finite_c(z)) { set_error("fks_solve: sigma has NaN/Inf"); return FKS_ERR_ARG; }
+  for (auto& z : tu) if (!finite_c(z)) { set_error("fks_solve: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    if (o->precision == FKS_PREC_FP64)
+      return solve_impl<double>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+                                shift_status, info, s);
+    return solve_impl<float>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+                             shift_status, info, s);
+  } catch (CudaError& e) {
+    set_error(std::string("fks_solve: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+}
+
+fks_status fks_profile_select(fks_op* op, int kclass, int level) {
+  if (!op) { set_error("fks_profile_select: NULL operator"); return FKS_ERR_ARG; }
+  if (kclass >= FKS_K_COUNT) { set_error("fks_profile_select: bad kernel class"); return FKS_ERR_ARG; }
+  op->prof.cls = kclass < 0 ? -1 : kclass;
+  op->prof.level = level;
+  return FKS_OK;
+}
+
+fks_status fks_profile_read(fks_op* op, int64_t* launches, double* total_ms, double* alg_bytes, double* alg_flops,
+                            int64_t* all_launches) {
+  if (!op) { set_error("fks_profile_read: NULL operator"); return FKS_ERR_ARG; }
+  Prof& p = op->prof;
+  p.collect();
+  if (launches) *launches = p.launches;
+  if (total_ms) *total_ms = p.ms;
+  if (alg_bytes) *alg_bytes = p.tot_bytes;
+  if (alg_flops) *alg_flops = p.tot_flops;
+  if (all_launches) *all_launches = p.all_launches;
+  p.launches = 0;
+  p.ms = 0;
+  p.tot_bytes = 0;
+  p.tot_flops = 0;
+  p.all_launches = 0;
+  return FKS_OK;
+}
+
+fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y, int n_vec, void* stream) {
+  if (!op || !x || !y || n_vec < 1) { set_error("fks_op_apply: bad argument"); return FKS_ERR_ARG; }
+  if (!finite_c(sh)) { set_error("fks_op_apply: shift has NaN/Inf"); return FKS_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    int64_t n = op->n;
+    bool xd = is_device_ptr(x), yd = is_device_ptr(y);
+    size_t bytes = sizeof(z64) * n * n_vec;
+    Arena& A = op->ws;
+    A.reserve(2 * bytes + 1024);
+    A.reset();
+    z64* xs = xd ? (z64*)x : A.take<z64>((size_t)n * n_vec);
+    z64* ys = yd ? (z64*)y : A.take<z64>((size_t)n * n_vec);
+    if (!xd) CK(cudaMemcpyAsync(xs, x, bytes, cudaMemcpyHostToDevice, s));
+    launch_apply<double>(op->levels[0], mk(sh.re, sh.im), nullptr, nullptr, xs, ys, n, n_vec, s);
+    CK(cudaGetLastError());
+    if (!yd) CK(cudaMemcpyAsync(y, ys, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } catch (CudaError& e) {
+    set_error(std::string("fks_op_apply: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return FKS_ERR_CUDA;
+  }
+  return FKS_OK;
+}
+
+fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c128* z, double eps, int max_cycles,
+                             int cycles, int precision, int32_t* out_cycles, double* out_pnorm, void* stream) {
+  if (!op || !v || !z) { set_error("fks_precond_apply: NULL argument"); return FKS_ERR_ARG; }
+  if (!finite_c(tau)) { set_error("fks_precond_apply: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_precond_apply: bad precision"); return FKS_ERR_ARG; }
+  if (cycles < 0 && !(eps > 0)) { set_error("fks_precond_apply: eps must be positive"); return FKS_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    Solve S{};
+    S.op = op;
+    S.s = s;
+    S.nslot = 1;
+    S.n_f = 1;
+    S.n_tau = 1;
+    S.m = 1;
+    S.sched_len = 1;
+    S.precision = precision;
+    S.n = op->n;
+    S.eps = eps;
+    S.max_cycles = max_cycles > 0 ? max_cycles : 50;
+    S.replay = cycles >= 0;
+    auto run = [&](auto tag) {
+      using VT = decltype(tag);
+      Arena probe;
+      carve<VT>(S, probe, false);
+      op->ws.reserve(probe.off + 4096);
+      carve<VT>(S, op->ws, false);
+      int64_t n = S.n;
+      copy_in(S.V, v, sizeof(z64) * n, s);
+      CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
+      int32_t cyc = cycles;
+      CK(cudaMemcpyAsync(S.rep_cyc, &cyc, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      SlotState st0{};
+      st0.active = 1;
+      st0.k = 1;
+      st0.tau = 0;
+      CK(cudaMemcpyAsync(S.st, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+      std::vector<SlotState> sh(1);
+      S.st_host = sh.data();
+      setup_levels<VT>(S);
+      inner_solve<VT>(S, S.V, n, S.Z, n);
+      CK(cudaGetLastError());
+      copy_out(z, S.Z, sizeof(z64) * n, s);
+      CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (out_cycles) *out_cycles = S.st_host[0].cycles;
+      if (out_pnorm) *out_pnorm = std::sqrt(S.st_host[0].pnorm2);
+    };
+    if (precision == FKS_PREC_FP64) run(double{});
+    else run(float{});
+  } catch (CudaError& e) {
+    set_error(std::string("fks_precond_apply: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+  return FKS_OK;
+}
+
+}  // extern "C"

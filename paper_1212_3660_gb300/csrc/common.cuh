@@ -1,0 +1,115 @@
+// Internal types shared by the kernels and the host engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+namespace fks {
+
+// ---------------------------------------------------------------- complex
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mk(T a, T b) { return cx<T>{a, b}; }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> conj(cx<T> a) { return mk(a.re, -a.im); }
+template <typename T>
+__host__ __device__ __forceinline__ T abs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+// conj(a) * b
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cdot(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+template <typename To, typename Ti>
+__host__ __device__ __forceinline__ cx<To> cvt(cx<Ti> a) { return mk((To)a.re, (To)a.im); }
+
+typedef cx<double> z64;
+typedef cx<float> z32;
+
+// ---------------------------------------------------------------- grid level
+// Coefficients of one multigrid level in precision T. Faces are stored for the
+// whole closed grid: fx has (nx+1) entries per x-row, fx[row*(nx+1) + i] being the
+// transmissibility of the face between cells i-1 and i (i = 0 and i = nx are the
+// boundary faces: 2 K A / h on a zero-head face, 0 on a no-flow face); likewise
+// fy with (ny+1) rows per plane and fz with (nz+1) planes. mm is the diagonal of M.
+// The diagonal of K at a cell is the sum of its 2d faces.
+template <typename T>
+struct LevelView {
+  int nx, ny, nz;
+  int64_t n;
+  const T* fx;
+  const T* fy;
+  const T* fz;  // unused when nz == 1
+  const T* mm;
+};
+
+constexpr int MAX_LEVELS = 16;
+constexpr int MAX_COARSE = 1024;
+constexpr int MAX_TAU = 16;
+constexpr int MAX_M = 128;
+
+struct LevelHost {
+  int nx, ny, nz;
+  int rx, ry, rz;     // ratio to the NEXT coarser level (1 or 2); 1,1,1 on the coarsest
+  int64_t n;
+  double h[3];
+  double* d64[4];     // fx, fy, fz, mm (device)
+  float* d32[4];      // fp32 copies (device)
+};
+
+template <typename T>
+inline LevelView<T> view(const LevelHost& L) {
+  LevelView<T> v;
+  v.nx = L.nx; v.ny = L.ny; v.nz = L.nz; v.n = L.n;
+  T* const* a;
+  if constexpr (sizeof(T) == 8) a = (T* const*)L.d64; else a = (T* const*)L.d32;
+  v.fx = a[0]; v.fy = a[1]; v.fz = a[2]; v.mm = a[3];
+  return v;
+}
+
+inline int64_t face_count(const LevelHost& L, int a) {
+  return a == 0 ? (int64_t)(L.nx + 1) * L.ny * L.nz
+       : a == 1 ? (int64_t)L.nx * (L.ny + 1) * L.nz
+                : (int64_t)L.nx * L.ny * (L.nz + 1);
+}
+
+// ---------------------------------------------------------------- per-source state
+// Small per-source (slot) state kept in device memory so that every kernel of a
+// step can read it without host involvement.
+struct SlotState {
+  double beta;      // ||b||
+  double vnorm2;    // ||v_k||^2
+  double pnorm2;    // ||v_k - (K + tau_k M) z||^2 of the current inner iterate
+  double w0norm2;   // ||M z_k||^2 (scale of the breakdown test)
+  int k;            // current step, 1-based (set when the step starts)
+  int tau;          // index of tau_bar for step k
+  int cycles;       // inner cycles done in this step
+  int inner_done;   // inner solve of this step finished
+  int active;       // source still iterating
+  int live;         // shifts not yet frozen
+  int breakdown;    // h_{k+1,k} vanished at step k
+  int inner_capped; // some inner solve hit its cycle cap
+};
+
+// error reporting
+void set_error(const std::string& msg);
+const char* get_error();
+
+}  // namespace fks

@@ -1,0 +1,599 @@
+// Structured-grid kernels: operator coefficients, the shifted operator apply,
+// and the geometric-multigrid pieces of the inexact inner solve (Section 4,
+// Eq. zmmoditer): red-black Gauss-Seidel, residual + restriction,
+// interpolation + correction, coarsest-level dense solve.
+//
+// Every vector kernel takes a batch of sources ("slots") on gridDim.y; vector
+// arguments point at slot 0 and consecutive slots are `vs` elements apart.
+#include "grid.cuh"
+#include "stencil.cuh"
+
+namespace fks {
+
+__device__ __forceinline__ bool slot_running(const SlotState* st, int slot) {
+  return st == nullptr || (st[slot].active && !st[slot].inner_done);
+}
+
+// --------------------------------------------------------------------- setup
+// Fine-level faces from cell conductivity (harmonic mean on interior faces,
+// 2 K A / h on zero-head faces). One thread per face of each orientation.
+__global__ void k_faces_from_cond(int nx, int ny, int nz, double hx, double hy, double hz, uint32_t mask,
+                                  const double* __restrict__ cond, double* fx, double* fy, double* fz) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t nfx = (int64_t)(nx + 1) * ny * nz, nfy = (int64_t)nx * (ny + 1) * nz;
+  int64_t nfz = nz > 1 ? (int64_t)nx * ny * (nz + 1) : 0;
+  if (t < nfx) {
+    int i = (int)(t % (nx + 1));
+    int64_t row = t / (nx + 1);  // k*ny + j
+    double g = (hy * hz) / hx;
+    int64_t c = row * nx + i;
+    double v;
+    if (i == 0) v = (mask & 1u) ? 2.0 * cond[c] * g : 0.0;
+    else if (i == nx) v = (mask & 2u) ? 2.0 * cond[c - 1] * g : 0.0;
+    else { double a = cond[c - 1], b = cond[c]; v = g * (2.0 * a * b / (a + b)); }
+    fx[t] = v;
+    return;
+  }
+  t -= nfx;
+  if (t < nfy) {
+    int i = (int)(t % nx);
+    int64_t q = t / nx;
+    int j = (int)(q % (ny + 1));
+    int k = (int)(q / (ny + 1));
+    double g = (hx * hz) / hy;
+    int64_t c = ((int64_t)k * ny + j) * nx + i;
+    double v;
+    if (j == 0) v = (mask & 4u) ? 2.0 * cond[c] * g : 0.0;
+    else if (j == ny) v = (mask & 8u) ? 2.0 * cond[c - nx] * g : 0.0;
+    else { double a = cond[c - nx], b = cond[c]; v = g * (2.0 * a * b / (a + b)); }
+    fy[t] = v;
+    return;
+  }
+  t -= nfy;
+  if (t < nfz) {
+    int64_t sxy = (int64_t)nx * ny;
+    int64_t ij = t % sxy;
+    int k = (int)(t / sxy);
+    double g = (hx * hy) / hz;
+    int64_t c = (int64_t)k * sxy + ij;
+    double v;
+    if (k == 0) v = (mask & 16u) ? 2.0 * cond[c] * g : 0.0;
+    else if (k == nz) v = (mask & 32u) ? 2.0 * cond[c - sxy] * g : 0.0;
+    else { double a = cond[c - sxy], b = cond[c]; v = g * (2.0 * a * b / (a + b)); }
+    fz[t] = v;
+  }
+}
+
+// Coarse faces: (sum of the fine faces on the coarse face) / r_a; coarse mass:
+// sum of the children. One thread per coarse face / cell.
+__global__ void k_coarsen(LevelView<double> F, int rx, int ry, int rz, int cx_, int cy, int cz, double* fx,
+                          double* fy, double* fz, double* mm) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t nfx = (int64_t)(cx_ + 1) * cy * cz, nfy = (int64_t)cx_ * (cy + 1) * cz;
+  int64_t nfz = cz > 1 || F.nz > 1 ? (int64_t)cx_ * cy * (cz + 1) : 0;
+  int64_t ncell = (int64_t)cx_ * cy * cz;
+  if (t < nfx) {
+    int I = (int)(t % (cx_ + 1));
+    int64_t q = t / (cx_ + 1);
+    int J = (int)(q % cy), K = (int)(q / cy);
+    double s = 0.0;
+    for (int c = 0; c < rz; ++c)
+      for (int b = 0; b < ry; ++b) {
+        int64_t row = (int64_t)(rz * K + c) * F.ny + (ry * J + b);
+        s += F.fx[row * (F.nx + 1) + (int64_t)rx * I];
+      }
+    fx[t] = s / rx;
+    return;
+  }
+  t -= nfx;
+  if (t < nfy) {
+    int I = (int)(t % cx_);
+    int64_t q = t / cx_;
+    int J = (int)(q % (cy + 1)), K = (int)(q / (cy + 1));
+    double s = 0.0;
+    for (int c = 0; c < rz; ++c)
+      for (int a = 0; a < rx; ++a)
+        s += F.fy[((int64_t)(rz * K + c) * (F.ny + 1) + (int64_t)ry * J) * F.nx + (rx * I + a)];
+    fy[t] = s / ry;
+    return;
+  }
+  t -= nfy;
+  if (t < nfz) {
+    int64_t sxy = (int64_t)cx_ * cy;
+    int64_t ij = t % sxy;
+    int K = (int)(t / sxy);
+    int I = (int)(ij % cx_), J = (int)(ij / cx_);
+    double s = 0.0;
+    for (int b = 0; b < ry; ++b)
+      for (int a = 0; a < rx; ++a)
+        s += F.fz[((int64_t)rz * K * F.ny + (ry * J + b)) * F.nx + (rx * I + a)];
+    fz[t] = s / rz;
+    return;
+  }
+  t -= nfz;
+  if (t < ncell) {
+    int I = (int)(t % cx_);
+    int64_t q = t / cx_;
+    int J = (int)(q % cy), K = (int)(q / cy);
+    double s = 0.0;
+    for (int c = 0; c < rz; ++c)
+      for (int b = 0; b < ry; ++b)
+        for (int a = 0; a < rx; ++a)
+          s += F.mm[((int64_t)(rz * K + c) * F.ny + (ry * J + b)) * F.nx + (rx * I + a)];
+    mm[t] = s;
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+
+// 1 / (K_cc + tau M_cc) per cell for every distinct tau, computed in fp64.
+template <typename T>
+__global__ void k_invd(LevelView<double> L, const z64* __restrict__ taus, int ntau, cx<T>* __restrict__ out) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  Cell p = cell_of(c, L.nx, L.ny);
+  Faces<double> f = faces_at(L, p);
+  double d = fsum(f), m = L.mm[c];
+  for (int q = 0; q < ntau; ++q) {
+    z64 D = mk(d + taus[q].re * m, taus[q].im * m);
+    double den = abs2(D);
+    out[(int64_t)q * L.n + c] = cvt<T>(mk(D.re / den, -D.im / den));
+  }
+}
+
+// Dense coarsest-level matrix K + tau M (row-major, n x n) for every tau.
+__global__ void k_coarse_dense(LevelView<double> L, const z64* __restrict__ taus, int ntau, z64* __restrict__ A) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  Cell p = cell_of(c, L.nx, L.ny);
+  Faces<double> f = faces_at(L, p);
+  double d = fsum(f), m = L.mm[c];
+  int64_t n = L.n, sxy = (int64_t)L.nx * L.ny;
+  for (int q = 0; q < ntau; ++q) {
+    z64* row = A + (int64_t)q * n * n + c * n;
+    for (int64_t l = 0; l < n; ++l) row[l] = mk(0.0, 0.0);
+    row[c] = mk(d + taus[q].re * m, taus[q].im * m);
+    if (p.i > 0) row[c - 1] = mk(-f.xl, 0.0);
+    if (p.i < L.nx - 1) row[c + 1] = mk(-f.xh, 0.0);
+    if (p.j > 0) row[c - L.nx] = mk(-f.yl, 0.0);
+    if (p.j < L.ny - 1) row[c + L.nx] = mk(-f.yh, 0.0);
+    if (L.nz > 1) {
+      if (p.k > 0) row[c - sxy] = mk(-f.zl, 0.0);
+      if (p.k < L.nz - 1) row[c + sxy] = mk(-f.zh, 0.0);
+    }
+  }
+}
+
+// --------------------------------------------------------------------- apply
+// y = (K + s M) x; the shift is `s` or, with `st`, taus[st[slot].tau].
+template <typename T>
+__global__ void k_apply(LevelView<T> L, z64 s_fixed, const SlotState* st, const z64* taus,
+                        const cx<T>* __restrict__ x, cx<T>* __restrict__ y, int64_t vs) {
+  int slot = blockIdx.y;
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  z64 s = st ? taus[st[slot].tau] : s_fixed;
+  Cell p = cell_of(c, L.nx, L.ny);
+  y[slot * vs + c] = apply_at(L, p, c, cvt<T>(s), x + slot * vs);
+}
+
+// --------------------------------------------------------------------- smoother
+// One red-black Gauss-Seidel half sweep on the cells of `color`
+// (color 0 = red: i + j + k even): z_c = (f_c + sum_nb t z_nb) / (K_cc + tau M_cc).
+// `zero_start`: the other colour is taken as zero (first sweep from z = 0).
+template <typename T>
+__global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+                     const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs, int color, int zero_start) {
+  int slot = blockIdx.y;
+  if (!slot_running(st, slot)) return;
+  int nxh = (L.nx + 1) >> 1;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t rows = (int64_t)L.ny * L.nz;
+  if (t >= (int64_t)nxh * rows) return;
+  int64_t row = t / nxh;
+  int j = (int)(row % L.ny), k = (int)(row / L.ny);
+  int i = 2 * (int)(t % nxh) + ((j + k + color) & 1);
+  if (i >= L.nx) return;
+  Cell p{i, j, k};
+  int64_t c = row * L.nx + i;
+  const cx<T>* fs = f + slot * vs;
+  cx<T>* zs = z + slot * vs;
+  cx<T> id = invd[(int64_t)st[slot].tau * L.n + c];
+  cx<T> rhs = fs[c];
+  if (!zero_start) {
+    Faces<T> fc = faces_at(L, p);
+    rhs = rhs + nb_sum(L, fc, p, c, zs);
+  }
+  zs[c] = id * rhs;
+}
+
+// --------------------------------------------------------------------- transfer
+// Coarse right-hand side = sum over the children of the fine residual f - A z.
+template <typename T>
+__global__ void k_residual_restrict(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz,
+                                    const SlotState* st, const z64* taus, const cx<T>* __restrict__ f,
+                                    const cx<T>* __restrict__ z, int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
+  int slot = blockIdx.y;
+  if (!slot_running(st, slot)) return;
+  int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t ncoarse = (int64_t)cnx * cny * cnz;
+  if (C >= ncoarse) return;
+  int I = (int)(C % cnx);
+  int64_t q = C / cnx;
+  int J = (int)(q % cny), K = (int)(q / cny);
+  cx<T> s = cvt<T>(taus[st[slot].tau]);
+  const cx<T>* fs = f + slot * vs;
+  const cx<T>* zs = z + slot * vs;
+  cx<T> acc = mk(T(0), T(0));
+  for (int c = 0; c < rz; ++c)
+    for (int b = 0; b < ry; ++b)
+      for (int a = 0; a < rx; ++a) {
+        Cell p{rx * I + a, ry * J + b, rz * K + c};
+        int64_t cc = ((int64_t)p.k * F.ny + p.j) * F.nx + p.i;
+        acc = acc + (fs[cc] - apply_at(F, p, cc, s, zs));
+      }
+  fc[slot * vsc + C] = acc;
+}
+
+// z_fine += P z_coarse, cell-centred (bi/tri)linear interpolation: per coarsened
+// axis weight 3/4 on the parent and 1/4 on the coarse neighbour on the child's
+// side; past a zero-head face the ghost is -parent (weight 1/2 on the parent),
+// past a no-flow face it is +parent (weight 1).
+template <typename T>
+__global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz, uint32_t mask,
+                              const SlotState* st, const cx<T>* __restrict__ zc, int64_t vsc,
+                              cx<T>* __restrict__ z, int64_t vs) {
+  int slot = blockIdx.y;
+  if (!slot_running(st, slot)) return;
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= F.n) return;
+  Cell p = cell_of(c, F.nx, F.ny);
+  int par[3] = {p.i / rx, p.j / ry, p.k / rz};
+  int idx[3] = {p.i, p.j, p.k};
+  int rr[3] = {rx, ry, rz};
+  int nn[3] = {cnx, cny, cnz};
+  // per axis: two (index, weight) taps
+  int ti[3][2];
+  T tw[3][2];
+  for (int a = 0; a < 3; ++a) {
+    ti[a][0] = par[a];
+    ti[a][1] = par[a];
+    if (rr[a] == 1) {
+      tw[a][0] = T(1);
+      tw[a][1] = T(0);
+      continue;
+    }
+    int nb = (idx[a] & 1) ? par[a] + 1 : par[a] - 1;
+    if (nb >= 0 && nb < nn[a]) {
+      tw[a][0] = T(0.75);
+      ti[a][1] = nb;
+      tw[a][1] = T(0.25);
+    } else {
+      bool dir = nb < 0 ? ((mask >> (2 * a)) & 1u) : ((mask >> (2 * a + 1)) & 1u);
+      tw[a][0] = dir ? T(0.5) : T(1);
+      tw[a][1] = T(0);
+    }
+  }
+  const cx<T>* zcs = zc + slot * vsc;
+  cx<T> acc = mk(T(0), T(0));
+  for (int c2 = 0; c2 < 2; ++c2) {
+    T wz = tw[2][c2];
+    if (wz == T(0)) continue;
+    for (int b = 0; b < 2; ++b) {
+      T wy = tw[1][b];
+      if (wy == T(0)) continue;
+      for (int a = 0; a < 2; ++a) {
+        T wx = tw[0][a];
+        if (wx == T(0)) continue;
+        int64_t cc = ((int64_t)ti[2][c2] * cny + ti[1][b]) * cnx + ti[0][a];
+        acc = acc + (wx * wy * wz) * zcs[cc];
+      }
+    }
+  }
+  cx<T>* zs = z + slot * vs;
+  zs[c] = zs[c] + acc;
+}
+
+// --------------------------------------------------------------------- coarsest
+// Gauss-Jordan inversion with partial pivoting of one n x n complex matrix per
+// block (blockIdx.x = tau index), in place on A (row-major) with the inverse
+// written to Ainv. n <= MAX_COARSE.
+__global__ void k_gauss_jordan(z64* A, z64* Ainv, int n, int* singular) {
+  z64* a = A + (int64_t)blockIdx.x * n * n;
+  z64* inv = Ainv + (int64_t)blockIdx.x * n * n;
+  __shared__ int piv;
+  __shared__ double best[1024];
+  __shared__ int besti[1024];
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x)
+    inv[t] = (t / n == t % n) ? mk(1.0, 0.0) : mk(0.0, 0.0);
+  __syncthreads();
+  for (int col = 0; col < n; ++col) {
+    double bv = -1.0;
+    int bi = col;
+    for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
+      double v = abs2(a[(int64_t)r * n + col]);
+      if (v > bv) { bv = v; bi = r; }
+    }
+    best[threadIdx.x] = bv;
+    besti[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        double o = best[threadIdx.x + s];
+        int oi = besti[threadIdx.x + s];
+        if (o > best[threadIdx.x] || (o == best[threadIdx.x] && oi < besti[threadIdx.x])) {
+          best[threadIdx.x] = o;
+          besti[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      piv = besti[0];
+      if (!(best[0] > 0.0)) *singular = 1;
+    }
+    __syncthreads();
+    int pr = piv;
+    if (pr != col) {
+      for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        z64 t1 = a[(int64_t)pr * n + l];
+        a[(int64_t)pr * n + l] = a[(int64_t)col * n + l];
+        a[(int64_t)col * n + l] = t1;
+        z64 t2 = inv[(int64_t)pr * n + l];
+        inv[(int64_t)pr * n + l] = inv[(int64_t)col * n + l];
+        inv[(int64_t)col * n + l] = t2;
+      }
+    }
+    __syncthreads();
+    z64 d = a[(int64_t)col * n + col];
+    double den = abs2(d);
+    z64 rd = den > 0.0 ? mk(d.re / den, -d.im / den) : mk(0.0, 0.0);
+    __syncthreads();
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      a[(int64_t)col * n + l] = rd * a[(int64_t)col * n + l];
+      inv[(int64_t)col * n + l] = rd * inv[(int64_t)col * n + l];
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+      int r = (int)(t / n), l = (int)(t % n);
+      if (r == col) continue;
+      z64 fct = a[(int64_t)r * n + col];
+      if (l != col) {
+        a[t] = a[t] - fct * a[(int64_t)col * n + l];
+      }
+      inv[t] = inv[t] - fct * inv[(int64_t)col * n + l];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      if (r != col) a[(int64_t)r * n + col] = mk(0.0, 0.0);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_to_prec(const z64* __restrict__ a, cx<T>* __restrict__ b, int64_t n) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = cvt<T>(a[t]);
+}
+
+// z = Ainv[tau] f on the coarsest level, one row per thread.
+template <typename T>
+__global__ void k_coarse_solve(const cx<T>* __restrict__ Ainv, int n, const SlotState* st,
+                               const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs) {
+  int slot = blockIdx.y;
+  if (!slot_running(st, slot)) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const cx<T>* a = Ainv + ((int64_t)st[slot].tau * n + r) * n;
+  const cx<T>* fs = f + slot * vs;
+  cx<T> acc = mk(T(0), T(0));
+  for (int l = 0; l < n; ++l) acc = acc + a[l] * fs[l];
+  z[slot * vs + r] = acc;
+}
+
+// --------------------------------------------------------------------- defect correction
+// z += e (first cycle: z = e), z in fp64, e in the cycle precision.
+template <typename T>
+__global__ void k_correct(const SlotState* st, cx<double>* __restrict__ z, int64_t zs, int64_t zcol,
+                          const cx<T>* __restrict__ e, int64_t es, int64_t n) {
+  int slot = blockIdx.y;
+  if (!slot_running(st, slot)) return;
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  z64 ev = cvt<double>(e[slot * es + c]);
+  z64* zp = z + slot * zs + (int64_t)(st[slot].k - 1) * zcol + c;
+  *zp = st[slot].cycles == 0 ? ev : (*zp + ev);
+}
+
+// r = v - (K + tau M) z in fp64; f0 = r in the cycle precision; per-block
+// partial sums of |r|^2 (and |v|^2 when `with_v`).
+template <typename T>
+__global__ void k_defect(LevelView<double> L, const SlotState* st, const z64* taus, const z64* __restrict__ v,
+                         int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col, int zero_z,
+                         cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v) {
+  int slot = blockIdx.y;
+  __shared__ double red[2][32];
+  bool run = slot_running(st, slot);
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double r2 = 0.0, v2 = 0.0;
+  if (run && c < L.n) {
+    int64_t off = (int64_t)(st[slot].k - 1) * col;
+    z64 vv = v[slot * vsv + off + c];
+    z64 r = vv;
+    if (!zero_z) {
+      Cell p = cell_of(c, L.nx, L.ny);
+      r = vv - apply_at(L, p, c, taus[st[slot].tau], z + slot * vsz + off);
+    }
+    f0[slot * vsf + c] = cvt<T>(r);
+    r2 = abs2(r);
+    v2 = abs2(vv);
+  }
+  if (!run) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[0][w] = r2; red[1][w] = v2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; b += red[1][q]; }
+    partial[((int64_t)slot * gridDim.x + blockIdx.x) * 2 + 0] = a;
+    partial[((int64_t)slot * gridDim.x + blockIdx.x) * 2 + 1] = b;
+  }
+}
+
+// Sum the per-block partials in a fixed order and decide whether the inner
+// solve of each slot is finished.
+__global__ void k_inner_decide(SlotState* st, int nslot, const double* __restrict__ partial, int nblocks,
+                               int first, double eps, int max_cycles, const int32_t* replay_cycles, int m_max) {
+  int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslot) return;
+  SlotState& s = st[slot];
+  if (!s.active || s.inner_done) return;
+  double a = 0.0, b = 0.0;
+  for (int q = 0; q < nblocks; ++q) {
+    a += partial[((int64_t)slot * nblocks + q) * 2 + 0];
+    b += partial[((int64_t)slot * nblocks + q) * 2 + 1];
+  }
+  s.pnorm2 = a;
+  if (first) {
+    s.vnorm2 = b;
+    s.cycles = 0;
+  } else {
+    s.cycles += 1;
+  }
+  bool done;
+  if (replay_cycles) done = s.cycles >= replay_cycles[(int64_t)slot * m_max + (s.k - 1)];
+  else if (first) done = false;
+  else {
+    done = a <= eps * eps * s.vnorm2 || s.cycles >= max_cycles;
+    if (!(a <= eps * eps * s.vnorm2) && s.cycles >= max_cycles) s.inner_capped = 1;
+  }
+  s.inner_done = done ? 1 : 0;
+}
+
+// --------------------------------------------------------------------- launchers
+static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond,
+                            cudaStream_t s) {
+  int64_t tot = face_count(L, 0) + face_count(L, 1) + (L.nz > 1 ? face_count(L, 2) : 0);
+  k_faces_from_cond<<<nb(tot, 256), 256, 0, s>>>(L.nx, L.ny, L.nz, h[0], h[1], h[2], mask, cond, L.d64[0],
+                                                  L.d64[1], L.d64[2]);
+}
+
+void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s) {
+  int64_t tot = face_count(C, 0) + face_count(C, 1) + (C.nz > 1 || F.nz > 1 ? face_count(C, 2) : 0) + C.n;
+  k_coarsen<<<nb(tot, 256), 256, 0, s>>>(view<double>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, C.d64[0], C.d64[1],
+                                          C.d64[2], C.d64[3]);
+}
+
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  k_to_f32<<<nb(n, 256), 256, 0, s>>>(a, b, n);
+}
+
+template <typename T>
+void launch_invd(const LevelHost& L, const z64* taus, int ntau, cx<T>* out, cudaStream_t s) {
+  k_invd<T><<<nb(L.n, 256), 256, 0, s>>>(view<double>(L), taus, ntau, out);
+}
+
+void launch_coarse_inverse(const LevelHost& L, const z64* taus, int ntau, z64* work, z64* inv, int* singular,
+                           cudaStream_t s) {
+  k_coarse_dense<<<nb(L.n, 128), 128, 0, s>>>(view<double>(L), taus, ntau, work);
+  k_gauss_jordan<<<ntau, 1024, 0, s>>>(work, inv, (int)L.n, singular);
+}
+
+template <typename T>
+void launch_to_prec(const z64* a, cx<T>* b, int64_t n, cudaStream_t s) {
+  k_to_prec<T><<<nb(n, 256), 256, 0, s>>>(a, b, n);
+}
+
+template <typename T>
+void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* taus, const cx<T>* x, cx<T>* y,
+                  int64_t vs, int nslot, cudaStream_t s) {
+  dim3 g(nb(L.n, 256), nslot);
+  k_apply<T><<<g, 256, 0, s>>>(view<T>(L), sfix, st, taus, x, y, vs);
+}
+
+template <typename T>
+void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
+               int nslot, int color, int zero_start, cudaStream_t s) {
+  int64_t work = (int64_t)((L.nx + 1) / 2) * L.ny * L.nz;
+  dim3 g(nb(work, 256), nslot);
+  k_gs<T><<<g, 256, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, zero_start);
+}
+
+template <typename T>
+void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
+                              const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
+                              cudaStream_t s) {
+  dim3 g(nb(C.n, 256), nslot);
+  k_residual_restrict<T><<<g, 256, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
+                                           vsc);
+}
+
+template <typename T>
+void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* zc,
+                        int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s) {
+  dim3 g(nb(F.n, 256), nslot);
+  k_prolong_add<T><<<g, 256, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, mask, st, zc, vsc, z, vs);
+}
+
+template <typename T>
+void launch_coarse_solve(const cx<T>* Ainv, int n, const SlotState* st, const cx<T>* f, cx<T>* z, int64_t vs,
+                         int nslot, cudaStream_t s) {
+  dim3 g(nb(n, 128), nslot);
+  k_coarse_solve<T><<<g, 128, 0, s>>>(Ainv, n, st, f, z, vs);
+}
+
+template <typename T>
+void launch_correct(const SlotState* st, z64* z, int64_t zs, int64_t zcol, const cx<T>* e, int64_t es, int64_t n,
+                    int nslot, cudaStream_t s) {
+  dim3 g(nb(n, 256), nslot);
+  k_correct<T><<<g, 256, 0, s>>>(st, z, zs, zcol, e, es, n);
+}
+
+int defect_blocks(int64_t n) { return (int)nb(n, 256); }
+
+template <typename T>
+void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
+                   int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
+                   int nslot, cudaStream_t s) {
+  dim3 g(nb(L.n, 256), nslot);
+  k_defect<T><<<g, 256, 0, s>>>(view<double>(L), st, taus, v, vsv, z, vsz, col, zero_z, f0, vsf, partial, with_v);
+}
+
+void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
+                         int max_cycles, const int32_t* replay_cycles, int m_max, cudaStream_t s) {
+  k_inner_decide<<<nb(nslot, 64), 64, 0, s>>>(st, nslot, partial, nblocks, first, eps, max_cycles, replay_cycles,
+                                                m_max);
+}
+
+#define INST(T)                                                                                                  \
+  template void launch_invd<T>(const LevelHost&, const z64*, int, cx<T>*, cudaStream_t);                          \
+  template void launch_to_prec<T>(const z64*, cx<T>*, int64_t, cudaStream_t);                                     \
+  template void launch_apply<T>(const LevelHost&, z64, const SlotState*, const z64*, const cx<T>*, cx<T>*, int64_t, \
+                                int, cudaStream_t);                                                               \
+  template void launch_gs<T>(const LevelHost&, const SlotState*, const cx<T>*, const cx<T>*, cx<T>*, int64_t, int,  \
+                             int, int, cudaStream_t);                                                             \
+  template void launch_residual_restrict<T>(const LevelHost&, const LevelHost&, const SlotState*, const z64*,      \
+                                            const cx<T>*, const cx<T>*, int64_t, cx<T>*, int64_t, int,           \
+                                            cudaStream_t);                                                        \
+  template void launch_prolong_add<T>(const LevelHost&, const LevelHost&, uint32_t, const SlotState*,             \
+                                      const cx<T>*, int64_t, cx<T>*, int64_t, int, cudaStream_t);                 \
+  template void launch_coarse_solve<T>(const cx<T>*, int, const SlotState*, const cx<T>*, cx<T>*, int64_t, int,    \
+                                       cudaStream_t);                                                             \
+  template void launch_correct<T>(const SlotState*, z64*, int64_t, int64_t, const cx<T>*, int64_t, int64_t, int,  \
+                                  cudaStream_t);                                                                  \
+  template void launch_defect<T>(const LevelHost&, const SlotState*, const z64*, const z64*, int64_t, const z64*,  \
+                                 int64_t, int64_t, int, cx<T>*, int64_t, double*, int, int, cudaStream_t);
+
+INST(double)
+INST(float)
+
+}  // namespace fks

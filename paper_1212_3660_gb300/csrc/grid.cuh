@@ -1,0 +1,43 @@
+// Launchers of the structured-grid and multigrid kernels (grid.cu).
+#pragma once
+#include "common.cuh"
+
+namespace fks {
+
+void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond, cudaStream_t s);
+void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s);
+void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_invd(const LevelHost& L, const z64* taus, int ntau, cx<T>* out, cudaStream_t s);
+void launch_coarse_inverse(const LevelHost& L, const z64* taus, int ntau, z64* work, z64* inv, int* singular,
+                           cudaStream_t s);
+template <typename T>
+void launch_to_prec(const z64* a, cx<T>* b, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* taus, const cx<T>* x, cx<T>* y,
+                  int64_t vs, int nslot, cudaStream_t s);
+template <typename T>
+void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
+               int nslot, int color, int zero_start, cudaStream_t s);
+template <typename T>
+void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
+                              const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
+                              cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* zc,
+                        int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s);
+template <typename T>
+void launch_coarse_solve(const cx<T>* Ainv, int n, const SlotState* st, const cx<T>* f, cx<T>* z, int64_t vs,
+                         int nslot, cudaStream_t s);
+template <typename T>
+void launch_correct(const SlotState* st, z64* z, int64_t zs, int64_t zcol, const cx<T>* e, int64_t es, int64_t n,
+                    int nslot, cudaStream_t s);
+int defect_blocks(int64_t n);
+template <typename T>
+void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
+                   int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
+                   int nslot, cudaStream_t s);
+void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
+                         int max_cycles, const int32_t* replay_cycles, int m_max, cudaStream_t s);
+
+}  // namespace fks

@@ -1,0 +1,201 @@
+"""ctypes binding of libfks.so (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of the method: arrays are passed by pointer (numpy arrays on the
+host, torch tensors on the host or the GPU), results come back in the
+caller's arrays. The library must have been built (paper_1212_3660_gb300.build);
+loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfks.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "fks.h")
+
+FKS_OK, FKS_NOT_CONVERGED, FKS_BREAKDOWN_EXACT, FKS_INNER_NOT_CONVERGED = 0, 1, 2, 3
+FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1, -2, -3, -4, -5
+FKS_FGMRES, FKS_FFOM = 0, 1
+FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
+
+
+class fks_c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class fks_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("m_max", C.c_int), ("variant", C.c_int), ("precision", C.c_int),
+                ("inner_tol", C.c_double), ("inner_max_cycles", C.c_int),
+                ("tau_schedule", C.POINTER(C.c_int32)), ("sched_len", C.c_int),
+                ("replay_mode", C.c_int), ("replay_inner_cycles", C.POINTER(C.c_int32)),
+                ("replay_mj", C.POINTER(C.c_int32))]
+
+
+class fks_info(C.Structure):
+    _fields_ = [("steps", C.POINTER(C.c_int32)), ("inner_cycles", C.POINTER(C.c_int32)),
+                ("pnorm", C.POINTER(C.c_double)), ("breakdown", C.POINTER(C.c_int32))]
+
+
+class FksError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fks status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Names of the functions declared in include/fks.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fks_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1212_3660_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32p, f64p = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    L.fks_last_error.restype = C.c_char_p
+    L.fks_version.restype = C.c_char_p
+    L.fks_create.argtypes = [C.POINTER(vp), C.c_int]
+    L.fks_destroy.argtypes = [vp]
+    L.fks_destroy.restype = None
+    L.fks_op_grid.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), vp, vp, C.c_uint32,
+                              C.POINTER(vp)]
+    L.fks_op_destroy.argtypes = [vp]
+    L.fks_op_destroy.restype = None
+    L.fks_op_size.argtypes = [vp]
+    L.fks_op_size.restype = C.c_int64
+    L.fks_solve.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp, C.c_int, C.POINTER(fks_options), vp, vp, vp, vp, vp,
+                            vp, C.POINTER(fks_info), vp]
+    L.fks_op_apply.argtypes = [vp, fks_c128, vp, vp, C.c_int, vp]
+    L.fks_precond_apply.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p, f64p, vp]
+    for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def fks_last_error() -> str:
+    return lib().fks_last_error().decode()
+
+
+def fks_version() -> str:
+    return lib().fks_version().decode()
+
+
+def fks_create(device: int = 0):
+    h = C.c_void_p()
+    st = lib().fks_create(C.byref(h), device)
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return h
+
+
+def fks_destroy(ctx) -> None:
+    lib().fks_destroy(ctx)
+
+
+def fks_op_grid(ctx, dim, ncell, h, cond, ss, dirichlet_mask):
+    """cond, ss: host float64 arrays of n cells (x fastest)."""
+    nc = (C.c_int64 * 3)(*[int(v) for v in (list(ncell) + [1, 1, 1])[:3]])
+    hh = (C.c_double * 3)(*[float(v) for v in (list(h) + [1.0, 1.0, 1.0])[:3]])
+    cond = np.ascontiguousarray(cond, dtype=np.float64).ravel()
+    ss = np.ascontiguousarray(ss, dtype=np.float64).ravel()
+    out = C.c_void_p()
+    st = lib().fks_op_grid(ctx, int(dim), nc, hh, _ptr(cond), _ptr(ss), int(dirichlet_mask), C.byref(out))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return out
+
+
+def fks_op_destroy(op) -> None:
+    lib().fks_op_destroy(op)
+
+
+def fks_op_size(op) -> int:
+    return int(lib().fks_op_size(op))
+
+
+def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP64, inner_tol=0.0,
+                 inner_max_cycles=50, schedule=(0,), replay_cycles=None, replay_mj=None):
+    """fks_options plus the arrays it points to (kept alive in the returned tuple)."""
+    sched = np.ascontiguousarray(schedule, dtype=np.int32)
+    o = fks_options()
+    o.tol, o.m_max, o.variant, o.precision = float(tol), int(m_max), int(variant), int(precision)
+    o.inner_tol, o.inner_max_cycles = float(inner_tol), int(inner_max_cycles)
+    o.tau_schedule = sched.ctypes.data_as(C.POINTER(C.c_int32))
+    o.sched_len = len(sched)
+    keep = [sched]
+    if replay_cycles is not None:
+        rc = np.ascontiguousarray(replay_cycles, dtype=np.int32)
+        rm = np.ascontiguousarray(replay_mj, dtype=np.int32)
+        o.replay_mode = 1
+        o.replay_inner_cycles = rc.ctypes.data_as(C.POINTER(C.c_int32))
+        o.replay_mj = rm.ctypes.data_as(C.POINTER(C.c_int32))
+        keep += [rc, rm]
+    return o, keep
+
+
+def fks_solve(op, b, n_rhs, sigma, n_f, tau, n_tau, options, X, res_est, res_bound, res_true, m_j, shift_status,
+              info=None, stream=None):
+    """Thin wrapper: every array argument is a numpy array or torch tensor; returns the status."""
+    st = lib().fks_solve(op, _ptr(b), int(n_rhs), _ptr(sigma), int(n_f), _ptr(tau), int(n_tau), C.byref(options),
+                         _ptr(X), _ptr(res_est), _ptr(res_bound), _ptr(res_true), _ptr(m_j), _ptr(shift_status),
+                         C.byref(info) if info is not None else None, stream)
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return st
+
+
+def fks_op_apply(op, s, x, y, n_vec, stream=None):
+    st = lib().fks_op_apply(op, fks_c128(complex(s).real, complex(s).imag), _ptr(x), _ptr(y), int(n_vec), stream)
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return st
+
+
+def fks_precond_apply(op, tau, v, z, eps, max_cycles=50, cycles=-1, precision=FKS_PREC_FP64, stream=None):
+    """Returns (status, cycles, ||p||)."""
+    oc = C.c_int32(0)
+    op_ = C.c_double(0.0)
+    st = lib().fks_precond_apply(op, fks_c128(complex(tau).real, complex(tau).imag), _ptr(v), _ptr(z), float(eps),
+                                 int(max_cycles), int(cycles), int(precision), C.byref(oc), C.byref(op_), stream)
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return st, int(oc.value), float(op_.value)
+
+
+def make_info(n_rhs, m_max):
+    arrs = dict(steps=np.zeros(n_rhs, np.int32), inner_cycles=np.zeros(n_rhs * m_max, np.int32),
+                pnorm=np.zeros(n_rhs * m_max, np.float64), breakdown=np.zeros(n_rhs, np.int32))
+    info = fks_info(arrs["steps"].ctypes.data_as(C.POINTER(C.c_int32)),
+                    arrs["inner_cycles"].ctypes.data_as(C.POINTER(C.c_int32)),
+                    arrs["pnorm"].ctypes.data_as(C.POINTER(C.c_double)),
+                    arrs["breakdown"].ctypes.data_as(C.POINTER(C.c_int32)))
+    return info, arrs

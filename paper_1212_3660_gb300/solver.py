@@ -1,0 +1,81 @@
+"""Convenience layer over the C ABI for synthetic problems (marshalling only).
+
+`Solver` owns a context and a grid operator built from a synth.Problem and
+calls fks_solve with numpy (host) or torch (device) buffers. It contains no
+arithmetic of the method: every step runs in libfks.so.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import fks
+
+
+@dataclasses.dataclass
+class SolveOutput:
+    status: int
+    X: object            # n_rhs x n_f x n (numpy or torch)
+    res_est: np.ndarray  # n_rhs x n_f
+    res_bound: np.ndarray
+    res_true: np.ndarray
+    m_j: np.ndarray
+    shift_status: np.ndarray
+    steps: np.ndarray
+    inner_cycles: np.ndarray  # n_rhs x m_max
+    pnorm: np.ndarray
+    breakdown: np.ndarray
+
+
+class Solver:
+    def __init__(self, problem, device: int = 0):
+        self.p = problem
+        self.ctx = fks.fks_create(device)
+        d = problem.dim
+        ncell = [problem.shape[d - 1 - a] for a in range(d)]
+        self.op = fks.fks_op_grid(self.ctx, d, ncell, problem.h, problem.cond, problem.ss, problem.dirichlet_mask)
+
+    def close(self):
+        if self.op is not None:
+            fks.fks_op_destroy(self.op)
+            self.op = None
+        if self.ctx is not None:
+            fks.fks_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b=None, *, precision=fks.FKS_PREC_FP64, variant=fks.FKS_FGMRES, tol=None, m_max=None,
+              inner_tol=0.0, inner_max_cycles=50, replay_cycles=None, replay_mj=None, device_out=False,
+              stream=None, sigma=None, tau=None, schedule=None):
+        p = self.p
+        b = p.rhs().T.copy() if b is None else b            # n_rhs x n
+        n_rhs = b.shape[0]
+        sigma = np.ascontiguousarray(p.sigma if sigma is None else sigma, dtype=np.complex128)
+        tau = np.ascontiguousarray(p.tau_bar if tau is None else tau, dtype=np.complex128)
+        sched = p.schedule if schedule is None else schedule
+        m_max = p.m_max if m_max is None else m_max
+        n_f = len(sigma)
+        opts, keep = fks.make_options(tol=p.tol if tol is None else tol, m_max=m_max, variant=variant,
+                                      precision=precision, inner_tol=inner_tol, inner_max_cycles=inner_max_cycles,
+                                      schedule=sched, replay_cycles=replay_cycles, replay_mj=replay_mj)
+        if device_out:
+            import torch
+            X = torch.empty((n_rhs, n_f, p.n), dtype=torch.complex128, device="cuda")
+        else:
+            X = np.zeros((n_rhs, n_f, p.n), dtype=np.complex128)
+        est = np.zeros((n_rhs, n_f))
+        bnd = np.zeros((n_rhs, n_f))
+        tru = np.zeros((n_rhs, n_f))
+        mj = np.zeros((n_rhs, n_f), np.int32)
+        sst = np.zeros((n_rhs, n_f), np.int32)
+        info, arr = fks.make_info(n_rhs, m_max)
+        st = fks.fks_solve(self.op, b, n_rhs, sigma, n_f, tau, len(tau), opts, X, est, bnd, tru, mj, sst, info,
+                           stream)
+        return SolveOutput(st, X, est, bnd, tru, mj, sst, arr["steps"], arr["inner_cycles"].reshape(n_rhs, m_max),
+                           arr["pnorm"].reshape(n_rhs, m_max), arr["breakdown"])

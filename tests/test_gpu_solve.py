@@ -1,0 +1,157 @@
+"""GPU parity of the whole flexible shifted solve against the oracle.
+
+Replay protocol: the oracle's inner-cycle counts and freeze steps m_j are fed
+to the GPU (replay mode), so both sides execute the same sequence of
+operations and differ only by rounding; every x_j must then agree to 1e-8
+relative (complex128 path). Free-running solves are checked by the true
+residual, recomputed on the CPU with the oracle's operator.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1212_3660_gb300 import fks, synth
+from paper_1212_3660_gb300.solver import Solver
+
+from gpu_util import need_gpu, oracle_run, replay_arrays, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(shape=(64, 64), n_f=10, periods=(10.0, 1000.0), n_p=1, seed=1),            # 64x64 workload
+    dict(shape=(40, 24), n_f=7, periods=(5.0, 3600.0), n_p=3, seed=8),               # ragged, 3 taus
+    dict(shape=(16, 16, 16), n_f=6, periods=(5.0, 3600.0), n_p=2, seed=9),           # 3D
+    dict(shape=(12, 20, 10), n_f=5, periods=(5.0, 3600.0), n_p=4, seed=10, corr_frac=(0.2, 0.2, 0.05),
+         ss_var=0.25),                                                               # aniso + lognormal S_s
+    dict(shape=(30, 18), n_f=4, periods=(10.0, 1000.0), n_p=2, seed=12, dirichlet_mask=0b0011),  # no-flow y
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c["shape"])))
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_replay_parity(case, precision):
+    need_gpu()
+    pr = synth.make_problem(m_max=80, **case)
+    eps = 1e-10
+    op, ref = oracle_run(pr, eps)
+    rc, mj = replay_arrays(pr, [ref])
+    s = Solver(pr)
+    out = s.solve(inner_tol=eps, precision=precision, replay_cycles=rc, replay_mj=mj)
+    assert out.status in (fks.FKS_OK, fks.FKS_NOT_CONVERGED)
+    assert np.array_equal(out.m_j[0], ref.m_j)
+    assert int(out.steps[0]) == ref.steps
+    tol = 1e-8 if precision == fks.FKS_PREC_FP64 else 1e-6
+    for j in range(len(pr.sigma)):
+        assert rel_err(out.X[0, j], ref.x[:, j]) <= tol, j
+    # the GPU's own true residual equals the oracle's recomputation
+    tr = oracle.true_residuals(op, pr.rhs()[:, 0], pr.sigma, out.X[0].T)
+    assert np.allclose(out.res_true[0], tr, rtol=1e-6, atol=1e-15)
+    assert np.allclose(out.res_bound[0], ref.res_bound, rtol=1e-5, atol=1e-4 * pr.tol)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_free_running_reaches_tolerance(precision):
+    need_gpu()
+    pr = synth.workload(1)
+    s = Solver(pr)
+    out = s.solve(precision=precision, inner_tol=1e-10)
+    assert out.status == fks.FKS_OK
+    op, ref = oracle_run(pr, 1e-10)
+    tr = oracle.true_residuals(op, pr.rhs()[:, 0], pr.sigma, out.X[0].T)
+    assert np.all(tr <= pr.tol * 1.0001)
+    assert np.all(out.res_bound[0] <= pr.tol)
+    assert np.all(tr <= out.res_bound[0] * (1 + 1e-6))              # Eq. trueresidual holds
+    # free-running vs oracle: within kappa * tol, reported not gated at 1e-8
+    for j in range(len(pr.sigma)):
+        assert rel_err(out.X[0, j], ref.x[:, j]) <= 1e-5
+    s.close()
+
+
+def test_multiple_sources_are_independent_processes():
+    need_gpu()
+    pr = synth.make_problem((32, 32), n_f=5, periods=(5.0, 3600.0), n_p=2, seed=14, n_src=3, m_max=60)
+    eps = 1e-10
+    refs = [oracle_run(pr, eps, src=r)[1] for r in range(3)]
+    rc, mj = replay_arrays(pr, refs)
+    s = Solver(pr)
+    out = s.solve(inner_tol=eps, replay_cycles=rc, replay_mj=mj)
+    for r in range(3):
+        for j in range(len(pr.sigma)):
+            assert rel_err(out.X[r, j], refs[r].x[:, j]) <= 1e-8
+    # solo solve of source 1 gives the same result as inside the batch
+    b1 = pr.rhs().T[1:2].copy()
+    solo = s.solve(b=b1, inner_tol=eps, replay_cycles=rc[1:2], replay_mj=mj[1:2])
+    assert np.array_equal(solo.X[0], out.X[1])
+    s.close()
+
+
+def test_ffom_variant_replay():
+    need_gpu()
+    pr = synth.make_problem((24, 24), n_f=5, periods=(10.0, 1000.0), n_p=2, seed=15, m_max=60)
+    eps = 1e-10
+    op, ref = oracle_run(pr, eps, variant="ffom")
+    rc, mj = replay_arrays(pr, [ref])
+    s = Solver(pr)
+    out = s.solve(inner_tol=eps, variant=fks.FKS_FFOM, replay_cycles=rc, replay_mj=mj)
+    for j in range(len(pr.sigma)):
+        assert rel_err(out.X[0, j], ref.x[:, j]) <= 1e-8
+    s.close()
+
+
+def test_zero_rhs_gives_zero_solution():
+    need_gpu()
+    pr = synth.make_problem((16, 16), n_f=3, periods=(10.0, 1000.0), n_p=1, seed=2)
+    s = Solver(pr)
+    out = s.solve(b=np.zeros((1, pr.n), np.complex128))
+    assert out.status == fks.FKS_OK
+    assert np.all(out.X == 0) and np.all(out.m_j == 0)
+    s.close()
+
+
+def test_sigma_equal_tau_and_single_mode_converge_in_one_step():
+    need_gpu()
+    pr = synth.make_problem((20, 20), n_f=2, periods=(10.0, 1000.0), n_p=1, seed=2, homogeneous=True)
+    s = Solver(pr)
+    tau = pr.tau_bar
+    out = s.solve(sigma=np.array([tau[0], 0.5 * tau[0]]), inner_tol=1e-12)
+    assert out.m_j[0, 0] == 1
+    # one sine mode of the homogeneous box is an eigenvector of K and M: every
+    # shift is solved exactly from the first basis vector (Section 3, breakdown)
+    ii, jj = np.meshgrid(np.arange(1, 21), np.arange(1, 21), indexing="xy")
+    kx, ky = 3, 2
+    mode = (np.sin(np.pi * kx * (ii - 0.5) / 20) * np.sin(np.pi * ky * (jj - 0.5) / 20)).ravel()
+    k0, s0 = float(pr.cond.flat[0]), float(pr.ss.flat[0])
+    lam = k0 * (4 * np.sin(np.pi * kx / 40) ** 2 + 4 * np.sin(np.pi * ky / 40) ** 2)
+    out = s.solve(b=mode.astype(np.complex128)[None, :], inner_tol=1e-13)
+    assert np.all(out.m_j[0] == 1)
+    for j, sg in enumerate(pr.sigma):
+        x = mode / (lam + sg * s0 * np.prod(pr.h))
+        assert rel_err(out.X[0, j], x) <= 1e-9
+    s.close()
+
+
+def test_m_max_reached_reports_not_converged():
+    need_gpu()
+    pr = synth.make_problem((32, 32), n_f=4, periods=(5.0, 3600.0), n_p=2, seed=3)
+    s = Solver(pr)
+    out = s.solve(m_max=3, tol=1e-12)
+    assert out.status == fks.FKS_NOT_CONVERGED
+    assert np.all(out.m_j <= 3) and np.any(out.shift_status == 1)
+    s.close()
+
+
+def test_invalid_arguments_rejected_before_device_work():
+    need_gpu()
+    pr = synth.make_problem((16, 16), n_f=3, periods=(10.0, 1000.0), n_p=1, seed=2)
+    s = Solver(pr)
+    with pytest.raises(fks.FksError) as e:
+        s.solve(tol=-1.0)
+    assert e.value.status == fks.FKS_ERR_ARG
+    with pytest.raises(fks.FksError):
+        s.solve(schedule=[3])
+    with pytest.raises(fks.FksError):
+        s.solve(sigma=np.array([np.nan + 0j]))
+    with pytest.raises(fks.FksError):
+        fks.fks_op_grid(s.ctx, 2, (16, 16), (1.0, 1.0), -np.ones(256), np.ones(256), 0xF)
+    s.close()
