@@ -1,0 +1,344 @@
+"""Benchmark: shifted solves per second at 1e-8 true residual on one GB300.
+
+A step is one fks_solve of the whole workload: every frequency shift of every
+source through the flexible Arnoldi basis, the per-shift least squares, the
+assembly x_j = Z y_j and the true-residual check. A shifted solve counts when
+its complex128 true relative residual ||b - (K + sigma_j M) x_j|| / ||b|| <= 1e-8.
+
+Default workload: 2D 512 x 512 cell-centred aquifer (n = 262144), lnK Gaussian
+field (variance 1, correlation 0.2 L, mean ln 1e-4), S_s = 1e-5, centre source,
+200 shifts (periods 5..3600 s log-spaced), 3 preconditioner shifts cycled per
+step, multigrid inner solve, complex128 throughout.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload 1|2|3|4] [--precision fp64|mixed]
+
+Under torchrun every rank solves its own copy of the workload (replicas, weak
+scaling; no data-path collective). Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shifted solves/s at 1e-8 residual"
+UNIT = "shifted solves/s"
+TOL = 1e-8
+INNER_EPS = 1e-10          # inner tolerance of the accuracy-gated runs (tol / 100)
+# Flexible Arnoldi steps the default 512 x 512 workload takes to converge every
+# shift (oracle run, multigrid inner eps 1e-10); used to extrapolate the
+# bounded CPU sample to a whole solve.
+WORKLOAD_STEPS = {1: 36, 2: 36, 3: 40, 4: 40}
+FP64_PEAK_TFLOPS = 1.25    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=6)
+    ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(pr, sample_steps, workload_steps, eps):
+    """The oracle (complex128 NumPy/SciPy) on the first `sample_steps` flexible
+    Arnoldi steps of the workload, extrapolated linearly to the steps a whole
+    solve takes. Returns (solves/s, seconds, description)."""
+    import oracle
+    from oracle.gmg import Hierarchy, GMGInner
+    t0 = time.perf_counter()
+    op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+    hier = Hierarchy(op, pr.tau_bar)
+    b = pr.rhs()[:, 0]
+    res = oracle.shifted_solve(op, b, pr.sigma, pr.tau_bar, pr.schedule, 0.0, sample_steps, GMGInner(hier, eps))
+    dt = time.perf_counter() - t0
+    t_full = dt * workload_steps / max(res.steps, 1)
+    desc = (f"oracle setup + first {res.steps} of {workload_steps} flexible Arnoldi steps of the same workload "
+            f"({dt:.1f} s), scaled linearly to {workload_steps} steps")
+    return len(pr.sigma) * len(pr.src_cells) / t_full, dt, desc
+
+
+def blas_threads():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if k in os.environ:
+            return int(os.environ[k])
+    return 1
+
+
+def run_reference(args):
+    from paper_1212_3660_gb300 import synth
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    pr = synth.workload(args.workload, m_max=100)
+    ws = WORKLOAD_STEPS.get(args.workload, 40)
+    vals, secs = [], []
+    sample = None
+    for i in range(args.warmup + args.steps):
+        v, dt, sample = cpu_oracle_sample(pr, max(1, args.cpu_sample_steps // 3), ws, INNER_EPS)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(pr.sigma) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": pr.name, "grid": "x".join(map(str, pr.shape[::-1])), "n_f": len(pr.sigma)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1212_3660_gb300 import build, fks, synth
+    from paper_1212_3660_gb300.solver import Solver
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    pr = synth.workload(args.workload, m_max=100)
+    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    t_setup0 = time.perf_counter()
+    solver = Solver(pr, device=local)
+    setup_ms = 1000 * (time.perf_counter() - t_setup0)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    n, n_f, n_rhs = pr.n, len(pr.sigma), len(pr.src_cells)
+    b_d = torch.from_numpy(pr.rhs().T.copy()).to(dev)
+    sig_d = torch.from_numpy(pr.sigma.astype(np.complex128)).to(dev)
+    tau_d = torch.from_numpy(pr.tau_bar.astype(np.complex128)).to(dev)
+    X_d = torch.empty((n_rhs, n_f, n), dtype=torch.complex128, device=dev)
+    est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
+    mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
+    opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                  schedule=pr.schedule)
+    info, info_arr = fks.make_info(n_rhs, pr.m_max)
+
+    def step(b, X):
+        return fks.fks_solve(solver.op, b, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X, est, bnd, tru, mj,
+                             sst, info, sh)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step(b_d, X_d)
+    # kernel-class survey (stderr only) and choice of the dominant class
+    totals = {}
+    for c, name in enumerate(fks.KERNEL_CLASSES):
+        fks.fks_profile_select(solver.op, c)
+        step(b_d, X_d)
+        totals[name] = fks.fks_profile_read(solver.op)
+    fks.fks_profile_select(solver.op, None)
+    fks.fks_profile_read(solver.op)
+    dominant = max(totals, key=lambda k: totals[k]["ms"])
+    if args.survey and rank == 0:
+        tot = sum(v["ms"] for v in totals.values())
+        for k, v in sorted(totals.items(), key=lambda kv: -kv[1]["ms"]):
+            print(f"# {k:9s} launches {v['launches']:7d} ms {v['ms']:9.3f} ({100 * v['ms'] / max(tot, 1e-9):5.1f}%) "
+                  f"GB/s {v['bytes'] / max(v['ms'], 1e-9) / 1e6:8.1f} GFLOP/s {v['flops'] / max(v['ms'], 1e-9) / 1e6:8.1f}",
+                  file=sys.stderr)
+
+    # ---- timed region (device-resident inputs)
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    converged = 0
+    with ClockSampler(gpu_index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(b_d, X_d)
+            converged += int(np.sum(tru <= TOL))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = fks.fks_profile_read(solver.op)["all_launches"]
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms)
+    conv_per_step = converged / args.steps
+    value = sum_over_ranks(conv_per_step) / (ms_max / 1000.0)
+
+    # ---- roofline of the dominant kernel class (events on the library's stream)
+    fks.fks_profile_select(solver.op, dominant)
+    for _ in range(args.steps):
+        step(b_d, X_d)
+    prof = fks.fks_profile_read(solver.op)
+    fks.fks_profile_select(solver.op, None)
+    hbm_peak, bf16_peak, peak_src = peaks()
+    gbs = prof["bytes"] / max(prof["ms"], 1e-12) / 1e6
+    tfl = prof["flops"] / max(prof["ms"], 1e-12) / 1e9
+    f_hbm = gbs / hbm_peak
+    f_alu = tfl / FP64_PEAK_TFLOPS if prec == fks.FKS_PREC_FP64 or dominant in ("mdot", "maxpy", "assemble",
+                                                                                 "defect", "tres") else 0.0
+    if f_alu > f_hbm:
+        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
+                "traffic": None, "kernel": dominant, "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                "launches": prof["launches"], "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
+                "hbm_frac_of_" + peak_src: f_hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm, "traffic": None,
+                "kernel": dominant, "peak_source": peak_src, "launches": prof["launches"],
+                "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1)}
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    b_h = torch.from_numpy(pr.rhs().T.copy()).pin_memory()
+    X_h = torch.empty((n_rhs, n_f, n), dtype=torch.complex128).pin_memory()
+    step(b_h, X_h)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    conv_e2e = 0
+    for _ in range(args.steps):
+        step(b_h, X_h)
+        conv_e2e += int(np.sum(tru <= TOL))
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e_value = sum_over_ranks(conv_e2e / args.steps) / t_e2e
+    h2d = b_h.numel() * 16 + (n_f + len(pr.tau_bar)) * 16
+    d2h = X_h.numel() * 16 + n_rhs * n_f * (8 * 3 + 4 * 2)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ws = int(info_arr["steps"].max()) or WORKLOAD_STEPS.get(args.workload, 40)
+        v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS)
+        cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer",
+                "data": "synthetic",
+                "config": {"workload": pr.name, "grid": "x".join(map(str, pr.shape[::-1])), "n": n, "n_f": n_f,
+                           "n_p": len(pr.tau_bar), "schedule": "cycled", "sources_per_gpu": n_rhs,
+                           "inner": f"multigrid V(2,2) red-black GS, defect correction to eps={INNER_EPS:g}",
+                           "precision": args.precision, "parallelism": f"replicas{world}",
+                           "l2": "working set larger than L2 (basis V, Z: 2 x 101 x n x 16 B)",
+                           "arnoldi_steps": int(info_arr["steps"].max()),
+                           "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
+                           "op_setup_ms": setup_ms},
+                "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -22,6 +22,8 @@ FKS_OK, FKS_NOT_CONVERGED, FKS_BREAKDOWN_EXACT, FKS_INNER_NOT_CONVERGED = 0, 1, 
 FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1, -2, -3, -4, -5
 FKS_FGMRES, FKS_FFOM = 0, 1
 FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
+KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
+                  "assemble", "tres"]
 
 
 class fks_c128(C.Structure):
@@ -80,7 +82,10 @@ def lib():
                             vp, C.POINTER(fks_info), vp]
     L.fks_op_apply.argtypes = [vp, fks_c128, vp, vp, C.c_int, vp]
     L.fks_precond_apply.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p, f64p, vp]
-    for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply"):
+    L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
+    L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
+    for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
+                 "fks_profile_read"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -199,3 +204,22 @@ def make_info(n_rhs, m_max):
                     arrs["pnorm"].ctypes.data_as(C.POINTER(C.c_double)),
                     arrs["breakdown"].ctypes.data_as(C.POINTER(C.c_int32)))
     return info, arrs
+
+
+def fks_profile_select(op, kclass, level=-1):
+    """kclass: index or name in KERNEL_CLASSES (None / -1 stops timing)."""
+    if isinstance(kclass, str):
+        kclass = KERNEL_CLASSES.index(kclass)
+    st = lib().fks_profile_select(op, -1 if kclass is None else int(kclass), int(level))
+    if st < 0:
+        raise FksError(st, fks_last_error())
+
+
+def fks_profile_read(op):
+    """Returns dict(launches, ms, bytes, flops, all_launches) and resets the counters."""
+    la, al = C.c_int64(0), C.c_int64(0)
+    ms, by, fl = C.c_double(0), C.c_double(0), C.c_double(0)
+    st = lib().fks_profile_read(op, C.byref(la), C.byref(ms), C.byref(by), C.byref(fl), C.byref(al))
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return dict(launches=la.value, ms=ms.value, bytes=by.value, flops=fl.value, all_launches=al.value)
