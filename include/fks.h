@@ -153,6 +153,28 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
                              double* out_pnorm, void* stream);
 
 /*
+ * Allocation-free variant of fks_precond_apply (the paper has no counterpart).
+ * For callers that may not allocate device memory: code inside a host framework
+ * whose memory pool owns the GPU's memory, or real-time code that cannot take
+ * cudaMalloc's implicit synchronisation. It computes exactly what
+ * fks_precond_apply computes, but its multigrid scratch is a fixed 16 MiB
+ * device array inside the library (held by every GPU that loads the library
+ * until the process exits) and it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *  - v, z must be device memory (the caller passes inputs and outputs).
+ *  - Limits: at most 65536 cells, coarsest multigrid level at most 256 cells;
+ *    larger grids return FKS_ERR_ARG with a message.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array and leave their contents in it; calls that
+ *    overlap on the GPU (other streams, other threads) race and must be
+ *    serialised by the caller.
+ */
+fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c128* z, double eps,
+                                     int max_cycles, int cycles, int precision, int32_t* out_cycles,
+                                     double* out_pnorm, void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper). Kernel classes of the solve:
  */
 enum {

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -771,3 +772,123 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free preconditioner apply
+// For callers that may not allocate device memory: code running inside a host
+// framework whose memory pool owns all of the GPU's memory, or code that cannot
+// afford cudaMalloc's implicit device synchronisation in a real-time loop. The
+// multigrid scratch lives in one fixed file-scope device array instead of the
+// operator's workspace. Every GPU that loads this library holds the array until
+// the process exits.
+namespace fks {
+
+constexpr size_t NOALLOC_BYTES = size_t(16) << 20;  // 16 MiB of scratch per device
+constexpr int64_t NOALLOC_MAX_CELLS = 65536;        // largest grid (e.g. 256 x 256, 40^3)
+constexpr int64_t NOALLOC_MAX_COARSE = 256;         // largest coarsest multigrid level
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+// Device address of g_noalloc_scratch on each device. In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per device
+// with cudaGetSymbolAddress and that pointer is what the kernels get.
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+static cudaError_t noalloc_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return cudaSuccess;
+}
+
+}  // namespace fks
+
+extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c128* z, double eps,
+                                                int max_cycles, int cycles, int precision, int32_t* out_cycles,
+                                                double* out_pnorm, void* stream) {
+  if (!op || !v || !z) { set_error("fks_precond_apply_noalloc: NULL argument"); return FKS_ERR_ARG; }
+  if (!finite_c(tau)) { set_error("fks_precond_apply_noalloc: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) {
+    set_error("fks_precond_apply_noalloc: bad precision");
+    return FKS_ERR_ARG;
+  }
+  if (cycles < 0 && !(eps > 0)) { set_error("fks_precond_apply_noalloc: eps must be positive"); return FKS_ERR_ARG; }
+  if (op->n > NOALLOC_MAX_CELLS) {
+    set_error("fks_precond_apply_noalloc: the grid has more than 65536 cells, the limit of the fixed scratch array");
+    return FKS_ERR_ARG;
+  }
+  if (op->levels.back().n > NOALLOC_MAX_COARSE) {
+    set_error("fks_precond_apply_noalloc: the coarsest multigrid level has more than 256 cells");
+    return FKS_ERR_ARG;
+  }
+  if (op->ctx->device < 0 || op->ctx->device >= NOALLOC_MAX_DEVICES) {
+    set_error("fks_precond_apply_noalloc: device index beyond 63");
+    return FKS_ERR_ARG;
+  }
+  if (!is_device_ptr(v) || !is_device_ptr(z)) {
+    set_error("fks_precond_apply_noalloc: v and z must be device memory");
+    return FKS_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    void* base = nullptr;
+    CK(noalloc_scratch(op->ctx->device, &base));
+    Solve S{};
+    S.op = op;
+    S.s = s;
+    S.nslot = 1;
+    S.n_f = 1;
+    S.n_tau = 1;
+    S.m = 1;
+    S.sched_len = 1;
+    S.precision = precision;
+    S.n = op->n;
+    S.eps = eps;
+    S.max_cycles = max_cycles > 0 ? max_cycles : 50;
+    S.replay = cycles >= 0;
+    SlotState st_host{};
+    S.st_host = &st_host;
+    auto run = [&](auto tag) -> bool {
+      using VT = decltype(tag);
+      Arena probe;
+      carve<VT>(S, probe, false);
+      if (probe.off > NOALLOC_BYTES) return false;
+      Arena A;
+      A.base = (char*)base;  // never reserve(): the arena only carves the fixed array
+      A.cap = NOALLOC_BYTES;
+      carve<VT>(S, A, false);
+      int64_t n = S.n;
+      CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
+      int32_t cyc = cycles;
+      CK(cudaMemcpyAsync(S.rep_cyc, &cyc, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      SlotState st0{};
+      st0.active = 1;
+      st0.k = 1;
+      st0.tau = 0;
+      CK(cudaMemcpyAsync(S.st, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+      setup_levels<VT>(S);
+      inner_solve<VT>(S, (const z64*)v, n, (z64*)z, n);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (out_cycles) *out_cycles = S.st_host->cycles;
+      if (out_pnorm) *out_pnorm = std::sqrt(S.st_host->pnorm2);
+      return true;
+    };
+    bool fits = precision == FKS_PREC_FP64 ? run(double{}) : run(float{});
+    if (!fits) {
+      set_error("fks_precond_apply_noalloc: the scratch this grid needs exceeds the 16 MiB fixed array");
+      return FKS_ERR_ARG;
+    }
+  } catch (CudaError& e) {
+    set_error(std::string("fks_precond_apply_noalloc: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return FKS_ERR_CUDA;
+  }
+  return FKS_OK;
+}

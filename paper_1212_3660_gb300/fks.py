@@ -82,10 +82,12 @@ def lib():
                             vp, C.POINTER(fks_info), vp]
     L.fks_op_apply.argtypes = [vp, fks_c128, vp, vp, C.c_int, vp]
     L.fks_precond_apply.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p, f64p, vp]
+    L.fks_precond_apply_noalloc.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p,
+                                            f64p, vp]
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
     for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
-                 "fks_profile_read"):
+                 "fks_profile_read", "fks_precond_apply_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -191,6 +193,18 @@ def fks_precond_apply(op, tau, v, z, eps, max_cycles=50, cycles=-1, precision=FK
     op_ = C.c_double(0.0)
     st = lib().fks_precond_apply(op, fks_c128(complex(tau).real, complex(tau).imag), _ptr(v), _ptr(z), float(eps),
                                  int(max_cycles), int(cycles), int(precision), C.byref(oc), C.byref(op_), stream)
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return st, int(oc.value), float(op_.value)
+
+
+def fks_precond_apply_noalloc(op, tau, v, z, eps, max_cycles=50, cycles=-1, precision=FKS_PREC_FP64, stream=None):
+    """Allocation-free fks_precond_apply (device v, z; fixed scratch in the library). Returns (status, cycles, ||p||)."""
+    oc = C.c_int32(0)
+    op_ = C.c_double(0.0)
+    st = lib().fks_precond_apply_noalloc(op, fks_c128(complex(tau).real, complex(tau).imag), _ptr(v), _ptr(z),
+                                         float(eps), int(max_cycles), int(cycles), int(precision), C.byref(oc),
+                                         C.byref(op_), stream)
     if st < 0:
         raise FksError(st, fks_last_error())
     return st, int(oc.value), float(op_.value)
