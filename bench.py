@@ -202,11 +202,14 @@ def main():
     est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
     mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
     opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
-                                  schedule=pr.schedule)
+                                  schedule=pr.schedule, launch_mode=0)
+    # host-driven launches (identical kernels) for per-launch event timing
+    opts_host, keep_host = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                            schedule=pr.schedule, launch_mode=1)
     info, info_arr = fks.make_info(n_rhs, pr.m_max)
 
-    def step(b, X):
-        return fks.fks_solve(solver.op, b, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X, est, bnd, tru, mj,
+    def step(b, X, o=opts):
+        return fks.fks_solve(solver.op, b, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), o, X, est, bnd, tru, mj,
                              sst, info, sh)
 
     def barrier():
@@ -233,7 +236,7 @@ def main():
     totals = {}
     for c, name in enumerate(fks.KERNEL_CLASSES):
         fks.fks_profile_select(solver.op, c)
-        step(b_d, X_d)
+        step(b_d, X_d, opts_host)
         totals[name] = fks.fks_profile_read(solver.op)
     fks.fks_profile_select(solver.op, None)
     fks.fks_profile_read(solver.op)
@@ -275,7 +278,7 @@ def main():
     # ---- roofline of the dominant kernel class (events on the library's stream)
     fks.fks_profile_select(solver.op, dominant)
     for _ in range(args.steps):
-        step(b_d, X_d)
+        step(b_d, X_d, opts_host)
     prof = fks.fks_profile_read(solver.op)
     fks.fks_profile_select(solver.op, None)
     hbm_peak, bf16_peak, peak_src = peaks()

@@ -103,6 +103,9 @@ typedef struct {
   int replay_mode;       /* 1: run exactly replay_inner_cycles / freeze at replay_mj          */
   const int32_t* replay_inner_cycles; /* host [m_max * n_rhs], step-major per source          */
   const int32_t* replay_mj;           /* host [n_f * n_rhs]                                   */
+  int launch_mode;       /* 0: the step loop runs as one CUDA graph with conditional WHILE nodes
+                            (no host round trip per step); 1: host-driven loop (one host sync per
+                            inner cycle; per-kernel timing with fks_profile_select works here)  */
 } fks_options;
 
 /* Optional per-solve diagnostics, host arrays owned by the caller (any may be NULL). */
@@ -181,7 +184,7 @@ enum {
   FKS_K_SMOOTH = 0,    /* red-black Gauss-Seidel half sweep (any level)           */
   FKS_K_RESTRICT = 1,  /* residual + restriction to the next coarser level        */
   FKS_K_PROLONG = 2,   /* interpolation + correction from the coarser level       */
-  FKS_K_COARSE = 3,    /* coarsest-level dense solve                              */
+  FKS_K_COARSE = 3,    /* coarsest-level dense solve (inside the tail kernel now)  */
   FKS_K_DEFECT = 4,    /* complex128 defect r = v - (K + tau M) z of the inner solve */
   FKS_K_CORRECT = 5,   /* z += e of the inner solve                               */
   FKS_K_MDOT = 6,      /* CGS projection pass h = V^* w                           */
@@ -189,7 +192,8 @@ enum {
   FKS_K_GIVENS = 8,    /* per-shift Givens least-squares update                   */
   FKS_K_ASSEMBLE = 9,  /* x_j = Z y_j                                             */
   FKS_K_TRES = 10,     /* true residuals                                          */
-  FKS_K_COUNT = 11
+  FKS_K_TAIL = 11,     /* the V-cycle of all small levels in one block per source */
+  FKS_K_COUNT = 12
 };
 /*
  * Time every launch of kernel class `kclass` (on level `level`, or every level

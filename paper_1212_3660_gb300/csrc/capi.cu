@@ -138,6 +138,10 @@ struct fks_op {
   std::vector<LevelHost> levels;
   Arena ws;
   Prof prof;
+  // instantiated graph of the step loop, valid for one workspace layout
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
+  int graph_outer = 0, graph_inner = 0;
 };
 
 namespace fks {
@@ -197,25 +201,47 @@ struct Solve {
   SlotState* st_host;  // pinned mirror
   z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
-  int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular;
+  int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular, *flags, *counter;
   // multigrid, cycle precision
   std::vector<void*> f, z, invd;
   void* cinv;      // coarse inverse in cycle precision
   z64* cwork;      // dense coarse matrices
   z64* cinv64;
+  bool capturing = false;  // enqueueing into a graph: no event timing
 };
 
-#define PROF(cls, lvl, by, fl, call)                          \
-  do {                                                       \
-    S.op->prof.begin((cls), (lvl), (by), (fl), S.s);         \
-    call;                                                    \
-    S.op->prof.end(S.s);                                     \
+#define PROF(cls, lvl, by, fl, call)                                           \
+  do {                                                                        \
+    S.op->prof.begin(S.capturing ? -1 : (cls), (lvl), (by), (fl), S.s);       \
+    call;                                                                     \
+    S.op->prof.end(S.s);                                                      \
   } while (0)
+
+// Largest level handled by the single-block tail V-cycle: fp64 arithmetic runs
+// at 2 DFMA/clk per SM on GB300, so the fp64 tail stops at 1024 cells; the
+// fp32 tail takes 4096.
+template <typename VT>
+static constexpr int64_t tail_max_cells() { return sizeof(VT) == 8 ? 1024 : 4096; }
+
+template <typename VT>
+static int tail_level(const std::vector<LevelHost>& Ls) {
+  for (size_t l = 0; l < Ls.size(); ++l)
+    if (Ls[l].n <= tail_max_cells<VT>()) return (int)l;
+  return (int)Ls.size() - 1;
+}
+
+template <typename VT>
+static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
+  size_t e = 0;
+  for (size_t l = lt; l < Ls.size(); ++l) e += 2 * (size_t)Ls[l].n;
+  return e * sizeof(cx<VT>);
+}
 
 template <typename VT>
 static void vcycle(Solve& S) {
   auto& Ls = S.op->levels;
   int nl = (int)Ls.size();
+  int lt = tail_level<VT>(Ls);
   cudaStream_t s = S.s;
   auto F = [&](int l) { return (cx<VT>*)S.f[l]; };
   auto Zl = [&](int l) { return (cx<VT>*)S.z[l]; };
@@ -226,7 +252,7 @@ static void vcycle(Solve& S) {
     return zs ? ns * L.n * 1.5 * cv : ns * L.n * (2 * cv + d * rv);
   };
   auto smooth_f = [&](const LevelHost& L, int zs) { return zs ? ns * L.n * 3.0 : ns * L.n * 0.5 * (8 * d + 6); };
-  for (int l = 0; l + 1 < nl; ++l) {
+  for (int l = 0; l < lt; ++l) {
     const LevelHost& L = Ls[l];
     for (int r = 0; r < NU1; ++r) {
       int zs = r == 0 ? 1 : 0;
@@ -239,10 +265,35 @@ static void vcycle(Solve& S) {
          launch_residual_restrict<VT>(L, Ls[l + 1], S.st, S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
                                       s));
   }
-  const LevelHost& C = Ls[nl - 1];
-  PROF(FKS_K_COARSE, nl - 1, ns * cv * (C.n * C.n + 2 * C.n), ns * 8.0 * C.n * C.n,
-       launch_coarse_solve<VT>((const cx<VT>*)S.cinv, (int)C.n, S.st, F(nl - 1), Zl(nl - 1), C.n, S.nslot, s));
-  for (int l = nl - 2; l >= 0; --l) {
+  {
+    // levels lt .. coarsest in one block per slot
+    TailParams<VT> P{};
+    P.nlev = nl - lt;
+    int off = 0;
+    double tb = 0, tf = 0;
+    for (int l = lt; l < nl; ++l) {
+      TailLevel<VT>& T = P.lev[l - lt];
+      T.L = view<VT>(Ls[l]);
+      T.rx = Ls[l].rx; T.ry = Ls[l].ry; T.rz = Ls[l].rz;
+      T.invd = I(l);
+      T.off = off;
+      off += 2 * (int)Ls[l].n;
+      tb += Ls[l].n * (8 * cv + d * rv);
+      tf += Ls[l].n * (8 * d + 6) * 4;
+    }
+    const LevelHost& C = Ls[nl - 1];
+    P.Ainv = (const cx<VT>*)S.cinv;
+    P.nc = (int)C.n;
+    P.mask = S.op->mask;
+    P.f_in = F(lt);
+    P.z_out = Zl(lt);
+    P.vs = Ls[lt].n;
+    P.taus = S.taus;
+    tb += cv * C.n * C.n;
+    tf += 8.0 * C.n * C.n;
+    PROF(FKS_K_TAIL, lt, ns * tb, ns * tf, launch_tail<VT>(P, tail_smem<VT>(Ls, lt), S.st, S.nslot, s));
+  }
+  for (int l = lt - 1; l >= 0; --l) {
     const LevelHost& L = Ls[l];
     PROF(FKS_K_PROLONG, l, ns * (2 * cv * L.n + cv * Ls[l + 1].n), ns * L.n * (4.0 * (1 << S.op->dim) + 2),
          launch_prolong_add<VT>(L, Ls[l + 1], S.op->mask, S.st, Zl(l + 1), Ls[l + 1].n, Zl(l), L.n, S.nslot, s));
@@ -271,39 +322,172 @@ static bool any_active(Solve& S) {
   return false;
 }
 
-// Inner solve of the current step: z_k (column k-1 of Z) from v_k (column k-1 of V).
+// ------------------------------------------------------------------ sections of a step
+// Each section only enqueues kernels on S.s and reads nothing back, so that it
+// can be captured into a graph; `use_cond` makes the deciding kernel set the
+// given graph loop condition.
+
+// First defect of the inner solve of step k: r = v_k (z = 0), ||v_k||.
 template <typename VT>
-static void inner_solve(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ) {
+static void sec_inner_first(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ, int use_cond,
+                            cudaGraphConditionalHandle hin) {
   const LevelHost& L0 = S.op->levels[0];
-  int nbl = defect_blocks(L0.n);
+  cx<VT>* f0 = (cx<VT>*)S.f[0];
+  const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
+  const double cv = sizeof(cx<VT>), ns = S.nslot, n = L0.n;
+  PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
+       launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 1, f0, L0.n, S.dpart, 1, S.nslot, S.s));
+  PROF(-1, -1, 0, 0,
+       launch_inner_decide(S.st, S.nslot, S.dpart, defect_blocks(L0), 1, S.eps, S.max_cycles, rc, S.m, use_cond,
+                           hin, S.flags, S.counter, S.s));
+}
+
+// One inner cycle: z += V-cycle(r), r = v - (K + tau M) z, decide.
+template <typename VT>
+static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ, int use_cond,
+                           cudaGraphConditionalHandle hin) {
+  const LevelHost& L0 = S.op->levels[0];
   cx<VT>* f0 = (cx<VT>*)S.f[0];
   cx<VT>* e0 = (cx<VT>*)S.z[0];
   const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
   const double cv = sizeof(cx<VT>), d = S.op->dim, ns = S.nslot, n = L0.n;
-  const double def_b = ns * n * (32 + 8 * (d + 1) + cv), def_f = ns * n * (8 * d + 14);
-  PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
-       launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 1, f0, L0.n, S.dpart, 1, S.nslot, S.s));
-  PROF(-1, -1, 0, 0, launch_inner_decide(S.st, S.nslot, S.dpart, nbl, 1, S.eps, S.max_cycles, rc, S.m, S.s));
+  vcycle<VT>(S);
+  PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
+       launch_correct<VT>(S.st, Z, vsZ, L0.n, e0, L0.n, L0.n, S.nslot, S.s));
+  PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 1) + cv), ns * n * (8 * d + 14),
+       launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 0, f0, L0.n, S.dpart, 0, S.nslot, S.s));
+  PROF(-1, -1, 0, 0,
+       launch_inner_decide(S.st, S.nslot, S.dpart, defect_blocks(L0), 0, S.eps, S.max_cycles, rc, S.m, use_cond,
+                           hin, S.flags, S.counter, S.s));
+}
+
+// Inner solve of the current step, host-driven: z_k (column k-1 of Z) from v_k.
+template <typename VT>
+static void inner_solve(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ) {
+  sec_inner_first<VT>(S, V, vsV, Z, vsZ, 0, 0);
   int guard = 0;
   while (any_inner_running(S)) {
-    vcycle<VT>(S);
-    PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
-         launch_correct<VT>(S.st, Z, vsZ, L0.n, e0, L0.n, L0.n, S.nslot, S.s));
-    PROF(FKS_K_DEFECT, 0, def_b, def_f,
-         launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 0, f0, L0.n, S.dpart, 0, S.nslot, S.s));
-    PROF(-1, -1, 0, 0, launch_inner_decide(S.st, S.nslot, S.dpart, nbl, 0, S.eps, S.max_cycles, rc, S.m, S.s));
+    sec_inner_body<VT>(S, V, vsV, Z, vsZ, 0, 0);
     if (++guard > 100000) break;
   }
+}
+
+static void sec_step_begin(Solve& S) {
+  PROF(-1, -1, 0, 0, launch_step_begin(S.st, S.nslot, S.sched, S.sched_len, S.taus, S.taus_k, S.m, S.s));
+}
+
+// After the inner solve: w = M z_k, CGS2, h_{k+1,k}, v_{k+1}, per-shift least
+// squares, end-of-step test. `step` only sizes the launches in host-driven
+// mode (graphs use m_max and let idle blocks exit).
+static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalHandle hout) {
+  const int64_t n = S.n;
+  const int m = S.m, n_f = S.n_f, n_rhs = S.nslot;
+  const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
+  const double ns = n_rhs, nn = (double)n, kk = step;
+  const int kmax = use_cond ? m : step;
+  PROF(-1, -1, 0, 0, launch_mass(S.st, S.op->levels[0].d64[3], S.Z, vsZ, S.w, n, S.mpart, n_rhs, S.s));
+  // CGS2: two projections; pass p writes its coefficients to h12[slot][p]
+  for (int pass = 0; pass < 2; ++pass) {
+    z64* hp = S.h12 + pass * MAX_M;
+    PROF(FKS_K_MDOT, -1, ns * 16 * nn * (kk + 1), ns * 8 * nn * kk,
+         launch_mdot(S.st, S.V, vsV, S.w, n, S.mdpart, kmax, n_rhs, S.s));
+    PROF(-1, -1, 0, 0, launch_hreduce(S.st, S.mdpart, n, hp, 2 * MAX_M, n_rhs, S.s));
+    PROF(FKS_K_MAXPY, -1, ns * 16 * nn * (kk + 2), ns * 8 * nn * kk,
+         launch_maxpy(S.st, S.V, vsV, hp, 2 * MAX_M, S.w, n, n_rhs, S.s));
+  }
+  PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 1, S.w, n, n, S.wpart, n_rhs, S.s));
+  PROF(-1, -1, 0, 0,
+       launch_arnoldi_finish(S.st, n_rhs, S.h12, S.wpart, S.mpart, norm_blocks(n), S.H, m, S.pn, S.cyc,
+                             BREAKDOWN_RTOL, S.s));
+  PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, S.s));
+  PROF(FKS_K_GIVENS, -1, ns * n_f * 48.0 * kk, ns * n_f * 26.0 * kk,
+       launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant, S.replay ? S.rep_mj : nullptr,
+                     S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, n_rhs, S.s));
+  PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, use_cond, hout, S.s));
+}
+
+// The loop over Arnoldi steps as one graph: outer WHILE (some source active) {
+// step begin, first defect, inner WHILE (some inner solve running) { V-cycle,
+// correct, defect, decide }, CGS2 ... end of step }. Kernel counts per section
+// are returned for the launch count.
+template <typename VT>
+static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int* inner_kernels) {
+  const int64_t n = S.n;
+  const int m = S.m;
+  const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
+  cudaStream_t user = S.s;
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  int64_t saved = S.op->prof.all_launches;
+  try {
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hout, hin;
+    CK(cudaGraphConditionalHandleCreate(&hout, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams po = {};
+    po.type = cudaGraphNodeTypeConditional;
+    po.conditional.handle = hout;
+    po.conditional.type = cudaGraphCondTypeWhile;
+    po.conditional.size = 1;
+    cudaGraphNode_t nout;
+    CK(cudaGraphAddNode(&nout, g, nullptr, nullptr, 0, &po));
+    cudaGraph_t body_out = po.conditional.phGraph_out[0];
+    S.s = cs;
+    S.capturing = true;
+    int64_t c0 = S.op->prof.all_launches;
+    CK(cudaStreamBeginCaptureToGraph(cs, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    sec_step_begin(S);
+    CK(cudaGraphConditionalHandleCreate(&hin, body_out, 0, 0));
+    sec_inner_first<VT>(S, S.V, vsV, S.Z, vsZ, 1, hin);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams pi = {};
+    pi.type = cudaGraphNodeTypeConditional;
+    pi.conditional.handle = hin;
+    pi.conditional.type = cudaGraphCondTypeWhile;
+    pi.conditional.size = 1;
+    cudaGraphNode_t nin;
+    CK(cudaGraphAddNode(&nin, body_out, deps, nullptr, ndeps, &pi));
+    cudaGraph_t body_in = pi.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(cs, &nin, nullptr, 1, cudaStreamSetCaptureDependencies));
+    sec_step_end(S, m, 1, hout);
+    cudaGraph_t cap = nullptr;
+    CK(cudaStreamEndCapture(cs, &cap));
+    int64_t c1 = S.op->prof.all_launches;
+    CK(cudaStreamBeginCaptureToGraph(cs, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    sec_inner_body<VT>(S, S.V, vsV, S.Z, vsZ, 1, hin);
+    CK(cudaStreamEndCapture(cs, &cap));
+    int64_t c2 = S.op->prof.all_launches;
+    *outer_kernels = (int)(c1 - c0);
+    *inner_kernels = (int)(c2 - c1);
+    CK(cudaGraphInstantiate(exec, g, 0));
+  } catch (...) {
+    S.s = user;
+    S.capturing = false;
+    S.op->prof.all_launches = saved;
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    throw;
+  }
+  S.s = user;
+  S.capturing = false;
+  S.op->prof.all_launches = saved;
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
 }
 
 template <typename VT>
 static void setup_levels(Solve& S) {
   auto& Ls = S.op->levels;
+  tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls)));
   for (size_t l = 0; l < Ls.size(); ++l)
     PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
   const LevelHost& C = Ls.back();
   int64_t nc = C.n;
   CK(cudaMemsetAsync(S.singular, 0, sizeof(int), S.s));
+  CK(cudaMemsetAsync(S.counter, 0, sizeof(int), S.s));
   S.op->prof.all_launches += 2;
   launch_coarse_inverse(C, S.taus, S.n_tau, S.cwork, S.cinv64, S.singular, S.s);
   if constexpr (sizeof(VT) == 8) {
@@ -342,7 +526,9 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.cinv64 = A.take<z64>((size_t)S.n_tau * nc * nc);
   S.cinv = A.take<cx<VT>>((size_t)S.n_tau * nc * nc);
   S.singular = A.take<int32_t>(1);
-  S.dpart = A.take<double>((size_t)ns * defect_blocks(n) * 2);
+  S.flags = A.take<int32_t>(ns);
+  S.counter = A.take<int32_t>(1);
+  S.dpart = A.take<double>((size_t)ns * defect_blocks(Ls[0]) * 2);
   S.npart = A.take<double>((size_t)ns * norm_blocks(n));
   S.mpart = A.take<double>((size_t)ns * norm_blocks(n));
   S.wpart = A.take<double>((size_t)ns * norm_blocks(n));
@@ -361,7 +547,7 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.mj = A.take<int32_t>((size_t)ns * nf);
   S.est = A.take<double>((size_t)ns * nf);
   S.bnd = A.take<double>((size_t)ns * nf);
-  S.tpart = A.take<double>((size_t)ns * nf * tres_blocks(n));
+  S.tpart = A.take<double>((size_t)ns * nf * tres_blocks(Ls[0]));
   S.tres = A.take<double>((size_t)ns * nf);
   S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
 }
@@ -419,33 +605,40 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
   CK(cudaMemsetAsync(S.cyc, 0, sizeof(int32_t) * m * n_rhs, s));
   const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
   int steps = 0;
+  bool use_graph = o->launch_mode == 0;
+  std::vector<int32_t> cyc_all((size_t)m * n_rhs);
   if (any_active(S)) {
-    for (int step = 1; step <= m; ++step) {
-      steps = step;
-      const double ns = n_rhs, nn = (double)n, kk = step, d = op->dim;
-      PROF(-1, -1, 0, 0, launch_step_begin(S.st, n_rhs, step, S.sched, S.sched_len, S.taus, S.taus_k, m, s));
-      inner_solve<VT>(S, S.V, vsV, S.Z, vsZ);
-      PROF(-1, -1, 0, 0, launch_mass(S.st, op->levels[0].d64[3], S.Z, vsZ, S.w, n, S.mpart, n_rhs, s));
-      // CGS2: two projections; pass p writes its coefficients to h12[slot][p]
-      for (int pass = 0; pass < 2; ++pass) {
-        z64* hp = S.h12 + pass * MAX_M;
-        PROF(FKS_K_MDOT, -1, ns * 16 * nn * (kk + 1), ns * 8 * nn * kk,
-             launch_mdot(S.st, S.V, vsV, S.w, n, S.mdpart, step, n_rhs, s));
-        PROF(-1, -1, 0, 0, launch_hreduce(S.st, S.mdpart, n, hp, 2 * MAX_M, n_rhs, s));
-        PROF(FKS_K_MAXPY, -1, ns * 16 * nn * (kk + 2), ns * 8 * nn * kk,
-             launch_maxpy(S.st, S.V, vsV, hp, 2 * MAX_M, S.w, n, n_rhs, s));
+    if (use_graph) {
+      std::vector<double> key = {(double)(uintptr_t)op->ws.base, (double)n_rhs, (double)n_f, (double)n_tau, (double)m,
+                                 (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
+                                 S.eps, S.tol, (double)S.max_cycles};
+      if (!op->graph || op->graph_key != key) {
+        if (op->graph) cudaGraphExecDestroy(op->graph);
+        op->graph = nullptr;
+        build_graph<VT>(S, &op->graph, &op->graph_outer, &op->graph_inner);
+        op->graph_key = key;
       }
-      PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 1, S.w, n, n, S.wpart, n_rhs, s));
-      PROF(-1, -1, 0, 0,
-           launch_arnoldi_finish(S.st, n_rhs, S.h12, S.wpart, S.mpart, nbn, S.H, m, S.pn, S.cyc, BREAKDOWN_RTOL, s));
-      PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, s));
-      PROF(FKS_K_GIVENS, -1, ns * n_f * 48.0 * kk, ns * n_f * 26.0 * kk,
-           launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant,
-                         S.replay ? S.rep_mj : nullptr, S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, n_rhs,
-                         s));
-      PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, s));
-      (void)d;
-      if (!any_active(S)) break;
+      CK(cudaGraphLaunch(op->graph, s));
+      // launch count: per step the outer section, per inner iteration the inner section
+      CK(cudaMemcpyAsync(cyc_all.data(), S.cyc, sizeof(int32_t) * m * n_rhs, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int r = 0; r < n_rhs; ++r) steps = std::max(steps, S.st_host[r].k);
+      int64_t inner_iters = 0;
+      for (int k = 0; k < steps; ++k) {
+        int mx = 0;
+        for (int r = 0; r < n_rhs; ++r) mx = std::max(mx, cyc_all[(size_t)r * m + k]);
+        inner_iters += mx;
+      }
+      op->prof.all_launches += (int64_t)steps * op->graph_outer + inner_iters * op->graph_inner;
+    } else {
+      for (int step = 1; step <= m; ++step) {
+        steps = step;
+        sec_step_begin(S);
+        inner_solve<VT>(S, S.V, vsV, S.Z, vsZ);
+        sec_step_end(S, step, 0, 0);
+        if (!any_active(S)) break;
+      }
     }
   }
   // assembly and true residual
@@ -611,6 +804,7 @@ void fks_op_destroy(fks_op* op) {
       if (L.d64[a]) cudaFree(L.d64[a]);
       if (L.d32[a]) cudaFree(L.d32[a]);
     }
+  if (op->graph) cudaGraphExecDestroy(op->graph);
   op->ws.release();
   op->prof.release();
   delete op;
@@ -626,6 +820,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
     return FKS_ERR_ARG;
   }
   if (n_rhs < 1 || n_f < 1 || n_tau < 1 || n_tau > MAX_TAU) { set_error("fks_solve: bad n_rhs / n_f / n_tau"); return FKS_ERR_ARG; }
+  if ((int64_t)n_f * n_rhs > 65535) { set_error("fks_solve: n_f * n_rhs must be at most 65535"); return FKS_ERR_ARG; }
   if (o->m_max < 1 || o->m_max > MAX_M) { set_error("fks_solve: m_max must be in 1..128"); return FKS_ERR_ARG; }
   if (!(o->tol > 0) || !std::isfinite(o->tol)) { set_error("fks_solve: tol must be positive"); return FKS_ERR_ARG; }
   if (o->variant != FKS_FGMRES && o->variant != FKS_FFOM) { set_error("fks_solve: bad variant"); return FKS_ERR_ARG; }
@@ -633,10 +828,14 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   if (o->sched_len < 1 || !o->tau_schedule) { set_error("fks_solve: empty tau schedule"); return FKS_ERR_ARG; }
   for (int i = 0; i < o->sched_len; ++i)
     if (o->tau_schedule[i] < 0 || o->tau_schedule[i] >= n_tau) { set_error("fks_solve: schedule index out of range"); return FKS_ERR_ARG; }
+  if (o->launch_mode != 0 && o->launch_mode != 1) { set_error("fks_solve: launch_mode must be 0 or 1"); return FKS_ERR_ARG; }
   if (o->replay_mode && (!o->replay_inner_cycles || !o->replay_mj)) { set_error("fks_solve: replay arrays missing"); return FKS_ERR_ARG; }
   if (o->replay_mode) {
     for (int i = 0; i < o->m_max * n_rhs; ++i)
-      if (o->replay_inner_cycles[i] < 0) { set_error("fks_solve: negative replay cycle count"); return FKS_ERR_ARG; }
+      if (o->replay_inner_cycles[i] < 0 || o->replay_inner_cycles[i] > 1000) {
+        set_error("fks_solve: replay cycle counts must be in 0..1000");
+        return FKS_ERR_ARG;
+      }
     for (int i = 0; i < n_f * n_rhs; ++i)
       if (o->replay_mj[i] < 1 || o->replay_mj[i] > o->m_max) { set_error("fks_solve: replay m_j out of range"); return FKS_ERR_ARG; }
   }

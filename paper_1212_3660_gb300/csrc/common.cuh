@@ -108,6 +108,22 @@ struct SlotState {
   int inner_capped; // some inner solve hit its cycle cap
 };
 
+// Fixed-order block reduction of one double (blockDim.x a multiple of 32, at
+// most 1024); the result is valid in thread 0. Deterministic for a given
+// blockDim, so the same inputs always give the same bits.
+__device__ __forceinline__ double block_sum(double v, double* scratch32) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) scratch32[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  v = threadIdx.x < nw ? scratch32[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
 // error reporting
 void set_error(const std::string& msg);
 const char* get_error();

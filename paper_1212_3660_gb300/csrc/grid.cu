@@ -132,7 +132,7 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 // 1 / (K_cc + tau M_cc) per cell for every distinct tau, computed in fp64.
 template <typename T>
 __global__ void k_invd(LevelView<double> L, const z64* __restrict__ taus, int ntau, cx<T>* __restrict__ out) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   Cell p = cell_of(c, L.nx, L.ny);
   Faces<double> f = faces_at(L, p);
@@ -146,7 +146,7 @@ __global__ void k_invd(LevelView<double> L, const z64* __restrict__ taus, int nt
 
 // Dense coarsest-level matrix K + tau M (row-major, n x n) for every tau.
 __global__ void k_coarse_dense(LevelView<double> L, const z64* __restrict__ taus, int ntau, z64* __restrict__ A) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   Cell p = cell_of(c, L.nx, L.ny);
   Faces<double> f = faces_at(L, p);
@@ -172,11 +172,11 @@ __global__ void k_coarse_dense(LevelView<double> L, const z64* __restrict__ taus
 template <typename T>
 __global__ void k_apply(LevelView<T> L, z64 s_fixed, const SlotState* st, const z64* taus,
                         const cx<T>* __restrict__ x, cx<T>* __restrict__ y, int64_t vs) {
-  int slot = blockIdx.y;
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= L.n) return;
+  int slot = blockIdx.z;
+  Cell p;
+  int c;
+  if (!grid_cell(L.nx, L.ny, L.nz, &p, &c)) return;
   z64 s = st ? taus[st[slot].tau] : s_fixed;
-  Cell p = cell_of(c, L.nx, L.ny);
   y[slot * vs + c] = apply_at(L, p, c, cvt<T>(s), x + slot * vs);
 }
 
@@ -187,27 +187,13 @@ __global__ void k_apply(LevelView<T> L, z64 s_fixed, const SlotState* st, const 
 template <typename T>
 __global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
                      const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs, int color, int zero_start) {
-  int slot = blockIdx.y;
+  int slot = blockIdx.z;
   if (!slot_running(st, slot)) return;
-  int nxh = (L.nx + 1) >> 1;
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t rows = (int64_t)L.ny * L.nz;
-  if (t >= (int64_t)nxh * rows) return;
-  int64_t row = t / nxh;
-  int j = (int)(row % L.ny), k = (int)(row / L.ny);
-  int i = 2 * (int)(t % nxh) + ((j + k + color) & 1);
-  if (i >= L.nx) return;
-  Cell p{i, j, k};
-  int64_t c = row * L.nx + i;
-  const cx<T>* fs = f + slot * vs;
-  cx<T>* zs = z + slot * vs;
+  Cell p;
+  int c;
+  if (!grid_color_cell(L.nx, L.ny, L.nz, color, &p, &c)) return;
   cx<T> id = invd[(int64_t)st[slot].tau * L.n + c];
-  cx<T> rhs = fs[c];
-  if (!zero_start) {
-    Faces<T> fc = faces_at(L, p);
-    rhs = rhs + nb_sum(L, fc, p, c, zs);
-  }
-  zs[c] = id * rhs;
+  z[slot * vs + c] = gs_value(L, p, c, id, f + slot * vs, z + slot * vs, zero_start);
 }
 
 // --------------------------------------------------------------------- transfer
@@ -216,85 +202,113 @@ template <typename T>
 __global__ void k_residual_restrict(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz,
                                     const SlotState* st, const z64* taus, const cx<T>* __restrict__ f,
                                     const cx<T>* __restrict__ z, int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
-  int slot = blockIdx.y;
+  int slot = blockIdx.z;
   if (!slot_running(st, slot)) return;
-  int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t ncoarse = (int64_t)cnx * cny * cnz;
-  if (C >= ncoarse) return;
-  int I = (int)(C % cnx);
-  int64_t q = C / cnx;
-  int J = (int)(q % cny), K = (int)(q / cny);
+  Cell pc;
+  int C;
+  if (!grid_cell(cnx, cny, cnz, &pc, &C)) return;
+  int I = pc.i, J = pc.j, K = pc.k;
   cx<T> s = cvt<T>(taus[st[slot].tau]);
-  const cx<T>* fs = f + slot * vs;
-  const cx<T>* zs = z + slot * vs;
-  cx<T> acc = mk(T(0), T(0));
-  for (int c = 0; c < rz; ++c)
-    for (int b = 0; b < ry; ++b)
-      for (int a = 0; a < rx; ++a) {
-        Cell p{rx * I + a, ry * J + b, rz * K + c};
-        int64_t cc = ((int64_t)p.k * F.ny + p.j) * F.nx + p.i;
-        acc = acc + (fs[cc] - apply_at(F, p, cc, s, zs));
-      }
-  fc[slot * vsc + C] = acc;
+  fc[slot * vsc + C] = restrict_value(F, rx, ry, rz, I, J, K, s, f + slot * vs, z + slot * vs);
 }
 
-// z_fine += P z_coarse, cell-centred (bi/tri)linear interpolation: per coarsened
-// axis weight 3/4 on the parent and 1/4 on the coarse neighbour on the child's
-// side; past a zero-head face the ghost is -parent (weight 1/2 on the parent),
-// past a no-flow face it is +parent (weight 1).
+// z_fine += P z_coarse
 template <typename T>
 __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz, uint32_t mask,
                               const SlotState* st, const cx<T>* __restrict__ zc, int64_t vsc,
                               cx<T>* __restrict__ z, int64_t vs) {
-  int slot = blockIdx.y;
+  int slot = blockIdx.z;
   if (!slot_running(st, slot)) return;
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= F.n) return;
-  Cell p = cell_of(c, F.nx, F.ny);
-  int par[3] = {p.i / rx, p.j / ry, p.k / rz};
-  int idx[3] = {p.i, p.j, p.k};
-  int rr[3] = {rx, ry, rz};
-  int nn[3] = {cnx, cny, cnz};
-  // per axis: two (index, weight) taps
-  int ti[3][2];
-  T tw[3][2];
-  for (int a = 0; a < 3; ++a) {
-    ti[a][0] = par[a];
-    ti[a][1] = par[a];
-    if (rr[a] == 1) {
-      tw[a][0] = T(1);
-      tw[a][1] = T(0);
-      continue;
-    }
-    int nb = (idx[a] & 1) ? par[a] + 1 : par[a] - 1;
-    if (nb >= 0 && nb < nn[a]) {
-      tw[a][0] = T(0.75);
-      ti[a][1] = nb;
-      tw[a][1] = T(0.25);
-    } else {
-      bool dir = nb < 0 ? ((mask >> (2 * a)) & 1u) : ((mask >> (2 * a + 1)) & 1u);
-      tw[a][0] = dir ? T(0.5) : T(1);
-      tw[a][1] = T(0);
-    }
-  }
-  const cx<T>* zcs = zc + slot * vsc;
-  cx<T> acc = mk(T(0), T(0));
-  for (int c2 = 0; c2 < 2; ++c2) {
-    T wz = tw[2][c2];
-    if (wz == T(0)) continue;
-    for (int b = 0; b < 2; ++b) {
-      T wy = tw[1][b];
-      if (wy == T(0)) continue;
-      for (int a = 0; a < 2; ++a) {
-        T wx = tw[0][a];
-        if (wx == T(0)) continue;
-        int64_t cc = ((int64_t)ti[2][c2] * cny + ti[1][b]) * cnx + ti[0][a];
-        acc = acc + (wx * wy * wz) * zcs[cc];
-      }
-    }
-  }
+  Cell p;
+  int c;
+  if (!grid_cell(F.nx, F.ny, F.nz, &p, &c)) return;
   cx<T>* zs = z + slot * vs;
-  zs[c] = zs[c] + acc;
+  zs[c] = zs[c] + prolong_value(p, rx, ry, rz, cnx, cny, cnz, mask, zc + slot * vsc);
+}
+
+// --------------------------------------------------------------------- tail
+// The V-cycle of every level from `lt` down (levels small enough for one CTA)
+// in one kernel: one block per slot, level vectors in shared memory,
+// coefficients read through the cache. Same operations, in the same order, as
+// the per-level kernels.
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, const SlotState* st) {
+  int slot = blockIdx.x;
+  if (!slot_running(st, slot)) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  cx<T>* sh = (cx<T>*)tail_smem;
+  const int tau = st[slot].tau;
+  const cx<T> sft = cvt<T>(P.taus[tau]);
+  const int nt = blockDim.x, tid = threadIdx.x;
+  {
+    const TailLevel<T>& A = P.lev[0];
+    const cx<T>* fin = P.f_in + slot * P.vs;
+    for (int c = tid; c < A.L.n; c += nt) sh[A.off + c] = fin[c];
+  }
+  __syncthreads();
+  auto sweep = [&](const TailLevel<T>& A, int color, int zs) {
+    const LevelView<T>& L = A.L;
+    cx<T>* F = sh + A.off;
+    cx<T>* Z = F + L.n;
+    const cx<T>* ID = A.invd + (int64_t)tau * L.n;
+    int work = ((L.nx + 1) >> 1) * L.ny * L.nz;
+    for (int t = tid; t < work; t += nt) {
+      Cell p;
+      int c;
+      if (color_cell(L.nx, L.ny, L.nz, color, t, &p, &c)) Z[c] = gs_value(L, p, c, ID[c], F, Z, zs);
+    }
+    __syncthreads();
+  };
+  for (int l = 0; l + 1 < P.nlev; ++l) {
+    const TailLevel<T>& A = P.lev[l];
+    const TailLevel<T>& B = P.lev[l + 1];
+    for (int r = 0; r < 2; ++r) {
+      sweep(A, 0, r == 0);
+      sweep(A, 1, 0);
+    }
+    cx<T>* F = sh + A.off;
+    cx<T>* Z = F + A.L.n;
+    cx<T>* FC = sh + B.off;
+    for (int C = tid; C < B.L.n; C += nt) {
+      Cell pc = cell_of(C, B.L.nx, B.L.ny);
+      FC[C] = restrict_value(A.L, A.rx, A.ry, A.rz, pc.i, pc.j, pc.k, sft, F, Z);
+    }
+    __syncthreads();
+  }
+  {
+    const TailLevel<T>& Cl = P.lev[P.nlev - 1];
+    const cx<T>* F = sh + Cl.off;
+    cx<T>* Z = sh + Cl.off + Cl.L.n;
+    const cx<T>* Ainv = P.Ainv + (int64_t)tau * P.nc * P.nc;
+    for (int r = tid; r < P.nc; r += nt) {
+      cx<T> acc = mk(T(0), T(0));
+      const cx<T>* row = Ainv + (int64_t)r * P.nc;
+      for (int l = 0; l < P.nc; ++l) acc = acc + row[l] * F[l];
+      Z[r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = P.nlev - 2; l >= 0; --l) {
+    const TailLevel<T>& A = P.lev[l];
+    const TailLevel<T>& B = P.lev[l + 1];
+    cx<T>* Z = sh + A.off + A.L.n;
+    const cx<T>* ZC = sh + B.off + B.L.n;
+    for (int c = tid; c < A.L.n; c += nt) {
+      Cell p = cell_of(c, A.L.nx, A.L.ny);
+      Z[c] = Z[c] + prolong_value(p, A.rx, A.ry, A.rz, B.L.nx, B.L.ny, B.L.nz, P.mask, ZC);
+    }
+    __syncthreads();
+    for (int r = 0; r < 2; ++r) {
+      sweep(A, 1, 0);
+      sweep(A, 0, 0);
+    }
+  }
+  {
+    const TailLevel<T>& A = P.lev[0];
+    cx<T>* zout = P.z_out + slot * P.vs;
+    const cx<T>* Z = sh + A.off + A.L.n;
+    for (int c = tid; c < A.L.n; c += nt) zout[c] = Z[c];
+  }
 }
 
 // --------------------------------------------------------------------- coarsest
@@ -414,71 +428,100 @@ template <typename T>
 __global__ void k_defect(LevelView<double> L, const SlotState* st, const z64* taus, const z64* __restrict__ v,
                          int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col, int zero_z,
                          cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v) {
-  int slot = blockIdx.y;
-  __shared__ double red[2][32];
+  int slot = blockIdx.z;
+  __shared__ double red[2][GX * GY / 32];
   bool run = slot_running(st, slot);
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (!run) return;
   double r2 = 0.0, v2 = 0.0;
-  if (run && c < L.n) {
+  Cell p;
+  int c;
+  if (grid_cell(L.nx, L.ny, L.nz, &p, &c)) {
     int64_t off = (int64_t)(st[slot].k - 1) * col;
     z64 vv = v[slot * vsv + off + c];
     z64 r = vv;
-    if (!zero_z) {
-      Cell p = cell_of(c, L.nx, L.ny);
-      r = vv - apply_at(L, p, c, taus[st[slot].tau], z + slot * vsz + off);
-    }
+    if (!zero_z) r = vv - apply_at(L, p, c, taus[st[slot].tau], z + slot * vsz + off);
     f0[slot * vsf + c] = cvt<T>(r);
     r2 = abs2(r);
     v2 = abs2(vv);
   }
-  if (!run) return;
   for (int o = 16; o > 0; o >>= 1) {
     r2 += __shfl_down_sync(0xffffffffu, r2, o);
     v2 += __shfl_down_sync(0xffffffffu, v2, o);
   }
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tl = thread_linear();
+  int w = tl >> 5, lane = tl & 31;
   if (lane == 0) { red[0][w] = r2; red[1][w] = v2; }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tl == 0) {
     double a = 0.0, b = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; b += red[1][q]; }
-    partial[((int64_t)slot * gridDim.x + blockIdx.x) * 2 + 0] = a;
-    partial[((int64_t)slot * gridDim.x + blockIdx.x) * 2 + 1] = b;
+    for (int q = 0; q < GX * GY / 32; ++q) { a += red[0][q]; b += red[1][q]; }
+    int nblk = gridDim.x * gridDim.y;
+    partial[((int64_t)slot * nblk + block_linear()) * 2 + 0] = a;
+    partial[((int64_t)slot * nblk + block_linear()) * 2 + 1] = b;
   }
 }
 
 // Sum the per-block partials in a fixed order and decide whether the inner
-// solve of each slot is finished.
+// solve of each slot is finished; one block per slot. With `use_cond` the last
+// block to finish sets the graph's loop condition to "some slot still runs its
+// inner solve" (flags[slot] collects the per-slot answers, counter[0] counts
+// finished blocks and is reset by the last one).
 __global__ void k_inner_decide(SlotState* st, int nslot, const double* __restrict__ partial, int nblocks,
-                               int first, double eps, int max_cycles, const int32_t* replay_cycles, int m_max) {
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= nslot) return;
+                               int first, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
+                               int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter) {
+  __shared__ double red[32];
+  __shared__ int last;
+  int slot = blockIdx.x;
   SlotState& s = st[slot];
-  if (!s.active || s.inner_done) return;
-  double a = 0.0, b = 0.0;
-  for (int q = 0; q < nblocks; ++q) {
-    a += partial[((int64_t)slot * nblocks + q) * 2 + 0];
-    b += partial[((int64_t)slot * nblocks + q) * 2 + 1];
+  bool act = s.active && !s.inner_done;
+  int running = 0;
+  if (act) {
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+      a += partial[((int64_t)slot * nblocks + q) * 2 + 0];
+      b += partial[((int64_t)slot * nblocks + q) * 2 + 1];
+    }
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) {
+      s.pnorm2 = a;
+      if (first) {
+        s.vnorm2 = b;
+        s.cycles = 0;
+      } else {
+        s.cycles += 1;
+      }
+      bool done;
+      if (replay_cycles) done = s.cycles >= replay_cycles[(int64_t)slot * m_max + (s.k - 1)];
+      else if (first) done = false;
+      else {
+        done = a <= eps * eps * s.vnorm2 || s.cycles >= max_cycles;
+        if (!(a <= eps * eps * s.vnorm2) && s.cycles >= max_cycles) s.inner_capped = 1;
+      }
+      s.inner_done = done ? 1 : 0;
+      running = done ? 0 : 1;
+    }
   }
-  s.pnorm2 = a;
-  if (first) {
-    s.vnorm2 = b;
-    s.cycles = 0;
-  } else {
-    s.cycles += 1;
+  if (!use_cond) return;
+  if (threadIdx.x == 0) {
+    flags[slot] = running;
+    __threadfence();
+    last = atomicAdd(counter, 1) == nslot - 1;
   }
-  bool done;
-  if (replay_cycles) done = s.cycles >= replay_cycles[(int64_t)slot * m_max + (s.k - 1)];
-  else if (first) done = false;
-  else {
-    done = a <= eps * eps * s.vnorm2 || s.cycles >= max_cycles;
-    if (!(a <= eps * eps * s.vnorm2) && s.cycles >= max_cycles) s.inner_capped = 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    int any = 0;
+    for (int q = 0; q < nslot; ++q) any |= ((volatile int*)flags)[q];
+    *counter = 0;
+    cudaGraphSetConditional(cond, any ? 1u : 0u);
   }
-  s.inner_done = done ? 1 : 0;
 }
 
 // --------------------------------------------------------------------- launchers
 static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+static inline dim3 grid2(int64_t nxw, int64_t rows, int nz) { return dim3(nb(nxw, GX), nb(rows, GY), nz); }
+static const dim3 B2(GX, GY);
 
 void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond,
                             cudaStream_t s) {
@@ -516,32 +559,39 @@ void launch_to_prec(const z64* a, cx<T>* b, int64_t n, cudaStream_t s) {
 template <typename T>
 void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* taus, const cx<T>* x, cx<T>* y,
                   int64_t vs, int nslot, cudaStream_t s) {
-  dim3 g(nb(L.n, 256), nslot);
-  k_apply<T><<<g, 256, 0, s>>>(view<T>(L), sfix, st, taus, x, y, vs);
+  k_apply<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), sfix, st, taus, x, y, vs);
 }
 
 template <typename T>
 void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
                int nslot, int color, int zero_start, cudaStream_t s) {
-  int64_t work = (int64_t)((L.nx + 1) / 2) * L.ny * L.nz;
-  dim3 g(nb(work, 256), nslot);
-  k_gs<T><<<g, 256, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, zero_start);
+  k_gs<T><<<grid2((L.nx + 1) / 2, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), st, invd, f, z, vs, color,
+                                                                          zero_start);
 }
 
 template <typename T>
 void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
                               const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
                               cudaStream_t s) {
-  dim3 g(nb(C.n, 256), nslot);
-  k_residual_restrict<T><<<g, 256, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
-                                           vsc);
+  k_residual_restrict<T><<<grid2(C.nx, (int64_t)C.ny * C.nz, nslot), B2, 0, s>>>(
+      view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc, vsc);
 }
 
 template <typename T>
 void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* zc,
                         int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s) {
-  dim3 g(nb(F.n, 256), nslot);
-  k_prolong_add<T><<<g, 256, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, mask, st, zc, vsc, z, vs);
+  k_prolong_add<T><<<grid2(F.nx, (int64_t)F.ny * F.nz, nslot), B2, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny,
+                                                                            C.nz, mask, st, zc, vsc, z, vs);
+}
+
+template <typename T>
+void tail_prepare(size_t smem_bytes) {
+  cudaFuncSetAttribute(k_tail_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+template <typename T>
+void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s) {
+  k_tail_vcycle<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
 }
 
 template <typename T>
@@ -558,23 +608,29 @@ void launch_correct(const SlotState* st, z64* z, int64_t zs, int64_t zcol, const
   k_correct<T><<<g, 256, 0, s>>>(st, z, zs, zcol, e, es, n);
 }
 
-int defect_blocks(int64_t n) { return (int)nb(n, 256); }
+int defect_blocks(const LevelHost& L) {
+  dim3 g = grid2(L.nx, (int64_t)L.ny * L.nz, 1);
+  return (int)(g.x * g.y);
+}
 
 template <typename T>
 void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
                    int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
                    int nslot, cudaStream_t s) {
-  dim3 g(nb(L.n, 256), nslot);
-  k_defect<T><<<g, 256, 0, s>>>(view<double>(L), st, taus, v, vsv, z, vsz, col, zero_z, f0, vsf, partial, with_v);
+  k_defect<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<double>(L), st, taus, v, vsv, z, vsz, col,
+                                                                       zero_z, f0, vsf, partial, with_v);
 }
 
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
-                         int max_cycles, const int32_t* replay_cycles, int m_max, cudaStream_t s) {
-  k_inner_decide<<<nb(nslot, 64), 64, 0, s>>>(st, nslot, partial, nblocks, first, eps, max_cycles, replay_cycles,
-                                                m_max);
+                         int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
+                         cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s) {
+  k_inner_decide<<<nslot, 512, 0, s>>>(st, nslot, partial, nblocks, first, eps, max_cycles, replay_cycles, m_max,
+                                        use_cond, cond, flags, counter);
 }
 
 #define INST(T)                                                                                                  \
+  template void tail_prepare<T>(size_t);                                                                          \
+  template void launch_tail<T>(const TailParams<T>&, size_t, const SlotState*, int, cudaStream_t);                \
   template void launch_invd<T>(const LevelHost&, const z64*, int, cx<T>*, cudaStream_t);                          \
   template void launch_to_prec<T>(const z64*, cx<T>*, int64_t, cudaStream_t);                                     \
   template void launch_apply<T>(const LevelHost&, z64, const SlotState*, const z64*, const cx<T>*, cx<T>*, int64_t, \

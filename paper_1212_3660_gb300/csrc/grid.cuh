@@ -4,6 +4,36 @@
 
 namespace fks {
 
+constexpr int TAIL_THREADS = 512;
+
+// One level of the single-block tail V-cycle; f lives at shared offset `off`
+// (in complex elements) and z right after it.
+template <typename T>
+struct TailLevel {
+  LevelView<T> L;
+  int rx, ry, rz;          // ratios to the next coarser level
+  const cx<T>* invd;       // [n_tau][n] inverse diagonals
+  int off;
+};
+
+template <typename T>
+struct TailParams {
+  int nlev;                // levels lt .. coarsest
+  TailLevel<T> lev[MAX_LEVELS];
+  const cx<T>* Ainv;       // [n_tau][nc][nc]
+  int nc;
+  uint32_t mask;
+  const cx<T>* f_in;       // level-lt right-hand side (global), slot stride vs
+  cx<T>* z_out;            // level-lt correction (global)
+  int64_t vs;
+  const z64* taus;
+};
+
+template <typename T>
+void tail_prepare(size_t smem_bytes);
+template <typename T>
+void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);
+
 void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond, cudaStream_t s);
 void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s);
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
@@ -32,12 +62,13 @@ void launch_coarse_solve(const cx<T>* Ainv, int n, const SlotState* st, const cx
 template <typename T>
 void launch_correct(const SlotState* st, z64* z, int64_t zs, int64_t zcol, const cx<T>* e, int64_t es, int64_t n,
                     int nslot, cudaStream_t s);
-int defect_blocks(int64_t n);
+int defect_blocks(const LevelHost& L);
 template <typename T>
 void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
                    int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
                    int nslot, cudaStream_t s);
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
-                         int max_cycles, const int32_t* replay_cycles, int m_max, cudaStream_t s);
+                         int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
+                         cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s);
 
 }  // namespace fks

@@ -40,10 +40,12 @@ __global__ void k_norm2_partial(const SlotState* st, int need_active, const z64*
 }
 
 __global__ void k_start(SlotState* st, int nslot, const double* __restrict__ partial, int nblocks, int nf) {
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= nslot) return;
+  __shared__ double red[32];
+  int slot = blockIdx.x;
   double s = 0.0;
-  for (int q = 0; q < nblocks; ++q) s += partial[(int64_t)slot * nblocks + q];
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) s += partial[(int64_t)slot * nblocks + q];
+  s = block_sum(s, red);
+  if (threadIdx.x != 0) return;
   SlotState& t = st[slot];
   t.beta = sqrt(s);
   t.active = t.beta > 0.0 ? 1 : 0;
@@ -84,13 +86,14 @@ __global__ void k_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, 
   for (int i = 0; i < m; ++i) Y[sj * m + i] = mk(0.0, 0.0);
 }
 
-// Start of step `step` (1-based): tau index from the schedule, record tau_k.
-__global__ void k_step_begin(SlotState* st, int nslot, int step, const int32_t* __restrict__ sched, int sched_len,
+// Start of the next step (k <- k + 1, 1-based): tau index from the schedule, record tau_k.
+__global__ void k_step_begin(SlotState* st, int nslot, const int32_t* __restrict__ sched, int sched_len,
                              const z64* __restrict__ taus, z64* __restrict__ taus_k, int m) {
   int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= nslot) return;
   SlotState& s = st[slot];
   if (!s.active) return;
+  int step = s.k + 1;
   s.k = step;
   s.tau = sched[(step - 1) % sched_len];
   taus_k[(int64_t)slot * m + step - 1] = taus[s.tau];
@@ -168,11 +171,14 @@ __global__ void k_hreduce(const SlotState* st, const z64* __restrict__ partial, 
   int slot = blockIdx.x;
   if (!st[slot].active) return;
   int k = st[slot].k;
-  int i = threadIdx.x;
-  if (i >= k) return;
-  z64 s = mk(0.0, 0.0);
-  for (int q = 0; q < nblocks; ++q) s = s + partial[((int64_t)slot * nblocks + q) * MAX_M + i];
-  h[(int64_t)slot * hstride + i] = s;
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = w; i < k; i += nw) {
+    z64 s = mk(0.0, 0.0);
+    for (int q = lane; q < nblocks; q += 32) s = s + partial[((int64_t)slot * nblocks + q) * MAX_M + i];
+    s.re = warp_sum(s.re);
+    s.im = warp_sum(s.im);
+    if (lane == 0) h[(int64_t)slot * hstride + i] = s;
+  }
 }
 
 // w -= sum_{i<k} V_i h_i
@@ -203,12 +209,15 @@ __global__ void k_arnoldi_finish(SlotState* st, int nslot, const z64* __restrict
   z64* Hc = H + (int64_t)slot * (m + 1) * m + (int64_t)(k - 1) * (m + 1);
   for (int i = threadIdx.x; i < k; i += blockDim.x)
     Hc[i] = h12[((int64_t)slot * 2 + 0) * MAX_M + i] + h12[((int64_t)slot * 2 + 1) * MAX_M + i];
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    a += wpart[(int64_t)slot * nblocks + q];
+    b += mpart[(int64_t)slot * nblocks + q];
+  }
+  __shared__ double red[32];
+  a = block_sum(a, red);
+  b = block_sum(b, red);
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < nblocks; ++q) {
-      a += wpart[(int64_t)slot * nblocks + q];
-      b += mpart[(int64_t)slot * nblocks + q];
-    }
     double hn = sqrt(a);
     Hc[k] = mk(hn, 0.0);
     s.w0norm2 = b;
@@ -344,12 +353,19 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   }
 }
 
-__global__ void k_step_end(SlotState* st, int nslot, int m) {
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= nslot) return;
-  SlotState& s = st[slot];
-  if (!s.active) return;
-  if (s.live <= 0 || s.breakdown || s.k >= m) s.active = 0;
+// End of a step: a slot stops when every shift is frozen, at breakdown or at
+// m_max. One block; with `use_cond` it sets the graph's outer loop condition
+// to "some slot still active".
+__global__ void k_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int slot = threadIdx.x; slot < nslot; slot += blockDim.x) {
+    SlotState& s = st[slot];
+    if (!s.active) continue;
+    if (s.live <= 0 || s.breakdown || s.k >= m) s.active = 0;
+    any |= s.active;
+  }
+  any = __syncthreads_or(any);
+  if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
 // X[:, j] = Z Y[:, j] for a tile of AS_J shifts (Y is zero beyond m_j).
@@ -387,35 +403,40 @@ __global__ void k_assemble(const z64* __restrict__ Z, int64_t vsZ, const z64* __
     if (j0 + jj < nf) X[((int64_t)slot * nf + j0 + jj) * n + row] = acc[jj];
 }
 
-// Partial sums of |b - (K + sigma_j M) x_j|^2, grid (blocks, n_f, slots).
+// Partial sums of |b - (K + sigma_j M) x_j|^2, grid (i blocks, row blocks, n_f * slots).
 __global__ void k_tres_partial(LevelView<double> L, const z64* __restrict__ sigma, int nf, const z64* __restrict__ b,
                                const z64* __restrict__ X, double* __restrict__ partial) {
-  int j = blockIdx.y, slot = blockIdx.z;
-  __shared__ double red[32];
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int slot = blockIdx.z / nf, j = blockIdx.z - slot * nf;
+  __shared__ double red[GX * GY / 32];
   double a = 0.0;
-  if (c < L.n) {
-    Cell p = cell_of(c, L.nx, L.ny);
+  Cell p;
+  int c;
+  if (grid_cell(L.nx, L.ny, L.nz, &p, &c)) {
     z64 r = b[slot * L.n + c] - apply_at(L, p, c, sigma[j], X + ((int64_t)slot * nf + j) * L.n);
     a = abs2(r);
   }
   a = warp_sum(a);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  int tl = thread_linear();
+  if ((tl & 31) == 0) red[tl >> 5] = a;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tl == 0) {
     double s = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-    partial[(((int64_t)slot * nf + j) * gridDim.x) + blockIdx.x] = s;
+    for (int q = 0; q < GX * GY / 32; ++q) s += red[q];
+    int nblk = gridDim.x * gridDim.y;
+    partial[((int64_t)slot * nf + j) * nblk + block_linear()] = s;
   }
 }
 
 __global__ void k_tres_finish(const SlotState* st, const double* __restrict__ partial, int nblocks, int nf, int nslot,
                               double* __restrict__ out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
   if (t >= nf * nslot) return;
   int slot = t / nf;
   double s = 0.0;
-  for (int q = 0; q < nblocks; ++q) s += partial[(int64_t)t * nblocks + q];
+  for (int q = lane; q < nblocks; q += 32) s += partial[(int64_t)t * nblocks + q];
+  s = warp_sum(s);
+  if (lane != 0) return;
   double beta = st[slot].beta;
   out[t] = beta > 0.0 ? sqrt(s) / beta : 0.0;
 }
@@ -431,7 +452,7 @@ void launch_norm2_partial(const SlotState* st, int need_active, const z64* x, in
   k_norm2_partial<<<g, 256, 0, s>>>(st, need_active, x, vs, n, partial);
 }
 void launch_start(SlotState* st, int nslot, const double* partial, int nblocks, int nf, cudaStream_t s) {
-  k_start<<<nbk(nslot, 64), 64, 0, s>>>(st, nslot, partial, nblocks, nf);
+  k_start<<<nslot, 512, 0, s>>>(st, nslot, partial, nblocks, nf);
 }
 void launch_init_v1(const SlotState* st, const z64* b, int64_t n, z64* V, int64_t vsV, int nslot, cudaStream_t s) {
   dim3 g(nbk(n, 256), nslot);
@@ -442,9 +463,9 @@ void launch_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_
   dim3 g(nbk(nf, 64), nslot);
   k_init_shifts<<<g, 64, 0, s>>>(st, nf, m, sst, mj, est, bnd, Y);
 }
-void launch_step_begin(SlotState* st, int nslot, int step, const int32_t* sched, int sched_len, const z64* taus,
-                       z64* taus_k, int m, cudaStream_t s) {
-  k_step_begin<<<nbk(nslot, 64), 64, 0, s>>>(st, nslot, step, sched, sched_len, taus, taus_k, m);
+void launch_step_begin(SlotState* st, int nslot, const int32_t* sched, int sched_len, const z64* taus, z64* taus_k,
+                       int m, cudaStream_t s) {
+  k_step_begin<<<nbk(nslot, 64), 64, 0, s>>>(st, nslot, sched, sched_len, taus, taus_k, m);
 }
 void launch_mass(const SlotState* st, const double* mm, const z64* Z, int64_t vsZ, z64* w, int64_t n, double* partial,
                  int nslot, cudaStream_t s) {
@@ -459,7 +480,7 @@ void launch_mdot(const SlotState* st, const z64* V, int64_t vsV, const z64* w, i
 }
 void launch_hreduce(const SlotState* st, const z64* partial, int64_t n, z64* h, int64_t hstride, int nslot,
                     cudaStream_t s) {
-  k_hreduce<<<nslot, MAX_M, 0, s>>>(st, partial, mdot_blocks(n), h, hstride);
+  k_hreduce<<<nslot, 1024, 0, s>>>(st, partial, mdot_blocks(n), h, hstride);
 }
 void launch_maxpy(const SlotState* st, const z64* V, int64_t vsV, const z64* h, int64_t hstride, z64* w, int64_t n,
                   int nslot, cudaStream_t s) {
@@ -468,7 +489,7 @@ void launch_maxpy(const SlotState* st, const z64* V, int64_t vsV, const z64* h, 
 }
 void launch_arnoldi_finish(SlotState* st, int nslot, const z64* h12, const double* wpart, const double* mpart,
                            int nblocks, z64* H, int m, double* pn, int32_t* cyc, double rtol, cudaStream_t s) {
-  k_arnoldi_finish<<<nslot, 128, 0, s>>>(st, nslot, h12, wpart, mpart, nblocks, H, m, pn, cyc, rtol);
+  k_arnoldi_finish<<<nslot, 512, 0, s>>>(st, nslot, h12, wpart, mpart, nblocks, H, m, pn, cyc, rtol);
 }
 void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, int m, z64* V, int64_t vsV, int nslot,
                   cudaStream_t s) {
@@ -482,20 +503,20 @@ void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H,
   k_givens<<<gr, GV_WARPS * 32, 0, s>>>(st, nf, m, sigma, H, taus_k, pn, tol, variant, replay_mj, g, rc, rs, R, Y, sst,
                                         mj, est, bnd);
 }
-void launch_step_end(SlotState* st, int nslot, int m, cudaStream_t s) {
-  k_step_end<<<nbk(nslot, 64), 64, 0, s>>>(st, nslot, m);
+void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_step_end<<<1, 256, 0, s>>>(st, nslot, m, use_cond, cond);
 }
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
                      int nslot, cudaStream_t s) {
   dim3 g(nbk(n, 256), nslot, nbk(nf, AS_J));
   k_assemble<<<g, 256, 0, s>>>(Z, vsZ, Y, mj, nf, m, X, n);
 }
-int tres_blocks(int64_t n) { return (int)nbk(n, 256); }
+int tres_blocks(const LevelHost& L) { return (int)(nbk(L.nx, GX) * nbk((int64_t)L.ny * L.nz, GY)); }
 void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z64* b, const z64* X, double* partial,
                           const SlotState* st, double* out, int nslot, cudaStream_t s) {
-  dim3 g(tres_blocks(L.n), nf, nslot);
-  k_tres_partial<<<g, 256, 0, s>>>(view<double>(L), sigma, nf, b, X, partial);
-  k_tres_finish<<<nbk((int64_t)nf * nslot, 128), 128, 0, s>>>(st, partial, tres_blocks(L.n), nf, nslot, out);
+  dim3 g(nbk(L.nx, GX), nbk((int64_t)L.ny * L.nz, GY), nf * nslot);
+  k_tres_partial<<<g, dim3(GX, GY), 0, s>>>(view<double>(L), sigma, nf, b, X, partial);
+  k_tres_finish<<<nbk((int64_t)nf * nslot, 8), 256, 0, s>>>(st, partial, tres_blocks(L), nf, nslot, out);
 }
 
 }  // namespace fks

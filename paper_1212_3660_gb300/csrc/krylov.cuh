@@ -12,7 +12,7 @@ constexpr int AS_J = 8;          // shifts per block of the assembly kernel
 
 int norm_blocks(int64_t n);
 int mdot_blocks(int64_t n);
-int tres_blocks(int64_t n);
+int tres_blocks(const LevelHost& L);
 
 void launch_norm2_partial(const SlotState* st, int need_active, const z64* x, int64_t vs, int64_t n, double* partial,
                           int nslot, cudaStream_t s);
@@ -20,8 +20,8 @@ void launch_start(SlotState* st, int nslot, const double* partial, int nblocks, 
 void launch_init_v1(const SlotState* st, const z64* b, int64_t n, z64* V, int64_t vsV, int nslot, cudaStream_t s);
 void launch_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_t* mj, double* est, double* bnd,
                         z64* Y, int nslot, cudaStream_t s);
-void launch_step_begin(SlotState* st, int nslot, int step, const int32_t* sched, int sched_len, const z64* taus,
-                       z64* taus_k, int m, cudaStream_t s);
+void launch_step_begin(SlotState* st, int nslot, const int32_t* sched, int sched_len, const z64* taus, z64* taus_k,
+                       int m, cudaStream_t s);
 void launch_mass(const SlotState* st, const double* mm, const z64* Z, int64_t vsZ, z64* w, int64_t n, double* partial,
                  int nslot, cudaStream_t s);
 void launch_mdot(const SlotState* st, const z64* V, int64_t vsV, const z64* w, int64_t n, z64* partial, int kmax,
@@ -37,7 +37,7 @@ void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, in
 void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H, const z64* taus_k, const double* pn,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
                    int32_t* sst, int32_t* mj, double* est, double* bnd, int nslot, cudaStream_t s);
-void launch_step_end(SlotState* st, int nslot, int m, cudaStream_t s);
+void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
                      int nslot, cudaStream_t s);
 void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z64* b, const z64* X, double* partial,

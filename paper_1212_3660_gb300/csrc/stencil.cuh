@@ -10,14 +10,47 @@ struct Cell {
   int i, j, k;
 };
 
-__device__ __forceinline__ Cell cell_of(int64_t c, int nx, int ny) {
+// Cell of flat index c (32-bit: a level has fewer than 2^31 cells).
+__device__ __forceinline__ Cell cell_of(int c, int nx, int ny) {
   Cell r;
-  r.i = (int)(c % nx);
-  int64_t q = c / nx;
-  r.j = (int)(q % ny);
-  r.k = (int)(q / ny);
+  int q = c / nx;
+  r.i = c - q * nx;
+  r.k = q / ny;
+  r.j = q - r.k * ny;
   return r;
 }
+
+// Launch shape of the grid kernels: block (GX, GY) threads, x along i, y along
+// the rows (j, k) of the level, z along the sources.
+constexpr int GX = 32, GY = 8;
+
+// Cell of this thread in a (i, row) launch; false past the grid.
+__device__ __forceinline__ bool grid_cell(int nx, int ny, int nz, Cell* p, int* c) {
+  int i = blockIdx.x * GX + threadIdx.x;
+  int row = blockIdx.y * GY + threadIdx.y;
+  if (i >= nx || row >= ny * nz) return false;
+  int k = row / ny;
+  *p = Cell{i, row - k * ny, k};
+  *c = row * nx + i;
+  return true;
+}
+
+// Cell of colour `color` of this thread in a (half-row index, row) launch.
+__device__ __forceinline__ bool grid_color_cell(int nx, int ny, int nz, int color, Cell* p, int* c) {
+  int ii = blockIdx.x * GX + threadIdx.x;
+  int row = blockIdx.y * GY + threadIdx.y;
+  if (row >= ny * nz) return false;
+  int k = row / ny;
+  int j = row - k * ny;
+  int i = 2 * ii + ((j + k + color) & 1);
+  if (i >= nx) return false;
+  *p = Cell{i, j, k};
+  *c = row * nx + i;
+  return true;
+}
+
+__device__ __forceinline__ int block_linear() { return blockIdx.y * gridDim.x + blockIdx.x; }
+__device__ __forceinline__ int thread_linear() { return threadIdx.y * GX + threadIdx.x; }
 
 template <typename T>
 struct Faces {
@@ -74,6 +107,103 @@ __device__ __forceinline__ cx<T> apply_at(const LevelView<T>& L, Cell p, int64_t
   T m = L.mm[c];
   cx<T> diag = mk(d + s.re * m, s.im * m);
   return diag * x[c] - nb_sum(L, f, p, c, x);
+}
+
+// Red-black Gauss-Seidel update of cell c: (f_c + sum_nb t z_nb) / (K_cc + tau M_cc),
+// the neighbours taken as zero when `zero_start`.
+template <typename T>
+__device__ __forceinline__ cx<T> gs_value(const LevelView<T>& L, Cell p, int64_t c, cx<T> id, const cx<T>* f,
+                                          const cx<T>* z, int zero_start) {
+  cx<T> rhs = f[c];
+  if (!zero_start) {
+    Faces<T> fc = faces_at(L, p);
+    rhs = rhs + nb_sum(L, fc, p, c, z);
+  }
+  return id * rhs;
+}
+
+// Cell of colour `color` handled by work item t of a half sweep (false if none).
+__device__ __forceinline__ bool color_cell(int nx, int ny, int nz, int color, int t, Cell* p, int* c) {
+  int nxh = (nx + 1) >> 1;
+  int rows = ny * nz;
+  if (t >= nxh * rows) return false;
+  int row = t / nxh;
+  int k = row / ny;
+  int j = row - k * ny;
+  int i = 2 * (t - row * nxh) + ((j + k + color) & 1);
+  if (i >= nx) return false;
+  *p = Cell{i, j, k};
+  *c = row * nx + i;
+  return true;
+}
+
+// Sum over the children of coarse cell (I,J,K) of the fine residual f - (K + s M) z.
+template <typename T>
+__device__ __forceinline__ cx<T> restrict_value(const LevelView<T>& F, int rx, int ry, int rz, int I, int J, int K,
+                                                cx<T> s, const cx<T>* f, const cx<T>* z) {
+  cx<T> acc = mk(T(0), T(0));
+  for (int c = 0; c < rz; ++c)
+    for (int b = 0; b < ry; ++b)
+      for (int a = 0; a < rx; ++a) {
+        Cell p{rx * I + a, ry * J + b, rz * K + c};
+        int64_t cc = ((int64_t)p.k * F.ny + p.j) * F.nx + p.i;
+        acc = acc + (f[cc] - apply_at(F, p, cc, s, z));
+      }
+  return acc;
+}
+
+// (P zc)_c: cell-centred (bi/tri)linear interpolation from the coarser level.
+// Per coarsened axis: 3/4 on the parent, 1/4 on the coarse neighbour on the
+// child's side; past a zero-head face the ghost is -parent (weight 1/2 on the
+// parent), past a no-flow face +parent (weight 1).
+template <typename T>
+__device__ __forceinline__ cx<T> prolong_value(Cell p, int rx, int ry, int rz, int cnx, int cny, int cnz,
+                                               uint32_t mask, const cx<T>* zc) {
+  int par[3] = {p.i / rx, p.j / ry, p.k / rz};
+  int idx[3] = {p.i, p.j, p.k};
+  int rr[3] = {rx, ry, rz};
+  int nn[3] = {cnx, cny, cnz};
+  int ti[3][2];
+  T tw[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ti[a][0] = par[a];
+    ti[a][1] = par[a];
+    if (rr[a] == 1) {
+      tw[a][0] = T(1);
+      tw[a][1] = T(0);
+      continue;
+    }
+    int nb = (idx[a] & 1) ? par[a] + 1 : par[a] - 1;
+    if (nb >= 0 && nb < nn[a]) {
+      tw[a][0] = T(0.75);
+      ti[a][1] = nb;
+      tw[a][1] = T(0.25);
+    } else {
+      bool dir = nb < 0 ? ((mask >> (2 * a)) & 1u) : ((mask >> (2 * a + 1)) & 1u);
+      tw[a][0] = dir ? T(0.5) : T(1);
+      tw[a][1] = T(0);
+    }
+  }
+  cx<T> acc = mk(T(0), T(0));
+#pragma unroll
+  for (int c2 = 0; c2 < 2; ++c2) {
+    T wz = tw[2][c2];
+    if (wz == T(0)) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      T wy = tw[1][b];
+      if (wy == T(0)) continue;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        T wx = tw[0][a];
+        if (wx == T(0)) continue;
+        int64_t cc = ((int64_t)ti[2][c2] * cny + ti[1][b]) * cnx + ti[0][a];
+        acc = acc + (wx * wy * wz) * zc[cc];
+      }
+    }
+  }
+  return acc;
 }
 
 }  // namespace fks

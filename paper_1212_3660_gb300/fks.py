@@ -23,7 +23,7 @@ FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1,
 FKS_FGMRES, FKS_FFOM = 0, 1
 FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
 KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
-                  "assemble", "tres"]
+                  "assemble", "tres", "tail"]
 
 
 class fks_c128(C.Structure):
@@ -35,7 +35,7 @@ class fks_options(C.Structure):
                 ("inner_tol", C.c_double), ("inner_max_cycles", C.c_int),
                 ("tau_schedule", C.POINTER(C.c_int32)), ("sched_len", C.c_int),
                 ("replay_mode", C.c_int), ("replay_inner_cycles", C.POINTER(C.c_int32)),
-                ("replay_mj", C.POINTER(C.c_int32))]
+                ("replay_mj", C.POINTER(C.c_int32)), ("launch_mode", C.c_int)]
 
 
 class fks_info(C.Structure):
@@ -150,7 +150,7 @@ def fks_op_size(op) -> int:
 
 
 def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP64, inner_tol=0.0,
-                 inner_max_cycles=50, schedule=(0,), replay_cycles=None, replay_mj=None):
+                 inner_max_cycles=50, schedule=(0,), replay_cycles=None, replay_mj=None, launch_mode=0):
     """fks_options plus the arrays it points to (kept alive in the returned tuple)."""
     sched = np.ascontiguousarray(schedule, dtype=np.int32)
     o = fks_options()
@@ -158,6 +158,7 @@ def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP6
     o.inner_tol, o.inner_max_cycles = float(inner_tol), int(inner_max_cycles)
     o.tau_schedule = sched.ctypes.data_as(C.POINTER(C.c_int32))
     o.sched_len = len(sched)
+    o.launch_mode = int(launch_mode)
     keep = [sched]
     if replay_cycles is not None:
         rc = np.ascontiguousarray(replay_cycles, dtype=np.int32)

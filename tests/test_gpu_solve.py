@@ -155,3 +155,19 @@ def test_invalid_arguments_rejected_before_device_work():
     with pytest.raises(fks.FksError):
         fks.fks_op_grid(s.ctx, 2, (16, 16), (1.0, 1.0), -np.ones(256), np.ones(256), 0xF)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_graph_and_host_driven_loops_agree_bitwise(precision):
+    """The step loop as one CUDA graph (conditional WHILE nodes) runs the same
+    kernels in the same order as the host-driven loop."""
+    need_gpu()
+    pr = synth.make_problem((48, 48), n_f=6, periods=(5.0, 3600.0), n_p=3, seed=16, n_src=2, m_max=60)
+    s = Solver(pr)
+    g = s.solve(precision=precision, inner_tol=1e-10, launch_mode=0)
+    h = s.solve(precision=precision, inner_tol=1e-10, launch_mode=1)
+    g2 = s.solve(precision=precision, inner_tol=1e-10, launch_mode=0)     # cached graph, second launch
+    assert np.array_equal(g.X, h.X) and np.array_equal(g2.X, h.X)
+    assert np.array_equal(g.m_j, h.m_j) and np.array_equal(g.inner_cycles, h.inner_cycles)
+    assert np.array_equal(g.steps, h.steps)
+    s.close()
