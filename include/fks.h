@@ -193,7 +193,9 @@ enum {
   FKS_K_ASSEMBLE = 9,  /* x_j = Z y_j                                             */
   FKS_K_TRES = 10,     /* true residuals                                          */
   FKS_K_TAIL = 11,     /* the V-cycle of all small levels in one block per source */
-  FKS_K_COUNT = 12
+  FKS_K_PRE2D = 12,    /* 2D level: four pre-smoothing half sweeps + residual + restriction */
+  FKS_K_POST2D = 13,   /* 2D level: prolongation + four post-smoothing half sweeps */
+  FKS_K_COUNT = 14
 };
 /*
  * Time every launch of kernel class `kclass` (on level `level`, or every level

@@ -203,7 +203,7 @@ struct Solve {
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
   int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular, *flags, *counter;
   // multigrid, cycle precision
-  std::vector<void*> f, z, invd;
+  std::vector<void*> f, z, z2, invd;
   void* cinv;      // coarse inverse in cycle precision
   z64* cwork;      // dense coarse matrices
   z64* cinv64;
@@ -237,8 +237,9 @@ static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
   return e * sizeof(cx<VT>);
 }
 
+// One V-cycle on f[0]; returns the buffer holding the level-0 correction.
 template <typename VT>
-static void vcycle(Solve& S) {
+static cx<VT>* vcycle(Solve& S) {
   auto& Ls = S.op->levels;
   int nl = (int)Ls.size();
   int lt = tail_level<VT>(Ls);
@@ -254,6 +255,12 @@ static void vcycle(Solve& S) {
   auto smooth_f = [&](const LevelHost& L, int zs) { return zs ? ns * L.n * 3.0 : ns * L.n * 0.5 * (8 * d + 6); };
   for (int l = 0; l < lt; ++l) {
     const LevelHost& L = Ls[l];
+    if (fused_level_ok(L)) {
+      PROF(FKS_K_PRE2D, l, ns * (L.n * (3 * cv + (d + 1) * rv) + cv * Ls[l + 1].n),
+           ns * L.n * (2 * (8 * d + 6) + 8 * d + 10),
+           launch_pre2d<VT>(L, Ls[l + 1], S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot, s));
+      continue;
+    }
     for (int r = 0; r < NU1; ++r) {
       int zs = r == 0 ? 1 : 0;
       PROF(FKS_K_SMOOTH, l, smooth_b(L, zs), smooth_f(L, zs),
@@ -293,17 +300,29 @@ static void vcycle(Solve& S) {
     tf += 8.0 * C.n * C.n;
     PROF(FKS_K_TAIL, lt, ns * tb, ns * tf, launch_tail<VT>(P, tail_smem<VT>(Ls, lt), S.st, S.nslot, s));
   }
+  cx<VT>* zfin = Zl(lt);  // final correction of the level below
   for (int l = lt - 1; l >= 0; --l) {
     const LevelHost& L = Ls[l];
+    if (fused_level_ok(L)) {
+      cx<VT>* out = (cx<VT>*)S.z2[l];
+      PROF(FKS_K_POST2D, l, ns * (L.n * (4 * cv + d * rv) + cv * Ls[l + 1].n),
+           ns * L.n * (18 + 2 * (8 * d + 6)),
+           launch_post2d<VT>(L, Ls[l + 1], S.op->mask, S.st, I(l), F(l), Zl(l), out, L.n, zfin, Ls[l + 1].n,
+                             S.nslot, s));
+      zfin = out;
+      continue;
+    }
     PROF(FKS_K_PROLONG, l, ns * (2 * cv * L.n + cv * Ls[l + 1].n), ns * L.n * (4.0 * (1 << S.op->dim) + 2),
-         launch_prolong_add<VT>(L, Ls[l + 1], S.op->mask, S.st, Zl(l + 1), Ls[l + 1].n, Zl(l), L.n, S.nslot, s));
+         launch_prolong_add<VT>(L, Ls[l + 1], S.op->mask, S.st, zfin, Ls[l + 1].n, Zl(l), L.n, S.nslot, s));
     for (int r = 0; r < NU2; ++r) {
       PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
            launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s));
       PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
            launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, 0, s));
     }
+    zfin = Zl(l);
   }
+  return zfin;
 }
 
 static bool any_inner_running(Solve& S) {
@@ -348,10 +367,9 @@ static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t 
                            cudaGraphConditionalHandle hin) {
   const LevelHost& L0 = S.op->levels[0];
   cx<VT>* f0 = (cx<VT>*)S.f[0];
-  cx<VT>* e0 = (cx<VT>*)S.z[0];
   const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
   const double cv = sizeof(cx<VT>), d = S.op->dim, ns = S.nslot, n = L0.n;
-  vcycle<VT>(S);
+  cx<VT>* e0 = vcycle<VT>(S);
   PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
        launch_correct<VT>(S.st, Z, vsZ, L0.n, e0, L0.n, L0.n, S.nslot, S.s));
   PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 1) + cv), ns * n * (8 * d + 14),
@@ -482,6 +500,7 @@ template <typename VT>
 static void setup_levels(Solve& S) {
   auto& Ls = S.op->levels;
   tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls)));
+  fused_prepare<VT>();
   for (size_t l = 0; l < Ls.size(); ++l)
     PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
   const LevelHost& C = Ls.back();
@@ -515,10 +534,12 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.w = A.take<z64>((size_t)ns * n);
   S.f.assign(Ls.size(), nullptr);
   S.z.assign(Ls.size(), nullptr);
+  S.z2.assign(Ls.size(), nullptr);
   S.invd.assign(Ls.size(), nullptr);
   for (size_t l = 0; l < Ls.size(); ++l) {
     S.f[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
     S.z[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
+    S.z2[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
     S.invd[l] = A.take<cx<VT>>((size_t)S.n_tau * Ls[l].n);
   }
   int64_t nc = Ls.back().n;

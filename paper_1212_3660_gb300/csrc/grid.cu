@@ -226,6 +226,164 @@ __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, i
   zs[c] = zs[c] + prolong_value(p, rx, ry, rz, cnx, cny, cnz, mask, zc + slot * vsc);
 }
 
+// --------------------------------------------------------------------- fused 2D level kernels
+// One level of the V-cycle on a 2D grid coarsened in both axes, in two
+// kernels over TX x TY tiles with a halo of H = 4 cells held in shared memory.
+// Red-black half sweeps only read the other colour, so every half sweep is
+// recomputed on a region that shrinks by one cell per sweep; the tile interior
+// then holds exactly the values of the per-sweep kernels.
+//   pre : z = four half sweeps from z = 0 (red, black, red, black); write z;
+//         coarse f = sum over children of (f - A z)
+//   post: z += P z_coarse; four half sweeps (black, red, black, red); write z
+constexpr int FH = 4;
+
+// sum over existing neighbours of t_face * z_nb for a 2D cell held at r in a
+// shared tile of row length RX (same order as nb_sum)
+template <typename T>
+__device__ __forceinline__ cx<T> nb_sum_tile(const LevelView<T>& L, Cell p, int r, int RX, const cx<T>* sZ) {
+  Faces<T> f = faces_at(L, p);
+  cx<T> s = mk(T(0), T(0));
+  if (p.i > 0) s = s + f.xl * sZ[r - 1];
+  if (p.i < L.nx - 1) s = s + f.xh * sZ[r + 1];
+  if (p.j > 0) s = s + f.yl * sZ[r - RX];
+  if (p.j < L.ny - 1) s = s + f.yh * sZ[r + RX];
+  return s;
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256) k_pre2d(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+                                               const z64* taus, const cx<T>* __restrict__ f, cx<T>* __restrict__ z,
+                                               int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
+  constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
+  extern __shared__ __align__(16) unsigned char pre_smem[];
+  cx<T>* sF = (cx<T>*)pre_smem;
+  cx<T>* sZ = sF + RX * RY;
+  int slot = blockIdx.z;
+  if (!slot_running(st, slot)) return;
+  const int tau = st[slot].tau;
+  const cx<T> sft = cvt<T>(taus[tau]);
+  const cx<T>* ID = invd + (int64_t)tau * L.n;
+  const cx<T>* fs = f + slot * vs;
+  const int x0 = blockIdx.x * TX - FH, y0 = blockIdx.y * TY - FH;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < RX * RY; q += nt) {
+    int ry = q / RX, rx = q - ry * RX;
+    int gx = x0 + rx, gy = y0 + ry;
+    bool in = gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny;
+    sF[q] = in ? fs[gy * L.nx + gx] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  for (int hs = 0; hs < 4; ++hs) {
+    const int color = hs & 1;
+    const int w = RX - 2 * hs, hgt = RY - 2 * hs;
+    const int wh = (w + 1) >> 1;
+    for (int q = tid; q < wh * hgt; q += nt) {
+      int yy = q / wh;
+      int ry = hs + yy;
+      int gy = y0 + ry;
+      int rx0 = hs + 2 * (q - yy * wh);
+      int gx = x0 + rx0;
+      if (((gx + gy) & 1) != color) { ++gx; ++rx0; }
+      if (rx0 >= RX - hs || gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) continue;
+      int r = ry * RX + rx0;
+      int c = gy * L.nx + gx;
+      cx<T> rhs = sF[r];
+      if (hs > 0) rhs = rhs + nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
+      sZ[r] = ID[c] * rhs;
+    }
+    __syncthreads();
+  }
+  cx<T>* zs = z + slot * vs;
+  for (int q = tid; q < TX * TY; q += nt) {
+    int yy = q / TX, xx = q - yy * TX;
+    int gx = x0 + FH + xx, gy = y0 + FH + yy;
+    if (gx < L.nx && gy < L.ny) zs[gy * L.nx + gx] = sZ[(yy + FH) * RX + xx + FH];
+  }
+  // residual + restriction to the (TX/2) x (TY/2) coarse cells of the tile
+  const int cnx = L.nx >> 1, cny = L.ny >> 1;
+  cx<T>* fcs = fc + slot * vsc;
+  for (int q = tid; q < (TX / 2) * (TY / 2); q += nt) {
+    int Yl = q / (TX / 2), Xl = q - Yl * (TX / 2);
+    int X = blockIdx.x * (TX / 2) + Xl, Y = blockIdx.y * (TY / 2) + Yl;
+    if (X >= cnx || Y >= cny) continue;
+    cx<T> acc = mk(T(0), T(0));
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        int gx = 2 * X + a, gy = 2 * Y + b;
+        int r = (gy - y0) * RX + (gx - x0);
+        int c = gy * L.nx + gx;
+        Faces<T> fa = faces_at(L, Cell{gx, gy, 0});
+        T d = fsum(fa), m = L.mm[c];
+        cx<T> Az = mk(d + sft.re * m, sft.im * m) * sZ[r] - nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
+        acc = acc + (sF[r] - Az);
+      }
+    fcs[Y * cnx + X] = acc;
+  }
+}
+
+// post reads the pre-smoothed z and writes zout (a different buffer): tiles
+// read their neighbours' cells as halo, which those tiles overwrite.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, const SlotState* st,
+                                                const cx<T>* __restrict__ invd, const cx<T>* __restrict__ f,
+                                                const cx<T>* __restrict__ z, cx<T>* __restrict__ zout, int64_t vs,
+                                                const cx<T>* __restrict__ zc, int64_t vsc) {
+  constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
+  extern __shared__ __align__(16) unsigned char post_smem[];
+  cx<T>* sF = (cx<T>*)post_smem;
+  cx<T>* sZ = sF + RX * RY;
+  int slot = blockIdx.z;
+  if (!slot_running(st, slot)) return;
+  const int tau = st[slot].tau;
+  const cx<T>* ID = invd + (int64_t)tau * L.n;
+  const cx<T>* fs = f + slot * vs;
+  const cx<T>* zs = z + slot * vs;
+  cx<T>* zo = zout + slot * vs;
+  const cx<T>* zcs = zc + slot * vsc;
+  const int cnx = L.nx >> 1, cny = L.ny >> 1;
+  const int x0 = blockIdx.x * TX - FH, y0 = blockIdx.y * TY - FH;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < RX * RY; q += nt) {
+    int ry = q / RX, rx = q - ry * RX;
+    int gx = x0 + rx, gy = y0 + ry;
+    bool in = gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny;
+    if (in) {
+      int c = gy * L.nx + gx;
+      sF[q] = fs[c];
+      sZ[q] = zs[c] + prolong_value(Cell{gx, gy, 0}, 2, 2, 1, cnx, cny, 1, mask, zcs);
+    } else {
+      sF[q] = mk(T(0), T(0));
+      sZ[q] = mk(T(0), T(0));
+    }
+  }
+  __syncthreads();
+  for (int hs = 0; hs < 4; ++hs) {
+    const int color = (hs & 1) ? 0 : 1;  // black, red, black, red
+    const int sh = hs + 1;
+    const int w = RX - 2 * sh, hgt = RY - 2 * sh;
+    const int wh = (w + 1) >> 1;
+    for (int q = tid; q < wh * hgt; q += nt) {
+      int yy = q / wh;
+      int ry = sh + yy;
+      int gy = y0 + ry;
+      int rx0 = sh + 2 * (q - yy * wh);
+      int gx = x0 + rx0;
+      if (((gx + gy) & 1) != color) { ++gx; ++rx0; }
+      if (rx0 >= RX - sh || gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) continue;
+      int r = ry * RX + rx0;
+      int c = gy * L.nx + gx;
+      cx<T> rhs = sF[r] + nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
+      sZ[r] = ID[c] * rhs;
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < TX * TY; q += nt) {
+    int yy = q / TX, xx = q - yy * TX;
+    int gx = x0 + FH + xx, gy = y0 + FH + yy;
+    if (gx < L.nx && gy < L.ny) zo[gy * L.nx + gx] = sZ[(yy + FH) * RX + xx + FH];
+  }
+}
+
 // --------------------------------------------------------------------- tail
 // The V-cycle of every level from `lt` down (levels small enough for one CTA)
 // in one kernel: one block per slot, level vectors in shared memory,
@@ -585,6 +743,43 @@ void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, c
 }
 
 template <typename T>
+static constexpr int fused_tx() { return 32; }
+template <typename T>
+static constexpr int fused_ty() { return 32; }
+template <typename T>
+static size_t fused_smem() {
+  return 2 * (size_t)(fused_tx<T>() + 2 * FH) * (fused_ty<T>() + 2 * FH) * sizeof(cx<T>);
+}
+
+bool fused_level_ok(const LevelHost& L) { return L.nz == 1 && L.rx == 2 && L.ry == 2 && L.rz == 1; }
+
+template <typename T>
+void fused_prepare() {
+  constexpr int TX = fused_tx<T>(), TY = fused_ty<T>();
+  cudaFuncSetAttribute(k_pre2d<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T>());
+  cudaFuncSetAttribute(k_post2d<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T>());
+}
+
+template <typename T>
+void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
+                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, cudaStream_t s) {
+  constexpr int TX = fused_tx<T>(), TY = fused_ty<T>();
+  dim3 g(nb(F.nx, TX), nb(F.ny, TY), nslot);
+  k_pre2d<T, TX, TY><<<g, 256, fused_smem<T>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+  (void)C;
+}
+
+template <typename T>
+void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
+                   const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
+                   cudaStream_t s) {
+  constexpr int TX = fused_tx<T>(), TY = fused_ty<T>();
+  dim3 g(nb(F.nx, TX), nb(F.ny, TY), nslot);
+  k_post2d<T, TX, TY><<<g, 256, fused_smem<T>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
+  (void)C;
+}
+
+template <typename T>
 void tail_prepare(size_t smem_bytes) {
   cudaFuncSetAttribute(k_tail_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
@@ -629,6 +824,12 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
 }
 
 #define INST(T)                                                                                                  \
+  template void fused_prepare<T>();                                                                               \
+  template void launch_pre2d<T>(const LevelHost&, const LevelHost&, const SlotState*, const cx<T>*, const z64*,    \
+                                const cx<T>*, cx<T>*, int64_t, cx<T>*, int64_t, int, cudaStream_t);               \
+  template void launch_post2d<T>(const LevelHost&, const LevelHost&, uint32_t, const SlotState*, const cx<T>*,     \
+                                 const cx<T>*, const cx<T>*, cx<T>*, int64_t, const cx<T>*, int64_t, int,         \
+                                 cudaStream_t);                                                                   \
   template void tail_prepare<T>(size_t);                                                                          \
   template void launch_tail<T>(const TailParams<T>&, size_t, const SlotState*, int, cudaStream_t);                \
   template void launch_invd<T>(const LevelHost&, const z64*, int, cx<T>*, cudaStream_t);                          \

@@ -31,6 +31,16 @@ struct TailParams {
 
 template <typename T>
 void tail_prepare(size_t smem_bytes);
+bool fused_level_ok(const LevelHost& L);
+template <typename T>
+void fused_prepare();
+template <typename T>
+void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
+                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, cudaStream_t s);
+template <typename T>
+void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
+                   const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
+                   cudaStream_t s);
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);
 

@@ -23,7 +23,7 @@ FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1,
 FKS_FGMRES, FKS_FFOM = 0, 1
 FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
 KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
-                  "assemble", "tres", "tail"]
+                  "assemble", "tres", "tail", "pre2d", "post2d"]
 
 
 class fks_c128(C.Structure):

@@ -34,7 +34,7 @@ def test_operator_apply_matches_oracle(shape, mask):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [(64, 64), (24, 20), (16, 16, 16), (12, 10, 8)])
+@pytest.mark.parametrize("shape", [(64, 64), (24, 20), (16, 16, 16), (12, 10, 8), (96, 80), (200, 136), (40, 40, 24)])
 @pytest.mark.parametrize("cycles", [1, 3])
 def test_fixed_cycles_match_oracle_vcycle(shape, cycles):
     need_gpu()
@@ -52,6 +52,10 @@ def test_fixed_cycles_match_oracle_vcycle(shape, cycles):
     assert c == cycles
     assert rel_err(z, z_ref) <= 1e-12
     assert abs(pn - p_ref) <= 1e-9 * p_ref + 1e-15
+    # complex64 cycles with complex128 defect correction: same iterate to fp32 accuracy
+    z32 = np.zeros_like(v)
+    st, c, pn32 = fks.fks_precond_apply(s.op, tau, v, z32, 1e-30, cycles=cycles, precision=fks.FKS_PREC_MIXED)
+    assert rel_err(z32, z_ref) <= 1e-4
     s.close()
 
 
