@@ -230,6 +230,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
+    tuned = fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
     for _ in range(args.warmup):
         step(b_d, X_d)
     # kernel-class survey (stderr only) and choice of the dominant class
@@ -332,7 +333,7 @@ def main():
                            "l2": "working set larger than L2 (basis V, Z: 2 x 101 x n x 16 B)",
                            "arnoldi_steps": int(info_arr["steps"].max()),
                            "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
-                           "op_setup_ms": setup_ms},
+                           "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),

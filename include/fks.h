@@ -156,6 +156,20 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
                              double* out_pnorm, void* stream);
 
 /*
+ * Autotuner (no counterpart in the paper): times one multigrid V-cycle of the
+ * operator on this GPU for every choice of which 2D levels use the fused
+ * shared-memory tile kernels (levels at most `chosen` cells), for the cycle
+ * precision `precision` and shift `tau`, and keeps the fastest in the operator
+ * for later solves. Solves before any tuning use 65536 (complex128 cycles) and
+ * all levels (complex64 cycles). `chosen` (host, may be NULL) receives the pick.
+ */
+fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen);
+/* Set that threshold directly (max_cells < 0: every fusable level). The fused and
+ * per-sweep kernels perform the same operations in the same order, so results
+ * do not depend on it. */
+fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells);
+
+/*
  * Allocation-free variant of fks_precond_apply (the paper has no counterpart).
  * For callers that may not allocate device memory: code inside a host framework
  * whose memory pool owns the GPU's memory, or real-time code that cannot take

@@ -6,6 +6,7 @@
 // correction in complex128. All per-step state lives in device memory; the
 // host only enqueues kernels and reads small flags to decide when a loop ends.
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -142,6 +143,9 @@ struct fks_op {
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
   int graph_outer = 0, graph_inner = 0;
+  // 2D levels with at most this many cells use the fused tile kernels
+  // ([0] complex128 cycles, [1] complex64 cycles); set by fks_op_autotune
+  int64_t fuse_max[2] = {65536, INT64_MAX};
 };
 
 namespace fks {
@@ -230,11 +234,37 @@ static int tail_level(const std::vector<LevelHost>& Ls) {
   return (int)Ls.size() - 1;
 }
 
+// Shared memory of the tail kernel: f and z of every tail level, then (when it
+// fits) each level's coefficients (faces, storage, inverse diagonals for the
+// current tau). Returns the bytes; `coef_byte` receives each level's offset.
 template <typename VT>
-static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
+static size_t tail_layout(const std::vector<LevelHost>& Ls, int lt, bool staged, std::vector<int>* coef_byte) {
   size_t e = 0;
   for (size_t l = lt; l < Ls.size(); ++l) e += 2 * (size_t)Ls[l].n;
-  return e * sizeof(cx<VT>);
+  size_t bytes = e * sizeof(cx<VT>);
+  if (coef_byte) coef_byte->assign(Ls.size(), -1);
+  if (!staged) return bytes;
+  for (size_t l = lt; l < Ls.size(); ++l) {
+    const LevelHost& L = Ls[l];
+    size_t realn = face_count(L, 0) + face_count(L, 1) + (L.nz > 1 ? face_count(L, 2) : 0) + L.n;
+    realn = (realn + 3) & ~(size_t)3;
+    bytes = (bytes + 15) & ~(size_t)15;
+    if (coef_byte) (*coef_byte)[l] = (int)bytes;
+    bytes += realn * sizeof(VT) + (size_t)L.n * sizeof(cx<VT>);
+  }
+  return bytes;
+}
+
+constexpr size_t TAIL_SMEM_LIMIT = 220 * 1024;
+
+template <typename VT>
+static bool tail_staged(const std::vector<LevelHost>& Ls, int lt) {
+  return tail_layout<VT>(Ls, lt, true, nullptr) <= TAIL_SMEM_LIMIT;
+}
+
+template <typename VT>
+static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
+  return tail_layout<VT>(Ls, lt, tail_staged<VT>(Ls, lt), nullptr);
 }
 
 // One V-cycle on f[0]; returns the buffer holding the level-0 correction.
@@ -253,9 +283,10 @@ static cx<VT>* vcycle(Solve& S) {
     return zs ? ns * L.n * 1.5 * cv : ns * L.n * (2 * cv + d * rv);
   };
   auto smooth_f = [&](const LevelHost& L, int zs) { return zs ? ns * L.n * 3.0 : ns * L.n * 0.5 * (8 * d + 6); };
+  const int64_t fmax = S.op->fuse_max[sizeof(VT) == 8 ? 0 : 1];
   for (int l = 0; l < lt; ++l) {
     const LevelHost& L = Ls[l];
-    if (fused_level_ok(L)) {
+    if (fused_level_ok(L) && L.n <= fmax) {
       PROF(FKS_K_PRE2D, l, ns * (L.n * (3 * cv + (d + 1) * rv) + cv * Ls[l + 1].n),
            ns * L.n * (2 * (8 * d + 6) + 8 * d + 10),
            launch_pre2d<VT>(L, Ls[l + 1], S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot, s));
@@ -276,6 +307,9 @@ static cx<VT>* vcycle(Solve& S) {
     // levels lt .. coarsest in one block per slot
     TailParams<VT> P{};
     P.nlev = nl - lt;
+    P.staged = tail_staged<VT>(Ls, lt) ? 1 : 0;
+    std::vector<int> cbyte;
+    tail_layout<VT>(Ls, lt, P.staged != 0, &cbyte);
     int off = 0;
     double tb = 0, tf = 0;
     for (int l = lt; l < nl; ++l) {
@@ -284,6 +318,7 @@ static cx<VT>* vcycle(Solve& S) {
       T.rx = Ls[l].rx; T.ry = Ls[l].ry; T.rz = Ls[l].rz;
       T.invd = I(l);
       T.off = off;
+      T.cbyte = cbyte[l];
       off += 2 * (int)Ls[l].n;
       tb += Ls[l].n * (8 * cv + d * rv);
       tf += Ls[l].n * (8 * d + 6) * 4;
@@ -303,7 +338,7 @@ static cx<VT>* vcycle(Solve& S) {
   cx<VT>* zfin = Zl(lt);  // final correction of the level below
   for (int l = lt - 1; l >= 0; --l) {
     const LevelHost& L = Ls[l];
-    if (fused_level_ok(L)) {
+    if (fused_level_ok(L) && L.n <= fmax) {
       cx<VT>* out = (cx<VT>*)S.z2[l];
       PROF(FKS_K_POST2D, l, ns * (L.n * (4 * cv + d * rv) + cv * Ls[l + 1].n),
            ns * L.n * (18 + 2 * (8 * d + 6)),
@@ -632,7 +667,8 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
     if (use_graph) {
       std::vector<double> key = {(double)(uintptr_t)op->ws.base, (double)n_rhs, (double)n_f, (double)n_tau, (double)m,
                                  (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
-                                 S.eps, S.tol, (double)S.max_cycles};
+                                 S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
+                                 (double)op->fuse_max[1]};
       if (!op->graph || op->graph_key != key) {
         if (op->graph) cudaGraphExecDestroy(op->graph);
         op->graph = nullptr;
@@ -879,6 +915,108 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
     set_error(std::string("fks_solve: ") + e.where + ": " + cudaGetErrorString(e.e));
     return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
   }
+}
+
+fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells) {
+  if (!op) { set_error("fks_op_set_fusion: NULL operator"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_fusion: bad precision"); return FKS_ERR_ARG; }
+  op->fuse_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
+  return FKS_OK;
+}
+
+fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen) {
+  if (!op) { set_error("fks_op_autotune: NULL operator"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_autotune: bad precision"); return FKS_ERR_ARG; }
+  if (!finite_c(tau)) { set_error("fks_op_autotune: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  int pi = precision == FKS_PREC_FP64 ? 0 : 1;
+  int64_t saved = op->fuse_max[pi];
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    Solve S{};
+    S.op = op;
+    S.s = s;
+    S.nslot = 1;
+    S.n_f = 1;
+    S.n_tau = 1;
+    S.m = 1;
+    S.sched_len = 1;
+    S.precision = precision;
+    S.n = op->n;
+    S.eps = 1e-30;
+    S.max_cycles = 1;
+    SlotState sh{};
+    S.st_host = &sh;
+    auto run = [&](auto tag) {
+      using VT = decltype(tag);
+      Arena probe;
+      carve<VT>(S, probe, false);
+      op->ws.reserve(probe.off + 4096);
+      carve<VT>(S, op->ws, false);
+      const LevelHost& L0 = op->levels[0];
+      CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
+      SlotState st0{};
+      st0.active = 1;
+      st0.k = 1;
+      CK(cudaMemcpyAsync(S.st, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(S.f[0], 0, sizeof(cx<VT>) * L0.n, s));
+      setup_levels<VT>(S);
+      // candidate thresholds that change which levels are fused
+      std::vector<int64_t> cand = {0};
+      for (auto& L : op->levels)
+        if (fused_level_ok(L)) cand.push_back(L.n);
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      cudaStream_t cs = nullptr;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      double best = 1e30;
+      int64_t pick = saved;
+      for (int64_t c : cand) {
+        op->fuse_max[pi] = c;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        S.s = cs;
+        S.capturing = true;
+        int64_t keep = op->prof.all_launches;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        vcycle<VT>(S);
+        CK(cudaStreamEndCapture(cs, &g));
+        op->prof.all_launches = keep;
+        S.capturing = false;
+        S.s = s;
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        for (int w = 0; w < 3; ++w) CK(cudaGraphLaunch(ge, s));
+        const int reps = 10;
+        CK(cudaEventRecord(e0, s));
+        for (int w = 0; w < reps; ++w) CK(cudaGraphLaunch(ge, s));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+        if (ms < best) {
+          best = ms;
+          pick = c;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaStreamDestroy(cs);
+      op->fuse_max[pi] = pick;
+    };
+    if (precision == FKS_PREC_FP64) run(double{});
+    else run(float{});
+  } catch (CudaError& e) {
+    op->fuse_max[pi] = saved;
+    set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return FKS_ERR_CUDA;
+  }
+  if (chosen) *chosen = op->fuse_max[pi];
+  return FKS_OK;
 }
 
 fks_status fks_profile_select(fks_op* op, int kclass, int level) {

@@ -16,6 +16,25 @@ struct alignas(2 * sizeof(T)) cx {
   T re, im;
 };
 
+// Rounding is pinned with explicit intrinsics (no compiler FMA contraction
+// choices), so that every kernel that computes the same update gets the same bits.
+template <typename T>
+__host__ __device__ __forceinline__ T fmaT(T a, T b, T c) {
+#ifdef __CUDA_ARCH__
+  if constexpr (sizeof(T) == 8) return __fma_rn(a, b, c); else return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+template <typename T>
+__host__ __device__ __forceinline__ T mulT(T a, T b) {
+#ifdef __CUDA_ARCH__
+  if constexpr (sizeof(T) == 8) return __dmul_rn(a, b); else return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { return cx<T>{a, b}; }
 template <typename T>
@@ -24,18 +43,23 @@ template <typename T>
 __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
-  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+  return mk(fmaT(a.re, b.re, -mulT(a.im, b.im)), fmaT(a.re, b.im, mulT(a.im, b.re)));
 }
 template <typename T>
-__host__ __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(s * a.re, s * a.im); }
+__host__ __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(mulT(s, a.re), mulT(s, a.im)); }
+// acc + s * x (real s)
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> axpy(T s, cx<T> x, cx<T> acc) {
+  return mk(fmaT(s, x.re, acc.re), fmaT(s, x.im, acc.im));
+}
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> conj(cx<T> a) { return mk(a.re, -a.im); }
 template <typename T>
-__host__ __device__ __forceinline__ T abs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+__host__ __device__ __forceinline__ T abs2(cx<T> a) { return fmaT(a.re, a.re, mulT(a.im, a.im)); }
 // conj(a) * b
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> cdot(cx<T> a, cx<T> b) {
-  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+  return mk(fmaT(a.re, b.re, mulT(a.im, b.im)), fmaT(a.re, b.im, -mulT(a.im, b.re)));
 }
 template <typename To, typename Ti>
 __host__ __device__ __forceinline__ cx<To> cvt(cx<Ti> a) { return mk((To)a.re, (To)a.im); }

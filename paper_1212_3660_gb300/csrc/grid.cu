@@ -243,10 +243,10 @@ template <typename T>
 __device__ __forceinline__ cx<T> nb_sum_tile(const LevelView<T>& L, Cell p, int r, int RX, const cx<T>* sZ) {
   Faces<T> f = faces_at(L, p);
   cx<T> s = mk(T(0), T(0));
-  if (p.i > 0) s = s + f.xl * sZ[r - 1];
-  if (p.i < L.nx - 1) s = s + f.xh * sZ[r + 1];
-  if (p.j > 0) s = s + f.yl * sZ[r - RX];
-  if (p.j < L.ny - 1) s = s + f.yh * sZ[r + RX];
+  if (p.i > 0) s = axpy(f.xl, sZ[r - 1], s);
+  if (p.i < L.nx - 1) s = axpy(f.xh, sZ[r + 1], s);
+  if (p.j > 0) s = axpy(f.yl, sZ[r - RX], s);
+  if (p.j < L.ny - 1) s = axpy(f.yh, sZ[r + RX], s);
   return s;
 }
 
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_pre2d(LevelView<T> L, const SlotState* 
         int c = gy * L.nx + gx;
         Faces<T> fa = faces_at(L, Cell{gx, gy, 0});
         T d = fsum(fa), m = L.mm[c];
-        cx<T> Az = mk(d + sft.re * m, sft.im * m) * sZ[r] - nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
+        cx<T> Az = mk(fmaT(sft.re, m, d), mulT(sft.im, m)) * sZ[r] - nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
         acc = acc + (sF[r] - Az);
       }
     fcs[Y * cnx + X] = acc;
@@ -394,21 +394,63 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
   int slot = blockIdx.x;
   if (!slot_running(st, slot)) return;
   extern __shared__ __align__(16) unsigned char tail_smem[];
+  __shared__ LevelView<T> SV[MAX_LEVELS];
+  __shared__ const cx<T>* SI[MAX_LEVELS];
   cx<T>* sh = (cx<T>*)tail_smem;
   const int tau = st[slot].tau;
   const cx<T> sft = cvt<T>(P.taus[tau]);
   const int nt = blockDim.x, tid = threadIdx.x;
+  // level views: coefficients staged in shared memory (one bulk copy) or read from global
+  if (tid < P.nlev) {
+    const TailLevel<T>& A = P.lev[tid];
+    LevelView<T> v = A.L;
+    const cx<T>* id = A.invd + (int64_t)tau * A.L.n;
+    if (P.staged) {
+      int nfx = (v.nx + 1) * v.ny * v.nz, nfy = v.nx * (v.ny + 1) * v.nz;
+      int nfz = v.nz > 1 ? v.nx * v.ny * (v.nz + 1) : 0;
+      T* base = (T*)(tail_smem + A.cbyte);
+      v.fx = base;
+      v.fy = base + nfx;
+      v.fz = base + nfx + nfy;
+      v.mm = base + nfx + nfy + nfz;
+      int realn = nfx + nfy + nfz + v.n;
+      realn = (realn + 3) & ~3;
+      id = (const cx<T>*)(base + realn);
+    }
+    SV[tid] = v;
+    SI[tid] = id;
+  }
+  __syncthreads();
+  if (P.staged) {
+    for (int l = 0; l < P.nlev; ++l) {
+      const TailLevel<T>& A = P.lev[l];
+      const LevelView<T>& v = SV[l];
+      int nfx = (v.nx + 1) * v.ny * v.nz, nfy = v.nx * (v.ny + 1) * v.nz;
+      int nfz = v.nz > 1 ? v.nx * v.ny * (v.nz + 1) : 0;
+      T* dfx = (T*)v.fx;
+      for (int q = tid; q < nfx; q += nt) dfx[q] = A.L.fx[q];
+      T* dfy = (T*)v.fy;
+      for (int q = tid; q < nfy; q += nt) dfy[q] = A.L.fy[q];
+      T* dfz = (T*)v.fz;
+      for (int q = tid; q < nfz; q += nt) dfz[q] = A.L.fz[q];
+      T* dmm = (T*)v.mm;
+      for (int q = tid; q < v.n; q += nt) dmm[q] = A.L.mm[q];
+      cx<T>* did = (cx<T>*)SI[l];
+      const cx<T>* gid = A.invd + (int64_t)tau * v.n;
+      for (int q = tid; q < v.n; q += nt) did[q] = gid[q];
+    }
+  }
   {
     const TailLevel<T>& A = P.lev[0];
     const cx<T>* fin = P.f_in + slot * P.vs;
     for (int c = tid; c < A.L.n; c += nt) sh[A.off + c] = fin[c];
   }
   __syncthreads();
-  auto sweep = [&](const TailLevel<T>& A, int color, int zs) {
-    const LevelView<T>& L = A.L;
-    cx<T>* F = sh + A.off;
+  auto sweep = [&](int l, int color, int zs) {
+    const LevelView<T>& L = SV[l];
+    cx<T>* F = sh + P.lev[l].off;
     cx<T>* Z = F + L.n;
-    const cx<T>* ID = A.invd + (int64_t)tau * L.n;
+    const cx<T>* ID = SI[l];
     int work = ((L.nx + 1) >> 1) * L.ny * L.nz;
     for (int t = tid; t < work; t += nt) {
       Cell p;
@@ -421,15 +463,16 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
     const TailLevel<T>& A = P.lev[l];
     const TailLevel<T>& B = P.lev[l + 1];
     for (int r = 0; r < 2; ++r) {
-      sweep(A, 0, r == 0);
-      sweep(A, 1, 0);
+      sweep(l, 0, r == 0);
+      sweep(l, 1, 0);
     }
     cx<T>* F = sh + A.off;
     cx<T>* Z = F + A.L.n;
     cx<T>* FC = sh + B.off;
+    const LevelView<T>& LA = SV[l];
     for (int C = tid; C < B.L.n; C += nt) {
       Cell pc = cell_of(C, B.L.nx, B.L.ny);
-      FC[C] = restrict_value(A.L, A.rx, A.ry, A.rz, pc.i, pc.j, pc.k, sft, F, Z);
+      FC[C] = restrict_value(LA, A.rx, A.ry, A.rz, pc.i, pc.j, pc.k, sft, F, Z);
     }
     __syncthreads();
   }
@@ -457,8 +500,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
     }
     __syncthreads();
     for (int r = 0; r < 2; ++r) {
-      sweep(A, 1, 0);
-      sweep(A, 0, 0);
+      sweep(l, 1, 0);
+      sweep(l, 0, 0);
     }
   }
   {

@@ -14,6 +14,7 @@ struct TailLevel {
   int rx, ry, rz;          // ratios to the next coarser level
   const cx<T>* invd;       // [n_tau][n] inverse diagonals
   int off;
+  int cbyte;               // byte offset of this level's coefficients staged in shared memory
 };
 
 template <typename T>
@@ -27,6 +28,7 @@ struct TailParams {
   cx<T>* z_out;            // level-lt correction (global)
   int64_t vs;
   const z64* taus;
+  int staged;              // coefficients copied to shared memory at kernel start
 };
 
 template <typename T>

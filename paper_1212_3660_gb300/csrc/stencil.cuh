@@ -88,13 +88,13 @@ __device__ __forceinline__ cx<T> nb_sum(const LevelView<T>& L, const Faces<T>& f
                                         const cx<T>* __restrict__ x) {
   cx<T> s = mk(T(0), T(0));
   int64_t sxy = (int64_t)L.nx * L.ny;
-  if (p.i > 0) s = s + f.xl * x[c - 1];
-  if (p.i < L.nx - 1) s = s + f.xh * x[c + 1];
-  if (p.j > 0) s = s + f.yl * x[c - L.nx];
-  if (p.j < L.ny - 1) s = s + f.yh * x[c + L.nx];
+  if (p.i > 0) s = axpy(f.xl, x[c - 1], s);
+  if (p.i < L.nx - 1) s = axpy(f.xh, x[c + 1], s);
+  if (p.j > 0) s = axpy(f.yl, x[c - L.nx], s);
+  if (p.j < L.ny - 1) s = axpy(f.yh, x[c + L.nx], s);
   if (L.nz > 1) {
-    if (p.k > 0) s = s + f.zl * x[c - sxy];
-    if (p.k < L.nz - 1) s = s + f.zh * x[c + sxy];
+    if (p.k > 0) s = axpy(f.zl, x[c - sxy], s);
+    if (p.k < L.nz - 1) s = axpy(f.zh, x[c + sxy], s);
   }
   return s;
 }
@@ -105,7 +105,7 @@ __device__ __forceinline__ cx<T> apply_at(const LevelView<T>& L, Cell p, int64_t
   Faces<T> f = faces_at(L, p);
   T d = fsum(f);
   T m = L.mm[c];
-  cx<T> diag = mk(d + s.re * m, s.im * m);
+  cx<T> diag = mk(fmaT(s.re, m, d), mulT(s.im, m));
   return diag * x[c] - nb_sum(L, f, p, c, x);
 }
 
@@ -199,7 +199,7 @@ __device__ __forceinline__ cx<T> prolong_value(Cell p, int rx, int ry, int rz, i
         T wx = tw[0][a];
         if (wx == T(0)) continue;
         int64_t cc = ((int64_t)ti[2][c2] * cny + ti[1][b]) * cnx + ti[0][a];
-        acc = acc + (wx * wy * wz) * zc[cc];
+        acc = axpy(mulT(mulT(wx, wy), wz), zc[cc], acc);
       }
     }
   }

@@ -84,10 +84,13 @@ def lib():
     L.fks_precond_apply.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p, f64p, vp]
     L.fks_precond_apply_noalloc.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p,
                                             f64p, vp]
+    L.fks_op_autotune.argtypes = [vp, C.c_int, fks_c128, vp, C.POINTER(C.c_int64)]
+    L.fks_op_set_fusion.argtypes = [vp, C.c_int, C.c_int64]
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
     for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
-                 "fks_profile_read", "fks_precond_apply_noalloc"):
+                 "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
+                 "fks_op_set_fusion"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -219,6 +222,22 @@ def make_info(n_rhs, m_max):
                     arrs["pnorm"].ctypes.data_as(C.POINTER(C.c_double)),
                     arrs["breakdown"].ctypes.data_as(C.POINTER(C.c_int32)))
     return info, arrs
+
+
+def fks_op_autotune(op, precision, tau, stream=None):
+    """Pick the fused-level threshold for `precision` by timing V-cycles; returns it."""
+    ch = C.c_int64(0)
+    st = lib().fks_op_autotune(op, int(precision), fks_c128(complex(tau).real, complex(tau).imag), stream,
+                               C.byref(ch))
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return int(ch.value)
+
+
+def fks_op_set_fusion(op, precision, max_cells):
+    st = lib().fks_op_set_fusion(op, int(precision), int(max_cells))
+    if st < 0:
+        raise FksError(st, fks_last_error())
 
 
 def fks_profile_select(op, kclass, level=-1):

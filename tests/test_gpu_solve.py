@@ -171,3 +171,21 @@ def test_graph_and_host_driven_loops_agree_bitwise(precision):
     assert np.array_equal(g.m_j, h.m_j) and np.array_equal(g.inner_cycles, h.inner_cycles)
     assert np.array_equal(g.steps, h.steps)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
+    """Fused 2D tile kernels and per-half-sweep kernels perform the same
+    operations in the same order; the autotuner's choice cannot change results."""
+    need_gpu()
+    pr = synth.make_problem((192, 160), n_f=5, periods=(5.0, 3600.0), n_p=3, seed=17, m_max=60)
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, 0)
+    a = s.solve(precision=precision, inner_tol=1e-10)
+    fks.fks_op_set_fusion(s.op, precision, -1)
+    b = s.solve(precision=precision, inner_tol=1e-10)
+    picked = fks.fks_op_autotune(s.op, precision, pr.tau_bar[1])
+    c = s.solve(precision=precision, inner_tol=1e-10)
+    assert np.array_equal(a.X, b.X) and np.array_equal(a.X, c.X), picked
+    assert np.array_equal(a.inner_cycles, b.inner_cycles)
+    s.close()
