@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer region (very large outputs)")
     return ap.parse_args()
 
 
@@ -298,22 +299,28 @@ def main():
                 "kernel": dominant, "peak_source": peak_src, "launches": prof["launches"],
                 "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1)}
 
-    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
-    b_h = torch.from_numpy(pr.rhs().T.copy()).pin_memory()
-    X_h = torch.empty((n_rhs, n_f, n), dtype=torch.complex128).pin_memory()
-    step(b_h, X_h)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    conv_e2e = 0
-    for _ in range(args.steps):
+    def end_to_end():
+        b_h = torch.from_numpy(pr.rhs().T.copy()).pin_memory()
+        X_h = torch.empty((n_rhs, n_f, n), dtype=torch.complex128).pin_memory()
         step(b_h, X_h)
-        conv_e2e += int(np.sum(tru <= TOL))
-    torch.cuda.synchronize()
-    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps)
-    e2e_value = sum_over_ranks(conv_e2e / args.steps) / t_e2e
-    h2d = b_h.numel() * 16 + (n_f + len(pr.tau_bar)) * 16
-    d2h = X_h.numel() * 16 + n_rhs * n_f * (8 * 3 + 4 * 2)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv_e2e = 0
+        for _ in range(args.steps):
+            step(b_h, X_h)
+            conv_e2e += int(np.sum(tru <= TOL))
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        e2e_value = sum_over_ranks(conv_e2e / args.steps) / t_e2e
+        h2d = b_h.numel() * 16 + (n_f + len(pr.tau_bar)) * 16
+        d2h = X_h.numel() * 16 + n_rhs * n_f * (8 * 3 + 4 * 2)
+        return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -335,7 +342,7 @@ def main():
                            "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
                            "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": e2e,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)

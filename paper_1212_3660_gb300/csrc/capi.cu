@@ -756,6 +756,75 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
 
 static bool finite_c(const fks_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
+static int status_rank(fks_status s) {
+  switch (s) {
+    case FKS_NOT_CONVERGED: return 3;
+    case FKS_BREAKDOWN_EXACT: return 2;
+    case FKS_INNER_NOT_CONVERGED: return 1;
+    default: return 0;
+  }
+}
+
+// Sources are solved in lockstep batches sized to the free device memory:
+// one batch when they all fit, otherwise equal batches one after another.
+template <typename VT>
+static fks_status solve_chunked(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
+                                const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X, double* res_est,
+                                double* res_bound, double* res_true, int32_t* m_j, int32_t* shift_status,
+                                fks_info* info, cudaStream_t s) {
+  bool x_dev = is_device_ptr(X);
+  auto ws_bytes = [&](int ns) {
+    Solve S{};
+    S.op = op;
+    S.nslot = ns;
+    S.n_f = n_f;
+    S.n_tau = n_tau;
+    S.m = o->m_max;
+    S.sched_len = o->sched_len;
+    S.n = op->n;
+    Arena probe;
+    carve<VT>(S, probe, !x_dev);
+    return probe.off + 4096;
+  };
+  size_t one = ws_bytes(1), two = ws_bytes(2);
+  size_t per = two > one ? two - one : one, fixed = one > per ? one - per : 0;
+  size_t freeb = 0, totb = 0;
+  CK(cudaMemGetInfo(&freeb, &totb));
+  size_t avail = freeb + op->ws.cap;
+  size_t reserve = std::min<size_t>(avail / 20, size_t(2) << 30);
+  avail = avail > reserve ? avail - reserve : 0;
+  int max_slots = (int)std::max<size_t>(1, avail > fixed ? (avail - fixed) / per : 1);
+  int nchunk = (n_rhs + max_slots - 1) / max_slots;
+  int chunk = (n_rhs + nchunk - 1) / nchunk;
+  if (nchunk == 1)
+    return solve_impl<VT>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+                          shift_status, info, s);
+  fks_status worst = FKS_OK;
+  for (int r0 = 0; r0 < n_rhs; r0 += chunk) {
+    int nr = std::min(chunk, n_rhs - r0);
+    fks_options oc = *o;
+    if (o->replay_mode) {
+      oc.replay_inner_cycles = o->replay_inner_cycles + (size_t)r0 * o->m_max;
+      oc.replay_mj = o->replay_mj + (size_t)r0 * n_f;
+    }
+    fks_info ic{};
+    if (info) {
+      ic.steps = info->steps ? info->steps + r0 : nullptr;
+      ic.inner_cycles = info->inner_cycles ? info->inner_cycles + (size_t)r0 * o->m_max : nullptr;
+      ic.pnorm = info->pnorm ? info->pnorm + (size_t)r0 * o->m_max : nullptr;
+      ic.breakdown = info->breakdown ? info->breakdown + r0 : nullptr;
+    }
+    size_t nf = (size_t)n_f * r0;
+    fks_status st = solve_impl<VT>(op, b + (size_t)r0 * op->n, nr, sigma, n_f, tau, n_tau, &oc,
+                                   X + (size_t)r0 * n_f * op->n, res_est + nf, res_bound + nf,
+                                   res_true ? res_true + nf : nullptr, m_j + nf, shift_status + nf,
+                                   info ? &ic : nullptr, s);
+    if (st < 0) return st;
+    if (status_rank(st) > status_rank(worst)) worst = st;
+  }
+  return worst;
+}
+
 }  // namespace fks
 
 // ====================================================================== C ABI
@@ -907,10 +976,10 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   try {
     CK(cudaSetDevice(op->ctx->device));
     if (o->precision == FKS_PREC_FP64)
-      return solve_impl<double>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+      return solve_chunked<double>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+                                   shift_status, info, s);
+    return solve_chunked<float>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
                                 shift_status, info, s);
-    return solve_impl<float>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
-                             shift_status, info, s);
   } catch (CudaError& e) {
     set_error(std::string("fks_solve: ") + e.where + ": " + cudaGetErrorString(e.e));
     return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
