@@ -156,6 +156,44 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
                              double* out_pnorm, void* stream);
 
 /*
+ * Serving (no counterpart in the paper): a request loop over fks_solve.
+ * Worker threads, each with its own stream and workspace ("lane"), admit queued
+ * requests while the device-memory budget allows; requests that share the
+ * operator, the shifts and the options are merged into one batch whose slots
+ * are their sources; batches on different lanes overlap on the device. Each
+ * request's result equals what fks_solve gives it alone. All request arrays are
+ * HOST memory owned by the caller and must stay valid until the request is done;
+ * options' tau_schedule is copied at submit. Replay mode is not accepted.
+ * The server is thread-safe.
+ */
+typedef struct fks_server fks_server;
+typedef struct {
+  fks_op* op;
+  const fks_c128* b; int n_rhs;          /* [n * n_rhs]                                        */
+  const fks_c128* sigma; int n_f;
+  const fks_c128* tau; int n_tau;
+  fks_options opt;
+  fks_c128* X;                           /* [n * n_f * n_rhs] out                               */
+  double* res_est; double* res_bound;    /* [n_f * n_rhs] out                                   */
+  double* res_true;                      /* [n_f * n_rhs] out or NULL                           */
+  int32_t* m_j; int32_t* shift_status;   /* [n_f * n_rhs] out                                   */
+} fks_request;
+/* lanes: concurrent batches (1..64); mem_budget_bytes: device memory the
+ * admitted batches' workspaces may use together (one oversized request still
+ * runs when nothing else is in flight). */
+fks_status fks_server_create(fks_ctx* ctx, size_t mem_budget_bytes, int lanes, fks_server** out);
+fks_status fks_server_submit(fks_server* srv, const fks_request* req, uint64_t* ticket);
+/* done = 1 when finished or cancelled; result = the request's status. */
+fks_status fks_server_poll(fks_server* srv, uint64_t ticket, int* done, fks_status* result);
+fks_status fks_server_wait(fks_server* srv, uint64_t ticket, fks_status* result);
+/* Cancels a request that has not started (FKS_ERR_ARG otherwise); its result is FKS_ERR_CANCELLED. */
+fks_status fks_server_cancel(fks_server* srv, uint64_t ticket);
+/* Host wall-clock seconds (steady clock) of submit, start and end of a request. */
+fks_status fks_server_times(fks_server* srv, uint64_t ticket, double* submit_s, double* start_s, double* end_s);
+/* Stops the workers after their current batches; queued requests are dropped. */
+void fks_server_destroy(fks_server* srv);
+
+/*
  * Autotuner (no counterpart in the paper): times one multigrid V-cycle of the
  * operator on this GPU for every choice of which 2D levels use the fused
  * shared-memory tile kernels (levels at most `chosen` cells), for the cycle

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libfks.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["capi.cu", "grid.cu", "krylov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-g", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

@@ -10,6 +10,12 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
+#include <thread>
+#include <memory>
+#include <deque>
+#include <condition_variable>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -21,6 +27,11 @@
 namespace fks {
 
 static thread_local std::string g_err;
+// Graph capture/instantiation and kernel attribute changes are serialised
+// across threads (the server builds graphs from several worker threads).
+static std::mutex g_build_mu;
+// Serialises the host-side CUDA calls of concurrent server batches.
+static std::mutex g_api_mu;
 void set_error(const std::string& msg) { g_err = msg; }
 const char* get_error() { return g_err.c_str(); }
 
@@ -44,12 +55,15 @@ struct Arena {
   char* base = nullptr;
   size_t cap = 0;
   size_t off = 0;
+  cudaStream_t astream = nullptr;  // stream-ordered allocation on this stream when set
   void reserve(size_t bytes) {
     if (bytes <= cap) return;
-    if (base) cudaFree(base);
+    if (base) {
+      if (astream) cudaFreeAsync(base, astream); else cudaFree(base);
+    }
     base = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc(&base, bytes);
+    cudaError_t e = astream ? cudaMallocAsync((void**)&base, bytes, astream) : cudaMalloc(&base, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       throw CudaError{e, "cudaMalloc(workspace)"};
@@ -57,7 +71,9 @@ struct Arena {
     cap = bytes;
   }
   void release() {
-    if (base) cudaFree(base);
+    if (base) {
+      if (astream) cudaFreeAsync(base, astream); else cudaFree(base);
+    }
     base = nullptr;
     cap = 0;
   }
@@ -122,6 +138,23 @@ struct Prof {
   }
 };
 
+// Everything one in-flight solve owns: workspace, the captured step-loop
+// graph, instrumentation. fks_solve uses the operator's own lane; the server
+// gives each concurrent batch a lane of its own.
+struct Lane {
+  Arena ws;
+  Prof prof;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
+  int graph_outer = 0, graph_inner = 0;
+  void release() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    ws.release();
+    prof.release();
+  }
+};
+
 }  // namespace fks
 
 using namespace fks;
@@ -137,12 +170,7 @@ struct fks_op {
   int64_t n;
   uint32_t mask;
   std::vector<LevelHost> levels;
-  Arena ws;
-  Prof prof;
-  // instantiated graph of the step loop, valid for one workspace layout
-  cudaGraphExec_t graph = nullptr;
-  std::vector<double> graph_key;
-  int graph_outer = 0, graph_inner = 0;
+  Lane lane0;  // workspace, graph and instrumentation of fks_solve / fks_precond_apply
   // 2D levels with at most this many cells use the fused tile kernels
   // ([0] complex128 cycles, [1] complex64 cycles); set by fks_op_autotune
   int64_t fuse_max[2] = {65536, INT64_MAX};
@@ -195,6 +223,7 @@ static std::vector<LevelHost> level_shapes(int nx, int ny, int nz, const double 
 // ------------------------------------------------------------------ solve state
 struct Solve {
   fks_op* op;
+  Lane* lane;
   cudaStream_t s;
   int nslot, n_f, n_tau, m, sched_len, precision, variant;
   int64_t n;
@@ -212,13 +241,16 @@ struct Solve {
   z64* cwork;      // dense coarse matrices
   z64* cinv64;
   bool capturing = false;  // enqueueing into a graph: no event timing
+  // server batches hold this lock for their host-side CUDA calls and release it
+  // only while they wait for their step-loop graph to finish
+  std::unique_lock<std::mutex>* api_lock = nullptr;
 };
 
 #define PROF(cls, lvl, by, fl, call)                                           \
   do {                                                                        \
-    S.op->prof.begin(S.capturing ? -1 : (cls), (lvl), (by), (fl), S.s);       \
+    S.lane->prof.begin(S.capturing ? -1 : (cls), (lvl), (by), (fl), S.s);     \
     call;                                                                     \
-    S.op->prof.end(S.s);                                                      \
+    S.lane->prof.end(S.s);                                                    \
   } while (0)
 
 // Largest level handled by the single-block tail V-cycle: fp64 arithmetic runs
@@ -465,13 +497,14 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
 // are returned for the launch count.
 template <typename VT>
 static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int* inner_kernels) {
+  std::lock_guard<std::mutex> build_lock(g_build_mu);
   const int64_t n = S.n;
   const int m = S.m;
   const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
   cudaStream_t user = S.s;
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
-  int64_t saved = S.op->prof.all_launches;
+  int64_t saved = S.lane->prof.all_launches;
   try {
     CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     CK(cudaGraphCreate(&g, 0));
@@ -487,7 +520,7 @@ static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int
     cudaGraph_t body_out = po.conditional.phGraph_out[0];
     S.s = cs;
     S.capturing = true;
-    int64_t c0 = S.op->prof.all_launches;
+    int64_t c0 = S.lane->prof.all_launches;
     CK(cudaStreamBeginCaptureToGraph(cs, body_out, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     sec_step_begin(S);
     CK(cudaGraphConditionalHandleCreate(&hin, body_out, 0, 0));
@@ -508,25 +541,25 @@ static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int
     sec_step_end(S, m, 1, hout);
     cudaGraph_t cap = nullptr;
     CK(cudaStreamEndCapture(cs, &cap));
-    int64_t c1 = S.op->prof.all_launches;
+    int64_t c1 = S.lane->prof.all_launches;
     CK(cudaStreamBeginCaptureToGraph(cs, body_in, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     sec_inner_body<VT>(S, S.V, vsV, S.Z, vsZ, 1, hin);
     CK(cudaStreamEndCapture(cs, &cap));
-    int64_t c2 = S.op->prof.all_launches;
+    int64_t c2 = S.lane->prof.all_launches;
     *outer_kernels = (int)(c1 - c0);
     *inner_kernels = (int)(c2 - c1);
     CK(cudaGraphInstantiate(exec, g, 0));
   } catch (...) {
     S.s = user;
     S.capturing = false;
-    S.op->prof.all_launches = saved;
+    S.lane->prof.all_launches = saved;
     if (g) cudaGraphDestroy(g);
     if (cs) cudaStreamDestroy(cs);
     throw;
   }
   S.s = user;
   S.capturing = false;
-  S.op->prof.all_launches = saved;
+  S.lane->prof.all_launches = saved;
   cudaGraphDestroy(g);
   cudaStreamDestroy(cs);
 }
@@ -534,15 +567,18 @@ static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int
 template <typename VT>
 static void setup_levels(Solve& S) {
   auto& Ls = S.op->levels;
-  tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls)));
-  fused_prepare<VT>();
+  {
+    std::lock_guard<std::mutex> build_lock(g_build_mu);
+    tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls)));
+    fused_prepare<VT>();
+  }
   for (size_t l = 0; l < Ls.size(); ++l)
     PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
   const LevelHost& C = Ls.back();
   int64_t nc = C.n;
   CK(cudaMemsetAsync(S.singular, 0, sizeof(int), S.s));
   CK(cudaMemsetAsync(S.counter, 0, sizeof(int), S.s));
-  S.op->prof.all_launches += 2;
+  S.lane->prof.all_launches += 2;
   launch_coarse_inverse(C, S.taus, S.n_tau, S.cwork, S.cinv64, S.singular, S.s);
   if constexpr (sizeof(VT) == 8) {
     CK(cudaMemcpyAsync(S.cinv, S.cinv64, sizeof(z64) * S.n_tau * nc * nc, cudaMemcpyDeviceToDevice, S.s));
@@ -608,14 +644,26 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
 }
 
+// Outputs of a run of consecutive slots [r0, r0 + nr) that belong to one
+// caller (the server merges several requests into one batch); host or device.
+struct OutGroup {
+  int r0, nr;
+  fks_c128* X;
+  double *est, *bnd, *tru;
+  int32_t *mj, *sst;
+};
+
 template <typename VT>
-static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
+static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
                              const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X, double* res_est,
                              double* res_bound, double* res_true, int32_t* m_j, int32_t* shift_status, fks_info* info,
-                             cudaStream_t s) {
+                             cudaStream_t s, const std::vector<OutGroup>* groups = nullptr,
+                             std::unique_lock<std::mutex>* api_lock = nullptr) {
   Solve S{};
   S.op = op;
+  S.lane = lane;
   S.s = s;
+  S.api_lock = api_lock;
   S.nslot = n_rhs;
   S.n_f = n_f;
   S.n_tau = n_tau;
@@ -628,13 +676,14 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
   S.eps = o->inner_tol > 0 ? o->inner_tol : std::min(1e-6, o->tol / 100.0);
   S.max_cycles = o->inner_max_cycles > 0 ? o->inner_max_cycles : 50;
   S.replay = o->replay_mode != 0;
-  bool x_dev = is_device_ptr(X);
+  bool x_dev = groups ? false : is_device_ptr(X);
+  if (groups && !res_true) res_true = (double*)1;  // grouped runs always compute true residuals
   // workspace size: carve once on a null base to measure
   Arena probe;
   carve<VT>(S, probe, !x_dev);
   size_t need = probe.off + 4096;
-  op->ws.reserve(need);
-  carve<VT>(S, op->ws, !x_dev);
+  lane->ws.reserve(need);
+  carve<VT>(S, lane->ws, !x_dev);
   z64* Xd = x_dev ? (z64*)X : S.X;
   std::vector<SlotState> st_host(n_rhs);
   S.st_host = st_host.data();
@@ -665,17 +714,28 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
   std::vector<int32_t> cyc_all((size_t)m * n_rhs);
   if (any_active(S)) {
     if (use_graph) {
-      std::vector<double> key = {(double)(uintptr_t)op->ws.base, (double)n_rhs, (double)n_f, (double)n_tau, (double)m,
+      std::vector<double> key = {(double)(uintptr_t)lane->ws.base, (double)n_rhs, (double)n_f, (double)n_tau, (double)m,
                                  (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
                                  (double)op->fuse_max[1]};
-      if (!op->graph || op->graph_key != key) {
-        if (op->graph) cudaGraphExecDestroy(op->graph);
-        op->graph = nullptr;
-        build_graph<VT>(S, &op->graph, &op->graph_outer, &op->graph_inner);
-        op->graph_key = key;
+      if (!lane->graph || lane->graph_key != key) {
+        if (lane->graph) cudaGraphExecDestroy(lane->graph);
+        lane->graph = nullptr;
+        build_graph<VT>(S, &lane->graph, &lane->graph_outer, &lane->graph_inner);
+        lane->graph_key = key;
       }
-      CK(cudaGraphLaunch(op->graph, s));
+      CK(cudaGraphLaunch(lane->graph, s));
+      if (S.api_lock) {
+        // let other batches set up and launch while this graph runs
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        S.api_lock->unlock();
+        cudaError_t we = cudaEventSynchronize(ev);
+        S.api_lock->lock();
+        cudaEventDestroy(ev);
+        CK(we);
+      }
       // launch count: per step the outer section, per inner iteration the inner section
       CK(cudaMemcpyAsync(cyc_all.data(), S.cyc, sizeof(int32_t) * m * n_rhs, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
@@ -687,7 +747,7 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
         for (int r = 0; r < n_rhs; ++r) mx = std::max(mx, cyc_all[(size_t)r * m + k]);
         inner_iters += mx;
       }
-      op->prof.all_launches += (int64_t)steps * op->graph_outer + inner_iters * op->graph_inner;
+      lane->prof.all_launches += (int64_t)steps * lane->graph_outer + inner_iters * lane->graph_inner;
     } else {
       for (int step = 1; step <= m; ++step) {
         steps = step;
@@ -706,18 +766,30 @@ static fks_status solve_impl(fks_op* op, const fks_c128* b, int n_rhs, const fks
     if (res_true)
       PROF(FKS_K_TRES, -1, ns * nn * (16.0 * n_f + 16 + 8 * (d + 1)), ns * nn * n_f * (8 * d + 14),
            launch_true_residual(op->levels[0], S.sigma, n_f, S.b, Xd, S.tpart, S.st, S.tres, n_rhs, s));
-    if (res_true) op->prof.all_launches += 1;  // the true residual is two kernels
+    if (res_true) lane->prof.all_launches += 1;  // the true residual is two kernels
   }
   CK(cudaGetLastError());
   // outputs
-  if (!x_dev) copy_out(X, Xd, sizeof(z64) * n * n_f * n_rhs, s);
-  copy_out(res_est, S.est, sizeof(double) * n_f * n_rhs, s);
-  copy_out(res_bound, S.bnd, sizeof(double) * n_f * n_rhs, s);
-  if (res_true) copy_out(res_true, S.tres, sizeof(double) * n_f * n_rhs, s);
-  copy_out(m_j, S.mj, sizeof(int32_t) * n_f * n_rhs, s);
   std::vector<int32_t> sst_h((size_t)n_f * n_rhs);
   CK(cudaMemcpyAsync(sst_h.data(), S.sst, sizeof(int32_t) * n_f * n_rhs, cudaMemcpyDeviceToHost, s));
-  copy_out(shift_status, S.sst, sizeof(int32_t) * n_f * n_rhs, s);
+  if (groups) {
+    for (const OutGroup& g : *groups) {
+      size_t o0 = (size_t)g.r0 * n_f, cnt = (size_t)g.nr * n_f;
+      copy_out(g.X, Xd + o0 * n, sizeof(z64) * n * cnt, s);
+      copy_out(g.est, S.est + o0, sizeof(double) * cnt, s);
+      copy_out(g.bnd, S.bnd + o0, sizeof(double) * cnt, s);
+      copy_out(g.tru, S.tres + o0, sizeof(double) * cnt, s);
+      copy_out(g.mj, S.mj + o0, sizeof(int32_t) * cnt, s);
+      copy_out(g.sst, S.sst + o0, sizeof(int32_t) * cnt, s);
+    }
+  } else {
+    if (!x_dev) copy_out(X, Xd, sizeof(z64) * n * n_f * n_rhs, s);
+    copy_out(res_est, S.est, sizeof(double) * n_f * n_rhs, s);
+    copy_out(res_bound, S.bnd, sizeof(double) * n_f * n_rhs, s);
+    if (res_true) copy_out(res_true, S.tres, sizeof(double) * n_f * n_rhs, s);
+    copy_out(m_j, S.mj, sizeof(int32_t) * n_f * n_rhs, s);
+    copy_out(shift_status, S.sst, sizeof(int32_t) * n_f * n_rhs, s);
+  }
   std::vector<int32_t> cyc_h;
   std::vector<double> pn_h;
   if (info && info->inner_cycles) cyc_h.resize((size_t)m * n_rhs);
@@ -768,7 +840,7 @@ static int status_rank(fks_status s) {
 // Sources are solved in lockstep batches sized to the free device memory:
 // one batch when they all fit, otherwise equal batches one after another.
 template <typename VT>
-static fks_status solve_chunked(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
+static fks_status solve_chunked(fks_op* op, Lane* lane, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
                                 const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X, double* res_est,
                                 double* res_bound, double* res_true, int32_t* m_j, int32_t* shift_status,
                                 fks_info* info, cudaStream_t s) {
@@ -790,14 +862,14 @@ static fks_status solve_chunked(fks_op* op, const fks_c128* b, int n_rhs, const 
   size_t per = two > one ? two - one : one, fixed = one > per ? one - per : 0;
   size_t freeb = 0, totb = 0;
   CK(cudaMemGetInfo(&freeb, &totb));
-  size_t avail = freeb + op->ws.cap;
+  size_t avail = freeb + lane->ws.cap;
   size_t reserve = std::min<size_t>(avail / 20, size_t(2) << 30);
   avail = avail > reserve ? avail - reserve : 0;
   int max_slots = (int)std::max<size_t>(1, avail > fixed ? (avail - fixed) / per : 1);
   int nchunk = (n_rhs + max_slots - 1) / max_slots;
   int chunk = (n_rhs + nchunk - 1) / nchunk;
   if (nchunk == 1)
-    return solve_impl<VT>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+    return solve_impl<VT>(op, lane, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
                           shift_status, info, s);
   fks_status worst = FKS_OK;
   for (int r0 = 0; r0 < n_rhs; r0 += chunk) {
@@ -815,7 +887,7 @@ static fks_status solve_chunked(fks_op* op, const fks_c128* b, int n_rhs, const 
       ic.breakdown = info->breakdown ? info->breakdown + r0 : nullptr;
     }
     size_t nf = (size_t)n_f * r0;
-    fks_status st = solve_impl<VT>(op, b + (size_t)r0 * op->n, nr, sigma, n_f, tau, n_tau, &oc,
+    fks_status st = solve_impl<VT>(op, lane, b + (size_t)r0 * op->n, nr, sigma, n_f, tau, n_tau, &oc,
                                    X + (size_t)r0 * n_f * op->n, res_est + nf, res_bound + nf,
                                    res_true ? res_true + nf : nullptr, m_j + nf, shift_status + nf,
                                    info ? &ic : nullptr, s);
@@ -930,9 +1002,7 @@ void fks_op_destroy(fks_op* op) {
       if (L.d64[a]) cudaFree(L.d64[a]);
       if (L.d32[a]) cudaFree(L.d32[a]);
     }
-  if (op->graph) cudaGraphExecDestroy(op->graph);
-  op->ws.release();
-  op->prof.release();
+  op->lane0.release();
   delete op;
 }
 
@@ -976,9 +1046,9 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   try {
     CK(cudaSetDevice(op->ctx->device));
     if (o->precision == FKS_PREC_FP64)
-      return solve_chunked<double>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+      return solve_chunked<double>(op, &op->lane0, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
                                    shift_status, info, s);
-    return solve_chunked<float>(op, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
+    return solve_chunked<float>(op, &op->lane0, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
                                 shift_status, info, s);
   } catch (CudaError& e) {
     set_error(std::string("fks_solve: ") + e.where + ": " + cudaGetErrorString(e.e));
@@ -1004,6 +1074,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
     S.op = op;
+    S.lane = &op->lane0;
     S.s = s;
     S.nslot = 1;
     S.n_f = 1;
@@ -1020,8 +1091,8 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       using VT = decltype(tag);
       Arena probe;
       carve<VT>(S, probe, false);
-      op->ws.reserve(probe.off + 4096);
-      carve<VT>(S, op->ws, false);
+      op->lane0.ws.reserve(probe.off + 4096);
+      carve<VT>(S, op->lane0.ws, false);
       const LevelHost& L0 = op->levels[0];
       CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
       SlotState st0{};
@@ -1049,11 +1120,11 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
         cudaGraphExec_t ge = nullptr;
         S.s = cs;
         S.capturing = true;
-        int64_t keep = op->prof.all_launches;
+        int64_t keep = op->lane0.prof.all_launches;
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         vcycle<VT>(S);
         CK(cudaStreamEndCapture(cs, &g));
-        op->prof.all_launches = keep;
+        op->lane0.prof.all_launches = keep;
         S.capturing = false;
         S.s = s;
         CK(cudaGraphInstantiate(&ge, g, 0));
@@ -1091,15 +1162,15 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
 fks_status fks_profile_select(fks_op* op, int kclass, int level) {
   if (!op) { set_error("fks_profile_select: NULL operator"); return FKS_ERR_ARG; }
   if (kclass >= FKS_K_COUNT) { set_error("fks_profile_select: bad kernel class"); return FKS_ERR_ARG; }
-  op->prof.cls = kclass < 0 ? -1 : kclass;
-  op->prof.level = level;
+  op->lane0.prof.cls = kclass < 0 ? -1 : kclass;
+  op->lane0.prof.level = level;
   return FKS_OK;
 }
 
 fks_status fks_profile_read(fks_op* op, int64_t* launches, double* total_ms, double* alg_bytes, double* alg_flops,
                             int64_t* all_launches) {
   if (!op) { set_error("fks_profile_read: NULL operator"); return FKS_ERR_ARG; }
-  Prof& p = op->prof;
+  Prof& p = op->lane0.prof;
   p.collect();
   if (launches) *launches = p.launches;
   if (total_ms) *total_ms = p.ms;
@@ -1123,7 +1194,7 @@ fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y,
     int64_t n = op->n;
     bool xd = is_device_ptr(x), yd = is_device_ptr(y);
     size_t bytes = sizeof(z64) * n * n_vec;
-    Arena& A = op->ws;
+    Arena& A = op->lane0.ws;
     A.reserve(2 * bytes + 1024);
     A.reset();
     z64* xs = xd ? (z64*)x : A.take<z64>((size_t)n * n_vec);
@@ -1151,6 +1222,7 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
     S.op = op;
+    S.lane = &op->lane0;
     S.s = s;
     S.nslot = 1;
     S.n_f = 1;
@@ -1166,8 +1238,8 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
       using VT = decltype(tag);
       Arena probe;
       carve<VT>(S, probe, false);
-      op->ws.reserve(probe.off + 4096);
-      carve<VT>(S, op->ws, false);
+      op->lane0.ws.reserve(probe.off + 4096);
+      carve<VT>(S, op->lane0.ws, false);
       int64_t n = S.n;
       copy_in(S.V, v, sizeof(z64) * n, s);
       CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
@@ -1268,6 +1340,7 @@ extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const 
     CK(noalloc_scratch(op->ctx->device, &base));
     Solve S{};
     S.op = op;
+    S.lane = &op->lane0;
     S.s = s;
     S.nslot = 1;
     S.n_f = 1;
@@ -1318,4 +1391,322 @@ extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const 
     return FKS_ERR_CUDA;
   }
   return FKS_OK;
+}
+
+// ====================================================================== serving
+// A request loop over the solver: worker threads, each with a lane (stream,
+// stream-ordered workspace, graph), admit queued requests while the device
+// memory budget allows; a worker merges queued requests that share the
+// operator, the shifts and the options into one lockstep batch (each request's
+// sources are slots of the batch). Batches on different lanes overlap on the
+// device. Every slot runs its own kernels, so a request's result does not
+// depend on what it was batched with.
+namespace fks {
+
+struct Request {
+  uint64_t ticket = 0;
+  fks_request req{};
+  std::vector<int32_t> sched;
+  std::vector<fks_c128> sigma, tau;
+  int state = 0;  // 0 queued, 1 running, 2 done, 3 cancelled
+  fks_status result = FKS_OK;
+  double t_submit = 0, t_start = 0, t_end = 0;
+  size_t est = 0;
+};
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static bool compatible(const Request& a, const Request& b) {
+  const fks_request &x = a.req, &y = b.req;
+  if (x.op != y.op || x.n_f != y.n_f || x.n_tau != y.n_tau) return false;
+  const fks_options &p = x.opt, &q = y.opt;
+  if (p.tol != q.tol || p.m_max != q.m_max || p.variant != q.variant || p.precision != q.precision ||
+      p.inner_tol != q.inner_tol || p.inner_max_cycles != q.inner_max_cycles || p.replay_mode || q.replay_mode ||
+      a.sched != b.sched)
+    return false;
+  for (int j = 0; j < x.n_f; ++j)
+    if (a.sigma[j].re != b.sigma[j].re || a.sigma[j].im != b.sigma[j].im) return false;
+  for (int j = 0; j < x.n_tau; ++j)
+    if (a.tau[j].re != b.tau[j].re || a.tau[j].im != b.tau[j].im) return false;
+  return true;
+}
+
+}  // namespace fks
+
+struct fks_server {
+  fks_ctx* ctx = nullptr;
+  size_t budget = 0, in_use = 0;
+  int max_batch = 64;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<std::shared_ptr<fks::Request>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<fks::Request>> all;
+  uint64_t next = 1;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<std::unique_ptr<fks::Lane>> lanes;
+  std::vector<cudaStream_t> streams;
+};
+
+namespace fks {
+
+template <typename VT>
+static size_t request_bytes(const fks_request& r, int n_rhs) {
+  Solve S{};
+  S.op = r.op;
+  S.nslot = n_rhs;
+  S.n_f = r.n_f;
+  S.n_tau = r.n_tau;
+  S.m = r.opt.m_max;
+  S.sched_len = r.opt.sched_len;
+  S.n = r.op->n;
+  Arena probe;
+  carve<VT>(S, probe, true);
+  return probe.off + 4096;
+}
+
+static void run_batch(fks_server* sv, int lane_id, std::vector<std::shared_ptr<Request>>& batch) {
+  Lane* lane = sv->lanes[lane_id].get();
+  cudaStream_t s = sv->streams[lane_id];
+  const fks_request& r0 = batch[0]->req;
+  int64_t n = r0.op->n;
+  int n_total = 0;
+  for (auto& q : batch) n_total += q->req.n_rhs;
+  std::vector<fks_c128> bcat((size_t)n * n_total);
+  std::vector<OutGroup> groups;
+  int at = 0;
+  for (auto& q : batch) {
+    std::memcpy(bcat.data() + (size_t)at * n, q->req.b, sizeof(fks_c128) * n * q->req.n_rhs);
+    groups.push_back(OutGroup{at, q->req.n_rhs, q->req.X, q->req.res_est, q->req.res_bound, q->req.res_true,
+                              q->req.m_j, q->req.shift_status});
+    at += q->req.n_rhs;
+  }
+  fks_options o = r0.opt;
+  o.tau_schedule = batch[0]->sched.data();
+  o.launch_mode = 0;
+  fks_status st;
+  std::unique_lock<std::mutex> api(g_api_mu);
+  try {
+    CK(cudaSetDevice(sv->ctx->device));
+    if (o.precision == FKS_PREC_FP64)
+      st = solve_impl<double>(r0.op, lane, bcat.data(), n_total, batch[0]->sigma.data(), r0.n_f,
+                              batch[0]->tau.data(), r0.n_tau, &o, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, s, &groups, &api);
+    else
+      st = solve_impl<float>(r0.op, lane, bcat.data(), n_total, batch[0]->sigma.data(), r0.n_f,
+                             batch[0]->tau.data(), r0.n_tau, &o, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, s, &groups, &api);
+  } catch (CudaError& e) {
+    set_error(std::string("fks_server: ") + e.where + ": " + cudaGetErrorString(e.e));
+    st = e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+  // per-request status from its own shifts
+  for (auto& q : batch) {
+    if (st < 0) {
+      q->result = st;
+      continue;
+    }
+    fks_status rs = FKS_OK;
+    for (int j = 0; j < q->req.n_f * q->req.n_rhs; ++j) {
+      int32_t v = q->req.shift_status[j];
+      if (v == 1 || v == -1) rs = FKS_NOT_CONVERGED;
+      else if (v == 2 && rs == FKS_OK) rs = FKS_BREAKDOWN_EXACT;
+    }
+    q->result = rs;
+  }
+}
+
+static void worker_loop(fks_server* sv, int lane_id) {
+  cudaSetDevice(sv->ctx->device);
+  while (true) {
+    std::vector<std::shared_ptr<Request>> batch;
+    size_t est = 0;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      while (true) {
+        if (sv->stop) return;
+        // first queued request that fits the free budget (a request larger than
+        // the whole budget runs when nothing else is in flight)
+        auto it = sv->queue.begin();
+        for (; it != sv->queue.end(); ++it)
+          if ((*it)->est + sv->in_use <= sv->budget || sv->in_use == 0) break;
+        if (it != sv->queue.end()) {
+          batch.push_back(*it);
+          est = (*it)->est;
+          sv->queue.erase(it);
+          int slots = batch[0]->req.n_rhs;
+          for (auto jt = sv->queue.begin(); jt != sv->queue.end();) {
+            size_t add = (*jt)->est;
+            if (slots + (*jt)->req.n_rhs <= sv->max_batch && compatible(*batch[0], **jt) &&
+                est + add + sv->in_use <= std::max(sv->budget, est)) {
+              slots += (*jt)->req.n_rhs;
+              est += add;
+              batch.push_back(*jt);
+              jt = sv->queue.erase(jt);
+            } else {
+              ++jt;
+            }
+          }
+          sv->in_use += est;
+          double t = now_s();
+          for (auto& q : batch) {
+            q->state = 1;
+            q->t_start = t;
+          }
+          break;
+        }
+        sv->cv.wait(lk);
+      }
+    }
+    run_batch(sv, lane_id, batch);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->in_use -= est;
+      double t = now_s();
+      for (auto& q : batch) {
+        q->state = 2;
+        q->t_end = t;
+      }
+    }
+    sv->cv.notify_all();
+    sv->done_cv.notify_all();
+  }
+}
+
+}  // namespace fks
+
+extern "C" fks_status fks_server_create(fks_ctx* ctx, size_t mem_budget_bytes, int lanes, fks_server** out) {
+  if (!out) { set_error("fks_server_create: out is NULL"); return FKS_ERR_ARG; }
+  *out = nullptr;
+  if (!ctx || lanes < 1 || lanes > 64 || mem_budget_bytes == 0) {
+    set_error("fks_server_create: need a context, 1..64 lanes and a positive budget");
+    return FKS_ERR_ARG;
+  }
+  fks_server* sv = new fks_server;
+  sv->ctx = ctx;
+  sv->budget = mem_budget_bytes;
+  try {
+    CK(cudaSetDevice(ctx->device));
+    for (int i = 0; i < lanes; ++i) {
+      cudaStream_t st;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      sv->streams.push_back(st);
+      sv->lanes.emplace_back(new Lane);
+      sv->lanes.back()->ws.astream = st;
+    }
+  } catch (CudaError& e) {
+    for (auto st : sv->streams) cudaStreamDestroy(st);
+    delete sv;
+    set_error(std::string("fks_server_create: ") + cudaGetErrorString(e.e));
+    return FKS_ERR_CUDA;
+  }
+  for (int i = 0; i < lanes; ++i) sv->workers.emplace_back(worker_loop, sv, i);
+  *out = sv;
+  return FKS_OK;
+}
+
+extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, uint64_t* ticket) {
+  if (!sv || !r || !ticket) { set_error("fks_server_submit: NULL argument"); return FKS_ERR_ARG; }
+  const fks_options& o = r->opt;
+  if (!r->op || !r->b || !r->sigma || !r->tau || !r->X || !r->res_est || !r->res_bound || !r->m_j ||
+      !r->shift_status || r->n_rhs < 1 || r->n_f < 1 || r->n_tau < 1 || r->n_tau > MAX_TAU ||
+      o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
+      (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
+      (o.variant != FKS_FGMRES && o.variant != FKS_FFOM)) {
+    set_error("fks_server_submit: bad request");
+    return FKS_ERR_ARG;
+  }
+  for (int i = 0; i < o.sched_len; ++i)
+    if (o.tau_schedule[i] < 0 || o.tau_schedule[i] >= r->n_tau) { set_error("fks_server_submit: bad schedule"); return FKS_ERR_ARG; }
+  if (is_device_ptr(r->b) || is_device_ptr(r->X)) { set_error("fks_server_submit: request arrays must be host memory"); return FKS_ERR_ARG; }
+  auto q = std::make_shared<Request>();
+  q->req = *r;
+  q->sched.assign(o.tau_schedule, o.tau_schedule + o.sched_len);
+  q->sigma.assign(r->sigma, r->sigma + r->n_f);
+  q->tau.assign(r->tau, r->tau + r->n_tau);
+  for (auto& z : q->sigma) if (!finite_c(z)) { set_error("fks_server_submit: sigma has NaN/Inf"); return FKS_ERR_ARG; }
+  for (auto& z : q->tau) if (!finite_c(z)) { set_error("fks_server_submit: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  q->est = o.precision == FKS_PREC_FP64 ? request_bytes<double>(*r, r->n_rhs) : request_bytes<float>(*r, r->n_rhs);
+  q->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    q->ticket = sv->next++;
+    sv->all[q->ticket] = q;
+    sv->queue.push_back(q);
+  }
+  sv->cv.notify_all();
+  *ticket = q->ticket;
+  return FKS_OK;
+}
+
+extern "C" fks_status fks_server_poll(fks_server* sv, uint64_t ticket, int* done, fks_status* result) {
+  if (!sv || !done) { set_error("fks_server_poll: NULL argument"); return FKS_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) { set_error("fks_server_poll: unknown ticket"); return FKS_ERR_ARG; }
+  *done = it->second->state >= 2;
+  if (result) *result = it->second->state == 3 ? FKS_ERR_CANCELLED : it->second->result;
+  return FKS_OK;
+}
+
+extern "C" fks_status fks_server_wait(fks_server* sv, uint64_t ticket, fks_status* result) {
+  if (!sv) { set_error("fks_server_wait: NULL server"); return FKS_ERR_ARG; }
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) { set_error("fks_server_wait: unknown ticket"); return FKS_ERR_ARG; }
+  auto q = it->second;
+  sv->done_cv.wait(lk, [&] { return q->state >= 2; });
+  if (result) *result = q->state == 3 ? FKS_ERR_CANCELLED : q->result;
+  return FKS_OK;
+}
+
+extern "C" fks_status fks_server_cancel(fks_server* sv, uint64_t ticket) {
+  if (!sv) { set_error("fks_server_cancel: NULL server"); return FKS_ERR_ARG; }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) { set_error("fks_server_cancel: unknown ticket"); return FKS_ERR_ARG; }
+    auto q = it->second;
+    if (q->state != 0) { set_error("fks_server_cancel: the request already started"); return FKS_ERR_ARG; }
+    for (auto jt = sv->queue.begin(); jt != sv->queue.end(); ++jt)
+      if (*jt == q) {
+        sv->queue.erase(jt);
+        break;
+      }
+    q->state = 3;
+    q->t_end = now_s();
+  }
+  sv->done_cv.notify_all();
+  return FKS_OK;
+}
+
+extern "C" fks_status fks_server_times(fks_server* sv, uint64_t ticket, double* submit_s, double* start_s,
+                                       double* end_s) {
+  if (!sv) { set_error("fks_server_times: NULL server"); return FKS_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) { set_error("fks_server_times: unknown ticket"); return FKS_ERR_ARG; }
+  if (submit_s) *submit_s = it->second->t_submit;
+  if (start_s) *start_s = it->second->t_start;
+  if (end_s) *end_s = it->second->t_end;
+  return FKS_OK;
+}
+
+extern "C" void fks_server_destroy(fks_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  for (auto& t : sv->workers) t.join();
+  cudaSetDevice(sv->ctx->device);
+  for (size_t i = 0; i < sv->lanes.size(); ++i) {
+    sv->lanes[i]->release();
+    cudaStreamSynchronize(sv->streams[i]);
+    cudaStreamDestroy(sv->streams[i]);
+  }
+  delete sv;
 }

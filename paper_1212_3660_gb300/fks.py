@@ -43,6 +43,13 @@ class fks_info(C.Structure):
                 ("pnorm", C.POINTER(C.c_double)), ("breakdown", C.POINTER(C.c_int32))]
 
 
+class fks_request(C.Structure):
+    _fields_ = [("op", C.c_void_p), ("b", C.c_void_p), ("n_rhs", C.c_int), ("sigma", C.c_void_p), ("n_f", C.c_int),
+                ("tau", C.c_void_p), ("n_tau", C.c_int), ("opt", fks_options), ("X", C.c_void_p),
+                ("res_est", C.c_void_p), ("res_bound", C.c_void_p), ("res_true", C.c_void_p), ("m_j", C.c_void_p),
+                ("shift_status", C.c_void_p)]
+
+
 class FksError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"fks status {status}: {msg}")
@@ -86,11 +93,20 @@ def lib():
                                             f64p, vp]
     L.fks_op_autotune.argtypes = [vp, C.c_int, fks_c128, vp, C.POINTER(C.c_int64)]
     L.fks_op_set_fusion.argtypes = [vp, C.c_int, C.c_int64]
+    L.fks_server_create.argtypes = [vp, C.c_size_t, C.c_int, C.POINTER(vp)]
+    L.fks_server_submit.argtypes = [vp, C.POINTER(fks_request), C.POINTER(C.c_uint64)]
+    L.fks_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fks_server_wait.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
+    L.fks_server_cancel.argtypes = [vp, C.c_uint64]
+    L.fks_server_times.argtypes = [vp, C.c_uint64, f64p, f64p, f64p]
+    L.fks_server_destroy.argtypes = [vp]
+    L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
     for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
-                 "fks_op_set_fusion"):
+                 "fks_op_set_fusion", "fks_server_create", "fks_server_submit", "fks_server_poll", "fks_server_wait",
+                 "fks_server_cancel", "fks_server_times"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -257,3 +273,79 @@ def fks_profile_read(op):
     if st < 0:
         raise FksError(st, fks_last_error())
     return dict(launches=la.value, ms=ms.value, bytes=by.value, flops=fl.value, all_launches=al.value)
+
+
+# ---------------------------------------------------------------- serving
+def fks_server_create(ctx, mem_budget_bytes, lanes=2):
+    out = C.c_void_p()
+    st = lib().fks_server_create(ctx, int(mem_budget_bytes), int(lanes), C.byref(out))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return out
+
+
+def fks_server_destroy(srv):
+    lib().fks_server_destroy(srv)
+
+
+class ServerRequest:
+    """A request and the host arrays it points to (kept alive until done)."""
+
+    def __init__(self, op, b, sigma, tau, options, keep, n):
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        self.n_rhs = b.shape[0] if b.ndim == 2 else 1
+        self.b = b.reshape(self.n_rhs, n)
+        self.sigma = np.ascontiguousarray(sigma, dtype=np.complex128)
+        self.tau = np.ascontiguousarray(tau, dtype=np.complex128)
+        n_f = len(self.sigma)
+        self.X = np.zeros((self.n_rhs, n_f, n), np.complex128)
+        self.res_est = np.zeros((self.n_rhs, n_f))
+        self.res_bound = np.zeros((self.n_rhs, n_f))
+        self.res_true = np.zeros((self.n_rhs, n_f))
+        self.m_j = np.zeros((self.n_rhs, n_f), np.int32)
+        self.shift_status = np.zeros((self.n_rhs, n_f), np.int32)
+        self.keep = keep
+        self.c = fks_request(op.value if hasattr(op, "value") else op, self.b.ctypes.data, self.n_rhs,
+                             self.sigma.ctypes.data, n_f, self.tau.ctypes.data, len(self.tau), options,
+                             self.X.ctypes.data, self.res_est.ctypes.data, self.res_bound.ctypes.data,
+                             self.res_true.ctypes.data, self.m_j.ctypes.data, self.shift_status.ctypes.data)
+        self.ticket = None
+
+
+def fks_server_submit(srv, req: ServerRequest):
+    t = C.c_uint64(0)
+    st = lib().fks_server_submit(srv, C.byref(req.c), C.byref(t))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    req.ticket = t.value
+    return t.value
+
+
+def fks_server_poll(srv, ticket):
+    d, r = C.c_int(0), C.c_int(0)
+    st = lib().fks_server_poll(srv, C.c_uint64(ticket), C.byref(d), C.byref(r))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return bool(d.value), r.value
+
+
+def fks_server_wait(srv, ticket):
+    r = C.c_int(0)
+    st = lib().fks_server_wait(srv, C.c_uint64(ticket), C.byref(r))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return r.value
+
+
+def fks_server_cancel(srv, ticket):
+    st = lib().fks_server_cancel(srv, C.c_uint64(ticket))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+
+
+def fks_server_times(srv, ticket):
+    a, b, c = C.c_double(0), C.c_double(0), C.c_double(0)
+    st = lib().fks_server_times(srv, C.c_uint64(ticket), C.byref(a), C.byref(b), C.byref(c))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return a.value, b.value, c.value

@@ -46,3 +46,10 @@ def test_no_gpu_create_fails_loudly(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(fks.FksError):
         fks.fks_create(0)
+
+
+def test_server_argument_errors_without_gpu(lib):
+    out = C.c_void_p()
+    assert lib.fks_server_create(None, 1 << 30, 2, C.byref(out)) == fks.FKS_ERR_ARG
+    assert lib.fks_server_submit(None, None, None) == fks.FKS_ERR_ARG
+    assert lib.fks_server_cancel(None, 1) == fks.FKS_ERR_ARG
