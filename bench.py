@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer region (very large outputs)")
+    ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
+                    help="graph: the step loop as one CUDA graph; host: the same kernels launched one by one")
     return ap.parse_args()
 
 
@@ -203,7 +205,7 @@ def main():
     est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
     mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
     opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
-                                  schedule=pr.schedule, launch_mode=0)
+                                  schedule=pr.schedule, launch_mode=0 if args.launch_mode == "graph" else 1)
     # host-driven launches (identical kernels) for per-launch event timing
     opts_host, keep_host = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
                                             schedule=pr.schedule, launch_mode=1)
@@ -264,12 +266,14 @@ def main():
     with ClockSampler(gpu_index) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("fks_timed")
         e0.record(stream)
         for _ in range(args.steps):
             step(b_d, X_d)
             converged += int(np.sum(tru <= TOL))
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier()
     launches = fks.fks_profile_read(solver.op)["all_launches"]
     ms = e0.elapsed_time(e1) / args.steps
@@ -340,7 +344,8 @@ def main():
                            "l2": "working set larger than L2 (basis V, Z: 2 x 101 x n x 16 B)",
                            "arnoldi_steps": int(info_arr["steps"].max()),
                            "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
-                           "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned},
+                           "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned,
+                           "launch_mode": args.launch_mode},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": e2e,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
