@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer region (very large outputs)")
+    ap.add_argument("--single", action="store_true",
+                    help="one untimed solve and exit (a small command for ncu captures)")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="graph: the step loop as one CUDA graph; host: the same kernels launched one by one")
     return ap.parse_args()
@@ -233,6 +235,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
+    if args.single:
+        st = step(b_d, X_d)
+        torch.cuda.synchronize()
+        print(json.dumps({"single_solve_status": st, "converged": int(np.sum(tru <= TOL))}), flush=True)
+        solver.close()
+        return
     tuned = fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
     for _ in range(args.warmup):
         step(b_d, X_d)

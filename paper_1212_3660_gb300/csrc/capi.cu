@@ -253,11 +253,11 @@ struct Solve {
     S.lane->prof.end(S.s);                                                    \
   } while (0)
 
-// Largest level handled by the single-block tail V-cycle: fp64 arithmetic runs
-// at 2 DFMA/clk per SM on GB300, so the fp64 tail stops at 1024 cells; the
-// fp32 tail takes 4096.
+// Largest level handled by the single-block tail V-cycle. The tail runs on one
+// SM, so only levels whose half sweeps take a few hundred cells go there
+// (16 x 16); larger levels spread over SMs in tile kernels.
 template <typename VT>
-static constexpr int64_t tail_max_cells() { return sizeof(VT) == 8 ? 1024 : 4096; }
+static constexpr int64_t tail_max_cells() { return 256; }
 
 template <typename VT>
 static int tail_level(const std::vector<LevelHost>& Ls) {

@@ -785,30 +785,32 @@ void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, c
                                                                             C.nz, mask, st, zc, vsc, z, vs);
 }
 
-template <typename T>
-static constexpr int fused_tx() { return 32; }
-template <typename T>
-static constexpr int fused_ty() { return 32; }
-template <typename T>
+// Tiles of 32x32 cells on large levels, 16x16 on levels of at most 128 x 128
+// (more blocks on small grids; the 4-cell halo is recomputed either way).
+static bool small_tiles(const LevelHost& L) { return L.nx <= 128 && L.ny <= 128; }
+template <typename T, int TX, int TY>
 static size_t fused_smem() {
-  return 2 * (size_t)(fused_tx<T>() + 2 * FH) * (fused_ty<T>() + 2 * FH) * sizeof(cx<T>);
+  return 2 * (size_t)(TX + 2 * FH) * (TY + 2 * FH) * sizeof(cx<T>);
 }
 
 bool fused_level_ok(const LevelHost& L) { return L.nz == 1 && L.rx == 2 && L.ry == 2 && L.rz == 1; }
 
 template <typename T>
 void fused_prepare() {
-  constexpr int TX = fused_tx<T>(), TY = fused_ty<T>();
-  cudaFuncSetAttribute(k_pre2d<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T>());
-  cudaFuncSetAttribute(k_post2d<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T>());
+  cudaFuncSetAttribute(k_pre2d<T, 32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T, 32, 32>());
+  cudaFuncSetAttribute(k_post2d<T, 32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T, 32, 32>());
 }
 
 template <typename T>
 void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
                   const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, cudaStream_t s) {
-  constexpr int TX = fused_tx<T>(), TY = fused_ty<T>();
-  dim3 g(nb(F.nx, TX), nb(F.ny, TY), nslot);
-  k_pre2d<T, TX, TY><<<g, 256, fused_smem<T>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+  if (small_tiles(F)) {
+    dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
+    k_pre2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+  } else {
+    dim3 g(nb(F.nx, 32), nb(F.ny, 32), nslot);
+    k_pre2d<T, 32, 32><<<g, 256, fused_smem<T, 32, 32>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+  }
   (void)C;
 }
 
@@ -816,9 +818,13 @@ template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
                    cudaStream_t s) {
-  constexpr int TX = fused_tx<T>(), TY = fused_ty<T>();
-  dim3 g(nb(F.nx, TX), nb(F.ny, TY), nslot);
-  k_post2d<T, TX, TY><<<g, 256, fused_smem<T>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
+  if (small_tiles(F)) {
+    dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
+    k_post2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
+  } else {
+    dim3 g(nb(F.nx, 32), nb(F.ny, 32), nslot);
+    k_post2d<T, 32, 32><<<g, 256, fused_smem<T, 32, 32>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
+  }
   (void)C;
 }
 
