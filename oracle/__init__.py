@@ -12,8 +12,10 @@ Modules:
              with the inexact-preconditioning stopping bound (Eq. trueresidual)
   direct     exact inner solves (sparse LU, the paper's "Flexible" variant) and the
              per-shift direct comparator ("Direct", Section 6.1)
+  csr        general sparse K, M and the BiCGSTAB-cycle inner solve (Section 6)
 """
 from .operator import assemble, GridOperator  # noqa: F401
 from .gmg import Hierarchy  # noqa: F401
 from .fgmres import shifted_solve, true_residuals, SolveResult  # noqa: F401
 from .direct import ExactInner, direct_solve  # noqa: F401
+from .csr import CSROperator, BiCGStabInner, csr_operator  # noqa: F401
