@@ -3,12 +3,14 @@
  *
  * Solves the shifted systems of Section 2, Eq. multipleshifted,
  *     (K + sigma_j M) x_j = b,   j = 1..n_f,
- * for a real symmetric positive definite stiffness K and a positive diagonal
- * storage matrix M (Section 2 allows a lumped, diagonal M), from ONE flexible
- * Arnoldi basis (Algorithm 3) built with the shifted preconditioners
- * (K + tau_k M)^{-1}, applied inexactly by a geometric-multigrid inner solve
- * (Section 4, Eq. zmmoditer), followed by a per-shift least-squares solve
- * (Algorithm 4, FGMRES) and the assembly x_j = Z_m y_j.
+ * for a real symmetric positive definite stiffness K and a storage (mass)
+ * matrix M, from ONE flexible Arnoldi basis (Algorithm 3) built with the
+ * shifted preconditioners (K + tau_k M)^{-1}, applied inexactly by an inner
+ * iterative solve (Section 4, Eq. zmmoditer), followed by a per-shift
+ * least-squares solve (Algorithm 4, FGMRES) and the assembly x_j = Z_m y_j.
+ * Grid operators (fks_op_grid: lumped, diagonal M) use geometric-multigrid
+ * cycles for the inner solve; general sparse operators (fks_op_csr) use
+ * BiCGSTAB cycles.
  *
  * Conventions (all entry points):
  *  - Every call returns fks_status; fks_last_error() gives the message of the
@@ -81,6 +83,29 @@ const char* fks_version(void);
 fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const double h[3],
                        const double* cond, const double* ss, uint32_t dirichlet_mask,
                        fks_op** out);
+/*
+ * General sparse operator: K and M given as CSR matrices (finite-element
+ * stiffness and consistent mass of Section 5.1, or any real K, M for which
+ * K + tau M has a nonzero diagonal). The inner solve (K + tau_k M)^{-1} v_k is
+ * then the same defect correction z <- z + C(v - (K + tau_k M) z) from z = 0 as
+ * for grids (Section 4, Eq. zmmoditer), where one cycle C is `inner_steps`
+ * BiCGSTAB steps (the Krylov inner method of Section 6) with the Jacobi
+ * preconditioner diag(K + tau_k M)^{-1}, started from zero; ||p_k|| is the
+ * complex128 defect, computed exactly.
+ *  n                       number of unknowns, 1 <= n < 2^31
+ *  k_rowptr[n+1], k_col[nnz_K], k_val[nnz_K]   CSR of K (int64 row pointers,
+ *                          int32 column indices, any order within a row,
+ *                          duplicates summed), host memory
+ *  m_rowptr, m_col, m_val  CSR of M, same conventions
+ *  out                     receives the operator (free with fks_op_destroy)
+ * K and M are stored on the device on the union of their patterns (a K and an M
+ * value per entry). Rows out of order, a column index outside 0..n-1 or a
+ * non-finite value return FKS_ERR_ARG. fks_op_autotune, fks_op_set_fusion and
+ * fks_precond_apply_noalloc are grid-only (FKS_ERR_ARG on a CSR operator).
+ */
+fks_status fks_op_csr(fks_ctx* ctx, int64_t n, const int64_t* k_rowptr, const int32_t* k_col,
+                      const double* k_val, const int64_t* m_rowptr, const int32_t* m_col,
+                      const double* m_val, fks_op** out);
 void fks_op_destroy(fks_op* op);
 /* Number of cells n of the operator (0 on a NULL operator). */
 int64_t fks_op_size(const fks_op* op);
@@ -106,12 +131,14 @@ typedef struct {
   int launch_mode;       /* 0: the step loop runs as one CUDA graph with conditional WHILE nodes
                             (no host round trip per step); 1: host-driven loop (one host sync per
                             inner cycle; per-kernel timing with fks_profile_select works here)  */
+  int inner_steps;       /* CSR operators: BiCGSTAB steps per inner cycle (<= 0 means 8, at most
+                            64); ignored by grid operators                                    */
 } fks_options;
 
 /* Optional per-solve diagnostics, host arrays owned by the caller (any may be NULL). */
 typedef struct {
   int32_t* steps;         /* [n_rhs] Arnoldi steps taken                                     */
-  int32_t* inner_cycles;  /* [m_max * n_rhs] multigrid cycles of step k (source-major)       */
+  int32_t* inner_cycles;  /* [m_max * n_rhs] inner cycles of step k (source-major)           */
   double* pnorm;          /* [m_max * n_rhs] ||p_k|| = ||v_k - (K + tau_k M) z_k||           */
   int32_t* breakdown;     /* [n_rhs] 1 if h_{k+1,k} vanished                                 */
 } fks_info;
@@ -247,7 +274,8 @@ enum {
   FKS_K_TAIL = 11,     /* the V-cycle of all small levels in one block per source */
   FKS_K_PRE2D = 12,    /* 2D level: four pre-smoothing half sweeps + residual + restriction */
   FKS_K_POST2D = 13,   /* 2D level: prolongation + four post-smoothing half sweeps */
-  FKS_K_COUNT = 14
+  FKS_K_BICGSTAB = 14, /* CSR operators: one BiCGSTAB cycle of the inner solve    */
+  FKS_K_COUNT = 15
 };
 /*
  * Time every launch of kernel class `kclass` (on level `level`, or every level

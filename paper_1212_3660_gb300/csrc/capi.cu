@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "grid.cuh"
 #include "krylov.cuh"
+#include "csr.cuh"
 
 namespace fks {
 
@@ -163,9 +164,31 @@ struct fks_ctx {
   int device;
 };
 
+// K and M of a general sparse operator on the device: union pattern, K and M
+// values per entry (fp64 and fp32), diagonals for the Jacobi preconditioner.
+struct CsrDev {
+  int64_t nnz = 0;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double *kv = nullptr, *mv = nullptr, *dk = nullptr, *dm = nullptr;
+  float *kv32 = nullptr, *mv32 = nullptr;
+  std::vector<double> dk_h, dm_h;  // host copies of the diagonals
+  template <typename T>
+  fks::CsrView<T> view(int64_t n) const {
+    fks::CsrView<T> v;
+    v.n = n;
+    v.rowptr = rowptr;
+    v.col = col;
+    if constexpr (sizeof(T) == 8) { v.kv = kv; v.mv = mv; } else { v.kv = kv32; v.mv = mv32; }
+    return v;
+  }
+};
+
 struct fks_op {
   fks_ctx* ctx;
-  int dim;
+  int dim;   // 2 or 3 for grid operators, 0 for CSR operators
+  bool csr = false;
+  CsrDev cd;
   int nx, ny, nz;
   int64_t n;
   uint32_t mask;
@@ -240,11 +263,31 @@ struct Solve {
   void* cinv;      // coarse inverse in cycle precision
   z64* cwork;      // dense coarse matrices
   z64* cinv64;
+  // CSR operators: BiCGSTAB cycle work vectors (cycle precision), scalars, Jacobi diagonals
+  int inner_steps = 8;
+  void* bv[9] = {};        // e, r, rh, p, v, ph, s, sh, t
+  void* dinv = nullptr;    // [n_tau][n]
+  BcgScal* bsc = nullptr;
+  double* bpart = nullptr;
+  int ndef = 0;            // blocks of the defect kernel (partials per slot)
   bool capturing = false;  // enqueueing into a graph: no event timing
   // server batches hold this lock for their host-side CUDA calls and release it
   // only while they wait for their step-loop graph to finish
   std::unique_lock<std::mutex>* api_lock = nullptr;
 };
+
+template <typename VT>
+static BcgVecs<VT> bcg_vecs(Solve& S) {
+  BcgVecs<VT> B;
+  B.f = (cx<VT>*)S.f[0];
+  cx<VT>** d[9] = {&B.e, &B.r, &B.rh, &B.p, &B.v, &B.ph, &B.s, &B.sh, &B.t};
+  for (int i = 0; i < 9; ++i) *d[i] = (cx<VT>*)S.bv[i];
+  return B;
+}
+
+static int defect_partials(const fks_op* op) {
+  return op->csr ? csr_blocks(op->n) : defect_blocks(op->levels[0]);
+}
 
 #define PROF(cls, lvl, by, fl, call)                                           \
   do {                                                                        \
@@ -417,33 +460,64 @@ static bool any_active(Solve& S) {
 template <typename VT>
 static void sec_inner_first(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ, int use_cond,
                             cudaGraphConditionalHandle hin) {
-  const LevelHost& L0 = S.op->levels[0];
   cx<VT>* f0 = (cx<VT>*)S.f[0];
   const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
-  const double cv = sizeof(cx<VT>), ns = S.nslot, n = L0.n;
-  PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
-       launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 1, f0, L0.n, S.dpart, 1, S.nslot, S.s));
+  const int64_t N = S.n;
+  const double cv = sizeof(cx<VT>), ns = S.nslot, n = N;
+  if (S.op->csr)
+    PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
+         launch_csr_defect<VT>(S.op->cd.view<double>(N), S.st, S.taus, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart,
+                               S.nslot, S.s));
+  else
+    PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
+         launch_defect<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart, 1, S.nslot, S.s));
   PROF(-1, -1, 0, 0,
-       launch_inner_decide(S.st, S.nslot, S.dpart, defect_blocks(L0), 1, S.eps, S.max_cycles, rc, S.m, use_cond,
-                           hin, S.flags, S.counter, S.s));
+       launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 1, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
+                           S.counter, S.s));
+}
+
+// One BiCGSTAB cycle of a CSR operator's inner solve; returns its result e.
+template <typename VT>
+static cx<VT>* bicgstab_cycle(Solve& S) {
+  const int64_t N = S.n;
+  const double cv = sizeof(cx<VT>), rv = sizeof(VT), ns = S.nslot, n = N, nnz = S.op->cd.nnz;
+  const double st = S.inner_steps;
+  // per step: two products over the union pattern (column + K + M per entry and
+  // the gathered vector), and about 24 vector passes
+  const double by = ns * (n * cv * 8 + st * (2 * (nnz * (4 + 2 * rv + cv) + 8 * n) + 24 * n * cv));
+  const double fl = ns * st * (2 * nnz * 10 + n * 60);
+  BcgVecs<VT> B = bcg_vecs<VT>(S);
+  int extra = 0;
+  PROF(FKS_K_BICGSTAB, 0, by, fl,
+       launch_bcg_cycle<VT>(S.op->cd.view<VT>(N), S.st, S.taus, B, (const cx<VT>*)S.dinv, S.bsc, S.bpart,
+                            S.inner_steps, S.nslot, S.s, &extra));
+  S.lane->prof.all_launches += extra - 1;
+  return B.e;
 }
 
 // One inner cycle: z += V-cycle(r), r = v - (K + tau M) z, decide.
 template <typename VT>
 static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t vsZ, int use_cond,
                            cudaGraphConditionalHandle hin) {
-  const LevelHost& L0 = S.op->levels[0];
   cx<VT>* f0 = (cx<VT>*)S.f[0];
   const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
-  const double cv = sizeof(cx<VT>), d = S.op->dim, ns = S.nslot, n = L0.n;
-  cx<VT>* e0 = vcycle<VT>(S);
+  const int64_t N = S.n;
+  const double cv = sizeof(cx<VT>), d = S.op->dim, ns = S.nslot, n = N;
+  cx<VT>* e0 = S.op->csr ? bicgstab_cycle<VT>(S) : vcycle<VT>(S);
   PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
-       launch_correct<VT>(S.st, Z, vsZ, L0.n, e0, L0.n, L0.n, S.nslot, S.s));
-  PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 1) + cv), ns * n * (8 * d + 14),
-       launch_defect<VT>(L0, S.st, S.taus, V, vsV, Z, vsZ, L0.n, 0, f0, L0.n, S.dpart, 0, S.nslot, S.s));
+       launch_correct<VT>(S.st, Z, vsZ, N, e0, N, N, S.nslot, S.s));
+  if (S.op->csr) {
+    const double nnz = S.op->cd.nnz;
+    PROF(FKS_K_DEFECT, 0, ns * (n * (40 + cv) + nnz * 20 + nnz * 16), ns * nnz * 10.0,
+         launch_csr_defect<VT>(S.op->cd.view<double>(N), S.st, S.taus, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart,
+                               S.nslot, S.s));
+  } else {
+    PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 1) + cv), ns * n * (8 * d + 14),
+         launch_defect<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart, 0, S.nslot, S.s));
+  }
   PROF(-1, -1, 0, 0,
-       launch_inner_decide(S.st, S.nslot, S.dpart, defect_blocks(L0), 0, S.eps, S.max_cycles, rc, S.m, use_cond,
-                           hin, S.flags, S.counter, S.s));
+       launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 0, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
+                           S.counter, S.s));
 }
 
 // Inner solve of the current step, host-driven: z_k (column k-1 of Z) from v_k.
@@ -470,7 +544,10 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
   const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
   const double ns = n_rhs, nn = (double)n, kk = step;
   const int kmax = use_cond ? m : step;
-  PROF(-1, -1, 0, 0, launch_mass(S.st, S.op->levels[0].d64[3], S.Z, vsZ, S.w, n, S.mpart, n_rhs, S.s));
+  if (S.op->csr)
+    PROF(-1, -1, 0, 0, launch_csr_mass(S.op->cd.view<double>(n), S.st, S.Z, vsZ, S.w, S.mpart, n_rhs, S.s));
+  else
+    PROF(-1, -1, 0, 0, launch_mass(S.st, S.op->levels[0].d64[3], S.Z, vsZ, S.w, n, S.mpart, n_rhs, S.s));
   // CGS2: two projections; pass p writes its coefficients to h12[slot][p]
   for (int pass = 0; pass < 2; ++pass) {
     z64* hp = S.h12 + pass * MAX_M;
@@ -566,6 +643,14 @@ static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int
 
 template <typename VT>
 static void setup_levels(Solve& S) {
+  if (S.op->csr) {
+    const CsrDev& C = S.op->cd;
+    PROF(-1, -1, 0, 0, launch_csr_dinv<VT>(S.n, C.dk, C.dm, S.taus, S.n_tau, (cx<VT>*)S.dinv, S.s));
+    CK(cudaMemsetAsync(S.singular, 0, sizeof(int), S.s));
+    CK(cudaMemsetAsync(S.counter, 0, sizeof(int), S.s));
+    S.lane->prof.all_launches += 2;
+    return;
+  }
   auto& Ls = S.op->levels;
   {
     std::lock_guard<std::mutex> build_lock(g_build_mu);
@@ -603,24 +688,39 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.V = A.take<z64>((size_t)ns * (m + 1) * n);
   S.Z = A.take<z64>((size_t)ns * m * n);
   S.w = A.take<z64>((size_t)ns * n);
-  S.f.assign(Ls.size(), nullptr);
-  S.z.assign(Ls.size(), nullptr);
-  S.z2.assign(Ls.size(), nullptr);
-  S.invd.assign(Ls.size(), nullptr);
-  for (size_t l = 0; l < Ls.size(); ++l) {
-    S.f[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
-    S.z[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
-    S.z2[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
-    S.invd[l] = A.take<cx<VT>>((size_t)S.n_tau * Ls[l].n);
+  S.ndef = defect_partials(S.op);
+  if (S.op->csr) {
+    S.f.assign(1, nullptr);
+    S.z.clear();
+    S.z2.clear();
+    S.invd.clear();
+    S.f[0] = A.take<cx<VT>>((size_t)ns * n);
+    for (int i = 0; i < 9; ++i) S.bv[i] = A.take<cx<VT>>((size_t)ns * n);
+    S.dinv = A.take<cx<VT>>((size_t)S.n_tau * n);
+    S.bsc = A.take<BcgScal>(ns);
+    S.bpart = A.take<double>((size_t)ns * csr_blocks(n) * 3);
+    S.cwork = S.cinv64 = nullptr;
+    S.cinv = nullptr;
+  } else {
+    S.f.assign(Ls.size(), nullptr);
+    S.z.assign(Ls.size(), nullptr);
+    S.z2.assign(Ls.size(), nullptr);
+    S.invd.assign(Ls.size(), nullptr);
+    for (size_t l = 0; l < Ls.size(); ++l) {
+      S.f[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
+      S.z[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
+      S.z2[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
+      S.invd[l] = A.take<cx<VT>>((size_t)S.n_tau * Ls[l].n);
+    }
+    int64_t nc = Ls.back().n;
+    S.cwork = A.take<z64>((size_t)S.n_tau * nc * nc);
+    S.cinv64 = A.take<z64>((size_t)S.n_tau * nc * nc);
+    S.cinv = A.take<cx<VT>>((size_t)S.n_tau * nc * nc);
   }
-  int64_t nc = Ls.back().n;
-  S.cwork = A.take<z64>((size_t)S.n_tau * nc * nc);
-  S.cinv64 = A.take<z64>((size_t)S.n_tau * nc * nc);
-  S.cinv = A.take<cx<VT>>((size_t)S.n_tau * nc * nc);
   S.singular = A.take<int32_t>(1);
   S.flags = A.take<int32_t>(ns);
   S.counter = A.take<int32_t>(1);
-  S.dpart = A.take<double>((size_t)ns * defect_blocks(Ls[0]) * 2);
+  S.dpart = A.take<double>((size_t)ns * S.ndef * 2);
   S.npart = A.take<double>((size_t)ns * norm_blocks(n));
   S.mpart = A.take<double>((size_t)ns * norm_blocks(n));
   S.wpart = A.take<double>((size_t)ns * norm_blocks(n));
@@ -639,7 +739,7 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.mj = A.take<int32_t>((size_t)ns * nf);
   S.est = A.take<double>((size_t)ns * nf);
   S.bnd = A.take<double>((size_t)ns * nf);
-  S.tpart = A.take<double>((size_t)ns * nf * tres_blocks(Ls[0]));
+  S.tpart = A.take<double>((size_t)ns * nf * (S.op->csr ? csr_blocks(n) : tres_blocks(Ls[0])));
   S.tres = A.take<double>((size_t)ns * nf);
   S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
 }
@@ -676,6 +776,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   S.eps = o->inner_tol > 0 ? o->inner_tol : std::min(1e-6, o->tol / 100.0);
   S.max_cycles = o->inner_max_cycles > 0 ? o->inner_max_cycles : 50;
   S.replay = o->replay_mode != 0;
+  S.inner_steps = o->inner_steps > 0 ? o->inner_steps : 8;
   bool x_dev = groups ? false : is_device_ptr(X);
   if (groups && !res_true) res_true = (double*)1;  // grouped runs always compute true residuals
   // workspace size: carve once on a null base to measure
@@ -717,7 +818,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
       std::vector<double> key = {(double)(uintptr_t)lane->ws.base, (double)n_rhs, (double)n_f, (double)n_tau, (double)m,
                                  (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
-                                 (double)op->fuse_max[1]};
+                                 (double)op->fuse_max[1], (double)S.inner_steps};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -763,7 +864,10 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
     const double ns = n_rhs, nn = (double)n, ks = steps, d = op->dim;
     PROF(FKS_K_ASSEMBLE, -1, ns * 16 * nn * (ks + n_f), ns * 8 * nn * ks * n_f,
          launch_assemble(S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, s));
-    if (res_true)
+    if (res_true && op->csr)
+      PROF(FKS_K_TRES, -1, ns * (nn * (16.0 * n_f + 16) + n_f * op->cd.nnz * 36.0), ns * n_f * op->cd.nnz * 10.0,
+           launch_csr_true_residual(op->cd.view<double>(n), S.sigma, n_f, S.b, Xd, S.tpart, S.st, S.tres, n_rhs, s));
+    else if (res_true)
       PROF(FKS_K_TRES, -1, ns * nn * (16.0 * n_f + 16 + 8 * (d + 1)), ns * nn * n_f * (8 * d + 14),
            launch_true_residual(op->levels[0], S.sigma, n_f, S.b, Xd, S.tpart, S.st, S.tres, n_rhs, s));
     if (res_true) lane->prof.all_launches += 1;  // the true residual is two kernels
@@ -897,6 +1001,17 @@ static fks_status solve_chunked(fks_op* op, Lane* lane, const fks_c128* b, int n
   return worst;
 }
 
+// A CSR operator's Jacobi preconditioner needs a nonzero diagonal of K + tau M.
+static bool csr_diag_ok(const fks_op* op, const fks_c128* tau, int n_tau) {
+  if (!op->csr) return true;
+  for (int q = 0; q < n_tau; ++q)
+    for (int64_t i = 0; i < op->n; ++i) {
+      double re = op->cd.dk_h[i] + tau[q].re * op->cd.dm_h[i], im = tau[q].im * op->cd.dm_h[i];
+      if (re == 0.0 && im == 0.0) return false;
+    }
+  return true;
+}
+
 }  // namespace fks
 
 // ====================================================================== C ABI
@@ -995,8 +1110,111 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
   return FKS_OK;
 }
 
+fks_status fks_op_csr(fks_ctx* ctx, int64_t n, const int64_t* k_rowptr, const int32_t* k_col, const double* k_val,
+                      const int64_t* m_rowptr, const int32_t* m_col, const double* m_val, fks_op** out) {
+  if (!out) { set_error("fks_op_csr: out is NULL"); return FKS_ERR_ARG; }
+  *out = nullptr;
+  if (!ctx || !k_rowptr || !m_rowptr) { set_error("fks_op_csr: NULL argument"); return FKS_ERR_ARG; }
+  if (n < 1 || n > INT32_MAX) { set_error("fks_op_csr: n must be in 1..2^31-1"); return FKS_ERR_ARG; }
+  // checks of both matrices
+  const int64_t* rp[2] = {k_rowptr, m_rowptr};
+  const int32_t* cl[2] = {k_col, m_col};
+  const double* vl[2] = {k_val, m_val};
+  for (int a = 0; a < 2; ++a) {
+    if (rp[a][0] != 0) { set_error("fks_op_csr: row pointers must start at 0"); return FKS_ERR_ARG; }
+    for (int64_t i = 0; i < n; ++i)
+      if (rp[a][i + 1] < rp[a][i]) { set_error("fks_op_csr: row pointers must not decrease"); return FKS_ERR_ARG; }
+    int64_t nz = rp[a][n];
+    if (nz > 0 && (!cl[a] || !vl[a])) { set_error("fks_op_csr: NULL column or value array"); return FKS_ERR_ARG; }
+    for (int64_t q = 0; q < nz; ++q) {
+      if (cl[a][q] < 0 || cl[a][q] >= n) { set_error("fks_op_csr: column index out of range"); return FKS_ERR_ARG; }
+      if (!std::isfinite(vl[a][q])) { set_error("fks_op_csr: value is NaN/Inf"); return FKS_ERR_ARG; }
+    }
+  }
+  // union pattern, sorted by column within a row, duplicates summed
+  std::vector<int64_t> rowptr(n + 1, 0);
+  std::vector<int32_t> col;
+  std::vector<double> kv, mv;
+  std::vector<double> dk(n, 0.0), dm(n, 0.0);
+  col.reserve(k_rowptr[n] + m_rowptr[n]);
+  kv.reserve(col.capacity());
+  mv.reserve(col.capacity());
+  std::vector<std::pair<int32_t, int>> ent;  // (column, index into vals)
+  std::vector<double> vals;
+  for (int64_t i = 0; i < n; ++i) {
+    ent.clear();
+    vals.clear();
+    for (int a = 0; a < 2; ++a)
+      for (int64_t q = rp[a][i]; q < rp[a][i + 1]; ++q) {
+        ent.push_back({cl[a][q], (int)vals.size() * 2 + a});
+        vals.push_back(vl[a][q]);
+      }
+    std::sort(ent.begin(), ent.end());
+    for (size_t e = 0; e < ent.size();) {
+      int32_t c = ent[e].first;
+      double ks = 0.0, ms = 0.0;
+      for (; e < ent.size() && ent[e].first == c; ++e) {
+        double v = vals[ent[e].second >> 1];
+        if (ent[e].second & 1) ms += v; else ks += v;
+      }
+      col.push_back(c);
+      kv.push_back(ks);
+      mv.push_back(ms);
+      if (c == i) { dk[i] = ks; dm[i] = ms; }
+    }
+    rowptr[i + 1] = (int64_t)col.size();
+  }
+  int64_t nnz = (int64_t)col.size();
+  fks_op* op = new fks_op;
+  op->ctx = ctx;
+  op->dim = 0;
+  op->nx = op->ny = op->nz = 0;
+  op->n = n;
+  op->mask = 0;
+  op->csr = true;
+  CsrDev& C = op->cd;
+  C.nnz = nnz;
+  try {
+    CK(cudaSetDevice(ctx->device));
+    std::vector<float> kf(kv.begin(), kv.end()), mf(mv.begin(), mv.end());
+    size_t z = (size_t)std::max<int64_t>(nnz, 1);
+    CK(cudaMalloc(&C.rowptr, sizeof(int64_t) * (n + 1)));
+    CK(cudaMalloc(&C.col, sizeof(int32_t) * z));
+    CK(cudaMalloc(&C.kv, sizeof(double) * z));
+    CK(cudaMalloc(&C.mv, sizeof(double) * z));
+    CK(cudaMalloc(&C.kv32, sizeof(float) * z));
+    CK(cudaMalloc(&C.mv32, sizeof(float) * z));
+    CK(cudaMalloc(&C.dk, sizeof(double) * n));
+    CK(cudaMalloc(&C.dm, sizeof(double) * n));
+    CK(cudaMemcpy(C.rowptr, rowptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+    if (nnz > 0) {
+      CK(cudaMemcpy(C.col, col.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(C.kv, kv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(C.mv, mv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(C.kv32, kf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(C.mv32, mf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(C.dk, dk.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.dm, dm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  } catch (CudaError& e) {
+    set_error(std::string("fks_op_csr: ") + e.where + ": " + cudaGetErrorString(e.e));
+    fks_op_destroy(op);
+    return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+  C.dk_h = std::move(dk);
+  C.dm_h = std::move(dm);
+  *out = op;
+  return FKS_OK;
+}
+
 void fks_op_destroy(fks_op* op) {
   if (!op) return;
+  {
+    CsrDev& C = op->cd;
+    void* ps[8] = {C.rowptr, C.col, C.kv, C.mv, C.kv32, C.mv32, C.dk, C.dm};
+    for (void* q : ps)
+      if (q) cudaFree(q);
+  }
   for (auto& L : op->levels)
     for (int a = 0; a < 4; ++a) {
       if (L.d64[a]) cudaFree(L.d64[a]);
@@ -1025,6 +1243,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   for (int i = 0; i < o->sched_len; ++i)
     if (o->tau_schedule[i] < 0 || o->tau_schedule[i] >= n_tau) { set_error("fks_solve: schedule index out of range"); return FKS_ERR_ARG; }
   if (o->launch_mode != 0 && o->launch_mode != 1) { set_error("fks_solve: launch_mode must be 0 or 1"); return FKS_ERR_ARG; }
+  if (o->inner_steps > 64) { set_error("fks_solve: inner_steps must be at most 64"); return FKS_ERR_ARG; }
   if (o->replay_mode && (!o->replay_inner_cycles || !o->replay_mj)) { set_error("fks_solve: replay arrays missing"); return FKS_ERR_ARG; }
   if (o->replay_mode) {
     for (int i = 0; i < o->m_max * n_rhs; ++i)
@@ -1042,6 +1261,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   if (cudaGetLastError() != cudaSuccess) { set_error("fks_solve: cannot read sigma / tau"); return FKS_ERR_ARG; }
   for (auto& z : sg) if (!finite_c(z)) { set_error("fks_solve: sigma has NaN/Inf"); return FKS_ERR_ARG; }
   for (auto& z : tu) if (!finite_c(z)) { set_error("fks_solve: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  if (!csr_diag_ok(op, tu.data(), n_tau)) { set_error("fks_solve: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   try {
     CK(cudaSetDevice(op->ctx->device));
@@ -1058,6 +1278,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
 
 fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_fusion: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_set_fusion: grid operators only"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_fusion: bad precision"); return FKS_ERR_ARG; }
   op->fuse_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
   return FKS_OK;
@@ -1065,6 +1286,7 @@ fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells) {
 
 fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen) {
   if (!op) { set_error("fks_op_autotune: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_autotune: grid operators only"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_autotune: bad precision"); return FKS_ERR_ARG; }
   if (!finite_c(tau)) { set_error("fks_op_autotune: tau has NaN/Inf"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
@@ -1186,7 +1408,7 @@ fks_status fks_profile_read(fks_op* op, int64_t* launches, double* total_ms, dou
 }
 
 fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y, int n_vec, void* stream) {
-  if (!op || !x || !y || n_vec < 1) { set_error("fks_op_apply: bad argument"); return FKS_ERR_ARG; }
+  if (!op || !x || !y || n_vec < 1 || n_vec > 65535) { set_error("fks_op_apply: bad argument"); return FKS_ERR_ARG; }
   if (!finite_c(sh)) { set_error("fks_op_apply: shift has NaN/Inf"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   try {
@@ -1200,7 +1422,10 @@ fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y,
     z64* xs = xd ? (z64*)x : A.take<z64>((size_t)n * n_vec);
     z64* ys = yd ? (z64*)y : A.take<z64>((size_t)n * n_vec);
     if (!xd) CK(cudaMemcpyAsync(xs, x, bytes, cudaMemcpyHostToDevice, s));
-    launch_apply<double>(op->levels[0], mk(sh.re, sh.im), nullptr, nullptr, xs, ys, n, n_vec, s);
+    if (op->csr)
+      launch_csr_apply<double>(op->cd.view<double>(n), mk(sh.re, sh.im), nullptr, nullptr, xs, ys, n, n_vec, s);
+    else
+      launch_apply<double>(op->levels[0], mk(sh.re, sh.im), nullptr, nullptr, xs, ys, n, n_vec, s);
     CK(cudaGetLastError());
     if (!yd) CK(cudaMemcpyAsync(y, ys, bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1217,6 +1442,7 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
   if (!finite_c(tau)) { set_error("fks_precond_apply: tau has NaN/Inf"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_precond_apply: bad precision"); return FKS_ERR_ARG; }
   if (cycles < 0 && !(eps > 0)) { set_error("fks_precond_apply: eps must be positive"); return FKS_ERR_ARG; }
+  if (!csr_diag_ok(op, &tau, 1)) { set_error("fks_precond_apply: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   try {
     CK(cudaSetDevice(op->ctx->device));
@@ -1311,6 +1537,7 @@ extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const 
                                                 int max_cycles, int cycles, int precision, int32_t* out_cycles,
                                                 double* out_pnorm, void* stream) {
   if (!op || !v || !z) { set_error("fks_precond_apply_noalloc: NULL argument"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_precond_apply_noalloc: grid operators only"); return FKS_ERR_ARG; }
   if (!finite_c(tau)) { set_error("fks_precond_apply_noalloc: tau has NaN/Inf"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) {
     set_error("fks_precond_apply_noalloc: bad precision");
@@ -1424,6 +1651,7 @@ static bool compatible(const Request& a, const Request& b) {
   const fks_options &p = x.opt, &q = y.opt;
   if (p.tol != q.tol || p.m_max != q.m_max || p.variant != q.variant || p.precision != q.precision ||
       p.inner_tol != q.inner_tol || p.inner_max_cycles != q.inner_max_cycles || p.replay_mode || q.replay_mode ||
+      std::max(p.inner_steps, 0) != std::max(q.inner_steps, 0) ||
       a.sched != b.sched)
     return false;
   for (int j = 0; j < x.n_f; ++j)
@@ -1614,7 +1842,7 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
       !r->shift_status || r->n_rhs < 1 || r->n_f < 1 || r->n_tau < 1 || r->n_tau > MAX_TAU ||
       o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
       (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
-      (o.variant != FKS_FGMRES && o.variant != FKS_FFOM)) {
+      (o.variant != FKS_FGMRES && o.variant != FKS_FFOM) || o.inner_steps > 64) {
     set_error("fks_server_submit: bad request");
     return FKS_ERR_ARG;
   }
@@ -1628,6 +1856,7 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
   q->tau.assign(r->tau, r->tau + r->n_tau);
   for (auto& z : q->sigma) if (!finite_c(z)) { set_error("fks_server_submit: sigma has NaN/Inf"); return FKS_ERR_ARG; }
   for (auto& z : q->tau) if (!finite_c(z)) { set_error("fks_server_submit: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  if (!csr_diag_ok(r->op, q->tau.data(), r->n_tau)) { set_error("fks_server_submit: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
   q->est = o.precision == FKS_PREC_FP64 ? request_bytes<double>(*r, r->n_rhs) : request_bytes<float>(*r, r->n_rhs);
   q->t_submit = now_s();
   {

@@ -1,0 +1,337 @@
+// General sparse operator (CSR) kernels: y = (K + s M) x on the union pattern
+// of K and M, the complex128 defect / mass / true-residual kernels of the
+// solver, and the BiCGSTAB cycle of the inner solve (s Jacobi-preconditioned
+// BiCGSTAB steps on A e = f from e = 0; the paper's inner Krylov method,
+// Section 6), all batched over sources on gridDim.y.
+#include "csr.cuh"
+#include "krylov.cuh"
+
+namespace fks {
+
+__device__ __forceinline__ bool csr_running(const SlotState* st, int slot) {
+  return st == nullptr || (st[slot].active && !st[slot].inner_done);
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> csr_row(const CsrView<T>& A, int64_t row, cx<T> s, const cx<T>* __restrict__ x) {
+  cx<T> acc = mk(T(0), T(0));
+  for (int64_t q = A.rowptr[row]; q < A.rowptr[row + 1]; ++q) {
+    cx<T> a = mk(fmaT(s.re, A.mv[q], A.kv[q]), mulT(s.im, A.mv[q]));
+    acc = acc + a * x[A.col[q]];
+  }
+  return acc;
+}
+
+// y = (K + s M) x, s fixed or tau of the slot
+template <typename T>
+__global__ void k_csr_apply(CsrView<T> A, z64 sfix, const SlotState* st, const z64* taus, const cx<T>* __restrict__ x,
+                            cx<T>* __restrict__ y, int64_t vs) {
+  int slot = blockIdx.y;
+  int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  z64 s = st ? taus[st[slot].tau] : sfix;
+  y[slot * vs + row] = csr_row(A, row, cvt<T>(s), x + slot * vs);
+}
+
+// r = v - (K + tau M) z (complex128), f0 = r in the cycle precision, partial |r|^2, |v|^2
+template <typename T>
+__global__ void k_csr_defect(CsrView<double> A, const SlotState* st, const z64* taus, const z64* __restrict__ v,
+                             int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col, int zero_z,
+                             cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot)) return;
+  __shared__ double red[32];
+  int64_t off = (int64_t)(st[slot].k - 1) * col;
+  double r2 = 0.0, v2 = 0.0;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.n; row += (int64_t)gridDim.x * blockDim.x) {
+    z64 vv = v[slot * vsv + off + row];
+    z64 r = zero_z ? vv : vv - csr_row(A, row, taus[st[slot].tau], z + slot * vsz + off);
+    f0[slot * vsf + row] = cvt<T>(r);
+    r2 += abs2(r);
+    v2 += abs2(vv);
+  }
+  r2 = block_sum(r2, red);
+  v2 = block_sum(v2, red);
+  if (threadIdx.x == 0) {
+    partial[((int64_t)slot * gridDim.x + blockIdx.x) * 2 + 0] = r2;
+    partial[((int64_t)slot * gridDim.x + blockIdx.x) * 2 + 1] = v2;
+  }
+}
+
+// w = M z_k (complex128) and partial |w|^2
+__global__ void k_csr_mass(CsrView<double> A, const SlotState* st, const z64* __restrict__ Z, int64_t vsZ,
+                           z64* __restrict__ w, double* __restrict__ partial) {
+  int slot = blockIdx.y;
+  if (!st[slot].active) return;
+  __shared__ double red[32];
+  const z64* z = Z + slot * vsZ + (int64_t)(st[slot].k - 1) * A.n;
+  double a = 0.0;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.n; row += (int64_t)gridDim.x * blockDim.x) {
+    z64 acc = mk(0.0, 0.0);
+    for (int64_t q = A.rowptr[row]; q < A.rowptr[row + 1]; ++q) acc = axpy(A.mv[q], z[A.col[q]], acc);
+    w[slot * A.n + row] = acc;
+    a += abs2(acc);
+  }
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) partial[(int64_t)slot * gridDim.x + blockIdx.x] = a;
+}
+
+// partial |b - (K + sigma_j M) x_j|^2, grid (blocks, n_f * slots)
+__global__ void k_csr_tres_partial(CsrView<double> A, const z64* __restrict__ sigma, int nf, const z64* __restrict__ b,
+                                   const z64* __restrict__ X, double* __restrict__ partial) {
+  int slot = blockIdx.y / nf, j = blockIdx.y - slot * nf;
+  __shared__ double red[32];
+  const z64* x = X + ((int64_t)slot * nf + j) * A.n;
+  double a = 0.0;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.n; row += (int64_t)gridDim.x * blockDim.x)
+    a += abs2(b[slot * A.n + row] - csr_row(A, row, sigma[j], x));
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) partial[((int64_t)slot * nf + j) * gridDim.x + blockIdx.x] = a;
+}
+
+// 1 / (K_ii + tau M_ii) for every distinct tau
+template <typename T>
+__global__ void k_csr_dinv(int64_t n, const double* __restrict__ dk, const double* __restrict__ dm,
+                           const z64* __restrict__ taus, int ntau, cx<T>* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < ntau; ++q) {
+    z64 D = mk(dk[i] + taus[q].re * dm[i], taus[q].im * dm[i]);
+    double den = abs2(D);
+    out[(int64_t)q * n + i] = cvt<T>(mk(D.re / den, -D.im / den));
+  }
+}
+
+// ------------------------------------------------------------------ BiCGSTAB cycle
+// Vector stage kernels (cycle precision T); scalars per slot in complex128.
+template <typename T>
+__global__ void k_bcg_init(const SlotState* st, BcgVecs<T> V, int64_t n, BcgScal* sc) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot)) return;
+  int64_t o = slot * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cx<T> f = V.f[o + i];
+    V.r[o + i] = f;
+    V.rh[o + i] = f;
+    V.p[o + i] = mk(T(0), T(0));
+    V.v[o + i] = mk(T(0), T(0));
+    V.e[o + i] = mk(T(0), T(0));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    BcgScal& s = sc[slot];
+    s.rho_old = mk(1.0, 0.0);
+    s.alpha = mk(1.0, 0.0);
+    s.omega = mk(1.0, 0.0);
+    s.halt = 0;
+    s.last = 0;
+  }
+}
+
+// partial sums of <a, b> (and <c, c> when c != nullptr) in complex128
+template <typename T>
+__global__ void k_bcg_dot(const SlotState* st, const BcgScal* sc, const cx<T>* __restrict__ a,
+                          const cx<T>* __restrict__ b, const cx<T>* __restrict__ c, int64_t n, double* partial) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot) || sc[slot].halt) return;
+  __shared__ double red[32];
+  int64_t o = slot * n;
+  double re = 0.0, im = 0.0, cc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    z64 x = cvt<double>(a[o + i]), y = cvt<double>(b[o + i]);
+    z64 d = cdot(x, y);
+    re += d.re;
+    im += d.im;
+    if (c) cc += abs2(cvt<double>(c[o + i]));
+  }
+  re = block_sum(re, red);
+  im = block_sum(im, red);
+  cc = block_sum(cc, red);
+  if (threadIdx.x == 0) {
+    double* p = partial + ((int64_t)slot * gridDim.x + blockIdx.x) * 3;
+    p[0] = re;
+    p[1] = im;
+    p[2] = cc;
+  }
+}
+
+__device__ __forceinline__ bool czero(z64 a) { return a.re == 0.0 && a.im == 0.0; }
+__device__ __forceinline__ z64 cdivd(z64 a, z64 b) {
+  double d = abs2(b);
+  return mk((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+
+// stage 0: rho, beta; stage 1: alpha; stage 2: omega. One block per slot.
+__global__ void k_bcg_scalar(const SlotState* st, BcgScal* sc, const double* __restrict__ partial, int nblocks,
+                             int stage) {
+  int slot = blockIdx.x;
+  if (!csr_running(st, slot) || sc[slot].halt) return;
+  __shared__ double red[32];
+  double re = 0.0, im = 0.0, cc = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    const double* p = partial + ((int64_t)slot * nblocks + q) * 3;
+    re += p[0];
+    im += p[1];
+    cc += p[2];
+  }
+  re = block_sum(re, red);
+  im = block_sum(im, red);
+  cc = block_sum(cc, red);
+  if (threadIdx.x != 0) return;
+  BcgScal& s = sc[slot];
+  z64 d = mk(re, im);
+  if (stage == 0) {
+    if (czero(d) || czero(s.omega)) { s.halt = 1; return; }
+    s.rho = d;
+    s.beta = cdivd(d, s.rho_old) * cdivd(s.alpha, s.omega);
+  } else if (stage == 1) {
+    if (czero(d)) { s.halt = 1; return; }
+    s.alpha = cdivd(s.rho, d);
+  } else {
+    if (cc == 0.0) { s.omega = mk(0.0, 0.0); s.last = 1; return; }
+    s.omega = mk(d.re / cc, d.im / cc);
+  }
+}
+
+// p = r + beta (p - omega v); ph = dinv p
+template <typename T>
+__global__ void k_bcg_p(const SlotState* st, const BcgScal* sc, BcgVecs<T> V, const cx<T>* __restrict__ dinv,
+                        int64_t n) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot) || sc[slot].halt) return;
+  const cx<T>* D = dinv + (int64_t)st[slot].tau * n;
+  cx<T> beta = cvt<T>(sc[slot].beta), om = cvt<T>(sc[slot].omega);
+  int64_t o = slot * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cx<T> p = V.r[o + i] + beta * (V.p[o + i] - om * V.v[o + i]);
+    V.p[o + i] = p;
+    V.ph[o + i] = D[i] * p;
+  }
+}
+
+// y = A x for the BiCGSTAB products (slot tau), cycle precision
+template <typename T>
+__global__ void k_bcg_spmv(CsrView<T> A, const SlotState* st, const BcgScal* sc, const z64* taus,
+                           const cx<T>* __restrict__ x, cx<T>* __restrict__ y) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot) || sc[slot].halt) return;
+  cx<T> s = cvt<T>(taus[st[slot].tau]);
+  int64_t o = slot * A.n;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.n; row += (int64_t)gridDim.x * blockDim.x)
+    y[o + row] = csr_row(A, row, s, x + o);
+}
+
+// s = r - alpha v; sh = dinv s
+template <typename T>
+__global__ void k_bcg_s(const SlotState* st, const BcgScal* sc, BcgVecs<T> V, const cx<T>* __restrict__ dinv,
+                        int64_t n) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot) || sc[slot].halt) return;
+  const cx<T>* D = dinv + (int64_t)st[slot].tau * n;
+  cx<T> al = cvt<T>(sc[slot].alpha);
+  int64_t o = slot * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cx<T> s = V.r[o + i] - al * V.v[o + i];
+    V.s[o + i] = s;
+    V.sh[o + i] = D[i] * s;
+  }
+}
+
+// e += alpha ph + omega sh; r = s - omega t; rho_old = rho (the last step of a
+// halting iteration, <t,t> = 0, has omega = 0)
+template <typename T>
+__global__ void k_bcg_update(const SlotState* st, BcgScal* sc, BcgVecs<T> V, int64_t n) {
+  int slot = blockIdx.y;
+  if (!csr_running(st, slot) || sc[slot].halt) return;
+  cx<T> al = cvt<T>(sc[slot].alpha), om = cvt<T>(sc[slot].omega);
+  int64_t o = slot * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    V.e[o + i] = V.e[o + i] + al * V.ph[o + i] + om * V.sh[o + i];
+    V.r[o + i] = V.s[o + i] - om * V.t[o + i];
+  }
+}
+
+__global__ void k_bcg_close(const SlotState* st, BcgScal* sc, int nslot) {
+  int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nslot || !csr_running(st, slot) || sc[slot].halt) return;
+  sc[slot].rho_old = sc[slot].rho;
+  if (sc[slot].last) sc[slot].halt = 1;
+}
+
+// ------------------------------------------------------------------ launchers
+static inline unsigned cnb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+int csr_blocks(int64_t n) { return (int)std::min<int64_t>(cnb(n, 256), 512); }
+
+template <typename T>
+void launch_csr_apply(const CsrView<T>& A, z64 sfix, const SlotState* st, const z64* taus, const cx<T>* x, cx<T>* y,
+                      int64_t vs, int nslot, cudaStream_t s) {
+  k_csr_apply<T><<<dim3(cnb(A.n, 256), nslot), 256, 0, s>>>(A, sfix, st, taus, x, y, vs);
+}
+
+template <typename T>
+void launch_csr_defect(const CsrView<double>& A, const SlotState* st, const z64* taus, const z64* v, int64_t vsv,
+                       const z64* z, int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial,
+                       int nslot, cudaStream_t s) {
+  k_csr_defect<T><<<dim3(csr_blocks(A.n), nslot), 256, 0, s>>>(A, st, taus, v, vsv, z, vsz, col, zero_z, f0, vsf,
+                                                               partial);
+}
+
+// partial sums over norm_blocks(n) blocks, the layout the Arnoldi finish reads
+void launch_csr_mass(const CsrView<double>& A, const SlotState* st, const z64* Z, int64_t vsZ, z64* w, double* partial,
+                     int nslot, cudaStream_t s) {
+  k_csr_mass<<<dim3(norm_blocks(A.n), nslot), 256, 0, s>>>(A, st, Z, vsZ, w, partial);
+}
+
+void launch_csr_true_residual(const CsrView<double>& A, const z64* sigma, int nf, const z64* b, const z64* X,
+                              double* partial, const SlotState* st, double* out, int nslot, cudaStream_t s) {
+  int nb = csr_blocks(A.n);
+  k_csr_tres_partial<<<dim3(nb, nf * nslot), 256, 0, s>>>(A, sigma, nf, b, X, partial);
+  launch_tres_finish(st, partial, nb, nf, nslot, out, s);
+}
+
+template <typename T>
+void launch_csr_dinv(int64_t n, const double* dk, const double* dm, const z64* taus, int ntau, cx<T>* out,
+                     cudaStream_t s) {
+  k_csr_dinv<T><<<cnb(n, 256), 256, 0, s>>>(n, dk, dm, taus, ntau, out);
+}
+
+// one cycle: `steps` BiCGSTAB steps from e = 0 on A e = f
+template <typename T>
+void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
+                      const cx<T>* dinv, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,
+                      int* launches) {
+  int nbk = csr_blocks(A.n);
+  dim3 g(nbk, nslot);
+  k_bcg_init<T><<<g, 256, 0, s>>>(st, V, A.n, sc);
+  int cnt = 1;
+  for (int it = 0; it < steps; ++it) {
+    k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.r, nullptr, A.n, partial);
+    k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 0);
+    k_bcg_p<T><<<g, 256, 0, s>>>(st, sc, V, dinv, A.n);
+    k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.ph, V.v);
+    k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.v, nullptr, A.n, partial);
+    k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 1);
+    k_bcg_s<T><<<g, 256, 0, s>>>(st, sc, V, dinv, A.n);
+    k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.sh, V.t);
+    k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.t, V.s, V.t, A.n, partial);
+    k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 2);
+    k_bcg_update<T><<<g, 256, 0, s>>>(st, sc, V, A.n);
+    k_bcg_close<<<cnb(nslot, 64), 64, 0, s>>>(st, sc, nslot);
+    cnt += 12;
+  }
+  if (launches) *launches += cnt;
+}
+
+#define CSR_INST(T)                                                                                              \
+  template void launch_csr_apply<T>(const CsrView<T>&, z64, const SlotState*, const z64*, const cx<T>*, cx<T>*,  \
+                                    int64_t, int, cudaStream_t);                                                 \
+  template void launch_csr_defect<T>(const CsrView<double>&, const SlotState*, const z64*, const z64*, int64_t,  \
+                                     const z64*, int64_t, int64_t, int, cx<T>*, int64_t, double*, int,           \
+                                     cudaStream_t);                                                              \
+  template void launch_csr_dinv<T>(int64_t, const double*, const double*, const z64*, int, cx<T>*, cudaStream_t); \
+  template void launch_bcg_cycle<T>(const CsrView<T>&, const SlotState*, const z64*, const BcgVecs<T>&,           \
+                                    const cx<T>*, BcgScal*, double*, int, int, cudaStream_t, int*);
+
+CSR_INST(double)
+CSR_INST(float)
+
+}  // namespace fks

@@ -516,7 +516,11 @@ void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z6
                           const SlotState* st, double* out, int nslot, cudaStream_t s) {
   dim3 g(nbk(L.nx, GX), nbk((int64_t)L.ny * L.nz, GY), nf * nslot);
   k_tres_partial<<<g, dim3(GX, GY), 0, s>>>(view<double>(L), sigma, nf, b, X, partial);
-  k_tres_finish<<<nbk((int64_t)nf * nslot, 8), 256, 0, s>>>(st, partial, tres_blocks(L), nf, nslot, out);
+  launch_tres_finish(st, partial, tres_blocks(L), nf, nslot, out, s);
+}
+void launch_tres_finish(const SlotState* st, const double* partial, int nblocks, int nf, int nslot, double* out,
+                        cudaStream_t s) {
+  k_tres_finish<<<nbk((int64_t)nf * nslot, 8), 256, 0, s>>>(st, partial, nblocks, nf, nslot, out);
 }
 
 }  // namespace fks

@@ -43,4 +43,8 @@ void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj,
 void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z64* b, const z64* X, double* partial,
                           const SlotState* st, double* out, int nslot, cudaStream_t s);
 
+// out[slot * nf + j] = sqrt(sum of the nblocks partials) / beta_slot
+void launch_tres_finish(const SlotState* st, const double* partial, int nblocks, int nf, int nslot, double* out,
+                        cudaStream_t s);
+
 }  // namespace fks

@@ -23,7 +23,7 @@ FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1,
 FKS_FGMRES, FKS_FFOM = 0, 1
 FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
 KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
-                  "assemble", "tres", "tail", "pre2d", "post2d"]
+                  "assemble", "tres", "tail", "pre2d", "post2d", "bicgstab"]
 
 
 class fks_c128(C.Structure):
@@ -35,7 +35,8 @@ class fks_options(C.Structure):
                 ("inner_tol", C.c_double), ("inner_max_cycles", C.c_int),
                 ("tau_schedule", C.POINTER(C.c_int32)), ("sched_len", C.c_int),
                 ("replay_mode", C.c_int), ("replay_inner_cycles", C.POINTER(C.c_int32)),
-                ("replay_mj", C.POINTER(C.c_int32)), ("launch_mode", C.c_int)]
+                ("replay_mj", C.POINTER(C.c_int32)), ("launch_mode", C.c_int),
+                ("inner_steps", C.c_int)]
 
 
 class fks_info(C.Structure):
@@ -81,6 +82,7 @@ def lib():
     L.fks_destroy.restype = None
     L.fks_op_grid.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), vp, vp, C.c_uint32,
                               C.POINTER(vp)]
+    L.fks_op_csr.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
     L.fks_op_destroy.argtypes = [vp]
     L.fks_op_destroy.restype = None
     L.fks_op_size.argtypes = [vp]
@@ -103,7 +105,7 @@ def lib():
     L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
-    for name in ("fks_create", "fks_op_grid", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
+    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_server_create", "fks_server_submit", "fks_server_poll", "fks_server_wait",
                  "fks_server_cancel", "fks_server_times"):
@@ -160,6 +162,18 @@ def fks_op_grid(ctx, dim, ncell, h, cond, ss, dirichlet_mask):
     return out
 
 
+def fks_op_csr(ctx, n, k_rowptr, k_col, k_val, m_rowptr, m_col, m_val):
+    """K and M as CSR arrays (row pointers int64, columns int32, values float64), host memory."""
+    a = [np.ascontiguousarray(k_rowptr, dtype=np.int64), np.ascontiguousarray(k_col, dtype=np.int32),
+         np.ascontiguousarray(k_val, dtype=np.float64), np.ascontiguousarray(m_rowptr, dtype=np.int64),
+         np.ascontiguousarray(m_col, dtype=np.int32), np.ascontiguousarray(m_val, dtype=np.float64)]
+    out = C.c_void_p()
+    st = lib().fks_op_csr(ctx, int(n), *[_ptr(x) for x in a], C.byref(out))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return out
+
+
 def fks_op_destroy(op) -> None:
     lib().fks_op_destroy(op)
 
@@ -169,7 +183,8 @@ def fks_op_size(op) -> int:
 
 
 def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP64, inner_tol=0.0,
-                 inner_max_cycles=50, schedule=(0,), replay_cycles=None, replay_mj=None, launch_mode=0):
+                 inner_max_cycles=50, schedule=(0,), replay_cycles=None, replay_mj=None, launch_mode=0,
+                 inner_steps=0):
     """fks_options plus the arrays it points to (kept alive in the returned tuple)."""
     sched = np.ascontiguousarray(schedule, dtype=np.int32)
     o = fks_options()
@@ -178,6 +193,7 @@ def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP6
     o.tau_schedule = sched.ctypes.data_as(C.POINTER(C.c_int32))
     o.sched_len = len(sched)
     o.launch_mode = int(launch_mode)
+    o.inner_steps = int(inner_steps)
     keep = [sched]
     if replay_cycles is not None:
         rc = np.ascontiguousarray(replay_cycles, dtype=np.int32)

@@ -1,8 +1,10 @@
 """Convenience layer over the C ABI for synthetic problems (marshalling only).
 
-`Solver` owns a context and a grid operator built from a synth.Problem and
-calls fks_solve with numpy (host) or torch (device) buffers. It contains no
-arithmetic of the method: every step runs in libfks.so.
+`Solver` owns a context and an operator and calls fks_solve with numpy (host)
+or torch (device) buffers. The operator is the grid operator of a
+synth.Problem, or, when `csr` is given, a general sparse K and M in CSR form
+(the problem then only supplies shifts, schedule, tolerance and sources). It
+contains no arithmetic of the method: every step runs in libfks.so.
 """
 from __future__ import annotations
 
@@ -29,9 +31,14 @@ class SolveOutput:
 
 
 class Solver:
-    def __init__(self, problem, device: int = 0):
+    def __init__(self, problem, device: int = 0, csr=None):
+        """csr: optional (k_rowptr, k_col, k_val, m_rowptr, m_col, m_val) of an n x n K and M."""
         self.p = problem
+        self.op = None
         self.ctx = fks.fks_create(device)
+        if csr is not None:
+            self.op = fks.fks_op_csr(self.ctx, problem.n, *csr)
+            return
         d = problem.dim
         ncell = [problem.shape[d - 1 - a] for a in range(d)]
         self.op = fks.fks_op_grid(self.ctx, d, ncell, problem.h, problem.cond, problem.ss, problem.dirichlet_mask)
@@ -52,7 +59,7 @@ class Solver:
 
     def solve(self, b=None, *, precision=fks.FKS_PREC_FP64, variant=fks.FKS_FGMRES, tol=None, m_max=None,
               inner_tol=0.0, inner_max_cycles=50, replay_cycles=None, replay_mj=None, device_out=False,
-              stream=None, sigma=None, tau=None, schedule=None, launch_mode=0):
+              stream=None, sigma=None, tau=None, schedule=None, launch_mode=0, inner_steps=0):
         p = self.p
         b = p.rhs().T.copy() if b is None else b            # n_rhs x n
         n_rhs = b.shape[0]
@@ -64,7 +71,7 @@ class Solver:
         opts, keep = fks.make_options(tol=p.tol if tol is None else tol, m_max=m_max, variant=variant,
                                       precision=precision, inner_tol=inner_tol, inner_max_cycles=inner_max_cycles,
                                       schedule=sched, replay_cycles=replay_cycles, replay_mj=replay_mj,
-                                      launch_mode=launch_mode)
+                                      launch_mode=launch_mode, inner_steps=inner_steps)
         if device_out:
             import torch
             X = torch.empty((n_rhs, n_f, p.n), dtype=torch.complex128, device="cuda")

@@ -38,6 +38,12 @@ def test_argument_errors_without_gpu(lib):
     assert st == fks.FKS_ERR_ARG
     assert "NULL" in fks.fks_last_error()
     assert lib.fks_op_size(None) == 0
+    rp = np.array([0, 1, 2], np.int64)
+    cl = np.array([0, 1], np.int32)
+    v = np.ones(2)
+    st = lib.fks_op_csr(None, 2, rp.ctypes.data, cl.ctypes.data, v.ctypes.data, rp.ctypes.data, cl.ctypes.data,
+                        v.ctypes.data, C.byref(out))
+    assert st == fks.FKS_ERR_ARG and not out.value
 
 
 def test_no_gpu_create_fails_loudly(lib):

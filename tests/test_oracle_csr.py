@@ -4,34 +4,13 @@ steps), the inner solve against sparse LU, and the whole shifted solve on a
 general sparse (non-grid) operator against dense solves."""
 import numpy as np
 import pytest
-import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 import oracle
 from oracle.csr import CSROperator, bicgstab_cycle, BiCGStabInner, csr_operator
 from paper_1212_3660_gb300 import synth
 
-
-def fe_like(n_side=12, seed=0):
-    """A 9-point (bilinear-element-like) SPD stiffness with random coefficients and a
-    consistent (non-diagonal) mass matrix on an n_side x n_side grid."""
-    rng = np.random.default_rng(seed)
-    n = n_side * n_side
-    K = sp.lil_matrix((n, n))
-    M = sp.lil_matrix((n, n))
-    idx = np.arange(n).reshape(n_side, n_side)
-    for j in range(n_side - 1):
-        for i in range(n_side - 1):
-            c = np.exp(rng.standard_normal())
-            nodes = [idx[j, i], idx[j, i + 1], idx[j + 1, i], idx[j + 1, i + 1]]
-            ke = c * (np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6.0)
-            me = np.array([[4, 2, 2, 1], [2, 4, 1, 2], [2, 1, 4, 2], [1, 2, 2, 4]]) / 36.0
-            for a in range(4):
-                for b in range(4):
-                    K[nodes[a], nodes[b]] += ke[a, b]
-                    M[nodes[a], nodes[b]] += me[a, b]
-    K = K.tocsr() + 1e-3 * sp.identity(n)        # zero-head anchoring keeps K SPD
-    return CSROperator(K.tocsr(), M.tocsr())
+from csr_util import fe_like
 
 
 @pytest.mark.parametrize("steps", [1, 3, 8])
