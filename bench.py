@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
     ap.add_argument("--workload", type=int, default=2)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="default: fp64 for workloads 1-2 (complex128 throughout), mixed for 3-5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
@@ -59,7 +60,208 @@ def parse():
                     help="one untimed solve and exit (a small command for ncu captures)")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="graph: the step loop as one CUDA graph; host: the same kernels launched one by one")
-    return ap.parse_args()
+    ap.add_argument("--requests", type=int, default=64, help="workload 5: requests in the stream")
+    ap.add_argument("--lanes", type=int, default=3, help="workload 5: concurrent server lanes")
+    ap.add_argument("--fuse-max", type=int, default=None,
+                    help="fused 2D levels up to this many cells (-1: all) instead of autotuning")
+    a = ap.parse_args()
+    if a.precision is None:
+        a.precision = "fp64" if a.workload in (1, 2) else "mixed"
+    return a
+
+
+def source_hash():
+    """Digest of the CUDA sources; DRAM traffic recorded for another digest is stale."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1212_3660_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, precision, kclass, level):
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of
+    this kernel class on this level, from the table in profiles/traffic.md, if it
+    was captured from the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None, None
+    cur = source_hash()
+    for line in open(path):
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) < 7 or cells[0] != workload:
+            continue
+        try:
+            if cells[1] == precision and cells[2] == kclass and int(cells[3]) == level:
+                return (float(cells[5]) if cells[6] == cur else None), cells[6]
+        except ValueError:
+            continue
+    return None, None
+
+
+# Serving stream (workload 5): request sizes are bounded so that every
+# request's host output (n x n_f x sources x 16 B) stays below 3.4 GB.
+SERVE_MAX_CELLS = 512 * 512
+SERVE_MAX_SOURCES = 4
+
+
+def serve_bench(args, rank, world, local, dist):
+    """Request loop over the server: a seeded Poisson stream of requests with
+    their own grids, fields, shift counts and sources, admitted by a device
+    memory budget onto concurrent lanes. Capacity is measured with every request
+    submitted at once; latency (submit to results in host memory) at Poisson
+    arrivals of 0.7x and 0.9x that capacity."""
+    import threading
+
+    import torch
+
+    from paper_1212_3660_gb300 import fks, synth
+    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    count = args.requests
+    stream = synth.make_request_stream(count, seed=3000 + rank, max_cells=SERVE_MAX_CELLS,
+                                       max_sources=SERVE_MAX_SOURCES)
+    probs = [synth.make_problem(m_max=100, **p) for _, p in stream]
+    arrival_unit = np.array([t for t, _ in stream])        # arrival times at 1 request/s
+    ctx = fks.fks_create(local)
+    t0 = time.perf_counter()
+    ops = []
+    for p in probs:
+        d = p.dim
+        ops.append(fks.fks_op_grid(ctx, d, [p.shape[d - 1 - a] for a in range(d)], p.h, p.cond, p.ss,
+                                   p.dirichlet_mask))
+    setup_ms = 1000 * (time.perf_counter() - t0)
+    free, _ = torch.cuda.mem_get_info(local)
+    budget = int(free * 0.6)
+    srv = fks.fks_server_create(ctx, budget, lanes=args.lanes)
+
+    def make_req(i):
+        p = probs[i]
+        opts, keep = fks.make_options(tol=TOL, m_max=p.m_max, precision=prec, inner_tol=INNER_EPS,
+                                      schedule=p.schedule)
+        return fks.ServerRequest(ops[i], p.rhs().T.copy(), p.sigma, p.tau_bar, opts, keep, p.n)
+
+    def run(idx, arrivals=None):
+        reqs = [None] * len(idx)
+        t_start = time.perf_counter()
+        err = []
+
+        def submitter():
+            try:
+                for q, i in enumerate(idx):
+                    if arrivals is not None:
+                        dt = t_start + arrivals[q] - time.perf_counter()
+                        if dt > 0:
+                            time.sleep(dt)
+                    r = make_req(i)
+                    fks.fks_server_submit(srv, r)
+                    reqs[q] = r
+            except Exception as e:  # noqa: BLE001
+                err.append(e)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        if err:
+            raise err[0]
+        lat, conv, total, ends, starts, statuses = [], 0, 0, [], [], []
+        h2d = d2h = 0
+        for r in reqs:
+            statuses.append(fks.fks_server_wait(srv, r.ticket))
+            ts, _, te = fks.fks_server_times(srv, r.ticket)
+            lat.append(1000 * (te - ts))
+            starts.append(ts)
+            ends.append(te)
+            conv += int(np.sum(r.res_true <= TOL))
+            total += r.res_true.size
+            h2d += r.b.nbytes + r.sigma.nbytes + r.tau.nbytes
+            d2h += r.X.nbytes + r.res_true.size * (8 * 3 + 4 * 2)
+        wall = max(ends) - min(starts)
+        return {"wall_s": wall, "converged": conv, "solves": total, "solves_per_s": conv / wall,
+                "requests_per_s": len(idx) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "h2d": h2d, "d2h": d2h,
+                "statuses": sorted(set(int(x) for x in statuses))}
+
+    # warm-up: the first few requests once (graph capture, workspaces)
+    for _ in range(max(args.warmup, 1)):
+        run(list(range(min(4, count))))
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    l0 = fks.fks_server_launches(srv)
+    with ClockSampler(gpu_index) as clk:
+        if world > 1:
+            dist.barrier()
+        cap = run(list(range(count)))
+        loads = {}
+        for f in (0.7, 0.9):
+            lam = f * cap["requests_per_s"]
+            loads[f"{f:.1f}"] = run(list(range(count)), arrivals=arrival_unit / lam)
+        if world > 1:
+            dist.barrier()
+    launches = fks.fks_server_launches(srv) - l0
+
+    def over_ranks(x, op):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=torch.device("cuda", local))
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    wall = over_ranks(cap["wall_s"], dist.ReduceOp.MAX if world > 1 else None)
+    value = over_ranks(cap["converged"], dist.ReduceOp.SUM if world > 1 else None) / wall
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        p0 = probs[0]
+        r0 = make_req(0)
+        fks.fks_server_submit(srv, r0)
+        fks.fks_server_wait(srv, r0.ticket)
+        ws = int(r0.m_j.max())
+        v, dt, desc = cpu_oracle_sample(p0, min(args.cpu_sample_steps, ws), ws, INNER_EPS)
+        cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"request 0 ({'x'.join(map(str, p0.shape[::-1]))}, {len(p0.sigma)} shifts, "
+                         f"{len(p0.src_cells)} sources; first source): " + desc}
+    fks.fks_server_destroy(srv)
+    for op in ops:
+        fks.fks_op_destroy(op)
+    fks.fks_destroy(ctx)
+    if rank == 0:
+        shapes = {}
+        for p in probs:
+            k = "x".join(map(str, p.shape[::-1]))
+            shapes[k] = shapes.get(k, 0) + 1
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
+                "warmup": max(args.warmup, 1), "ms_per_step": 1000 * wall, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer", "data": "synthetic",
+                "config": {"workload": "serving-stream", "requests": count, "grids": shapes,
+                           "max_cells": SERVE_MAX_CELLS, "max_sources": SERVE_MAX_SOURCES,
+                           "shifted_solves": cap["solves"], "lanes": args.lanes, "mem_budget_bytes": budget,
+                           "precision": args.precision, "parallelism": f"replicas{world}",
+                           "step": "one pass over the stream with every request submitted at once",
+                           "op_setup_ms_all_requests": setup_ms,
+                           "l2": "requests up to 512^2 / 64^3 cells; bases and outputs exceed L2"},
+                "latency_ms": {"closed_loop": {"p50": cap["p50_ms"], "p99": cap["p99_ms"]},
+                               **{f"poisson_{k}x_capacity": {"p50": v_["p50_ms"], "p99": v_["p99_ms"],
+                                                             "solves_per_s": v_["solves_per_s"],
+                                                             "offered_requests_per_s": float(k) * cap["requests_per_s"]}
+                                  for k, v_ in loads.items()}},
+                "converged_per_step": cap["converged"], "request_statuses": cap["statuses"],
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": cap["h2d"],
+                        "d2h_bytes_per_step": cap["d2h"],
+                        "note": "the server API takes host buffers: every request's copies are inside the timed region"},
+                "roofline": None,
+                "roofline_note": "per-kernel event timing runs on fks_solve's lane; the kernels are those of the "
+                                 "workload 1-4 lines",
+                "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
 
 
 def dist_env():
@@ -139,9 +341,9 @@ def cpu_oracle_sample(pr, sample_steps, workload_steps, eps):
     res = oracle.shifted_solve(op, b, pr.sigma, pr.tau_bar, pr.schedule, 0.0, sample_steps, GMGInner(hier, eps))
     dt = time.perf_counter() - t0
     t_full = dt * workload_steps / max(res.steps, 1)
-    desc = (f"oracle setup + first {res.steps} of {workload_steps} flexible Arnoldi steps of the same workload "
+    desc = (f"oracle setup + first {res.steps} of {workload_steps} flexible Arnoldi steps of the first source "
             f"({dt:.1f} s), scaled linearly to {workload_steps} steps")
-    return len(pr.sigma) * len(pr.src_cells) / t_full, dt, desc
+    return len(pr.sigma) / t_full, dt, desc   # one source's shifted solves
 
 
 def blas_threads():
@@ -156,7 +358,13 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    pr = synth.workload(args.workload, m_max=100)
+    if args.workload == 5:
+        # the stream's first request stands for the stream
+        _, p0 = synth.make_request_stream(1, seed=3000, max_cells=SERVE_MAX_CELLS, max_sources=SERVE_MAX_SOURCES)[0]
+        pr = synth.make_problem(m_max=100, **p0)
+        pr.name = "serving-stream"
+    else:
+        pr = synth.workload(args.workload, m_max=100)
     ws = WORKLOAD_STEPS.get(args.workload, 40)
     vals, secs = [], []
     sample = None
@@ -191,6 +399,11 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     build.build()
+    if args.workload == 5:
+        serve_bench(args, rank, world, local, dist)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     pr = synth.workload(args.workload, m_max=100)
     prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
     t_setup0 = time.perf_counter()
@@ -235,13 +448,18 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
+    if args.fuse_max is not None:
+        fks.fks_op_set_fusion(solver.op, prec, args.fuse_max)
     if args.single:
         st = step(b_d, X_d)
         torch.cuda.synchronize()
         print(json.dumps({"single_solve_status": st, "converged": int(np.sum(tru <= TOL))}), flush=True)
         solver.close()
         return
-    tuned = fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+    if args.fuse_max is not None:
+        tuned = args.fuse_max
+    else:
+        tuned = fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
     for _ in range(args.warmup):
         step(b_d, X_d)
     # kernel-class survey (stderr only) and choice of the dominant class
@@ -289,12 +507,21 @@ def main():
     conv_per_step = converged / args.steps
     value = sum_over_ranks(conv_per_step) / (ms_max / 1000.0)
 
-    # ---- roofline of the dominant kernel class (events on the library's stream)
-    fks.fks_profile_select(solver.op, dominant)
-    for _ in range(args.steps):
-        step(b_d, X_d, opts_host)
-    prof = fks.fks_profile_read(solver.op)
-    fks.fks_profile_select(solver.op, None)
+    # ---- roofline of the dominant kernel class (events on the library's stream),
+    # on the finest level where the class runs per level
+    def timed_class(level):
+        fks.fks_profile_select(solver.op, dominant, level)
+        for _ in range(args.steps):
+            step(b_d, X_d, opts_host)
+        pr_ = fks.fks_profile_read(solver.op)
+        fks.fks_profile_select(solver.op, None)
+        return pr_
+    roof_level = 0
+    prof = timed_class(0)
+    if prof["launches"] == 0:
+        roof_level = -1
+        prof = timed_class(-1)
+    traffic, traffic_src = recorded_traffic(pr.name, args.precision, dominant, roof_level)
     hbm_peak, bf16_peak, peak_src = peaks()
     gbs = prof["bytes"] / max(prof["ms"], 1e-12) / 1e6
     tfl = prof["flops"] / max(prof["ms"], 1e-12) / 1e9
@@ -303,12 +530,13 @@ def main():
                                                                                  "defect", "tres") else 0.0
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
-                "traffic": None, "kernel": dominant, "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                "traffic": traffic, "kernel": dominant, "level": roof_level,
+                "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz",
                 "launches": prof["launches"], "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
                 "hbm_frac_of_" + peak_src: f_hbm}
     else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm, "traffic": None,
-                "kernel": dominant, "peak_source": peak_src, "launches": prof["launches"],
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm, "traffic": traffic,
+                "kernel": dominant, "level": roof_level, "peak_source": peak_src, "launches": prof["launches"],
                 "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1)}
 
     def end_to_end():
@@ -340,6 +568,9 @@ def main():
         v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS)
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
 
+    roof["alg_bytes_per_launch"] = prof["bytes"] / max(prof["launches"], 1)
+    roof["traffic_source"] = ("profiles/traffic.md (ncu, sources " + traffic_src + ")") if traffic is not None else (
+        "stale: kernels changed since the ncu capture" if traffic_src else "no ncu capture recorded")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

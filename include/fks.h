@@ -217,6 +217,8 @@ fks_status fks_server_wait(fks_server* srv, uint64_t ticket, fks_status* result)
 fks_status fks_server_cancel(fks_server* srv, uint64_t ticket);
 /* Host wall-clock seconds (steady clock) of submit, start and end of a request. */
 fks_status fks_server_times(fks_server* srv, uint64_t ticket, double* submit_s, double* start_s, double* end_s);
+/* Kernel launches made by the server's lanes since it was created. */
+fks_status fks_server_launches(fks_server* srv, int64_t* launches);
 /* Stops the workers after their current batches; queued requests are dropped. */
 void fks_server_destroy(fks_server* srv);
 

@@ -1923,6 +1923,16 @@ extern "C" fks_status fks_server_times(fks_server* sv, uint64_t ticket, double* 
   return FKS_OK;
 }
 
+extern "C" fks_status fks_server_launches(fks_server* sv, int64_t* launches) {
+  if (!sv || !launches) { set_error("fks_server_launches: NULL argument"); return FKS_ERR_ARG; }
+  // the lanes' counters are updated by batches holding this lock
+  std::lock_guard<std::mutex> lk(g_api_mu);
+  int64_t t = 0;
+  for (auto& l : sv->lanes) t += l->prof.all_launches;
+  *launches = t;
+  return FKS_OK;
+}
+
 extern "C" void fks_server_destroy(fks_server* sv) {
   if (!sv) return;
   {

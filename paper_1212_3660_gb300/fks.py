@@ -101,6 +101,7 @@ def lib():
     L.fks_server_wait.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int)]
     L.fks_server_cancel.argtypes = [vp, C.c_uint64]
     L.fks_server_times.argtypes = [vp, C.c_uint64, f64p, f64p, f64p]
+    L.fks_server_launches.argtypes = [vp, C.POINTER(C.c_int64)]
     L.fks_server_destroy.argtypes = [vp]
     L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
@@ -108,7 +109,7 @@ def lib():
     for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_server_create", "fks_server_submit", "fks_server_poll", "fks_server_wait",
-                 "fks_server_cancel", "fks_server_times"):
+                 "fks_server_cancel", "fks_server_times", "fks_server_launches"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -357,6 +358,14 @@ def fks_server_cancel(srv, ticket):
     st = lib().fks_server_cancel(srv, C.c_uint64(ticket))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
+
+
+def fks_server_launches(srv):
+    n = C.c_int64(0)
+    st = lib().fks_server_launches(srv, C.byref(n))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return int(n.value)
 
 
 def fks_server_times(srv, ticket):
