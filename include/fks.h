@@ -133,6 +133,10 @@ typedef struct {
                             inner cycle; per-kernel timing with fks_profile_select works here)  */
   int inner_steps;       /* CSR operators: BiCGSTAB steps per inner cycle (<= 0 means 8, at most
                             64); ignored by grid operators                                    */
+  int assembly;          /* x_j = Z y_j (Algorithm 4): 0 = tensor cores (Z and Y cut into eight
+                            7-bit bf16 slices, exact fp32 accumulation of the slice products,
+                            error at the level of an FP64 GEMM; used when 2 * steps <= 128,
+                            else the FP64 kernel); 1 = FP64 FMA kernel                         */
 } fks_options;
 
 /* Optional per-solve diagnostics, host arrays owned by the caller (any may be NULL). */

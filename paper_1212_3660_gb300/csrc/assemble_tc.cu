@@ -1,0 +1,393 @@
+// X = Z Y on the tensor cores (see assemble_tc.cuh for the slicing scheme).
+//
+// Kernels: k_tc_slice_a (row exponents and slices of [Re z, Im z]),
+// k_tc_slice_b (column exponents and slices of the interleaved Y columns) and
+// k_tc_gemm: one CTA per (32-column tile, 128-row tile, source); one thread
+// streams 16-wide k' slabs of all slices into shared memory with bulk async
+// copies (two stages, mbarrier transaction counts) and issues the 36
+// tcgen05.mma per slab into eight TMEM accumulators; then four warps read the
+// accumulators with tcgen05.ld and write x_j. Every wait on an mbarrier gives
+// up after two seconds, sets the error flag and still releases TMEM.
+#include "assemble_tc.cuh"
+
+namespace fks {
+
+namespace {
+
+constexpr int STAGE_BYTES = TC_A_SLAB + TC_B_SLAB;
+constexpr int GEMM_SMEM = 2 * STAGE_BYTES + 64;
+constexpr uint32_t TMEM_COLS = 256;  // 8 levels x 32 columns
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63) == 0) {
+      uint64_t t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > 2000000000ull) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8 rows x
+// 16 bytes; lbo = byte step between the two core matrices along k, sbo = byte
+// step between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of sm_100 and later
+  return d;                // base offset 0, relative lbo, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D, M = 128, N = 32.
+__host__ __device__ constexpr uint32_t mma_idesc() {
+  return (1u << 4)                        // D format: f32
+         | (1u << 7)                      // A format: bf16
+         | (1u << 10)                     // B format: bf16
+         | ((uint32_t)(TC_N >> 3) << 17)  // N / 8
+         | ((uint32_t)(TC_M >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Sources whose step count keeps the padded 2K within the exactness bound.
+__host__ __device__ __forceinline__ bool tc_slot(int K) {
+  return K >= 0 && ((2 * K + TC_KSLAB - 1) / TC_KSLAB) * TC_KSLAB <= TC_MAX_KP;
+}
+
+// Exponent e with max |row| < 2^e (0 for a zero row).
+__device__ __forceinline__ int pow2_above(double amax) {
+  if (amax == 0.0) return 0;
+  int e;
+  frexp(amax, &e);
+  return e;
+}
+
+// Eight signed 7-bit digits of v / 2^e (|v| < 2^e): v = 2^e sum_s d_s 2^{-7(s+1)}
+// up to the truncated bits below 2^{e-56}.
+__device__ __forceinline__ void digits7(double v, int e, int (&d)[TC_SLICES]) {
+  const unsigned long long X = (unsigned long long)__double2ull_rz(scalbn(fabs(v), 56 - e));
+  const int sg = v < 0.0 ? -1 : 1;
+#pragma unroll
+  for (int s = 0; s < TC_SLICES; ++s) d[s] = sg * (int)((X >> (49 - 7 * s)) & 127ull);
+}
+
+// bf16 bits of a small integer (exact: at most 8 significant bits)
+__device__ __forceinline__ uint32_t bf16_of(int d) { return __float_as_uint((float)d) >> 16; }
+
+__device__ __forceinline__ uint4 pack8(const int (&d)[8][TC_SLICES], int s) {
+  uint4 w;
+  w.x = bf16_of(d[0][s]) | (bf16_of(d[1][s]) << 16);
+  w.y = bf16_of(d[2][s]) | (bf16_of(d[3][s]) << 16);
+  w.z = bf16_of(d[4][s]) | (bf16_of(d[5][s]) << 16);
+  w.w = bf16_of(d[6][s]) | (bf16_of(d[7][s]) << 16);
+  return w;
+}
+
+}  // namespace
+
+// Slices of A = [Re z_k, Im z_k] (k' = 2k, 2k + 1), one thread per row.
+// Layout (16-byte rows): [slot][row tile][slab][slice][8-row group 16][k chunk 2][row 8].
+__global__ void __launch_bounds__(TC_M) k_tc_slice_a(const SlotState* __restrict__ st, const z64* __restrict__ Z,
+                                                      int64_t vsZ, int64_t n, int nslab, int nrt,
+                                                      uint4* __restrict__ As, int* __restrict__ erow) {
+  const int rt = blockIdx.x, slot = blockIdx.y, r = threadIdx.x;
+  // this source's own steps: the columns of Z it wrote in this solve
+  const int K = st[slot].k;
+  if (!tc_slot(K)) return;
+  const int64_t i = (int64_t)rt * TC_M + r;
+  const z64* Zs = Z + slot * vsZ;
+  double amax = 0.0;
+  if (i < n)
+    for (int k = 0; k < K; ++k) {
+      z64 z = Zs[(int64_t)k * n + i];
+      amax = fmax(amax, fmax(fabs(z.re), fabs(z.im)));
+    }
+  const int e = pow2_above(amax);
+  erow[((int64_t)slot * nrt + rt) * TC_M + r] = e;
+  const int g = r >> 3, rr = r & 7;
+  uint4* base = As + (size_t)(slot * nrt + rt) * nslab * (TC_A_SLAB / 16);
+  for (int c = 0; c < 2 * nslab; ++c) {
+    int d[8][TC_SLICES];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * c + q;
+      z64 z = (i < n && k < K) ? Zs[(int64_t)k * n + i] : mk(0.0, 0.0);
+      digits7(z.re, e, d[2 * q]);
+      digits7(z.im, e, d[2 * q + 1]);
+    }
+    const int slab = c >> 1, kc = c & 1;
+    uint4* sb = base + (size_t)slab * (TC_A_SLAB / 16);
+#pragma unroll
+    for (int s = 0; s < TC_SLICES; ++s) sb[((s * 16 + g) * 2 + kc) * 8 + rr] = pack8(d, s);
+  }
+}
+
+// Slices of B: column 2j = [Re y_j; -Im y_j], column 2j + 1 = [Im y_j; Re y_j],
+// interleaved over k like A; y_{j,k} = 0 for k >= m_j. One thread per column.
+// Layout: [slot][column tile][slab][slice][8-column group 4][k chunk 2][column 8].
+__global__ void __launch_bounds__(TC_N) k_tc_slice_b(const SlotState* __restrict__ st, const z64* __restrict__ Y,
+                                                      const int32_t* __restrict__ mj, int nf, int m, int nslab,
+                                                      int nct, uint4* __restrict__ Bs, int* __restrict__ ecol) {
+  const int ct = blockIdx.x, slot = blockIdx.y, c = threadIdx.x;
+  const int K = st[slot].k;
+  if (!tc_slot(K)) return;
+  const int jp = ct * TC_N + c, j = jp >> 1, part = jp & 1;
+  const int mjj = j < nf ? min((int)mj[(int64_t)slot * nf + j], K) : 0;
+  const z64* y = Y + ((int64_t)slot * nf + (j < nf ? j : 0)) * m;
+  auto val = [&](int kp) -> double {
+    const int k = kp >> 1;
+    if (k >= mjj) return 0.0;
+    const z64 v = y[k];
+    const int h = kp & 1;
+    return part == 0 ? (h == 0 ? v.re : -v.im) : (h == 0 ? v.im : v.re);
+  };
+  double amax = 0.0;
+  for (int kp = 0; kp < 2 * mjj; ++kp) amax = fmax(amax, fabs(val(kp)));
+  const int e = pow2_above(amax);
+  ecol[((int64_t)slot * nct + ct) * TC_N + c] = e;
+  const int g = c >> 3, rr = c & 7;
+  uint4* base = Bs + (size_t)(slot * nct + ct) * nslab * (TC_B_SLAB / 16);
+  for (int cc = 0; cc < 2 * nslab; ++cc) {
+    int d[8][TC_SLICES];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) digits7(val(8 * cc + q), e, d[q]);
+    const int slab = cc >> 1, kc = cc & 1;
+    uint4* sb = base + (size_t)slab * (TC_B_SLAB / 16);
+#pragma unroll
+    for (int s = 0; s < TC_SLICES; ++s) sb[((s * 4 + g) * 2 + kc) * 8 + rr] = pack8(d, s);
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const SlotState* __restrict__ st,
+                                                     const unsigned char* __restrict__ As,
+                                                     const unsigned char* __restrict__ Bs,
+                                                     const int* __restrict__ erow, const int* __restrict__ ecol,
+                                                     int nslab, int nrt, int nct, int64_t n, int nf,
+                                                     z64* __restrict__ X, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * STAGE_BYTES);  // full[2], free[2], done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
+  int* sfail = reinterpret_cast<int*>(tslot + 1);
+  const int ct = blockIdx.x, rt = blockIdx.y, slot = blockIdx.z;
+  if (!tc_slot(st[slot].k)) return;  // this source is assembled by the FP64 kernel
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t full0 = smem_u32(&bars[0]), free0 = smem_u32(&bars[2]), done = smem_u32(&bars[4]);
+  if (threadIdx.x == 0) {
+    mbar_init(full0, 1);
+    mbar_init(full0 + 8, 1);
+    mbar_init(free0, 1);
+    mbar_init(free0 + 8, 1);
+    mbar_init(done, 1);
+    *sfail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    const unsigned char* asrc = As + (size_t)(slot * nrt + rt) * nslab * TC_A_SLAB;
+    const unsigned char* bsrc = Bs + (size_t)(slot * nct + ct) * nslab * TC_B_SLAB;
+    constexpr uint32_t idesc = mma_idesc();
+    bool ok = true;
+    int loaded = 1, consumed = 0;
+    mbar_expect_tx(full0, STAGE_BYTES);
+    bulk_g2s(sbase, asrc, TC_A_SLAB, full0);
+    bulk_g2s(sbase + TC_A_SLAB, bsrc, TC_B_SLAB, full0);
+    uint32_t started = 0;  // accumulators already written
+    for (int q = 0; q < nslab; ++q) {
+      const int st = q & 1;
+      if (q + 1 < nslab) {
+        const int ns = (q + 1) & 1;
+        // the stage is free once the MMAs of slab q - 1 completed
+        if (q + 1 >= 2 && !mbar_wait(free0 + 8 * ns, ((q + 1) / 2 - 1) & 1)) { ok = false; break; }
+        const uint32_t dst = sbase + ns * STAGE_BYTES, fb = full0 + 8 * ns;
+        mbar_expect_tx(fb, STAGE_BYTES);
+        bulk_g2s(dst, asrc + (size_t)(q + 1) * TC_A_SLAB, TC_A_SLAB, fb);
+        bulk_g2s(dst + TC_A_SLAB, bsrc + (size_t)(q + 1) * TC_B_SLAB, TC_B_SLAB, fb);
+        ++loaded;
+      }
+      if (!mbar_wait(full0 + 8 * st, (q / 2) & 1)) { ok = false; break; }
+      ++consumed;
+      tc_fence_after();
+      const uint32_t a0 = sbase + st * STAGE_BYTES, b0 = a0 + TC_A_SLAB;
+#pragma unroll 1
+      for (int s = 0; s < TC_SLICES; ++s)
+#pragma unroll 1
+        for (int t = 0; s + t < TC_SLICES; ++t) {
+          const int lev = s + t;
+          mma_bf16(tmem + (uint32_t)(lev * TC_N), smem_desc(a0 + s * (TC_A_SLAB / TC_SLICES), 128, 256),
+                   smem_desc(b0 + t * (TC_B_SLAB / TC_SLICES), 128, 256), idesc, (started >> lev) & 1u);
+          started |= 1u << lev;
+        }
+      mma_commit(free0 + 8 * st);
+    }
+    mma_commit(done);
+    if (!ok) {
+      atomicExch(err, 1);
+      *sfail = 1;
+      // let copies still in flight land before the CTA exits
+      for (int q = consumed; q < loaded; ++q) mbar_wait(full0 + 8 * (q & 1), (q / 2) & 1);
+    }
+  }
+  if (warp == 0) __syncwarp();  // the other lanes of the issuing warp wait here, not in a spin
+  if (!mbar_wait(done, 0)) {
+    atomicExch(err, 2);
+    *sfail = 1;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (*sfail == 0) {  // uniform over the CTA: tcgen05.ld is executed by whole warps
+    const int r = warp * 32 + lane;
+    const int64_t i = (int64_t)rt * TC_M + r;
+    const int e = erow[((int64_t)slot * nrt + rt) * TC_M + r];
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+#pragma unroll 1
+      for (int lev = 0; lev < TC_SLICES; ++lev) {
+        uint32_t v[16];
+        tmem_ld16(trow + (uint32_t)(lev * TC_N + h * 16), v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const long long a = (long long)__float2int_rn(__uint_as_float(v[c]));
+          if (lev < 4) hi[c] = hi[c] * 128 + a;
+          else lo[c] = lo[c] * 128 + a;
+        }
+      }
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+          const int jp = ct * TC_N + h * 16 + c;
+          const int j = jp >> 1;
+          if (j >= nf) break;
+          const int f0 = ecol[((int64_t)slot * nct + ct) * TC_N + h * 16 + c];
+          const int f1 = ecol[((int64_t)slot * nct + ct) * TC_N + h * 16 + c + 1];
+          z64 x;
+          x.re = scalbn(fma((double)lo[c], 0x1p-28, (double)hi[c]), e + f0 - 35);
+          x.im = scalbn(fma((double)lo[c + 1], 0x1p-28, (double)hi[c + 1]), e + f1 - 35);
+          X[((int64_t)slot * nf + j) * n + i] = x;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------ host
+bool tc_supported(int K, int64_t n) { return K >= 1 && tc_slot(K) && (n + TC_M - 1) / TC_M <= 65535; }
+
+TcLayout tc_layout(int64_t n, int nf, int K, int nslot) {
+  TcLayout T{};
+  T.K = K;
+  T.nslab = (2 * K + TC_KSLAB - 1) / TC_KSLAB;
+  T.nrt = (int)((n + TC_M - 1) / TC_M);
+  T.nct = (2 * nf + TC_N - 1) / TC_N;
+  T.a_bytes = (size_t)nslot * T.nrt * T.nslab * TC_A_SLAB;
+  T.b_bytes = (size_t)nslot * T.nct * T.nslab * TC_B_SLAB;
+  T.e_bytes = (size_t)nslot * T.nrt * TC_M * sizeof(int);
+  T.f_bytes = (size_t)nslot * T.nct * TC_N * sizeof(int);
+  return T;
+}
+
+void tc_prepare() {
+  cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+}
+
+static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int launch_tc_assemble(const TcLayout& T, const SlotState* st, const z64* Z, int64_t vsZ, const z64* Y,
+                       const int32_t* mj, int nf, int m, z64* X, int64_t n, int nslot, void* ws, int* err,
+                       cudaStream_t s) {
+  unsigned char* w = (unsigned char*)ws;
+  uint4* As = (uint4*)w;
+  w += align256(T.a_bytes);
+  uint4* Bs = (uint4*)w;
+  w += align256(T.b_bytes);
+  int* erow = (int*)w;
+  w += align256(T.e_bytes);
+  int* ecol = (int*)w;
+  k_tc_slice_a<<<dim3(T.nrt, nslot), TC_M, 0, s>>>(st, Z, vsZ, n, T.nslab, T.nrt, As, erow);
+  k_tc_slice_b<<<dim3(T.nct, nslot), TC_N, 0, s>>>(st, Y, mj, nf, m, T.nslab, T.nct, Bs, ecol);
+  k_tc_gemm<<<dim3(T.nct, T.nrt, nslot), 128, GEMM_SMEM, s>>>(st, (const unsigned char*)As, (const unsigned char*)Bs,
+                                                                erow, ecol, T.nslab, T.nrt, T.nct, n, nf, X, err);
+  return 3;
+}
+
+}  // namespace fks

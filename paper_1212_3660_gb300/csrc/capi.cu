@@ -24,6 +24,7 @@
 #include "grid.cuh"
 #include "krylov.cuh"
 #include "csr.cuh"
+#include "assemble_tc.cuh"
 
 namespace fks {
 
@@ -144,6 +145,7 @@ struct Prof {
 // gives each concurrent batch a lane of its own.
 struct Lane {
   Arena ws;
+  Arena tcws;  // slices of the tensor-core assembly
   Prof prof;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
@@ -152,6 +154,7 @@ struct Lane {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
     ws.release();
+    tcws.release();
     prof.release();
   }
 };
@@ -860,10 +863,46 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
     }
   }
   // assembly and true residual
+  int tc_err_h = 0;
+  int* tc_err = nullptr;
   {
     const double ns = n_rhs, nn = (double)n, ks = steps, d = op->dim;
-    PROF(FKS_K_ASSEMBLE, -1, ns * 16 * nn * (ks + n_f), ns * 8 * nn * ks * n_f,
-         launch_assemble(S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, s));
+    // each source's own step count decides its kernel, so that a source is
+    // assembled the same way alone and in a batch
+    CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int k_tc = 0;
+    bool any_fp64 = false;
+    for (int r = 0; r < n_rhs; ++r) {
+      if (tc_supported(std::max(S.st_host[r].k, 1), n)) k_tc = std::max(k_tc, S.st_host[r].k);
+      else any_fp64 = true;
+    }
+    const bool use_tc = o->assembly == 0 && k_tc >= 1;
+    if (use_tc) {
+      // tensor cores: slices of Z and Y, the product, the epilogue
+      TcLayout T = tc_layout(n, n_f, k_tc, n_rhs);
+      size_t need = 0;
+      for (size_t b : {T.a_bytes, T.b_bytes, T.e_bytes, T.f_bytes}) need += (b + 255) & ~(size_t)255;
+      lane->tcws.reserve(need + 256);
+      tc_err = (int*)(lane->tcws.base + need);
+      {
+        std::lock_guard<std::mutex> build_lock(g_build_mu);
+        tc_prepare();
+      }
+      CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
+      const double kt = k_tc, kp = 16.0 * T.nslab;
+      int launched = 0;
+      PROF(FKS_K_ASSEMBLE, -1, ns * (2 * 16 * nn * kt + 2 * 16 * nn * kp + 16 * nn * n_f),
+           ns * 8 * nn * kt * n_f,
+           launched = launch_tc_assemble(T, S.st, S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, lane->tcws.base,
+                                         tc_err, s));
+      lane->prof.all_launches += launched - 1;  // the two slicing kernels beyond the one PROF counted
+    }
+    if (!use_tc || any_fp64) {
+      const int skip = use_tc ? TC_MAX_KP / 2 : -1;  // sources up to this step count were done above
+      PROF(FKS_K_ASSEMBLE, -1, ns * 16 * nn * (ks + n_f), ns * 8 * nn * ks * n_f,
+           launch_assemble(S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, s, use_tc ? S.st : nullptr, skip));
+    }
     if (res_true && op->csr)
       PROF(FKS_K_TRES, -1, ns * (nn * (16.0 * n_f + 16) + n_f * op->cd.nnz * 36.0), ns * n_f * op->cd.nnz * 10.0,
            launch_csr_true_residual(op->cd.view<double>(n), S.sigma, n_f, S.b, Xd, S.tpart, S.st, S.tres, n_rhs, s));
@@ -903,6 +942,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
   int singular = 0;
   CK(cudaMemcpyAsync(&singular, S.singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (tc_err) CK(cudaMemcpyAsync(&tc_err_h, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   if (info) {
@@ -914,6 +954,10 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
     if (info->pnorm) std::memcpy(info->pnorm, pn_h.data(), sizeof(double) * m * n_rhs);
   }
   (void)steps;
+  if (tc_err_h) {
+    set_error("tensor-core assembly: a wait for copies or MMAs gave up after two seconds");
+    return FKS_ERR_CUDA;
+  }
   if (singular) {
     set_error("coarsest multigrid level is singular for some tau");
     return FKS_ERR_ARG;
@@ -1244,6 +1288,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
     if (o->tau_schedule[i] < 0 || o->tau_schedule[i] >= n_tau) { set_error("fks_solve: schedule index out of range"); return FKS_ERR_ARG; }
   if (o->launch_mode != 0 && o->launch_mode != 1) { set_error("fks_solve: launch_mode must be 0 or 1"); return FKS_ERR_ARG; }
   if (o->inner_steps > 64) { set_error("fks_solve: inner_steps must be at most 64"); return FKS_ERR_ARG; }
+  if (o->assembly != 0 && o->assembly != 1) { set_error("fks_solve: assembly must be 0 or 1"); return FKS_ERR_ARG; }
   if (o->replay_mode && (!o->replay_inner_cycles || !o->replay_mj)) { set_error("fks_solve: replay arrays missing"); return FKS_ERR_ARG; }
   if (o->replay_mode) {
     for (int i = 0; i < o->m_max * n_rhs; ++i)
@@ -1651,7 +1696,7 @@ static bool compatible(const Request& a, const Request& b) {
   const fks_options &p = x.opt, &q = y.opt;
   if (p.tol != q.tol || p.m_max != q.m_max || p.variant != q.variant || p.precision != q.precision ||
       p.inner_tol != q.inner_tol || p.inner_max_cycles != q.inner_max_cycles || p.replay_mode || q.replay_mode ||
-      std::max(p.inner_steps, 0) != std::max(q.inner_steps, 0) ||
+      std::max(p.inner_steps, 0) != std::max(q.inner_steps, 0) || p.assembly != q.assembly ||
       a.sched != b.sched)
     return false;
   for (int j = 0; j < x.n_f; ++j)
@@ -1842,7 +1887,8 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
       !r->shift_status || r->n_rhs < 1 || r->n_f < 1 || r->n_tau < 1 || r->n_tau > MAX_TAU ||
       o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
       (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
-      (o.variant != FKS_FGMRES && o.variant != FKS_FFOM) || o.inner_steps > 64) {
+      (o.variant != FKS_FGMRES && o.variant != FKS_FFOM) || o.inner_steps > 64 ||
+      (o.assembly != 0 && o.assembly != 1)) {
     set_error("fks_server_submit: bad request");
     return FKS_ERR_ARG;
   }

@@ -370,8 +370,9 @@ __global__ void k_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGr
 
 // X[:, j] = Z Y[:, j] for a tile of AS_J shifts (Y is zero beyond m_j).
 __global__ void k_assemble(const z64* __restrict__ Z, int64_t vsZ, const z64* __restrict__ Y, const int32_t* __restrict__ mj,
-                           int nf, int m, z64* __restrict__ X, int64_t n) {
+                           int nf, int m, z64* __restrict__ X, int64_t n, const SlotState* st, int skip_k_le) {
   int slot = blockIdx.y;
+  if (st && st[slot].k <= skip_k_le) return;  // assembled on the tensor cores
   int j0 = blockIdx.z * AS_J;
   __shared__ z64 ys[AS_J][MAX_M];
   __shared__ int kmax_s;
@@ -507,9 +508,9 @@ void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphCon
   k_step_end<<<1, 256, 0, s>>>(st, nslot, m, use_cond, cond);
 }
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
-                     int nslot, cudaStream_t s) {
+                     int nslot, cudaStream_t s, const SlotState* st, int skip_k_le) {
   dim3 g(nbk(n, 256), nslot, nbk(nf, AS_J));
-  k_assemble<<<g, 256, 0, s>>>(Z, vsZ, Y, mj, nf, m, X, n);
+  k_assemble<<<g, 256, 0, s>>>(Z, vsZ, Y, mj, nf, m, X, n, st, skip_k_le);
 }
 int tres_blocks(const LevelHost& L) { return (int)(nbk(L.nx, GX) * nbk((int64_t)L.ny * L.nz, GY)); }
 void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z64* b, const z64* X, double* partial,

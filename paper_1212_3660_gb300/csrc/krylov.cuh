@@ -38,8 +38,9 @@ void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
                    int32_t* sst, int32_t* mj, double* est, double* bnd, int nslot, cudaStream_t s);
 void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s);
+// x_j = Z y_j in FP64; with st given, sources with st[slot].k <= skip_k_le are skipped
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
-                     int nslot, cudaStream_t s);
+                     int nslot, cudaStream_t s, const SlotState* st = nullptr, int skip_k_le = -1);
 void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z64* b, const z64* X, double* partial,
                           const SlotState* st, double* out, int nslot, cudaStream_t s);
 

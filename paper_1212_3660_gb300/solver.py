@@ -59,7 +59,7 @@ class Solver:
 
     def solve(self, b=None, *, precision=fks.FKS_PREC_FP64, variant=fks.FKS_FGMRES, tol=None, m_max=None,
               inner_tol=0.0, inner_max_cycles=50, replay_cycles=None, replay_mj=None, device_out=False,
-              stream=None, sigma=None, tau=None, schedule=None, launch_mode=0, inner_steps=0):
+              stream=None, sigma=None, tau=None, schedule=None, launch_mode=0, inner_steps=0, assembly=0):
         p = self.p
         b = p.rhs().T.copy() if b is None else b            # n_rhs x n
         n_rhs = b.shape[0]
@@ -71,7 +71,8 @@ class Solver:
         opts, keep = fks.make_options(tol=p.tol if tol is None else tol, m_max=m_max, variant=variant,
                                       precision=precision, inner_tol=inner_tol, inner_max_cycles=inner_max_cycles,
                                       schedule=sched, replay_cycles=replay_cycles, replay_mj=replay_mj,
-                                      launch_mode=launch_mode, inner_steps=inner_steps)
+                                      launch_mode=launch_mode, inner_steps=inner_steps,
+                                      assembly=assembly)
         if device_out:
             import torch
             X = torch.empty((n_rhs, n_f, p.n), dtype=torch.complex128, device="cuda")

@@ -41,3 +41,17 @@ def replay_arrays(pr, refs):
 
 def rel_err(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def residual_floor(op, b, sigmas, X):
+    """Rounding floor of a computed relative residual ||b - (K + s M) x|| / ||b||:
+    8 u || |K| |x| + |s| |M| |x| || / ||b|| per shift (X: n x n_f). Residuals
+    below it are not resolved by floating point on either side."""
+    b = np.asarray(b).reshape(-1)
+    nb = float(np.linalg.norm(b)) or 1.0
+    aK, aM = abs(op.K), abs(op.M)
+    out = np.zeros(len(sigmas))
+    for j, s in enumerate(sigmas):
+        ax = np.abs(X[:, j])
+        out[j] = 8 * 2.0 ** -53 * np.linalg.norm(aK @ ax + abs(s) * (aM @ ax)) / nb
+    return out
