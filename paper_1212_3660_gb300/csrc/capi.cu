@@ -260,7 +260,7 @@ struct Solve {
   SlotState* st_host;  // pinned mirror
   z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
-  int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular, *flags, *counter;
+  int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular, *flags, *counter, *bcount;
   // multigrid, cycle precision
   std::vector<void*> f, z, z2, invd;
   void* cinv;      // coarse inverse in cycle precision
@@ -467,16 +467,19 @@ static void sec_inner_first(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t
   const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
   const int64_t N = S.n;
   const double cv = sizeof(cx<VT>), ns = S.nslot, n = N;
-  if (S.op->csr)
+  if (S.op->csr) {
     PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
          launch_csr_defect<VT>(S.op->cd.view<double>(N), S.st, S.taus, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart,
                                S.nslot, S.s));
-  else
+    PROF(-1, -1, 0, 0,
+         launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 1, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
+                             S.counter, S.s));
+  } else {
+    // defect and decision in one launch
     PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
-         launch_defect<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart, 1, S.nslot, S.s));
-  PROF(-1, -1, 0, 0,
-       launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 1, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
-                           S.counter, S.s));
+         launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart, S.eps,
+                                  S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot, S.s));
+  }
 }
 
 // One BiCGSTAB cycle of a CSR operator's inner solve; returns its result e.
@@ -514,13 +517,15 @@ static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t 
     PROF(FKS_K_DEFECT, 0, ns * (n * (40 + cv) + nnz * 20 + nnz * 16), ns * nnz * 10.0,
          launch_csr_defect<VT>(S.op->cd.view<double>(N), S.st, S.taus, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart,
                                S.nslot, S.s));
+    PROF(-1, -1, 0, 0,
+         launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 0, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
+                             S.counter, S.s));
   } else {
-    PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 1) + cv), ns * n * (8 * d + 14),
-         launch_defect<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart, 0, S.nslot, S.s));
+    // defect and decision in one launch (the K diagonal is precomputed on this level)
+    PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 2) + cv), ns * n * (8 * d + 10),
+         launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart, S.eps,
+                                  S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot, S.s));
   }
-  PROF(-1, -1, 0, 0,
-       launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 0, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
-                           S.counter, S.s));
 }
 
 // Inner solve of the current step, host-driven: z_k (column k-1 of Z) from v_k.
@@ -666,7 +671,8 @@ static void setup_levels(Solve& S) {
   int64_t nc = C.n;
   CK(cudaMemsetAsync(S.singular, 0, sizeof(int), S.s));
   CK(cudaMemsetAsync(S.counter, 0, sizeof(int), S.s));
-  S.lane->prof.all_launches += 2;
+  CK(cudaMemsetAsync(S.bcount, 0, sizeof(int) * S.nslot, S.s));
+  S.lane->prof.all_launches += 3;
   launch_coarse_inverse(C, S.taus, S.n_tau, S.cwork, S.cinv64, S.singular, S.s);
   if constexpr (sizeof(VT) == 8) {
     CK(cudaMemcpyAsync(S.cinv, S.cinv64, sizeof(z64) * S.n_tau * nc * nc, cudaMemcpyDeviceToDevice, S.s));
@@ -723,6 +729,7 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.singular = A.take<int32_t>(1);
   S.flags = A.take<int32_t>(ns);
   S.counter = A.take<int32_t>(1);
+  S.bcount = A.take<int32_t>(ns);
   S.dpart = A.take<double>((size_t)ns * S.ndef * 2);
   S.npart = A.take<double>((size_t)ns * norm_blocks(n));
   S.mpart = A.take<double>((size_t)ns * norm_blocks(n));
@@ -1136,6 +1143,8 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
     CK(cudaMemcpy(op->levels[0].d64[3], mass.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     launch_faces_from_cond(op->levels[0], hh, mask, cond_d, s);
     for (size_t l = 0; l + 1 < op->levels.size(); ++l) launch_coarsen(op->levels[l], op->levels[l + 1], s);
+    CK(cudaMalloc(&op->levels[0].kd64, sizeof(double) * n));
+    launch_kdiag(op->levels[0], op->levels[0].kd64, s);
     for (auto& L : op->levels)
       for (int a = 0; a < 4; ++a) {
         int64_t cnt = a < 3 ? (a == 2 && L.nz == 1 ? 1 : face_count(L, a)) : L.n;
@@ -1259,11 +1268,13 @@ void fks_op_destroy(fks_op* op) {
     for (void* q : ps)
       if (q) cudaFree(q);
   }
-  for (auto& L : op->levels)
+  for (auto& L : op->levels) {
     for (int a = 0; a < 4; ++a) {
       if (L.d64[a]) cudaFree(L.d64[a]);
       if (L.d32[a]) cudaFree(L.d32[a]);
     }
+    if (L.kd64) cudaFree(L.kd64);
+  }
   op->lane0.release();
   delete op;
 }

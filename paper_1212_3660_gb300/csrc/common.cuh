@@ -82,6 +82,7 @@ struct LevelView {
   const T* fy;
   const T* fz;  // unused when nz == 1
   const T* mm;
+  const T* kd;  // diagonal of K (sum of the cell's faces), when precomputed; else null
 };
 
 constexpr int MAX_LEVELS = 16;
@@ -96,6 +97,7 @@ struct LevelHost {
   double h[3];
   double* d64[4];     // fx, fy, fz, mm (device)
   float* d32[4];      // fp32 copies (device)
+  double* kd64;       // diagonal of K in fp64 (finest level only; else null)
 };
 
 template <typename T>
@@ -105,6 +107,7 @@ inline LevelView<T> view(const LevelHost& L) {
   T* const* a;
   if constexpr (sizeof(T) == 8) a = (T* const*)L.d64; else a = (T* const*)L.d32;
   v.fx = a[0]; v.fy = a[1]; v.fz = a[2]; v.mm = a[3];
+  if constexpr (sizeof(T) == 8) v.kd = (const T*)L.kd64; else v.kd = nullptr;
   return v;
 }
 

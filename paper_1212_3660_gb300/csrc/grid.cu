@@ -623,16 +623,78 @@ __global__ void k_correct(const SlotState* st, cx<double>* __restrict__ z, int64
   *zp = st[slot].cycles == 0 ? ev : (*zp + ev);
 }
 
+// After the per-slot decisions: with `use_cond`, the last slot to report sets
+// the graph's loop condition to "some slot still runs its inner solve"
+// (flags[slot] collects the answers, counter[0] counts reports and is reset by
+// the last one).
+__device__ __forceinline__ void report_slot(int slot, int running, int nslot, int* flags, int* counter,
+                                            cudaGraphConditionalHandle cond) {
+  flags[slot] = running;
+  __threadfence();
+  if (atomicAdd(counter, 1) == nslot - 1) {
+    __threadfence();
+    int any = 0;
+    for (int q = 0; q < nslot; ++q) any |= ((volatile int*)flags)[q];
+    *counter = 0;
+    cudaGraphSetConditional(cond, any ? 1u : 0u);
+  }
+}
+
+// The inner-solve decision of one slot from ||p||^2 = a and ||v||^2 = b
+// (Section 4: stop when ||p_k|| <= eps ||v_k||, or after max_cycles, or after the
+// replayed number of cycles). Returns whether the slot keeps cycling.
+__device__ __forceinline__ int decide_slot(SlotState& s, int slot, double a, double b, int first, double eps,
+                                           int max_cycles, const int32_t* replay_cycles, int m_max) {
+  s.pnorm2 = a;
+  if (first) {
+    s.vnorm2 = b;
+    s.cycles = 0;
+  } else {
+    s.cycles += 1;
+  }
+  bool done;
+  if (replay_cycles) done = s.cycles >= replay_cycles[(int64_t)slot * m_max + (s.k - 1)];
+  else if (first) done = false;
+  else {
+    done = a <= eps * eps * s.vnorm2 || s.cycles >= max_cycles;
+    if (!(a <= eps * eps * s.vnorm2) && s.cycles >= max_cycles) s.inner_capped = 1;
+  }
+  s.inner_done = done ? 1 : 0;
+  return done ? 0 : 1;
+}
+
+struct DecideArgs {
+  int on;                        // decide in the last block of each slot
+  double eps;
+  int max_cycles;
+  const int32_t* replay_cycles;  // null unless replaying
+  int m_max;
+  int use_cond;
+  cudaGraphConditionalHandle cond;
+  int* flags;
+  int* counter;
+  int* bcount;                   // per-slot count of finished blocks, reset by the last one
+  int nslot;
+};
+
 // r = v - (K + tau M) z in fp64; f0 = r in the cycle precision; per-block
-// partial sums of |r|^2 (and |v|^2 when `with_v`).
+// partial sums of |r|^2 (and |v|^2 when `with_v`). With D.on the last block of
+// each slot sums the partials in a fixed order and takes the inner-solve
+// decision (the work of k_inner_decide, without a launch of its own).
 template <typename T>
-__global__ void k_defect(LevelView<double> L, const SlotState* st, const z64* taus, const z64* __restrict__ v,
+__global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, const z64* __restrict__ v,
                          int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col, int zero_z,
-                         cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v) {
+                         cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v, DecideArgs D) {
   int slot = blockIdx.z;
   __shared__ double red[2][GX * GY / 32];
-  bool run = slot_running(st, slot);
-  if (!run) return;
+  __shared__ int last_blk;
+  const int tl = thread_linear();
+  if (!slot_running(st, slot)) {
+    // a slot that is not cycling still reports "not running"
+    if (D.on && D.use_cond && blockIdx.x == 0 && blockIdx.y == 0 && tl == 0)
+      report_slot(slot, 0, D.nslot, D.flags, D.counter, D.cond);
+    return;
+  }
   double r2 = 0.0, v2 = 0.0;
   Cell p;
   int c;
@@ -643,22 +705,49 @@ __global__ void k_defect(LevelView<double> L, const SlotState* st, const z64* ta
     if (!zero_z) r = vv - apply_at(L, p, c, taus[st[slot].tau], z + slot * vsz + off);
     f0[slot * vsf + c] = cvt<T>(r);
     r2 = abs2(r);
-    v2 = abs2(vv);
+    if (with_v) v2 = abs2(vv);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    r2 += __shfl_down_sync(0xffffffffu, r2, o);
-    v2 += __shfl_down_sync(0xffffffffu, v2, o);
-  }
-  int tl = thread_linear();
+  for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
+  if (with_v)
+    for (int o = 16; o > 0; o >>= 1) v2 += __shfl_down_sync(0xffffffffu, v2, o);
   int w = tl >> 5, lane = tl & 31;
   if (lane == 0) { red[0][w] = r2; red[1][w] = v2; }
   __syncthreads();
+  const int nblk = gridDim.x * gridDim.y;
   if (tl == 0) {
     double a = 0.0, b = 0.0;
     for (int q = 0; q < GX * GY / 32; ++q) { a += red[0][q]; b += red[1][q]; }
-    int nblk = gridDim.x * gridDim.y;
     partial[((int64_t)slot * nblk + block_linear()) * 2 + 0] = a;
     partial[((int64_t)slot * nblk + block_linear()) * 2 + 1] = b;
+    if (D.on) {
+      __threadfence();
+      last_blk = atomicAdd(&D.bcount[slot], 1) == nblk - 1;
+    }
+  }
+  if (!D.on) return;
+  __syncthreads();
+  if (!last_blk) return;
+  __threadfence();
+  const double* ps = partial + (int64_t)slot * nblk * 2;
+  double a = 0.0, b = 0.0;
+  for (int q = tl; q < nblk; q += GX * GY) {
+    a += __ldcg(ps + 2 * q);
+    b += __ldcg(ps + 2 * q + 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) { red[0][w] = a; red[1][w] = b; }
+  __syncthreads();
+  if (tl == 0) {
+    a = 0.0;
+    b = 0.0;
+    for (int q = 0; q < GX * GY / 32; ++q) { a += red[0][q]; b += red[1][q]; }
+    D.bcount[slot] = 0;
+    int running = decide_slot(st[slot], slot, a, b, zero_z, D.eps, D.max_cycles, D.replay_cycles, D.m_max);
+    if (D.use_cond) report_slot(slot, running, D.nslot, D.flags, D.counter, D.cond);
   }
 }
 
@@ -671,7 +760,6 @@ __global__ void k_inner_decide(SlotState* st, int nslot, const double* __restric
                                int first, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
                                int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter) {
   __shared__ double red[32];
-  __shared__ int last;
   int slot = blockIdx.x;
   SlotState& s = st[slot];
   bool act = s.active && !s.inner_done;
@@ -684,39 +772,17 @@ __global__ void k_inner_decide(SlotState* st, int nslot, const double* __restric
     }
     a = block_sum(a, red);
     b = block_sum(b, red);
-    if (threadIdx.x == 0) {
-      s.pnorm2 = a;
-      if (first) {
-        s.vnorm2 = b;
-        s.cycles = 0;
-      } else {
-        s.cycles += 1;
-      }
-      bool done;
-      if (replay_cycles) done = s.cycles >= replay_cycles[(int64_t)slot * m_max + (s.k - 1)];
-      else if (first) done = false;
-      else {
-        done = a <= eps * eps * s.vnorm2 || s.cycles >= max_cycles;
-        if (!(a <= eps * eps * s.vnorm2) && s.cycles >= max_cycles) s.inner_capped = 1;
-      }
-      s.inner_done = done ? 1 : 0;
-      running = done ? 0 : 1;
-    }
+    if (threadIdx.x == 0) running = decide_slot(s, slot, a, b, first, eps, max_cycles, replay_cycles, m_max);
   }
-  if (!use_cond) return;
-  if (threadIdx.x == 0) {
-    flags[slot] = running;
-    __threadfence();
-    last = atomicAdd(counter, 1) == nslot - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    int any = 0;
-    for (int q = 0; q < nslot; ++q) any |= ((volatile int*)flags)[q];
-    *counter = 0;
-    cudaGraphSetConditional(cond, any ? 1u : 0u);
-  }
+  if (use_cond && threadIdx.x == 0) report_slot(slot, running, nslot, flags, counter, cond);
+}
+
+// K diagonal (sum of each cell's faces), the same sum apply_at forms.
+__global__ void k_kdiag(LevelView<double> L, double* __restrict__ kd) {
+  Cell p;
+  int c;
+  if (!grid_cell(L.nx, L.ny, L.nz, &p, &c)) return;
+  kd[c] = fsum(faces_at(L, p));
 }
 
 // --------------------------------------------------------------------- launchers
@@ -861,8 +927,24 @@ template <typename T>
 void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
                    int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
                    int nslot, cudaStream_t s) {
+  DecideArgs D{};
+  k_defect<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(
+      view<double>(L), const_cast<SlotState*>(st), taus, v, vsv, z, vsz, col, zero_z, f0, vsf, partial, with_v, D);
+}
+
+template <typename T>
+void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
+                          int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial,
+                          double eps, int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
+                          cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount, int nslot,
+                          cudaStream_t s) {
+  DecideArgs D{1, eps, max_cycles, replay_cycles, m_max, use_cond, cond, flags, counter, bcount, nslot};
   k_defect<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<double>(L), st, taus, v, vsv, z, vsz, col,
-                                                                       zero_z, f0, vsf, partial, with_v);
+                                                                       zero_z, f0, vsf, partial, zero_z, D);
+}
+
+void launch_kdiag(const LevelHost& L, double* kd, cudaStream_t s) {
+  k_kdiag<<<grid2(L.nx, (int64_t)L.ny * L.nz, 1), B2, 0, s>>>(view<double>(L), kd);
 }
 
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
@@ -897,7 +979,11 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
   template void launch_correct<T>(const SlotState*, z64*, int64_t, int64_t, const cx<T>*, int64_t, int64_t, int,  \
                                   cudaStream_t);                                                                  \
   template void launch_defect<T>(const LevelHost&, const SlotState*, const z64*, const z64*, int64_t, const z64*,  \
-                                 int64_t, int64_t, int, cx<T>*, int64_t, double*, int, int, cudaStream_t);
+                                 int64_t, int64_t, int, cx<T>*, int64_t, double*, int, int, cudaStream_t);       \
+  template void launch_defect_decide<T>(const LevelHost&, SlotState*, const z64*, const z64*, int64_t, const z64*, \
+                                        int64_t, int64_t, int, cx<T>*, int64_t, double*, double, int,             \
+                                        const int32_t*, int, int, cudaGraphConditionalHandle, int*, int*, int*, int, \
+                                        cudaStream_t);
 
 INST(double)
 INST(float)

@@ -79,6 +79,17 @@ template <typename T>
 void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
                    int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
                    int nslot, cudaStream_t s);
+// The defect of launch_defect with the inner-solve decision of
+// launch_inner_decide taken by the last block of each slot (one launch);
+// bcount: nslot zero ints, left zero.
+template <typename T>
+void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
+                          int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial,
+                          double eps, int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
+                          cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount, int nslot,
+                          cudaStream_t s);
+// kd[c] = sum of the faces of cell c (the diagonal of K) in fp64
+void launch_kdiag(const LevelHost& L, double* kd, cudaStream_t s);
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
                          int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
                          cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s);

@@ -103,7 +103,7 @@ template <typename T>
 __device__ __forceinline__ cx<T> apply_at(const LevelView<T>& L, Cell p, int64_t c, cx<T> s,
                                           const cx<T>* __restrict__ x) {
   Faces<T> f = faces_at(L, p);
-  T d = fsum(f);
+  T d = L.kd ? L.kd[c] : fsum(f);  // same sum either way
   T m = L.mm[c];
   cx<T> diag = mk(fmaT(s.re, m, d), mulT(s.im, m));
   return diag * x[c] - nb_sum(L, f, p, c, x);
