@@ -584,6 +584,7 @@ def main():
                            "arnoldi_steps": int(info_arr["steps"].max()),
                            "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
                            "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned,
+                           "tile16_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[1],
                            "launch_mode": args.launch_mode},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": e2e,

@@ -229,16 +229,27 @@ void fks_server_destroy(fks_server* srv);
 /*
  * Autotuner (no counterpart in the paper): times one multigrid V-cycle of the
  * operator on this GPU for every choice of which 2D levels use the fused
- * shared-memory tile kernels (levels at most `chosen` cells), for the cycle
- * precision `precision` and shift `tau`, and keeps the fastest in the operator
- * for later solves. Solves before any tuning use 65536 (complex128 cycles) and
- * all levels (complex64 cycles). `chosen` (host, may be NULL) receives the pick.
+ * shared-memory tile kernels (levels at most `chosen` cells) and which of those
+ * run on 16 x 16 rather than 32 x 32 tiles, for the cycle precision `precision`
+ * and shift `tau`, and keeps the fastest in the operator for later solves.
+ * Solves before any tuning fuse levels up to 65536 cells (complex128 cycles) or
+ * all levels (complex64 cycles) and use 16 x 16 tiles up to 16384 cells.
+ * `chosen` (host, may be NULL) receives the fusion threshold (fks_op_tiling
+ * reads both).
  */
 fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen);
 /* Set that threshold directly (max_cells < 0: every fusable level). The fused and
  * per-sweep kernels perform the same operations in the same order, so results
  * do not depend on it. */
 fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells);
+/*
+ * Fused 2D levels with at most max_cells cells run on 16 x 16 tiles, larger
+ * ones on 32 x 32 (< 0: all on 16 x 16). The tiling does not change results.
+ * fks_op_autotune picks it together with the fusion threshold. Grid operators only.
+ */
+fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells);
+/* The current fusion threshold and 16 x 16 tile threshold of `precision`. */
+fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max);
 
 /*
  * Allocation-free variant of fks_precond_apply (the paper has no counterpart).

@@ -200,6 +200,8 @@ struct fks_op {
   // 2D levels with at most this many cells use the fused tile kernels
   // ([0] complex128 cycles, [1] complex64 cycles); set by fks_op_autotune
   int64_t fuse_max[2] = {65536, INT64_MAX};
+  // fused 2D levels with at most this many cells use 16 x 16 tiles (else 32 x 32)
+  int64_t tile16_max[2] = {16384, 16384};
 };
 
 namespace fks {
@@ -273,6 +275,10 @@ struct Solve {
   BcgScal* bsc = nullptr;
   double* bpart = nullptr;
   int ndef = 0;            // blocks of the defect kernel (partials per slot)
+  z64* diag64 = nullptr;           // finest level: K_cc + tau M_cc per distinct tau (fp64)
+  unsigned char* tblob = nullptr;  // tail coefficients per tau in the shared-memory layout
+  size_t tblob_bytes = 0;
+  int tcoef0 = 0;
   bool capturing = false;  // enqueueing into a graph: no event timing
   // server batches hold this lock for their host-side CUDA calls and release it
   // only while they wait for their step-loop graph to finish
@@ -312,6 +318,8 @@ static int tail_level(const std::vector<LevelHost>& Ls) {
   return (int)Ls.size() - 1;
 }
 
+constexpr size_t TAIL_SMEM_LIMIT = 220 * 1024;
+
 // Shared memory of the tail kernel: f and z of every tail level, then (when it
 // fits) each level's coefficients (faces, storage, inverse diagonals for the
 // current tau). Returns the bytes; `coef_byte` receives each level's offset.
@@ -330,10 +338,8 @@ static size_t tail_layout(const std::vector<LevelHost>& Ls, int lt, bool staged,
     if (coef_byte) (*coef_byte)[l] = (int)bytes;
     bytes += realn * sizeof(VT) + (size_t)L.n * sizeof(cx<VT>);
   }
-  return bytes;
+  return (bytes + 15) & ~(size_t)15;
 }
-
-constexpr size_t TAIL_SMEM_LIMIT = 220 * 1024;
 
 template <typename VT>
 static bool tail_staged(const std::vector<LevelHost>& Ls, int lt) {
@@ -343,6 +349,21 @@ static bool tail_staged(const std::vector<LevelHost>& Ls, int lt) {
 template <typename VT>
 static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
   return tail_layout<VT>(Ls, lt, tail_staged<VT>(Ls, lt), nullptr);
+}
+
+// Bytes per tau of the tail's staged coefficients and their shared-memory
+// offset (0 bytes when the tail reads its coefficients from global memory).
+template <typename VT>
+static size_t tail_blob_bytes(const std::vector<LevelHost>& Ls, int* coef0) {
+  const int lt = tail_level<VT>(Ls);
+  std::vector<int> cb;
+  if (!tail_staged<VT>(Ls, lt)) {
+    *coef0 = 0;
+    return 0;
+  }
+  size_t total = tail_layout<VT>(Ls, lt, true, &cb);
+  *coef0 = cb[lt];
+  return total - (size_t)cb[lt];
 }
 
 // One V-cycle on f[0]; returns the buffer holding the level-0 correction.
@@ -362,12 +383,14 @@ static cx<VT>* vcycle(Solve& S) {
   };
   auto smooth_f = [&](const LevelHost& L, int zs) { return zs ? ns * L.n * 3.0 : ns * L.n * 0.5 * (8 * d + 6); };
   const int64_t fmax = S.op->fuse_max[sizeof(VT) == 8 ? 0 : 1];
+  const int64_t t16 = S.op->tile16_max[sizeof(VT) == 8 ? 0 : 1];
   for (int l = 0; l < lt; ++l) {
     const LevelHost& L = Ls[l];
     if (fused_level_ok(L) && L.n <= fmax) {
       PROF(FKS_K_PRE2D, l, ns * (L.n * (3 * cv + (d + 1) * rv) + cv * Ls[l + 1].n),
            ns * L.n * (2 * (8 * d + 6) + 8 * d + 10),
-           launch_pre2d<VT>(L, Ls[l + 1], S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot, s));
+           launch_pre2d<VT>(L, Ls[l + 1], S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
+                            L.n <= t16, s));
       continue;
     }
     for (int r = 0; r < NU1; ++r) {
@@ -409,6 +432,9 @@ static cx<VT>* vcycle(Solve& S) {
     P.z_out = Zl(lt);
     P.vs = Ls[lt].n;
     P.taus = S.taus;
+    P.blob = S.tblob;
+    P.blob_bytes = (int)S.tblob_bytes;
+    P.coef0 = S.tcoef0;
     tb += cv * C.n * C.n;
     tf += 8.0 * C.n * C.n;
     PROF(FKS_K_TAIL, lt, ns * tb, ns * tf, launch_tail<VT>(P, tail_smem<VT>(Ls, lt), S.st, S.nslot, s));
@@ -421,7 +447,7 @@ static cx<VT>* vcycle(Solve& S) {
       PROF(FKS_K_POST2D, l, ns * (L.n * (4 * cv + d * rv) + cv * Ls[l + 1].n),
            ns * L.n * (18 + 2 * (8 * d + 6)),
            launch_post2d<VT>(L, Ls[l + 1], S.op->mask, S.st, I(l), F(l), Zl(l), out, L.n, zfin, Ls[l + 1].n,
-                             S.nslot, s));
+                             S.nslot, L.n <= t16, s));
       zfin = out;
       continue;
     }
@@ -477,7 +503,7 @@ static void sec_inner_first(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t
   } else {
     // defect and decision in one launch
     PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
-         launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart, S.eps,
+         launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, S.diag64, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart, S.eps,
                                   S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot, S.s));
   }
 }
@@ -523,7 +549,7 @@ static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t 
   } else {
     // defect and decision in one launch (the K diagonal is precomputed on this level)
     PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 2) + cv), ns * n * (8 * d + 10),
-         launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart, S.eps,
+         launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, S.diag64, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart, S.eps,
                                   S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot, S.s));
   }
 }
@@ -667,6 +693,29 @@ static void setup_levels(Solve& S) {
   }
   for (size_t l = 0; l < Ls.size(); ++l)
     PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
+  PROF(-1, -1, 0, 0, launch_diag64(Ls[0], S.taus, S.n_tau, S.diag64, S.s));
+  if (S.tblob) {
+    // the tail's coefficients per tau, laid out as in its shared memory
+    const int lt = tail_level<VT>(Ls);
+    std::vector<int> cb;
+    tail_layout<VT>(Ls, lt, true, &cb);
+    for (int q = 0; q < S.n_tau; ++q)
+      for (size_t l = lt; l < Ls.size(); ++l) {
+        const LevelHost& L = Ls[l];
+        unsigned char* dst = S.tblob + (size_t)q * S.tblob_bytes + (cb[l] - S.tcoef0);
+        VT* const* src = sizeof(VT) == 8 ? (VT* const*)L.d64 : (VT* const*)L.d32;
+        size_t nfx = face_count(L, 0), nfy = face_count(L, 1), nfz = L.nz > 1 ? face_count(L, 2) : 0;
+        size_t off = 0;
+        const size_t cnt[4] = {nfx, nfy, nfz, (size_t)L.n};
+        for (int a = 0; a < 4; ++a) {
+          if (cnt[a]) CK(cudaMemcpyAsync(dst + off, src[a], cnt[a] * sizeof(VT), cudaMemcpyDeviceToDevice, S.s));
+          off += cnt[a] * sizeof(VT);
+        }
+        size_t realn = (nfx + nfy + nfz + L.n + 3) & ~(size_t)3;
+        CK(cudaMemcpyAsync(dst + realn * sizeof(VT), (const cx<VT>*)S.invd[l] + (size_t)q * L.n,
+                           sizeof(cx<VT>) * L.n, cudaMemcpyDeviceToDevice, S.s));
+      }
+  }
   const LevelHost& C = Ls.back();
   int64_t nc = C.n;
   CK(cudaMemsetAsync(S.singular, 0, sizeof(int), S.s));
@@ -721,6 +770,9 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
       S.z2[l] = A.take<cx<VT>>((size_t)ns * Ls[l].n);
       S.invd[l] = A.take<cx<VT>>((size_t)S.n_tau * Ls[l].n);
     }
+    S.diag64 = A.take<z64>((size_t)S.n_tau * n);
+    S.tblob_bytes = tail_blob_bytes<VT>(Ls, &S.tcoef0);
+    S.tblob = S.tblob_bytes ? A.take<unsigned char>((size_t)S.n_tau * S.tblob_bytes) : nullptr;
     int64_t nc = Ls.back().n;
     S.cwork = A.take<z64>((size_t)S.n_tau * nc * nc);
     S.cinv64 = A.take<z64>((size_t)S.n_tau * nc * nc);
@@ -828,7 +880,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
       std::vector<double> key = {(double)(uintptr_t)lane->ws.base, (double)n_rhs, (double)n_f, (double)n_tau, (double)m,
                                  (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
-                                 (double)op->fuse_max[1], (double)S.inner_steps};
+                                 (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
+                                 (double)op->tile16_max[1]};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1340,6 +1393,23 @@ fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells) {
   return FKS_OK;
 }
 
+fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells) {
+  if (!op) { set_error("fks_op_set_tiles: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_set_tiles: grid operators only"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_tiles: bad precision"); return FKS_ERR_ARG; }
+  op->tile16_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
+  return FKS_OK;
+}
+
+fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max) {
+  if (!op) { set_error("fks_op_tiling: NULL operator"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_tiling: bad precision"); return FKS_ERR_ARG; }
+  int pi = precision == FKS_PREC_FP64 ? 0 : 1;
+  if (fuse_max) *fuse_max = op->fuse_max[pi];
+  if (tile16_max) *tile16_max = op->tile16_max[pi];
+  return FKS_OK;
+}
+
 fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen) {
   if (!op) { set_error("fks_op_autotune: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_autotune: grid operators only"); return FKS_ERR_ARG; }
@@ -1347,7 +1417,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
   if (!finite_c(tau)) { set_error("fks_op_autotune: tau has NaN/Inf"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
-  int64_t saved = op->fuse_max[pi];
+  int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi];
   try {
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
@@ -1391,9 +1461,14 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       double best = 1e30;
-      int64_t pick = saved;
-      for (int64_t c : cand) {
+      int64_t pick = saved, pick16 = saved16;
+      std::vector<std::pair<int64_t, int64_t>> pairs;
+      for (int64_t c : cand)
+        for (int64_t t : cand)
+          if (t <= c) pairs.push_back({c, t});
+      for (auto [c, t16] : pairs) {
         op->fuse_max[pi] = c;
+        op->tile16_max[pi] = t16;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
         S.s = cs;
@@ -1419,17 +1494,20 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
         if (ms < best) {
           best = ms;
           pick = c;
+          pick16 = t16;
         }
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       cudaStreamDestroy(cs);
       op->fuse_max[pi] = pick;
+      op->tile16_max[pi] = pick16;
     };
     if (precision == FKS_PREC_FP64) run(double{});
     else run(float{});
   } catch (CudaError& e) {
     op->fuse_max[pi] = saved;
+    op->tile16_max[pi] = saved16;
     set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
   }

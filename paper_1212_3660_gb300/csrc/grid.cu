@@ -236,13 +236,15 @@ __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, i
 //         coarse f = sum over children of (f - A z)
 //   post: z += P z_coarse; four half sweeps (black, red, black, red); write z
 constexpr int FH = 4;
+constexpr int DEFECT_ROWS = 2;  // rows of cells per thread in the defect kernel
 
 // sum over existing neighbours of t_face * z_nb for a 2D cell held at r in a
 // shared tile of row length RX (same order as nb_sum)
 template <typename T>
-__device__ __forceinline__ cx<T> nb_sum_tile(const LevelView<T>& L, Cell p, int r, int RX, const cx<T>* sZ) {
+__device__ __forceinline__ cx<T> nb_sum_tile(const LevelView<T>& L, Cell p, int r, int RX, const cx<T>* sZ,
+                                             cx<T> s0 = cx<T>{T(0), T(0)}) {
   Faces<T> f = faces_at(L, p);
-  cx<T> s = mk(T(0), T(0));
+  cx<T> s = s0;
   if (p.i > 0) s = axpy(f.xl, sZ[r - 1], s);
   if (p.i < L.nx - 1) s = axpy(f.xh, sZ[r + 1], s);
   if (p.j > 0) s = axpy(f.yl, sZ[r - RX], s);
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(256) k_pre2d(LevelView<T> L, const SlotState* 
       int r = ry * RX + rx0;
       int c = gy * L.nx + gx;
       cx<T> rhs = sF[r];
-      if (hs > 0) rhs = rhs + nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
+      if (hs > 0) rhs = nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ, rhs);
       sZ[r] = ID[c] * rhs;
     }
     __syncthreads();
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, c
       if (rx0 >= RX - sh || gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) continue;
       int r = ry * RX + rx0;
       int c = gy * L.nx + gx;
-      cx<T> rhs = sF[r] + nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ);
+      cx<T> rhs = nb_sum_tile(L, Cell{gx, gy, 0}, r, RX, sZ, sF[r]);
       sZ[r] = ID[c] * rhs;
     }
     __syncthreads();
@@ -420,8 +422,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
     SV[tid] = v;
     SI[tid] = id;
   }
+  if (P.staged && P.blob) {
+    // one flat copy of this tau's coefficients of all tail levels
+    const uint4* src = (const uint4*)(P.blob + (size_t)tau * P.blob_bytes);
+    uint4* dst = (uint4*)(tail_smem + P.coef0);
+    for (int q = tid; q < P.blob_bytes / 16; q += nt) dst[q] = src[q];
+  }
   __syncthreads();
-  if (P.staged) {
+  if (P.staged && !P.blob) {
     for (int l = 0; l < P.nlev; ++l) {
       const TailLevel<T>& A = P.lev[l];
       const LevelView<T>& v = SV[l];
@@ -682,9 +690,10 @@ struct DecideArgs {
 // each slot sums the partials in a fixed order and takes the inner-solve
 // decision (the work of k_inner_decide, without a launch of its own).
 template <typename T>
-__global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, const z64* __restrict__ v,
-                         int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col, int zero_z,
-                         cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v, DecideArgs D) {
+__global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, const z64* __restrict__ diag64,
+                         const z64* __restrict__ v, int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col,
+                         int zero_z, cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v,
+                         DecideArgs D) {
   int slot = blockIdx.z;
   __shared__ double red[2][GX * GY / 32];
   __shared__ int last_blk;
@@ -696,16 +705,29 @@ __global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, co
     return;
   }
   double r2 = 0.0, v2 = 0.0;
-  Cell p;
-  int c;
-  if (grid_cell(L.nx, L.ny, L.nz, &p, &c)) {
-    int64_t off = (int64_t)(st[slot].k - 1) * col;
-    z64 vv = v[slot * vsv + off + c];
+  const int i = blockIdx.x * GX + threadIdx.x;
+  const int rows = L.ny * L.nz;
+  const int64_t off = (int64_t)(st[slot].k - 1) * col;
+  const int tau = st[slot].tau;
+  const z64* dg = diag64 ? diag64 + (int64_t)tau * L.n : nullptr;
+  const z64* zz = z + slot * vsz + off;
+#pragma unroll
+  for (int q = 0; q < DEFECT_ROWS; ++q) {
+    const int row = (blockIdx.y * DEFECT_ROWS + q) * GY + threadIdx.y;
+    if (i >= L.nx || row >= rows) continue;
+    const int k = row / L.ny;
+    const Cell p{i, row - k * L.ny, k};
+    const int c = row * L.nx + i;
+    const z64 vv = v[slot * vsv + off + c];
     z64 r = vv;
-    if (!zero_z) r = vv - apply_at(L, p, c, taus[st[slot].tau], z + slot * vsz + off);
+    if (!zero_z) r = dg ? defect_at(L, p, c, dg[c], vv, zz) : vv - apply_at(L, p, c, taus[tau], zz);
     f0[slot * vsf + c] = cvt<T>(r);
-    r2 = abs2(r);
-    if (with_v) v2 = abs2(vv);
+    r2 = fmaT(r.re, r.re, r2);
+    r2 = fmaT(r.im, r.im, r2);
+    if (with_v) {
+      v2 = fmaT(vv.re, vv.re, v2);
+      v2 = fmaT(vv.im, vv.im, v2);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
   if (with_v)
@@ -775,6 +797,16 @@ __global__ void k_inner_decide(SlotState* st, int nslot, const double* __restric
     if (threadIdx.x == 0) running = decide_slot(s, slot, a, b, first, eps, max_cycles, replay_cycles, m_max);
   }
   if (use_cond && threadIdx.x == 0) report_slot(slot, running, nslot, flags, counter, cond);
+}
+
+// K_cc + tau_q M_cc for every distinct tau in fp64 (the diagonal apply_at forms).
+__global__ void k_diag64(LevelView<double> L, const z64* __restrict__ taus, int ntau, z64* __restrict__ out) {
+  Cell p;
+  int c;
+  if (!grid_cell(L.nx, L.ny, L.nz, &p, &c)) return;
+  const double d = L.kd ? L.kd[c] : fsum(faces_at(L, p));
+  const double m = L.mm[c];
+  for (int q = 0; q < ntau; ++q) out[(int64_t)q * L.n + c] = mk(fmaT(taus[q].re, m, d), mulT(taus[q].im, m));
 }
 
 // K diagonal (sum of each cell's faces), the same sum apply_at forms.
@@ -851,9 +883,8 @@ void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, c
                                                                             C.nz, mask, st, zc, vsc, z, vs);
 }
 
-// Tiles of 32x32 cells on large levels, 16x16 on levels of at most 128 x 128
-// (more blocks on small grids; the 4-cell halo is recomputed either way).
-static bool small_tiles(const LevelHost& L) { return L.nx <= 128 && L.ny <= 128; }
+// Tiles of 32x32 or 16x16 cells (16x16: more blocks on small grids, a larger
+// share of recomputed halo); the caller picks per level.
 template <typename T, int TX, int TY>
 static size_t fused_smem() {
   return 2 * (size_t)(TX + 2 * FH) * (TY + 2 * FH) * sizeof(cx<T>);
@@ -869,8 +900,8 @@ void fused_prepare() {
 
 template <typename T>
 void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
-                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, cudaStream_t s) {
-  if (small_tiles(F)) {
+                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, bool small, cudaStream_t s) {
+  if (small) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
     k_pre2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
   } else {
@@ -883,8 +914,8 @@ void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, c
 template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
-                   cudaStream_t s) {
-  if (small_tiles(F)) {
+                   bool small, cudaStream_t s) {
+  if (small) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
     k_post2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
   } else {
@@ -918,8 +949,12 @@ void launch_correct(const SlotState* st, z64* z, int64_t zs, int64_t zcol, const
   k_correct<T><<<g, 256, 0, s>>>(st, z, zs, zcol, e, es, n);
 }
 
+static dim3 defect_grid(const LevelHost& L, int nslot) {
+  return dim3(nb(L.nx, GX), nb((int64_t)L.ny * L.nz, GY * DEFECT_ROWS), nslot);
+}
+
 int defect_blocks(const LevelHost& L) {
-  dim3 g = grid2(L.nx, (int64_t)L.ny * L.nz, 1);
+  dim3 g = defect_grid(L, 1);
   return (int)(g.x * g.y);
 }
 
@@ -928,19 +963,23 @@ void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, con
                    int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
                    int nslot, cudaStream_t s) {
   DecideArgs D{};
-  k_defect<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(
-      view<double>(L), const_cast<SlotState*>(st), taus, v, vsv, z, vsz, col, zero_z, f0, vsf, partial, with_v, D);
+  k_defect<T><<<defect_grid(L, nslot), B2, 0, s>>>(view<double>(L), const_cast<SlotState*>(st), taus, nullptr, v, vsv,
+                                                   z, vsz, col, zero_z, f0, vsf, partial, with_v, D);
 }
 
 template <typename T>
-void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
-                          int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial,
-                          double eps, int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
-                          cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount, int nslot,
-                          cudaStream_t s) {
+void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, const z64* diag64, const z64* v,
+                          int64_t vsv, const z64* z, int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf,
+                          double* partial, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
+                          int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount,
+                          int nslot, cudaStream_t s) {
   DecideArgs D{1, eps, max_cycles, replay_cycles, m_max, use_cond, cond, flags, counter, bcount, nslot};
-  k_defect<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<double>(L), st, taus, v, vsv, z, vsz, col,
-                                                                       zero_z, f0, vsf, partial, zero_z, D);
+  k_defect<T><<<defect_grid(L, nslot), B2, 0, s>>>(view<double>(L), st, taus, diag64, v, vsv, z, vsz, col, zero_z,
+                                                   f0, vsf, partial, zero_z, D);
+}
+
+void launch_diag64(const LevelHost& L, const z64* taus, int ntau, z64* out, cudaStream_t s) {
+  k_diag64<<<grid2(L.nx, (int64_t)L.ny * L.nz, 1), B2, 0, s>>>(view<double>(L), taus, ntau, out);
 }
 
 void launch_kdiag(const LevelHost& L, double* kd, cudaStream_t s) {
@@ -957,9 +996,9 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
 #define INST(T)                                                                                                  \
   template void fused_prepare<T>();                                                                               \
   template void launch_pre2d<T>(const LevelHost&, const LevelHost&, const SlotState*, const cx<T>*, const z64*,    \
-                                const cx<T>*, cx<T>*, int64_t, cx<T>*, int64_t, int, cudaStream_t);               \
+                                const cx<T>*, cx<T>*, int64_t, cx<T>*, int64_t, int, bool, cudaStream_t);         \
   template void launch_post2d<T>(const LevelHost&, const LevelHost&, uint32_t, const SlotState*, const cx<T>*,     \
-                                 const cx<T>*, const cx<T>*, cx<T>*, int64_t, const cx<T>*, int64_t, int,         \
+                                 const cx<T>*, const cx<T>*, cx<T>*, int64_t, const cx<T>*, int64_t, int, bool,   \
                                  cudaStream_t);                                                                   \
   template void tail_prepare<T>(size_t);                                                                          \
   template void launch_tail<T>(const TailParams<T>&, size_t, const SlotState*, int, cudaStream_t);                \
@@ -980,8 +1019,8 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
                                   cudaStream_t);                                                                  \
   template void launch_defect<T>(const LevelHost&, const SlotState*, const z64*, const z64*, int64_t, const z64*,  \
                                  int64_t, int64_t, int, cx<T>*, int64_t, double*, int, int, cudaStream_t);       \
-  template void launch_defect_decide<T>(const LevelHost&, SlotState*, const z64*, const z64*, int64_t, const z64*, \
-                                        int64_t, int64_t, int, cx<T>*, int64_t, double*, double, int,             \
+  template void launch_defect_decide<T>(const LevelHost&, SlotState*, const z64*, const z64*, const z64*, int64_t, \
+                                        const z64*, int64_t, int64_t, int, cx<T>*, int64_t, double*, double, int, \
                                         const int32_t*, int, int, cudaGraphConditionalHandle, int*, int*, int*, int, \
                                         cudaStream_t);
 

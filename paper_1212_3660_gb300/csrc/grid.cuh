@@ -29,6 +29,9 @@ struct TailParams {
   int64_t vs;
   const z64* taus;
   int staged;              // coefficients copied to shared memory at kernel start
+  const unsigned char* blob;  // staged coefficients per tau, already in the shared-memory layout (or null)
+  int blob_bytes;          // bytes per tau (multiple of 16)
+  int coef0;               // shared-memory byte offset of the coefficient region
 };
 
 template <typename T>
@@ -36,13 +39,14 @@ void tail_prepare(size_t smem_bytes);
 bool fused_level_ok(const LevelHost& L);
 template <typename T>
 void fused_prepare();
+// small: 16 x 16 tiles (else 32 x 32); the results do not depend on the tiling
 template <typename T>
 void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
-                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, cudaStream_t s);
+                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, bool small, cudaStream_t s);
 template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
-                   cudaStream_t s);
+                   bool small, cudaStream_t s);
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);
 
@@ -82,12 +86,14 @@ void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, con
 // The defect of launch_defect with the inner-solve decision of
 // launch_inner_decide taken by the last block of each slot (one launch);
 // bcount: nslot zero ints, left zero.
+// diag64: [n_tau][n] K_cc + tau M_cc of this level (launch_diag64), or null.
 template <typename T>
-void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, const z64* v, int64_t vsv, const z64* z,
-                          int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial,
-                          double eps, int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
-                          cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount, int nslot,
-                          cudaStream_t s);
+void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, const z64* diag64, const z64* v,
+                          int64_t vsv, const z64* z, int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf,
+                          double* partial, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
+                          int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount,
+                          int nslot, cudaStream_t s);
+void launch_diag64(const LevelHost& L, const z64* taus, int ntau, z64* out, cudaStream_t s);
 // kd[c] = sum of the faces of cell c (the diagonal of K) in fp64
 void launch_kdiag(const LevelHost& L, double* kd, cudaStream_t s);
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,

@@ -82,11 +82,11 @@ __device__ __forceinline__ T fsum(const Faces<T>& f) {
   return ((f.xl + f.xh) + (f.yl + f.yh)) + (f.zl + f.zh);
 }
 
-// sum over existing neighbours of t_face * x_nb
+// s0 + sum over existing neighbours of t_face * x_nb (accumulated in this order)
 template <typename T>
 __device__ __forceinline__ cx<T> nb_sum(const LevelView<T>& L, const Faces<T>& f, Cell p, int64_t c,
-                                        const cx<T>* __restrict__ x) {
-  cx<T> s = mk(T(0), T(0));
+                                        const cx<T>* __restrict__ x, cx<T> s0 = cx<T>{T(0), T(0)}) {
+  cx<T> s = s0;
   int64_t sxy = (int64_t)L.nx * L.ny;
   if (p.i > 0) s = axpy(f.xl, x[c - 1], s);
   if (p.i < L.nx - 1) s = axpy(f.xh, x[c + 1], s);
@@ -109,6 +109,20 @@ __device__ __forceinline__ cx<T> apply_at(const LevelView<T>& L, Cell p, int64_t
   return diag * x[c] - nb_sum(L, f, p, c, x);
 }
 
+// v_c - ((K + tau M) x)_c with diag = K_cc + tau M_cc given: the neighbour
+// terms accumulate onto v, then diag * x_c is subtracted with fused
+// multiply-adds (fewer FP64 operations than v - apply_at).
+template <typename T>
+__device__ __forceinline__ cx<T> defect_at(const LevelView<T>& L, Cell p, int64_t c, cx<T> diag, cx<T> v,
+                                           const cx<T>* __restrict__ x) {
+  Faces<T> f = faces_at(L, p);
+  cx<T> acc = nb_sum(L, f, p, c, x, v);
+  const cx<T> xc = x[c];
+  acc.re = fmaT(-diag.re, xc.re, fmaT(diag.im, xc.im, acc.re));
+  acc.im = fmaT(-diag.re, xc.im, fmaT(-diag.im, xc.re, acc.im));
+  return acc;
+}
+
 // Red-black Gauss-Seidel update of cell c: (f_c + sum_nb t z_nb) / (K_cc + tau M_cc),
 // the neighbours taken as zero when `zero_start`.
 template <typename T>
@@ -117,7 +131,7 @@ __device__ __forceinline__ cx<T> gs_value(const LevelView<T>& L, Cell p, int64_t
   cx<T> rhs = f[c];
   if (!zero_start) {
     Faces<T> fc = faces_at(L, p);
-    rhs = rhs + nb_sum(L, fc, p, c, z);
+    rhs = nb_sum(L, fc, p, c, z, rhs);  // f + sum t z_nb, accumulated from f
   }
   return id * rhs;
 }

@@ -189,4 +189,10 @@ def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
     c = s.solve(precision=precision, inner_tol=1e-10)
     assert np.array_equal(a.X, b.X) and np.array_equal(a.X, c.X), picked
     assert np.array_equal(a.inner_cycles, b.inner_cycles)
+    # the tile shape of the fused kernels does not change any cell's update
+    fks.fks_op_set_fusion(s.op, precision, -1)
+    for t16 in (0, -1):
+        fks.fks_op_set_tiles(s.op, precision, t16)
+        d = s.solve(precision=precision, inner_tol=1e-10)
+        assert np.array_equal(a.X, d.X), t16
     s.close()
