@@ -366,9 +366,11 @@ static size_t tail_blob_bytes(const std::vector<LevelHost>& Ls, int* coef0) {
   return total - (size_t)cb[lt];
 }
 
-// One V-cycle on f[0]; returns the buffer holding the level-0 correction.
+// One V-cycle on f[0]; returns the buffer holding the level-0 correction, or
+// null when the finest level's post-smoothing kernel already added it to
+// column k - 1 of Zk (given with its strides; Zk null: never).
 template <typename VT>
-static cx<VT>* vcycle(Solve& S) {
+static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0) {
   auto& Ls = S.op->levels;
   int nl = (int)Ls.size();
   int lt = tail_level<VT>(Ls);
@@ -444,11 +446,12 @@ static cx<VT>* vcycle(Solve& S) {
     const LevelHost& L = Ls[l];
     if (fused_level_ok(L) && L.n <= fmax) {
       cx<VT>* out = (cx<VT>*)S.z2[l];
+      const bool add_to_zk = l == 0 && Zk;
       PROF(FKS_K_POST2D, l, ns * (L.n * (4 * cv + d * rv) + cv * Ls[l + 1].n),
            ns * L.n * (18 + 2 * (8 * d + 6)),
            launch_post2d<VT>(L, Ls[l + 1], S.op->mask, S.st, I(l), F(l), Zl(l), out, L.n, zfin, Ls[l + 1].n,
-                             S.nslot, L.n <= t16, s));
-      zfin = out;
+                             S.nslot, L.n <= t16, s, add_to_zk ? Zk : nullptr, vsZk, zcol));
+      zfin = add_to_zk ? nullptr : out;
       continue;
     }
     PROF(FKS_K_PROLONG, l, ns * (2 * cv * L.n + cv * Ls[l + 1].n), ns * L.n * (4.0 * (1 << S.op->dim) + 2),
@@ -535,9 +538,10 @@ static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t 
   const int32_t* rc = S.replay ? S.rep_cyc : nullptr;
   const int64_t N = S.n;
   const double cv = sizeof(cx<VT>), d = S.op->dim, ns = S.nslot, n = N;
-  cx<VT>* e0 = S.op->csr ? bicgstab_cycle<VT>(S) : vcycle<VT>(S);
-  PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
-       launch_correct<VT>(S.st, Z, vsZ, N, e0, N, N, S.nslot, S.s));
+  cx<VT>* e0 = S.op->csr ? bicgstab_cycle<VT>(S) : vcycle<VT>(S, Z, vsZ, N);
+  if (e0)  // else the finest post-smoothing kernel already added the correction
+    PROF(FKS_K_CORRECT, 0, ns * n * (cv + 32), ns * n * 2.0,
+         launch_correct<VT>(S.st, Z, vsZ, N, e0, N, N, S.nslot, S.s));
   if (S.op->csr) {
     const double nnz = S.op->cd.nnz;
     PROF(FKS_K_DEFECT, 0, ns * (n * (40 + cv) + nnz * 20 + nnz * 16), ns * nnz * 10.0,

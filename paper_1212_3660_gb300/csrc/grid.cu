@@ -324,12 +324,15 @@ __global__ void __launch_bounds__(256) k_pre2d(LevelView<T> L, const SlotState* 
 }
 
 // post reads the pre-smoothed z and writes zout (a different buffer): tiles
-// read their neighbours' cells as halo, which those tiles overwrite.
+// read their neighbours' cells as halo, which those tiles overwrite. With Zk
+// given (finest level), the result e is instead added to the outer iterate,
+// z_k = e on the first cycle and z_k + e after (the update of k_correct).
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, const SlotState* st,
                                                 const cx<T>* __restrict__ invd, const cx<T>* __restrict__ f,
                                                 const cx<T>* __restrict__ z, cx<T>* __restrict__ zout, int64_t vs,
-                                                const cx<T>* __restrict__ zc, int64_t vsc) {
+                                                const cx<T>* __restrict__ zc, int64_t vsc, z64* __restrict__ Zk,
+                                                int64_t vsZk, int64_t zcol) {
   constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
   extern __shared__ __align__(16) unsigned char post_smem[];
   cx<T>* sF = (cx<T>*)post_smem;
@@ -378,6 +381,20 @@ __global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, c
       sZ[r] = ID[c] * rhs;
     }
     __syncthreads();
+  }
+  if (Zk) {
+    z64* zk = Zk + slot * vsZk + (int64_t)(st[slot].k - 1) * zcol;
+    const bool first = st[slot].cycles == 0;
+    for (int q = tid; q < TX * TY; q += nt) {
+      int yy = q / TX, xx = q - yy * TX;
+      int gx = x0 + FH + xx, gy = y0 + FH + yy;
+      if (gx < L.nx && gy < L.ny) {
+        const int c = gy * L.nx + gx;
+        const z64 ev = cvt<double>(sZ[(yy + FH) * RX + xx + FH]);
+        zk[c] = first ? ev : (zk[c] + ev);
+      }
+    }
+    return;
   }
   for (int q = tid; q < TX * TY; q += nt) {
     int yy = q / TX, xx = q - yy * TX;
@@ -914,13 +931,15 @@ void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, c
 template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
-                   bool small, cudaStream_t s) {
+                   bool small, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
   if (small) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
-    k_post2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
+    k_post2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
+                                                                 Zk, vsZk, zcol);
   } else {
     dim3 g(nb(F.nx, 32), nb(F.ny, 32), nslot);
-    k_post2d<T, 32, 32><<<g, 256, fused_smem<T, 32, 32>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc);
+    k_post2d<T, 32, 32><<<g, 256, fused_smem<T, 32, 32>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
+                                                                 Zk, vsZk, zcol);
   }
   (void)C;
 }
@@ -999,7 +1018,7 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
                                 const cx<T>*, cx<T>*, int64_t, cx<T>*, int64_t, int, bool, cudaStream_t);         \
   template void launch_post2d<T>(const LevelHost&, const LevelHost&, uint32_t, const SlotState*, const cx<T>*,     \
                                  const cx<T>*, const cx<T>*, cx<T>*, int64_t, const cx<T>*, int64_t, int, bool,   \
-                                 cudaStream_t);                                                                   \
+                                 cudaStream_t, z64*, int64_t, int64_t);                                           \
   template void tail_prepare<T>(size_t);                                                                          \
   template void launch_tail<T>(const TailParams<T>&, size_t, const SlotState*, int, cudaStream_t);                \
   template void launch_invd<T>(const LevelHost&, const z64*, int, cx<T>*, cudaStream_t);                          \

@@ -43,10 +43,12 @@ void fused_prepare();
 template <typename T>
 void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
                   const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, bool small, cudaStream_t s);
+// Zk (optional): instead of writing zout, add the result to column k - 1 of the
+// outer iterates Zk (slot stride vsZk, column stride zcol), as launch_correct does.
 template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
-                   bool small, cudaStream_t s);
+                   bool small, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0);
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);
 

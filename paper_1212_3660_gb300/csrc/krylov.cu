@@ -146,11 +146,16 @@ __global__ void __launch_bounds__(MD_THREADS) k_mdot(const SlotState* st, const 
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = c0; c < c1; ++c) {
     const z64* col = Vs + (int64_t)c * n;
+    // acc += conj(v) w with four fused multiply-adds per row
     z64 acc = mk(0.0, 0.0);
 #pragma unroll
     for (int r = 0; r < MD_ROWS; ++r) {
       int64_t row = row0 + (int64_t)r * MD_THREADS;
-      if (row < n) acc = acc + cdot(col[row], wr[r]);
+      if (row < n) {
+        const z64 a = col[row], b = wr[r];
+        acc.re = fmaT(a.re, b.re, fmaT(a.im, b.im, acc.re));
+        acc.im = fmaT(a.re, b.im, fmaT(-a.im, b.re, acc.im));
+      }
     }
     acc.re = warp_sum(acc.re);
     acc.im = warp_sum(acc.im);
@@ -194,7 +199,12 @@ __global__ void k_maxpy(const SlotState* st, const z64* __restrict__ V, int64_t 
   if (row >= n) return;
   const z64* Vs = V + slot * vsV;
   z64 acc = w[slot * n + row];
-  for (int i = 0; i < k; ++i) acc = acc - Vs[(int64_t)i * n + row] * hs[i];
+  // acc -= v h with four fused multiply-adds per column
+  for (int i = 0; i < k; ++i) {
+    const z64 v = Vs[(int64_t)i * n + row], h = hs[i];
+    acc.re = fmaT(-v.re, h.re, fmaT(v.im, h.im, acc.re));
+    acc.im = fmaT(-v.re, h.im, fmaT(-v.im, h.re, acc.im));
+  }
   w[slot * n + row] = acc;
 }
 
