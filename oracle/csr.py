@@ -108,6 +108,12 @@ class BiCGStabInner:
             nr = np.linalg.norm(r)
         return z, c, nr
 
-    def __call__(self, v, p, k):
+    def __call__(self, v, p, k, eps=None):
         cyc = None if self.replay is None else int(self.replay[k - 1])
-        return self.solve(v, p, cyc)
+        if eps is None:
+            return self.solve(v, p, cyc)
+        keep, self.eps = self.eps, eps
+        try:
+            return self.solve(v, p, cyc)
+        finally:
+            self.eps = keep

@@ -16,7 +16,7 @@ class ExactInner:
         self.A = [op.shifted(t).tocsc() for t in taus]
         self.lu = [spla.splu(A) for A in self.A]
 
-    def __call__(self, v, p, k):
+    def __call__(self, v, p, k, eps=None):  # exact: a tolerance does not apply
         z = self.lu[p].solve(v)
         return z, 0, float(np.linalg.norm(v - self.A[p] @ z))
 

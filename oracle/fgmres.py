@@ -21,6 +21,10 @@ Followed passages:
       ||r_0|| = beta, x_0 = 0, as in Section 6.1), and is then frozen with (m_j, y_j).
   Section 3 (after Prop. 3): h_{k+1,k} = 0 means the iterate is exact; the solve
       stops there (status "breakdown").
+  Section 4 (last paragraph) points to inner tolerances that grow as the outer
+      residual falls (Simoncini and Szyld); the paper does not pursue them. The
+      optional relaxation here (relaxed_eps) follows that idea; the stopping test
+      is unchanged, so a relaxed solve is certified by the same bound.
 
 Everything is complex128 and runs one shift and one step at a time.
 """
@@ -32,6 +36,7 @@ import numpy as np
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 BREAKDOWN_RTOL = 1e-13
+RELAX_EPS_MAX = 1e-3      # cap on a relaxed inner tolerance
 
 
 @dataclasses.dataclass
@@ -52,6 +57,7 @@ class SolveResult:
     Z: np.ndarray | None = None
     y: list | None = None
     hist: list | None = None     # per step: r_est / beta of every shift still live
+    eps_k: np.ndarray | None = None  # per step: the relaxed inner tolerance used
 
 
 def shifted_hessenberg(H, taus, sigma, k):
@@ -71,13 +77,27 @@ def small_solve(Hs, beta, k, variant):
     return y, float(np.linalg.norm(rhs - Hs @ y))
 
 
+def relaxed_eps(eps, relax, tol, r_prev):
+    """Inner tolerance of a step under relaxation (after Simoncini and Szyld, the
+    theory Section 4 refers to): the inner residual may grow as the outer
+    residual falls, eps_k = min(RELAX_EPS_MAX, max(eps, relax * tol / R_{k-1})),
+    R_{k-1} the largest relative residual estimate of the shifts still
+    iterating after step k-1 (1 before the first step). relax <= 0: eps."""
+    if relax <= 0:
+        return eps
+    return min(RELAX_EPS_MAX, max(eps, relax * tol / r_prev))
+
+
 def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fgmres",
-                  replay_mj=None, keep_basis=False, history=False) -> SolveResult:
+                  replay_mj=None, keep_basis=False, history=False, inner_relax=0.0, eps=0.0) -> SolveResult:
     """Solve (K + sigma_j M) x_j = b for all shifts from one flexible Arnoldi basis.
 
     op: object with .M (sparse) and .n; inner(v, tau_index, k) -> (z, cycles, ||p||);
     taus_bar: distinct preconditioner shifts; sched: tau_bar index per step, cycled.
     replay_mj: optional per-shift step at which to freeze (otherwise the bound decides).
+    inner_relax > 0: the inner tolerance of step k is relaxed_eps(eps, inner_relax,
+    tol, R_{k-1}) and is passed as inner(v, tau_index, k, eps_k); the stopping
+    test stays the bound of Eq. trueresidual with the measured ||p_i||.
     """
     n = op.n
     sigmas = np.asarray(sigmas, dtype=np.complex128)
@@ -99,6 +119,8 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
     taus = np.zeros(m_max, dtype=np.complex128)
     pnorm = np.zeros(m_max)
     cycles = np.zeros(m_max, dtype=np.int64)
+    eps_k = np.zeros(m_max)
+    r_prev = 1.0
     ys = [None] * nf
     V[:, 0] = b / beta
     live = np.ones(nf, dtype=bool)
@@ -110,7 +132,11 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
         k += 1
         p = int(sched[(k - 1) % len(sched)])
         taus[k - 1] = taus_bar[p]
-        z, c, pn = inner(V[:, k - 1], p, k)
+        if inner_relax > 0:
+            eps_k[k - 1] = relaxed_eps(eps, inner_relax, tol, r_prev)
+            z, c, pn = inner(V[:, k - 1], p, k, eps_k[k - 1])
+        else:
+            z, c, pn = inner(V[:, k - 1], p, k)
         Z[:, k - 1] = z
         pnorm[k - 1] = pn
         cycles[k - 1] = c
@@ -128,6 +154,7 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
             V[:, k] = w / hn
         if history:
             hist.append(np.full(nf, np.nan))
+        r_prev = 0.0
         for j in np.nonzero(live)[0]:
             Hs = shifted_hessenberg(H, taus, sigmas[j], k)
             y, rt = small_solve(Hs, beta, k, variant)
@@ -147,6 +174,8 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
                 res_est[j] = rt / beta
                 res_bound[j] = bound / beta
                 status[j] = OK if conv else (BREAKDOWN if breakdown else NOT_CONVERGED)
+            else:
+                r_prev = max(r_prev, rt / beta)
         if breakdown or not live.any():
             break
     for j in range(nf):
@@ -155,6 +184,7 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
     res = SolveResult(x, m_j, status, res_est, res_bound, k, bool(breakdown), beta, pnorm[:k], cycles[:k],
                       taus[:k], H[:k + 1, :k].copy())
     res.hist = hist
+    res.eps_k = eps_k[:k].copy() if inner_relax > 0 else None
     if keep_basis:
         res.V = V[:, :k + 1].copy()
         res.Z = Z[:, :k].copy()

@@ -196,6 +196,6 @@ class GMGInner:
         self.max_cycles = max_cycles
         self.replay = None if replay_cycles is None else list(replay_cycles)
 
-    def __call__(self, v, p, k):
+    def __call__(self, v, p, k, eps=None):
         cyc = None if self.replay is None else int(self.replay[k - 1])
-        return self.hier.solve(v, p, self.eps, self.max_cycles, cyc)
+        return self.hier.solve(v, p, self.eps if eps is None else eps, self.max_cycles, cyc)
