@@ -60,6 +60,9 @@ def parse():
                     help="one untimed solve and exit (a small command for ncu captures)")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="graph: the step loop as one CUDA graph; host: the same kernels launched one by one")
+    ap.add_argument("--inner-relax", type=float, default=0.01,
+                    help="relaxed inner tolerance constant l (eps_k = min(1e-3, max(eps, l tol / R_k-1))); "
+                         "0: the fixed eps of every step")
     ap.add_argument("--requests", type=int, default=64, help="workload 5: requests in the stream")
     ap.add_argument("--lanes", type=int, default=3, help="workload 5: concurrent server lanes")
     ap.add_argument("--fuse-max", type=int, default=None,
@@ -141,7 +144,7 @@ def serve_bench(args, rank, world, local, dist):
     def make_req(i):
         p = probs[i]
         opts, keep = fks.make_options(tol=TOL, m_max=p.m_max, precision=prec, inner_tol=INNER_EPS,
-                                      schedule=p.schedule)
+                                      schedule=p.schedule, inner_relax=args.inner_relax)
         return fks.ServerRequest(ops[i], p.rhs().T.copy(), p.sigma, p.tau_bar, opts, keep, p.n)
 
     def run(idx, arrivals=None):
@@ -224,7 +227,7 @@ def serve_bench(args, rank, world, local, dist):
         fks.fks_server_submit(srv, r0)
         fks.fks_server_wait(srv, r0.ticket)
         ws = int(r0.m_j.max())
-        v, dt, desc = cpu_oracle_sample(p0, min(args.cpu_sample_steps, ws), ws, INNER_EPS)
+        v, dt, desc = cpu_oracle_sample(p0, min(args.cpu_sample_steps, ws), ws, INNER_EPS, args.inner_relax)
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                "sample": f"request 0 ({'x'.join(map(str, p0.shape[::-1]))}, {len(p0.sigma)} shifts, "
                          f"{len(p0.src_cells)} sources; first source): " + desc}
@@ -328,21 +331,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_sample(pr, sample_steps, workload_steps, eps):
+def cpu_oracle_sample(pr, sample_steps, workload_steps, eps, relax=0.0, total_cycles=None):
     """The oracle (complex128 NumPy/SciPy) on the first `sample_steps` flexible
-    Arnoldi steps of the workload, extrapolated linearly to the steps a whole
-    solve takes. Returns (solves/s, seconds, description)."""
+    Arnoldi steps of the workload's first source, with the same inner-tolerance
+    rule, extrapolated to a whole solve: by inner cycles when the whole solve's
+    count is known (the multigrid cycles are most of the oracle's time),
+    otherwise linearly in steps. Returns (solves/s, seconds, description)."""
     import oracle
     from oracle.gmg import Hierarchy, GMGInner
     t0 = time.perf_counter()
     op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
     hier = Hierarchy(op, pr.tau_bar)
     b = pr.rhs()[:, 0]
-    res = oracle.shifted_solve(op, b, pr.sigma, pr.tau_bar, pr.schedule, 0.0, sample_steps, GMGInner(hier, eps))
+    t_setup = time.perf_counter() - t0
+    res = oracle.shifted_solve(op, b, pr.sigma, pr.tau_bar, pr.schedule, TOL, sample_steps, GMGInner(hier, eps),
+                               inner_relax=relax, eps=eps)
     dt = time.perf_counter() - t0
-    t_full = dt * workload_steps / max(res.steps, 1)
+    c_sample = int(res.cycles.sum())
+    if total_cycles and c_sample > 0:
+        t_full = t_setup + (dt - t_setup) * total_cycles / c_sample
+        how = f"scaled by inner cycles ({c_sample} of the solve's {total_cycles})"
+    else:
+        t_full = dt * workload_steps / max(res.steps, 1)
+        how = f"scaled linearly to {workload_steps} steps" + (
+            " (with a relaxed tolerance the first steps take the most cycles: an upper estimate)" if relax > 0 else "")
     desc = (f"oracle setup + first {res.steps} of {workload_steps} flexible Arnoldi steps of the first source "
-            f"({dt:.1f} s), scaled linearly to {workload_steps} steps")
+            f"({dt:.1f} s), {how}")
     return len(pr.sigma) / t_full, dt, desc   # one source's shifted solves
 
 
@@ -369,7 +383,7 @@ def run_reference(args):
     vals, secs = [], []
     sample = None
     for i in range(args.warmup + args.steps):
-        v, dt, sample = cpu_oracle_sample(pr, max(1, args.cpu_sample_steps // 3), ws, INNER_EPS)
+        v, dt, sample = cpu_oracle_sample(pr, max(1, args.cpu_sample_steps // 3), ws, INNER_EPS, args.inner_relax)
         if i >= args.warmup:
             vals.append(v)
             secs.append(dt)
@@ -420,10 +434,11 @@ def main():
     est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
     mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
     opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
-                                  schedule=pr.schedule, launch_mode=0 if args.launch_mode == "graph" else 1)
+                                  schedule=pr.schedule, launch_mode=0 if args.launch_mode == "graph" else 1,
+                                  inner_relax=args.inner_relax)
     # host-driven launches (identical kernels) for per-launch event timing
     opts_host, keep_host = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
-                                            schedule=pr.schedule, launch_mode=1)
+                                            schedule=pr.schedule, launch_mode=1, inner_relax=args.inner_relax)
     info, info_arr = fks.make_info(n_rhs, pr.m_max)
 
     def step(b, X, o=opts):
@@ -565,7 +580,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = int(info_arr["steps"].max()) or WORKLOAD_STEPS.get(args.workload, 40)
-        v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS)
+        v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS, args.inner_relax,
+                                        int(info_arr["inner_cycles"][:pr.m_max].sum()))
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
 
     roof["alg_bytes_per_launch"] = prof["bytes"] / max(prof["launches"], 1)
@@ -578,7 +594,9 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": pr.name, "grid": "x".join(map(str, pr.shape[::-1])), "n": n, "n_f": n_f,
                            "n_p": len(pr.tau_bar), "schedule": "cycled", "sources_per_gpu": n_rhs,
-                           "inner": f"multigrid V(2,2) red-black GS, defect correction to eps={INNER_EPS:g}",
+                           "inner": (f"multigrid V(2,2) red-black GS, defect correction to eps={INNER_EPS:g}"
+                                     + (f", relaxed: eps_k = min(1e-3, max(eps, {args.inner_relax:g} tol / R_k-1))"
+                                        if args.inner_relax > 0 else "")),
                            "precision": args.precision, "parallelism": f"replicas{world}",
                            "l2": "working set larger than L2 (basis V, Z: 2 x 101 x n x 16 B)",
                            "arnoldi_steps": int(info_arr["steps"].max()),

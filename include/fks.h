@@ -137,6 +137,12 @@ typedef struct {
                             7-bit bf16 slices, exact fp32 accumulation of the slice products,
                             error at the level of an FP64 GEMM; used when 2 * steps <= 128,
                             else the FP64 kernel); 1 = FP64 FMA kernel                         */
+  double inner_relax;    /* l > 0: relaxed inner tolerance, step k uses
+                            min(1e-3, max(eps, l * tol / R_{k-1})) with R_{k-1} the largest
+                            ||beta e_1 - H_bar(sigma_j) y|| / beta of the shifts still iterating
+                            after step k-1 (R_0 = 1); the idea Section 4 closes with (after
+                            Simoncini and Szyld). Convergence is still decided by the bound of
+                            Eq. trueresidual with the measured ||p_k||. <= 0: eps at every step */
 } fks_options;
 
 /* Optional per-solve diagnostics, host arrays owned by the caller (any may be NULL). */

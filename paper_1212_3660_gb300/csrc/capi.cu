@@ -270,6 +270,7 @@ struct Solve {
   z64* cinv64;
   // CSR operators: BiCGSTAB cycle work vectors (cycle precision), scalars, Jacobi diagonals
   int inner_steps = 8;
+  double relax = 0.0;  // relaxed inner tolerance constant (0: fixed eps)
   void* bv[9] = {};        // e, r, rh, p, v, ph, s, sh, t
   void* dinv = nullptr;    // [n_tau][n]
   BcgScal* bsc = nullptr;
@@ -502,12 +503,13 @@ static void sec_inner_first(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t
                                S.nslot, S.s));
     PROF(-1, -1, 0, 0,
          launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 1, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
-                             S.counter, S.s));
+                             S.counter, S.s, S.relax, S.tol));
   } else {
     // defect and decision in one launch
     PROF(FKS_K_DEFECT, 0, ns * n * (16 + cv), ns * n * 4.0,
          launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, S.diag64, V, vsV, Z, vsZ, N, 1, f0, N, S.dpart, S.eps,
-                                  S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot, S.s));
+                                  S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot,
+                                  S.relax, S.tol, S.s));
   }
 }
 
@@ -549,12 +551,13 @@ static void sec_inner_body(Solve& S, const z64* V, int64_t vsV, z64* Z, int64_t 
                                S.nslot, S.s));
     PROF(-1, -1, 0, 0,
          launch_inner_decide(S.st, S.nslot, S.dpart, S.ndef, 0, S.eps, S.max_cycles, rc, S.m, use_cond, hin, S.flags,
-                             S.counter, S.s));
+                             S.counter, S.s, S.relax, S.tol));
   } else {
     // defect and decision in one launch (the K diagonal is precomputed on this level)
     PROF(FKS_K_DEFECT, 0, ns * n * (32 + 8 * (d + 2) + cv), ns * n * (8 * d + 10),
          launch_defect_decide<VT>(S.op->levels[0], S.st, S.taus, S.diag64, V, vsV, Z, vsZ, N, 0, f0, N, S.dpart, S.eps,
-                                  S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot, S.s));
+                                  S.max_cycles, rc, S.m, use_cond, hin, S.flags, S.counter, S.bcount, S.nslot,
+                                  S.relax, S.tol, S.s));
   }
 }
 
@@ -843,6 +846,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   S.max_cycles = o->inner_max_cycles > 0 ? o->inner_max_cycles : 50;
   S.replay = o->replay_mode != 0;
   S.inner_steps = o->inner_steps > 0 ? o->inner_steps : 8;
+  S.relax = o->inner_relax > 0 ? o->inner_relax : 0.0;
   bool x_dev = groups ? false : is_device_ptr(X);
   if (groups && !res_true) res_true = (double*)1;  // grouped runs always compute true residuals
   // workspace size: carve once on a null base to measure
@@ -885,7 +889,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
                                  (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
-                                 (double)op->tile16_max[1]};
+                                 (double)op->tile16_max[1], S.relax};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1357,6 +1361,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   if (o->launch_mode != 0 && o->launch_mode != 1) { set_error("fks_solve: launch_mode must be 0 or 1"); return FKS_ERR_ARG; }
   if (o->inner_steps > 64) { set_error("fks_solve: inner_steps must be at most 64"); return FKS_ERR_ARG; }
   if (o->assembly != 0 && o->assembly != 1) { set_error("fks_solve: assembly must be 0 or 1"); return FKS_ERR_ARG; }
+  if (!std::isfinite(o->inner_relax)) { set_error("fks_solve: inner_relax is not finite"); return FKS_ERR_ARG; }
   if (o->replay_mode && (!o->replay_inner_cycles || !o->replay_mj)) { set_error("fks_solve: replay arrays missing"); return FKS_ERR_ARG; }
   if (o->replay_mode) {
     for (int i = 0; i < o->m_max * n_rhs; ++i)
@@ -1790,6 +1795,7 @@ static bool compatible(const Request& a, const Request& b) {
   if (p.tol != q.tol || p.m_max != q.m_max || p.variant != q.variant || p.precision != q.precision ||
       p.inner_tol != q.inner_tol || p.inner_max_cycles != q.inner_max_cycles || p.replay_mode || q.replay_mode ||
       std::max(p.inner_steps, 0) != std::max(q.inner_steps, 0) || p.assembly != q.assembly ||
+      std::max(p.inner_relax, 0.0) != std::max(q.inner_relax, 0.0) ||
       a.sched != b.sched)
     return false;
   for (int j = 0; j < x.n_f; ++j)
@@ -1981,7 +1987,7 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
       o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
       (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
       (o.variant != FKS_FGMRES && o.variant != FKS_FFOM) || o.inner_steps > 64 ||
-      (o.assembly != 0 && o.assembly != 1)) {
+      (o.assembly != 0 && o.assembly != 1) || !std::isfinite(o.inner_relax)) {
     set_error("fks_server_submit: bad request");
     return FKS_ERR_ARG;
   }

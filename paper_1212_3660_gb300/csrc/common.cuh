@@ -133,7 +133,19 @@ struct SlotState {
   int live;         // shifts not yet frozen
   int breakdown;    // h_{k+1,k} vanished at step k
   int inner_capped; // some inner solve hit its cycle cap
+  double rmax;      // largest relative residual estimate of the live shifts after the last step (1 at start)
+  unsigned long long rmax_next;  // the same for the step in progress (bits of a non-negative double, atomic max)
 };
+
+constexpr double RELAX_EPS_MAX = 1e-3;  // cap on a relaxed inner tolerance
+
+// Inner tolerance of the current step: eps, or with relax > 0 the relaxed
+// min(RELAX_EPS_MAX, max(eps, relax * tol / rmax)) (Section 4's closing remark).
+__host__ __device__ inline double inner_eps(double eps, double relax, double tol, double rmax) {
+  if (!(relax > 0.0)) return eps;
+  double e = rmax > 0.0 ? relax * tol / rmax : RELAX_EPS_MAX;
+  return fmin(RELAX_EPS_MAX, fmax(eps, e));
+}
 
 // Fixed-order block reduction of one double (blockDim.x a multiple of 32, at
 // most 1024); the result is valid in thread 0. Deterministic for a given

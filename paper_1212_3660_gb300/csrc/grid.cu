@@ -669,7 +669,9 @@ __device__ __forceinline__ void report_slot(int slot, int running, int nslot, in
 // (Section 4: stop when ||p_k|| <= eps ||v_k||, or after max_cycles, or after the
 // replayed number of cycles). Returns whether the slot keeps cycling.
 __device__ __forceinline__ int decide_slot(SlotState& s, int slot, double a, double b, int first, double eps,
-                                           int max_cycles, const int32_t* replay_cycles, int m_max) {
+                                           int max_cycles, const int32_t* replay_cycles, int m_max, double relax,
+                                           double tol) {
+  eps = inner_eps(eps, relax, tol, s.rmax);
   s.pnorm2 = a;
   if (first) {
     s.vnorm2 = b;
@@ -700,6 +702,7 @@ struct DecideArgs {
   int* counter;
   int* bcount;                   // per-slot count of finished blocks, reset by the last one
   int nslot;
+  double relax, tol;             // relaxed inner tolerance (relax <= 0: eps)
 };
 
 // r = v - (K + tau M) z in fp64; f0 = r in the cycle precision; per-block
@@ -785,7 +788,8 @@ __global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, co
     b = 0.0;
     for (int q = 0; q < GX * GY / 32; ++q) { a += red[0][q]; b += red[1][q]; }
     D.bcount[slot] = 0;
-    int running = decide_slot(st[slot], slot, a, b, zero_z, D.eps, D.max_cycles, D.replay_cycles, D.m_max);
+    int running = decide_slot(st[slot], slot, a, b, zero_z, D.eps, D.max_cycles, D.replay_cycles, D.m_max, D.relax,
+                              D.tol);
     if (D.use_cond) report_slot(slot, running, D.nslot, D.flags, D.counter, D.cond);
   }
 }
@@ -797,7 +801,8 @@ __global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, co
 // finished blocks and is reset by the last one).
 __global__ void k_inner_decide(SlotState* st, int nslot, const double* __restrict__ partial, int nblocks,
                                int first, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
-                               int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter) {
+                               int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter, double relax,
+                               double tol) {
   __shared__ double red[32];
   int slot = blockIdx.x;
   SlotState& s = st[slot];
@@ -811,7 +816,8 @@ __global__ void k_inner_decide(SlotState* st, int nslot, const double* __restric
     }
     a = block_sum(a, red);
     b = block_sum(b, red);
-    if (threadIdx.x == 0) running = decide_slot(s, slot, a, b, first, eps, max_cycles, replay_cycles, m_max);
+    if (threadIdx.x == 0)
+      running = decide_slot(s, slot, a, b, first, eps, max_cycles, replay_cycles, m_max, relax, tol);
   }
   if (use_cond && threadIdx.x == 0) report_slot(slot, running, nslot, flags, counter, cond);
 }
@@ -991,8 +997,8 @@ void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, co
                           int64_t vsv, const z64* z, int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf,
                           double* partial, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
                           int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount,
-                          int nslot, cudaStream_t s) {
-  DecideArgs D{1, eps, max_cycles, replay_cycles, m_max, use_cond, cond, flags, counter, bcount, nslot};
+                          int nslot, double relax, double tol, cudaStream_t s) {
+  DecideArgs D{1, eps, max_cycles, replay_cycles, m_max, use_cond, cond, flags, counter, bcount, nslot, relax, tol};
   k_defect<T><<<defect_grid(L, nslot), B2, 0, s>>>(view<double>(L), st, taus, diag64, v, vsv, z, vsz, col, zero_z,
                                                    f0, vsf, partial, zero_z, D);
 }
@@ -1007,9 +1013,10 @@ void launch_kdiag(const LevelHost& L, double* kd, cudaStream_t s) {
 
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
                          int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
-                         cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s) {
+                         cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s, double relax,
+                         double tol) {
   k_inner_decide<<<nslot, 512, 0, s>>>(st, nslot, partial, nblocks, first, eps, max_cycles, replay_cycles, m_max,
-                                        use_cond, cond, flags, counter);
+                                        use_cond, cond, flags, counter, relax, tol);
 }
 
 #define INST(T)                                                                                                  \
@@ -1041,7 +1048,7 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
   template void launch_defect_decide<T>(const LevelHost&, SlotState*, const z64*, const z64*, const z64*, int64_t, \
                                         const z64*, int64_t, int64_t, int, cx<T>*, int64_t, double*, double, int, \
                                         const int32_t*, int, int, cudaGraphConditionalHandle, int*, int*, int*, int, \
-                                        cudaStream_t);
+                                        double, double, cudaStream_t);
 
 INST(double)
 INST(float)

@@ -94,12 +94,13 @@ void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, co
                           int64_t vsv, const z64* z, int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf,
                           double* partial, double eps, int max_cycles, const int32_t* replay_cycles, int m_max,
                           int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount,
-                          int nslot, cudaStream_t s);
+                          int nslot, double relax, double tol, cudaStream_t s);
 void launch_diag64(const LevelHost& L, const z64* taus, int ntau, z64* out, cudaStream_t s);
 // kd[c] = sum of the faces of cell c (the diagonal of K) in fp64
 void launch_kdiag(const LevelHost& L, double* kd, cudaStream_t s);
 void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nblocks, int first, double eps,
                          int max_cycles, const int32_t* replay_cycles, int m_max, int use_cond,
-                         cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s);
+                         cudaGraphConditionalHandle cond, int* flags, int* counter, cudaStream_t s,
+                         double relax = 0.0, double tol = 0.0);
 
 }  // namespace fks

@@ -59,6 +59,8 @@ __global__ void k_start(SlotState* st, int nslot, const double* __restrict__ par
   t.vnorm2 = 0.0;
   t.pnorm2 = 0.0;
   t.w0norm2 = 0.0;
+  t.rmax = 1.0;
+  t.rmax_next = 0ull;
 }
 
 // v_1 = b / beta; shift bookkeeping reset (status LIVE, g_1 = beta, Y = 0).
@@ -329,7 +331,11 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   int rmj = replay_mj ? replay_mj[sj] : 0;
   double est = sd[warp];
   bool need = variant == 1 || est <= tol * beta || brk || k == m || (replay_mj && k == rmj);
-  if (!need) return;
+  if (!need) {
+    // still iterating: its estimate enters the next step's relaxed tolerance
+    if (lane == 0) atomicMax(&s.rmax_next, (unsigned long long)__double_as_longlong(est / beta));
+    return;
+  }
   // back substitution: R y = g (FGMRES) or the square factor (FFOM)
   for (int i = lane; i < k; i += 32) rhs[warp][i] = gj[i];
   __syncwarp();
@@ -352,7 +358,10 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   double bound = est + part;
   bool conv = bound <= tol * beta;
   bool freeze = replay_mj ? (k == rmj || brk) : (conv || brk || k == m);
-  if (!freeze) return;
+  if (!freeze) {
+    if (lane == 0) atomicMax(&s.rmax_next, (unsigned long long)__double_as_longlong(est / beta));
+    return;
+  }
   for (int i = lane; i < m; i += 32) Y[sj * m + i] = i < k ? yv[warp][i] : mk(0.0, 0.0);
   if (lane == 0) {
     mj[sj] = k;
@@ -371,6 +380,8 @@ __global__ void k_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGr
   for (int slot = threadIdx.x; slot < nslot; slot += blockDim.x) {
     SlotState& s = st[slot];
     if (!s.active) continue;
+    s.rmax = __longlong_as_double((long long)s.rmax_next);
+    s.rmax_next = 0ull;
     if (s.live <= 0 || s.breakdown || s.k >= m) s.active = 0;
     any |= s.active;
   }
