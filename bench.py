@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer region (very large outputs)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the plain (complex128, fixed tolerance) and mixed relaxed variants")
     ap.add_argument("--single", action="store_true",
                     help="one untimed solve and exit (a small command for ncu captures)")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
@@ -577,11 +579,46 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end()
 
+    main_info = {k: v.copy() for k, v in info_arr.items()}   # this line's solve, before the variants
+
+    # ---- the same workload in the paper's plain configuration (complex128,
+    # fixed inner tolerance) and in the mixed, relaxed one, on this GPU
+    def variant(v_prec, v_relax, reps=3, warm=2):
+        if v_prec == prec and v_relax == args.inner_relax:
+            return None
+        o_v, keep_v = fks.make_options(tol=TOL, m_max=pr.m_max, precision=v_prec, inner_tol=INNER_EPS,
+                                       schedule=pr.schedule, inner_relax=v_relax)
+        fks.fks_op_autotune(solver.op, v_prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+        for _ in range(warm):
+            step(b_d, X_d, o_v)
+        barrier()
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        conv_v = 0
+        v0.record(stream)
+        for _ in range(reps):
+            step(b_d, X_d, o_v)
+            conv_v += int(np.sum(tru <= TOL))
+        v1.record(stream)
+        torch.cuda.synchronize()
+        ms_v = max_over_ranks(v0.elapsed_time(v1) / reps)
+        return {"value": sum_over_ranks(conv_v / reps) / (ms_v / 1000.0), "ms_per_step": ms_v,
+                "precision": "fp64" if v_prec == fks.FKS_PREC_FP64 else "mixed", "inner_relax": v_relax,
+                "inner_cycles_total": int(info_arr["inner_cycles"].sum()), "steps_timed": reps}
+    comparison = None
+    if args.workload in (1, 2, 3, 4) and not args.no_compare:
+        comparison = {"this_line": {"value": value, "precision": args.precision, "inner_relax": args.inner_relax},
+                      "plain_fp64_fixed_eps": variant(fks.FKS_PREC_FP64, 0.0),
+                      "mixed_relaxed": variant(fks.FKS_PREC_MIXED, 0.01)}
+        # restore this line's tuning for what follows
+        fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ws = int(info_arr["steps"].max()) or WORKLOAD_STEPS.get(args.workload, 40)
+        ws = int(main_info["steps"].max()) or WORKLOAD_STEPS.get(args.workload, 40)
         v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS, args.inner_relax,
-                                        int(info_arr["inner_cycles"][:pr.m_max].sum()))
+                                        int(main_info["inner_cycles"][:pr.m_max].sum()))
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
 
     roof["alg_bytes_per_launch"] = prof["bytes"] / max(prof["launches"], 1)
@@ -599,13 +636,13 @@ def main():
                                         if args.inner_relax > 0 else "")),
                            "precision": args.precision, "parallelism": f"replicas{world}",
                            "l2": "working set larger than L2 (basis V, Z: 2 x 101 x n x 16 B)",
-                           "arnoldi_steps": int(info_arr["steps"].max()),
-                           "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
+                           "arnoldi_steps": int(main_info["steps"].max()),
+                           "inner_cycles_total": int(main_info["inner_cycles"].sum()),
                            "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned,
                            "tile16_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[1],
                            "launch_mode": args.launch_mode},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
-                "e2e": e2e,
+                "e2e": e2e, "comparison": comparison,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)
