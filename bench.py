@@ -62,13 +62,17 @@ def parse():
                     help="one untimed solve and exit (a small command for ncu captures)")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="graph: the step loop as one CUDA graph; host: the same kernels launched one by one")
-    ap.add_argument("--inner-relax", type=float, default=0.01,
+    ap.add_argument("--inner-relax", type=float, default=0.003,
                     help="relaxed inner tolerance constant l (eps_k = min(1e-3, max(eps, l tol / R_k-1))); "
                          "0: the fixed eps of every step")
     ap.add_argument("--requests", type=int, default=64, help="workload 5: requests in the stream")
     ap.add_argument("--lanes", type=int, default=3, help="workload 5: concurrent server lanes")
     ap.add_argument("--fuse-max", type=int, default=None,
                     help="fused 2D levels up to this many cells (-1: all) instead of autotuning")
+    ap.add_argument("--tile16-max", type=int, default=None,
+                    help="with --fuse-max: fused levels up to this many cells on 16 x 16 tiles (-1: all)")
+    ap.add_argument("--no-survey", action="store_true",
+                    help="skip the per-class timing survey and the roofline (a short command for ncu launch lists)")
     a = ap.parse_args()
     if a.precision is None:
         a.precision = "fp64" if a.workload in (1, 2) else "mixed"
@@ -467,6 +471,8 @@ def main():
 
     if args.fuse_max is not None:
         fks.fks_op_set_fusion(solver.op, prec, args.fuse_max)
+        if args.tile16_max is not None:
+            fks.fks_op_set_tiles(solver.op, prec, args.tile16_max)
     if args.single:
         st = step(b_d, X_d)
         torch.cuda.synchronize()
@@ -481,13 +487,13 @@ def main():
         step(b_d, X_d)
     # kernel-class survey (stderr only) and choice of the dominant class
     totals = {}
-    for c, name in enumerate(fks.KERNEL_CLASSES):
+    for c, name in enumerate([] if args.no_survey else fks.KERNEL_CLASSES):
         fks.fks_profile_select(solver.op, c)
         step(b_d, X_d, opts_host)
         totals[name] = fks.fks_profile_read(solver.op)
     fks.fks_profile_select(solver.op, None)
     fks.fks_profile_read(solver.op)
-    dominant = max(totals, key=lambda k: totals[k]["ms"])
+    dominant = max(totals, key=lambda k: totals[k]["ms"]) if totals else None
     if args.survey and rank == 0:
         tot = sum(v["ms"] for v in totals.values())
         for k, v in sorted(totals.items(), key=lambda kv: -kv[1]["ms"]):
@@ -524,37 +530,39 @@ def main():
     conv_per_step = converged / args.steps
     value = sum_over_ranks(conv_per_step) / (ms_max / 1000.0)
 
-    # ---- roofline of the dominant kernel class (events on the library's stream),
-    # on the finest level where the class runs per level
-    def timed_class(level):
-        fks.fks_profile_select(solver.op, dominant, level)
-        for _ in range(args.steps):
-            step(b_d, X_d, opts_host)
-        pr_ = fks.fks_profile_read(solver.op)
-        fks.fks_profile_select(solver.op, None)
-        return pr_
-    roof_level = 0
-    prof = timed_class(0)
-    if prof["launches"] == 0:
-        roof_level = -1
-        prof = timed_class(-1)
-    traffic, traffic_src = recorded_traffic(pr.name, args.precision, dominant, roof_level)
-    hbm_peak, bf16_peak, peak_src = peaks()
-    gbs = prof["bytes"] / max(prof["ms"], 1e-12) / 1e6
-    tfl = prof["flops"] / max(prof["ms"], 1e-12) / 1e9
-    f_hbm = gbs / hbm_peak
-    f_alu = tfl / FP64_PEAK_TFLOPS if prec == fks.FKS_PREC_FP64 or dominant in ("mdot", "maxpy", "assemble",
-                                                                                 "defect", "tres") else 0.0
-    if f_alu > f_hbm:
-        roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
-                "traffic": traffic, "kernel": dominant, "level": roof_level,
-                "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz",
-                "launches": prof["launches"], "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
-                "hbm_frac_of_" + peak_src: f_hbm}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm, "traffic": traffic,
-                "kernel": dominant, "level": roof_level, "peak_source": peak_src, "launches": prof["launches"],
-                "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1)}
+    roof = None
+    if dominant is not None:
+        # ---- roofline of the dominant kernel class (events on the library's stream),
+        # on the finest level where the class runs per level
+        def timed_class(level):
+            fks.fks_profile_select(solver.op, dominant, level)
+            for _ in range(args.steps):
+                step(b_d, X_d, opts_host)
+            pr_ = fks.fks_profile_read(solver.op)
+            fks.fks_profile_select(solver.op, None)
+            return pr_
+        roof_level = 0
+        prof = timed_class(0)
+        if prof["launches"] == 0:
+            roof_level = -1
+            prof = timed_class(-1)
+        traffic, traffic_src = recorded_traffic(pr.name, args.precision, dominant, roof_level)
+        hbm_peak, bf16_peak, peak_src = peaks()
+        gbs = prof["bytes"] / max(prof["ms"], 1e-12) / 1e6
+        tfl = prof["flops"] / max(prof["ms"], 1e-12) / 1e9
+        f_hbm = gbs / hbm_peak
+        f_alu = tfl / FP64_PEAK_TFLOPS if prec == fks.FKS_PREC_FP64 or dominant in ("mdot", "maxpy", "assemble",
+                                                                                     "defect", "tres") else 0.0
+        if f_alu > f_hbm:
+            roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
+                    "traffic": traffic, "kernel": dominant, "level": roof_level,
+                    "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                    "launches": prof["launches"], "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
+                    "hbm_frac_of_" + peak_src: f_hbm}
+        else:
+            roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm, "traffic": traffic,
+                    "kernel": dominant, "level": roof_level, "peak_source": peak_src, "launches": prof["launches"],
+                    "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1)}
 
     def end_to_end():
         b_h = torch.from_numpy(pr.rhs().T.copy()).pin_memory()
@@ -610,7 +618,7 @@ def main():
     if args.workload in (1, 2, 3, 4) and not args.no_compare:
         comparison = {"this_line": {"value": value, "precision": args.precision, "inner_relax": args.inner_relax},
                       "plain_fp64_fixed_eps": variant(fks.FKS_PREC_FP64, 0.0),
-                      "mixed_relaxed": variant(fks.FKS_PREC_MIXED, 0.01)}
+                      "mixed_relaxed": variant(fks.FKS_PREC_MIXED, args.inner_relax if args.inner_relax > 0 else 0.003)}
         # restore this line's tuning for what follows
         fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
 
@@ -621,9 +629,10 @@ def main():
                                         int(main_info["inner_cycles"][:pr.m_max].sum()))
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
 
-    roof["alg_bytes_per_launch"] = prof["bytes"] / max(prof["launches"], 1)
-    roof["traffic_source"] = ("profiles/traffic.md (ncu, sources " + traffic_src + ")") if traffic is not None else (
-        "stale: kernels changed since the ncu capture" if traffic_src else "no ncu capture recorded")
+    if roof is not None:
+        roof["alg_bytes_per_launch"] = prof["bytes"] / max(prof["launches"], 1)
+        roof["traffic_source"] = ("profiles/traffic.md (ncu, sources " + traffic_src + ")") if traffic is not None \
+            else ("stale: kernels changed since the ncu capture" if traffic_src else "no ncu capture recorded")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
