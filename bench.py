@@ -71,6 +71,8 @@ def parse():
                     help="fused 2D levels up to this many cells (-1: all) instead of autotuning")
     ap.add_argument("--tile16-max", type=int, default=None,
                     help="with --fuse-max: fused levels up to this many cells on 16 x 16 tiles (-1: all)")
+    ap.add_argument("--tail-max", type=int, default=None,
+                    help="with --fuse-max: levels up to this many cells in the single-block tail kernel")
     ap.add_argument("--no-survey", action="store_true",
                     help="skip the per-class timing survey and the roofline (a short command for ncu launch lists)")
     a = ap.parse_args()
@@ -473,6 +475,8 @@ def main():
         fks.fks_op_set_fusion(solver.op, prec, args.fuse_max)
         if args.tile16_max is not None:
             fks.fks_op_set_tiles(solver.op, prec, args.tile16_max)
+        if args.tail_max is not None:
+            fks.fks_op_set_tail(solver.op, prec, args.tail_max)
     if args.single:
         st = step(b_d, X_d)
         torch.cuda.synchronize()
@@ -649,6 +653,7 @@ def main():
                            "inner_cycles_total": int(main_info["inner_cycles"].sum()),
                            "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned,
                            "tile16_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[1],
+                           "tail_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[2],
                            "launch_mode": args.launch_mode},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": e2e, "comparison": comparison,

@@ -235,11 +235,13 @@ void fks_server_destroy(fks_server* srv);
 /*
  * Autotuner (no counterpart in the paper): times one multigrid V-cycle of the
  * operator on this GPU for every choice of which 2D levels use the fused
- * shared-memory tile kernels (levels at most `chosen` cells) and which of those
- * run on 16 x 16 rather than 32 x 32 tiles, for the cycle precision `precision`
+ * shared-memory tile kernels (levels at most `chosen` cells), which of those
+ * run on 16 x 16 rather than 32 x 32 tiles and which small levels run in the
+ * single-block tail kernel (256, 1024 or 4096 cells), for the cycle precision `precision`
  * and shift `tau`, and keeps the fastest in the operator for later solves.
  * Solves before any tuning fuse levels up to 65536 cells (complex128 cycles) or
- * all levels (complex64 cycles) and use 16 x 16 tiles up to 16384 cells.
+ * all levels (complex64 cycles), use 16 x 16 tiles up to 16384 cells and a tail
+ * of at most 256 cells.
  * `chosen` (host, may be NULL) receives the fusion threshold (fks_op_tiling
  * reads both).
  */
@@ -254,8 +256,15 @@ fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells);
  * fks_op_autotune picks it together with the fusion threshold. Grid operators only.
  */
 fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells);
-/* The current fusion threshold and 16 x 16 tile threshold of `precision`. */
-fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max);
+/* Levels with at most max_cells cells (the coarsest always) run in the
+ * single-block tail kernel; FKS_ERR_ARG if their vectors do not fit in shared
+ * memory. The results do not depend on it. Grid operators only. */
+fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells);
+/* The current fusion threshold, 16 x 16 tile threshold and single-block tail
+ * threshold (levels of at most tail_max cells run in one block per source) of
+ * `precision`; any output may be NULL. */
+fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
+                         int64_t* tail_max);
 
 /*
  * Allocation-free variant of fks_precond_apply (the paper has no counterpart).

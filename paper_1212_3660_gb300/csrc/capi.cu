@@ -202,6 +202,8 @@ struct fks_op {
   int64_t fuse_max[2] = {65536, INT64_MAX};
   // fused 2D levels with at most this many cells use 16 x 16 tiles (else 32 x 32)
   int64_t tile16_max[2] = {16384, 16384};
+  // levels with at most this many cells run in the single-block tail kernel
+  int64_t tail_max[2] = {256, 256};
 };
 
 namespace fks {
@@ -306,18 +308,19 @@ static int defect_partials(const fks_op* op) {
     S.lane->prof.end(S.s);                                                    \
   } while (0)
 
-// Largest level handled by the single-block tail V-cycle. The tail runs on one
-// SM, so only levels whose half sweeps take a few hundred cells go there
-// (16 x 16); larger levels spread over SMs in tile kernels.
+// First level handled by the single-block tail V-cycle: the first with at most
+// `tmax` cells (the operator's tail threshold for the cycle precision, chosen
+// by fks_op_autotune; the tail runs on one SM, larger levels spread over SMs
+// in tile kernels).
 template <typename VT>
-static constexpr int64_t tail_max_cells() { return 256; }
-
-template <typename VT>
-static int tail_level(const std::vector<LevelHost>& Ls) {
+static int tail_level(const std::vector<LevelHost>& Ls, int64_t tmax) {
   for (size_t l = 0; l < Ls.size(); ++l)
-    if (Ls[l].n <= tail_max_cells<VT>()) return (int)l;
+    if (Ls[l].n <= tmax) return (int)l;
   return (int)Ls.size() - 1;
 }
+
+template <typename VT>
+static int64_t tail_max_of(const fks_op* op) { return op->tail_max[sizeof(VT) == 8 ? 0 : 1]; }
 
 constexpr size_t TAIL_SMEM_LIMIT = 220 * 1024;
 
@@ -355,8 +358,8 @@ static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
 // Bytes per tau of the tail's staged coefficients and their shared-memory
 // offset (0 bytes when the tail reads its coefficients from global memory).
 template <typename VT>
-static size_t tail_blob_bytes(const std::vector<LevelHost>& Ls, int* coef0) {
-  const int lt = tail_level<VT>(Ls);
+static size_t tail_blob_bytes(const std::vector<LevelHost>& Ls, int64_t tmax, int* coef0) {
+  const int lt = tail_level<VT>(Ls, tmax);
   std::vector<int> cb;
   if (!tail_staged<VT>(Ls, lt)) {
     *coef0 = 0;
@@ -374,7 +377,7 @@ template <typename VT>
 static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0) {
   auto& Ls = S.op->levels;
   int nl = (int)Ls.size();
-  int lt = tail_level<VT>(Ls);
+  int lt = tail_level<VT>(Ls, tail_max_of<VT>(S.op));
   cudaStream_t s = S.s;
   auto F = [&](int l) { return (cx<VT>*)S.f[l]; };
   auto Zl = [&](int l) { return (cx<VT>*)S.z[l]; };
@@ -695,7 +698,7 @@ static void setup_levels(Solve& S) {
   auto& Ls = S.op->levels;
   {
     std::lock_guard<std::mutex> build_lock(g_build_mu);
-    tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls)));
+    tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls, tail_max_of<VT>(S.op))));
     fused_prepare<VT>();
   }
   for (size_t l = 0; l < Ls.size(); ++l)
@@ -703,7 +706,7 @@ static void setup_levels(Solve& S) {
   PROF(-1, -1, 0, 0, launch_diag64(Ls[0], S.taus, S.n_tau, S.diag64, S.s));
   if (S.tblob) {
     // the tail's coefficients per tau, laid out as in its shared memory
-    const int lt = tail_level<VT>(Ls);
+    const int lt = tail_level<VT>(Ls, tail_max_of<VT>(S.op));
     std::vector<int> cb;
     tail_layout<VT>(Ls, lt, true, &cb);
     for (int q = 0; q < S.n_tau; ++q)
@@ -778,7 +781,7 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
       S.invd[l] = A.take<cx<VT>>((size_t)S.n_tau * Ls[l].n);
     }
     S.diag64 = A.take<z64>((size_t)S.n_tau * n);
-    S.tblob_bytes = tail_blob_bytes<VT>(Ls, &S.tcoef0);
+    S.tblob_bytes = tail_blob_bytes<VT>(Ls, tail_max_of<VT>(S.op), &S.tcoef0);
     S.tblob = S.tblob_bytes ? A.take<unsigned char>((size_t)S.n_tau * S.tblob_bytes) : nullptr;
     int64_t nc = Ls.back().n;
     S.cwork = A.take<z64>((size_t)S.n_tau * nc * nc);
@@ -889,7 +892,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)S.sched_len, (double)S.precision, (double)S.variant, (double)S.replay,
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
                                  (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
-                                 (double)op->tile16_max[1], S.relax};
+                                 (double)op->tile16_max[1], S.relax, (double)op->tail_max[0],
+                                 (double)op->tail_max[1]};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1410,12 +1414,33 @@ fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells) {
   return FKS_OK;
 }
 
-fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max) {
+fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells) {
+  if (!op) { set_error("fks_op_set_tail: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_set_tail: grid operators only"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_tail: bad precision"); return FKS_ERR_ARG; }
+  if (max_cells < 1) { set_error("fks_op_set_tail: max_cells must be >= 1"); return FKS_ERR_ARG; }
+  int lt;
+  size_t smem;
+  if (precision == FKS_PREC_FP64) {
+    lt = tail_level<double>(op->levels, max_cells);
+    smem = tail_smem<double>(op->levels, lt);
+  } else {
+    lt = tail_level<float>(op->levels, max_cells);
+    smem = tail_smem<float>(op->levels, lt);
+  }
+  if (smem > TAIL_SMEM_LIMIT) { set_error("fks_op_set_tail: the tail levels do not fit in shared memory"); return FKS_ERR_ARG; }
+  op->tail_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells;
+  return FKS_OK;
+}
+
+fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
+                         int64_t* tail_max) {
   if (!op) { set_error("fks_op_tiling: NULL operator"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_tiling: bad precision"); return FKS_ERR_ARG; }
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   if (fuse_max) *fuse_max = op->fuse_max[pi];
   if (tile16_max) *tile16_max = op->tile16_max[pi];
+  if (tail_max) *tail_max = op->tail_max[pi];
   return FKS_OK;
 }
 
@@ -1426,7 +1451,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
   if (!finite_c(tau)) { set_error("fks_op_autotune: tau has NaN/Inf"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
-  int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi];
+  int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi], savedt = op->tail_max[pi];
   try {
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
@@ -1470,14 +1495,33 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       double best = 1e30;
-      int64_t pick = saved, pick16 = saved16;
-      std::vector<std::pair<int64_t, int64_t>> pairs;
-      for (int64_t c : cand)
-        for (int64_t t : cand)
-          if (t <= c) pairs.push_back({c, t});
-      for (auto [c, t16] : pairs) {
-        op->fuse_max[pi] = c;
-        op->tile16_max[pi] = t16;
+      int64_t pick = saved, pick16 = saved16, pickt = savedt;
+      struct Choice { int64_t fuse, t16, tail; };
+      std::vector<Choice> choices;
+      for (int64_t tm : {int64_t(256), int64_t(1024), int64_t(4096)}) {
+        const int lt = tail_level<VT>(op->levels, tm);
+        if (tail_smem<VT>(op->levels, lt) > TAIL_SMEM_LIMIT) continue;  // f and z must fit
+        for (int64_t c : cand)
+          for (int64_t t : cand)
+            if (t <= c) choices.push_back({c, t, tm});
+      }
+      for (const Choice& ch : choices) {
+        op->fuse_max[pi] = ch.fuse;
+        op->tile16_max[pi] = ch.t16;
+        op->tail_max[pi] = ch.tail;
+        {
+          // the tail's shared memory and coefficient blob follow the threshold
+          std::lock_guard<std::mutex> build_lock(g_build_mu);
+          tail_prepare<VT>(tail_smem<VT>(op->levels, tail_level<VT>(op->levels, ch.tail)));
+        }
+        Arena probe2;
+        carve<VT>(S, probe2, false);
+        op->lane0.ws.reserve(probe2.off + 4096);
+        carve<VT>(S, op->lane0.ws, false);
+        CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(S.st, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(S.f[0], 0, sizeof(cx<VT>) * L0.n, s));
+        setup_levels<VT>(S);
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
         S.s = cs;
@@ -1502,8 +1546,9 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
         cudaGraphDestroy(g);
         if (ms < best) {
           best = ms;
-          pick = c;
-          pick16 = t16;
+          pick = ch.fuse;
+          pick16 = ch.t16;
+          pickt = ch.tail;
         }
       }
       cudaEventDestroy(e0);
@@ -1511,12 +1556,14 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       cudaStreamDestroy(cs);
       op->fuse_max[pi] = pick;
       op->tile16_max[pi] = pick16;
+      op->tail_max[pi] = pickt;
     };
     if (precision == FKS_PREC_FP64) run(double{});
     else run(float{});
   } catch (CudaError& e) {
     op->fuse_max[pi] = saved;
     op->tile16_max[pi] = saved16;
+    op->tail_max[pi] = savedt;
     set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
   }

@@ -96,7 +96,8 @@ def lib():
     L.fks_op_autotune.argtypes = [vp, C.c_int, fks_c128, vp, C.POINTER(C.c_int64)]
     L.fks_op_set_fusion.argtypes = [vp, C.c_int, C.c_int64]
     L.fks_op_set_tiles.argtypes = [vp, C.c_int, C.c_int64]
-    L.fks_op_tiling.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.fks_op_set_tail.argtypes = [vp, C.c_int, C.c_int64]
+    L.fks_op_tiling.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.fks_server_create.argtypes = [vp, C.c_size_t, C.c_int, C.POINTER(vp)]
     L.fks_server_submit.argtypes = [vp, C.POINTER(fks_request), C.POINTER(C.c_uint64)]
     L.fks_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -110,7 +111,7 @@ def lib():
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
     for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
-                 "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_tiling", "fks_server_create",
+                 "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_tiling", "fks_server_create",
                  "fks_server_submit", "fks_server_poll", "fks_server_wait",
                  "fks_server_cancel", "fks_server_times", "fks_server_launches"):
         getattr(L, name).restype = C.c_int
@@ -268,13 +269,19 @@ def fks_op_set_tiles(op, precision, max_cells):
         raise FksError(st, fks_last_error())
 
 
-def fks_op_tiling(op, precision):
-    """(fusion threshold, 16 x 16 tile threshold) in cells."""
-    a, b = C.c_int64(0), C.c_int64(0)
-    st = lib().fks_op_tiling(op, int(precision), C.byref(a), C.byref(b))
+def fks_op_set_tail(op, precision, max_cells):
+    st = lib().fks_op_set_tail(op, int(precision), int(max_cells))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
-    return int(a.value), int(b.value)
+
+
+def fks_op_tiling(op, precision):
+    """(fusion threshold, 16 x 16 tile threshold, tail threshold) in cells."""
+    a, b, t = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    st = lib().fks_op_tiling(op, int(precision), C.byref(a), C.byref(b), C.byref(t))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return int(a.value), int(b.value), int(t.value)
 
 
 def fks_op_autotune(op, precision, tau, stream=None):
