@@ -269,6 +269,9 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   __shared__ z64 col[GV_WARPS][MAX_M + 1];
   __shared__ z64 yv[GV_WARPS][MAX_M];
   __shared__ z64 rhs[GV_WARPS][MAX_M];
+  __shared__ z64 dg[GV_WARPS][MAX_M];      // diagonal of R (or of the square factor)
+  __shared__ double rcs[GV_WARPS][MAX_M];  // this shift's stored rotations, staged
+  __shared__ z64 rss[GV_WARPS][MAX_M];
   __shared__ z64 sc[GV_WARPS][2];   // pre (diagonal before the new rotation), g_k before it
   __shared__ double sd[GV_WARPS];   // residual estimate
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -288,13 +291,21 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   z64* rsj = rs + sj * m;
   z64* Rj = R + sj * m * m;
   z64* cl = col[warp];
+  // the new column of H_bar(sigma_j; T) and the stored rotations, loaded by all
+  // lanes at once; lane 0 then runs the dependent chain from shared memory
+  for (int i = lane; i <= k; i += 32) cl[i] = dsig * Hc[i];
+  for (int i = lane; i + 1 < k; i += 32) {
+    rcs[warp][i] = rcj[i];
+    rss[warp][i] = rsj[i];
+  }
+  __syncwarp();
+  z64* Rc = Rj + (int64_t)(k - 1) * m;
   if (lane == 0) {
-    for (int i = 0; i <= k; ++i) cl[i] = dsig * Hc[i];
     cl[k - 1] = cl[k - 1] + mk(1.0, 0.0);
     for (int i = 0; i + 1 < k; ++i) {
       z64 a = cl[i], b = cl[i + 1];
-      double c = rcj[i];
-      z64 sn = rsj[i];
+      double c = rcs[warp][i];
+      z64 sn = rss[warp][i];
       cl[i] = c * a + sn * b;
       cl[i + 1] = c * b - conj(sn) * a;
     }
@@ -315,8 +326,6 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
     }
     rcj[k - 1] = c;
     rsj[k - 1] = sn;
-    z64* Rc = Rj + (int64_t)(k - 1) * m;
-    for (int i = 0; i + 1 < k; ++i) Rc[i] = cl[i];
     Rc[k - 1] = r;
     if (k == 1) gj[0] = mk(beta, 0.0);
     z64 gk = gj[k - 1];
@@ -327,6 +336,8 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
     sd[warp] = cabs(gj[k]);
   }
   __syncwarp();
+  for (int i = lane; i + 1 < k; i += 32) Rc[i] = cl[i];  // the rotated column of R
+  __syncwarp();
   bool brk = s.breakdown != 0;
   int rmj = replay_mj ? replay_mj[sj] : 0;
   double est = sd[warp];
@@ -336,20 +347,40 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
     if (lane == 0) atomicMax(&s.rmax_next, (unsigned long long)__double_as_longlong(est / beta));
     return;
   }
-  // back substitution: R y = g (FGMRES) or the square factor (FFOM)
-  for (int i = lane; i < k; i += 32) rhs[warp][i] = gj[i];
+  // back substitution: R y = g (FGMRES) or the square factor (FFOM). The
+  // diagonal is staged first and every column of R is loaded one step ahead,
+  // so the dependent chain over i waits on arithmetic, not on memory.
+  for (int i = lane; i < k; i += 32) {
+    rhs[warp][i] = gj[i];
+    dg[warp][i] = (variant == 1 && i == k - 1) ? sc[warp][0] : Rj[(int64_t)i * m + i];
+  }
   __syncwarp();
   if (variant == 1 && lane == 0) rhs[warp][k - 1] = sc[warp][1];
   __syncwarp();
+  constexpr int RPL = MAX_M / 32;  // rows per lane
+  z64 colv[RPL], nextv[RPL];
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int l = lane + 32 * q;
+    colv[q] = l < k - 1 ? Rj[(int64_t)(k - 1) * m + l] : mk(0.0, 0.0);
+  }
   for (int i = k - 1; i >= 0; --i) {
-    if (lane == 0) {
-      z64 d = (variant == 1 && i == k - 1) ? sc[warp][0] : Rj[(int64_t)i * m + i];
-      yv[warp][i] = cdiv(rhs[warp][i], d);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int l = lane + 32 * q;
+      nextv[q] = (i > 0 && l < i - 1) ? Rj[(int64_t)(i - 1) * m + l] : mk(0.0, 0.0);
     }
+    if (lane == 0) yv[warp][i] = cdiv(rhs[warp][i], dg[warp][i]);
     __syncwarp();
     z64 yi = yv[warp][i];
-    for (int l = lane; l < i; l += 32) rhs[warp][l] = rhs[warp][l] - Rj[(int64_t)i * m + l] * yi;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int l = lane + 32 * q;
+      if (l < i) rhs[warp][l] = rhs[warp][l] - colv[q] * yi;
+    }
     __syncwarp();
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) colv[q] = nextv[q];
   }
   if (variant == 1) est = cabs(dsig) * Hc[k].re * cabs(yv[warp][k - 1]);
   double part = 0.0;
@@ -431,11 +462,23 @@ __global__ void k_tres_partial(LevelView<double> L, const z64* __restrict__ sigm
   int slot = blockIdx.z / nf, j = blockIdx.z - slot * nf;
   __shared__ double red[GX * GY / 32];
   double a = 0.0;
-  Cell p;
-  int c;
-  if (grid_cell(L.nx, L.ny, L.nz, &p, &c)) {
-    z64 r = b[slot * L.n + c] - apply_at(L, p, c, sigma[j], X + ((int64_t)slot * nf + j) * L.n);
-    a = abs2(r);
+  const z64 sg = sigma[j];
+  const z64* x = X + ((int64_t)slot * nf + j) * L.n;
+  const int i = blockIdx.x * GX + threadIdx.x;
+  const int rows = L.ny * L.nz;
+#pragma unroll
+  for (int q = 0; q < TRES_ROWS; ++q) {
+    const int row = (blockIdx.y * TRES_ROWS + q) * GY + threadIdx.y;
+    if (i >= L.nx || row >= rows) continue;
+    const int k = row / L.ny;
+    const Cell p{i, row - k * L.ny, k};
+    const int c = row * L.nx + i;
+    // b - (K + sigma M) x with the neighbour terms accumulated onto b
+    const double d = L.kd ? L.kd[c] : fsum(faces_at(L, p));
+    const double mc = L.mm[c];
+    const z64 r = defect_at(L, p, c, mk(fmaT(sg.re, mc, d), mulT(sg.im, mc)), b[slot * L.n + c], x);
+    a = fmaT(r.re, r.re, a);
+    a = fmaT(r.im, r.im, a);
   }
   a = warp_sum(a);
   int tl = thread_linear();
@@ -533,10 +576,10 @@ void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj,
   dim3 g(nbk(n, 256), nslot, nbk(nf, AS_J));
   k_assemble<<<g, 256, 0, s>>>(Z, vsZ, Y, mj, nf, m, X, n, st, skip_k_le);
 }
-int tres_blocks(const LevelHost& L) { return (int)(nbk(L.nx, GX) * nbk((int64_t)L.ny * L.nz, GY)); }
+int tres_blocks(const LevelHost& L) { return (int)(nbk(L.nx, GX) * nbk((int64_t)L.ny * L.nz, GY * TRES_ROWS)); }
 void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z64* b, const z64* X, double* partial,
                           const SlotState* st, double* out, int nslot, cudaStream_t s) {
-  dim3 g(nbk(L.nx, GX), nbk((int64_t)L.ny * L.nz, GY), nf * nslot);
+  dim3 g(nbk(L.nx, GX), nbk((int64_t)L.ny * L.nz, GY * TRES_ROWS), nf * nslot);
   k_tres_partial<<<g, dim3(GX, GY), 0, s>>>(view<double>(L), sigma, nf, b, X, partial);
   launch_tres_finish(st, partial, tres_blocks(L), nf, nslot, out, s);
 }

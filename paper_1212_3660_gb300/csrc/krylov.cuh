@@ -9,6 +9,7 @@ constexpr int MD_ROWS = 8;       // rows per thread
 constexpr int MD_COLS = 16;      // basis columns per block
 constexpr int GV_WARPS = 4;      // shifts per block of the Givens kernel
 constexpr int AS_J = 8;          // shifts per block of the assembly kernel
+constexpr int TRES_ROWS = 2;     // rows of cells per thread in the true-residual kernel
 
 int norm_blocks(int64_t n);
 int mdot_blocks(int64_t n);
