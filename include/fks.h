@@ -237,13 +237,15 @@ void fks_server_destroy(fks_server* srv);
  * operator on this GPU for every choice of which 2D levels use the fused
  * shared-memory tile kernels (levels at most `chosen` cells), which of those
  * run on 16 x 16 rather than 32 x 32 tiles and which small levels run in the
- * single-block tail kernel (256, 1024 or 4096 cells), for the cycle precision `precision`
- * and shift `tau`, and keeps the fastest in the operator for later solves.
+ * single-block tail kernel (256, 1024 or 4096 cells) or, instead of the tail,
+ * which lower levels run in the cluster kernel (fks_op_set_cluster), for the
+ * cycle precision `precision` and shift `tau`, and keeps the fastest in the
+ * operator for later solves.
  * Solves before any tuning fuse levels up to 65536 cells (complex128 cycles) or
  * all levels (complex64 cycles), use 16 x 16 tiles up to 16384 cells and a tail
- * of at most 256 cells.
+ * of at most 256 cells and no cluster kernel.
  * `chosen` (host, may be NULL) receives the fusion threshold (fks_op_tiling
- * reads both).
+ * reads all four).
  */
 fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen);
 /* Set that threshold directly (max_cells < 0: every fusable level). The fused and
@@ -260,11 +262,28 @@ fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells);
  * single-block tail kernel; FKS_ERR_ARG if their vectors do not fit in shared
  * memory. The results do not depend on it. Grid operators only. */
 fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells);
-/* The current fusion threshold, 16 x 16 tile threshold and single-block tail
- * threshold (levels of at most tail_max cells run in one block per source) of
- * `precision`; any output may be NULL. */
+/*
+ * Cluster V-cycle (Section 4's multigrid inner solve, lower levels): from the
+ * first level with at most max_cells cells down to the coarsest, the V-cycle runs
+ * in one kernel, one cluster of 8 CTAs per source. Every level of that range
+ * is split into 8 bands of rows held in the CTAs' shared memory together with
+ * the band's coefficients; rows across a band edge are read from the
+ * neighbouring CTA's shared memory and half sweeps are separated by cluster
+ * barriers. Replaces the tail kernel when on. It applies to 2D operators whose
+ * levels from there on halve in both axes, have a multiple of 8 rows (of 16
+ * where a further banded level follows) and a coarsest level of at most 64
+ * cells, and whose bands fit in 200 KB of shared memory; if the first level
+ * with at most max_cells cells does not, the next coarser one is tried.
+ * max_cells <= 0 turns it off. FKS_ERR_ARG if no level qualifies or the GPU
+ * cannot schedule the cluster. The results do not depend on it. Grid
+ * operators only.
+ */
+fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells);
+/* The current fusion threshold, 16 x 16 tile threshold, single-block tail
+ * threshold (levels of at most tail_max cells run in one block per source) and
+ * cluster threshold (0: off) of `precision`; any output may be NULL. */
 fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
-                         int64_t* tail_max);
+                         int64_t* tail_max, int64_t* cluster_max);
 
 /*
  * Allocation-free variant of fks_precond_apply (the paper has no counterpart).
@@ -307,7 +326,8 @@ enum {
   FKS_K_PRE2D = 12,    /* 2D level: four pre-smoothing half sweeps + residual + restriction */
   FKS_K_POST2D = 13,   /* 2D level: prolongation + four post-smoothing half sweeps */
   FKS_K_BICGSTAB = 14, /* CSR operators: one BiCGSTAB cycle of the inner solve    */
-  FKS_K_COUNT = 15
+  FKS_K_CLUSTER = 15,  /* the V-cycle of the lower 2D levels in one 8-CTA cluster per source */
+  FKS_K_COUNT = 16
 };
 /*
  * Time every launch of kernel class `kclass` (on level `level`, or every level

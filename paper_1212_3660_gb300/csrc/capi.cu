@@ -25,6 +25,7 @@
 #include "krylov.cuh"
 #include "csr.cuh"
 #include "assemble_tc.cuh"
+#include "cluster.cuh"
 
 namespace fks {
 
@@ -204,6 +205,9 @@ struct fks_op {
   int64_t tile16_max[2] = {16384, 16384};
   // levels with at most this many cells run in the single-block tail kernel
   int64_t tail_max[2] = {256, 256};
+  // from the first level with at most this many cells (and a cluster layout)
+  // down, the V-cycle runs in the cluster kernel instead of the tail (0: off)
+  int64_t cluster_max[2] = {0, 0};
 };
 
 namespace fks {
@@ -282,6 +286,7 @@ struct Solve {
   unsigned char* tblob = nullptr;  // tail coefficients per tau in the shared-memory layout
   size_t tblob_bytes = 0;
   int tcoef0 = 0;
+  unsigned char* cblob = nullptr;  // cluster kernel: band coefficients per tau and CTA
   bool capturing = false;  // enqueueing into a graph: no event timing
   // server batches hold this lock for their host-side CUDA calls and release it
   // only while they wait for their step-loop graph to finish
@@ -321,6 +326,32 @@ static int tail_level(const std::vector<LevelHost>& Ls, int64_t tmax) {
 
 template <typename VT>
 static int64_t tail_max_of(const fks_op* op) { return op->tail_max[sizeof(VT) == 8 ? 0 : 1]; }
+
+// First level of the cluster V-cycle for threshold cmax: the first level with
+// at most cmax cells whose cluster layout applies, else the next coarser one
+// that does; -1 when off or none applies. P / smem receive the layout.
+template <typename VT>
+static int cluster_level_for(const std::vector<LevelHost>& Ls, int64_t cmax, ClusterParams<VT>* P = nullptr,
+                             size_t* smem = nullptr) {
+  if (cmax <= 0) return -1;
+  for (size_t l = 0; l + 1 < Ls.size(); ++l) {
+    if (Ls[l].n > cmax) continue;
+    ClusterParams<VT> Q;
+    size_t sm = 0;
+    if (cluster_layout<VT>(Ls, (int)l, &Q, &sm)) {
+      if (P) *P = Q;
+      if (smem) *smem = sm;
+      return (int)l;
+    }
+  }
+  return -1;
+}
+
+template <typename VT>
+static int cluster_level(const fks_op* op, ClusterParams<VT>* P = nullptr, size_t* smem = nullptr) {
+  if (op->csr) return -1;
+  return cluster_level_for<VT>(op->levels, op->cluster_max[sizeof(VT) == 8 ? 0 : 1], P, smem);
+}
 
 constexpr size_t TAIL_SMEM_LIMIT = 220 * 1024;
 
@@ -377,7 +408,11 @@ template <typename VT>
 static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0) {
   auto& Ls = S.op->levels;
   int nl = (int)Ls.size();
-  int lt = tail_level<VT>(Ls, tail_max_of<VT>(S.op));
+  ClusterParams<VT> CP{};
+  size_t csmem = 0;
+  const int lc = cluster_level<VT>(S.op, &CP, &csmem);
+  // first level of the single-launch lower part: the cluster kernel's, else the tail's
+  int lt = lc >= 0 ? lc : tail_level<VT>(Ls, tail_max_of<VT>(S.op));
   cudaStream_t s = S.s;
   auto F = [&](int l) { return (cx<VT>*)S.f[l]; };
   auto Zl = [&](int l) { return (cx<VT>*)S.z[l]; };
@@ -410,7 +445,24 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
          launch_residual_restrict<VT>(L, Ls[l + 1], S.st, S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
                                       s));
   }
-  {
+  if (lc >= 0) {
+    // levels lc .. coarsest in one cluster per slot
+    CP.mask = S.op->mask;
+    CP.f_in = F(lc);
+    CP.z_out = Zl(lc);
+    CP.vs = Ls[lc].n;
+    CP.blob = S.cblob;
+    CP.taus = S.taus;
+    double tb = 0, tf = 0;
+    for (int l = lc; l < nl; ++l) {
+      tb += Ls[l].n * (8 * cv + d * rv);
+      tf += Ls[l].n * (8 * d + 6) * 4;
+    }
+    const int64_t nc = Ls[nl - 1].n;
+    tb += cv * nc * nc;
+    tf += 8.0 * nc * nc;
+    PROF(FKS_K_CLUSTER, lc, ns * tb, ns * tf, launch_cluster_vcycle<VT>(CP, csmem, S.st, S.nslot, s));
+  } else {
     // levels lt .. coarsest in one block per slot
     TailParams<VT> P{};
     P.nlev = nl - lt;
@@ -700,6 +752,8 @@ static void setup_levels(Solve& S) {
     std::lock_guard<std::mutex> build_lock(g_build_mu);
     tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls, tail_max_of<VT>(S.op))));
     fused_prepare<VT>();
+    size_t csm = 0;
+    if (cluster_level<VT>(S.op, nullptr, &csm) >= 0) cluster_prepare<VT>(csm);
   }
   for (size_t l = 0; l < Ls.size(); ++l)
     PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
@@ -737,6 +791,14 @@ static void setup_levels(Solve& S) {
     CK(cudaMemcpyAsync(S.cinv, S.cinv64, sizeof(z64) * S.n_tau * nc * nc, cudaMemcpyDeviceToDevice, S.s));
   } else {
     PROF(-1, -1, 0, 0, launch_to_prec<VT>(S.cinv64, (cx<VT>*)S.cinv, (int64_t)S.n_tau * nc * nc, S.s));
+  }
+  ClusterParams<VT> CP{};
+  const int lc = cluster_level<VT>(S.op, &CP);
+  if (lc >= 0) {
+    // the cluster kernel's band coefficients and coarsest inverse per tau
+    std::vector<const cx<VT>*> iv(Ls.size());
+    for (size_t l = 0; l < Ls.size(); ++l) iv[l] = (const cx<VT>*)S.invd[l];
+    PROF(-1, -1, 0, 0, launch_cluster_blob<VT>(Ls, lc, CP, iv.data(), (const cx<VT>*)S.cinv, S.n_tau, S.cblob, S.s));
   }
 }
 
@@ -783,6 +845,9 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
     S.diag64 = A.take<z64>((size_t)S.n_tau * n);
     S.tblob_bytes = tail_blob_bytes<VT>(Ls, tail_max_of<VT>(S.op), &S.tcoef0);
     S.tblob = S.tblob_bytes ? A.take<unsigned char>((size_t)S.n_tau * S.tblob_bytes) : nullptr;
+    ClusterParams<VT> CP{};
+    S.cblob = cluster_level<VT>(S.op, &CP) >= 0 ? A.take<unsigned char>((size_t)S.n_tau * CL_SIZE * CP.region)
+                                                : nullptr;
     int64_t nc = Ls.back().n;
     S.cwork = A.take<z64>((size_t)S.n_tau * nc * nc);
     S.cinv64 = A.take<z64>((size_t)S.n_tau * nc * nc);
@@ -893,7 +958,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
                                  (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
                                  (double)op->tile16_max[1], S.relax, (double)op->tail_max[0],
-                                 (double)op->tail_max[1]};
+                                 (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1]};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1433,14 +1498,53 @@ fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells) {
   return FKS_OK;
 }
 
+fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
+  if (!op) { set_error("fks_op_set_cluster: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_set_cluster: grid operators only"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_cluster: bad precision"); return FKS_ERR_ARG; }
+  const int pi = precision == FKS_PREC_FP64 ? 0 : 1;
+  if (max_cells <= 0) {
+    op->cluster_max[pi] = 0;
+    return FKS_OK;
+  }
+  size_t smem = 0;
+  bool ok;
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    if (precision == FKS_PREC_FP64) {
+      ok = cluster_level_for<double>(op->levels, max_cells, nullptr, &smem) >= 0;
+      if (ok) {
+        std::lock_guard<std::mutex> build_lock(g_build_mu);
+        ok = cluster_launchable<double>(smem);
+      }
+    } else {
+      ok = cluster_level_for<float>(op->levels, max_cells, nullptr, &smem) >= 0;
+      if (ok) {
+        std::lock_guard<std::mutex> build_lock(g_build_mu);
+        ok = cluster_launchable<float>(smem);
+      }
+    }
+  } catch (CudaError& e) {
+    set_error(std::string("fks_op_set_cluster: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return FKS_ERR_CUDA;
+  }
+  if (!ok) {
+    set_error("fks_op_set_cluster: no level qualifies for the cluster V-cycle, or its cluster cannot be scheduled");
+    return FKS_ERR_ARG;
+  }
+  op->cluster_max[pi] = max_cells;
+  return FKS_OK;
+}
+
 fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
-                         int64_t* tail_max) {
+                         int64_t* tail_max, int64_t* cluster_max) {
   if (!op) { set_error("fks_op_tiling: NULL operator"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_tiling: bad precision"); return FKS_ERR_ARG; }
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   if (fuse_max) *fuse_max = op->fuse_max[pi];
   if (tile16_max) *tile16_max = op->tile16_max[pi];
   if (tail_max) *tail_max = op->tail_max[pi];
+  if (cluster_max) *cluster_max = op->cluster_max[pi];
   return FKS_OK;
 }
 
@@ -1452,6 +1556,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi], savedt = op->tail_max[pi];
+  int64_t savedc = op->cluster_max[pi];
   try {
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
@@ -1495,20 +1600,42 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       double best = 1e30;
-      int64_t pick = saved, pick16 = saved16, pickt = savedt;
-      struct Choice { int64_t fuse, t16, tail; };
+      int64_t pick = saved, pick16 = saved16, pickt = savedt, pickc = savedc;
+      struct Choice { int64_t fuse, t16, tail, cl; };
       std::vector<Choice> choices;
+      // fusion choices for the levels above the single-launch lower part
+      // starting at level ls (thresholds below those levels' sizes are all "none")
+      auto add = [&](int ls, int64_t tm, int64_t cm) {
+        std::vector<int64_t> cs = {0};
+        for (int64_t c : cand)
+          if (c > op->levels[ls].n) cs.push_back(c);
+        for (int64_t c : cs)
+          for (int64_t t : cs)
+            if (t <= c) choices.push_back({c, t, tm, cm});
+      };
       for (int64_t tm : {int64_t(256), int64_t(1024), int64_t(4096)}) {
         const int lt = tail_level<VT>(op->levels, tm);
         if (tail_smem<VT>(op->levels, lt) > TAIL_SMEM_LIMIT) continue;  // f and z must fit
-        for (int64_t c : cand)
-          for (int64_t t : cand)
-            if (t <= c) choices.push_back({c, t, tm});
+        add(lt, tm, 0);
+      }
+      // the cluster kernel from every level where it applies, down to 1024 cells
+      for (size_t l = 0; l + 1 < op->levels.size(); ++l) {
+        const int64_t cm = op->levels[l].n;
+        if (cm < 1024) break;
+        size_t csm = 0;
+        if (cluster_level_for<VT>(op->levels, cm, nullptr, &csm) != (int)l) continue;
+        bool ok;
+        {
+          std::lock_guard<std::mutex> build_lock(g_build_mu);
+          ok = cluster_launchable<VT>(csm);
+        }
+        if (ok) add((int)l, savedt, cm);
       }
       for (const Choice& ch : choices) {
         op->fuse_max[pi] = ch.fuse;
         op->tile16_max[pi] = ch.t16;
         op->tail_max[pi] = ch.tail;
+        op->cluster_max[pi] = ch.cl;
         {
           // the tail's shared memory and coefficient blob follow the threshold
           std::lock_guard<std::mutex> build_lock(g_build_mu);
@@ -1549,6 +1676,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
           pick = ch.fuse;
           pick16 = ch.t16;
           pickt = ch.tail;
+          pickc = ch.cl;
         }
       }
       cudaEventDestroy(e0);
@@ -1557,6 +1685,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       op->fuse_max[pi] = pick;
       op->tile16_max[pi] = pick16;
       op->tail_max[pi] = pickt;
+      op->cluster_max[pi] = pickc;
     };
     if (precision == FKS_PREC_FP64) run(double{});
     else run(float{});
@@ -1564,6 +1693,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
     op->fuse_max[pi] = saved;
     op->tile16_max[pi] = saved16;
     op->tail_max[pi] = savedt;
+    op->cluster_max[pi] = savedc;
     set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
   }

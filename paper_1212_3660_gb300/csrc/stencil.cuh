@@ -170,9 +170,10 @@ __device__ __forceinline__ cx<T> restrict_value(const LevelView<T>& F, int rx, i
 // Per coarsened axis: 3/4 on the parent, 1/4 on the coarse neighbour on the
 // child's side; past a zero-head face the ghost is -parent (weight 1/2 on the
 // parent), past a no-flow face +parent (weight 1).
-template <typename T>
-__device__ __forceinline__ cx<T> prolong_value(Cell p, int rx, int ry, int rz, int cnx, int cny, int cnz,
-                                               uint32_t mask, const cx<T>* zc) {
+// get(X, Y, Z) returns the coarse value at coarse cell (X, Y, Z).
+template <typename T, typename Get>
+__device__ __forceinline__ cx<T> prolong_value_at(Cell p, int rx, int ry, int rz, int cnx, int cny, int cnz,
+                                                  uint32_t mask, Get get) {
   int par[3] = {p.i / rx, p.j / ry, p.k / rz};
   int idx[3] = {p.i, p.j, p.k};
   int rr[3] = {rx, ry, rz};
@@ -212,12 +213,19 @@ __device__ __forceinline__ cx<T> prolong_value(Cell p, int rx, int ry, int rz, i
       for (int a = 0; a < 2; ++a) {
         T wx = tw[0][a];
         if (wx == T(0)) continue;
-        int64_t cc = ((int64_t)ti[2][c2] * cny + ti[1][b]) * cnx + ti[0][a];
-        acc = axpy(mulT(mulT(wx, wy), wz), zc[cc], acc);
+        acc = axpy(mulT(mulT(wx, wy), wz), get(ti[0][a], ti[1][b], ti[2][c2]), acc);
       }
     }
   }
   return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> prolong_value(Cell p, int rx, int ry, int rz, int cnx, int cny, int cnz,
+                                               uint32_t mask, const cx<T>* zc) {
+  return prolong_value_at<T>(p, rx, ry, rz, cnx, cny, cnz, mask, [&](int X, int Y, int Z) {
+    return zc[((int64_t)Z * cny + Y) * cnx + X];
+  });
 }
 
 }  // namespace fks

@@ -204,6 +204,56 @@ def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
 
 
 @pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+@pytest.mark.parametrize("shape,n_src", [((64, 80), 1), ((256, 256), 3)])
+def test_cluster_vcycle_agrees_bitwise(precision, shape, n_src):
+    """The cluster kernel (lower levels as bands of rows in the shared memory of
+    an 8-CTA cluster) updates every cell with the operations of the per-level
+    kernels in the same order: the same bits from every starting level. 64 x 80
+    ends on a 4 x 5 coarsest level (odd rows on the last banded level, a single
+    banded level when started there); 256 x 256 with three sources."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=5, periods=(5.0, 3600.0), n_p=3, seed=31, n_src=n_src, m_max=60)
+    s = Solver(pr)
+    a = s.solve(precision=precision, inner_tol=1e-10)
+    assert fks.fks_op_tiling(s.op, precision)[3] == 0
+    starts = set()
+    for cmax in (1 << 40, 4096, 1024, 256, 80, 64):
+        try:
+            fks.fks_op_set_cluster(s.op, precision, cmax)
+        except fks.FksError:
+            continue
+        assert fks.fks_op_tiling(s.op, precision)[3] == cmax
+        d = s.solve(precision=precision, inner_tol=1e-10)
+        assert np.array_equal(a.X, d.X), cmax
+        assert np.array_equal(a.inner_cycles, d.inner_cycles) and np.array_equal(a.m_j, d.m_j)
+        starts.add(cmax)
+    assert len(starts) >= 3, starts
+    # host-driven loop, and the tuner's pick
+    fks.fks_op_set_cluster(s.op, precision, 1024)
+    h = s.solve(precision=precision, inner_tol=1e-10, launch_mode=1)
+    assert np.array_equal(a.X, h.X)
+    fks.fks_op_autotune(s.op, precision, pr.tau_bar[1])
+    c = s.solve(precision=precision, inner_tol=1e-10)
+    assert np.array_equal(a.X, c.X), fks.fks_op_tiling(s.op, precision)
+    fks.fks_op_set_cluster(s.op, precision, 0)
+    assert fks.fks_op_tiling(s.op, precision)[3] == 0
+    s.close()
+
+
+def test_cluster_vcycle_rejects_inapplicable_levels():
+    """48 x 48 coarsens to 24 x 24 (3 rows per band, followed by a 12-row level
+    that does not split into 8 bands): no starting level qualifies."""
+    need_gpu()
+    pr = synth.make_problem((48, 48), n_f=3, periods=(5.0, 3600.0), n_p=2, seed=32, m_max=40)
+    s = Solver(pr)
+    for prec in (fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED):
+        with pytest.raises(fks.FksError):
+            fks.fks_op_set_cluster(s.op, prec, 1 << 40)
+        assert fks.fks_op_tiling(s.op, prec)[3] == 0
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
 def test_relaxed_inner_tolerance(precision):
     """Relaxed inner tolerances: every shift is still certified (the true
     residual, recomputed by the oracle, within the bound and tol), the inner
