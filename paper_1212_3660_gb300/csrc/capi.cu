@@ -386,6 +386,25 @@ static size_t tail_smem(const std::vector<LevelHost>& Ls, int lt) {
   return tail_layout<VT>(Ls, lt, tail_staged<VT>(Ls, lt), nullptr);
 }
 
+// Shared memory of the tail launch from level lt; *pairs = 1 when it is the
+// register-resident 2D kernel (coefficients staged, the levels qualify and the
+// coarsest inverse, staged at *ainv_off, fits as well).
+template <typename VT>
+static size_t tail_launch_smem(const std::vector<LevelHost>& Ls, int lt, int* pairs = nullptr,
+                               int* ainv_off = nullptr) {
+  const size_t b = tail_smem<VT>(Ls, lt);
+  if (pairs) *pairs = 0;
+  if (ainv_off) *ainv_off = 0;
+  if (!tail_staged<VT>(Ls, lt) || !tail2d_ok(Ls, lt)) return b;
+  const size_t nc = (size_t)Ls.back().n;
+  const size_t a = (b + 15) & ~(size_t)15;
+  const size_t b2 = a + nc * nc * sizeof(cx<VT>);
+  if (b2 > TAIL_SMEM_LIMIT) return b;
+  if (pairs) *pairs = 1;
+  if (ainv_off) *ainv_off = (int)a;
+  return b2;
+}
+
 // Bytes per tau of the tail's staged coefficients and their shared-memory
 // offset (0 bytes when the tail reads its coefficients from global memory).
 template <typename VT>
@@ -495,7 +514,9 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
     P.coef0 = S.tcoef0;
     tb += cv * C.n * C.n;
     tf += 8.0 * C.n * C.n;
-    PROF(FKS_K_TAIL, lt, ns * tb, ns * tf, launch_tail<VT>(P, tail_smem<VT>(Ls, lt), S.st, S.nslot, s));
+    const size_t tsm = tail_launch_smem<VT>(Ls, lt, &P.pairs, &P.ainv_off);
+    if (!P.blob) P.pairs = 0;
+    PROF(FKS_K_TAIL, lt, ns * tb, ns * tf, launch_tail<VT>(P, tsm, S.st, S.nslot, s));
   }
   cx<VT>* zfin = Zl(lt);  // final correction of the level below
   for (int l = lt - 1; l >= 0; --l) {
@@ -750,7 +771,7 @@ static void setup_levels(Solve& S) {
   auto& Ls = S.op->levels;
   {
     std::lock_guard<std::mutex> build_lock(g_build_mu);
-    tail_prepare<VT>(tail_smem<VT>(Ls, tail_level<VT>(Ls, tail_max_of<VT>(S.op))));
+    tail_prepare<VT>(tail_launch_smem<VT>(Ls, tail_level<VT>(Ls, tail_max_of<VT>(S.op))));
     fused_prepare<VT>();
     size_t csm = 0;
     if (cluster_level<VT>(S.op, nullptr, &csm) >= 0) cluster_prepare<VT>(csm);
@@ -1639,7 +1660,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
         {
           // the tail's shared memory and coefficient blob follow the threshold
           std::lock_guard<std::mutex> build_lock(g_build_mu);
-          tail_prepare<VT>(tail_smem<VT>(op->levels, tail_level<VT>(op->levels, ch.tail)));
+          tail_prepare<VT>(tail_launch_smem<VT>(op->levels, tail_level<VT>(op->levels, ch.tail)));
         }
         Arena probe2;
         carve<VT>(S, probe2, false);

@@ -64,7 +64,7 @@ bool cluster_layout(const std::vector<LevelHost>& Ls, int l0, ClusterParams<T>* 
   Q.zC = (int)off;
   off = al16(off + (size_t)Q.nc * c);
   // residuals of the last banded level (its restriction crosses bands)
-  const ClLevel& last = Q.lev[nlev - 1];
+  const ClLevel last = Q.lev[nlev - 1];
   Q.rs = (int)off;
   off = al16(off + (size_t)last.R * last.nx * c);
   Q.coef0 = (int)off;
@@ -104,7 +104,7 @@ __global__ void k_cluster_blob(ClusterParams<T> P, ClBlobArgs<T> A, unsigned cha
   const int b = blockIdx.x, q = blockIdx.y;
   unsigned char* dst = blob + ((size_t)q * CL_SIZE + b) * P.region;  // shared offset o -> dst + (o - coef0)
   for (int l = 0; l < P.nlev; ++l) {
-    const ClLevel& L = P.lev[l];
+    const ClLevel L = P.lev[l];
     T* fx = (T*)(dst + (L.fx - P.coef0));
     T* fy = (T*)(dst + (L.fy - P.coef0));
     T* mm = (T*)(dst + (L.mm - P.coef0));
@@ -122,7 +122,7 @@ __global__ void k_cluster_blob(ClusterParams<T> P, ClBlobArgs<T> A, unsigned cha
 }
 
 template <typename T>
-__global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
+__global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 1)
     k_cluster_vcycle(ClusterParams<T> P, const SlotState* st) {
   cg::cluster_group cl = cg::this_cluster();
   const int b = (int)cl.block_rank();
@@ -136,7 +136,7 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
     const uint4* src = (const uint4*)(P.blob + ((size_t)tau * CL_SIZE + b) * P.region);
     uint4* dst = (uint4*)(csm + P.coef0);
     for (int q = tid; q < P.region / 16; q += nt) dst[q] = src[q];
-    const ClLevel& A = P.lev[0];
+    const ClLevel A = P.lev[0];
     cx<T>* F = (cx<T>*)(csm + A.f);
     const cx<T>* fin = P.f_in + slot * P.vs + (int64_t)b * A.R * A.nx;
     for (int q = tid; q < A.R * A.nx; q += nt) F[q] = fin[q];
@@ -145,12 +145,12 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
 
   // z of the row just above (below) this band at level A: the last (first) row
   // of the neighbouring CTA's band
-  auto zrow = [&](const ClLevel& A, cx<T>* Z, int lj, int i) -> cx<T> {
+  auto zrow = [&](const ClLevel A, cx<T>* Z, int lj, int i) -> cx<T> {
     if (lj < 0) return cl.map_shared_rank(Z, b - 1)[(A.R - 1) * A.nx + i];
     if (lj >= A.R) return cl.map_shared_rank(Z, b + 1)[i];
     return Z[lj * A.nx + i];
   };
-  auto sweep = [&](const ClLevel& A, int color, int zs) {
+  auto sweep = [&](const ClLevel A, int color, int zs) {
     const cx<T>* F = (const cx<T>*)(csm + A.f);
     cx<T>* Z = (cx<T>*)(csm + A.z);
     const T* FX = (const T*)(csm + A.fx);
@@ -177,7 +177,7 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
     cl.sync();
   };
   // f - (K + tau M) z at local cell (i, lj) of level A
-  auto residual = [&](const ClLevel& A, int i, int lj) -> cx<T> {
+  auto residual = [&](const ClLevel A, int i, int lj) -> cx<T> {
     const cx<T>* F = (const cx<T>*)(csm + A.f);
     cx<T>* Z = (cx<T>*)(csm + A.z);
     const T* FX = (const T*)(csm + A.fx);
@@ -203,14 +203,14 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
 
   // ---- down: smoothing and restriction on the banded levels
   for (int li = 0; li < P.nlev; ++li) {
-    const ClLevel& A = P.lev[li];
+    const ClLevel A = P.lev[li];
     for (int r = 0; r < 2; ++r) {
       sweep(A, 0, r == 0);
       sweep(A, 1, 0);
     }
     const int cnx = A.nx / 2;
     if (li + 1 < P.nlev) {
-      const ClLevel& B = P.lev[li + 1];
+      const ClLevel B = P.lev[li + 1];
       cx<T>* FN = (cx<T>*)(csm + B.f);
       for (int t = tid; t < B.R * cnx; t += nt) {
         const int lJ = t / cnx, I = t - lJ * cnx;
@@ -258,10 +258,10 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
 
   // ---- up: prolongation and smoothing
   for (int li = P.nlev - 1; li >= 0; --li) {
-    const ClLevel& A = P.lev[li];
+    const ClLevel A = P.lev[li];
     cx<T>* Z = (cx<T>*)(csm + A.z);
     if (li + 1 < P.nlev) {
-      const ClLevel& B = P.lev[li + 1];
+      const ClLevel B = P.lev[li + 1];
       cx<T>* ZB = (cx<T>*)(csm + B.z);
       auto get = [&](int X, int Y, int) -> cx<T> { return zrow(B, ZB, Y - b * B.R, X); };
       for (int t = tid; t < A.R * A.nx; t += nt) {
@@ -283,7 +283,7 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
     }
   }
   {
-    const ClLevel& A = P.lev[0];
+    const ClLevel A = P.lev[0];
     const cx<T>* Z = (const cx<T>*)(csm + A.z);
     cx<T>* zo = P.z_out + slot * P.vs + (int64_t)b * A.R * A.nx;
     for (int q = tid; q < A.R * A.nx; q += nt) zo[q] = Z[q];

@@ -253,7 +253,7 @@ __device__ __forceinline__ cx<T> nb_sum_tile(const LevelView<T>& L, Cell p, int 
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256) k_pre2d(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (TX == 16 ? 8 : 6) : 4) k_pre2d(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
                                                const z64* taus, const cx<T>* __restrict__ f, cx<T>* __restrict__ z,
                                                int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
   constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(256) k_pre2d(LevelView<T> L, const SlotState* 
     int X = blockIdx.x * (TX / 2) + Xl, Y = blockIdx.y * (TY / 2) + Yl;
     if (X >= cnx || Y >= cny) continue;
     cx<T> acc = mk(T(0), T(0));
+#pragma unroll 1
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         int gx = 2 * X + a, gy = 2 * Y + b;
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, c
 // coefficients read through the cache. Same operations, in the same order, as
 // the per-level kernels.
 template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, const SlotState* st) {
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail_vcycle(TailParams<T> P, const SlotState* st) {
   int slot = blockIdx.x;
   if (!slot_running(st, slot)) return;
   extern __shared__ __align__(16) unsigned char tail_smem[];
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
   }
   __syncthreads();
   auto sweep = [&](int l, int color, int zs) {
-    const LevelView<T>& L = SV[l];
+    const LevelView<T> L = SV[l];  // a register copy: the loop's shared-memory stores cannot alias it
     cx<T>* F = sh + P.lev[l].off;
     cx<T>* Z = F + L.n;
     const cx<T>* ID = SI[l];
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
     cx<T>* F = sh + A.off;
     cx<T>* Z = F + A.L.n;
     cx<T>* FC = sh + B.off;
-    const LevelView<T>& LA = SV[l];
+    const LevelView<T> LA = SV[l];
     for (int C = tid; C < B.L.n; C += nt) {
       Cell pc = cell_of(C, B.L.nx, B.L.ny);
       FC[C] = restrict_value(LA, A.rx, A.ry, A.rz, pc.i, pc.j, pc.k, sft, F, Z);
@@ -535,6 +536,226 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_tail_vcycle(TailParams<T> P, c
     const cx<T>* Z = sh + A.off + A.L.n;
     for (int c = tid; c < A.L.n; c += nt) zout[c] = Z[c];
   }
+}
+
+// --------------------------------------------------------------------- 2D tail
+// The tail V-cycle for 2D levels halved in both axes, with the cells of every
+// level owned in horizontal pairs: thread t owns cells 2t and 2t + 1 of the
+// level it is on (one red, one black, as nx is even), and keeps their faces,
+// storage, inverse diagonals, right-hand sides and iterates in registers for
+// the whole visit of the level; only the iterates go through shared memory,
+// for the neighbours. Each cell update performs the operations of gs_value,
+// restrict_value and prolong_value in the same order as k_tail_vcycle.
+template <typename T>
+struct TailPair {
+  int i0, j, c0;
+  bool own;
+  T fxa, fxb, fxc;           // x faces left of c0, between, right of c1
+  T yl0, yh0, yl1, yh1;      // y faces of c0 and c1
+  T m0, m1;
+  cx<T> id0, id1, f0, f1, z0, z1;
+};
+
+template <typename T>
+__device__ __forceinline__ void tail2d_load(const TailLevel<T>& A, const unsigned char* smem, const cx<T>* F, int t,
+                                            int tau, TailPair<T>& q) {
+  const int nx = A.L.nx, ny = A.L.ny;
+  const int n = nx * ny;
+  q.own = 2 * t < n;
+  if (!q.own) return;
+  q.c0 = 2 * t;
+  q.j = q.c0 / nx;
+  q.i0 = q.c0 - q.j * nx;
+  const int nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
+  const T* fx = (const T*)(smem + A.cbyte);
+  const T* fy = fx + nfx;
+  const T* mm = fy + nfy;
+  const cx<T>* id = (const cx<T>*)(fx + ((nfx + nfy + n + 3) & ~3));
+  const int rx = q.j * (nx + 1) + q.i0;
+  q.fxa = fx[rx];
+  q.fxb = fx[rx + 1];
+  q.fxc = fx[rx + 2];
+  q.yl0 = fy[q.c0];
+  q.yl1 = fy[q.c0 + 1];
+  q.yh0 = fy[q.c0 + nx];
+  q.yh1 = fy[q.c0 + nx + 1];
+  q.m0 = mm[q.c0];
+  q.m1 = mm[q.c0 + 1];
+  q.id0 = id[q.c0];
+  q.id1 = id[q.c0 + 1];
+  q.f0 = F[q.c0];
+  q.f1 = F[q.c0 + 1];
+  (void)tau;
+}
+
+// half sweep of `color` on the owned cell of that colour
+template <typename T>
+__device__ __forceinline__ void tail2d_gs(TailPair<T>& q, int nx, int ny, cx<T>* Z, int color, int zs) {
+  if (!q.own) return;
+  const bool first = ((q.j & 1) == color);  // c0 = (i0 even, j) has colour j & 1
+  if (first) {
+    cx<T> rhs = q.f0;
+    if (!zs) {
+      if (q.i0 > 0) rhs = axpy(q.fxa, Z[q.c0 - 1], rhs);
+      rhs = axpy(q.fxb, q.z1, rhs);
+      if (q.j > 0) rhs = axpy(q.yl0, Z[q.c0 - nx], rhs);
+      if (q.j < ny - 1) rhs = axpy(q.yh0, Z[q.c0 + nx], rhs);
+    }
+    q.z0 = q.id0 * rhs;
+    Z[q.c0] = q.z0;
+  } else {
+    cx<T> rhs = q.f1;
+    if (!zs) {
+      rhs = axpy(q.fxb, q.z0, rhs);
+      if (q.i0 + 1 < nx - 1) rhs = axpy(q.fxc, Z[q.c0 + 2], rhs);
+      if (q.j > 0) rhs = axpy(q.yl1, Z[q.c0 + 1 - nx], rhs);
+      if (q.j < ny - 1) rhs = axpy(q.yh1, Z[q.c0 + 1 + nx], rhs);
+    }
+    q.z1 = q.id1 * rhs;
+    Z[q.c0 + 1] = q.z1;
+  }
+}
+
+// f - (K + s M) z on the two owned cells (apply_at with d the sum of the faces)
+template <typename T>
+__device__ __forceinline__ void tail2d_residual(const TailPair<T>& q, int nx, int ny, const cx<T>* Z, cx<T> s,
+                                                cx<T>* r0, cx<T>* r1) {
+  const T zero = T(0);
+  {
+    Faces<T> fa{q.fxa, q.fxb, q.yl0, q.yh0, zero, zero};
+    const T d = fsum(fa);
+    cx<T> nb = mk(zero, zero);
+    if (q.i0 > 0) nb = axpy(q.fxa, Z[q.c0 - 1], nb);
+    nb = axpy(q.fxb, q.z1, nb);
+    if (q.j > 0) nb = axpy(q.yl0, Z[q.c0 - nx], nb);
+    if (q.j < ny - 1) nb = axpy(q.yh0, Z[q.c0 + nx], nb);
+    *r0 = q.f0 - (mk(fmaT(s.re, q.m0, d), mulT(s.im, q.m0)) * q.z0 - nb);
+  }
+  {
+    Faces<T> fa{q.fxb, q.fxc, q.yl1, q.yh1, zero, zero};
+    const T d = fsum(fa);
+    cx<T> nb = mk(zero, zero);
+    nb = axpy(q.fxb, q.z0, nb);
+    if (q.i0 + 1 < nx - 1) nb = axpy(q.fxc, Z[q.c0 + 2], nb);
+    if (q.j > 0) nb = axpy(q.yl1, Z[q.c0 + 1 - nx], nb);
+    if (q.j < ny - 1) nb = axpy(q.yh1, Z[q.c0 + 1 + nx], nb);
+    *r1 = q.f1 - (mk(fmaT(s.re, q.m1, d), mulT(s.im, q.m1)) * q.z1 - nb);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail2d(TailParams<T> P, const SlotState* st) {
+  const int slot = blockIdx.x;
+  if (!slot_running(st, slot)) return;
+  extern __shared__ __align__(16) unsigned char t2_smem[];
+  cx<T>* sh = (cx<T>*)t2_smem;
+  const int tau = st[slot].tau;
+  const cx<T> sft = cvt<T>(P.taus[tau]);
+  const int nt = blockDim.x, tid = threadIdx.x;
+  {
+    const uint4* src = (const uint4*)(P.blob + (size_t)tau * P.blob_bytes);
+    uint4* dst = (uint4*)(t2_smem + P.coef0);
+    for (int q = tid; q < P.blob_bytes / 16; q += nt) dst[q] = src[q];
+    const cx<T>* ag = P.Ainv + (int64_t)tau * P.nc * P.nc;
+    cx<T>* as = (cx<T>*)(t2_smem + P.ainv_off);
+    for (int q = tid; q < P.nc * P.nc; q += nt) as[q] = ag[q];
+    const TailLevel<T>& A = P.lev[0];
+    const cx<T>* fin = P.f_in + slot * P.vs;
+    for (int c = tid; c < A.L.n; c += nt) sh[A.off + c] = fin[c];
+  }
+  __syncthreads();
+  TailPair<T> q;
+  // ---- down
+  for (int l = 0; l + 1 < P.nlev; ++l) {
+    const TailLevel<T>& A = P.lev[l];
+    const TailLevel<T>& B = P.lev[l + 1];
+    const int nx = A.L.nx, ny = A.L.ny;
+    cx<T>* F = sh + A.off;
+    cx<T>* Z = F + A.L.n;
+    tail2d_load(A, t2_smem, F, tid, tau, q);
+    for (int r = 0; r < 2; ++r) {
+      tail2d_gs(q, nx, ny, Z, 0, r == 0);
+      __syncthreads();
+      tail2d_gs(q, nx, ny, Z, 1, 0);
+      __syncthreads();
+    }
+    // restriction: the pair in row 2J sums its two residuals, the pair in
+    // row 2J + 1 adds its own onto that (the child order of restrict_value)
+    const int cnx = B.L.nx;
+    cx<T>* FC = sh + B.off;
+    cx<T>* S = FC + B.L.n;  // the coarse iterate's storage, free until its first sweep
+    cx<T> r0, r1;
+    if (q.own) {
+      tail2d_residual(q, nx, ny, Z, sft, &r0, &r1);
+      if ((q.j & 1) == 0) S[(q.j >> 1) * cnx + (q.i0 >> 1)] = (mk(T(0), T(0)) + r0) + r1;
+    }
+    __syncthreads();
+    if (q.own && (q.j & 1)) {
+      const int C = (q.j >> 1) * cnx + (q.i0 >> 1);
+      FC[C] = (S[C] + r0) + r1;
+    }
+    __syncthreads();
+  }
+  {
+    const TailLevel<T>& Cl = P.lev[P.nlev - 1];
+    const cx<T>* F = sh + Cl.off;
+    cx<T>* Z = sh + Cl.off + Cl.L.n;
+    const cx<T>* Ainv = (const cx<T>*)(t2_smem + P.ainv_off);
+    for (int r = tid; r < P.nc; r += nt) {
+      cx<T> acc = mk(T(0), T(0));
+      const cx<T>* row = Ainv + r * P.nc;
+      for (int l = 0; l < P.nc; ++l) acc = acc + row[l] * F[l];
+      Z[r] = acc;
+    }
+    __syncthreads();
+  }
+  if (P.nlev == 1) {
+    const TailLevel<T>& A = P.lev[0];
+    cx<T>* zout = P.z_out + slot * P.vs;
+    const cx<T>* Z = sh + A.off + A.L.n;
+    for (int c = tid; c < A.L.n; c += nt) zout[c] = Z[c];
+    return;
+  }
+  // ---- up
+  for (int l = P.nlev - 2; l >= 0; --l) {
+    const TailLevel<T>& A = P.lev[l];
+    const TailLevel<T>& B = P.lev[l + 1];
+    const int nx = A.L.nx, ny = A.L.ny;
+    cx<T>* F = sh + A.off;
+    cx<T>* Z = F + A.L.n;
+    const cx<T>* ZC = sh + B.off + B.L.n;
+    const int cnx = B.L.nx, cny = B.L.ny;
+    tail2d_load(A, t2_smem, F, tid, tau, q);
+    if (q.own) {
+      auto get = [&](int X, int Y, int) { return ZC[Y * cnx + X]; };
+      q.z0 = Z[q.c0] + prolong_value_at<T>(Cell{q.i0, q.j, 0}, 2, 2, 1, cnx, cny, 1, P.mask, get);
+      q.z1 = Z[q.c0 + 1] + prolong_value_at<T>(Cell{q.i0 + 1, q.j, 0}, 2, 2, 1, cnx, cny, 1, P.mask, get);
+      Z[q.c0] = q.z0;
+      Z[q.c0 + 1] = q.z1;
+    }
+    __syncthreads();
+    for (int r = 0; r < 2; ++r) {
+      tail2d_gs(q, nx, ny, Z, 1, 0);
+      __syncthreads();
+      tail2d_gs(q, nx, ny, Z, 0, 0);
+      __syncthreads();
+    }
+  }
+  if (q.own) {
+    cx<T>* zout = P.z_out + slot * P.vs;
+    zout[q.c0] = q.z0;
+    zout[q.c0 + 1] = q.z1;
+  }
+}
+
+bool tail2d_ok(const std::vector<LevelHost>& Ls, int lt) {
+  const int nl = (int)Ls.size();
+  if (Ls[nl - 1].nz != 1) return false;
+  for (int l = lt; l + 1 < nl; ++l) {
+    const LevelHost& A = Ls[l];
+    if (A.nz != 1 || A.rx != 2 || A.ry != 2 || A.n > 2 * TAIL_THREADS) return false;
+  }
+  return true;
 }
 
 // --------------------------------------------------------------------- coarsest
@@ -953,11 +1174,15 @@ void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const 
 template <typename T>
 void tail_prepare(size_t smem_bytes) {
   cudaFuncSetAttribute(k_tail_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  cudaFuncSetAttribute(k_tail2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s) {
-  k_tail_vcycle<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
+  if (P.pairs)
+    k_tail2d<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
+  else
+    k_tail_vcycle<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
 }
 
 template <typename T>

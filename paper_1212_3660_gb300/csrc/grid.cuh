@@ -32,6 +32,11 @@ struct TailParams {
   const unsigned char* blob;  // staged coefficients per tau, already in the shared-memory layout (or null)
   int blob_bytes;          // bytes per tau (multiple of 16)
   int coef0;               // shared-memory byte offset of the coefficient region
+  // register-resident 2D variant (tail2d_ok): every level but the coarsest is 2D,
+  // halved in both axes and has at most 2 * TAIL_THREADS cells; the coarsest
+  // inverse of the current tau is staged at shared byte offset ainv_off
+  int pairs;
+  int ainv_off;
 };
 
 template <typename T>
@@ -49,8 +54,11 @@ template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
                    bool small, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0);
+// P.pairs selects the register-resident 2D kernel (same results)
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);
+// whether levels lt .. coarsest qualify for the register-resident 2D tail
+bool tail2d_ok(const std::vector<LevelHost>& Ls, int lt);
 
 void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond, cudaStream_t s);
 void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s);

@@ -240,6 +240,31 @@ def test_cluster_vcycle_agrees_bitwise(precision, shape, n_src):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+@pytest.mark.parametrize("shape,n_src", [((64, 80), 2), ((128, 128), 3)])
+def test_tail_kernels_agree_bitwise(precision, shape, n_src):
+    """The single-block tail in its register-resident 2D form (levels of at
+    most 1024 cells, cells owned in pairs), in its general form (a 4096-cell
+    level) and the per-level kernels with only the coarsest level in the tail
+    give the same bits."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=5, periods=(5.0, 3600.0), n_p=3, seed=33, n_src=n_src, m_max=60)
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, -1)
+    fks.fks_op_set_tail(s.op, precision, 1)       # the coarsest level alone
+    a = s.solve(precision=precision, inner_tol=1e-10)
+    for tail in (80, 320, 1024, 4096):
+        fks.fks_op_set_tail(s.op, precision, tail)
+        d = s.solve(precision=precision, inner_tol=1e-10)
+        assert np.array_equal(a.X, d.X), tail
+        assert np.array_equal(a.inner_cycles, d.inner_cycles), tail
+    fks.fks_op_set_fusion(s.op, precision, 0)     # per-sweep kernels above the tail
+    fks.fks_op_set_tail(s.op, precision, 1024)
+    d = s.solve(precision=precision, inner_tol=1e-10)
+    assert np.array_equal(a.X, d.X)
+    s.close()
+
+
 def test_cluster_vcycle_rejects_inapplicable_levels():
     """48 x 48 coarsens to 24 x 24 (3 rows per band, followed by a 12-row level
     that does not split into 8 bands): no starting level qualifies."""
