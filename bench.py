@@ -73,6 +73,8 @@ def parse():
                     help="with --fuse-max: fused levels up to this many cells on 16 x 16 tiles (-1: all)")
     ap.add_argument("--tail-max", type=int, default=None,
                     help="with --fuse-max: levels up to this many cells in the single-block tail kernel")
+    ap.add_argument("--tile8-max", type=int, default=None,
+                    help="with --fuse-max: fused levels up to this many cells on 8 x 8 tiles (-1: all)")
     ap.add_argument("--cluster-max", type=int, default=None,
                     help="with --fuse-max: from the first level of at most this many cells down, the cluster "
                          "V-cycle kernel (0: off)")
@@ -483,6 +485,8 @@ def main():
             fks.fks_op_set_tail(solver.op, prec, args.tail_max)
         if args.cluster_max is not None:
             fks.fks_op_set_cluster(solver.op, prec, args.cluster_max)
+        if args.tile8_max is not None:
+            fks.fks_op_set_tiles8(solver.op, prec, args.tile8_max)
     if args.single:
         st = step(b_d, X_d)
         torch.cuda.synchronize()
@@ -661,6 +665,7 @@ def main():
                            "tile16_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[1],
                            "tail_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[2],
                            "cluster_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[3],
+                           "tile8_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[4],
                            "launch_mode": args.launch_mode},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": e2e, "comparison": comparison,

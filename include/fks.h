@@ -237,10 +237,11 @@ void fks_server_destroy(fks_server* srv);
  * operator on this GPU for every choice of which 2D levels use the fused
  * shared-memory tile kernels (levels at most `chosen` cells), which of those
  * run on 16 x 16 rather than 32 x 32 tiles and which small levels run in the
- * single-block tail kernel (256, 1024 or 4096 cells) or, instead of the tail,
+ * single-block tail kernel (64, 256, 1024 or 4096 cells) or, instead of the tail,
  * which lower levels run in the cluster kernel (fks_op_set_cluster), for the
  * cycle precision `precision` and shift `tau`, and keeps the fastest in the
- * operator for later solves.
+ * operator for later solves; then, for that choice, which of the smallest fused
+ * levels run on 8 x 8 tiles.
  * Solves before any tuning fuse levels up to 65536 cells (complex128 cycles) or
  * all levels (complex64 cycles), use 16 x 16 tiles up to 16384 cells and a tail
  * of at most 256 cells and no cluster kernel.
@@ -258,6 +259,10 @@ fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells);
  * fks_op_autotune picks it together with the fusion threshold. Grid operators only.
  */
 fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells);
+/* Fused 2D levels with at most max_cells cells run on 8 x 8 tiles (before the
+ * 16 x 16 rule; < 0: all, 0: none): more CTAs on small levels, at more
+ * recomputed halo. The tiling does not change results. Grid operators only. */
+fks_status fks_op_set_tiles8(fks_op* op, int precision, int64_t max_cells);
 /* Levels with at most max_cells cells (the coarsest always) run in the
  * single-block tail kernel; FKS_ERR_ARG if their vectors do not fit in shared
  * memory. The results do not depend on it. Grid operators only. */
@@ -280,10 +285,11 @@ fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells);
  */
 fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells);
 /* The current fusion threshold, 16 x 16 tile threshold, single-block tail
- * threshold (levels of at most tail_max cells run in one block per source) and
- * cluster threshold (0: off) of `precision`; any output may be NULL. */
+ * threshold (levels of at most tail_max cells run in one block per source),
+ * cluster threshold (0: off) and 8 x 8 tile threshold of `precision`; any
+ * output may be NULL. */
 fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
-                         int64_t* tail_max, int64_t* cluster_max);
+                         int64_t* tail_max, int64_t* cluster_max, int64_t* tile8_max);
 
 /*
  * Allocation-free variant of fks_precond_apply (the paper has no counterpart).

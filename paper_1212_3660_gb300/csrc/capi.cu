@@ -203,6 +203,8 @@ struct fks_op {
   int64_t fuse_max[2] = {65536, INT64_MAX};
   // fused 2D levels with at most this many cells use 16 x 16 tiles (else 32 x 32)
   int64_t tile16_max[2] = {16384, 16384};
+  // ... and with at most this many, 8 x 8 tiles (more CTAs on small levels)
+  int64_t tile8_max[2] = {0, 0};
   // levels with at most this many cells run in the single-block tail kernel
   int64_t tail_max[2] = {256, 256};
   // from the first level with at most this many cells (and a cluster layout)
@@ -444,13 +446,15 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
   auto smooth_f = [&](const LevelHost& L, int zs) { return zs ? ns * L.n * 3.0 : ns * L.n * 0.5 * (8 * d + 6); };
   const int64_t fmax = S.op->fuse_max[sizeof(VT) == 8 ? 0 : 1];
   const int64_t t16 = S.op->tile16_max[sizeof(VT) == 8 ? 0 : 1];
+  const int64_t t8 = S.op->tile8_max[sizeof(VT) == 8 ? 0 : 1];
+  auto tile_of = [&](const LevelHost& L) { return L.n <= t8 ? 8 : (L.n <= t16 ? 16 : 32); };
   for (int l = 0; l < lt; ++l) {
     const LevelHost& L = Ls[l];
     if (fused_level_ok(L) && L.n <= fmax) {
       PROF(FKS_K_PRE2D, l, ns * (L.n * (3 * cv + (d + 1) * rv) + cv * Ls[l + 1].n),
            ns * L.n * (2 * (8 * d + 6) + 8 * d + 10),
            launch_pre2d<VT>(L, Ls[l + 1], S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
-                            L.n <= t16, s));
+                            tile_of(L), s));
       continue;
     }
     for (int r = 0; r < NU1; ++r) {
@@ -527,7 +531,7 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
       PROF(FKS_K_POST2D, l, ns * (L.n * (4 * cv + d * rv) + cv * Ls[l + 1].n),
            ns * L.n * (18 + 2 * (8 * d + 6)),
            launch_post2d<VT>(L, Ls[l + 1], S.op->mask, S.st, I(l), F(l), Zl(l), out, L.n, zfin, Ls[l + 1].n,
-                             S.nslot, L.n <= t16, s, add_to_zk ? Zk : nullptr, vsZk, zcol));
+                             S.nslot, tile_of(L), s, add_to_zk ? Zk : nullptr, vsZk, zcol));
       zfin = add_to_zk ? nullptr : out;
       continue;
     }
@@ -979,7 +983,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  S.eps, S.tol, (double)S.max_cycles, (double)op->fuse_max[0],
                                  (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
                                  (double)op->tile16_max[1], S.relax, (double)op->tail_max[0],
-                                 (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1]};
+                                 (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1],
+                                 (double)op->tile8_max[0], (double)op->tile8_max[1]};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1500,6 +1505,14 @@ fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells) {
   return FKS_OK;
 }
 
+fks_status fks_op_set_tiles8(fks_op* op, int precision, int64_t max_cells) {
+  if (!op) { set_error("fks_op_set_tiles8: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_set_tiles8: grid operators only"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_tiles8: bad precision"); return FKS_ERR_ARG; }
+  op->tile8_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
+  return FKS_OK;
+}
+
 fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_tail: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_tail: grid operators only"); return FKS_ERR_ARG; }
@@ -1558,7 +1571,7 @@ fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
 }
 
 fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
-                         int64_t* tail_max, int64_t* cluster_max) {
+                         int64_t* tail_max, int64_t* cluster_max, int64_t* tile8_max) {
   if (!op) { set_error("fks_op_tiling: NULL operator"); return FKS_ERR_ARG; }
   if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_tiling: bad precision"); return FKS_ERR_ARG; }
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
@@ -1566,6 +1579,7 @@ fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int
   if (tile16_max) *tile16_max = op->tile16_max[pi];
   if (tail_max) *tail_max = op->tail_max[pi];
   if (cluster_max) *cluster_max = op->cluster_max[pi];
+  if (tile8_max) *tile8_max = op->tile8_max[pi];
   return FKS_OK;
 }
 
@@ -1577,7 +1591,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi], savedt = op->tail_max[pi];
-  int64_t savedc = op->cluster_max[pi];
+  int64_t savedc = op->cluster_max[pi], saved8 = op->tile8_max[pi];
   try {
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
@@ -1621,8 +1635,8 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       double best = 1e30;
-      int64_t pick = saved, pick16 = saved16, pickt = savedt, pickc = savedc;
-      struct Choice { int64_t fuse, t16, tail, cl; };
+      int64_t pick = saved, pick16 = saved16, pickt = savedt, pickc = savedc, pick8 = 0;
+      struct Choice { int64_t fuse, t16, tail, cl, t8; };
       std::vector<Choice> choices;
       // fusion choices for the levels above the single-launch lower part
       // starting at level ls (thresholds below those levels' sizes are all "none")
@@ -1632,9 +1646,9 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
           if (c > op->levels[ls].n) cs.push_back(c);
         for (int64_t c : cs)
           for (int64_t t : cs)
-            if (t <= c) choices.push_back({c, t, tm, cm});
+            if (t <= c) choices.push_back({c, t, tm, cm, 0});
       };
-      for (int64_t tm : {int64_t(256), int64_t(1024), int64_t(4096)}) {
+      for (int64_t tm : {int64_t(64), int64_t(256), int64_t(1024), int64_t(4096)}) {
         const int lt = tail_level<VT>(op->levels, tm);
         if (tail_smem<VT>(op->levels, lt) > TAIL_SMEM_LIMIT) continue;  // f and z must fit
         add(lt, tm, 0);
@@ -1652,11 +1666,12 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
         }
         if (ok) add((int)l, savedt, cm);
       }
-      for (const Choice& ch : choices) {
+      auto measure = [&](const Choice& ch) -> float {
         op->fuse_max[pi] = ch.fuse;
         op->tile16_max[pi] = ch.t16;
         op->tail_max[pi] = ch.tail;
         op->cluster_max[pi] = ch.cl;
+        op->tile8_max[pi] = ch.t8;
         {
           // the tail's shared memory and coefficient blob follow the threshold
           std::lock_guard<std::mutex> build_lock(g_build_mu);
@@ -1692,12 +1707,25 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
         CK(cudaEventElapsedTime(&ms, e0, e1));
         cudaGraphExecDestroy(ge);
         cudaGraphDestroy(g);
+        return ms;
+      };
+      for (const Choice& ch : choices) {
+        const float ms = measure(ch);
         if (ms < best) {
           best = ms;
           pick = ch.fuse;
           pick16 = ch.t16;
           pickt = ch.tail;
           pickc = ch.cl;
+        }
+      }
+      // then 8 x 8 tiles for the smallest fused levels of the pick
+      for (int64_t u : cand) {
+        if (u == 0 || u > pick16 || u > pick) continue;
+        const float ms = measure({pick, pick16, pickt, pickc, u});
+        if (ms < best) {
+          best = ms;
+          pick8 = u;
         }
       }
       cudaEventDestroy(e0);
@@ -1707,6 +1735,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       op->tile16_max[pi] = pick16;
       op->tail_max[pi] = pickt;
       op->cluster_max[pi] = pickc;
+      op->tile8_max[pi] = pick8;
     };
     if (precision == FKS_PREC_FP64) run(double{});
     else run(float{});
@@ -1715,6 +1744,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
     op->tile16_max[pi] = saved16;
     op->tail_max[pi] = savedt;
     op->cluster_max[pi] = savedc;
+    op->tile8_max[pi] = saved8;
     set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
   }

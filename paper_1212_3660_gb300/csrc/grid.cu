@@ -253,7 +253,7 @@ __device__ __forceinline__ cx<T> nb_sum_tile(const LevelView<T>& L, Cell p, int 
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (TX == 16 ? 8 : 6) : 4) k_pre2d(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (TX == 32 ? 6 : 8) : 4) k_pre2d(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
                                                const z64* taus, const cx<T>* __restrict__ f, cx<T>* __restrict__ z,
                                                int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
   constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
@@ -1138,14 +1138,18 @@ bool fused_level_ok(const LevelHost& L) { return L.nz == 1 && L.rx == 2 && L.ry 
 
 template <typename T>
 void fused_prepare() {
+  // 8 x 8 and 16 x 16 tiles stay under the 48 KB default
   cudaFuncSetAttribute(k_pre2d<T, 32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T, 32, 32>());
   cudaFuncSetAttribute(k_post2d<T, 32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<T, 32, 32>());
 }
 
 template <typename T>
 void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
-                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, bool small, cudaStream_t s) {
-  if (small) {
+                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, int tile, cudaStream_t s) {
+  if (tile == 8) {
+    dim3 g(nb(F.nx, 8), nb(F.ny, 8), nslot);
+    k_pre2d<T, 8, 8><<<g, 256, fused_smem<T, 8, 8>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+  } else if (tile == 16) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
     k_pre2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
   } else {
@@ -1158,8 +1162,12 @@ void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, c
 template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
-                   bool small, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
-  if (small) {
+                   int tile, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
+  if (tile == 8) {
+    dim3 g(nb(F.nx, 8), nb(F.ny, 8), nslot);
+    k_post2d<T, 8, 8><<<g, 256, fused_smem<T, 8, 8>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc, Zk,
+                                                             vsZk, zcol);
+  } else if (tile == 16) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
     k_post2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
                                                                  Zk, vsZk, zcol);
@@ -1247,9 +1255,9 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
 #define INST(T)                                                                                                  \
   template void fused_prepare<T>();                                                                               \
   template void launch_pre2d<T>(const LevelHost&, const LevelHost&, const SlotState*, const cx<T>*, const z64*,    \
-                                const cx<T>*, cx<T>*, int64_t, cx<T>*, int64_t, int, bool, cudaStream_t);         \
+                                const cx<T>*, cx<T>*, int64_t, cx<T>*, int64_t, int, int, cudaStream_t);          \
   template void launch_post2d<T>(const LevelHost&, const LevelHost&, uint32_t, const SlotState*, const cx<T>*,     \
-                                 const cx<T>*, const cx<T>*, cx<T>*, int64_t, const cx<T>*, int64_t, int, bool,   \
+                                 const cx<T>*, const cx<T>*, cx<T>*, int64_t, const cx<T>*, int64_t, int, int,    \
                                  cudaStream_t, z64*, int64_t, int64_t);                                           \
   template void tail_prepare<T>(size_t);                                                                          \
   template void launch_tail<T>(const TailParams<T>&, size_t, const SlotState*, int, cudaStream_t);                \

@@ -44,16 +44,16 @@ void tail_prepare(size_t smem_bytes);
 bool fused_level_ok(const LevelHost& L);
 template <typename T>
 void fused_prepare();
-// small: 16 x 16 tiles (else 32 x 32); the results do not depend on the tiling
+// tile: 8, 16 or 32 (tiles of tile x tile cells); the results do not depend on the tiling
 template <typename T>
 void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, const cx<T>* invd, const z64* taus,
-                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, bool small, cudaStream_t s);
+                  const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, int tile, cudaStream_t s);
 // Zk (optional): instead of writing zout, add the result to column k - 1 of the
 // outer iterates Zk (slot stride vsZk, column stride zcol), as launch_correct does.
 template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
-                   bool small, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0);
+                   int tile, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0);
 // P.pairs selects the register-resident 2D kernel (same results)
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);

@@ -98,8 +98,9 @@ def lib():
     L.fks_op_set_tiles.argtypes = [vp, C.c_int, C.c_int64]
     L.fks_op_set_tail.argtypes = [vp, C.c_int, C.c_int64]
     L.fks_op_set_cluster.argtypes = [vp, C.c_int, C.c_int64]
+    L.fks_op_set_tiles8.argtypes = [vp, C.c_int, C.c_int64]
     L.fks_op_tiling.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
-                                C.POINTER(C.c_int64)]
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.fks_server_create.argtypes = [vp, C.c_size_t, C.c_int, C.POINTER(vp)]
     L.fks_server_submit.argtypes = [vp, C.POINTER(fks_request), C.POINTER(C.c_uint64)]
     L.fks_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -113,7 +114,7 @@ def lib():
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
     for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
-                 "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_tiling",
+                 "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
                  "fks_server_create",
                  "fks_server_submit", "fks_server_poll", "fks_server_wait",
                  "fks_server_cancel", "fks_server_times", "fks_server_launches"):
@@ -284,14 +285,21 @@ def fks_op_set_cluster(op, precision, max_cells):
         raise FksError(st, fks_last_error())
 
 
-def fks_op_tiling(op, precision):
-    """(fusion threshold, 16 x 16 tile threshold, tail threshold, cluster
-    threshold) in cells; the cluster threshold is 0 when the cluster kernel is off."""
-    a, b, t, c = C.c_int64(0), C.c_int64(0), C.c_int64(0), C.c_int64(0)
-    st = lib().fks_op_tiling(op, int(precision), C.byref(a), C.byref(b), C.byref(t), C.byref(c))
+def fks_op_set_tiles8(op, precision, max_cells):
+    st = lib().fks_op_set_tiles8(op, int(precision), int(max_cells))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
-    return int(a.value), int(b.value), int(t.value), int(c.value)
+
+
+def fks_op_tiling(op, precision):
+    """(fusion threshold, 16 x 16 tile threshold, tail threshold, cluster
+    threshold, 8 x 8 tile threshold) in cells; the cluster threshold is 0 when
+    the cluster kernel is off."""
+    a, b, t, c, e = (C.c_int64(0) for _ in range(5))
+    st = lib().fks_op_tiling(op, int(precision), C.byref(a), C.byref(b), C.byref(t), C.byref(c), C.byref(e))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return int(a.value), int(b.value), int(t.value), int(c.value), int(e.value)
 
 
 def fks_op_autotune(op, precision, tau, stream=None):

@@ -195,6 +195,10 @@ def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
         fks.fks_op_set_tiles(s.op, precision, t16)
         d = s.solve(precision=precision, inner_tol=1e-10)
         assert np.array_equal(a.X, d.X), t16
+    for t8 in (-1, 7680, 0):
+        fks.fks_op_set_tiles8(s.op, precision, t8)
+        d = s.solve(precision=precision, inner_tol=1e-10)
+        assert np.array_equal(a.X, d.X), t8
     # nor does moving small levels into the single-block tail kernel
     for tail in (1024, 4096, 256):
         fks.fks_op_set_tail(s.op, precision, tail)
