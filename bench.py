@@ -225,15 +225,9 @@ def serve_bench(args, rank, world, local, dist):
             dist.barrier()
     launches = fks.fks_server_launches(srv) - l0
 
-    def over_ranks(x, op):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=torch.device("cuda", local))
-        dist.all_reduce(t, op=op)
-        return float(t.item())
-
-    wall = over_ranks(cap["wall_s"], dist.ReduceOp.MAX if world > 1 else None)
-    value = over_ranks(cap["converged"], dist.ReduceOp.SUM if world > 1 else None) / wall
+    replicas = Replicas(dist, world, torch.device("cuda", local))
+    wall = replicas.max(cap["wall_s"])
+    value = replicas.throughput(cap["converged"], cap["wall_s"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         p0 = probs[0]
@@ -283,6 +277,39 @@ def serve_bench(args, rank, world, local, dist):
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Replicas:
+    """N-GPU mode: every rank solves its own copy of the workload (the path does
+    not shard, so there is no data-path collective). Only the bookkeeping is
+    combined: a barrier around the timed region, the slowest rank's time and
+    the sum of the ranks' certified solves. `device` holds the reduction
+    buffers (the rank's GPU under NCCL, the CPU under gloo)."""
+
+    def __init__(self, dist=None, world=1, device="cpu"):
+        self.dist, self.world, self.device = dist, world, device
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.world == 1:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX if self.world > 1 else None)
+
+    def sum(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM if self.world > 1 else None)
+
+    def throughput(self, units, seconds):
+        """Whole-job units per second: the units of all ranks over the slowest rank's time."""
+        return self.sum(units) / self.max(seconds)
 
 
 def peaks():
@@ -459,23 +486,8 @@ def main():
         return fks.fks_solve(solver.op, b, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), o, X, est, bnd, tru, mj,
                              sst, info, sh)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    replicas = Replicas(dist, world, dev)
+    barrier, max_over_ranks, sum_over_ranks = replicas.barrier, replicas.max, replicas.sum
 
     if args.fuse_max is not None:
         fks.fks_op_set_fusion(solver.op, prec, args.fuse_max)
