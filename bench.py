@@ -11,7 +11,11 @@ field (variance 1, correlation 0.2 L, mean ln 1e-4), S_s = 1e-5, centre source,
 step, multigrid inner solve, complex128 throughout.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-                  [--workload 1|2|3|4] [--precision fp64|mixed]
+                  [--workload 1|2|3|4|5|6] [--precision fp64|mixed]
+
+Workload 5 is the serving stream (request loop); workload 6 the sensitivity
+matrix of workload 2's aquifer (Algorithm 6: forward solve, adjoint solves of 8
+sensors, adjoint-state inner products for ln K and ln S_s), in Jacobian rows/s.
 
 Under torchrun every rank solves its own copy of the workload (replicas, weak
 scaling; no data-path collective). Prints one JSON line on rank 0.
@@ -40,6 +44,7 @@ INNER_EPS = 1e-10          # inner tolerance of the accuracy-gated runs (tol / 1
 # shift (oracle run, multigrid inner eps 1e-10); used to extrapolate the
 # bounded CPU sample to a whole solve.
 WORKLOAD_STEPS = {1: 36, 2: 36, 3: 40, 4: 40}
+JAC_SENSORS = 8   # sensors of the Jacobian workload (6)
 FP64_PEAK_TFLOPS = 1.25    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 
 
@@ -51,7 +56,7 @@ def parse():
     ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
-                    help="default: fp64 for workloads 1-2 (complex128 throughout), mixed for 3-5")
+                    help="default: fp64 for workloads 1, 2 and 6 (complex128 throughout), mixed for 3-5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
@@ -78,25 +83,38 @@ def parse():
     ap.add_argument("--cluster-max", type=int, default=None,
                     help="with --fuse-max: from the first level of at most this many cells down, the cluster "
                          "V-cycle kernel (0: off)")
+    ap.add_argument("--sensors", type=int, default=JAC_SENSORS, help="workload 6: sensors (adjoint sources)")
+    ap.add_argument("--shift-stride", type=int, default=1,
+                    help="workload 6: every k-th shift of the workload (a smaller case, e.g. for ncu)")
     ap.add_argument("--no-survey", action="store_true",
                     help="skip the per-class timing survey and the roofline (a short command for ncu launch lists)")
     a = ap.parse_args()
     if a.precision is None:
-        a.precision = "fp64" if a.workload in (1, 2) else "mixed"
+        a.precision = "fp64" if a.workload in (1, 2, 6) else "mixed"
     return a
 
 
-def source_hash():
-    """Digest of the device code (every CUDA source but the host engine
-    capi.cu); DRAM traffic recorded for another digest is stale."""
+# The CUDA sources that define each kernel class (its translation unit and the
+# headers it includes); DRAM traffic recorded for another digest of them is stale.
+_GRID_SOURCES = ("grid.cu", "grid.cuh", "stencil.cuh", "common.cuh")
+CLASS_SOURCES = {"smooth": _GRID_SOURCES, "restrict": _GRID_SOURCES, "prolong": _GRID_SOURCES,
+                 "pre2d": _GRID_SOURCES, "post2d": _GRID_SOURCES, "tail": _GRID_SOURCES, "defect": _GRID_SOURCES,
+                 "sensitivity": ("sensitivity.cu", "sensitivity.cuh", "stencil.cuh", "common.cuh")}
+
+
+def source_hash(kclass=None):
+    """Digest (sha256, first 16 hex digits) of the CUDA sources of a kernel
+    class (CLASS_SOURCES), or of all device code but the host engine capi.cu."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1212_3660_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")) and f != "capi.cu":
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    files = CLASS_SOURCES.get(kclass)
+    if files is None:
+        files = [f for f in os.listdir(d) if f.endswith((".cu", ".cuh")) and f != "capi.cu"]
+    for f in sorted(files):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -107,7 +125,7 @@ def recorded_traffic(workload, precision, kclass, level):
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None, None
-    cur = source_hash()
+    cur = source_hash(kclass)
     for line in open(path):
         cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
         if len(cells) < 7 or cells[0] != workload:
@@ -275,6 +293,159 @@ def serve_bench(args, rank, world, local, dist):
         print(json.dumps(line), flush=True)
 
 
+def jacobian_bench(args, rank, world, local, dist):
+    """Sensitivity matrix of the 512 x 512 workload (Algorithm 6): the forward
+    solve of the source, the adjoint solves of JAC_SENSORS sensors (one batched
+    fks_solve with the right-hand sides -e_m, Eq. adjoint) and the adjoint-state
+    inner products (Eq. sensitivity) for ln K and ln S_s of every cell. A step
+    is one whole Jacobian; the unit is a Jacobian row, the paper's
+    N_y = 2 n_f n_y real rows (real and imaginary part per sensor and
+    frequency), each holding both parameter fields; a row counts when its
+    forward and adjoint solves are certified at 1e-8."""
+    import torch
+
+    from paper_1212_3660_gb300 import fks, synth
+    from paper_1212_3660_gb300.solver import Solver
+    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    pr = synth.workload(2, m_max=100)
+    pr.sigma = pr.sigma[::max(1, args.shift_stride)].copy()
+    ns = args.sensors
+    name = f"jacobian-512x512-f{len(pr.sigma)}-s{ns}"
+    sensors = synth.well_cells(pr.shape, ns, np.random.default_rng(2006))
+    solver = Solver(pr, device=local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    n, n_f = pr.n, len(pr.sigma)
+    b_f = torch.from_numpy(pr.rhs().T.copy()).to(dev)
+    b_a = torch.zeros((ns, n), dtype=torch.complex128, device=dev)
+    for m, c in enumerate(sensors):
+        b_a[m, int(c)] = -1.0
+    X_f = torch.empty((1, n_f, n), dtype=torch.complex128, device=dev)
+    X_a = torch.empty((ns, n_f, n), dtype=torch.complex128, device=dev)
+    jk = torch.empty_like(X_a)
+    js = torch.empty_like(X_a)
+    sig_d = torch.from_numpy(pr.sigma.astype(np.complex128)).to(dev)
+    tau_d = torch.from_numpy(pr.tau_bar.astype(np.complex128)).to(dev)
+    outs = {k: (np.zeros((k, n_f)), np.zeros((k, n_f)), np.zeros((k, n_f)), np.zeros((k, n_f), np.int32),
+                np.zeros((k, n_f), np.int32)) for k in (1, ns)}
+    opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                  schedule=pr.schedule, inner_relax=args.inner_relax)
+    info1, info1_arrays = fks.make_info(1, pr.m_max)   # the arrays back the struct's pointers: keep them
+    infon, infon_arrays = fks.make_info(ns, pr.m_max)
+    fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step():
+        ev[0].record(stream)
+        fks.fks_solve(solver.op, b_f, 1, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X_f, *outs[1], info1, sh)
+        ev[1].record(stream)
+        fks.fks_solve(solver.op, b_a, ns, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X_a, *outs[ns], infon, sh)
+        ev[2].record(stream)
+        fks.fks_sensitivity(solver.op, X_f, X_a, ns, sig_d, n_f, jk, js, sh)
+        ev[3].record(stream)
+        ok_f = outs[1][2][0] <= TOL
+        ok_a = outs[ns][2] <= TOL
+        return 2 * int(np.sum(ok_a & ok_f[None, :]))
+
+    for _ in range(args.warmup):
+        step()
+    replicas = Replicas(dist, world, dev)
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    l0 = fks.fks_profile_read(solver.op)["all_launches"]
+    parts = np.zeros(3)
+    rows = 0
+    with ClockSampler(gpu_index) as clk:
+        replicas.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            rows += step()
+            torch.cuda.synchronize()
+            parts += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+        t1.record(stream)
+        torch.cuda.synchronize()
+        replicas.barrier()
+    launches = fks.fks_profile_read(solver.op)["all_launches"] - l0 + args.steps  # + the sensitivity kernel
+    ms = t0.elapsed_time(t1) / args.steps
+    value = replicas.throughput(rows / args.steps, ms / 1000.0)
+    parts /= args.steps
+    # roofline of the inner-product kernel: algorithmic bytes and FP64 flops per
+    # launch (per sensor, shift and cell: psi read, two results written; per
+    # face 2 subtractions and 4 fused multiply-adds, plus one complex product;
+    # per shift and cell the folded face weights)
+    d = len(pr.shape)
+    sens_bytes = ns * n_f * n * (16 + 2 * 16) + n_f * n * 16 + n * (8 + 8 + 8 * d) + n_f * 16
+    sens_flops = ns * n_f * n * (10 * 2 * d + 6) + n_f * n * (8 * 2 * d + 6)
+    hbm_peak, _, peak_src = peaks()
+    sens_gbs = sens_bytes / (parts[2] / 1000.0) / 1e9
+    sens_tfl = sens_flops / (parts[2] / 1000.0) / 1e12
+    traffic, traffic_src = recorded_traffic(name, args.precision, "sensitivity", 0)
+    if sens_tfl / FP64_PEAK_TFLOPS > sens_gbs / hbm_peak:
+        roof = {"bound": "alu", "achieved": sens_tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": sens_tfl / FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                "hbm_frac_of_" + peak_src: sens_gbs / hbm_peak}
+    else:
+        roof = {"bound": "hbm", "achieved": sens_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": sens_gbs / hbm_peak,
+                "peak_source": peak_src}
+    roof.update({"traffic": traffic, "kernel": "k_sensitivity",
+            "alg_bytes_per_launch": sens_bytes, "alg_flops_per_launch": sens_flops, "launch_ms": parts[2],
+            "traffic_source": ("profiles/traffic.md (ncu, sources " + traffic_src + ")") if traffic is not None
+            else ("stale: kernels changed since the ncu capture" if traffic_src else "no ncu capture recorded")})
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, _, desc = jacobian_cpu_sample(pr, args, ns)
+        cpu = {"value": v, "unit": "rows/s", "cores": blas_threads(), "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {"metric": "Jacobian rows/s at 1e-8 residual", "value": value, "unit": "rows/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": replicas.max(ms),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer", "data": "synthetic",
+                "config": {"workload": name, "grid": "x".join(map(str, pr.shape[::-1])), "n": n, "n_f": n_f,
+                           "sensors": ns, "parameters": ["ln K", "ln S_s"], "precision": args.precision,
+                           "inner_relax": args.inner_relax, "parallelism": f"replicas{world}",
+                           "l2": "adjoint phasors and sensitivities (3 x 6.7 GB) exceed L2"},
+                "breakdown_ms": {"forward": parts[0], "adjoint": parts[1], "inner_product": parts[2]},
+                "shifted_solves_per_s": (1 + ns) * n_f / ((parts[0] + parts[1]) / 1000.0),
+                "rows_per_step": rows / args.steps,
+                "e2e": None, "e2e_note": "device-resident only: the host copies of 20 GB of phasors and "
+                                         "sensitivities per step would measure the host link",
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    solver.close()
+
+
+def jacobian_cpu_sample(pr, args, ns):
+    """The oracle on the Jacobian workload: a bounded sample of its solves
+    (cpu_oracle_sample, scaled to the 1 + ns sources' shifted solves) and of its
+    inner products (two (sensor, shift) pairs, scaled to all). Returns (rows/s,
+    seconds spent, description)."""
+    from oracle.sensitivity import sensitivities
+    n_f = len(pr.sigma)
+    v_s, dt_s, desc_s = cpu_oracle_sample(pr, max(1, args.cpu_sample_steps // 2), WORKLOAD_STEPS[2], INNER_EPS,
+                                          args.inner_relax)
+    rng = np.random.default_rng(0)
+    phi = rng.standard_normal((2, pr.n)) + 1j * rng.standard_normal((2, pr.n))
+    psi = rng.standard_normal((2, pr.n)) + 1j * rng.standard_normal((2, pr.n))
+    c0 = time.perf_counter()
+    for j in range(2):
+        sensitivities(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask, pr.sigma[j], phi[j], psi[j])
+    dt_ip = time.perf_counter() - c0
+    t_ip = dt_ip / 2 * ns * n_f
+    t_cpu = (1 + ns) * n_f / v_s + t_ip
+    desc = (f"solves: {desc_s}, for 1 + {ns} sources; inner products: 2 of the {ns * n_f} (sensor, shift) "
+            f"pairs timed ({dt_ip:.1f} s) and scaled")
+    return 2 * ns * n_f / t_cpu, dt_s + dt_ip, desc
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -413,6 +584,26 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == 6:
+        pr = synth.workload(2, m_max=100)
+        vals = []
+        sample = None
+        for i in range(args.warmup + args.steps):
+            v, _, sample = jacobian_cpu_sample(pr, args, JAC_SENSORS)
+            if i >= args.warmup:
+                vals.append(v)
+        value = statistics.median(vals)
+        line = {"impl": "reference", "metric": "Jacobian rows/s at 1e-8 residual", "value": value, "unit": "rows/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * 2 * JAC_SENSORS * len(pr.sigma) / value, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+                "config": {"workload": f"jacobian-512x512-f{len(pr.sigma)}-s{JAC_SENSORS}",
+                           "grid": "x".join(map(str, pr.shape[::-1])), "n_f": len(pr.sigma), "sensors": JAC_SENSORS},
+                "cpu_baseline": {"value": value, "unit": "rows/s", "cores": blas_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == 5:
         # the stream's first request stands for the stream
         _, p0 = synth.make_request_stream(1, seed=3000, max_cells=SERVE_MAX_CELLS, max_sources=SERVE_MAX_SOURCES)[0]
@@ -456,6 +647,11 @@ def main():
     build.build()
     if args.workload == 5:
         serve_bench(args, rank, world, local, dist)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == 6:
+        jacobian_bench(args, rank, world, local, dist)
         if world > 1:
             dist.destroy_process_group()
         return

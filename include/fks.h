@@ -183,6 +183,33 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
 fks_status fks_op_apply(fks_op* op, fks_c128 s, const fks_c128* x, fks_c128* y, int n_vec, void* stream);
 
 /*
+ * Sensitivities of the phasor measurements by the adjoint-state method
+ * (Section 5: Eq. measurement, Eq. sensitivity, Eq. adjoint, Algorithm 6), for
+ * grid operators (fks_op_grid). Sensor m sits in cell x_m and records
+ * h = Phi_j(x_m) at shift sigma_j (real and imaginary part: the two
+ * coefficients per frequency). With A = K + sigma_j M, A Phi_j = b and the
+ * adjoint phasor A Psi_mj = -e_{x_m} (A is complex symmetric, so the adjoint
+ * solves are plain fks_solve calls with the right-hand sides -e_{x_m}),
+ *   dh/dp = Psi_mj^T (dA/dp) Phi_j   (no conjugation), and per cell c:
+ *   j_lnk: dh/dlnK_c = sum over c's interior faces (to nb, transmissibility t)
+ *          of t K_nb/(K_c + K_nb) (Psi_c - Psi_nb)(Phi_c - Phi_nb), plus t Psi_c Phi_c
+ *          over its zero-head boundary faces (the dK grad Phi . grad Psi term)
+ *   j_lns: dh/dlnS_s,c = sigma_j M_cc Psi_c Phi_c   (the i omega dS_s Phi Psi term)
+ *  phi    [n_f * n] in: forward phasors Phi_j (one source's X of fks_solve)
+ *  psi    [n_m * n_f * n] in: adjoint phasors, measurement-major (the X of an
+ *         fks_solve with n_rhs = n_m right-hand sides -e_{x_m})
+ *  sigma  [n_f] in: the shifts
+ *  j_lnk, j_lns [n_m * n_f * n] out, indexed ((m * n_f) + j) * n + c
+ * Pointers host or device; with all four arrays on the device the call runs
+ * one kernel on them in place, otherwise it stages one measurement at a time.
+ * FKS_ERR_ARG for CSR operators, n_m < 1, n_f outside [1, 65535], NULL
+ * arrays or non-finite host sigma. Outputs are complete when the call returns.
+ */
+fks_status fks_sensitivity(fks_op* op, const fks_c128* phi, const fks_c128* psi, int n_m,
+                           const fks_c128* sigma, int n_f, fks_c128* j_lnk, fks_c128* j_lns,
+                           void* stream);
+
+/*
  * Inexact preconditioner apply (Section 4, Eq. zmmoditer): z ~ (K + tau M)^{-1} v by
  * multigrid cycles from z = 0 until ||v - (K + tau M) z|| <= eps ||v|| or max_cycles
  * (cycles >= 0 forces exactly that many). precision as in fks_options.

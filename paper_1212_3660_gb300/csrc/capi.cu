@@ -26,6 +26,7 @@
 #include "csr.cuh"
 #include "assemble_tc.cuh"
 #include "cluster.cuh"
+#include "sensitivity.cuh"
 
 namespace fks {
 
@@ -196,6 +197,7 @@ struct fks_op {
   int nx, ny, nz;
   int64_t n;
   uint32_t mask;
+  double* cond_d = nullptr;  // grid operators: cell conductivity (device), for the sensitivities
   std::vector<LevelHost> levels;
   Lane lane0;  // workspace, graph and instrumentation of fks_solve / fks_precond_apply
   // 2D levels with at most this many cells use the fused tile kernels
@@ -1308,7 +1310,7 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
       }
     CK(cudaDeviceSynchronize());
     CK(cudaGetLastError());
-    cudaFree(cond_d);
+    op->cond_d = cond_d;
   } catch (CudaError& e) {
     if (cond_d) cudaFree(cond_d);
     set_error(std::string("fks_op_grid: ") + e.where + ": " + cudaGetErrorString(e.e));
@@ -1431,6 +1433,7 @@ void fks_op_destroy(fks_op* op) {
     }
     if (L.kd64) cudaFree(L.kd64);
   }
+  if (op->cond_d) cudaFree(op->cond_d);
   op->lane0.release();
   delete op;
 }
@@ -1803,6 +1806,53 @@ fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y,
   } catch (CudaError& e) {
     set_error(std::string("fks_op_apply: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
+  }
+  return FKS_OK;
+}
+
+fks_status fks_sensitivity(fks_op* op, const fks_c128* phi, const fks_c128* psi, int n_m, const fks_c128* sigma,
+                           int n_f, fks_c128* j_lnk, fks_c128* j_lns, void* stream) {
+  if (!op || !phi || !psi || !sigma || !j_lnk || !j_lns) { set_error("fks_sensitivity: NULL argument"); return FKS_ERR_ARG; }
+  if (op->csr || !op->cond_d) { set_error("fks_sensitivity: grid operators only"); return FKS_ERR_ARG; }
+  if (n_m < 1 || n_f < 1 || n_f > 65535) { set_error("fks_sensitivity: need n_m >= 1 and 1 <= n_f <= 65535"); return FKS_ERR_ARG; }
+  if (!is_device_ptr(sigma))
+    for (int j = 0; j < n_f; ++j)
+      if (!finite_c(sigma[j])) { set_error("fks_sensitivity: sigma has NaN/Inf"); return FKS_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    const int64_t n = op->n;
+    const size_t blk = sizeof(z64) * (size_t)n * n_f;  // one measurement's n_f phasors
+    const bool all_dev = is_device_ptr(phi) && is_device_ptr(psi) && is_device_ptr(j_lnk) && is_device_ptr(j_lns);
+    Arena& A = op->lane0.ws;
+    const size_t need = (all_dev ? 0 : 4 * blk) + sizeof(z64) * n_f + 8192;
+    A.reserve(need);
+    A.reset();
+    z64* sg = A.take<z64>(n_f);
+    copy_in(sg, sigma, sizeof(z64) * n_f, s);
+    if (all_dev) {
+      launch_sensitivity(op->levels[0], op->cond_d, (const z64*)phi, (const z64*)psi, n_m, n_f, sg, (z64*)j_lnk,
+                         (z64*)j_lns, s);
+      CK(cudaGetLastError());
+    } else {
+      // one measurement at a time through device staging buffers
+      z64* ph = A.take<z64>((size_t)n * n_f);
+      z64* ps = A.take<z64>((size_t)n * n_f);
+      z64* jk = A.take<z64>((size_t)n * n_f);
+      z64* js = A.take<z64>((size_t)n * n_f);
+      copy_in(ph, phi, blk, s);
+      for (int m = 0; m < n_m; ++m) {
+        copy_in(ps, psi + (size_t)m * n * n_f, blk, s);
+        launch_sensitivity(op->levels[0], op->cond_d, ph, ps, 1, n_f, sg, jk, js, s);
+        CK(cudaGetLastError());
+        copy_out(j_lnk + (size_t)m * n * n_f, jk, blk, s);
+        copy_out(j_lns + (size_t)m * n * n_f, js, blk, s);
+      }
+    }
+    CK(cudaStreamSynchronize(s));
+  } catch (CudaError& e) {
+    set_error(std::string("fks_sensitivity: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
   }
   return FKS_OK;
 }

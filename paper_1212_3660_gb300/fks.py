@@ -90,6 +90,7 @@ def lib():
     L.fks_solve.argtypes = [vp, vp, C.c_int, vp, C.c_int, vp, C.c_int, C.POINTER(fks_options), vp, vp, vp, vp, vp,
                             vp, C.POINTER(fks_info), vp]
     L.fks_op_apply.argtypes = [vp, fks_c128, vp, vp, C.c_int, vp]
+    L.fks_sensitivity.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, vp]
     L.fks_precond_apply.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p, f64p, vp]
     L.fks_precond_apply_noalloc.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p,
                                             f64p, vp]
@@ -112,7 +113,7 @@ def lib():
     L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
-    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_precond_apply", "fks_profile_select",
+    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
                  "fks_server_create",
@@ -234,6 +235,15 @@ def fks_op_apply(op, s, x, y, n_vec, stream=None):
     return st
 
 
+def fks_sensitivity(op, phi, psi, n_m, sigma, n_f, j_lnk, j_lns, stream=None):
+    """dh/dlnK and dh/dlnS of every measurement, shift and cell (arrays as numpy or torch)."""
+    st = lib().fks_sensitivity(op, _ptr(phi), _ptr(psi), int(n_m), _ptr(sigma), int(n_f), _ptr(j_lnk), _ptr(j_lns),
+                               stream)
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return st
+
+
 def fks_precond_apply(op, tau, v, z, eps, max_cycles=50, cycles=-1, precision=FKS_PREC_FP64, stream=None):
     """Returns (status, cycles, ||p||)."""
     oc = C.c_int32(0)
@@ -264,6 +274,7 @@ def make_info(n_rhs, m_max):
                     arrs["inner_cycles"].ctypes.data_as(C.POINTER(C.c_int32)),
                     arrs["pnorm"].ctypes.data_as(C.POINTER(C.c_double)),
                     arrs["breakdown"].ctypes.data_as(C.POINTER(C.c_int32)))
+    info._arrays = arrs   # the struct holds raw pointers into these: they live as long as it does
     return info, arrs
 
 

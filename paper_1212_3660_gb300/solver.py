@@ -89,3 +89,23 @@ class Solver:
                            stream)
         return SolveOutput(st, X, est, bnd, tru, mj, sst, arr["steps"], arr["inner_cycles"].reshape(n_rhs, m_max),
                            arr["pnorm"].reshape(n_rhs, m_max), arr["breakdown"])
+
+    def sensitivity(self, phi, psi, sigma=None, stream=None):
+        """(dh/dlnK, dh/dlnS), each n_m x n_f x n complex128, from forward phasors
+        phi (n_f x n) and adjoint phasors psi (n_m x n_f x n); numpy in, numpy
+        out (torch tensors on the device are used in place)."""
+        sigma = np.ascontiguousarray(self.p.sigma if sigma is None else sigma, dtype=np.complex128)
+        n_f = len(sigma)
+        if hasattr(psi, "is_cuda") and psi.is_cuda:
+            import torch
+            n_m = psi.shape[0]
+            jk = torch.empty_like(psi)
+            js = torch.empty_like(psi)
+        else:
+            phi = np.ascontiguousarray(phi, dtype=np.complex128)
+            psi = np.ascontiguousarray(psi, dtype=np.complex128)
+            n_m = psi.shape[0]
+            jk = np.zeros_like(psi)
+            js = np.zeros_like(psi)
+        fks.fks_sensitivity(self.op, phi, psi, n_m, sigma, n_f, jk, js, stream)
+        return jk, js
