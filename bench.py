@@ -31,6 +31,11 @@ import subprocess
 import sys
 import time
 
+# the CPU oracle legs run single-threaded unless the caller says otherwise, so
+# that the reported core count is the one used (set before NumPy loads BLAS)
+for _k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_k, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -44,6 +49,10 @@ INNER_EPS = 1e-10          # inner tolerance of the accuracy-gated runs (tol / 1
 # shift (oracle run, multigrid inner eps 1e-10); used to extrapolate the
 # bounded CPU sample to a whole solve.
 WORKLOAD_STEPS = {1: 36, 2: 36, 3: 40, 4: 40}
+# Inner cycles of the oracle's own complete solve of a workload (first source)
+# with the relaxed rule, for extrapolating its bounded samples: workload 2 at
+# l = 0.003 takes 36 steps and 307 cycles when the oracle runs to the end.
+ORACLE_CYCLES = {(2, 0.003): 307}
 JAC_SENSORS = 8   # sensors of the Jacobian workload (6)
 FP64_PEAK_TFLOPS = 1.25    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 
@@ -614,8 +623,10 @@ def run_reference(args):
     ws = WORKLOAD_STEPS.get(args.workload, 40)
     vals, secs = [], []
     sample = None
+    total_cycles = ORACLE_CYCLES.get((args.workload, round(args.inner_relax, 6)))
     for i in range(args.warmup + args.steps):
-        v, dt, sample = cpu_oracle_sample(pr, max(1, args.cpu_sample_steps // 3), ws, INNER_EPS, args.inner_relax)
+        v, dt, sample = cpu_oracle_sample(pr, max(1, args.cpu_sample_steps // 3), ws, INNER_EPS, args.inner_relax,
+                                          total_cycles)
         if i >= args.warmup:
             vals.append(v)
             secs.append(dt)

@@ -151,6 +151,19 @@ typedef struct {
   int32_t* inner_cycles;  /* [m_max * n_rhs] inner cycles of step k (source-major)           */
   double* pnorm;          /* [m_max * n_rhs] ||p_k|| = ||v_k - (K + tau_k M) z_k||           */
   int32_t* breakdown;     /* [n_rhs] 1 if h_{k+1,k} vanished                                 */
+  /* Monitors (Section 3); each may be NULL, host or device:
+   * gmres_alpha [n_f * n_rhs]: Prop. 3's alpha = ||eta H_m(sigma_j; T)^{-*} e_m||,
+   *   eta = h_{m+1,m}(sigma_j - tau_m), at the shift's freeze step m = m_j, so
+   *   ||r_fom - r_gmres|| <= alpha (1 + alpha) / (1 + alpha^2) ||r_fom||; a large
+   *   alpha flags FGMRES stagnation (infinite when H_m(sigma_j; T) is singular)
+   * hbar [(m_max + 1) * m_max * n_rhs]: the flexible Hessenberg H_bar of each
+   *   source, column-major: h_{i,k} at r (m_max + 1) m_max + (k - 1)(m_max + 1) + i - 1
+   *   (zero beyond the steps taken)
+   * tau_k [m_max * n_rhs]: the preconditioner shift of each step (T_m's diagonal)
+   * Together with steps they give Prop. 1's Ritz values (fks_ritz). */
+  double* gmres_alpha;
+  fks_c128* hbar;
+  fks_c128* tau_k;
 } fks_info;
 
 /*

@@ -272,6 +272,7 @@ struct Solve {
   SlotState* st_host;  // pinned mirror
   z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
+  double* alpha;   // Prop. 3's alpha per (source, shift) at its freeze step
   int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular, *flags, *counter, *bcount;
   // multigrid, cycle precision
   std::vector<void*> f, z, z2, invd;
@@ -687,7 +688,7 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
   PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, S.s));
   PROF(FKS_K_GIVENS, -1, ns * n_f * 48.0 * kk, ns * n_f * 26.0 * kk,
        launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant, S.replay ? S.rep_mj : nullptr,
-                     S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, n_rhs, S.s));
+                     S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, S.alpha, n_rhs, S.s));
   PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, use_cond, hout, S.s));
 }
 
@@ -903,6 +904,7 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.mj = A.take<int32_t>((size_t)ns * nf);
   S.est = A.take<double>((size_t)ns * nf);
   S.bnd = A.take<double>((size_t)ns * nf);
+  S.alpha = A.take<double>((size_t)ns * nf);
   S.tpart = A.take<double>((size_t)ns * nf * (S.op->csr ? csr_blocks(n) : tres_blocks(Ls[0])));
   S.tres = A.take<double>((size_t)ns * nf);
   S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
@@ -971,9 +973,11 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 0, S.b, n, n, S.npart, n_rhs, s));
   PROF(-1, -1, 0, 0, launch_start(S.st, n_rhs, S.npart, nbn, n_f, s));
   PROF(-1, -1, 0, 0, launch_init_v1(S.st, S.b, n, S.V, (m + 1) * n, n_rhs, s));
-  PROF(-1, -1, 0, 0, launch_init_shifts(S.st, n_f, m, S.sst, S.mj, S.est, S.bnd, S.Y, n_rhs, s));
+  PROF(-1, -1, 0, 0, launch_init_shifts(S.st, n_f, m, S.sst, S.mj, S.est, S.bnd, S.Y, S.alpha, n_rhs, s));
   CK(cudaMemsetAsync(S.pn, 0, sizeof(double) * m * n_rhs, s));
   CK(cudaMemsetAsync(S.cyc, 0, sizeof(int32_t) * m * n_rhs, s));
+  CK(cudaMemsetAsync(S.H, 0, sizeof(z64) * (m + 1) * m * n_rhs, s));
+  CK(cudaMemsetAsync(S.taus_k, 0, sizeof(z64) * m * n_rhs, s));
   const int64_t vsV = (int64_t)(m + 1) * n, vsZ = (int64_t)m * n;
   int steps = 0;
   bool use_graph = o->launch_mode == 0;
@@ -1103,6 +1107,9 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   if (info && info->inner_cycles) cyc_h.resize((size_t)m * n_rhs);
   if (info && info->pnorm) pn_h.resize((size_t)m * n_rhs);
   if (!cyc_h.empty()) CK(cudaMemcpyAsync(cyc_h.data(), S.cyc, sizeof(int32_t) * m * n_rhs, cudaMemcpyDeviceToHost, s));
+  if (info && info->gmres_alpha) copy_out(info->gmres_alpha, S.alpha, sizeof(double) * n_f * n_rhs, s);
+  if (info && info->hbar) copy_out(info->hbar, S.H, sizeof(z64) * (m + 1) * m * n_rhs, s);
+  if (info && info->tau_k) copy_out(info->tau_k, S.taus_k, sizeof(z64) * m * n_rhs, s);
   if (!pn_h.empty()) CK(cudaMemcpyAsync(pn_h.data(), S.pn, sizeof(double) * m * n_rhs, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
   int singular = 0;
@@ -1198,6 +1205,9 @@ static fks_status solve_chunked(fks_op* op, Lane* lane, const fks_c128* b, int n
       ic.inner_cycles = info->inner_cycles ? info->inner_cycles + (size_t)r0 * o->m_max : nullptr;
       ic.pnorm = info->pnorm ? info->pnorm + (size_t)r0 * o->m_max : nullptr;
       ic.breakdown = info->breakdown ? info->breakdown + r0 : nullptr;
+      ic.gmres_alpha = info->gmres_alpha ? info->gmres_alpha + (size_t)r0 * n_f : nullptr;
+      ic.hbar = info->hbar ? info->hbar + (size_t)r0 * (o->m_max + 1) * o->m_max : nullptr;
+      ic.tau_k = info->tau_k ? info->tau_k + (size_t)r0 * o->m_max : nullptr;
     }
     size_t nf = (size_t)n_f * r0;
     fks_status st = solve_impl<VT>(op, lane, b + (size_t)r0 * op->n, nr, sigma, n_f, tau, n_tau, &oc,

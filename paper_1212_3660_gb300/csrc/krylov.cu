@@ -75,7 +75,7 @@ __global__ void k_init_v1(const SlotState* st, const z64* __restrict__ b, int64_
 }
 
 __global__ void k_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_t* mj, double* est,
-                              double* bnd, z64* Y) {
+                              double* bnd, z64* Y, double* alpha) {
   int slot = blockIdx.y;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nf) return;
@@ -85,6 +85,7 @@ __global__ void k_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, 
   mj[sj] = 0;
   est[sj] = 0.0;
   bnd[sj] = 0.0;
+  alpha[sj] = 0.0;
   for (int i = 0; i < m; ++i) Y[sj * m + i] = mk(0.0, 0.0);
 }
 
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
                                                           const double* __restrict__ pn, double tol, int variant,
                                                           const int32_t* __restrict__ replay_mj, z64* g, double* rc,
                                                           z64* rs, z64* R, z64* Y, int32_t* sst, int32_t* mj,
-                                                          double* est_out, double* bnd_out) {
+                                                          double* est_out, double* bnd_out, double* alpha_out) {
   __shared__ z64 col[GV_WARPS][MAX_M + 1];
   __shared__ z64 yv[GV_WARPS][MAX_M];
   __shared__ z64 rhs[GV_WARPS][MAX_M];
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   __shared__ z64 rss[GV_WARPS][MAX_M];
   __shared__ z64 sc[GV_WARPS][2];   // pre (diagonal before the new rotation), g_k before it
   __shared__ double sd[GV_WARPS];   // residual estimate
+  __shared__ double sal[GV_WARPS];  // Prop. 3's alpha at this step
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int slot = blockIdx.y;
   int j = blockIdx.x * GV_WARPS + warp;
@@ -334,6 +336,11 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
     sc[warp][0] = a;      // diagonal of the square (FFOM) factor
     sc[warp][1] = gk;
     sd[warp] = cabs(gj[k]);
+    // Prop. 3: alpha = ||eta H_k(sigma; T)^{-*} e_k||, eta = h_{k+1,k}(sigma - tau_k) = b.
+    // With H_k(sigma; T) = Q R (the rotations so far), the last row of its
+    // inverse has norm 1 / |R_kk| = 1 / |a|: alpha = |b| / |a|, the tangent of
+    // the new rotation.
+    sal[warp] = aa > 0.0 ? bb / aa : (bb > 0.0 ? (double)INFINITY : 0.0);
   }
   __syncwarp();
   for (int i = lane; i + 1 < k; i += 32) Rc[i] = cl[i];  // the rotated column of R
@@ -396,6 +403,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   for (int i = lane; i < m; i += 32) Y[sj * m + i] = i < k ? yv[warp][i] : mk(0.0, 0.0);
   if (lane == 0) {
     mj[sj] = k;
+    alpha_out[sj] = sal[warp];
     sst[sj] = conv ? 0 : (brk ? 2 : 1);
     est_out[sj] = est / beta;
     bnd_out[sj] = bound / beta;
@@ -524,9 +532,9 @@ void launch_init_v1(const SlotState* st, const z64* b, int64_t n, z64* V, int64_
   k_init_v1<<<g, 256, 0, s>>>(st, b, n, V, vsV);
 }
 void launch_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_t* mj, double* est, double* bnd,
-                        z64* Y, int nslot, cudaStream_t s) {
+                        z64* Y, double* alpha, int nslot, cudaStream_t s) {
   dim3 g(nbk(nf, 64), nslot);
-  k_init_shifts<<<g, 64, 0, s>>>(st, nf, m, sst, mj, est, bnd, Y);
+  k_init_shifts<<<g, 64, 0, s>>>(st, nf, m, sst, mj, est, bnd, Y, alpha);
 }
 void launch_step_begin(SlotState* st, int nslot, const int32_t* sched, int sched_len, const z64* taus, z64* taus_k,
                        int m, cudaStream_t s) {
@@ -563,10 +571,10 @@ void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, in
 }
 void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H, const z64* taus_k, const double* pn,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
-                   int32_t* sst, int32_t* mj, double* est, double* bnd, int nslot, cudaStream_t s) {
+                   int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s) {
   dim3 gr(nbk(nf, GV_WARPS), nslot);
   k_givens<<<gr, GV_WARPS * 32, 0, s>>>(st, nf, m, sigma, H, taus_k, pn, tol, variant, replay_mj, g, rc, rs, R, Y, sst,
-                                        mj, est, bnd);
+                                        mj, est, bnd, alpha);
 }
 void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s) {
   k_step_end<<<1, 256, 0, s>>>(st, nslot, m, use_cond, cond);

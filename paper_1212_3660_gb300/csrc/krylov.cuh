@@ -20,7 +20,7 @@ void launch_norm2_partial(const SlotState* st, int need_active, const z64* x, in
 void launch_start(SlotState* st, int nslot, const double* partial, int nblocks, int nf, cudaStream_t s);
 void launch_init_v1(const SlotState* st, const z64* b, int64_t n, z64* V, int64_t vsV, int nslot, cudaStream_t s);
 void launch_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_t* mj, double* est, double* bnd,
-                        z64* Y, int nslot, cudaStream_t s);
+                        z64* Y, double* alpha, int nslot, cudaStream_t s);
 void launch_step_begin(SlotState* st, int nslot, const int32_t* sched, int sched_len, const z64* taus, z64* taus_k,
                        int m, cudaStream_t s);
 void launch_mass(const SlotState* st, const double* mm, const z64* Z, int64_t vsZ, z64* w, int64_t n, double* partial,
@@ -37,7 +37,7 @@ void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, in
                   cudaStream_t s);
 void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H, const z64* taus_k, const double* pn,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
-                   int32_t* sst, int32_t* mj, double* est, double* bnd, int nslot, cudaStream_t s);
+                   int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s);
 void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s);
 // x_j = Z y_j in FP64; with st given, sources with st[slot].k <= skip_k_le are skipped
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,

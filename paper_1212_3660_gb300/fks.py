@@ -41,7 +41,8 @@ class fks_options(C.Structure):
 
 class fks_info(C.Structure):
     _fields_ = [("steps", C.POINTER(C.c_int32)), ("inner_cycles", C.POINTER(C.c_int32)),
-                ("pnorm", C.POINTER(C.c_double)), ("breakdown", C.POINTER(C.c_int32))]
+                ("pnorm", C.POINTER(C.c_double)), ("breakdown", C.POINTER(C.c_int32)),
+                ("gmres_alpha", C.c_void_p), ("hbar", C.c_void_p), ("tau_k", C.c_void_p)]
 
 
 class fks_request(C.Structure):
@@ -267,13 +268,19 @@ def fks_precond_apply_noalloc(op, tau, v, z, eps, max_cycles=50, cycles=-1, prec
     return st, int(oc.value), float(op_.value)
 
 
-def make_info(n_rhs, m_max):
+def make_info(n_rhs, m_max, n_f=0):
+    """fks_info with host arrays; with n_f > 0 also the monitors (Prop. 3's alpha
+    per shift, the Hessenberg matrices and the steps' tau)."""
     arrs = dict(steps=np.zeros(n_rhs, np.int32), inner_cycles=np.zeros(n_rhs * m_max, np.int32),
                 pnorm=np.zeros(n_rhs * m_max, np.float64), breakdown=np.zeros(n_rhs, np.int32))
+    if n_f > 0:
+        arrs.update(gmres_alpha=np.zeros((n_rhs, n_f)), hbar=np.zeros((n_rhs, m_max, m_max + 1), np.complex128),
+                    tau_k=np.zeros((n_rhs, m_max), np.complex128))
     info = fks_info(arrs["steps"].ctypes.data_as(C.POINTER(C.c_int32)),
                     arrs["inner_cycles"].ctypes.data_as(C.POINTER(C.c_int32)),
                     arrs["pnorm"].ctypes.data_as(C.POINTER(C.c_double)),
-                    arrs["breakdown"].ctypes.data_as(C.POINTER(C.c_int32)))
+                    arrs["breakdown"].ctypes.data_as(C.POINTER(C.c_int32)),
+                    *([arrs[k].ctypes.data for k in ("gmres_alpha", "hbar", "tau_k")] if n_f > 0 else [None] * 3))
     info._arrays = arrs   # the struct holds raw pointers into these: they live as long as it does
     return info, arrs
 

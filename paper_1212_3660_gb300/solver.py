@@ -28,6 +28,9 @@ class SolveOutput:
     inner_cycles: np.ndarray  # n_rhs x m_max
     pnorm: np.ndarray
     breakdown: np.ndarray
+    gmres_alpha: np.ndarray = None  # n_rhs x n_f: Prop. 3's alpha at each shift's freeze step
+    hbar: np.ndarray = None         # n_rhs x m_max x (m_max + 1): column k-1 of H_bar is hbar[r, k-1]
+    tau_k: np.ndarray = None        # n_rhs x m_max
 
 
 class Solver:
@@ -84,11 +87,12 @@ class Solver:
         tru = np.zeros((n_rhs, n_f))
         mj = np.zeros((n_rhs, n_f), np.int32)
         sst = np.zeros((n_rhs, n_f), np.int32)
-        info, arr = fks.make_info(n_rhs, m_max)
+        info, arr = fks.make_info(n_rhs, m_max, n_f)
         st = fks.fks_solve(self.op, b, n_rhs, sigma, n_f, tau, len(tau), opts, X, est, bnd, tru, mj, sst, info,
                            stream)
         return SolveOutput(st, X, est, bnd, tru, mj, sst, arr["steps"], arr["inner_cycles"].reshape(n_rhs, m_max),
-                           arr["pnorm"].reshape(n_rhs, m_max), arr["breakdown"])
+                           arr["pnorm"].reshape(n_rhs, m_max), arr["breakdown"], arr["gmres_alpha"], arr["hbar"],
+                           arr["tau_k"])
 
     def sensitivity(self, phi, psi, sigma=None, stream=None):
         """(dh/dlnK, dh/dlnS), each n_m x n_f x n complex128, from forward phasors
