@@ -822,6 +822,26 @@ def main():
 
     main_info = {k: v.copy() for k, v in info_arr.items()}   # this line's solve, before the variants
 
+    # ---- convergence monitors (Section 3): one more solve exporting H_bar and
+    # tau_k (Prop. 3's alpha comes from the Givens update at no extra launch),
+    # then Prop. 1's Ritz values of every source on the GPU
+    mon_info, mon_arr = fks.make_info(n_rhs, pr.m_max, n_f)
+    fks.fks_solve(solver.op, b_d, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X_d, est, bnd, tru, mj, sst,
+                  mon_info, sh)
+    theta = np.zeros((n_rhs, pr.m_max), np.complex128)
+    rstat = np.zeros(n_rhs, np.int32)
+    steps_m = np.ascontiguousarray(mon_arr["steps"])
+    fks.fks_ritz(solver.ctx, mon_arr["hbar"], mon_arr["tau_k"], steps_m, n_rhs, pr.m_max, theta, rstat, sh)
+    r0 = time.perf_counter()
+    fks.fks_ritz(solver.ctx, mon_arr["hbar"], mon_arr["tau_k"], steps_m, n_rhs, pr.m_max, theta, rstat, sh)
+    ritz_ms = 1000 * (time.perf_counter() - r0)
+    k0 = int(steps_m[0])
+    monitors = {"ritz_ms": ritz_ms, "ritz_status": rstat.tolist(), "ritz_steps": k0,
+                "ritz_real_range": [float(theta[0, :k0].real.min()), float(theta[0, :k0].real.max())] if k0 else None,
+                "max_gmres_alpha": float(np.max(mon_arr["gmres_alpha"])),
+                "note": "Prop. 3's alpha is recorded by the Givens update; the Ritz values (sigma = 0) take one "
+                        "launch of one warp per source, timed here with its host copies"}
+
     # ---- the same workload in the paper's plain configuration (complex128,
     # fixed inner tolerance) and in the mixed, relaxed one, on this GPU
     def variant(v_prec, v_relax, reps=3, warm=2):
@@ -887,7 +907,7 @@ def main():
                            "tile8_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[4],
                            "launch_mode": args.launch_mode},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
-                "e2e": e2e, "comparison": comparison,
+                "e2e": e2e, "comparison": comparison, "monitors": monitors,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)

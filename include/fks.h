@@ -196,6 +196,25 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
 fks_status fks_op_apply(fks_op* op, fks_c128 s, const fks_c128* x, fks_c128* y, int n_vec, void* stream);
 
 /*
+ * Prop. 1's Ritz values (Section 3, Eq. genritz) of every source of a solve,
+ * from its monitors (fks_info hbar, tau_k, steps): the eigenvalues theta of
+ * H_m(sigma; T_m) f = theta H_m f with m = steps[r], at sigma = 0. At another
+ * shift they are theta + sigma (H_m^{-1} H_m(sigma; T_m) = H_m^{-1} - T_m + sigma I);
+ * they approximate lambda + sigma, lambda the eigenvalues of K x = lambda M x.
+ * Computed on the GPU, one warp per source: Gauss-Jordan inverse of H_m,
+ * Householder reduction of H_m^{-1} - T_m to Hessenberg form, shifted QR.
+ *  hbar   [(m_max + 1) * m_max * n_rhs], tau_k [m_max * n_rhs], steps [n_rhs] in
+ *         (the layouts of fks_info; 0 <= steps[r] <= m_max)
+ *  theta  [m_max * n_rhs] out: source r's m values at r * m_max (unordered),
+ *         zero beyond them
+ *  status [n_rhs] out: 0 converged; 1 the QR sweep limit (60 m) was reached and
+ *         theta holds the unconverged diagonal; 2 H_m is singular (theta zero)
+ * Pointers host or device; m_max <= 128. Outputs complete when the call returns.
+ */
+fks_status fks_ritz(fks_ctx* ctx, const fks_c128* hbar, const fks_c128* tau_k, const int32_t* steps,
+                    int n_rhs, int m_max, fks_c128* theta, int32_t* status, void* stream);
+
+/*
  * Sensitivities of the phasor measurements by the adjoint-state method
  * (Section 5: Eq. measurement, Eq. sensitivity, Eq. adjoint, Algorithm 6), for
  * grid operators (fks_op_grid). Sensor m sits in cell x_m and records

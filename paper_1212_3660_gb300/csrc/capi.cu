@@ -27,6 +27,7 @@
 #include "assemble_tc.cuh"
 #include "cluster.cuh"
 #include "sensitivity.cuh"
+#include "monitors.cuh"
 
 namespace fks {
 
@@ -1818,6 +1819,52 @@ fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y,
     return FKS_ERR_CUDA;
   }
   return FKS_OK;
+}
+
+fks_status fks_ritz(fks_ctx* ctx, const fks_c128* hbar, const fks_c128* tau_k, const int32_t* steps, int n_rhs,
+                    int m_max, fks_c128* theta, int32_t* status, void* stream) {
+  if (!ctx || !hbar || !tau_k || !steps || !theta || !status) { set_error("fks_ritz: NULL argument"); return FKS_ERR_ARG; }
+  if (n_rhs < 1 || m_max < 1 || m_max > MAX_M) { set_error("fks_ritz: need n_rhs >= 1 and 1 <= m_max <= 128"); return FKS_ERR_ARG; }
+  if (!is_device_ptr(steps))
+    for (int r = 0; r < n_rhs; ++r)
+      if (steps[r] < 0 || steps[r] > m_max) { set_error("fks_ritz: steps outside [0, m_max]"); return FKS_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nh = (size_t)(m_max + 1) * m_max * n_rhs, nt = (size_t)m_max * n_rhs;
+  std::vector<void*> owned;
+  auto dev = [&](const void* p, size_t bytes) -> void* {
+    if (is_device_ptr(p)) return (void*)p;
+    void* d = nullptr;
+    CK(cudaMallocAsync(&d, bytes, s));
+    owned.push_back(d);
+    CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s));
+    return d;
+  };
+  fks_status ret = FKS_OK;
+  try {
+    CK(cudaSetDevice(ctx->device));
+    const z64* hd = (const z64*)dev(hbar, sizeof(z64) * nh);
+    const z64* td = (const z64*)dev(tau_k, sizeof(z64) * nt);
+    const int32_t* sd = (const int32_t*)dev(steps, sizeof(int32_t) * n_rhs);
+    z64* scratch = nullptr;
+    CK(cudaMallocAsync((void**)&scratch, sizeof(z64) * 2 * (size_t)n_rhs * m_max * m_max, s));
+    owned.push_back(scratch);
+    z64* thd = is_device_ptr(theta) ? (z64*)theta : nullptr;
+    if (!thd) { CK(cudaMallocAsync((void**)&thd, sizeof(z64) * nt, s)); owned.push_back(thd); }
+    int32_t* std_ = is_device_ptr(status) ? status : nullptr;
+    if (!std_) { CK(cudaMallocAsync((void**)&std_, sizeof(int32_t) * n_rhs, s)); owned.push_back(std_); }
+    launch_ritz(hd, td, sd, n_rhs, m_max, scratch, thd, std_, s);
+    CK(cudaGetLastError());
+    if (thd != (z64*)theta) CK(cudaMemcpyAsync(theta, thd, sizeof(z64) * nt, cudaMemcpyDeviceToHost, s));
+    if (std_ != status) CK(cudaMemcpyAsync(status, std_, sizeof(int32_t) * n_rhs, cudaMemcpyDeviceToHost, s));
+    for (void* p : owned) cudaFreeAsync(p, s);
+    owned.clear();
+    CK(cudaStreamSynchronize(s));
+  } catch (CudaError& e) {
+    for (void* p : owned) cudaFreeAsync(p, s);
+    set_error(std::string("fks_ritz: ") + e.where + ": " + cudaGetErrorString(e.e));
+    ret = e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+  return ret;
 }
 
 fks_status fks_sensitivity(fks_op* op, const fks_c128* phi, const fks_c128* psi, int n_m, const fks_c128* sigma,

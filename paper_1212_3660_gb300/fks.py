@@ -92,6 +92,7 @@ def lib():
                             vp, C.POINTER(fks_info), vp]
     L.fks_op_apply.argtypes = [vp, fks_c128, vp, vp, C.c_int, vp]
     L.fks_sensitivity.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, vp]
+    L.fks_ritz.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp, vp, vp]
     L.fks_precond_apply.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p, f64p, vp]
     L.fks_precond_apply_noalloc.argtypes = [vp, fks_c128, vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, i32p,
                                             f64p, vp]
@@ -114,7 +115,7 @@ def lib():
     L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
-    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_precond_apply", "fks_profile_select",
+    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
                  "fks_server_create",
@@ -240,6 +241,15 @@ def fks_sensitivity(op, phi, psi, n_m, sigma, n_f, j_lnk, j_lns, stream=None):
     """dh/dlnK and dh/dlnS of every measurement, shift and cell (arrays as numpy or torch)."""
     st = lib().fks_sensitivity(op, _ptr(phi), _ptr(psi), int(n_m), _ptr(sigma), int(n_f), _ptr(j_lnk), _ptr(j_lns),
                                stream)
+    if st < 0:
+        raise FksError(st, fks_last_error())
+    return st
+
+
+def fks_ritz(ctx, hbar, tau_k, steps, n_rhs, m_max, theta, status, stream=None):
+    """Prop. 1's Ritz values at sigma = 0 of every source (arrays as numpy or torch)."""
+    st = lib().fks_ritz(ctx, _ptr(hbar), _ptr(tau_k), _ptr(steps), int(n_rhs), int(m_max), _ptr(theta), _ptr(status),
+                        stream)
     if st < 0:
         raise FksError(st, fks_last_error())
     return st

@@ -113,3 +113,15 @@ class Solver:
             js = np.zeros_like(psi)
         fks.fks_sensitivity(self.op, phi, psi, n_m, sigma, n_f, jk, js, stream)
         return jk, js
+
+    def ritz(self, out):
+        """(theta, status) of Prop. 1 for every source of a SolveOutput: theta
+        n_rhs x m_max at sigma = 0 (the first steps[r] entries of row r are its
+        Ritz values; add sigma for another shift), status per source."""
+        n_rhs, m_max = out.hbar.shape[0], out.hbar.shape[1]
+        theta = np.zeros((n_rhs, m_max), np.complex128)
+        status = np.zeros(n_rhs, np.int32)
+        steps = np.ascontiguousarray(out.steps, dtype=np.int32)
+        fks.fks_ritz(self.ctx, np.ascontiguousarray(out.hbar), np.ascontiguousarray(out.tau_k), steps, n_rhs, m_max,
+                     theta, status)
+        return theta, status

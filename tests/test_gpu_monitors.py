@@ -50,3 +50,86 @@ def test_alpha_of_zero_rhs_source_and_multi_source_slices():
     assert np.array_equal(out.gmres_alpha[2], solo.gmres_alpha[0])
     assert np.array_equal(out.hbar[2], solo.hbar[0]) and np.array_equal(out.tau_k[2], solo.tau_k[0])
     s.close()
+
+
+def _match(a, b):
+    """max distance of a greedy nearest pairing of two multisets of complex values"""
+    b = list(b)
+    worst = 0.0
+    for x in sorted(a, key=lambda z: -abs(z)):
+        d = [abs(x - y) for y in b]
+        i = int(np.argmin(d))
+        worst = max(worst, d[i])
+        b.pop(i)
+    return worst
+
+
+def test_ritz_values_of_a_solve_match_oracle():
+    """fks_ritz on a solve's exported H_bar and tau_k (two sources, one with a zero
+    right-hand side) against the oracle's Ritz values of the same matrices."""
+    need_gpu()
+    from oracle.monitors import ritz_pairs
+    pr = synth.make_problem((40, 36), n_f=8, periods=(5.0, 3600.0), n_p=3, seed=53, n_src=2, m_max=60)
+    s = Solver(pr)
+    b = pr.rhs().T.copy()
+    b[1] = 0
+    out = s.solve(b, inner_tol=1e-10)
+    theta, status = s.ritz(out)
+    k = int(out.steps[0])
+    assert k > 5 and np.all(status == 0)
+    H = out.hbar[0, :k, :k + 1].T
+    ref = ritz_pairs(H, out.tau_k[0], 0.0, k)[0]
+    assert _match(theta[0, :k], ref) <= 1e-9 * np.max(np.abs(ref))
+    assert np.all(theta[0, k:] == 0) and np.all(theta[1] == 0) and int(out.steps[1]) == 0
+    s.close()
+
+
+@pytest.mark.parametrize("m", [1, 2, 17, 64, 128])
+def test_ritz_values_of_random_hessenberg_matrices(m):
+    """The GPU eigenvalue solver against NumPy on random upper Hessenberg H_bar
+    (positive subdiagonal, as Arnoldi produces; eigenvalues that a relative
+    perturbation of 1e-14 moves by at most 1e-13) and random tau, up to m_max."""
+    need_gpu()
+    from paper_1212_3660_gb300 import fks as F
+    rng = np.random.default_rng(m)
+    n_rhs, m_max = 3, max(m, 2)
+    hbar = np.zeros((n_rhs, m_max, m_max + 1), np.complex128)
+    tau = np.zeros((n_rhs, m_max), np.complex128)
+    steps = np.array([m, max(1, m // 2), m], np.int32)
+    ctx = F.fks_create(0)
+    refs = []
+    for r in range(n_rhs):
+        k = int(steps[r])
+        Hm = np.triu(rng.standard_normal((k + 1, k)) + 1j * rng.standard_normal((k + 1, k)), -1)
+        for c in range(k):
+            Hm[c + 1, c] = abs(Hm[c + 1, c]) + 0.1
+        # a dominant diagonal keeps H_m and the eigenvalues well conditioned
+        # (random Hessenberg matrices of order 64 reach cond 1e10)
+        Hm[:k, :k] += (2.0 + 1.0j) * np.sqrt(k) * np.eye(k)
+        hbar[r, :k, :k + 1] = Hm.T
+        tau[r, :k] = 1j * np.exp(rng.uniform(-3, 0, k))
+        G = np.linalg.inv(Hm[:k, :k]) - np.diag(tau[r, :k])
+        refs.append(np.linalg.eigvals(G))
+    theta = np.zeros((n_rhs, m_max), np.complex128)
+    status = np.zeros(n_rhs, np.int32)
+    F.fks_ritz(ctx, hbar, tau, steps, n_rhs, m_max, theta, status)
+    assert np.all(status == 0), status
+    for r in range(n_rhs):
+        k = int(steps[r])
+        assert _match(theta[r, :k], refs[r]) <= 1e-8 * np.max(np.abs(refs[r])), r
+    F.fks_destroy(ctx)
+
+
+def test_ritz_rejects_bad_arguments():
+    need_gpu()
+    from paper_1212_3660_gb300 import fks as F
+    ctx = F.fks_create(0)
+    h = np.zeros((1, 4, 5), np.complex128)
+    t = np.zeros((1, 4), np.complex128)
+    th = np.zeros((1, 4), np.complex128)
+    stt = np.zeros(1, np.int32)
+    with pytest.raises(F.FksError):
+        F.fks_ritz(ctx, h, t, np.array([5], np.int32), 1, 4, th, stt)
+    with pytest.raises(F.FksError):
+        F.fks_ritz(ctx, h, t, np.array([2], np.int32), 1, 129, th, stt)
+    F.fks_destroy(ctx)
