@@ -98,10 +98,14 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
     inner_relax > 0: the inner tolerance of step k is relaxed_eps(eps, inner_relax,
     tol, R_{k-1}) and is passed as inner(v, tau_index, k, eps_k); the stopping
     test stays the bound of Eq. trueresidual with the measured ||p_i||.
+    tol may be one value or one per shift (a restarted solve gives each shift
+    its own share of the tolerance); the relaxed rule uses the smallest.
     """
     n = op.n
     sigmas = np.asarray(sigmas, dtype=np.complex128)
     nf = len(sigmas)
+    tols = np.broadcast_to(np.asarray(tol, dtype=np.float64), (nf,))
+    tol = float(tols.min()) if nf else 0.0
     b = np.asarray(b, dtype=np.complex128).reshape(n)
     beta = float(np.linalg.norm(b))
     x = np.zeros((n, nf), dtype=np.complex128)
@@ -163,9 +167,9 @@ def shifted_solve(op, b, sigmas, taus_bar, sched, tol, m_max, inner, variant="fg
             bound = rt + float(np.sum(np.abs(y) * pnorm[:k]))
             if replay_mj is not None:
                 done = k == int(replay_mj[j]) or breakdown
-                conv = bound <= tol * beta
+                conv = bound <= tols[j] * beta
             else:
-                conv = bound <= tol * beta
+                conv = bound <= tols[j] * beta
                 done = conv or breakdown or k == m_max
             if done:
                 live[j] = False
