@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--cluster-max", type=int, default=None,
                     help="with --fuse-max: from the first level of at most this many cells down, the cluster "
                          "V-cycle kernel (0: off)")
+    ap.add_argument("--variant", default="fgmres", choices=["fgmres", "ffom"])
+    ap.add_argument("--restart", type=int, default=0,
+                    help="restarted FFOM with cycles of this many steps (needs --variant ffom; 0: none)")
     ap.add_argument("--sensors", type=int, default=JAC_SENSORS, help="workload 6: sensors (adjoint sources)")
     ap.add_argument("--shift-stride", type=int, default=1,
                     help="workload 6: every k-th shift of the workload (a smaller case, e.g. for ncu)")
@@ -681,12 +684,14 @@ def main():
     X_d = torch.empty((n_rhs, n_f, n), dtype=torch.complex128, device=dev)
     est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
     mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
+    variant = fks.FKS_FFOM if args.variant == "ffom" else fks.FKS_FGMRES
     opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
                                   schedule=pr.schedule, launch_mode=0 if args.launch_mode == "graph" else 1,
-                                  inner_relax=args.inner_relax)
+                                  inner_relax=args.inner_relax, variant=variant, restart_len=args.restart)
     # host-driven launches (identical kernels) for per-launch event timing
     opts_host, keep_host = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
-                                            schedule=pr.schedule, launch_mode=1, inner_relax=args.inner_relax)
+                                            schedule=pr.schedule, launch_mode=1, inner_relax=args.inner_relax,
+                                            variant=variant, restart_len=args.restart)
     info, info_arr = fks.make_info(n_rhs, pr.m_max)
 
     def step(b, X, o=opts):
@@ -826,7 +831,11 @@ def main():
     # tau_k (Prop. 3's alpha comes from the Givens update at no extra launch),
     # then Prop. 1's Ritz values of every source on the GPU
     mon_info, mon_arr = fks.make_info(n_rhs, pr.m_max, n_f)
-    fks.fks_solve(solver.op, b_d, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X_d, est, bnd, tru, mj, sst,
+    mon_opts = opts
+    if args.restart > 0:   # restarted solves export no monitors: take them from one unrestarted solve
+        mon_opts, mon_keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                              schedule=pr.schedule, inner_relax=args.inner_relax, variant=variant)
+    fks.fks_solve(solver.op, b_d, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), mon_opts, X_d, est, bnd, tru, mj, sst,
                   mon_info, sh)
     theta = np.zeros((n_rhs, pr.m_max), np.complex128)
     rstat = np.zeros(n_rhs, np.int32)
@@ -905,7 +914,9 @@ def main():
                            "tail_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[2],
                            "cluster_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[3],
                            "tile8_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[4],
-                           "launch_mode": args.launch_mode},
+                           "launch_mode": args.launch_mode, "variant": args.variant,
+                           "restart_len": args.restart,
+                           "basis_bytes_per_source": (2 * (args.restart or pr.m_max) + 1) * n * 16},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": e2e, "comparison": comparison, "monitors": monitors,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),

@@ -143,6 +143,19 @@ typedef struct {
                             after step k-1 (R_0 = 1); the idea Section 4 closes with (after
                             Simoncini and Szyld). Convergence is still decided by the bound of
                             Eq. trueresidual with the measured ||p_k||. <= 0: eps at every step */
+  int restart_len;       /* > 0: restarted FFOM (Section 2.2.2): cycles of at most restart_len
+                            steps (<= m_max), each restarted on the common residual direction
+                            v_{k+1} of the shifts not yet certified (FOM residuals are
+                            collinear, Eq. fomresidualsimplified), x_j += C_j d_j; the tau
+                            schedule continues across cycles; each shift carries the part of
+                            its error the finished cycles' estimates did not see (Eq.
+                            trueresidual) and is certified when that plus its current bound is
+                            <= tol. Needs variant FKS_FFOM and no replay; the workspace holds
+                            restart_len + 1 basis vectors per source instead of m_max + 1.
+                            m_j counts steps over all cycles; fks_info reports steps and
+                            breakdown only. 0: no restarts                                     */
+  int max_restarts;      /* cycles after the first (<= 0: 20); shifts still open then are
+                            FKS_NOT_CONVERGED                                                  */
 } fks_options;
 
 /* Optional per-solve diagnostics, host arrays owned by the caller (any may be NULL). */
@@ -278,6 +291,8 @@ typedef struct {
  * admitted batches' workspaces may use together (one oversized request still
  * runs when nothing else is in flight). */
 fks_status fks_server_create(fks_ctx* ctx, size_t mem_budget_bytes, int lanes, fks_server** out);
+/* FKS_ERR_ARG for replayed (replay_mode) or restarted (restart_len) requests:
+ * those go through fks_solve. */
 fks_status fks_server_submit(fks_server* srv, const fks_request* req, uint64_t* ticket);
 /* done = 1 when finished or cancelled; result = the request's status. */
 fks_status fks_server_poll(fks_server* srv, uint64_t ticket, int* done, fks_status* result);

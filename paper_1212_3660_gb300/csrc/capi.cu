@@ -6,6 +6,7 @@
 // correction in complex128. All per-step state lives in device memory; the
 // host only enqueues kernels and reads small flags to decide when a loop ends.
 #include <algorithm>
+#include <complex>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -260,6 +261,15 @@ static std::vector<LevelHost> level_shapes(int nx, int ny, int nz, const double 
 }
 
 // ------------------------------------------------------------------ solve state
+// Hooks of one cycle of a restarted solve (solve_restarted) into solve_impl.
+struct RestartIO {
+  const double* tol_shift;  // host [n_f * n_rhs]: each shift's tolerance, relative to its source's ||b||
+  z64* coef;                // host out [n_f * n_rhs]: FFOM residual coefficient c at each shift's freeze step
+  double* beta;             // host out [n_rhs]: ||b|| of each source
+  int32_t* steps;           // host out [n_rhs]: Arnoldi steps taken
+  z64* v_next;              // device out [n * n_rhs]: v_{k+1} after the last step, the common residual direction
+};
+
 struct Solve {
   fks_op* op;
   Lane* lane;
@@ -274,6 +284,9 @@ struct Solve {
   z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
   double* alpha;   // Prop. 3's alpha per (source, shift) at its freeze step
+  double* tolv;    // per-shift tolerances of a restart cycle (used when tolv_on)
+  z64* rcoef;      // FFOM residual coefficient per shift at its freeze step (restart cycles)
+  bool tolv_on = false;
   int32_t *cyc, *sst, *mj, *sched, *rep_cyc, *rep_mj, *singular, *flags, *counter, *bcount;
   // multigrid, cycle precision
   std::vector<void*> f, z, z2, invd;
@@ -689,7 +702,8 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
   PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, S.s));
   PROF(FKS_K_GIVENS, -1, ns * n_f * 48.0 * kk, ns * n_f * 26.0 * kk,
        launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant, S.replay ? S.rep_mj : nullptr,
-                     S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, S.alpha, n_rhs, S.s));
+                     S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, S.alpha, n_rhs, S.s,
+                     S.tolv_on ? S.tolv : nullptr, S.tolv_on ? S.rcoef : nullptr));
   PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, use_cond, hout, S.s));
 }
 
@@ -906,6 +920,8 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.est = A.take<double>((size_t)ns * nf);
   S.bnd = A.take<double>((size_t)ns * nf);
   S.alpha = A.take<double>((size_t)ns * nf);
+  S.tolv = A.take<double>((size_t)ns * nf);
+  S.rcoef = A.take<z64>((size_t)ns * nf);
   S.tpart = A.take<double>((size_t)ns * nf * (S.op->csr ? csr_blocks(n) : tres_blocks(Ls[0])));
   S.tres = A.take<double>((size_t)ns * nf);
   S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
@@ -925,7 +941,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                              const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X, double* res_est,
                              double* res_bound, double* res_true, int32_t* m_j, int32_t* shift_status, fks_info* info,
                              cudaStream_t s, const std::vector<OutGroup>* groups = nullptr,
-                             std::unique_lock<std::mutex>* api_lock = nullptr) {
+                             std::unique_lock<std::mutex>* api_lock = nullptr, const RestartIO* rio = nullptr) {
   Solve S{};
   S.op = op;
   S.lane = lane;
@@ -943,6 +959,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   S.eps = o->inner_tol > 0 ? o->inner_tol : std::min(1e-6, o->tol / 100.0);
   S.max_cycles = o->inner_max_cycles > 0 ? o->inner_max_cycles : 50;
   S.replay = o->replay_mode != 0;
+  S.tolv_on = rio != nullptr;
   S.inner_steps = o->inner_steps > 0 ? o->inner_steps : 8;
   S.relax = o->inner_relax > 0 ? o->inner_relax : 0.0;
   bool x_dev = groups ? false : is_device_ptr(X);
@@ -960,6 +977,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   int m = S.m;
   // inputs
   copy_in(S.b, b, sizeof(z64) * n * n_rhs, s);
+  if (rio) CK(cudaMemcpyAsync(S.tolv, rio->tol_shift, sizeof(double) * n_f * n_rhs, cudaMemcpyHostToDevice, s));
   copy_in(S.sigma, sigma, sizeof(z64) * n_f, s);
   copy_in(S.taus, tau, sizeof(z64) * n_tau, s);
   CK(cudaMemcpyAsync(S.sched, o->tau_schedule, sizeof(int32_t) * o->sched_len, cudaMemcpyHostToDevice, s));
@@ -991,7 +1009,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
                                  (double)op->tile16_max[1], S.relax, (double)op->tail_max[0],
                                  (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1],
-                                 (double)op->tile8_max[0], (double)op->tile8_max[1]};
+                                 (double)op->tile8_max[0], (double)op->tile8_max[1], (double)S.tolv_on};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1111,6 +1129,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   if (info && info->gmres_alpha) copy_out(info->gmres_alpha, S.alpha, sizeof(double) * n_f * n_rhs, s);
   if (info && info->hbar) copy_out(info->hbar, S.H, sizeof(z64) * (m + 1) * m * n_rhs, s);
   if (info && info->tau_k) copy_out(info->tau_k, S.taus_k, sizeof(z64) * m * n_rhs, s);
+  if (rio) CK(cudaMemcpyAsync(rio->coef, S.rcoef, sizeof(z64) * n_f * n_rhs, cudaMemcpyDeviceToHost, s));
   if (!pn_h.empty()) CK(cudaMemcpyAsync(pn_h.data(), S.pn, sizeof(double) * m * n_rhs, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * n_rhs, cudaMemcpyDeviceToHost, s));
   int singular = 0;
@@ -1127,6 +1146,17 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
     if (info->pnorm) std::memcpy(info->pnorm, pn_h.data(), sizeof(double) * m * n_rhs);
   }
   (void)steps;
+  if (rio) {
+    // the common residual direction v_{k+1} of each source for the next cycle
+    for (int r = 0; r < n_rhs; ++r) {
+      rio->beta[r] = S.st_host[r].beta;
+      rio->steps[r] = S.st_host[r].beta > 0 ? S.st_host[r].k : 0;
+      if (rio->steps[r] > 0)
+        CK(cudaMemcpyAsync(rio->v_next + (size_t)r * n, S.V + (size_t)r * (m + 1) * n + (size_t)rio->steps[r] * n,
+                           sizeof(z64) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+  }
   if (tc_err_h) {
     set_error("tensor-core assembly: a wait for copies or MMAs gave up after two seconds");
     return FKS_ERR_CUDA;
@@ -1160,6 +1190,184 @@ static int status_rank(fks_status s) {
 
 // Sources are solved in lockstep batches sized to the free device memory:
 // one batch when they all fit, otherwise equal batches one after another.
+// Restarted flexible FOM (Section 2.2.2): FOM residuals of all shifts are
+// collinear, r_j = c_j v_{k+1} (Eq. fomresidualsimplified), so a cycle of at
+// most restart_len steps is followed by one on v_{k+1} for the shifts not yet
+// certified, each with its right-hand side scaled by its own coefficient.
+// With the residual estimate C_j v of the current iterate and the part A_j that
+// the estimates of the finished cycles did not see (Eq. trueresidual), shift j
+// is certified when its cycle's bound reaches (tol ||b|| - A_j) / |C_j| (its
+// per-shift tolerance), and x_j += C_j d_j. The tau schedule continues across
+// cycles. One source at a time; every cycle is an ordinary solve_impl.
+template <typename VT>
+static fks_status solve_restarted(fks_op* op, Lane* lane, const fks_c128* b, int n_rhs, const fks_c128* sigma,
+                                  int n_f, const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X,
+                                  double* res_est, double* res_bound, double* res_true, int32_t* m_j,
+                                  int32_t* shift_status, fks_info* info, cudaStream_t s) {
+  const int64_t n = op->n;
+  const int len = o->restart_len;
+  const int max_cycles = (o->max_restarts > 0 ? o->max_restarts : 20) + 1;
+  const double tol = o->tol;
+  std::vector<fks_c128> sg(n_f);
+  CK(cudaMemcpy(sg.data(), sigma, sizeof(fks_c128) * n_f, cudaMemcpyDefault));
+  const int nblk = op->csr ? csr_blocks(n) : tres_blocks(op->levels[0]);
+  // device buffers of one source: accumulated x, a cycle's x, residual directions,
+  // right-hand side, and the final true residual's inputs
+  std::vector<void*> owned;
+  auto dmalloc = [&](size_t bytes) {
+    void* p = nullptr;
+    CK(cudaMallocAsync(&p, bytes, s));
+    owned.push_back(p);
+    return p;
+  };
+  struct Freer {
+    std::vector<void*>& v;
+    cudaStream_t s;
+    ~Freer() { for (void* p : v) cudaFreeAsync(p, s); }
+  } freer{owned, s};
+  z64* xacc = (z64*)dmalloc(sizeof(z64) * n * n_f);
+  z64* xhat = (z64*)dmalloc(sizeof(z64) * n * n_f);
+  z64* vcur = (z64*)dmalloc(sizeof(z64) * n);
+  z64* vnext = (z64*)dmalloc(sizeof(z64) * n);
+  z64* bdev = (z64*)dmalloc(sizeof(z64) * n);
+  z64* sgd = (z64*)dmalloc(sizeof(z64) * n_f);
+  double* tpart = (double*)dmalloc(sizeof(double) * n_f * nblk);
+  double* trd = (double*)dmalloc(sizeof(double) * n_f);
+  SlotState* std_ = (SlotState*)dmalloc(sizeof(SlotState));
+  int32_t* idxd = (int32_t*)dmalloc(sizeof(int32_t) * n_f);
+  z64* acd = (z64*)dmalloc(sizeof(z64) * n_f);
+  CK(cudaMemcpyAsync(sgd, sg.data(), sizeof(z64) * n_f, cudaMemcpyHostToDevice, s));
+  std::vector<double> est((size_t)n_f * n_rhs), bnd((size_t)n_f * n_rhs), tru((size_t)n_f * n_rhs);
+  std::vector<int32_t> mj((size_t)n_f * n_rhs), sst((size_t)n_f * n_rhs);
+  bool any_nc = false, any_bd = false;
+  for (int r = 0; r < n_rhs; ++r) {
+    CK(cudaMemsetAsync(xacc, 0, sizeof(z64) * n * n_f, s));
+    copy_in(bdev, b + (size_t)r * n, sizeof(z64) * n, s);
+    std::vector<std::complex<double>> C(n_f, 1.0);
+    std::vector<double> A(n_f, 0.0);
+    std::vector<int> live(n_f);
+    for (int j = 0; j < n_f; ++j) live[j] = j;
+    double beta0 = 0.0;
+    int done_steps = 0;
+    bool breakdown = false;
+    double* er = est.data() + (size_t)r * n_f;
+    double* br = bnd.data() + (size_t)r * n_f;
+    int32_t* mr = mj.data() + (size_t)r * n_f;
+    int32_t* sr = sst.data() + (size_t)r * n_f;
+    for (int j = 0; j < n_f; ++j) sr[j] = FKS_NOT_CONVERGED;
+    for (int cyc = 0; cyc < max_cycles && !live.empty(); ++cyc) {
+      const int nl = (int)live.size();
+      std::vector<fks_c128> ss(nl);
+      std::vector<double> tl(nl);
+      for (int i = 0; i < nl; ++i) {
+        const int j = live[i];
+        // cycle 0 solves with b itself (figures relative to ||b||), later ones with a unit v
+        tl[i] = cyc == 0 ? tol : (tol * beta0 - A[j]) / std::abs(C[j]);
+      }
+      // shifts whose carried error alone exceeds the tolerance cannot be certified
+      std::vector<int> nlive;
+      std::vector<double> ntl;
+      for (int i = 0; i < nl; ++i)
+        if (tl[i] > 0.0) { nlive.push_back(live[i]); ntl.push_back(tl[i]); }
+      live = nlive;
+      if (live.empty()) break;
+      const int nk = (int)live.size();
+      for (int i = 0; i < nk; ++i) ss[i] = sg[live[i]];
+      ss.resize(nk);
+      std::vector<int32_t> sched(o->sched_len);
+      for (int i = 0; i < o->sched_len; ++i) sched[i] = o->tau_schedule[(done_steps + i) % o->sched_len];
+      fks_options oc = *o;
+      oc.m_max = len;
+      oc.tau_schedule = sched.data();
+      oc.restart_len = 0;
+      std::vector<double> e_c(nk), b_c(nk);
+      std::vector<int32_t> m_c(nk), s_c(nk);
+      std::vector<z64> coef(nk);
+      double beta_c = 0.0;
+      int32_t steps_c = 0;
+      RestartIO rio{ntl.data(), coef.data(), &beta_c, &steps_c, vnext};
+      const fks_c128* rhs = cyc == 0 ? (const fks_c128*)bdev : (const fks_c128*)vcur;
+      fks_status st = solve_impl<VT>(op, lane, rhs, 1, ss.data(), nk, tau, n_tau, &oc, (fks_c128*)xhat, e_c.data(),
+                                     b_c.data(), nullptr, m_c.data(), s_c.data(), nullptr, s, nullptr, nullptr, &rio);
+      if (st < 0) return st;
+      if (cyc == 0) {
+        beta0 = beta_c;
+        if (beta0 == 0.0) {   // zero right-hand side: x = 0 for every shift
+          for (int j = 0; j < n_f; ++j) { sr[j] = FKS_OK; er[j] = br[j] = 0.0; mr[j] = 0; }
+          live.clear();
+          break;
+        }
+      }
+      // x_j += a_j d_j with a_j = 1 on the first cycle (its right-hand side is b), C_j after
+      std::vector<int32_t> idx(nk);
+      std::vector<z64> acoef(nk);
+      for (int i = 0; i < nk; ++i) {
+        idx[i] = live[i];
+        const std::complex<double> a = cyc == 0 ? std::complex<double>(1.0) : C[live[i]];
+        acoef[i] = mk(a.real(), a.imag());
+      }
+      CK(cudaMemcpyAsync(idxd, idx.data(), sizeof(int32_t) * nk, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(acd, acoef.data(), sizeof(z64) * nk, cudaMemcpyHostToDevice, s));
+      launch_axpy_cols(xacc, xhat, idxd, acd, nk, n, s);
+      CK(cudaGetLastError());
+      std::vector<int> next;
+      for (int i = 0; i < nk; ++i) {
+        const int j = live[i];
+        const double sc = cyc == 0 ? beta0 : std::abs(C[j]);   // absolute scale of the cycle's relative figures
+        const double rs = cyc == 0 ? 1.0 : sc / beta0;         // the same, relative to ||b||
+        const std::complex<double> a(acoef[i].re, acoef[i].im);
+        if (s_c[i] == FKS_OK || s_c[i] == FKS_BREAKDOWN_EXACT) {
+          sr[j] = s_c[i];
+          er[j] = rs * e_c[i];
+          br[j] = rs * b_c[i] + A[j] / beta0;
+          mr[j] = done_steps + m_c[i];
+        } else {
+          A[j] += sc * (b_c[i] - e_c[i]);
+          C[j] = a * std::complex<double>(coef[i].re, coef[i].im);
+          er[j] = std::abs(C[j]) / beta0;
+          br[j] = (std::abs(C[j]) + A[j]) / beta0;
+          mr[j] = done_steps + m_c[i];
+          next.push_back(j);
+        }
+      }
+      done_steps += steps_c;
+      if (steps_c < len && !next.empty()) breakdown = true;  // cannot happen without a breakdown status
+      live = next;
+      std::swap(vcur, vnext);
+      if (breakdown) break;
+    }
+    for (int j = 0; j < n_f; ++j) {
+      if (sr[j] == FKS_NOT_CONVERGED) any_nc = true;
+      if (sr[j] == FKS_BREAKDOWN_EXACT) any_bd = true;
+    }
+    // true residuals of the accumulated x against b
+    if (res_true) {
+      SlotState sh{};
+      sh.beta = beta0;
+      CK(cudaMemcpyAsync(std_, &sh, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+      if (op->csr)
+        launch_csr_true_residual(op->cd.view<double>(n), sgd, n_f, bdev, xacc, tpart, std_, trd, 1, s);
+      else
+        launch_true_residual(op->levels[0], sgd, n_f, bdev, xacc, tpart, std_, trd, 1, s);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(tru.data() + (size_t)r * n_f, trd, sizeof(double) * n_f, cudaMemcpyDeviceToHost, s));
+    }
+    copy_out(X + (size_t)r * n_f * n, xacc, sizeof(z64) * n * n_f, s);
+    CK(cudaStreamSynchronize(s));
+    if (info) {
+      if (info->steps) info->steps[r] = done_steps;
+      if (info->breakdown) info->breakdown[r] = breakdown ? 1 : 0;
+    }
+  }
+  copy_out(res_est, est.data(), sizeof(double) * n_f * n_rhs, s);
+  copy_out(res_bound, bnd.data(), sizeof(double) * n_f * n_rhs, s);
+  if (res_true) copy_out(res_true, tru.data(), sizeof(double) * n_f * n_rhs, s);
+  copy_out(m_j, mj.data(), sizeof(int32_t) * n_f * n_rhs, s);
+  copy_out(shift_status, sst.data(), sizeof(int32_t) * n_f * n_rhs, s);
+  CK(cudaStreamSynchronize(s));
+  return any_nc ? FKS_NOT_CONVERGED : (any_bd ? FKS_BREAKDOWN_EXACT : FKS_OK);
+}
+
 template <typename VT>
 static fks_status solve_chunked(fks_op* op, Lane* lane, const fks_c128* b, int n_rhs, const fks_c128* sigma, int n_f,
                                 const fks_c128* tau, int n_tau, const fks_options* o, fks_c128* X, double* res_est,
@@ -1472,6 +1680,11 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   if (o->assembly != 0 && o->assembly != 1) { set_error("fks_solve: assembly must be 0 or 1"); return FKS_ERR_ARG; }
   if (!std::isfinite(o->inner_relax)) { set_error("fks_solve: inner_relax is not finite"); return FKS_ERR_ARG; }
   if (o->replay_mode && (!o->replay_inner_cycles || !o->replay_mj)) { set_error("fks_solve: replay arrays missing"); return FKS_ERR_ARG; }
+  if (o->restart_len < 0 || o->restart_len > o->m_max) { set_error("fks_solve: restart_len must be in 0..m_max"); return FKS_ERR_ARG; }
+  if (o->restart_len > 0 && (o->variant != FKS_FFOM || o->replay_mode)) {
+    set_error("fks_solve: restarts need the FFOM variant (collinear residuals) and no replay");
+    return FKS_ERR_ARG;
+  }
   if (o->replay_mode) {
     for (int i = 0; i < o->m_max * n_rhs; ++i)
       if (o->replay_inner_cycles[i] < 0 || o->replay_inner_cycles[i] > 1000) {
@@ -1492,6 +1705,13 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   cudaStream_t s = (cudaStream_t)stream;
   try {
     CK(cudaSetDevice(op->ctx->device));
+    if (o->restart_len > 0) {
+      if (o->precision == FKS_PREC_FP64)
+        return solve_restarted<double>(op, &op->lane0, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound,
+                                       res_true, m_j, shift_status, info, s);
+      return solve_restarted<float>(op, &op->lane0, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound,
+                                    res_true, m_j, shift_status, info, s);
+    }
     if (o->precision == FKS_PREC_FP64)
       return solve_chunked<double>(op, &op->lane0, b, n_rhs, sigma, n_f, tau, n_tau, o, X, res_est, res_bound, res_true, m_j,
                                    shift_status, info, s);
@@ -2322,8 +2542,8 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
       o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
       (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
       (o.variant != FKS_FGMRES && o.variant != FKS_FFOM) || o.inner_steps > 64 ||
-      (o.assembly != 0 && o.assembly != 1) || !std::isfinite(o.inner_relax)) {
-    set_error("fks_server_submit: bad request");
+      (o.assembly != 0 && o.assembly != 1) || !std::isfinite(o.inner_relax) || o.restart_len != 0) {
+    set_error("fks_server_submit: bad request (restarted solves go through fks_solve)");
     return FKS_ERR_ARG;
   }
   for (int i = 0; i < o.sched_len; ++i)

@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
                                                           const double* __restrict__ pn, double tol, int variant,
                                                           const int32_t* __restrict__ replay_mj, z64* g, double* rc,
                                                           z64* rs, z64* R, z64* Y, int32_t* sst, int32_t* mj,
-                                                          double* est_out, double* bnd_out, double* alpha_out) {
+                                                          double* est_out, double* bnd_out, double* alpha_out,
+                                                          const double* __restrict__ tol_shift, z64* coef_out) {
   __shared__ z64 col[GV_WARPS][MAX_M + 1];
   __shared__ z64 yv[GV_WARPS][MAX_M];
   __shared__ z64 rhs[GV_WARPS][MAX_M];
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   bool brk = s.breakdown != 0;
   int rmj = replay_mj ? replay_mj[sj] : 0;
   double est = sd[warp];
+  if (tol_shift) tol = tol_shift[sj];  // a restarted solve gives each shift its own tolerance
   bool need = variant == 1 || est <= tol * beta || brk || k == m || (replay_mj && k == rmj);
   if (!need) {
     // still iterating: its estimate enters the next step's relaxed tolerance
@@ -404,6 +406,8 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   if (lane == 0) {
     mj[sj] = k;
     alpha_out[sj] = sal[warp];
+    // FFOM: the residual is c v_{k+1}, c = -(sigma - tau_k) h_{k+1,k} y_k (Eq. fomresidualsimplified)
+    if (coef_out) coef_out[sj] = mk(0.0, 0.0) - (Hc[k].re * yv[warp][k - 1]) * dsig;
     sst[sj] = conv ? 0 : (brk ? 2 : 1);
     est_out[sj] = est / beta;
     bnd_out[sj] = bound / beta;
@@ -571,10 +575,11 @@ void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, in
 }
 void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H, const z64* taus_k, const double* pn,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
-                   int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s) {
+                   int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s,
+                   const double* tol_shift, z64* coef) {
   dim3 gr(nbk(nf, GV_WARPS), nslot);
   k_givens<<<gr, GV_WARPS * 32, 0, s>>>(st, nf, m, sigma, H, taus_k, pn, tol, variant, replay_mj, g, rc, rs, R, Y, sst,
-                                        mj, est, bnd, alpha);
+                                        mj, est, bnd, alpha, tol_shift, coef);
 }
 void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s) {
   k_step_end<<<1, 256, 0, s>>>(st, nslot, m, use_cond, cond);
@@ -590,6 +595,18 @@ void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z6
   dim3 g(nbk(L.nx, GX), nbk((int64_t)L.ny * L.nz, GY * TRES_ROWS), nf * nslot);
   k_tres_partial<<<g, dim3(GX, GY), 0, s>>>(view<double>(L), sigma, nf, b, X, partial);
   launch_tres_finish(st, partial, tres_blocks(L), nf, nslot, out, s);
+}
+// X[idx[i]] += a[i] Xh[i] for the columns of a restart cycle (x_j += C_j d_j)
+__global__ void k_axpy_cols(z64* __restrict__ X, const z64* __restrict__ Xh, const int32_t* __restrict__ idx,
+                            const z64* __restrict__ a, int64_t n) {
+  const int i = blockIdx.y;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  z64* x = X + (int64_t)idx[i] * n + c;
+  *x = *x + a[i] * Xh[(int64_t)i * n + c];
+}
+void launch_axpy_cols(z64* X, const z64* Xh, const int32_t* idx, const z64* a, int ncols, int64_t n, cudaStream_t s) {
+  k_axpy_cols<<<dim3(nbk(n, 256), ncols), 256, 0, s>>>(X, Xh, idx, a, n);
 }
 void launch_tres_finish(const SlotState* st, const double* partial, int nblocks, int nf, int nslot, double* out,
                         cudaStream_t s) {

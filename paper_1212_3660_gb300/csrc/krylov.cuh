@@ -37,7 +37,8 @@ void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, in
                   cudaStream_t s);
 void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H, const z64* taus_k, const double* pn,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
-                   int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s);
+                   int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s,
+                   const double* tol_shift = nullptr, z64* coef = nullptr);
 void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s);
 // x_j = Z y_j in FP64; with st given, sources with st[slot].k <= skip_k_le are skipped
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
@@ -46,6 +47,8 @@ void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z6
                           const SlotState* st, double* out, int nslot, cudaStream_t s);
 
 // out[slot * nf + j] = sqrt(sum of the nblocks partials) / beta_slot
+// X[idx[i]] += a[i] Xh[i] (columns of n), i < ncols
+void launch_axpy_cols(z64* X, const z64* Xh, const int32_t* idx, const z64* a, int ncols, int64_t n, cudaStream_t s);
 void launch_tres_finish(const SlotState* st, const double* partial, int nblocks, int nf, int nslot, double* out,
                         cudaStream_t s);
 

@@ -36,7 +36,8 @@ class fks_options(C.Structure):
                 ("tau_schedule", C.POINTER(C.c_int32)), ("sched_len", C.c_int),
                 ("replay_mode", C.c_int), ("replay_inner_cycles", C.POINTER(C.c_int32)),
                 ("replay_mj", C.POINTER(C.c_int32)), ("launch_mode", C.c_int),
-                ("inner_steps", C.c_int), ("assembly", C.c_int), ("inner_relax", C.c_double)]
+                ("inner_steps", C.c_int), ("assembly", C.c_int), ("inner_relax", C.c_double),
+                ("restart_len", C.c_int), ("max_restarts", C.c_int)]
 
 
 class fks_info(C.Structure):
@@ -196,7 +197,7 @@ def fks_op_size(op) -> int:
 
 def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP64, inner_tol=0.0,
                  inner_max_cycles=50, schedule=(0,), replay_cycles=None, replay_mj=None, launch_mode=0,
-                 inner_steps=0, assembly=0, inner_relax=0.0):
+                 inner_steps=0, assembly=0, inner_relax=0.0, restart_len=0, max_restarts=0):
     """fks_options plus the arrays it points to (kept alive in the returned tuple)."""
     sched = np.ascontiguousarray(schedule, dtype=np.int32)
     o = fks_options()
@@ -208,6 +209,8 @@ def make_options(tol=1e-8, m_max=100, variant=FKS_FGMRES, precision=FKS_PREC_FP6
     o.inner_steps = int(inner_steps)
     o.assembly = int(assembly)
     o.inner_relax = float(inner_relax)
+    o.restart_len = int(restart_len)
+    o.max_restarts = int(max_restarts)
     keep = [sched]
     if replay_cycles is not None:
         rc = np.ascontiguousarray(replay_cycles, dtype=np.int32)

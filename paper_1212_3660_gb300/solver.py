@@ -63,7 +63,7 @@ class Solver:
     def solve(self, b=None, *, precision=fks.FKS_PREC_FP64, variant=fks.FKS_FGMRES, tol=None, m_max=None,
               inner_tol=0.0, inner_max_cycles=50, replay_cycles=None, replay_mj=None, device_out=False,
               stream=None, sigma=None, tau=None, schedule=None, launch_mode=0, inner_steps=0, assembly=0,
-              inner_relax=0.0):
+              inner_relax=0.0, restart_len=0, max_restarts=0):
         p = self.p
         b = p.rhs().T.copy() if b is None else b            # n_rhs x n
         n_rhs = b.shape[0]
@@ -76,7 +76,8 @@ class Solver:
                                       precision=precision, inner_tol=inner_tol, inner_max_cycles=inner_max_cycles,
                                       schedule=sched, replay_cycles=replay_cycles, replay_mj=replay_mj,
                                       launch_mode=launch_mode, inner_steps=inner_steps,
-                                      assembly=assembly, inner_relax=inner_relax)
+                                      assembly=assembly, inner_relax=inner_relax, restart_len=restart_len,
+                                      max_restarts=max_restarts)
         if device_out:
             import torch
             X = torch.empty((n_rhs, n_f, p.n), dtype=torch.complex128, device="cuda")
