@@ -11,11 +11,13 @@ field (variance 1, correlation 0.2 L, mean ln 1e-4), S_s = 1e-5, centre source,
 step, multigrid inner solve, complex128 throughout.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-                  [--workload 1|2|3|4|5|6] [--precision fp64|mixed]
+                  [--workload 1|2|3|4|5|6|7] [--precision fp64|mixed]
 
 Workload 5 is the serving stream (request loop); workload 6 the sensitivity
 matrix of workload 2's aquifer (Algorithm 6: forward solve, adjoint solves of 8
-sensors, adjoint-state inner products for ln K and ln S_s), in Jacobian rows/s.
+sensors, adjoint-state inner products for ln K and ln S_s), in Jacobian rows/s;
+workload 7 a general sparse operator through the CSR path (K and M as CSR
+arrays, BiCGSTAB inner cycles).
 
 Under torchrun every rank solves its own copy of the workload (replicas, weak
 scaling; no data-path collective). Prints one JSON line on rank 0.
@@ -102,7 +104,7 @@ def parse():
                     help="skip the per-class timing survey and the roofline (a short command for ncu launch lists)")
     a = ap.parse_args()
     if a.precision is None:
-        a.precision = "fp64" if a.workload in (1, 2, 6) else "mixed"
+        a.precision = "fp64" if a.workload in (1, 2, 6, 7) else "mixed"
     return a
 
 
@@ -435,6 +437,141 @@ def jacobian_bench(args, rank, world, local, dist):
     solver.close()
 
 
+def csr_bench(args, rank, world, local, dist):
+    """Workload 7: the general-operator path (K and M given as CSR arrays, inner
+    solves by BiCGSTAB cycles with Jacobi preconditioning and complex128 defect
+    correction) on a finite-element-like operator. Same timing, survey, roofline,
+    end-to-end and CPU-oracle legs as the grid workloads."""
+    import torch
+
+    from paper_1212_3660_gb300 import fks, synth
+    from paper_1212_3660_gb300.solver import Solver
+    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    pr = synth.fe_workload()
+    solver = Solver(pr, device=local, csr=pr.csr_arrays())
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    n, n_f, n_rhs = pr.n, len(pr.sigma), len(pr.src_cells)
+    b_d = torch.from_numpy(pr.rhs().T.copy()).to(dev)
+    sig_d = torch.from_numpy(pr.sigma.astype(np.complex128)).to(dev)
+    tau_d = torch.from_numpy(pr.tau_bar.astype(np.complex128)).to(dev)
+    X_d = torch.empty((n_rhs, n_f, n), dtype=torch.complex128, device=dev)
+    est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
+    mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
+    opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                  schedule=pr.schedule, inner_relax=args.inner_relax)
+    opts_host, keep_host = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                            schedule=pr.schedule, launch_mode=1, inner_relax=args.inner_relax)
+    info, info_arr = fks.make_info(n_rhs, pr.m_max)
+
+    def step(b, X, o=opts):
+        return fks.fks_solve(solver.op, b, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), o, X, est, bnd, tru, mj,
+                             sst, info, sh)
+
+    for _ in range(args.warmup):
+        step(b_d, X_d)
+    totals = {}
+    for c, name in enumerate([] if args.no_survey else fks.KERNEL_CLASSES):
+        fks.fks_profile_select(solver.op, c)
+        step(b_d, X_d, opts_host)
+        totals[name] = fks.fks_profile_read(solver.op)
+    fks.fks_profile_select(solver.op, None)
+    fks.fks_profile_read(solver.op)
+    dominant = max(totals, key=lambda k: totals[k]["ms"]) if totals else None
+    if args.survey and rank == 0:
+        tot = sum(v["ms"] for v in totals.values())
+        for k, v in sorted(totals.items(), key=lambda kv: -kv[1]["ms"]):
+            print(f"# {k:9s} launches {v['launches']:7d} ms {v['ms']:9.3f} ({100 * v['ms'] / max(tot, 1e-9):5.1f}%) "
+                  f"GB/s {v['bytes'] / max(v['ms'], 1e-9) / 1e6:8.1f}", file=sys.stderr)
+    replicas = Replicas(dist, world, dev)
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    converged = 0
+    with ClockSampler(gpu_index) as clk:
+        replicas.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(b_d, X_d)
+            converged += int(np.sum(tru <= TOL))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        replicas.barrier()
+    launches = fks.fks_profile_read(solver.op)["all_launches"]
+    ms = e0.elapsed_time(e1) / args.steps
+    value = replicas.throughput(converged / args.steps, ms / 1000.0)
+    main_info = {k: v.copy() for k, v in info_arr.items()}
+    roof = None
+    if dominant is not None:
+        fks.fks_profile_select(solver.op, dominant, 0)
+        for _ in range(args.steps):
+            step(b_d, X_d, opts_host)
+        prof = fks.fks_profile_read(solver.op)
+        fks.fks_profile_select(solver.op, None)
+        hbm_peak, _, peak_src = peaks()
+        gbs = prof["bytes"] / max(prof["ms"], 1e-12) / 1e6
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "traffic_source": "no ncu capture recorded", "kernel": dominant,
+                "peak_source": peak_src, "launches": prof["launches"],
+                "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
+                "alg_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1)}
+    e2e = None
+    if not args.no_e2e:
+        b_h = torch.from_numpy(pr.rhs().T.copy()).pin_memory()
+        X_h = torch.empty((n_rhs, n_f, n), dtype=torch.complex128).pin_memory()
+        step(b_h, X_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv = 0
+        for _ in range(args.steps):
+            step(b_h, X_h)
+            conv += int(np.sum(tru <= TOL))
+        t_e2e = replicas.max((time.perf_counter() - t0) / args.steps)
+        e2e = {"value": replicas.sum(conv / args.steps) / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": b_h.numel() * 16 + (n_f + len(pr.tau_bar)) * 16,
+               "d2h_bytes_per_step": X_h.numel() * 16 + n_rhs * n_f * (8 * 3 + 4 * 2)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        from oracle.csr import BiCGStabInner
+        op = oracle.CSROperator(pr.K, pr.M)
+        c0 = time.perf_counter()
+        res = oracle.shifted_solve(op, pr.rhs()[:, 0], pr.sigma, pr.tau_bar, pr.schedule, TOL,
+                                   max(1, args.cpu_sample_steps // 3), BiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=8),
+                                   inner_relax=args.inner_relax, eps=INNER_EPS)
+        dt = time.perf_counter() - c0
+        total = int(main_info["inner_cycles"][:pr.m_max].sum())
+        c_s = int(res.cycles.sum())
+        t_full = dt * total / max(c_s, 1)
+        cpu = {"value": n_f / t_full, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"first {res.steps} flexible Arnoldi steps of the source ({dt:.1f} s, {c_s} BiCGSTAB cycles), "
+                         f"scaled by the solve's {total} cycles"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": replicas.max(ms), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer",
+                "data": "synthetic",
+                "config": {"workload": pr.name, "n": n, "nnz_K": int(pr.K.nnz), "n_f": n_f,
+                           "n_p": len(pr.tau_bar), "schedule": "cycled", "sources_per_gpu": n_rhs,
+                           "inner": f"BiCGSTAB cycles of 8 steps (Jacobi), defect correction to eps={INNER_EPS:g}"
+                                    + (f", relaxed l = {args.inner_relax:g}" if args.inner_relax > 0 else ""),
+                           "precision": args.precision, "parallelism": f"replicas{world}",
+                           "arnoldi_steps": int(main_info["steps"].max()),
+                           "inner_cycles_total": int(main_info["inner_cycles"].sum())},
+                "solves_per_step": n_f * n_rhs, "converged_per_step": converged / args.steps,
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    solver.close()
+
+
 def jacobian_cpu_sample(pr, args, ns):
     """The oracle on the Jacobian workload: a bounded sample of its solves
     (cpu_oracle_sample, scaled to the 1 + ns sources' shifted solves) and of its
@@ -666,6 +803,11 @@ def main():
         return
     if args.workload == 6:
         jacobian_bench(args, rank, world, local, dist)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == 7:
+        csr_bench(args, rank, world, local, dist)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -7,26 +7,12 @@ import numpy as np
 import scipy.sparse as sp
 
 from oracle.csr import CSROperator
-
-# bilinear (Q1) element matrices on a unit square, nodes (0,0), (1,0), (0,1), (1,1)
-KE = np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6.0
-ME = np.array([[4, 2, 2, 1], [2, 4, 1, 2], [2, 1, 4, 2], [1, 2, 2, 4]]) / 36.0
-
+from paper_1212_3660_gb300 import synth
 
 def fe_like(n_side=12, seed=0, anchor=1e-3):
     """n_side x n_side nodes; K gets `anchor` * I so that it is SPD (a zero-head anchoring)."""
-    rng = np.random.default_rng(seed)
-    n = n_side * n_side
-    idx = np.arange(n).reshape(n_side, n_side)
-    nodes = np.stack([idx[:-1, :-1].ravel(), idx[:-1, 1:].ravel(), idx[1:, :-1].ravel(), idx[1:, 1:].ravel()], 1)
-    c = np.exp(rng.standard_normal(len(nodes)))
-    rows = np.repeat(nodes, 4, axis=1).ravel()
-    cols = np.tile(nodes, (1, 4)).ravel()
-    kdat = (c[:, None] * KE.ravel()[None, :]).ravel()
-    mdat = np.tile(ME.ravel(), len(nodes))
-    K = sp.coo_matrix((kdat, (rows, cols)), shape=(n, n)).tocsr() + anchor * sp.identity(n, format="csr")
-    M = sp.coo_matrix((mdat, (rows, cols)), shape=(n, n)).tocsr()
-    return CSROperator(K.tocsr(), M.tocsr())
+    K, M = synth.fe_matrices(n_side, seed, anchor)
+    return CSROperator(K, M)
 
 
 def csr_arrays(K, M):
