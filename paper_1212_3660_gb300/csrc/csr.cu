@@ -3,8 +3,12 @@
 // solver, and the BiCGSTAB cycle of the inner solve (s Jacobi-preconditioned
 // BiCGSTAB steps on A e = f from e = 0; the paper's inner Krylov method,
 // Section 6), all batched over sources on gridDim.y.
+#include <cooperative_groups.h>
+
 #include "csr.cuh"
 #include "krylov.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fks {
 
@@ -257,6 +261,191 @@ __global__ void k_bcg_close(const SlotState* st, BcgScal* sc, int nslot) {
   if (sc[slot].last) sc[slot].halt = 1;
 }
 
+// The whole cycle in one cooperative launch. Every block runs the arithmetic of
+// the stage kernels above over the same grid-stride partition (gridDim.x =
+// csr_blocks(n), 256 threads), with the dot products accumulated in the loops
+// that produce their operands (same elements, same order), and derives the
+// scalars itself from the block partials exactly as k_bcg_scalar does: the
+// results are bitwise those of the stage kernels. Grid barriers replace the
+// launches (five per step); every block passes every barrier.
+// csr_row with the vector read through L2 (x was written by other blocks
+// before the last grid barrier: no stale L1 or read-only-cache copy)
+template <typename T>
+__device__ __forceinline__ cx<T> ldcg_cx(const cx<T>* p) {
+  if constexpr (sizeof(T) == 8) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mk(v.x, v.y);
+  } else {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return mk(v.x, v.y);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> csr_row_cg(const CsrView<T>& A, int64_t row, cx<T> s, const cx<T>* x) {
+  cx<T> acc = mk(T(0), T(0));
+  for (int64_t q = A.rowptr[row]; q < A.rowptr[row + 1]; ++q) {
+    cx<T> a = mk(fmaT(s.re, A.mv[q], A.kv[q]), mulT(s.im, A.mv[q]));
+    acc = acc + a * ldcg_cx(x + A.col[q]);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void bcg_partial(double re, double im, double cc, double* red, double* partial, int slot) {
+  re = block_sum(re, red);
+  im = block_sum(im, red);
+  cc = block_sum(cc, red);
+  if (threadIdx.x == 0) {
+    double* p = partial + ((int64_t)slot * gridDim.x + blockIdx.x) * 3;
+    p[0] = re;
+    p[1] = im;
+    p[2] = cc;
+  }
+}
+
+// k_bcg_scalar in every block, on a block-local copy of the slot's scalars
+__device__ __forceinline__ void bcg_scalar_local(BcgScal& s, const double* __restrict__ partial, int slot, int stage,
+                                                 double* red) {
+  const int nblocks = gridDim.x;
+  double re = 0.0, im = 0.0, cc = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    const double* p = partial + ((int64_t)slot * nblocks + q) * 3;
+    re += __ldcg(p);
+    im += __ldcg(p + 1);
+    cc += __ldcg(p + 2);
+  }
+  re = block_sum(re, red);
+  im = block_sum(im, red);
+  cc = block_sum(cc, red);
+  if (threadIdx.x == 0) {
+    z64 d = mk(re, im);
+    if (stage == 0) {
+      if (czero(d) || czero(s.omega)) s.halt = 1;
+      else {
+        s.rho = d;
+        s.beta = cdivd(d, s.rho_old) * cdivd(s.alpha, s.omega);
+      }
+    } else if (stage == 1) {
+      if (czero(d)) s.halt = 1;
+      else s.alpha = cdivd(s.rho, d);
+    } else {
+      if (cc == 0.0) { s.omega = mk(0.0, 0.0); s.last = 1; }
+      else s.omega = mk(d.re / cc, d.im / cc);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bcg_cycle(CsrView<T> A, const SlotState* st, const z64* taus, BcgVecs<T> V,
+                                                   const cx<T>* __restrict__ dinv, BcgScal* scg, double* partial,
+                                                   int steps) {
+  cg::grid_group grid = cg::this_grid();
+  const int slot = blockIdx.y;
+  const bool run = csr_running(st, slot);
+  const int64_t n = A.n, o = slot * n;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  __shared__ double red[32];
+  __shared__ BcgScal sc;
+  const int tau = run ? st[slot].tau : 0;
+  const cx<T>* D = dinv + (int64_t)tau * n;
+  const cx<T> shift = cvt<T>(taus[tau]);
+  if (threadIdx.x == 0) {
+    sc.rho_old = mk(1.0, 0.0);
+    sc.alpha = mk(1.0, 0.0);
+    sc.omega = mk(1.0, 0.0);
+    sc.halt = run ? 0 : 1;
+    sc.last = 0;
+  }
+  __syncthreads();
+  // k_bcg_init, then the first step's <rh, r>
+  {
+    double re = 0.0, im = 0.0;
+    if (run)
+      for (int64_t i = i0; i < n; i += stride) {
+        const cx<T> f = V.f[o + i];
+        V.r[o + i] = f;
+        V.rh[o + i] = f;
+        V.p[o + i] = mk(T(0), T(0));
+        V.v[o + i] = mk(T(0), T(0));
+        V.e[o + i] = mk(T(0), T(0));
+        const z64 d = cdot(cvt<double>(f), cvt<double>(f));
+        re += d.re;
+        im += d.im;
+      }
+    if (run) bcg_partial(re, im, 0.0, red, partial, slot);
+  }
+  for (int it = 0; it < steps; ++it) {
+    grid.sync();
+    if (!sc.halt) bcg_scalar_local(sc, partial, slot, 0, red);
+    if (!sc.halt) {   // k_bcg_p
+      const cx<T> beta = cvt<T>(sc.beta), om = cvt<T>(sc.omega);
+      for (int64_t i = i0; i < n; i += stride) {
+        const cx<T> p = V.r[o + i] + beta * (V.p[o + i] - om * V.v[o + i]);
+        V.p[o + i] = p;
+        V.ph[o + i] = D[i] * p;
+      }
+    }
+    grid.sync();
+    if (!sc.halt) {   // k_bcg_spmv (v = A ph) and <rh, v>
+      double re = 0.0, im = 0.0;
+      for (int64_t row = i0; row < n; row += stride) {
+        const cx<T> y = csr_row_cg(A, row, shift, V.ph + o);
+        V.v[o + row] = y;
+        const z64 d = cdot(cvt<double>(V.rh[o + row]), cvt<double>(y));
+        re += d.re;
+        im += d.im;
+      }
+      bcg_partial(re, im, 0.0, red, partial, slot);
+    }
+    grid.sync();
+    if (!sc.halt) bcg_scalar_local(sc, partial, slot, 1, red);
+    if (!sc.halt) {   // k_bcg_s
+      const cx<T> al = cvt<T>(sc.alpha);
+      for (int64_t i = i0; i < n; i += stride) {
+        const cx<T> sv = V.r[o + i] - al * V.v[o + i];
+        V.s[o + i] = sv;
+        V.sh[o + i] = D[i] * sv;
+      }
+    }
+    grid.sync();
+    if (!sc.halt) {   // k_bcg_spmv (t = A sh) and <t, s>, <t, t>
+      double re = 0.0, im = 0.0, cc = 0.0;
+      for (int64_t row = i0; row < n; row += stride) {
+        const cx<T> y = csr_row_cg(A, row, shift, V.sh + o);
+        V.t[o + row] = y;
+        const z64 ty = cvt<double>(y);
+        const z64 d = cdot(ty, cvt<double>(V.s[o + row]));
+        re += d.re;
+        im += d.im;
+        cc += abs2(ty);
+      }
+      bcg_partial(re, im, cc, red, partial, slot);
+    }
+    grid.sync();
+    if (!sc.halt) bcg_scalar_local(sc, partial, slot, 2, red);
+    if (!sc.halt) {   // k_bcg_update and k_bcg_close, then the next step's <rh, r>
+      const cx<T> al = cvt<T>(sc.alpha), om = cvt<T>(sc.omega);
+      double re = 0.0, im = 0.0;
+      for (int64_t i = i0; i < n; i += stride) {
+        V.e[o + i] = V.e[o + i] + al * V.ph[o + i] + om * V.sh[o + i];
+        const cx<T> r = V.s[o + i] - om * V.t[o + i];
+        V.r[o + i] = r;
+        const z64 d = cdot(cvt<double>(V.rh[o + i]), cvt<double>(r));
+        re += d.re;
+        im += d.im;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sc.rho_old = sc.rho;
+        if (sc.last) sc.halt = 1;
+      }
+      bcg_partial(re, im, 0.0, red, partial, slot);   // block_sum synchronises the block first
+    }
+  }
+  if (run && blockIdx.x == 0 && threadIdx.x == 0) scg[slot] = sc;
+}
+
 // ------------------------------------------------------------------ launchers
 static inline unsigned cnb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 int csr_blocks(int64_t n) { return (int)std::min<int64_t>(cnb(n, 256), 512); }
@@ -301,6 +490,35 @@ void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus,
                       int* launches) {
   int nbk = csr_blocks(A.n);
   dim3 g(nbk, nslot);
+  // one cooperative launch when every block of the batch can be resident
+  static int resident[2] = {-1, -1};
+  int& res = resident[sizeof(T) == 8 ? 0 : 1];
+  if (res < 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bcg_cycle<T>, 256, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per = 0;
+    }
+    res = per * sms;
+  }
+  if ((int64_t)nbk * nslot <= res) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_bcg_cycle<T>, A, st, taus, V, dinv, sc, partial, steps) == cudaSuccess) {
+      if (launches) *launches += 1;
+      return;
+    }
+    cudaGetLastError();  // not launched: the stage kernels below compute the same
+  }
   k_bcg_init<T><<<g, 256, 0, s>>>(st, V, A.n, sc);
   int cnt = 1;
   for (int it = 0; it < steps; ++it) {

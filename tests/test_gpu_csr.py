@@ -249,3 +249,24 @@ def test_csr_invalid_input_rejected():
         s.solve(inner_steps=65)
     s0.close()
     s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_cooperative_and_stage_kernel_cycles_agree_bitwise(precision):
+    """One source at 65,536 unknowns runs each BiCGSTAB cycle as one cooperative
+    launch; three sources exceed the resident blocks and run the stage kernels.
+    Both perform the same arithmetic in the same order: every source of the batch
+    is bitwise its solo solve."""
+    need_gpu()
+    op = fe_like(256, seed=9)
+    pr = sparse_problem(op.n, n_f=4, n_src=3, seed=9, m_max=100)
+    s = Solver(pr, csr=csr_arrays(op.K, op.M))
+    batch = s.solve(precision=precision, inner_tol=1e-10, inner_relax=0.003)
+    b = pr.rhs().T.copy()
+    for r in range(3):
+        solo = s.solve(b[[r]], precision=precision, inner_tol=1e-10, inner_relax=0.003)
+        assert np.array_equal(batch.X[r], solo.X[0]), r
+        assert np.array_equal(batch.inner_cycles[r], solo.inner_cycles[0]), r
+        assert np.array_equal(batch.shift_status[r], solo.shift_status[0]), r
+        assert np.array_equal(batch.m_j[r], solo.m_j[0]), r
+    s.close()
