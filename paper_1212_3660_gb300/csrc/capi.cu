@@ -6,6 +6,7 @@
 // correction in complex128. All per-step state lives in device memory; the
 // host only enqueues kernels and reads small flags to decide when a loop ends.
 #include <algorithm>
+#include <limits>
 #include <complex>
 #include <climits>
 #include <cstdio>
@@ -268,6 +269,7 @@ struct RestartIO {
   double* beta;             // host out [n_rhs]: ||b|| of each source
   int32_t* steps;           // host out [n_rhs]: Arnoldi steps taken
   z64* v_next;              // device out [n * n_rhs]: v_{k+1} after the last step, the common residual direction
+  int reuse_setup;          // the workspace still holds this operator's preconditioner setup for these taus
 };
 
 struct Solve {
@@ -986,7 +988,13 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
     CK(cudaMemcpyAsync(S.rep_mj, o->replay_mj, sizeof(int32_t) * n_f * n_rhs, cudaMemcpyHostToDevice, s));
   }
   // preconditioner setup for the distinct taus (inverse diagonals, coarse inverse)
-  setup_levels<VT>(S);
+  if (rio && rio->reuse_setup) {
+    // a later restart cycle with the same layout: only the deciding kernels' counters
+    CK(cudaMemsetAsync(S.counter, 0, sizeof(int), s));
+    if (!op->csr) CK(cudaMemsetAsync(S.bcount, 0, sizeof(int) * S.nslot, s));
+  } else {
+    setup_levels<VT>(S);
+  }
   // start: beta, v_1
   int nbn = norm_blocks(n);
   PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 0, S.b, n, n, S.npart, n_rhs, s));
@@ -1255,39 +1263,43 @@ static fks_status solve_restarted(fks_op* op, Lane* lane, const fks_c128* b, int
     int32_t* mr = mj.data() + (size_t)r * n_f;
     int32_t* sr = sst.data() + (size_t)r * n_f;
     for (int j = 0; j < n_f; ++j) sr[j] = FKS_NOT_CONVERGED;
+    // Every cycle passes all shifts, those already certified (or abandoned) with an
+    // infinite tolerance (they freeze at the first step and are ignored), so the
+    // workspace layout, the preconditioner setup and the captured graph of the
+    // first cycle serve every later one.
+    std::vector<double> tl(n_f);
+    std::vector<double> e_c(n_f), b_c(n_f);
+    std::vector<int32_t> m_c(n_f), s_c(n_f);
+    std::vector<z64> coef(n_f);
+    std::vector<int32_t> sched(o->sched_len);
+    const double inf = std::numeric_limits<double>::infinity();
     for (int cyc = 0; cyc < max_cycles && !live.empty(); ++cyc) {
-      const int nl = (int)live.size();
-      std::vector<fks_c128> ss(nl);
-      std::vector<double> tl(nl);
-      for (int i = 0; i < nl; ++i) {
-        const int j = live[i];
-        // cycle 0 solves with b itself (figures relative to ||b||), later ones with a unit v
-        tl[i] = cyc == 0 ? tol : (tol * beta0 - A[j]) / std::abs(C[j]);
-      }
-      // shifts whose carried error alone exceeds the tolerance cannot be certified
+      std::fill(tl.begin(), tl.end(), inf);
       std::vector<int> nlive;
-      std::vector<double> ntl;
-      for (int i = 0; i < nl; ++i)
-        if (tl[i] > 0.0) { nlive.push_back(live[i]); ntl.push_back(tl[i]); }
+      for (int j : live) {
+        // cycle 0 solves with b itself (figures relative to ||b||), later ones with a unit v
+        const double t = cyc == 0 ? tol : (tol * beta0 - A[j]) / std::abs(C[j]);
+        if (t > 0.0) {   // otherwise the carried error alone exceeds the tolerance: not certifiable
+          tl[j] = t;
+          nlive.push_back(j);
+        }
+      }
       live = nlive;
       if (live.empty()) break;
-      const int nk = (int)live.size();
-      for (int i = 0; i < nk; ++i) ss[i] = sg[live[i]];
-      ss.resize(nk);
-      std::vector<int32_t> sched(o->sched_len);
       for (int i = 0; i < o->sched_len; ++i) sched[i] = o->tau_schedule[(done_steps + i) % o->sched_len];
       fks_options oc = *o;
       oc.m_max = len;
       oc.tau_schedule = sched.data();
       oc.restart_len = 0;
-      std::vector<double> e_c(nk), b_c(nk);
-      std::vector<int32_t> m_c(nk), s_c(nk);
-      std::vector<z64> coef(nk);
+      // the relaxed inner tolerance of a cycle follows its shifts' own tolerances
+      // (relative to its unit right-hand side), not the original one
+      oc.tol = inf;
+      for (int j : live) oc.tol = std::min(oc.tol, tl[j]);
       double beta_c = 0.0;
       int32_t steps_c = 0;
-      RestartIO rio{ntl.data(), coef.data(), &beta_c, &steps_c, vnext};
+      RestartIO rio{tl.data(), coef.data(), &beta_c, &steps_c, vnext, cyc > 0 ? 1 : 0};
       const fks_c128* rhs = cyc == 0 ? (const fks_c128*)bdev : (const fks_c128*)vcur;
-      fks_status st = solve_impl<VT>(op, lane, rhs, 1, ss.data(), nk, tau, n_tau, &oc, (fks_c128*)xhat, e_c.data(),
+      fks_status st = solve_impl<VT>(op, lane, rhs, 1, sg.data(), n_f, tau, n_tau, &oc, (fks_c128*)xhat, e_c.data(),
                                      b_c.data(), nullptr, m_c.data(), s_c.data(), nullptr, s, nullptr, nullptr, &rio);
       if (st < 0) return st;
       if (cyc == 0) {
@@ -1299,6 +1311,7 @@ static fks_status solve_restarted(fks_op* op, Lane* lane, const fks_c128* b, int
         }
       }
       // x_j += a_j d_j with a_j = 1 on the first cycle (its right-hand side is b), C_j after
+      const int nk = (int)live.size();
       std::vector<int32_t> idx(nk);
       std::vector<z64> acoef(nk);
       for (int i = 0; i < nk; ++i) {
@@ -1316,17 +1329,17 @@ static fks_status solve_restarted(fks_op* op, Lane* lane, const fks_c128* b, int
         const double sc = cyc == 0 ? beta0 : std::abs(C[j]);   // absolute scale of the cycle's relative figures
         const double rs = cyc == 0 ? 1.0 : sc / beta0;         // the same, relative to ||b||
         const std::complex<double> a(acoef[i].re, acoef[i].im);
-        if (s_c[i] == FKS_OK || s_c[i] == FKS_BREAKDOWN_EXACT) {
-          sr[j] = s_c[i];
-          er[j] = rs * e_c[i];
-          br[j] = rs * b_c[i] + A[j] / beta0;
-          mr[j] = done_steps + m_c[i];
+        if (s_c[j] == FKS_OK || s_c[j] == FKS_BREAKDOWN_EXACT) {
+          sr[j] = s_c[j];
+          er[j] = rs * e_c[j];
+          br[j] = rs * b_c[j] + A[j] / beta0;
+          mr[j] = done_steps + m_c[j];
         } else {
-          A[j] += sc * (b_c[i] - e_c[i]);
-          C[j] = a * std::complex<double>(coef[i].re, coef[i].im);
+          A[j] += sc * (b_c[j] - e_c[j]);
+          C[j] = a * std::complex<double>(coef[j].re, coef[j].im);
           er[j] = std::abs(C[j]) / beta0;
           br[j] = (std::abs(C[j]) + A[j]) / beta0;
-          mr[j] = done_steps + m_c[i];
+          mr[j] = done_steps + m_c[j];
           next.push_back(j);
         }
       }

@@ -596,14 +596,14 @@ void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z6
   k_tres_partial<<<g, dim3(GX, GY), 0, s>>>(view<double>(L), sigma, nf, b, X, partial);
   launch_tres_finish(st, partial, tres_blocks(L), nf, nslot, out, s);
 }
-// X[idx[i]] += a[i] Xh[i] for the columns of a restart cycle (x_j += C_j d_j)
+// X[idx[i]] += a[i] Xh[idx[i]] for the columns of a restart cycle (x_j += C_j d_j)
 __global__ void k_axpy_cols(z64* __restrict__ X, const z64* __restrict__ Xh, const int32_t* __restrict__ idx,
                             const z64* __restrict__ a, int64_t n) {
   const int i = blockIdx.y;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   z64* x = X + (int64_t)idx[i] * n + c;
-  *x = *x + a[i] * Xh[(int64_t)i * n + c];
+  *x = *x + a[i] * Xh[(int64_t)idx[i] * n + c];
 }
 void launch_axpy_cols(z64* X, const z64* Xh, const int32_t* idx, const z64* a, int ncols, int64_t n, cudaStream_t s) {
   k_axpy_cols<<<dim3(nbk(n, 256), ncols), 256, 0, s>>>(X, Xh, idx, a, n);

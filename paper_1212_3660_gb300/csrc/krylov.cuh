@@ -47,7 +47,7 @@ void launch_true_residual(const LevelHost& L, const z64* sigma, int nf, const z6
                           const SlotState* st, double* out, int nslot, cudaStream_t s);
 
 // out[slot * nf + j] = sqrt(sum of the nblocks partials) / beta_slot
-// X[idx[i]] += a[i] Xh[i] (columns of n), i < ncols
+// X[idx[i]] += a[i] Xh[idx[i]] (columns of n), i < ncols
 void launch_axpy_cols(z64* X, const z64* Xh, const int32_t* idx, const z64* a, int ncols, int64_t n, cudaStream_t s);
 void launch_tres_finish(const SlotState* st, const double* partial, int nblocks, int nf, int nslot, double* out,
                         cudaStream_t s);
