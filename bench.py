@@ -30,6 +30,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -651,7 +652,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.p = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples go to FKS_CLOCKS_DIR (default: the system temp folder)
+        d = os.environ.get("FKS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"fks_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
