@@ -13,6 +13,8 @@ Modules:
   direct     exact inner solves (sparse LU, the paper's "Flexible" variant) and the
              per-shift direct comparator ("Direct", Section 6.1)
   csr        general sparse K, M and the BiCGSTAB-cycle inner solve (Section 6)
+  amg        smoothed-aggregation AMG hierarchy and V-cycle, the preconditioner of
+             the BiCGSTAB cycles in the paper's inner solver (Section 6)
   sensitivity  adjoint-state sensitivities of the phasor measurements (Section 5,
              Eq. sensitivity, Eq. adjoint, Algorithm 6)
 """

@@ -50,7 +50,10 @@ def csr_operator(n, rowptr, col, kval, m_rowptr, m_col, mval) -> CSROperator:
 
 
 def bicgstab_cycle(A, dinv, f, steps):
-    """`steps` Jacobi-preconditioned BiCGSTAB steps on A e = f from e = 0."""
+    """`steps` preconditioned BiCGSTAB steps on A e = f from e = 0. The
+    preconditioner `dinv` is the Jacobi diagonal D^{-1} (an array, applied
+    elementwise) or a callable (the AMG V-cycle of oracle.amg)."""
+    prec = dinv if callable(dinv) else (lambda x: dinv * x)
     e = np.zeros_like(f)
     r = f.copy()
     rh = f.copy()
@@ -63,14 +66,14 @@ def bicgstab_cycle(A, dinv, f, steps):
             break
         beta = (rho / rho_old) * (alpha / omega)
         p = r + beta * (p - omega * v)
-        ph = dinv * p
+        ph = prec(p)
         v = A @ ph
         den = np.vdot(rh, v)
         if den == 0:
             break
         alpha = rho / den
         s = r - alpha * v
-        sh = dinv * s
+        sh = prec(s)
         t = A @ sh
         tt = np.vdot(t, t)
         if tt == 0:
