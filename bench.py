@@ -96,6 +96,8 @@ def parse():
                     help="with --fuse-max: from the first level of at most this many cells down, the cluster "
                          "V-cycle kernel (0: off)")
     ap.add_argument("--variant", default="fgmres", choices=["fgmres", "ffom"])
+    ap.add_argument("--precond", default="amg", choices=["amg", "jacobi"],
+                    help="workload 7: preconditioner of the BiCGSTAB inner cycles")
     ap.add_argument("--restart", type=int, default=0,
                     help="restarted FFOM with cycles of this many steps (needs --variant ffom; 0: none)")
     ap.add_argument("--sensors", type=int, default=JAC_SENSORS, help="workload 6: sensors (adjoint sources)")
@@ -440,16 +442,26 @@ def jacobian_bench(args, rank, world, local, dist):
 
 def csr_bench(args, rank, world, local, dist):
     """Workload 7: the general-operator path (K and M given as CSR arrays, inner
-    solves by BiCGSTAB cycles with Jacobi preconditioning and complex128 defect
+    solves by BiCGSTAB cycles preconditioned by a smoothed-aggregation AMG V-cycle,
+    the paper's inner solver, or by Jacobi with --precond jacobi; complex128 defect
     correction) on a finite-element-like operator. Same timing, survey, roofline,
-    end-to-end and CPU-oracle legs as the grid workloads."""
+    end-to-end and CPU-oracle legs as the grid workloads. The AMG hierarchies of
+    the taus are built once before the timed region (like the operator) and their
+    host setup time is reported in config."""
     import torch
 
     from paper_1212_3660_gb300 import fks, synth
     from paper_1212_3660_gb300.solver import Solver
     prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
     pr = synth.fe_workload()
-    solver = Solver(pr, device=local, csr=pr.csr_arrays())
+    amg = args.precond == "amg"
+    solver = Solver(pr, device=local, csr=pr.csr_arrays(), amg=amg)
+    amg_cfg = {}
+    if amg:
+        amg_ms = fks.fks_op_amg_setup(solver.op, pr.tau_bar, prec)
+        sizes, _ = fks.fks_op_amg_info(solver.op)
+        amg_cfg = {"amg_setup_ms": amg_ms, "amg_levels": [int(x) for x in sizes]}
+    bcg_steps = 4 if amg else 8
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
@@ -542,11 +554,15 @@ def csr_bench(args, rank, world, local, dist):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
+        from oracle.amg import AMGBiCGStabInner
         from oracle.csr import BiCGStabInner
         op = oracle.CSROperator(pr.K, pr.M)
+        # the oracle's AMG setup is left out like the library's (built before the timed region)
+        inner = (AMGBiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=bcg_steps) if amg
+                 else BiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=bcg_steps))
         c0 = time.perf_counter()
         res = oracle.shifted_solve(op, pr.rhs()[:, 0], pr.sigma, pr.tau_bar, pr.schedule, TOL,
-                                   max(1, args.cpu_sample_steps // 3), BiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=8),
+                                   max(1, args.cpu_sample_steps // 3), inner,
                                    inner_relax=args.inner_relax, eps=INNER_EPS)
         dt = time.perf_counter() - c0
         total = int(main_info["inner_cycles"][:pr.m_max].sum())
@@ -562,8 +578,11 @@ def csr_bench(args, rank, world, local, dist):
                 "data": "synthetic",
                 "config": {"workload": pr.name, "n": n, "nnz_K": int(pr.K.nnz), "n_f": n_f,
                            "n_p": len(pr.tau_bar), "schedule": "cycled", "sources_per_gpu": n_rhs,
-                           "inner": f"BiCGSTAB cycles of 8 steps (Jacobi), defect correction to eps={INNER_EPS:g}"
+                           "inner": f"BiCGSTAB cycles of {bcg_steps} steps ("
+                                    + ("smoothed-aggregation AMG V(2,2), damped Jacobi" if amg else "Jacobi")
+                                    + f"), defect correction to eps={INNER_EPS:g}"
                                     + (f", relaxed l = {args.inner_relax:g}" if args.inner_relax > 0 else ""),
+                           **amg_cfg,
                            "precision": args.precision, "parallelism": f"replicas{world}",
                            "arnoldi_steps": int(main_info["steps"].max()),
                            "inner_cycles_total": int(main_info["inner_cycles"].sum())},

@@ -106,6 +106,44 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
 fks_status fks_op_csr(fks_ctx* ctx, int64_t n, const int64_t* k_rowptr, const int32_t* k_col,
                       const double* k_val, const int64_t* m_rowptr, const int32_t* m_col,
                       const double* m_val, fks_op** out);
+/*
+ * Smoothed-aggregation algebraic multigrid as the BiCGSTAB preconditioner of a
+ * CSR operator's inner solve: Section 6 inverts each K + tau_k M with BiCGSTAB
+ * preconditioned by smoothed-aggregation AMG. With enable != 0 every BiCGSTAB
+ * step applies one V-cycle of K + tau_k M's hierarchy where the Jacobi
+ * diagonal was applied; enable = 0 returns to Jacobi. The hierarchy:
+ *  - strength graph: the stored connections of A_l (level 0: the entries where
+ *    K or M is nonzero), so the aggregates depend on the pattern only and are
+ *    shared by every tau;
+ *  - standard two-pass aggregation (ascending nodes; pass 2 joins a node to the
+ *    aggregate of its first neighbour placed by pass 1);
+ *  - tentative prolongator from the near-null-space vector (1 on level 0),
+ *    smoothed P = (I - omega D^{-1} A) T with omega = 4 / (3 rho), rho the
+ *    Gershgorin bound max_i sum_j |a_ij| / |a_ii|;
+ *  - A_{l+1} = P^T A_l P (plain transpose); the coarsest level (at most
+ *    max_coarse unknowns, or level max_levels - 1) is solved by its dense inverse;
+ *  - V-cycle: nu damped-Jacobi sweeps (weight omega) from zero, residual,
+ *    restriction by P^T, coarse correction by P, nu sweeps.
+ *  max_levels  1..16 (0: 10);  max_coarse 1..4096 (0: 256);  nu 1..8 (0: 2)
+ * Hierarchies are built on the host when a solve first needs a tau (or by
+ * fks_op_amg_setup) and kept on the operator per (tau, precision) until the
+ * next fks_op_amg call, which must not run while a solve on this operator is in
+ * flight. The default inner_steps becomes 4. FKS_ERR_ARG on a grid operator or
+ * out-of-range arguments; a later solve returns FKS_ERR_ARG when a level has a
+ * zero diagonal entry or the coarsest level is singular or above 4096 unknowns.
+ */
+fks_status fks_op_amg(fks_op* op, int enable, int max_levels, int64_t max_coarse, int nu);
+/* Build (or find) the hierarchies of K + tau_q M for the n_tau taus (host array,
+ * 1..16) in the cycle precision (FKS_PREC_FP64: complex128 values,
+ * FKS_PREC_MIXED: complex64). setup_ms (may be NULL) receives the host time
+ * spent, including the uploads. */
+fks_status fks_op_amg_setup(fks_op* op, const fks_c128* tau, int n_tau, int precision, double* setup_ms);
+/* The hierarchy's shape once one has been built: *n_levels, sizes[l] (at least
+ * n_levels entries, may be NULL) and, level after level, the aggregate of every
+ * unknown of every level but the coarsest in agg (may be NULL; agg_cap entries
+ * at least sum of sizes[0 .. n_levels - 2]). FKS_ERR_ARG before the first build. */
+fks_status fks_op_amg_info(fks_op* op, int* n_levels, int64_t* sizes, int sizes_cap, int32_t* agg,
+                           int64_t agg_cap);
 void fks_op_destroy(fks_op* op);
 /* Number of cells n of the operator (0 on a NULL operator). */
 int64_t fks_op_size(const fks_op* op);
@@ -131,8 +169,8 @@ typedef struct {
   int launch_mode;       /* 0: the step loop runs as one CUDA graph with conditional WHILE nodes
                             (no host round trip per step); 1: host-driven loop (one host sync per
                             inner cycle; per-kernel timing with fks_profile_select works here)  */
-  int inner_steps;       /* CSR operators: BiCGSTAB steps per inner cycle (<= 0 means 8, at most
-                            64); ignored by grid operators                                    */
+  int inner_steps;       /* CSR operators: BiCGSTAB steps per inner cycle (<= 0 means 8, or 4
+                            with AMG; at most 64); ignored by grid operators                  */
   int assembly;          /* x_j = Z y_j (Algorithm 4): 0 = tensor cores (Z and Y cut into eight
                             7-bit bf16 slices, exact fp32 accumulation of the slice products,
                             error at the level of an FP64 GEMM; used when 2 * steps <= 128,

@@ -30,6 +30,7 @@
 #include "cluster.cuh"
 #include "sensitivity.cuh"
 #include "monitors.cuh"
+#include "amg.cuh"
 
 namespace fks {
 
@@ -181,6 +182,10 @@ struct CsrDev {
   double *kv = nullptr, *mv = nullptr, *dk = nullptr, *dm = nullptr;
   float *kv32 = nullptr, *mv32 = nullptr;
   std::vector<double> dk_h, dm_h;  // host copies of the diagonals
+  // host copies of the union pattern and values (the AMG setup reads them)
+  std::vector<int64_t> rowptr_h;
+  std::vector<int32_t> col_h;
+  std::vector<double> kv_h, mv_h;
   template <typename T>
   fks::CsrView<T> view(int64_t n) const {
     fks::CsrView<T> v;
@@ -192,11 +197,43 @@ struct CsrDev {
   }
 };
 
+// Smoothed-aggregation AMG of a CSR operator: parameters, the aggregates
+// (fixed by the first build), and the device hierarchies built so far, one
+// per (tau, cycle precision).
+struct AmgEntry {
+  fks_c128 tau;
+  int prec;
+  std::vector<void*> mem;
+  std::vector<unsigned char> lv;  // AmgLevel<T> of every level: rows of a solve's device table
+};
+
+struct AmgState {
+  bool on = false;
+  int max_levels = 10, nu = 2;
+  int64_t max_coarse = 256;
+  int gen = 0;                    // changes with the parameters (part of the graph key)
+  AmgAgg agg;
+  std::vector<int64_t> sizes, nnz, pnnz;  // per level: unknowns, entries of A and of P
+  std::vector<AmgEntry> cache;
+  std::mutex mu;
+  void clear() {
+    if (!cache.empty()) cudaDeviceSynchronize();  // no launch may still read a hierarchy
+    for (auto& e : cache)
+      for (void* p : e.mem) cudaFree(p);
+    cache.clear();
+    agg = AmgAgg{};
+    sizes.clear();
+    nnz.clear();
+    pnnz.clear();
+  }
+};
+
 struct fks_op {
   fks_ctx* ctx;
   int dim;   // 2 or 3 for grid operators, 0 for CSR operators
   bool csr = false;
   CsrDev cd;
+  AmgState amg;
   int nx, ny, nz;
   int64_t n;
   uint32_t mask;
@@ -300,6 +337,13 @@ struct Solve {
   double relax = 0.0;  // relaxed inner tolerance constant (0: fixed eps)
   void* bv[9] = {};        // e, r, rh, p, v, ph, s, sh, t
   void* dinv = nullptr;    // [n_tau][n]
+  // AMG-preconditioned cycles: device table [n_tau][L] and per-level vectors
+  bool amg = false;
+  int amg_L = 0;
+  void* amg_tab = nullptr;
+  std::vector<unsigned char> amg_table;  // host image of the table
+  void *amg_f[AMG_MAX_LEVELS] = {}, *amg_x[AMG_MAX_LEVELS] = {}, *amg_y[AMG_MAX_LEVELS] = {},
+       *amg_r[AMG_MAX_LEVELS] = {};
   BcgScal* bsc = nullptr;
   double* bpart = nullptr;
   int ndef = 0;            // blocks of the defect kernel (partials per slot)
@@ -624,11 +668,132 @@ static cx<VT>* bicgstab_cycle(Solve& S) {
   const double fl = ns * st * (2 * nnz * 10 + n * 60);
   BcgVecs<VT> B = bcg_vecs<VT>(S);
   int extra = 0;
-  PROF(FKS_K_BICGSTAB, 0, by, fl,
-       launch_bcg_cycle<VT>(S.op->cd.view<VT>(N), S.st, S.taus, B, (const cx<VT>*)S.dinv, S.bsc, S.bpart,
-                            S.inner_steps, S.nslot, S.s, &extra));
+  if (S.amg) {
+    const AmgState& M = S.op->amg;
+    AmgRun<VT> R{};
+    R.tab = (const AmgLevel<VT>*)S.amg_tab;
+    R.L = S.amg_L;
+    R.nu = M.nu;
+    // per step two V-cycles: on every level but the coarsest nu + 2 products
+    // with A_l (the first two sweeps share one), P and P^T, and the vectors
+    // they stream; the coarsest level's dense inverse
+    double vb = 0.0, vf = 0.0;
+    for (int l = 0; l < S.amg_L; ++l) {
+      const double nl = (double)M.sizes[l], al = (double)M.nnz[l];
+      if (l + 1 < S.amg_L) {
+        const double pl = (double)M.pnnz[l], passes = M.nu + 1 + (M.nu >= 2 ? 1 : 0);
+        vb += passes * (al * (12 + cv) + nl * 4 * cv) + 2 * (pl * (12 + cv) + nl * 2 * cv);
+        vf += passes * al * 8 + 2 * pl * 8;
+      } else {
+        vb += nl * nl * cv + 2 * nl * cv;
+        vf += nl * nl * 8;
+      }
+    }
+    const double aby = ns * (n * cv * 8 + st * (2 * (nnz * (4 + 2 * rv + cv) + 8 * n) + 24 * n * cv + 2 * vb));
+    const double afl = ns * st * (2 * nnz * 10 + n * 60 + 2 * vf);
+    for (int l = 0; l < S.amg_L; ++l) {
+      R.n[l] = M.sizes[l];
+      R.f[l] = (cx<VT>*)S.amg_f[l];
+      R.x[l] = (cx<VT>*)S.amg_x[l];
+      R.y[l] = (cx<VT>*)S.amg_y[l];
+      R.r[l] = (cx<VT>*)S.amg_r[l];
+    }
+    PROF(FKS_K_BICGSTAB, 0, aby, afl,
+         launch_bcg_cycle_amg<VT>(S.op->cd.view<VT>(N), S.st, S.taus, B, R, S.bsc, S.bpart, S.inner_steps, S.nslot,
+                                  S.s, &extra));
+  } else {
+    PROF(FKS_K_BICGSTAB, 0, by, fl,
+         launch_bcg_cycle<VT>(S.op->cd.view<VT>(N), S.st, S.taus, B, (const cx<VT>*)S.dinv, S.bsc, S.bpart,
+                              S.inner_steps, S.nslot, S.s, &extra));
+  }
   S.lane->prof.all_launches += extra - 1;
   return B.e;
+}
+
+// K + tau M on the entries where K or M is nonzero (and the diagonal): level 0
+// of the AMG hierarchy, whose pattern is the strength graph
+static AmgCsr amg_level0(const fks_op* op, fks_c128 tau) {
+  const CsrDev& C = op->cd;
+  AmgCsr A;
+  A.n = A.m = op->n;
+  A.rp.assign(op->n + 1, 0);
+  for (int64_t i = 0; i < op->n; ++i) {
+    for (int64_t q = C.rowptr_h[i]; q < C.rowptr_h[i + 1]; ++q) {
+      const double k = C.kv_h[q], m = C.mv_h[q];
+      if (C.col_h[q] != i && k == 0.0 && m == 0.0) continue;
+      A.ci.push_back(C.col_h[q]);
+      A.v.push_back(mk(k + tau.re * m, tau.im * m));
+    }
+    A.rp[i + 1] = (int64_t)A.ci.size();
+  }
+  return A;
+}
+
+// The hierarchies of the n_tau taus in cycle precision VT (built on first use,
+// then cached on the operator); `table` receives their levels, tau after tau.
+// Returns "" or an error message.
+template <typename VT>
+static std::string amg_ensure(fks_op* op, const fks_c128* tau, int n_tau, std::vector<AmgLevel<VT>>* table,
+                              double* setup_ms = nullptr) {
+  AmgState& M = op->amg;
+  std::lock_guard<std::mutex> lock(M.mu);
+  const int prec = sizeof(VT) == 8 ? FKS_PREC_FP64 : FKS_PREC_MIXED;
+  const auto t0 = std::chrono::steady_clock::now();
+  table->clear();
+  for (int q = 0; q < n_tau; ++q) {
+    int hit = -1;
+    for (size_t e = 0; e < M.cache.size(); ++e)
+      if (M.cache[e].prec == prec && M.cache[e].tau.re == tau[q].re && M.cache[e].tau.im == tau[q].im) hit = (int)e;
+    if (hit < 0) {
+      AmgHost h;
+      std::string err = amg_build(amg_level0(op, tau[q]), M.max_levels, M.max_coarse, &M.agg, &h);
+      if (!err.empty()) return err;
+      if (M.sizes.empty())
+        for (const auto& L : h.lv) {
+          M.sizes.push_back(L.A.n);
+          M.nnz.push_back((int64_t)L.A.ci.size());
+          M.pnnz.push_back((int64_t)L.P.ci.size());
+        }
+      AmgEntry ne;
+      ne.tau = tau[q];
+      ne.prec = prec;
+      std::vector<AmgLevel<VT>> lv;
+      cudaError_t ce = amg_upload<VT>(h, ne.mem, lv);
+      if (ce != cudaSuccess) {
+        for (void* p : ne.mem) cudaFree(p);
+        throw CudaError{ce, "AMG upload"};
+      }
+      ne.lv.resize(sizeof(AmgLevel<VT>) * lv.size());
+      std::memcpy(ne.lv.data(), lv.data(), ne.lv.size());
+      M.cache.push_back(std::move(ne));
+      hit = (int)M.cache.size() - 1;
+    }
+    const AmgEntry& E = M.cache[hit];
+    const size_t nl = E.lv.size() / sizeof(AmgLevel<VT>);
+    const size_t at = table->size();
+    table->resize(at + nl);
+    std::memcpy(table->data() + at, E.lv.data(), E.lv.size());
+  }
+  if (setup_ms)
+    *setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return "";
+}
+
+// Before the carve of a CSR solve with AMG: the taus' hierarchies and the
+// host image of the solve's table. Returns "" or an error message.
+template <typename VT>
+static std::string amg_prepare(Solve& S, const fks_c128* tau) {
+  S.amg = S.op->csr && S.op->amg.on;
+  if (!S.amg) return "";
+  std::vector<fks_c128> th(S.n_tau);
+  CK(cudaMemcpy(th.data(), tau, sizeof(fks_c128) * S.n_tau, cudaMemcpyDefault));
+  std::vector<AmgLevel<VT>> tab;
+  std::string err = amg_ensure<VT>(S.op, th.data(), S.n_tau, &tab);
+  if (!err.empty()) return err;
+  S.amg_L = (int)S.op->amg.sizes.size();
+  S.amg_table.resize(sizeof(AmgLevel<VT>) * tab.size());
+  std::memcpy(S.amg_table.data(), tab.data(), S.amg_table.size());
+  return "";
 }
 
 // One inner cycle: z += V-cycle(r), r = v - (K + tau M) z, decide.
@@ -872,6 +1037,16 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
     S.f[0] = A.take<cx<VT>>((size_t)ns * n);
     for (int i = 0; i < 9; ++i) S.bv[i] = A.take<cx<VT>>((size_t)ns * n);
     S.dinv = A.take<cx<VT>>((size_t)S.n_tau * n);
+    if (S.amg) {
+      const auto& sz = S.op->amg.sizes;
+      S.amg_tab = A.take<AmgLevel<VT>>((size_t)S.n_tau * S.amg_L);
+      for (int l = 0; l < S.amg_L; ++l) {
+        S.amg_f[l] = l ? A.take<cx<VT>>((size_t)ns * sz[l]) : nullptr;
+        S.amg_x[l] = A.take<cx<VT>>((size_t)ns * sz[l]);
+        S.amg_y[l] = A.take<cx<VT>>((size_t)ns * sz[l]);
+        S.amg_r[l] = A.take<cx<VT>>((size_t)ns * sz[l]);
+      }
+    }
     S.bsc = A.take<BcgScal>(ns);
     S.bpart = A.take<double>((size_t)ns * csr_blocks(n) * 3);
     S.cwork = S.cinv64 = nullptr;
@@ -962,8 +1137,15 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   S.max_cycles = o->inner_max_cycles > 0 ? o->inner_max_cycles : 50;
   S.replay = o->replay_mode != 0;
   S.tolv_on = rio != nullptr;
-  S.inner_steps = o->inner_steps > 0 ? o->inner_steps : 8;
+  S.inner_steps = o->inner_steps > 0 ? o->inner_steps : (op->csr && op->amg.on ? 4 : 8);
   S.relax = o->inner_relax > 0 ? o->inner_relax : 0.0;
+  {
+    std::string err = amg_prepare<VT>(S, tau);
+    if (!err.empty()) {
+      set_error("fks_solve: " + err);
+      return FKS_ERR_ARG;
+    }
+  }
   bool x_dev = groups ? false : is_device_ptr(X);
   if (groups && !res_true) res_true = (double*)1;  // grouped runs always compute true residuals
   // workspace size: carve once on a null base to measure
@@ -972,6 +1154,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   size_t need = probe.off + 4096;
   lane->ws.reserve(need);
   carve<VT>(S, lane->ws, !x_dev);
+  if (S.amg)
+    CK(cudaMemcpyAsync(S.amg_tab, S.amg_table.data(), S.amg_table.size(), cudaMemcpyHostToDevice, s));
   z64* Xd = x_dev ? (z64*)X : S.X;
   std::vector<SlotState> st_host(n_rhs);
   S.st_host = st_host.data();
@@ -1017,7 +1201,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)op->fuse_max[1], (double)S.inner_steps, (double)op->tile16_max[0],
                                  (double)op->tile16_max[1], S.relax, (double)op->tail_max[0],
                                  (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1],
-                                 (double)op->tile8_max[0], (double)op->tile8_max[1], (double)S.tolv_on};
+                                 (double)op->tile8_max[0], (double)op->tile8_max[1], (double)S.tolv_on,
+                                 (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L};
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -1646,6 +1831,10 @@ fks_status fks_op_csr(fks_ctx* ctx, int64_t n, const int64_t* k_rowptr, const in
   }
   C.dk_h = std::move(dk);
   C.dm_h = std::move(dm);
+  C.rowptr_h = std::move(rowptr);
+  C.col_h = std::move(col);
+  C.kv_h = std::move(kv);
+  C.mv_h = std::move(mv);
   *out = op;
   return FKS_OK;
 }
@@ -1666,6 +1855,7 @@ void fks_op_destroy(fks_op* op) {
     if (L.kd64) cudaFree(L.kd64);
   }
   if (op->cond_d) cudaFree(op->cond_d);
+  op->amg.clear();
   op->lane0.release();
   delete op;
 }
@@ -2054,6 +2244,78 @@ fks_status fks_op_apply(fks_op* op, fks_c128 sh, const fks_c128* x, fks_c128* y,
   return FKS_OK;
 }
 
+fks_status fks_op_amg(fks_op* op, int enable, int max_levels, int64_t max_coarse, int nu) {
+  if (!op || !op->csr) { set_error("fks_op_amg: needs a CSR operator"); return FKS_ERR_ARG; }
+  if (max_levels < 0 || max_levels > AMG_MAX_LEVELS || max_coarse < 0 || max_coarse > AMG_MAX_DENSE || nu < 0 ||
+      nu > 8) {
+    set_error("fks_op_amg: need 0 <= max_levels <= 16, 0 <= max_coarse <= 4096, 0 <= nu <= 8");
+    return FKS_ERR_ARG;
+  }
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    std::lock_guard<std::mutex> lock(op->amg.mu);
+    op->amg.clear();
+    op->amg.on = enable != 0;
+    op->amg.max_levels = max_levels ? max_levels : 10;
+    op->amg.max_coarse = max_coarse ? max_coarse : 256;
+    op->amg.nu = nu ? nu : 2;
+    op->amg.gen++;
+  } catch (CudaError& e) {
+    set_error(std::string("fks_op_amg: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return FKS_ERR_CUDA;
+  }
+  return FKS_OK;
+}
+
+fks_status fks_op_amg_setup(fks_op* op, const fks_c128* tau, int n_tau, int precision, double* setup_ms) {
+  if (!op || !tau || !op->csr || !op->amg.on) { set_error("fks_op_amg_setup: needs a CSR operator with AMG on"); return FKS_ERR_ARG; }
+  if (n_tau < 1 || n_tau > MAX_TAU) { set_error("fks_op_amg_setup: n_tau must be in 1..16"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_amg_setup: bad precision"); return FKS_ERR_ARG; }
+  for (int q = 0; q < n_tau; ++q)
+    if (!finite_c(tau[q])) { set_error("fks_op_amg_setup: tau has NaN/Inf"); return FKS_ERR_ARG; }
+  if (!csr_diag_ok(op, tau, n_tau)) { set_error("fks_op_amg_setup: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
+  try {
+    CK(cudaSetDevice(op->ctx->device));
+    std::string err;
+    if (precision == FKS_PREC_FP64) {
+      std::vector<AmgLevel<double>> t;
+      err = amg_ensure<double>(op, tau, n_tau, &t, setup_ms);
+    } else {
+      std::vector<AmgLevel<float>> t;
+      err = amg_ensure<float>(op, tau, n_tau, &t, setup_ms);
+    }
+    if (!err.empty()) { set_error("fks_op_amg_setup: " + err); return FKS_ERR_ARG; }
+  } catch (CudaError& e) {
+    set_error(std::string("fks_op_amg_setup: ") + e.where + ": " + cudaGetErrorString(e.e));
+    return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
+  }
+  return FKS_OK;
+}
+
+fks_status fks_op_amg_info(fks_op* op, int* n_levels, int64_t* sizes, int sizes_cap, int32_t* agg, int64_t agg_cap) {
+  if (!op || !n_levels || !op->csr) { set_error("fks_op_amg_info: needs a CSR operator"); return FKS_ERR_ARG; }
+  std::lock_guard<std::mutex> lock(op->amg.mu);
+  const AmgState& M = op->amg;
+  if (M.sizes.empty()) { set_error("fks_op_amg_info: no hierarchy built yet"); return FKS_ERR_ARG; }
+  const int L = (int)M.sizes.size();
+  *n_levels = L;
+  if (sizes) {
+    if (sizes_cap < L) { set_error("fks_op_amg_info: sizes_cap too small"); return FKS_ERR_ARG; }
+    for (int l = 0; l < L; ++l) sizes[l] = M.sizes[l];
+  }
+  if (agg) {
+    int64_t need = 0;
+    for (const auto& a : M.agg.agg) need += (int64_t)a.size();
+    if (agg_cap < need) { set_error("fks_op_amg_info: agg_cap too small"); return FKS_ERR_ARG; }
+    int64_t at = 0;
+    for (const auto& a : M.agg.agg) {
+      std::memcpy(agg + at, a.data(), sizeof(int32_t) * a.size());
+      at += (int64_t)a.size();
+    }
+  }
+  return FKS_OK;
+}
+
 fks_status fks_ritz(fks_ctx* ctx, const fks_c128* hbar, const fks_c128* tau_k, const int32_t* steps, int n_rhs,
                     int m_max, fks_c128* theta, int32_t* status, void* stream) {
   if (!ctx || !hbar || !tau_k || !steps || !theta || !status) { set_error("fks_ritz: NULL argument"); return FKS_ERR_ARG; }
@@ -2171,12 +2433,18 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
     S.eps = eps;
     S.max_cycles = max_cycles > 0 ? max_cycles : 50;
     S.replay = cycles >= 0;
+    S.inner_steps = op->csr && op->amg.on ? 4 : 8;
+    std::string amg_err;
     auto run = [&](auto tag) {
       using VT = decltype(tag);
+      amg_err = amg_prepare<VT>(S, &tau);
+      if (!amg_err.empty()) return;
       Arena probe;
       carve<VT>(S, probe, false);
       op->lane0.ws.reserve(probe.off + 4096);
       carve<VT>(S, op->lane0.ws, false);
+      if (S.amg)
+        CK(cudaMemcpyAsync(S.amg_tab, S.amg_table.data(), S.amg_table.size(), cudaMemcpyHostToDevice, s));
       int64_t n = S.n;
       copy_in(S.V, v, sizeof(z64) * n, s);
       CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
@@ -2200,6 +2468,10 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
     };
     if (precision == FKS_PREC_FP64) run(double{});
     else run(float{});
+    if (!amg_err.empty()) {
+      set_error("fks_precond_apply: " + amg_err);
+      return FKS_ERR_ARG;
+    }
   } catch (CudaError& e) {
     set_error(std::string("fks_precond_apply: ") + e.where + ": " + cudaGetErrorString(e.e));
     return e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;

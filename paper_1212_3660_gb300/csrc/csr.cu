@@ -5,6 +5,7 @@
 // Section 6), all batched over sources on gridDim.y.
 #include <cooperative_groups.h>
 
+#include "amg.cuh"
 #include "csr.cuh"
 #include "krylov.cuh"
 
@@ -196,19 +197,20 @@ __global__ void k_bcg_scalar(const SlotState* st, BcgScal* sc, const double* __r
   }
 }
 
-// p = r + beta (p - omega v); ph = dinv p
+// p = r + beta (p - omega v); ph = dinv p (Jacobi; with dinv null the AMG
+// V-cycle computes ph afterwards)
 template <typename T>
 __global__ void k_bcg_p(const SlotState* st, const BcgScal* sc, BcgVecs<T> V, const cx<T>* __restrict__ dinv,
                         int64_t n) {
   int slot = blockIdx.y;
   if (!csr_running(st, slot) || sc[slot].halt) return;
-  const cx<T>* D = dinv + (int64_t)st[slot].tau * n;
+  const cx<T>* D = dinv ? dinv + (int64_t)st[slot].tau * n : nullptr;
   cx<T> beta = cvt<T>(sc[slot].beta), om = cvt<T>(sc[slot].omega);
   int64_t o = slot * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     cx<T> p = V.r[o + i] + beta * (V.p[o + i] - om * V.v[o + i]);
     V.p[o + i] = p;
-    V.ph[o + i] = D[i] * p;
+    if (D) V.ph[o + i] = D[i] * p;
   }
 }
 
@@ -224,19 +226,19 @@ __global__ void k_bcg_spmv(CsrView<T> A, const SlotState* st, const BcgScal* sc,
     y[o + row] = csr_row(A, row, s, x + o);
 }
 
-// s = r - alpha v; sh = dinv s
+// s = r - alpha v; sh = dinv s (with dinv null: the V-cycle, afterwards)
 template <typename T>
 __global__ void k_bcg_s(const SlotState* st, const BcgScal* sc, BcgVecs<T> V, const cx<T>* __restrict__ dinv,
                         int64_t n) {
   int slot = blockIdx.y;
   if (!csr_running(st, slot) || sc[slot].halt) return;
-  const cx<T>* D = dinv + (int64_t)st[slot].tau * n;
+  const cx<T>* D = dinv ? dinv + (int64_t)st[slot].tau * n : nullptr;
   cx<T> al = cvt<T>(sc[slot].alpha);
   int64_t o = slot * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     cx<T> s = V.r[o + i] - al * V.v[o + i];
     V.s[o + i] = s;
-    V.sh[o + i] = D[i] * s;
+    if (D) V.sh[o + i] = D[i] * s;
   }
 }
 
@@ -539,6 +541,36 @@ void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus,
   if (launches) *launches += cnt;
 }
 
+// one cycle with the AMG V-cycle as the preconditioner: the stage kernels,
+// with ph = V(p) and sh = V(s) in place of the Jacobi products
+template <typename T>
+void launch_bcg_cycle_amg(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
+                          const AmgRun<T>& R, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,
+                          int* launches) {
+  int nbk = csr_blocks(A.n);
+  dim3 g(nbk, nslot);
+  k_bcg_init<T><<<g, 256, 0, s>>>(st, V, A.n, sc);
+  int cnt = 1;
+  for (int it = 0; it < steps; ++it) {
+    k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.r, nullptr, A.n, partial);
+    k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 0);
+    k_bcg_p<T><<<g, 256, 0, s>>>(st, sc, V, nullptr, A.n);
+    cnt += 3 + launch_amg_vcycle<T>(R, st, sc, V.p, V.ph, nslot, s);
+    k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.ph, V.v);
+    k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.v, nullptr, A.n, partial);
+    k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 1);
+    k_bcg_s<T><<<g, 256, 0, s>>>(st, sc, V, nullptr, A.n);
+    cnt += 4 + launch_amg_vcycle<T>(R, st, sc, V.s, V.sh, nslot, s);
+    k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.sh, V.t);
+    k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.t, V.s, V.t, A.n, partial);
+    k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 2);
+    k_bcg_update<T><<<g, 256, 0, s>>>(st, sc, V, A.n);
+    k_bcg_close<<<cnb(nslot, 64), 64, 0, s>>>(st, sc, nslot);
+    cnt += 5;
+  }
+  if (launches) *launches += cnt;
+}
+
 #define CSR_INST(T)                                                                                              \
   template void launch_csr_apply<T>(const CsrView<T>&, z64, const SlotState*, const z64*, const cx<T>*, cx<T>*,  \
                                     int64_t, int, cudaStream_t);                                                 \
@@ -547,7 +579,9 @@ void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus,
                                      cudaStream_t);                                                              \
   template void launch_csr_dinv<T>(int64_t, const double*, const double*, const z64*, int, cx<T>*, cudaStream_t); \
   template void launch_bcg_cycle<T>(const CsrView<T>&, const SlotState*, const z64*, const BcgVecs<T>&,           \
-                                    const cx<T>*, BcgScal*, double*, int, int, cudaStream_t, int*);
+                                    const cx<T>*, BcgScal*, double*, int, int, cudaStream_t, int*);           \
+  template void launch_bcg_cycle_amg<T>(const CsrView<T>&, const SlotState*, const z64*, const BcgVecs<T>&,       \
+                                        const AmgRun<T>&, BcgScal*, double*, int, int, cudaStream_t, int*);
 
 CSR_INST(double)
 CSR_INST(float)

@@ -3,6 +3,11 @@
 #include "common.cuh"
 
 namespace fks {
+template <typename T>
+struct AmgRun;
+}
+
+namespace fks {
 
 // K + s M on the union pattern of K and M: one column index and a K and an M
 // value per stored entry (zero where a matrix has no entry).
@@ -57,5 +62,10 @@ template <typename T>
 void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
                       const cx<T>* dinv, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,
                       int* launches);
+// the same cycle preconditioned by the AMG V-cycle of R (amg.cuh)
+template <typename T>
+void launch_bcg_cycle_amg(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
+                          const AmgRun<T>& R, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,
+                          int* launches);
 
 }  // namespace fks

@@ -86,6 +86,9 @@ def lib():
                               C.POINTER(vp)]
     L.fks_op_csr.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
     L.fks_op_destroy.argtypes = [vp]
+    L.fks_op_amg.argtypes = [vp, C.c_int, C.c_int, C.c_int64, C.c_int]
+    L.fks_op_amg_setup.argtypes = [vp, vp, C.c_int, C.c_int, f64p]
+    L.fks_op_amg_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int, vp, C.c_int64]
     L.fks_op_destroy.restype = None
     L.fks_op_size.argtypes = [vp]
     L.fks_op_size.restype = C.c_int64
@@ -116,7 +119,7 @@ def lib():
     L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
-    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
+    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_op_amg", "fks_op_amg_setup", "fks_op_amg_info", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
                  "fks_server_create",
@@ -185,6 +188,46 @@ def fks_op_csr(ctx, n, k_rowptr, k_col, k_val, m_rowptr, m_col, m_val):
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
     return out
+
+
+def fks_op_amg(op, enable=True, max_levels=0, max_coarse=0, nu=0):
+    """Smoothed-aggregation AMG as the BiCGSTAB preconditioner of a CSR operator (0 = default)."""
+    st = lib().fks_op_amg(op, int(bool(enable)), int(max_levels), int(max_coarse), int(nu))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+
+
+def fks_op_amg_setup(op, taus, precision=FKS_PREC_FP64) -> float:
+    """Builds the hierarchies of K + tau M for the taus; returns the host time in ms."""
+    t = np.ascontiguousarray(np.asarray(taus, dtype=np.complex128).ravel())
+    ms = C.c_double(0.0)
+    st = lib().fks_op_amg_setup(op, _ptr(t), len(t), int(precision), C.byref(ms))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return float(ms.value)
+
+
+def fks_op_amg_info(op):
+    """(level sizes, [aggregates of each level but the coarsest]) of the built hierarchy."""
+    nl = C.c_int(0)
+    st = lib().fks_op_amg_info(op, C.byref(nl), None, 0, None, 0)
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    sizes = np.zeros(nl.value, np.int64)
+    nagg = 0
+    st = lib().fks_op_amg_info(op, C.byref(nl), sizes.ctypes.data_as(C.POINTER(C.c_int64)), nl.value, None, 0)
+    if st == FKS_OK:
+        nagg = int(sizes[:-1].sum())
+        agg = np.zeros(max(nagg, 1), np.int32)
+        st = lib().fks_op_amg_info(op, C.byref(nl), sizes.ctypes.data_as(C.POINTER(C.c_int64)), nl.value,
+                                   _ptr(agg), nagg)
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    out, at = [], 0
+    for l in range(len(sizes) - 1):
+        out.append(agg[at:at + sizes[l]].copy())
+        at += sizes[l]
+    return sizes, out
 
 
 def fks_op_destroy(op) -> None:

@@ -34,13 +34,17 @@ class SolveOutput:
 
 
 class Solver:
-    def __init__(self, problem, device: int = 0, csr=None):
-        """csr: optional (k_rowptr, k_col, k_val, m_rowptr, m_col, m_val) of an n x n K and M."""
+    def __init__(self, problem, device: int = 0, csr=None, amg=None):
+        """csr: optional (k_rowptr, k_col, k_val, m_rowptr, m_col, m_val) of an n x n K and M.
+        amg: for a CSR operator, True or a dict of fks_op_amg's max_levels, max_coarse, nu:
+        the BiCGSTAB steps of the inner solve are then preconditioned by an AMG V-cycle."""
         self.p = problem
         self.op = None
         self.ctx = fks.fks_create(device)
         if csr is not None:
             self.op = fks.fks_op_csr(self.ctx, problem.n, *csr)
+            if amg:
+                fks.fks_op_amg(self.op, True, **(amg if isinstance(amg, dict) else {}))
             return
         d = problem.dim
         ncell = [problem.shape[d - 1 - a] for a in range(d)]
