@@ -345,109 +345,70 @@ __device__ __forceinline__ const AmgLevel<T>& amg_level(const AmgLevel<T>* tab, 
   return tab[(st ? st[slot].tau : 0) * L + l];
 }
 
-// sum_q a_q x[col_q] over one CSR row
-template <typename T>
-__device__ __forceinline__ cx<T> row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                         const cx<T>* __restrict__ v, int64_t row, const cx<T>* __restrict__ x) {
-  cx<T> acc = mk(T(0), T(0));
-  for (int64_t q = rp[row]; q < rp[row + 1]; ++q) acc = acc + v[q] * x[ci[q]];
-  return acc;
-}
-
-// x = omega D^{-1} f, and with `two` the second sweep x += omega D^{-1} (f - A x)
-// (the first sweep's value at a neighbour is recomputed from f)
-template <typename T>
-__global__ void k_amg_smooth0(const AmgLevel<T>* tab, int L, int l, const SlotState* st, const BcgScal* sc,
-                              const cx<T>* __restrict__ f, cx<T>* __restrict__ x, int64_t n, int two) {
-  const int slot = blockIdx.y;
-  if (!amg_live(st, sc, slot)) return;
-  const AmgLevel<T>& A = amg_level(tab, st, slot, L, l);
-  const cx<T>* fs = f + slot * n;
-  const T om = A.omega;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    cx<T> xi = om * (A.dinv[i] * fs[i]);
-    if (two) {
-      cx<T> acc = mk(T(0), T(0));
-      for (int64_t q = A.arp[i]; q < A.arp[i + 1]; ++q) {
-        const int32_t j = A.aci[q];
-        acc = acc + A.av[q] * (om * (A.dinv[j] * fs[j]));
-      }
-      xi = xi + om * (A.dinv[i] * (fs[i] - acc));
-    }
-    x[slot * n + i] = xi;
-  }
-}
-
 // xo = xi + omega D^{-1} (f - A xi)
 template <typename T>
 __global__ void k_amg_smooth(const AmgLevel<T>* tab, int L, int l, const SlotState* st, const BcgScal* sc,
-                             const cx<T>* __restrict__ f, const cx<T>* __restrict__ xi, cx<T>* __restrict__ xo,
-                             int64_t n) {
+                             const cx<T>* f, const cx<T>* xi, cx<T>* __restrict__ xo, int64_t n) {
   const int slot = blockIdx.y;
   if (!amg_live(st, sc, slot)) return;
   const AmgLevel<T>& A = amg_level(tab, st, slot, L, l);
   const int64_t o = slot * n;
-  const T om = A.omega;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const cx<T> ax = row_dot(A.arp, A.aci, A.av, i, xi + o);
-    xo[o + i] = xi[o + i] + om * (A.dinv[i] * (f[o + i] - ax));
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    xo[o + i] = amg_sweep(A, i, f + o, xi + o);
 }
 
 // r = f - A x
 template <typename T>
 __global__ void k_amg_resid(const AmgLevel<T>* tab, int L, int l, const SlotState* st, const BcgScal* sc,
-                            const cx<T>* __restrict__ f, const cx<T>* __restrict__ x, cx<T>* __restrict__ r,
-                            int64_t n) {
+                            const cx<T>* f, const cx<T>* x, cx<T>* __restrict__ r, int64_t n) {
   const int slot = blockIdx.y;
   if (!amg_live(st, sc, slot)) return;
   const AmgLevel<T>& A = amg_level(tab, st, slot, L, l);
   const int64_t o = slot * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    r[o + i] = f[o + i] - row_dot(A.arp, A.aci, A.av, i, x + o);
+    r[o + i] = amg_resid(A, i, f + o, x + o);
 }
 
-// fc = P^T r (rows of R over the coarse unknowns)
+// fc = P^T r on level l + 1, and there (unless it is the coarsest) the first
+// sweep xc = omega D^{-1} fc
 template <typename T>
 __global__ void k_amg_restrict(const AmgLevel<T>* tab, int L, int l, const SlotState* st, const BcgScal* sc,
-                               const cx<T>* __restrict__ r, cx<T>* __restrict__ fc, int64_t n, int64_t nc) {
+                               const cx<T>* r, cx<T>* __restrict__ fc, cx<T>* __restrict__ xc, int64_t n, int64_t nc) {
   const int slot = blockIdx.y;
   if (!amg_live(st, sc, slot)) return;
   const AmgLevel<T>& A = amg_level(tab, st, slot, L, l);
-  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nc; a += (int64_t)gridDim.x * blockDim.x)
-    fc[slot * nc + a] = row_dot(A.rrp, A.rci, A.rv, a, r + slot * n);
+  const AmgLevel<T>& C = amg_level(tab, st, slot, L, l + 1);
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nc; a += (int64_t)gridDim.x * blockDim.x) {
+    const cx<T> v = amg_row(A.rrp, A.rci, A.rv, a, r + slot * n);
+    fc[slot * nc + a] = v;
+    if (l + 2 < L) xc[slot * nc + a] = amg_first(C, a, v);
+  }
 }
 
 // x += P e (e: the next level's result)
 template <typename T>
 __global__ void k_amg_prolong(const AmgLevel<T>* tab, int L, int l, const SlotState* st, const BcgScal* sc,
-                              cx<T>* __restrict__ x, const cx<T>* __restrict__ e, int64_t n, int64_t nc) {
+                              cx<T>* __restrict__ x, const cx<T>* e, int64_t n, int64_t nc) {
   const int slot = blockIdx.y;
   if (!amg_live(st, sc, slot)) return;
   const AmgLevel<T>& A = amg_level(tab, st, slot, L, l);
   const int64_t o = slot * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[o + i] = x[o + i] + row_dot(A.prp, A.pci, A.pv, i, e + slot * nc);
+    x[o + i] = amg_ld(x + o + i) + amg_row(A.prp, A.pci, A.pv, i, e + slot * nc);
 }
 
-// out = Cinv f on the coarsest level: one warp per row, lanes over columns,
-// fixed-order shuffle reduction
+// out = Cinv f on the coarsest level, one warp per row
 template <typename T>
 __global__ void k_amg_coarse(const AmgLevel<T>* tab, int L, const SlotState* st, const BcgScal* sc,
-                             const cx<T>* __restrict__ f, cx<T>* __restrict__ out, int64_t n) {
+                             const cx<T>* f, cx<T>* __restrict__ out, int64_t n) {
   const int slot = blockIdx.y;
   if (!amg_live(st, sc, slot)) return;
   const AmgLevel<T>& A = amg_level(tab, st, slot, L, L - 1);
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
-    cx<T> acc = mk(T(0), T(0));
-    for (int64_t j = lane; j < n; j += 32) acc = acc + A.cinv[row * n + j] * f[slot * n + j];
-    for (int s = 16; s > 0; s >>= 1) {
-      acc.re += __shfl_down_sync(0xffffffffu, acc.re, s);
-      acc.im += __shfl_down_sync(0xffffffffu, acc.im, s);
-    }
-    if (lane == 0) out[slot * n + row] = acc;
+    const cx<T> v = amg_coarse_row(A, row, f + slot * n, lane);
+    if (lane == 0) out[slot * n + row] = v;
   }
 }
 
@@ -466,18 +427,16 @@ int launch_amg_vcycle(const AmgRun<T>& R, const SlotState* st, const BcgScal* sc
     const int64_t n = R.n[l];
     const dim3 g(amg_blocks(n), nslot);
     const cx<T>* f = l == 0 ? f0 : R.f[l];
-    cur[l] = R.x[l];
+    cur[l] = R.x[l];   // holds the first sweep (written with f)
     oth[l] = R.y[l];
-    k_amg_smooth0<T><<<g, 256, 0, s>>>(R.tab, L, l, st, sc, f, cur[l], n, nu >= 2 ? 1 : 0);
-    ++cnt;
-    for (int k = 2; k < nu; ++k) {
+    for (int k = 1; k < nu; ++k) {
       k_amg_smooth<T><<<g, 256, 0, s>>>(R.tab, L, l, st, sc, f, cur[l], oth[l], n);
       std::swap(cur[l], oth[l]);
       ++cnt;
     }
     k_amg_resid<T><<<g, 256, 0, s>>>(R.tab, L, l, st, sc, f, cur[l], R.r[l], n);
-    k_amg_restrict<T><<<dim3(amg_blocks(R.n[l + 1]), nslot), 256, 0, s>>>(R.tab, L, l, st, sc, R.r[l], R.f[l + 1], n,
-                                                                          R.n[l + 1]);
+    k_amg_restrict<T><<<dim3(amg_blocks(R.n[l + 1]), nslot), 256, 0, s>>>(R.tab, L, l, st, sc, R.r[l], R.f[l + 1],
+                                                                          R.x[l + 1], n, R.n[l + 1]);
     cnt += 2;
   }
   {

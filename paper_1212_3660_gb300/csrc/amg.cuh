@@ -84,8 +84,69 @@ struct AmgRun {
 struct BcgScal;
 struct SlotState;
 
+#ifdef __CUDACC__
+// Per-row arithmetic of the V-cycle, shared by the stage kernels (amg.cu) and
+// the cooperative cycle (csr.cu) so that both give the same bits. Vectors are
+// read through L2 (__ldcg): in the cooperative kernel other blocks wrote them
+// before the last grid barrier.
+template <typename T>
+__device__ __forceinline__ cx<T> amg_ld(const cx<T>* p) {
+  if constexpr (sizeof(T) == 8) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mk(v.x, v.y);
+  } else {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return mk(v.x, v.y);
+  }
+}
+
+// sum_q v_q x[col_q] over one CSR row
+template <typename T>
+__device__ __forceinline__ cx<T> amg_row(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const cx<T>* __restrict__ v, int64_t row, const cx<T>* x) {
+  cx<T> acc = mk(T(0), T(0));
+  for (int64_t q = rp[row]; q < rp[row + 1]; ++q) acc = acc + v[q] * amg_ld(x + ci[q]);
+  return acc;
+}
+
+// first sweep from zero: omega D^{-1} f at row i (elementwise; its producer computes it)
+template <typename T>
+__device__ __forceinline__ cx<T> amg_first(const AmgLevel<T>& A, int64_t i, cx<T> f) {
+  return A.omega * (A.dinv[i] * f);
+}
+
+// a later sweep: x_i + omega D^{-1} (f - A x)_i
+template <typename T>
+__device__ __forceinline__ cx<T> amg_sweep(const AmgLevel<T>& A, int64_t i, const cx<T>* f, const cx<T>* x) {
+  const cx<T> ax = amg_row(A.arp, A.aci, A.av, i, x);
+  return amg_ld(x + i) + A.omega * (A.dinv[i] * (amg_ld(f + i) - ax));
+}
+
+// (f - A x)_i
+template <typename T>
+__device__ __forceinline__ cx<T> amg_resid(const AmgLevel<T>& A, int64_t i, const cx<T>* f, const cx<T>* x) {
+  return amg_ld(f + i) - amg_row(A.arp, A.aci, A.av, i, x);
+}
+
+// row `row` of the coarsest level's dense inverse times f, by one warp (lanes
+// over columns, fixed-order shuffle reduction); the sum is valid in lane 0
+template <typename T>
+__device__ __forceinline__ cx<T> amg_coarse_row(const AmgLevel<T>& A, int64_t row, const cx<T>* f, int lane) {
+  const int64_t n = A.n;
+  cx<T> acc = mk(T(0), T(0));
+  for (int64_t j = lane; j < n; j += 32) acc = acc + A.cinv[row * n + j] * amg_ld(f + j);
+  for (int s = 16; s > 0; s >>= 1) {
+    acc.re += __shfl_down_sync(0xffffffffu, acc.re, s);
+    acc.im += __shfl_down_sync(0xffffffffu, acc.im, s);
+  }
+  return acc;
+}
+#endif
+
 // out0 = V_0(f0) for every slot whose inner solve runs and whose BiCGSTAB
-// cycle has not halted (sc may be null); returns the number of launches.
+// cycle has not halted (sc may be null); returns the number of launches. The
+// first sweep of level 0, R.x[0] = omega_0 D_0^{-1} f0, must already be there:
+// the kernel that produces f0 writes it.
 template <typename T>
 int launch_amg_vcycle(const AmgRun<T>& R, const SlotState* st, const BcgScal* sc, const cx<T>* f0, cx<T>* out0,
                       int nslot, cudaStream_t s);

@@ -197,20 +197,22 @@ __global__ void k_bcg_scalar(const SlotState* st, BcgScal* sc, const double* __r
   }
 }
 
-// p = r + beta (p - omega v); ph = dinv p (Jacobi; with dinv null the AMG
-// V-cycle computes ph afterwards)
+// p = r + beta (p - omega v); ph = dinv p (Jacobi), or with an AMG table the
+// V-cycle's first sweep x1 = omega_0 D_0^{-1} p (the V-cycle then computes ph)
 template <typename T>
 __global__ void k_bcg_p(const SlotState* st, const BcgScal* sc, BcgVecs<T> V, const cx<T>* __restrict__ dinv,
-                        int64_t n) {
+                        const AmgLevel<T>* tab, int L, cx<T>* __restrict__ x1, int64_t n) {
   int slot = blockIdx.y;
   if (!csr_running(st, slot) || sc[slot].halt) return;
   const cx<T>* D = dinv ? dinv + (int64_t)st[slot].tau * n : nullptr;
+  const AmgLevel<T>* A0 = tab ? tab + st[slot].tau * L : nullptr;
   cx<T> beta = cvt<T>(sc[slot].beta), om = cvt<T>(sc[slot].omega);
   int64_t o = slot * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     cx<T> p = V.r[o + i] + beta * (V.p[o + i] - om * V.v[o + i]);
     V.p[o + i] = p;
     if (D) V.ph[o + i] = D[i] * p;
+    if (A0) x1[o + i] = amg_first(*A0, i, p);
   }
 }
 
@@ -226,19 +228,21 @@ __global__ void k_bcg_spmv(CsrView<T> A, const SlotState* st, const BcgScal* sc,
     y[o + row] = csr_row(A, row, s, x + o);
 }
 
-// s = r - alpha v; sh = dinv s (with dinv null: the V-cycle, afterwards)
+// s = r - alpha v; sh = dinv s, or the AMG first sweep x1 = omega_0 D_0^{-1} s
 template <typename T>
 __global__ void k_bcg_s(const SlotState* st, const BcgScal* sc, BcgVecs<T> V, const cx<T>* __restrict__ dinv,
-                        int64_t n) {
+                        const AmgLevel<T>* tab, int L, cx<T>* __restrict__ x1, int64_t n) {
   int slot = blockIdx.y;
   if (!csr_running(st, slot) || sc[slot].halt) return;
   const cx<T>* D = dinv ? dinv + (int64_t)st[slot].tau * n : nullptr;
+  const AmgLevel<T>* A0 = tab ? tab + st[slot].tau * L : nullptr;
   cx<T> al = cvt<T>(sc[slot].alpha);
   int64_t o = slot * n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     cx<T> s = V.r[o + i] - al * V.v[o + i];
     V.s[o + i] = s;
     if (D) V.sh[o + i] = D[i] * s;
+    if (A0) x1[o + i] = amg_first(*A0, i, s);
   }
 }
 
@@ -448,6 +452,194 @@ __global__ void __launch_bounds__(256) k_bcg_cycle(CsrView<T> A, const SlotState
   if (run && blockIdx.x == 0 && threadIdx.x == 0) scg[slot] = sc;
 }
 
+// V_0(f0) -> out0 inside a cooperative cycle: the phases of the stage kernels
+// of launch_amg_vcycle (same rows, same per-row arithmetic, so the same bits)
+// separated by grid barriers. Every block of the launch passes every barrier:
+// the loop bounds are kernel arguments, the same in all blocks; `work` only
+// decides whether a block computes its rows. The first sweep of level 0 is in
+// R.x[0] (written with f0).
+template <typename T>
+__device__ void amg_vcycle_grid(const AmgRun<T>& R, const AmgLevel<T>* lv, bool work, int slot, const cx<T>* f0,
+                                cx<T>* out0, cg::grid_group& grid) {
+  const int L = R.L, nu = R.nu;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  cx<T>* cur[AMG_MAX_LEVELS];
+  cx<T>* oth[AMG_MAX_LEVELS];
+  for (int l = 0; l + 1 < L; ++l) {
+    const int64_t n = R.n[l], o = slot * n;
+    const cx<T>* f = (l == 0 ? f0 : R.f[l]) + o;
+    cur[l] = R.x[l];
+    oth[l] = R.y[l];
+    for (int k = 1; k < nu; ++k) {
+      grid.sync();
+      if (work)
+        for (int64_t i = t0; i < n; i += stride) oth[l][o + i] = amg_sweep(lv[l], i, f, cur[l] + o);
+      cx<T>* t = cur[l];
+      cur[l] = oth[l];
+      oth[l] = t;
+    }
+    grid.sync();
+    if (work)
+      for (int64_t i = t0; i < n; i += stride) R.r[l][o + i] = amg_resid(lv[l], i, f, cur[l] + o);
+    grid.sync();
+    if (work) {
+      const int64_t nc = R.n[l + 1];
+      for (int64_t a = t0; a < nc; a += stride) {
+        const cx<T> v = amg_row(lv[l].rrp, lv[l].rci, lv[l].rv, a, R.r[l] + o);
+        R.f[l + 1][slot * nc + a] = v;
+        if (l + 2 < L) R.x[l + 1][slot * nc + a] = amg_first(lv[l + 1], a, v);
+      }
+    }
+  }
+  grid.sync();
+  if (work) {
+    const int64_t n = R.n[L - 1];
+    const cx<T>* f = (L == 1 ? f0 : R.f[L - 1]) + slot * n;
+    cx<T>* out = (L == 1 ? out0 : R.r[L - 1]) + slot * n;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
+      const cx<T> v = amg_coarse_row(lv[L - 1], row, f, lane);
+      if (lane == 0) out[row] = v;
+    }
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const int64_t n = R.n[l], o = slot * n, nc = R.n[l + 1];
+    const cx<T>* f = (l == 0 ? f0 : R.f[l]) + o;
+    cx<T>* out = (l == 0 ? out0 : R.r[l]) + o;
+    grid.sync();
+    if (work)
+      for (int64_t i = t0; i < n; i += stride)
+        cur[l][o + i] = amg_ld(cur[l] + o + i) + amg_row(lv[l].prp, lv[l].pci, lv[l].pv, i, R.r[l + 1] + slot * nc);
+    for (int k = 0; k < nu; ++k) {
+      grid.sync();
+      cx<T>* dst = k == nu - 1 ? out : oth[l] + o;
+      if (work)
+        for (int64_t i = t0; i < n; i += stride) dst[i] = amg_sweep(lv[l], i, f, cur[l] + o);
+      if (k < nu - 1) {
+        cx<T>* t = cur[l];
+        cur[l] = oth[l];
+        oth[l] = t;
+      }
+    }
+  }
+}
+
+// The AMG-preconditioned cycle in one cooperative launch: k_bcg_cycle's phases
+// with ph = V(p), sh = V(s) (amg_vcycle_grid) in place of the Jacobi products.
+// Bitwise the stage kernels of launch_bcg_cycle_amg.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bcg_cycle_amg(CsrView<T> A, const SlotState* st, const z64* taus,
+                                                       BcgVecs<T> V, AmgRun<T> R, BcgScal* scg, double* partial,
+                                                       int steps) {
+  cg::grid_group grid = cg::this_grid();
+  const int slot = blockIdx.y;
+  const bool run = csr_running(st, slot);
+  const int64_t n = A.n, o = slot * n;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  __shared__ double red[32];
+  __shared__ BcgScal sc;
+  const int tau = run ? st[slot].tau : 0;
+  const AmgLevel<T>* lv = R.tab + tau * R.L;
+  const cx<T> shift = cvt<T>(taus[tau]);
+  cx<T>* x1 = R.x[0];
+  if (threadIdx.x == 0) {
+    sc.rho_old = mk(1.0, 0.0);
+    sc.alpha = mk(1.0, 0.0);
+    sc.omega = mk(1.0, 0.0);
+    sc.halt = run ? 0 : 1;
+    sc.last = 0;
+  }
+  __syncthreads();
+  {   // k_bcg_init, then the first step's <rh, r>
+    double re = 0.0, im = 0.0;
+    if (run)
+      for (int64_t i = i0; i < n; i += stride) {
+        const cx<T> f = V.f[o + i];
+        V.r[o + i] = f;
+        V.rh[o + i] = f;
+        V.p[o + i] = mk(T(0), T(0));
+        V.v[o + i] = mk(T(0), T(0));
+        V.e[o + i] = mk(T(0), T(0));
+        const z64 d = cdot(cvt<double>(f), cvt<double>(f));
+        re += d.re;
+        im += d.im;
+      }
+    if (run) bcg_partial(re, im, 0.0, red, partial, slot);
+  }
+  for (int it = 0; it < steps; ++it) {
+    grid.sync();
+    if (!sc.halt) bcg_scalar_local(sc, partial, slot, 0, red);
+    if (!sc.halt) {   // k_bcg_p with the first sweep
+      const cx<T> beta = cvt<T>(sc.beta), om = cvt<T>(sc.omega);
+      for (int64_t i = i0; i < n; i += stride) {
+        const cx<T> p = V.r[o + i] + beta * (V.p[o + i] - om * V.v[o + i]);
+        V.p[o + i] = p;
+        x1[o + i] = amg_first(lv[0], i, p);
+      }
+    }
+    amg_vcycle_grid(R, lv, !sc.halt, slot, V.p, V.ph, grid);
+    grid.sync();
+    if (!sc.halt) {   // v = A ph and <rh, v>
+      double re = 0.0, im = 0.0;
+      for (int64_t row = i0; row < n; row += stride) {
+        const cx<T> y = csr_row_cg(A, row, shift, V.ph + o);
+        V.v[o + row] = y;
+        const z64 d = cdot(cvt<double>(V.rh[o + row]), cvt<double>(y));
+        re += d.re;
+        im += d.im;
+      }
+      bcg_partial(re, im, 0.0, red, partial, slot);
+    }
+    grid.sync();
+    if (!sc.halt) bcg_scalar_local(sc, partial, slot, 1, red);
+    if (!sc.halt) {   // k_bcg_s with the first sweep
+      const cx<T> al = cvt<T>(sc.alpha);
+      for (int64_t i = i0; i < n; i += stride) {
+        const cx<T> sv = V.r[o + i] - al * V.v[o + i];
+        V.s[o + i] = sv;
+        x1[o + i] = amg_first(lv[0], i, sv);
+      }
+    }
+    amg_vcycle_grid(R, lv, !sc.halt, slot, V.s, V.sh, grid);
+    grid.sync();
+    if (!sc.halt) {   // t = A sh and <t, s>, <t, t>
+      double re = 0.0, im = 0.0, cc = 0.0;
+      for (int64_t row = i0; row < n; row += stride) {
+        const cx<T> y = csr_row_cg(A, row, shift, V.sh + o);
+        V.t[o + row] = y;
+        const z64 ty = cvt<double>(y);
+        const z64 d = cdot(ty, cvt<double>(V.s[o + row]));
+        re += d.re;
+        im += d.im;
+        cc += abs2(ty);
+      }
+      bcg_partial(re, im, cc, red, partial, slot);
+    }
+    grid.sync();
+    if (!sc.halt) bcg_scalar_local(sc, partial, slot, 2, red);
+    if (!sc.halt) {   // k_bcg_update and k_bcg_close, then the next step's <rh, r>
+      const cx<T> al = cvt<T>(sc.alpha), om = cvt<T>(sc.omega);
+      double re = 0.0, im = 0.0;
+      for (int64_t i = i0; i < n; i += stride) {
+        V.e[o + i] = V.e[o + i] + al * amg_ld(V.ph + o + i) + om * amg_ld(V.sh + o + i);
+        const cx<T> r = V.s[o + i] - om * V.t[o + i];
+        V.r[o + i] = r;
+        const z64 d = cdot(cvt<double>(V.rh[o + i]), cvt<double>(r));
+        re += d.re;
+        im += d.im;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sc.rho_old = sc.rho;
+        if (sc.last) sc.halt = 1;
+      }
+      bcg_partial(re, im, 0.0, red, partial, slot);   // block_sum synchronises the block first
+    }
+  }
+  if (run && blockIdx.x == 0 && threadIdx.x == 0) scg[slot] = sc;
+}
+
 // ------------------------------------------------------------------ launchers
 static inline unsigned cnb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 int csr_blocks(int64_t n) { return (int)std::min<int64_t>(cnb(n, 256), 512); }
@@ -526,11 +718,11 @@ void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus,
   for (int it = 0; it < steps; ++it) {
     k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.r, nullptr, A.n, partial);
     k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 0);
-    k_bcg_p<T><<<g, 256, 0, s>>>(st, sc, V, dinv, A.n);
+    k_bcg_p<T><<<g, 256, 0, s>>>(st, sc, V, dinv, nullptr, 0, nullptr, A.n);
     k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.ph, V.v);
     k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.v, nullptr, A.n, partial);
     k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 1);
-    k_bcg_s<T><<<g, 256, 0, s>>>(st, sc, V, dinv, A.n);
+    k_bcg_s<T><<<g, 256, 0, s>>>(st, sc, V, dinv, nullptr, 0, nullptr, A.n);
     k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.sh, V.t);
     k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.t, V.s, V.t, A.n, partial);
     k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 2);
@@ -541,25 +733,57 @@ void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus,
   if (launches) *launches += cnt;
 }
 
-// one cycle with the AMG V-cycle as the preconditioner: the stage kernels,
-// with ph = V(p) and sh = V(s) in place of the Jacobi products
+int g_bcg_amg_coop = 1;
+
+// one cycle with the AMG V-cycle as the preconditioner: one cooperative launch
+// when the batch's blocks can all be resident, else the stage kernels, with
+// ph = V(p) and sh = V(s) in place of the Jacobi products
 template <typename T>
 void launch_bcg_cycle_amg(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
                           const AmgRun<T>& R, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,
                           int* launches) {
   int nbk = csr_blocks(A.n);
   dim3 g(nbk, nslot);
+  // one cooperative launch when every block of the batch can be resident
+  static int resident[2] = {-1, -1};
+  int& res = resident[sizeof(T) == 8 ? 0 : 1];
+  if (res < 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bcg_cycle_amg<T>, 256, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per = 0;
+    }
+    res = per * sms;
+  }
+  if ((int64_t)nbk * nslot <= res && g_bcg_amg_coop) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_bcg_cycle_amg<T>, A, st, taus, V, R, sc, partial, steps) == cudaSuccess) {
+      if (launches) *launches += 1;
+      return;
+    }
+    cudaGetLastError();  // not launched: the stage kernels below compute the same
+  }
   k_bcg_init<T><<<g, 256, 0, s>>>(st, V, A.n, sc);
   int cnt = 1;
   for (int it = 0; it < steps; ++it) {
     k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.r, nullptr, A.n, partial);
     k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 0);
-    k_bcg_p<T><<<g, 256, 0, s>>>(st, sc, V, nullptr, A.n);
+    k_bcg_p<T><<<g, 256, 0, s>>>(st, sc, V, nullptr, R.tab, R.L, R.x[0], A.n);
     cnt += 3 + launch_amg_vcycle<T>(R, st, sc, V.p, V.ph, nslot, s);
     k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.ph, V.v);
     k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.rh, V.v, nullptr, A.n, partial);
     k_bcg_scalar<<<nslot, 256, 0, s>>>(st, sc, partial, nbk, 1);
-    k_bcg_s<T><<<g, 256, 0, s>>>(st, sc, V, nullptr, A.n);
+    k_bcg_s<T><<<g, 256, 0, s>>>(st, sc, V, nullptr, R.tab, R.L, R.x[0], A.n);
     cnt += 4 + launch_amg_vcycle<T>(R, st, sc, V.s, V.sh, nslot, s);
     k_bcg_spmv<T><<<g, 256, 0, s>>>(A, st, sc, taus, V.sh, V.t);
     k_bcg_dot<T><<<g, 256, 0, s>>>(st, sc, V.t, V.s, V.t, A.n, partial);

@@ -62,7 +62,10 @@ template <typename T>
 void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
                       const cx<T>* dinv, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,
                       int* launches);
-// the same cycle preconditioned by the AMG V-cycle of R (amg.cuh)
+// the same cycle preconditioned by the AMG V-cycle of R (amg.cuh); with
+// g_bcg_amg_coop = 0 always as stage kernels (the cooperative launch computes
+// the same bits)
+extern int g_bcg_amg_coop;
 template <typename T>
 void launch_bcg_cycle_amg(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
                           const AmgRun<T>& R, BcgScal* sc, double* partial, int steps, int nslot, cudaStream_t s,

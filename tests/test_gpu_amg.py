@@ -108,7 +108,10 @@ def _replay_check(op, pr, steps=4):
     tr = oracle.true_residuals(op, b, pr.sigma, out.X[0].T)
     assert np.allclose(out.res_true[0], tr, rtol=1e-6, atol=1e-15)
     assert np.all(out.pnorm[0, :ref.steps] <= 10 * eps) and np.all(ref.pnorm <= eps)
-    assert np.all(tr <= out.res_bound[0] * (1 + 1e-6) + residual_floor(op, b, pr.sigma, out.X[0].T))
+    # the bound holds for the exact Arnoldi relation; the computed one carries
+    # rounding of about one residual evaluation per step
+    floor = residual_floor(op, b, pr.sigma, out.X[0].T) * ref.steps
+    assert np.all(tr <= out.res_bound[0] * (1 + 1e-6) + floor)
     s.close()
 
 
@@ -144,7 +147,8 @@ def test_amg_mixed_precision_converges():
     b = pr.rhs()[:, 0]
     tr = oracle.true_residuals(op, b, pr.sigma, out.X[0].T)
     assert np.all(tr <= pr.tol * 1.0001)
-    assert np.all(tr <= out.res_bound[0] * (1 + 1e-6) + residual_floor(op, b, pr.sigma, out.X[0].T))
+    floor = residual_floor(op, b, pr.sigma, out.X[0].T) * int(out.steps[0])
+    assert np.all(tr <= out.res_bound[0] * (1 + 1e-6) + floor)
     xd = oracle.direct_solve(op, b, pr.sigma)
     for j in range(len(pr.sigma)):
         assert rel_err(out.X[0, j], xd[:, j]) <= 1e-5, j
@@ -234,3 +238,24 @@ def test_fe_workload_full_size_sampled():
             xd = spla.splu(op.shifted(pr.sigma[j]).tocsc()).solve(b)
             assert np.linalg.norm(X[j] - xd) <= 1e-6 * np.linalg.norm(xd), j
         s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_cooperative_and_stage_amg_cycles_agree_bitwise(precision):
+    """One source at 65,536 unknowns runs each AMG-preconditioned cycle as one
+    cooperative launch; three sources exceed the resident blocks and run the
+    stage kernels. Same rows, same per-row arithmetic: every source of the batch
+    is bitwise its solo solve."""
+    need_gpu()
+    op = fe_like(256, seed=9)
+    pr = sparse_problem(op.n, n_f=4, n_src=3, seed=9, m_max=100)
+    s = _solver(op, pr)
+    batch = s.solve(precision=precision, inner_tol=1e-10, inner_relax=0.003)
+    assert batch.status == fks.FKS_OK
+    b = pr.rhs().T.copy()
+    for r in range(3):
+        solo = s.solve(b[[r]], precision=precision, inner_tol=1e-10, inner_relax=0.003)
+        assert np.array_equal(batch.X[r], solo.X[0]), r
+        assert np.array_equal(batch.inner_cycles[r], solo.inner_cycles[0]), r
+        assert np.array_equal(batch.m_j[r], solo.m_j[0]), r
+    s.close()
