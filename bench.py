@@ -531,11 +531,20 @@ def csr_bench(args, rank, world, local, dist):
         fks.fks_profile_select(solver.op, None)
         hbm_peak, _, peak_src = peaks()
         gbs = prof["bytes"] / max(prof["ms"], 1e-12) / 1e6
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": None, "traffic_source": "no ncu capture recorded", "kernel": dominant,
-                "peak_source": peak_src, "launches": prof["launches"],
-                "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
-                "alg_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1)}
+        tfl = prof["flops"] / max(prof["ms"], 1e-12) / 1e9
+        f_hbm = gbs / hbm_peak
+        f_alu = tfl / FP64_PEAK_TFLOPS if prec == fks.FKS_PREC_FP64 else 0.0
+        common = {"traffic": None, "traffic_source": "no ncu capture recorded", "kernel": dominant,
+                  "launches": prof["launches"], "avg_launch_us": 1000 * prof["ms"] / max(prof["launches"], 1),
+                  "alg_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
+                  "alg_flops_per_launch": prof["flops"] / max(prof["launches"], 1)}
+        if f_alu > f_hbm:
+            roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
+                    "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2.07 GHz", "hbm_frac_of_" + peak_src: f_hbm,
+                    **common}
+        else:
+            roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
+                    "peak_source": peak_src, **common}
     e2e = None
     if not args.no_e2e:
         b_h = torch.from_numpy(pr.rhs().T.copy()).pin_memory()

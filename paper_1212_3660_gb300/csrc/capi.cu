@@ -674,14 +674,16 @@ static cx<VT>* bicgstab_cycle(Solve& S) {
     R.tab = (const AmgLevel<VT>*)S.amg_tab;
     R.L = S.amg_L;
     R.nu = M.nu;
-    // per step two V-cycles: on every level but the coarsest nu + 2 products
-    // with A_l (the first two sweeps share one), P and P^T, and the vectors
-    // they stream; the coarsest level's dense inverse
+    // per step two V-cycles: on every level but the coarsest 2 nu products with
+    // A_l (nu - 1 sweeps and the residual down, nu sweeps up; the first sweep
+    // is elementwise, done by the kernel that writes the level's right-hand
+    // side), P and P^T, and the vectors they stream; the coarsest level's dense
+    // inverse. Flops count a complex multiply-add as 8.
     double vb = 0.0, vf = 0.0;
     for (int l = 0; l < S.amg_L; ++l) {
       const double nl = (double)M.sizes[l], al = (double)M.nnz[l];
       if (l + 1 < S.amg_L) {
-        const double pl = (double)M.pnnz[l], passes = M.nu + 1 + (M.nu >= 2 ? 1 : 0);
+        const double pl = (double)M.pnnz[l], passes = 2.0 * M.nu;
         vb += passes * (al * (12 + cv) + nl * 4 * cv) + 2 * (pl * (12 + cv) + nl * 2 * cv);
         vf += passes * al * 8 + 2 * pl * 8;
       } else {
