@@ -562,24 +562,8 @@ def csr_bench(args, rank, world, local, dist):
                "d2h_bytes_per_step": X_h.numel() * 16 + n_rhs * n_f * (8 * 3 + 4 * 2)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        from oracle.amg import AMGBiCGStabInner
-        from oracle.csr import BiCGStabInner
-        op = oracle.CSROperator(pr.K, pr.M)
-        # the oracle's AMG setup is left out like the library's (built before the timed region)
-        inner = (AMGBiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=bcg_steps) if amg
-                 else BiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=bcg_steps))
-        c0 = time.perf_counter()
-        res = oracle.shifted_solve(op, pr.rhs()[:, 0], pr.sigma, pr.tau_bar, pr.schedule, TOL,
-                                   max(1, args.cpu_sample_steps // 3), inner,
-                                   inner_relax=args.inner_relax, eps=INNER_EPS)
-        dt = time.perf_counter() - c0
-        total = int(main_info["inner_cycles"][:pr.m_max].sum())
-        c_s = int(res.cycles.sum())
-        t_full = dt * total / max(c_s, 1)
-        cpu = {"value": n_f / t_full, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"first {res.steps} flexible Arnoldi steps of the source ({dt:.1f} s, {c_s} BiCGSTAB cycles), "
-                         f"scaled by the solve's {total} cycles"}
+        v, _, desc = csr_cpu_sample(pr, args, amg, int(main_info["inner_cycles"][:pr.m_max].sum()))
+        cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": replicas.max(ms), "higher_is_better": True, "scaling": "weak",
@@ -599,6 +583,34 @@ def csr_bench(args, rank, world, local, dist):
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     solver.close()
+
+
+# inner cycles of the whole workload-7 solve (complex128, relaxed l = 0.003) on the GPU,
+# by which the reference arm scales its bounded sample
+CSR_CYCLES = {"amg": 114, "jacobi": 701}
+
+
+def csr_cpu_sample(pr, args, amg, total_cycles):
+    """The oracle on workload 7: the first Arnoldi steps of the source with the
+    same inner solver (AMG- or Jacobi-preconditioned BiCGSTAB cycles, the same
+    inner rule), scaled to a whole solve by its inner-cycle count. The oracle's
+    AMG setup is left out, like the library's (built before the timed region).
+    Returns (solves/s, seconds, description)."""
+    import oracle
+    from oracle.amg import AMGBiCGStabInner
+    from oracle.csr import BiCGStabInner
+    op = oracle.CSROperator(pr.K, pr.M)
+    inner = (AMGBiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=4) if amg
+             else BiCGStabInner(op, pr.tau_bar, INNER_EPS, steps=8))
+    c0 = time.perf_counter()
+    res = oracle.shifted_solve(op, pr.rhs()[:, 0], pr.sigma, pr.tau_bar, pr.schedule, TOL,
+                               max(1, args.cpu_sample_steps // 3), inner, inner_relax=args.inner_relax, eps=INNER_EPS)
+    dt = time.perf_counter() - c0
+    c_s = int(res.cycles.sum())
+    t_full = dt * total_cycles / max(c_s, 1)
+    desc = (f"first {res.steps} flexible Arnoldi steps of the source ({dt:.1f} s, {c_s} BiCGSTAB cycles), "
+            f"scaled by the solve's {total_cycles} cycles")
+    return len(pr.sigma) / t_full, dt, desc
 
 
 def jacobian_cpu_sample(pr, args, ns):
@@ -782,6 +794,25 @@ def run_reference(args):
                 "cpu_baseline": {"value": value, "unit": "rows/s", "cores": blas_threads(), "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    if args.workload == 7:
+        pr = synth.fe_workload()
+        vals = []
+        sample = None
+        for i in range(args.warmup + args.steps):
+            v, _, sample = csr_cpu_sample(pr, args, args.precond == "amg", CSR_CYCLES[args.precond])
+            if i >= args.warmup:
+                vals.append(v)
+        value = statistics.median(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(pr.sigma) / value,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": {"workload": pr.name, "n": pr.n, "n_f": len(pr.sigma),
+                                                "precond": args.precond},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
     if args.workload == 5:

@@ -144,6 +144,21 @@ fks_status fks_op_amg_setup(fks_op* op, const fks_c128* tau, int n_tau, int prec
  * at least sum of sizes[0 .. n_levels - 2]). FKS_ERR_ARG before the first build. */
 fks_status fks_op_amg_info(fks_op* op, int* n_levels, int64_t* sizes, int sizes_cap, int32_t* agg,
                            int64_t agg_cap);
+/*
+ * Host only (no GPU, no device memory): the hierarchy fks_op_amg would build
+ * for one complex matrix A0, given as CSR in host memory (int64 row pointers,
+ * int32 columns ascending within each row, complex128 values; its pattern is
+ * the strength graph, so pass only the entries that are structurally nonzero).
+ * Returns *n_levels and per level (arrays of sizes_cap >= n_levels entries, each
+ * may be NULL): unknowns, entries of A_l, entries of P_l (0 on the coarsest)
+ * and the Jacobi weight omega_l; agg as in fks_op_amg_info. max_levels and
+ * max_coarse as in fks_op_amg (0: default). FKS_ERR_ARG on malformed input, a
+ * zero diagonal entry, a singular or too large coarsest level.
+ */
+fks_status fks_amg_host_shape(int64_t n, const int64_t* rowptr, const int32_t* col, const fks_c128* val,
+                              int max_levels, int64_t max_coarse, int* n_levels, int64_t* sizes,
+                              int64_t* nnz_a, int64_t* nnz_p, double* omega, int sizes_cap, int32_t* agg,
+                              int64_t agg_cap);
 void fks_op_destroy(fks_op* op);
 /* Number of cells n of the operator (0 on a NULL operator). */
 int64_t fks_op_size(const fks_op* op);

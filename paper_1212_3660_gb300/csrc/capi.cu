@@ -2318,6 +2318,58 @@ fks_status fks_op_amg_info(fks_op* op, int* n_levels, int64_t* sizes, int sizes_
   return FKS_OK;
 }
 
+fks_status fks_amg_host_shape(int64_t n, const int64_t* rowptr, const int32_t* col, const fks_c128* val,
+                              int max_levels, int64_t max_coarse, int* n_levels, int64_t* sizes, int64_t* nnz_a,
+                              int64_t* nnz_p, double* omega, int sizes_cap, int32_t* agg, int64_t agg_cap) {
+  if (!rowptr || !n_levels || n < 1 || n > INT32_MAX) { set_error("fks_amg_host_shape: bad arguments"); return FKS_ERR_ARG; }
+  if (max_levels < 0 || max_levels > AMG_MAX_LEVELS || max_coarse < 0 || max_coarse > AMG_MAX_DENSE) {
+    set_error("fks_amg_host_shape: need 0 <= max_levels <= 16, 0 <= max_coarse <= 4096");
+    return FKS_ERR_ARG;
+  }
+  if (rowptr[0] != 0) { set_error("fks_amg_host_shape: row pointers must start at 0"); return FKS_ERR_ARG; }
+  AmgCsr A;
+  A.n = A.m = n;
+  A.rp.assign(rowptr, rowptr + n + 1);
+  for (int64_t i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) { set_error("fks_amg_host_shape: row pointers must not decrease"); return FKS_ERR_ARG; }
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      if (col[q] < 0 || col[q] >= n || (q > rowptr[i] && col[q] <= col[q - 1])) {
+        set_error("fks_amg_host_shape: columns must be in range and ascending within a row");
+        return FKS_ERR_ARG;
+      }
+      if (!finite_c(val[q])) { set_error("fks_amg_host_shape: value is NaN/Inf"); return FKS_ERR_ARG; }
+    }
+  }
+  const int64_t nnz = rowptr[n];
+  A.ci.assign(col, col + nnz);
+  A.v.resize(nnz);
+  for (int64_t q = 0; q < nnz; ++q) A.v[q] = mk(val[q].re, val[q].im);
+  AmgAgg ag;
+  AmgHost h;
+  std::string err = amg_build(A, max_levels ? max_levels : 10, max_coarse ? max_coarse : 256, &ag, &h);
+  if (!err.empty()) { set_error("fks_amg_host_shape: " + err); return FKS_ERR_ARG; }
+  const int L = (int)h.lv.size();
+  *n_levels = L;
+  if (sizes_cap < L && (sizes || nnz_a || nnz_p || omega)) { set_error("fks_amg_host_shape: sizes_cap too small"); return FKS_ERR_ARG; }
+  for (int l = 0; l < L; ++l) {
+    if (sizes) sizes[l] = h.lv[l].A.n;
+    if (nnz_a) nnz_a[l] = (int64_t)h.lv[l].A.ci.size();
+    if (nnz_p) nnz_p[l] = (int64_t)h.lv[l].P.ci.size();
+    if (omega) omega[l] = h.lv[l].omega;
+  }
+  if (agg) {
+    int64_t need = 0;
+    for (const auto& a : ag.agg) need += (int64_t)a.size();
+    if (agg_cap < need) { set_error("fks_amg_host_shape: agg_cap too small"); return FKS_ERR_ARG; }
+    int64_t at = 0;
+    for (const auto& a : ag.agg) {
+      std::memcpy(agg + at, a.data(), sizeof(int32_t) * a.size());
+      at += (int64_t)a.size();
+    }
+  }
+  return FKS_OK;
+}
+
 fks_status fks_ritz(fks_ctx* ctx, const fks_c128* hbar, const fks_c128* tau_k, const int32_t* steps, int n_rhs,
                     int m_max, fks_c128* theta, int32_t* status, void* stream) {
   if (!ctx || !hbar || !tau_k || !steps || !theta || !status) { set_error("fks_ritz: NULL argument"); return FKS_ERR_ARG; }

@@ -89,6 +89,8 @@ def lib():
     L.fks_op_amg.argtypes = [vp, C.c_int, C.c_int, C.c_int64, C.c_int]
     L.fks_op_amg_setup.argtypes = [vp, vp, C.c_int, C.c_int, f64p]
     L.fks_op_amg_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int, vp, C.c_int64]
+    L.fks_amg_host_shape.argtypes = [C.c_int64, vp, vp, vp, C.c_int, C.c_int64, C.POINTER(C.c_int), vp, vp, vp, vp,
+                                     C.c_int, vp, C.c_int64]
     L.fks_op_destroy.restype = None
     L.fks_op_size.argtypes = [vp]
     L.fks_op_size.restype = C.c_int64
@@ -119,7 +121,7 @@ def lib():
     L.fks_server_destroy.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
-    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_op_amg", "fks_op_amg_setup", "fks_op_amg_info", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
+    for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_op_amg", "fks_op_amg_setup", "fks_op_amg_info", "fks_amg_host_shape", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
                  "fks_server_create",
@@ -228,6 +230,31 @@ def fks_op_amg_info(op):
         out.append(agg[at:at + sizes[l]].copy())
         at += sizes[l]
     return sizes, out
+
+
+def fks_amg_host_shape(A0, max_levels=0, max_coarse=0):
+    """Host-only AMG hierarchy of a complex scipy CSR matrix A0 (sorted columns; no GPU needed):
+    dict(sizes, nnz_a, nnz_p, omega, agg=[aggregates of each level but the coarsest])."""
+    rp = np.ascontiguousarray(A0.indptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A0.indices, dtype=np.int32)
+    va = np.ascontiguousarray(A0.data, dtype=np.complex128)
+    nl = C.c_int(0)
+    cap = 16
+    sizes, nnz_a, nnz_p = (np.zeros(cap, np.int64) for _ in range(3))
+    om = np.zeros(cap)
+    n = A0.shape[0]
+    agg = np.zeros(n * 2, np.int32)
+    st = lib().fks_amg_host_shape(int(n), _ptr(rp), _ptr(ci), _ptr(va), int(max_levels), int(max_coarse),
+                                  C.byref(nl), _ptr(sizes), _ptr(nnz_a), _ptr(nnz_p), _ptr(om), cap, _ptr(agg),
+                                  len(agg))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    L = nl.value
+    out, at = [], 0
+    for l in range(L - 1):
+        out.append(agg[at:at + sizes[l]].copy())
+        at += int(sizes[l])
+    return dict(sizes=sizes[:L].copy(), nnz_a=nnz_a[:L].copy(), nnz_p=nnz_p[:L].copy(), omega=om[:L].copy(), agg=out)
 
 
 def fks_op_destroy(op) -> None:

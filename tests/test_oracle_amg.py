@@ -212,3 +212,19 @@ def test_shifted_solve_with_amg_inner_is_certified():
     xd = oracle.direct_solve(op, b, pr.sigma)
     for j in range(len(pr.sigma)):
         assert np.linalg.norm(res.x[:, j] - xd[:, j]) <= 1e-5 * np.linalg.norm(xd[:, j]), j
+
+
+def test_vcycle_is_a_complex_symmetric_operator():
+    """With R = P^T, a diagonal smoother and as many sweeps after the coarse
+    correction as before, the V-cycle of a complex-symmetric A is itself complex
+    symmetric (B = B^T, not B^H): a restriction by P^H or unequal sweep counts
+    break it."""
+    op = fe_like(14, seed=13)
+    A = op.shifted(0.3 + 2j)
+    h = sa_hierarchy(A, strength0(op.K, op.M), max_coarse=8)
+    assert len(h.levels) >= 3
+    I = np.eye(op.n, dtype=complex)
+    for nu in (1, 2):
+        B = np.stack([vcycle(h, I[:, j], 0, nu) for j in range(op.n)], axis=1)
+        assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+        assert np.abs(B - B.conj().T).max() > 1e-3 * np.abs(B).max()
