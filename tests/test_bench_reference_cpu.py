@@ -1,0 +1,30 @@
+"""The bench's reference arm (the oracle on the host cores) for the finite-
+element CSR workload, run on the CPU with a one-step sample: one JSON line
+with the contract's keys, the oracle as its kind, and no host-device bytes."""
+import contextlib
+import io
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_workload7_line(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "7", "--steps", "1",
+                                      "--warmup", "0", "--cpu-sample-steps", "3"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.main()
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["unit"] == "shifted solves/s" and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "fe-256x256-f50-p3-csr" and line["config"]["precond"] == "amg"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert "BiCGSTAB cycles" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
