@@ -29,7 +29,7 @@ namespace fks {
 // ================================================================== host setup
 namespace {
 
-struct hz {   // host complex128 with plain (uncontracted-by-intent) arithmetic
+struct hz {   // host complex128; plain formulas (std::complex multiplication adds NaN/Inf recovery)
   double re, im;
 };
 inline hz H(z64 a) { return {a.re, a.im}; }
