@@ -228,3 +228,21 @@ def test_vcycle_is_a_complex_symmetric_operator():
         B = np.stack([vcycle(h, I[:, j], 0, nu) for j in range(op.n)], axis=1)
         assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
         assert np.abs(B - B.conj().T).max() > 1e-3 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("steps", [1, 2, 4])
+def test_amg_bicgstab_cycle_equals_scipy_bicgstab(steps):
+    """A cycle of AMG-preconditioned BiCGSTAB steps equals SciPy's own bicgstab
+    with the V-cycle as its preconditioner M (zero start, the same number of
+    steps): the composition of the Krylov method and the V-cycle is pinned by a
+    second implementation."""
+    op = fe_like(24, seed=14)
+    A = op.shifted(0.4 + 3j)
+    h = sa_hierarchy(A, strength0(op.K, op.M), max_coarse=16)
+    assert len(h.levels) >= 3
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(op.n) + 1j * rng.standard_normal(op.n)
+    e = bicgstab_cycle(A, lambda x: vcycle(h, x), f, steps)
+    Mop = spla.LinearOperator(A.shape, matvec=lambda x: vcycle(h, np.asarray(x).ravel()), dtype=complex)
+    e_ref, _ = spla.bicgstab(A, f, x0=np.zeros_like(f), rtol=1e-300, atol=0.0, maxiter=steps, M=Mop)
+    assert np.linalg.norm(e - e_ref) <= 1e-10 * np.linalg.norm(e_ref)
