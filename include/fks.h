@@ -312,6 +312,7 @@ fks_status fks_sensitivity(fks_op* op, const fks_c128* phi, const fks_c128* psi,
  * multigrid cycles from z = 0 until ||v - (K + tau M) z|| <= eps ||v|| or max_cycles
  * (cycles >= 0 forces exactly that many). precision as in fks_options.
  * v, z [n] host or device; out_cycles, out_pnorm host scalars (may be NULL).
+ * z is written in full: z = 0 where no cycle runs (cycles == 0, or v = 0).
  */
 fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c128* z, double eps,
                              int max_cycles, int cycles, int precision, int32_t* out_cycles,
@@ -427,11 +428,17 @@ fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int
  * device array inside the library (held by every GPU that loads the library
  * until the process exits) and it calls no cudaMalloc, cudaFree or other
  * allocating routine.
- *  - v, z must be device memory (the caller passes inputs and outputs).
+ *  - v, z must be device memory (the caller passes inputs and outputs). z may
+ *    alias v (an in-place call): v is first copied into the fixed array.
+ *  - z is written in full; where no cycle runs (cycles == 0 in replay, or
+ *    v = 0), z = 0.
  *  - Limits: at most 65536 cells, coarsest multigrid level at most 256 cells;
  *    larger grids return FKS_ERR_ARG with a message.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for later calls.
+ *  - The call is synchronous on `stream` (it reads the cycle count and ||p||
+ *    back to the host before it returns), so it must not be made while that
+ *    stream is being captured into a CUDA graph.
  *  - All calls share the one array and leave their contents in it; calls that
  *    overlap on the GPU (other streams, other threads) race and must be
  *    serialised by the caller.

@@ -8,6 +8,8 @@
 // tcgen05.mma per slab into eight TMEM accumulators; then four warps read the
 // accumulators with tcgen05.ld and write x_j. Every wait on an mbarrier gives
 // up after two seconds, sets the error flag and still releases TMEM.
+#include <algorithm>
+
 #include "assemble_tc.cuh"
 
 namespace fks {
@@ -364,6 +366,19 @@ TcLayout tc_layout(int64_t n, int nf, int K, int nslot) {
   T.e_bytes = (size_t)nslot * T.nrt * TC_M * sizeof(int);
   T.f_bytes = (size_t)nslot * T.nct * TC_N * sizeof(int);
   return T;
+}
+
+size_t tc_ws_bytes(const TcLayout& T) {
+  size_t need = 0;
+  for (size_t b : {T.a_bytes, T.b_bytes, T.e_bytes, T.f_bytes}) need += (b + 255) & ~(size_t)255;
+  return need;
+}
+
+int tc_group_size(int64_t n, int nf, int K, int nslot) {
+  const size_t cap = size_t(4) << 30;
+  const size_t one = tc_ws_bytes(tc_layout(n, nf, K, 1));
+  const size_t g = one > 0 ? cap / one : (size_t)nslot;
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)nslot, g));
 }
 
 void tc_prepare() {

@@ -34,6 +34,12 @@ struct TcLayout {
 };
 
 TcLayout tc_layout(int64_t n, int nf, int K, int nslot);
+// Bytes of the workspace a layout needs (a, b, e, f, each 256-byte aligned).
+size_t tc_ws_bytes(const TcLayout& T);
+// Sources assembled per launch group: all of them while their slices take at
+// most 4 GiB, else as many as fit (at least one), so that the slice workspace
+// stays bounded for large batches.
+int tc_group_size(int64_t n, int nf, int K, int nslot);
 // 2K padded to 16 within the exactness bound, and the row tiles within a grid dimension
 bool tc_supported(int K, int64_t n);
 void tc_prepare();

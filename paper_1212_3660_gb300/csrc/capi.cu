@@ -1262,10 +1262,11 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
     }
     const bool use_tc = o->assembly == 0 && k_tc >= 1;
     if (use_tc) {
-      // tensor cores: slices of Z and Y, the product, the epilogue
-      TcLayout T = tc_layout(n, n_f, k_tc, n_rhs);
-      size_t need = 0;
-      for (size_t b : {T.a_bytes, T.b_bytes, T.e_bytes, T.f_bytes}) need += (b + 255) & ~(size_t)255;
+      // tensor cores: slices of Z and Y, the product, the epilogue; sources in
+      // groups of tc_group_size, whose slices the workspace holds at a time
+      const int sb = tc_group_size(n, n_f, k_tc, n_rhs);
+      TcLayout T = tc_layout(n, n_f, k_tc, sb);
+      const size_t need = tc_ws_bytes(T);
       lane->tcws.reserve(need + 256);
       tc_err = (int*)(lane->tcws.base + need);
       {
@@ -1273,13 +1274,18 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
         tc_prepare();
       }
       CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
-      const double kt = k_tc, kp = 16.0 * T.nslab;
-      int launched = 0;
-      PROF(FKS_K_ASSEMBLE, -1, ns * (2 * 16 * nn * kt + 2 * 16 * nn * kp + 16 * nn * n_f),
-           ns * 8 * nn * kt * n_f,
-           launched = launch_tc_assemble(T, S.st, S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, lane->tcws.base,
-                                         tc_err, s));
-      lane->prof.all_launches += launched - 1;  // the two slicing kernels beyond the one PROF counted
+      lane->prof.all_launches += 1;
+      for (int r0 = 0; r0 < n_rhs; r0 += sb) {
+        const int nr = std::min(sb, n_rhs - r0);
+        const double kt = k_tc, kp = 16.0 * T.nslab, nsb = nr;
+        int launched = 0;
+        PROF(FKS_K_ASSEMBLE, -1, nsb * (2 * 16 * nn * kt + 2 * 16 * nn * kp + 16 * nn * n_f),
+             nsb * 8 * nn * kt * n_f,
+             launched = launch_tc_assemble(T, S.st + r0, S.Z + (size_t)r0 * vsZ, vsZ, S.Y + (size_t)r0 * n_f * m,
+                                           S.mj + (size_t)r0 * n_f, n_f, m, Xd + (size_t)r0 * n_f * n, n, nr,
+                                           lane->tcws.base, tc_err, s));
+        lane->prof.all_launches += launched - 1;  // the two slicing kernels beyond the one PROF counted
+      }
     }
     if (!use_tc || any_fp64) {
       const int skip = use_tc ? TC_MAX_KP / 2 : -1;  // sources up to this step count were done above
@@ -1585,7 +1591,12 @@ static fks_status solve_chunked(fks_op* op, Lane* lane, const fks_c128* b, int n
     S.n = op->n;
     Arena probe;
     carve<VT>(S, probe, !x_dev);
-    return probe.off + 4096;
+    // the tensor-core assembly's slices of the first group of sources
+    const int kmax = std::min(o->m_max, TC_MAX_KP / 2);
+    const size_t tc = o->assembly == 0 && tc_supported(kmax, op->n)
+                          ? tc_ws_bytes(tc_layout(op->n, n_f, kmax, tc_group_size(op->n, n_f, kmax, ns)))
+                          : 0;
+    return probe.off + tc + 4096;
   };
   size_t one = ws_bytes(1), two = ws_bytes(2);
   size_t per = two > one ? two - one : one, fixed = one > per ? one - per : 0;
@@ -2501,6 +2512,8 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
         CK(cudaMemcpyAsync(S.amg_tab, S.amg_table.data(), S.amg_table.size(), cudaMemcpyHostToDevice, s));
       int64_t n = S.n;
       copy_in(S.V, v, sizeof(z64) * n, s);
+      // z = 0 when no cycle runs (a replayed count of 0, or v = 0 in the eps mode)
+      CK(cudaMemsetAsync(S.Z, 0, sizeof(z64) * n, s));
       CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
       int32_t cyc = cycles;
       CK(cudaMemcpyAsync(S.rep_cyc, &cyc, sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -2628,6 +2641,11 @@ extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const 
       A.cap = NOALLOC_BYTES;
       carve<VT>(S, A, false);
       int64_t n = S.n;
+      // v is copied into the fixed array first, so z may alias v (an in-place
+      // call): the defects of later cycles read the copy, not z
+      CK(cudaMemcpyAsync(S.V, v, sizeof(z64) * n, cudaMemcpyDeviceToDevice, s));
+      // z = 0 when no cycle runs (a replayed count of 0, or v = 0 in the eps mode)
+      CK(cudaMemsetAsync(z, 0, sizeof(z64) * n, s));
       CK(cudaMemcpyAsync(S.taus, &tau, sizeof(z64), cudaMemcpyHostToDevice, s));
       int32_t cyc = cycles;
       CK(cudaMemcpyAsync(S.rep_cyc, &cyc, sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -2637,7 +2655,7 @@ extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const 
       st0.tau = 0;
       CK(cudaMemcpyAsync(S.st, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));
       setup_levels<VT>(S);
-      inner_solve<VT>(S, (const z64*)v, n, (z64*)z, n);
+      inner_solve<VT>(S, S.V, n, (z64*)z, n);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));

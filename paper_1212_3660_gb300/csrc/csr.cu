@@ -5,6 +5,8 @@
 // Section 6), all batched over sources on gridDim.y.
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 #include "amg.cuh"
 #include "csr.cuh"
 #include "krylov.cuh"
@@ -677,6 +679,32 @@ void launch_csr_dinv(int64_t n, const double* dk, const double* dm, const z64* t
   k_csr_dinv<T><<<cnb(n, 256), 256, 0, s>>>(n, dk, dm, taus, ntau, out);
 }
 
+// Blocks of 256 threads of `kernel` that can be resident at once on the
+// current device, cached per (kernel variant, device): operators on devices with
+// different SM counts or occupancy each get their own figure. 0 = not yet known
+// (the cache holds the count + 1).
+constexpr int COOP_MAX_DEVICES = 64;
+static std::atomic<int> g_coop_resident[4][COOP_MAX_DEVICES];
+
+template <typename Kern>
+static int coop_capacity(int which, Kern kernel) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= COOP_MAX_DEVICES) {
+    cudaGetLastError();
+    return 0;
+  }
+  int r = g_coop_resident[which][dev].load(std::memory_order_relaxed);
+  if (r > 0) return r - 1;
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
+  }
+  g_coop_resident[which][dev].store(per * sms + 1, std::memory_order_relaxed);
+  return per * sms;
+}
+
 // one cycle: `steps` BiCGSTAB steps from e = 0 on A e = f
 template <typename T>
 void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus, const BcgVecs<T>& V,
@@ -685,18 +713,7 @@ void launch_bcg_cycle(const CsrView<T>& A, const SlotState* st, const z64* taus,
   int nbk = csr_blocks(A.n);
   dim3 g(nbk, nslot);
   // one cooperative launch when every block of the batch can be resident
-  static int resident[2] = {-1, -1};
-  int& res = resident[sizeof(T) == 8 ? 0 : 1];
-  if (res < 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bcg_cycle<T>, 256, 0) != cudaSuccess) {
-      cudaGetLastError();
-      per = 0;
-    }
-    res = per * sms;
-  }
+  const int res = coop_capacity(sizeof(T) == 8 ? 0 : 1, k_bcg_cycle<T>);
   if ((int64_t)nbk * nslot <= res) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = g;
@@ -745,18 +762,7 @@ void launch_bcg_cycle_amg(const CsrView<T>& A, const SlotState* st, const z64* t
   int nbk = csr_blocks(A.n);
   dim3 g(nbk, nslot);
   // one cooperative launch when every block of the batch can be resident
-  static int resident[2] = {-1, -1};
-  int& res = resident[sizeof(T) == 8 ? 0 : 1];
-  if (res < 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bcg_cycle_amg<T>, 256, 0) != cudaSuccess) {
-      cudaGetLastError();
-      per = 0;
-    }
-    res = per * sms;
-  }
+  const int res = coop_capacity(sizeof(T) == 8 ? 2 : 3, k_bcg_cycle_amg<T>);
   if ((int64_t)nbk * nslot <= res && g_bcg_amg_coop) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = g;
