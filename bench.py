@@ -5,10 +5,14 @@ source through the flexible Arnoldi basis, the per-shift least squares, the
 assembly x_j = Z y_j and the true-residual check. A shifted solve counts when
 its complex128 true relative residual ||b - (K + sigma_j M) x_j|| / ||b|| <= 1e-8.
 
-Default workload: 2D 512 x 512 cell-centred aquifer (n = 262144), lnK Gaussian
-field (variance 1, correlation 0.2 L, mean ln 1e-4), S_s = 1e-5, centre source,
-200 shifts (periods 5..3600 s log-spaced), 3 preconditioner shifts cycled per
-step, multigrid inner solve, complex128 throughout.
+Default workload (3): 3D 128^3 cell-centred aquifer (n = 2,097,152), anisotropic
+lnK Gaussian field (variance 1, correlation lengths 0.2/0.2/0.05 L, mean
+ln 1e-4), lognormal S_s (variance 0.25 of ln S_s), centre source, 200 shifts
+(periods 5..3600 s log-spaced), 4 preconditioner shifts cycled per step,
+multigrid inner solve in complex64 with complex128 defect correction, complex128
+outer Arnoldi / least squares / assembly / true residual ("mixed"). Its
+`comparison` times the same workload in plain complex128 on the same GPU, and
+the batched workload 4 (3D 96^3, 64 well sources, 100 shifts).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
                   [--workload 1|2|3|4|5|6|7] [--precision fp64|mixed]
@@ -56,6 +60,9 @@ WORKLOAD_STEPS = {1: 36, 2: 36, 3: 40, 4: 40}
 # with the relaxed rule, for extrapolating its bounded samples: workload 2 at
 # l = 0.003 takes 36 steps and 307 cycles when the oracle runs to the end.
 ORACLE_CYCLES = {(2, 0.003): 307}
+# The same for the 3D 128^3 workload (3) at l = 0.003: (Arnoldi steps, inner
+# cycles) of the oracle's complete solve of its source.
+ORACLE_SOLVE = {(1, 0.003): (37, 281), (2, 0.003): (36, 307)}
 JAC_SENSORS = 8   # sensors of the Jacobian workload (6)
 FP64_PEAK_TFLOPS = 1.25    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 
@@ -66,11 +73,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
-    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="default: fp64 for workloads 1, 2 and 6 (complex128 throughout), mixed for 3-5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=6)
+    ap.add_argument("--cpu-sample-steps", type=int, default=6,
+                    help="2D workloads: Arnoldi steps of the oracle's CPU sample")
+    ap.add_argument("--cpu-sample-cycles", type=int, default=4,
+                    help="3D workloads: inner multigrid cycles of the oracle's CPU sample")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="workload 3: skip timing the batched workload 4 beside the line")
     ap.add_argument("--survey", action="store_true", help="time every kernel class (stderr)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer region (very large outputs)")
     ap.add_argument("--no-compare", action="store_true",
@@ -564,6 +576,17 @@ def csr_bench(args, rank, world, local, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, _, desc = csr_cpu_sample(pr, args, amg, int(main_info["inner_cycles"][:pr.m_max].sum()))
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
+    tiling = fks.fks_op_tiling(solver.op, prec)
+    zchunks = fks.fks_op_zchunks(solver.op, prec) if len(pr.shape) == 3 else None
+    # ---- the batched workload (3D 96^3, 64 well sources) beside the 128^3 line
+    batched = None
+    if args.workload == 3 and not args.no_compare and not args.no_batched:
+        del X_d, b_d
+        solver.close()
+        torch.cuda.empty_cache()
+        batched = batched_sample(args, local, dist, world)
+    else:
+        solver.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": replicas.max(ms), "higher_is_better": True, "scaling": "weak",
@@ -764,6 +787,104 @@ def cpu_oracle_sample(pr, sample_steps, workload_steps, eps, relax=0.0, total_cy
     return len(pr.sigma) / t_full, dt, desc   # one source's shifted solves
 
 
+class OracleModel:
+    """Timed parts of the oracle's solve of a large workload, for a CPU baseline
+    that a bounded sample can measure: the setup (operator and multigrid
+    hierarchy), one inner cycle (defect and V-cycle on v_1 = b / ||b||), one
+    flexible Arnoldi orthogonalisation (M z, then two Gram-Schmidt passes
+    against k_avg basis vectors), and the final assembly x_j = Z y_j with its
+    true residual (timed on a few shifts and scaled to n_f). A whole solve of S
+    steps and C cycles is estimated as setup + C cycle + S orthogonalisation +
+    final."""
+
+    def __init__(self, pr, eps):
+        import oracle
+        from oracle.gmg import Hierarchy
+        self.pr, self.eps = pr, eps
+        t0 = time.perf_counter()
+        self.op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+        self.hier = Hierarchy(self.op, pr.tau_bar)
+        self.t_setup = time.perf_counter() - t0
+        b = pr.rhs()[:, 0]
+        self.b = b
+        self.v1 = b / np.linalg.norm(b)
+        self.calls = 0
+
+    def cycle(self):
+        """Seconds of one inner cycle (defect + V-cycle), taus in turn."""
+        p = self.calls % len(self.pr.tau_bar)
+        self.calls += 1
+        t0 = time.perf_counter()
+        self.hier.solve(self.v1, p, self.eps, 50, cycles=1)
+        return time.perf_counter() - t0
+
+    def outer(self, k_avg, k_final, shifts=4):
+        """Seconds of one orthogonalisation at k_avg, and of the final assembly
+        and true residual of all shifts at k_final steps (timed on `shifts`)."""
+        import oracle
+        rng = np.random.default_rng(0)
+        n = self.op.n
+        V = rng.standard_normal((n, k_avg + 1)) + 1j * rng.standard_normal((n, k_avg + 1))
+        z = self.v1.copy()
+        t0 = time.perf_counter()
+        w = self.op.M @ z
+        for _ in range(2):
+            for i in range(k_avg):
+                w -= np.vdot(V[:, i], w) * V[:, i]
+        np.linalg.norm(w)
+        t_orth = time.perf_counter() - t0
+        Z = V[:, :k_final] if k_final <= k_avg + 1 else rng.standard_normal((n, k_final)) + 0j
+        Y = rng.standard_normal((k_final, shifts)) + 1j * rng.standard_normal((k_final, shifts))
+        sig = self.pr.sigma[:shifts]
+        t0 = time.perf_counter()
+        X = Z @ Y
+        oracle.true_residuals(self.op, self.b, sig, X)
+        t_final = (time.perf_counter() - t0) * len(self.pr.sigma) / shifts
+        return t_orth, t_final
+
+    def estimate(self, t_cycle, steps, cycles):
+        t_orth, t_final = self.outer(max(1, steps // 2), steps)
+        total = self.t_setup + cycles * t_cycle + steps * t_orth + t_final
+        parts = {"setup_s": self.t_setup, "cycle_s": t_cycle, "orth_s_at_k_avg": t_orth, "final_s": t_final,
+                 "steps": steps, "cycles": cycles}
+        return total, parts
+
+
+def oracle_model_sample(pr, n_cycles, steps, cycles, eps):
+    """CPU baseline of a 3D workload: the oracle's timed parts (OracleModel),
+    n_cycles inner cycles measured, scaled to a whole solve of `steps` Arnoldi
+    steps and `cycles` inner cycles. Returns (solves/s, seconds, description)."""
+    t0 = time.perf_counter()
+    m = OracleModel(pr, eps)
+    ts = [m.cycle() for _ in range(max(1, n_cycles))]
+    t_cycle = statistics.median(ts)
+    total, parts = m.estimate(t_cycle, steps, cycles)
+    dt = time.perf_counter() - t0
+    desc = (f"oracle setup, {len(ts)} inner multigrid cycles (median {t_cycle:.2f} s), one orthogonalisation "
+            f"at k = {max(1, steps // 2)} and the final assembly + true residuals (timed on 4 shifts) of the first "
+            f"source, {dt:.1f} s in all; scaled to a whole solve of {steps} steps and {cycles} cycles "
+            f"(estimate {total:.1f} s)")
+    return len(pr.sigma) / total, dt, desc
+
+
+def direct_sample(pr, shifts=3):
+    """The paper's "Direct" comparator (Section 6.1): a sparse LU factorisation
+    and solve of K + sigma_j M per shift (SciPy SuperLU), timed on `shifts`
+    shifts spread over the range and scaled to all n_f. Returns (solves/s,
+    seconds, description)."""
+    import oracle
+    from oracle.direct import direct_solve
+    op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+    b = pr.rhs()[:, 0]
+    idx = np.unique(np.linspace(0, len(pr.sigma) - 1, shifts).round().astype(int))
+    t0 = time.perf_counter()
+    direct_solve(op, b, pr.sigma[idx])
+    dt = time.perf_counter() - t0
+    per = dt / len(idx)
+    return 1.0 / per, dt, (f"SuperLU factorisation + solve of K + sigma_j M for {len(idx)} of {len(pr.sigma)} "
+                           f"shifts ({dt:.1f} s, {per:.2f} s per shift), one source")
+
+
 def blas_threads():
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         if k in os.environ:
@@ -815,6 +936,39 @@ def run_reference(args):
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
+    if args.workload in (1, 2, 3, 4) and (args.workload, round(args.inner_relax, 6)) in ORACLE_SOLVE:
+        # each step: one inner multigrid cycle of the oracle at the workload's
+        # size; the value is the oracle's whole solve estimated from its timed
+        # parts and its own step and cycle counts (OracleModel)
+        pr = synth.workload(args.workload, m_max=100)
+        steps_o, cycles_o = ORACLE_SOLVE[(args.workload, round(args.inner_relax, 6))]
+        m = OracleModel(pr, INNER_EPS)
+        ts = []
+        for i in range(args.warmup + args.steps):
+            t = m.cycle()
+            if i >= args.warmup:
+                ts.append(t)
+        t_cycle = statistics.median(ts)
+        total, parts = m.estimate(t_cycle, steps_o, cycles_o)
+        n_src = len(pr.src_cells)
+        value = len(pr.sigma) / total    # every source is an independent solve of the same cost
+        sample = (f"one inner multigrid cycle per step (defect + V-cycle, median {t_cycle:.2f} s) of the first "
+                  f"source; setup, one orthogonalisation at k = {max(1, steps_o // 2)} and the final assembly + "
+                  f"true residuals timed once; whole solve estimated from the oracle's own {steps_o} steps and "
+                  f"{cycles_o} cycles: {total:.1f} s")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_cycle,
+                "step": "one inner multigrid cycle of the oracle (the measured unit; value is extrapolated)",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic",
+                "config": {"workload": pr.name, "grid": "x".join(map(str, pr.shape[::-1])), "n_f": len(pr.sigma),
+                           "sources": n_src},
+                "extrapolation": parts,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == 5:
         # the stream's first request stands for the stream
         _, p0 = synth.make_request_stream(1, seed=3000, max_cells=SERVE_MAX_CELLS, max_sources=SERVE_MAX_SOURCES)[0]
@@ -841,6 +995,63 @@ def run_reference(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batched_sample(args, local, dist, world):
+    """The batched workload (3D 96^3, 64 well sources x 100 shifts, complex64
+    cycles with complex128 outer work, relaxed inner tolerance): the sources
+    advance in lockstep batches sized to free device memory, one CUDA graph per
+    batch, tiles and z-chunks from the autotuner. Timed like the line itself
+    (device-resident inputs, CUDA events on the library's stream)."""
+    import torch
+
+    from paper_1212_3660_gb300 import fks, synth
+    from paper_1212_3660_gb300.solver import Solver
+    pr = synth.workload(4, m_max=100)
+    prec = fks.FKS_PREC_MIXED
+    solver = Solver(pr, device=local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    n, n_f, n_rhs = pr.n, len(pr.sigma), len(pr.src_cells)
+    b_d = torch.from_numpy(pr.rhs().T.copy()).to(dev)
+    sig_d = torch.from_numpy(pr.sigma.astype(np.complex128)).to(dev)
+    tau_d = torch.from_numpy(pr.tau_bar.astype(np.complex128)).to(dev)
+    X_d = torch.empty((n_rhs, n_f, n), dtype=torch.complex128, device=dev)
+    est = np.zeros((n_rhs, n_f)); bnd = np.zeros((n_rhs, n_f)); tru = np.zeros((n_rhs, n_f))
+    mj = np.zeros((n_rhs, n_f), np.int32); sst = np.zeros((n_rhs, n_f), np.int32)
+    opts, keep = fks.make_options(tol=TOL, m_max=pr.m_max, precision=prec, inner_tol=INNER_EPS,
+                                  schedule=pr.schedule, inner_relax=args.inner_relax if args.inner_relax > 0 else 0.003)
+    info, info_arr = fks.make_info(n_rhs, pr.m_max)
+    fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+
+    def step():
+        return fks.fks_solve(solver.op, b_d, n_rhs, sig_d, n_f, tau_d, len(pr.tau_bar), opts, X_d, est, bnd, tru,
+                             mj, sst, info, sh)
+
+    step()
+    reps = 2
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    conv = 0
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+        conv += int(np.sum(tru <= TOL))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out = {"value": conv / reps / (ms / 1000.0), "ms_per_step": ms, "precision": "mixed",
+           "workload": pr.name, "sources": n_rhs, "n_f": n_f, "grid": "x".join(map(str, pr.shape[::-1])),
+           "converged_per_step": conv / reps, "solves_per_step": n_f * n_rhs,
+           "arnoldi_steps_max": int(info_arr["steps"].max()), "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
+           "steps_timed": reps, "tiling": list(fks.fks_op_tiling(solver.op, prec)),
+           "zchunks": fks.fks_op_zchunks(solver.op, prec)}
+    del X_d
+    solver.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -1084,21 +1295,47 @@ def main():
     if args.workload in (1, 2, 3, 4) and not args.no_compare:
         comparison = {"this_line": {"value": value, "precision": args.precision, "inner_relax": args.inner_relax},
                       "plain_fp64_fixed_eps": variant(fks.FKS_PREC_FP64, 0.0),
+                      "fp64_relaxed": variant(fks.FKS_PREC_FP64, args.inner_relax if args.inner_relax > 0 else 0.003),
                       "mixed_relaxed": variant(fks.FKS_PREC_MIXED, args.inner_relax if args.inner_relax > 0 else 0.003)}
         # restore this line's tuning for what follows
         fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
 
     cpu = None
+    direct = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ws = int(main_info["steps"].max()) or WORKLOAD_STEPS.get(args.workload, 40)
-        v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS, args.inner_relax,
-                                        int(main_info["inner_cycles"][:pr.m_max].sum()))
+        cyc0 = int(main_info["inner_cycles"][:pr.m_max].sum())
+        if len(pr.shape) == 3:
+            v, dt, desc = oracle_model_sample(pr, args.cpu_sample_cycles, int(main_info["steps"][0]) or ws, cyc0,
+                                              INNER_EPS)
+            desc += " (the GPU solve's step and cycle counts)"
+        else:
+            v, dt, desc = cpu_oracle_sample(pr, args.cpu_sample_steps, ws, INNER_EPS, args.inner_relax, cyc0)
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
+        if len(pr.shape) == 2:
+            dv, _, ddesc = direct_sample(pr)
+            direct = {"value": dv, "unit": UNIT, "cores": blas_threads(), "kind": "direct (paper's comparator)",
+                      "sample": ddesc}
+        else:
+            direct = {"value": None, "note": "not timed: a SuperLU factorisation of a 3D operator of this size "
+                                             "(seven-point stencil, millions of unknowns) per shift does not fit "
+                                             "a bounded sample"}
 
     if roof is not None:
         roof["alg_bytes_per_launch"] = prof["bytes"] / max(prof["launches"], 1)
         roof["traffic_source"] = ("profiles/traffic.md (ncu, sources " + traffic_src + ")") if traffic is not None \
             else ("stale: kernels changed since the ncu capture" if traffic_src else "no ncu capture recorded")
+    tiling = fks.fks_op_tiling(solver.op, prec)
+    zchunks = fks.fks_op_zchunks(solver.op, prec) if len(pr.shape) == 3 else None
+    # ---- the batched workload (3D 96^3, 64 well sources) beside the 128^3 line
+    batched = None
+    if args.workload == 3 and not args.no_compare and not args.no_batched:
+        del X_d, b_d
+        solver.close()
+        torch.cuda.empty_cache()
+        batched = batched_sample(args, local, dist, world)
+    else:
+        solver.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -1114,19 +1351,19 @@ def main():
                            "arnoldi_steps": int(main_info["steps"].max()),
                            "inner_cycles_total": int(main_info["inner_cycles"].sum()),
                            "op_setup_ms": setup_ms, "fused_levels_max_cells": tuned,
-                           "tile16_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[1],
-                           "tail_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[2],
-                           "cluster_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[3],
-                           "tile8_levels_max_cells": fks.fks_op_tiling(solver.op, prec)[4],
+                           "tile16_levels_max_cells": tiling[1], "tail_levels_max_cells": tiling[2],
+                           "cluster_levels_max_cells": tiling[3], "tile8_levels_max_cells": tiling[4],
+                           "zchunk_planes_per_level": zchunks,
                            "launch_mode": args.launch_mode, "variant": args.variant,
                            "restart_len": args.restart,
                            "basis_bytes_per_source": (2 * (args.restart or pr.m_max) + 1) * n * 16},
                 "solves_per_step": n_f * n_rhs, "converged_per_step": conv_per_step,
                 "e2e": e2e, "comparison": comparison, "monitors": monitors,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "roofline": roof, "cpu_baseline": cpu, "direct_baseline": direct, "clocks": clk.summary(),
                 "gpu_launches": launches}
+        if batched is not None and line["comparison"] is not None:
+            line["comparison"]["batched_workload4"] = batched
         print(json.dumps(line), flush=True)
-    solver.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -412,6 +412,22 @@ fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells);
  * operators only.
  */
 fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells);
+/*
+ * Fused 3D levels (Section 4's multigrid inner solve): a 3D level coarsened by
+ * 2 in every axis and within the fusion threshold runs its pre-smoothing
+ * (four half sweeps, residual, restriction) and its post-smoothing
+ * (interpolation, four half sweeps) as one kernel each. A block owns a tile of
+ * cells in the x-y plane (8 x 8, 16 x 16 or 32 x 16, by the same thresholds as
+ * the 2D tiles) and a chunk of `planes` consecutive planes, and marches through
+ * them. This sets the chunk of multigrid level `level` (0 = finest) for
+ * `precision`; planes is rounded down to an even number >= 2, and planes <= 0
+ * means the whole level. FKS_ERR_ARG for a bad level. The results do not
+ * depend on it. Grid operators only.
+ */
+fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes);
+/* The z-chunk of every multigrid level of `precision` (planes[0 .. levels-1],
+ * as fks_op_set_zchunk stores them); *levels receives the level count. */
+fks_status fks_op_zchunks(const fks_op* op, int precision, int32_t* planes, int cap, int* levels);
 /* The current fusion threshold, 16 x 16 tile threshold, single-block tail
  * threshold (levels of at most tail_max cells run in one block per source),
  * cluster threshold (0: off) and 8 x 8 tile threshold of `precision`; any
@@ -467,7 +483,9 @@ enum {
   FKS_K_POST2D = 13,   /* 2D level: prolongation + four post-smoothing half sweeps */
   FKS_K_BICGSTAB = 14, /* CSR operators: one BiCGSTAB cycle of the inner solve    */
   FKS_K_CLUSTER = 15,  /* the V-cycle of the lower 2D levels in one 8-CTA cluster per source */
-  FKS_K_COUNT = 16
+  FKS_K_PRE3D = 16,    /* 3D level: four pre-smoothing half sweeps + residual + restriction (z-march) */
+  FKS_K_POST3D = 17,   /* 3D level: prolongation + four post-smoothing half sweeps (z-march) */
+  FKS_K_COUNT = 18
 };
 /*
  * Time every launch of kernel class `kclass` (on level `level`, or every level

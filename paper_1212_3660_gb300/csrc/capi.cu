@@ -252,6 +252,9 @@ struct fks_op {
   // from the first level with at most this many cells (and a cluster layout)
   // down, the V-cycle runs in the cluster kernel instead of the tail (0: off)
   int64_t cluster_max[2] = {0, 0};
+  // planes per block of the fused 3D level kernels, per level (0: the whole level)
+  int zchunk[2][MAX_LEVELS] = {{16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16},
+                               {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16}};
 };
 
 namespace fks {
@@ -511,6 +514,7 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
   const int64_t t16 = S.op->tile16_max[sizeof(VT) == 8 ? 0 : 1];
   const int64_t t8 = S.op->tile8_max[sizeof(VT) == 8 ? 0 : 1];
   auto tile_of = [&](const LevelHost& L) { return L.n <= t8 ? 8 : (L.n <= t16 ? 16 : 32); };
+  const int pix = sizeof(VT) == 8 ? 0 : 1;
   for (int l = 0; l < lt; ++l) {
     const LevelHost& L = Ls[l];
     if (fused_level_ok(L) && L.n <= fmax) {
@@ -518,6 +522,13 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
            ns * L.n * (2 * (8 * d + 6) + 8 * d + 10),
            launch_pre2d<VT>(L, Ls[l + 1], S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
                             tile_of(L), s));
+      continue;
+    }
+    if (fused3d_level_ok(L) && L.n <= fmax) {
+      PROF(FKS_K_PRE3D, l, ns * (L.n * (3 * cv + (d + 1) * rv) + cv * Ls[l + 1].n),
+           ns * L.n * (2 * (8 * d + 6) + 8 * d + 10),
+           launch_pre3d<VT>(L, S.st, I(l), S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot, tile_of(L),
+                            S.op->zchunk[pix][l], s));
       continue;
     }
     for (int r = 0; r < NU1; ++r) {
@@ -598,15 +609,28 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
       zfin = add_to_zk ? nullptr : out;
       continue;
     }
+    if (fused3d_level_ok(L) && L.n <= fmax) {
+      cx<VT>* out = (cx<VT>*)S.z2[l];
+      const bool add_to_zk = l == 0 && Zk;
+      PROF(FKS_K_POST3D, l, ns * (L.n * (4 * cv + d * rv) + cv * Ls[l + 1].n),
+           ns * L.n * (18 + 2 * (8 * d + 6)),
+           launch_post3d<VT>(L, S.op->mask, S.st, I(l), F(l), Zl(l), out, L.n, zfin, Ls[l + 1].n, S.nslot,
+                             tile_of(L), S.op->zchunk[pix][l], s, add_to_zk ? Zk : nullptr, vsZk, zcol));
+      zfin = add_to_zk ? nullptr : out;
+      continue;
+    }
     PROF(FKS_K_PROLONG, l, ns * (2 * cv * L.n + cv * Ls[l + 1].n), ns * L.n * (4.0 * (1 << S.op->dim) + 2),
          launch_prolong_add<VT>(L, Ls[l + 1], S.op->mask, S.st, zfin, Ls[l + 1].n, Zl(l), L.n, S.nslot, s));
+    // on the finest level the last half sweep also adds the correction to z_k
+    const bool add_to_zk = l == 0 && Zk;
     for (int r = 0; r < NU2; ++r) {
       PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
            launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s));
-      PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
-           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, 0, s));
+      const bool last = add_to_zk && r == NU2 - 1;
+      PROF(FKS_K_SMOOTH, l, smooth_b(L, 0) + (last ? ns * L.n * 32.0 : 0.0), smooth_f(L, 0) + (last ? ns * L.n * 2.0 : 0.0),
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, 0, s, last ? Zk : nullptr, vsZk, zcol));
     }
-    zfin = Zl(l);
+    zfin = add_to_zk ? nullptr : Zl(l);
   }
   return zfin;
 }
@@ -964,6 +988,7 @@ static void setup_levels(Solve& S) {
     std::lock_guard<std::mutex> build_lock(g_build_mu);
     tail_prepare<VT>(tail_launch_smem<VT>(Ls, tail_level<VT>(Ls, tail_max_of<VT>(S.op))));
     fused_prepare<VT>();
+    fused3d_prepare<VT>();
     size_t csm = 0;
     if (cluster_level<VT>(S.op, nullptr, &csm) >= 0) cluster_prepare<VT>(csm);
   }
@@ -1205,6 +1230,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1],
                                  (double)op->tile8_max[0], (double)op->tile8_max[1], (double)S.tolv_on,
                                  (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L};
+      for (int pz = 0; pz < 2; ++pz)
+        for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
@@ -2020,6 +2047,24 @@ fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
   return FKS_OK;
 }
 
+fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes) {
+  if (!op) { set_error("fks_op_set_zchunk: NULL operator"); return FKS_ERR_ARG; }
+  if (op->csr) { set_error("fks_op_set_zchunk: grid operators only"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_zchunk: bad precision"); return FKS_ERR_ARG; }
+  if (level < 0 || level >= (int)op->levels.size()) { set_error("fks_op_set_zchunk: no such level"); return FKS_ERR_ARG; }
+  op->zchunk[precision == FKS_PREC_FP64 ? 0 : 1][level] = planes <= 0 ? 0 : std::max(2, planes & ~1);
+  return FKS_OK;
+}
+
+fks_status fks_op_zchunks(const fks_op* op, int precision, int32_t* planes, int cap, int* levels) {
+  if (!op) { set_error("fks_op_zchunks: NULL operator"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_zchunks: bad precision"); return FKS_ERR_ARG; }
+  const int nl = (int)op->levels.size();
+  if (levels) *levels = nl;
+  for (int l = 0; l < nl && l < cap && planes; ++l) planes[l] = op->zchunk[precision == FKS_PREC_FP64 ? 0 : 1][l];
+  return FKS_OK;
+}
+
 fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
                          int64_t* tail_max, int64_t* cluster_max, int64_t* tile8_max) {
   if (!op) { set_error("fks_op_tiling: NULL operator"); return FKS_ERR_ARG; }
@@ -2042,6 +2087,8 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi], savedt = op->tail_max[pi];
   int64_t savedc = op->cluster_max[pi], saved8 = op->tile8_max[pi];
+  int savedz[MAX_LEVELS];
+  std::memcpy(savedz, op->zchunk[pi], sizeof(savedz));
   try {
     CK(cudaSetDevice(op->ctx->device));
     Solve S{};
@@ -2076,7 +2123,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       // candidate thresholds that change which levels are fused
       std::vector<int64_t> cand = {0};
       for (auto& L : op->levels)
-        if (fused_level_ok(L)) cand.push_back(L.n);
+        if (fused_level_ok(L) || fused3d_level_ok(L)) cand.push_back(L.n);
       std::sort(cand.begin(), cand.end());
       cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
       cudaStream_t cs = nullptr;
@@ -2178,6 +2225,26 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
           pick8 = u;
         }
       }
+      // then the z-chunk of every fused 3D level of the pick, level by level
+      {
+        const Choice ch{pick, pick16, pickt, pickc, pick8};
+        const int lt = tail_level<VT>(op->levels, pickt);
+        for (int l = 0; l < lt && l < MAX_LEVELS; ++l) {
+          const LevelHost& L = op->levels[l];
+          if (!fused3d_level_ok(L) || L.n > pick) continue;
+          int bestz = op->zchunk[pi][l];
+          for (int zc : {2, 4, 8, 16, 32, 64, 0}) {
+            if (zc > L.nz || zc == bestz) continue;
+            op->zchunk[pi][l] = zc;
+            const float ms = measure(ch);
+            if (ms < best) {
+              best = ms;
+              bestz = zc;
+            }
+          }
+          op->zchunk[pi][l] = bestz;
+        }
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       cudaStreamDestroy(cs);
@@ -2195,6 +2262,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
     op->tail_max[pi] = savedt;
     op->cluster_max[pi] = savedc;
     op->tile8_max[pi] = saved8;
+    std::memcpy(op->zchunk[pi], savedz, sizeof(savedz));
     set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
   }

@@ -196,6 +196,41 @@ __global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restric
   z[slot * vs + c] = gs_value(L, p, c, id, f + slot * vs, z + slot * vs, zero_start);
 }
 
+// The last half sweep of the finest level's post-smoothing fused with the
+// defect correction: thread (ii, row) owns cells 2 ii and 2 ii + 1 of the row,
+// updates the one of colour `color` as k_gs does, and adds both final values
+// e to column k - 1 of the outer iterates (z_k = e on the first cycle, z_k + e
+// after), the update of k_correct. z itself is not written: nothing reads the
+// finest level's correction after this.
+template <typename T>
+__global__ void k_gs_correct(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+                             const cx<T>* __restrict__ f, const cx<T>* __restrict__ z, int64_t vs, int color,
+                             z64* __restrict__ Zk, int64_t vsZk, int64_t zcol) {
+  const int slot = blockIdx.z;
+  if (!slot_running(st, slot)) return;
+  const int ii = blockIdx.x * GX + threadIdx.x;
+  const int row = blockIdx.y * GY + threadIdx.y;
+  if (row >= L.ny * L.nz || 2 * ii >= L.nx) return;
+  const int k = row / L.ny, j = row - k * L.ny;
+  const cx<T>* zs = z + slot * vs;
+  z64* zk = Zk + slot * vsZk + (int64_t)(st[slot].k - 1) * zcol;
+  const bool first = st[slot].cycles == 0;
+  for (int h = 0; h < 2; ++h) {
+    const int i = 2 * ii + h;
+    if (i >= L.nx) break;
+    const int c = row * L.nx + i;
+    cx<T> e;
+    if (((i + j + k) & 1) == color) {
+      const cx<T> id = invd[(int64_t)st[slot].tau * L.n + c];
+      e = gs_value(L, Cell{i, j, k}, c, id, f + slot * vs, zs, 0);
+    } else {
+      e = zs[c];
+    }
+    const z64 ev = cvt<double>(e);
+    zk[c] = first ? ev : (zk[c] + ev);
+  }
+}
+
 // --------------------------------------------------------------------- transfer
 // Coarse right-hand side = sum over the children of the fine residual f - A z.
 template <typename T>
@@ -235,7 +270,6 @@ __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, i
 //   pre : z = four half sweeps from z = 0 (red, black, red, black); write z;
 //         coarse f = sum over children of (f - A z)
 //   post: z += P z_coarse; four half sweeps (black, red, black, red); write z
-constexpr int FH = 4;
 constexpr int DEFECT_ROWS = 2;  // rows of cells per thread in the defect kernel
 
 // sum over existing neighbours of t_face * z_nb for a 2D cell held at r in a
@@ -1107,7 +1141,12 @@ void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* 
 
 template <typename T>
 void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
-               int nslot, int color, int zero_start, cudaStream_t s) {
+               int nslot, int color, int zero_start, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
+  if (Zk) {
+    k_gs_correct<T><<<grid2((L.nx + 1) / 2, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), st, invd, f, z, vs,
+                                                                                    color, Zk, vsZk, zcol);
+    return;
+  }
   k_gs<T><<<grid2((L.nx + 1) / 2, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), st, invd, f, z, vs, color,
                                                                           zero_start);
 }
@@ -1266,7 +1305,7 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
   template void launch_apply<T>(const LevelHost&, z64, const SlotState*, const z64*, const cx<T>*, cx<T>*, int64_t, \
                                 int, cudaStream_t);                                                               \
   template void launch_gs<T>(const LevelHost&, const SlotState*, const cx<T>*, const cx<T>*, cx<T>*, int64_t, int,  \
-                             int, int, cudaStream_t);                                                             \
+                             int, int, cudaStream_t, z64*, int64_t, int64_t);                                     \
   template void launch_residual_restrict<T>(const LevelHost&, const LevelHost&, const SlotState*, const z64*,      \
                                             const cx<T>*, const cx<T>*, int64_t, cx<T>*, int64_t, int,           \
                                             cudaStream_t);                                                        \

@@ -5,6 +5,8 @@
 namespace fks {
 
 constexpr int TAIL_THREADS = 512;
+// halo of the fused level kernels: four half sweeps, one cell each
+constexpr int FH = 4;
 
 // One level of the single-block tail V-cycle; f lives at shared offset `off`
 // (in complex elements) and z right after it.
@@ -54,6 +56,18 @@ template <typename T>
 void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* invd,
                    const cx<T>* f, const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot,
                    int tile, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0);
+// 3D levels coarsened by 2 in every axis (grid3d.cu): tile 8 (8 x 8), 16
+// (16 x 16) or 32 (32 x 16) cells in x-y, zc planes per block (even; <= 0: all)
+bool fused3d_level_ok(const LevelHost& L);
+template <typename T>
+void fused3d_prepare();
+template <typename T>
+void launch_pre3d(const LevelHost& F, const SlotState* st, const cx<T>* invd, const z64* taus, const cx<T>* f,
+                  cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, int tile, int zc, cudaStream_t s);
+template <typename T>
+void launch_post3d(const LevelHost& F, uint32_t mask, const SlotState* st, const cx<T>* invd, const cx<T>* f,
+                   const cx<T>* z, cx<T>* zout, int64_t vs, const cx<T>* zc, int64_t vsc, int nslot, int tile,
+                   int zch, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0);
 // P.pairs selects the register-resident 2D kernel (same results)
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s);
@@ -72,9 +86,13 @@ void launch_to_prec(const z64* a, cx<T>* b, int64_t n, cudaStream_t s);
 template <typename T>
 void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* taus, const cx<T>* x, cx<T>* y,
                   int64_t vs, int nslot, cudaStream_t s);
+// Zk (optional): the finest level's last half sweep, fused with the defect
+// correction (both cells of each pair are added to column k - 1 of Zk, as
+// launch_correct does; z is not written)
 template <typename T>
 void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
-               int nslot, int color, int zero_start, cudaStream_t s);
+               int nslot, int color, int zero_start, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0,
+               int64_t zcol = 0);
 template <typename T>
 void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
                               const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,

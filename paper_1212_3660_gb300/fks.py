@@ -23,7 +23,7 @@ FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1,
 FKS_FGMRES, FKS_FFOM = 0, 1
 FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
 KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
-                  "assemble", "tres", "tail", "pre2d", "post2d", "bicgstab", "cluster"]
+                  "assemble", "tres", "tail", "pre2d", "post2d", "bicgstab", "cluster", "pre3d", "post3d"]
 
 
 class fks_c128(C.Structure):
@@ -110,6 +110,8 @@ def lib():
     L.fks_op_set_tiles8.argtypes = [vp, C.c_int, C.c_int64]
     L.fks_op_tiling.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.fks_op_set_zchunk.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.fks_op_zchunks.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_int)]
     L.fks_server_create.argtypes = [vp, C.c_size_t, C.c_int, C.POINTER(vp)]
     L.fks_server_submit.argtypes = [vp, C.POINTER(fks_request), C.POINTER(C.c_uint64)]
     L.fks_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -124,6 +126,7 @@ def lib():
     for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_op_amg", "fks_op_amg_setup", "fks_op_amg_info", "fks_amg_host_shape", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
+                 "fks_op_set_zchunk", "fks_op_zchunks",
                  "fks_server_create",
                  "fks_server_submit", "fks_server_poll", "fks_server_wait",
                  "fks_server_cancel", "fks_server_times", "fks_server_launches"):
@@ -390,6 +393,23 @@ def fks_op_set_tiles8(op, precision, max_cells):
     st = lib().fks_op_set_tiles8(op, int(precision), int(max_cells))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
+
+
+def fks_op_set_zchunk(op, precision, level, planes):
+    """Planes per block of the fused 3D kernels on multigrid level `level` (<= 0: all)."""
+    st = lib().fks_op_set_zchunk(op, int(precision), int(level), int(planes))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+
+
+def fks_op_zchunks(op, precision):
+    """The z-chunk of every multigrid level (list of planes per block)."""
+    buf = (C.c_int32 * 16)()
+    nl = C.c_int(0)
+    st = lib().fks_op_zchunks(op, int(precision), buf, 16, C.byref(nl))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return [int(buf[i]) for i in range(nl.value)]
 
 
 def fks_op_tiling(op, precision):

@@ -28,3 +28,27 @@ def test_reference_arm_workload7_line(monkeypatch):
     assert "BiCGSTAB cycles" in line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_grid_workload_line(monkeypatch):
+    """The reference arm of a grid workload: every step one inner multigrid
+    cycle of the oracle, the value the oracle's whole solve estimated from its
+    timed parts and its own step and cycle counts (2D 64 x 64 workload here)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "1", "--steps", "2",
+                                      "--warmup", "1"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.main()
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["config"]["workload"] == "2d-64x64-f10-p1"
+    ex = line["extrapolation"]
+    assert ex["steps"] == 37 and ex["cycles"] == 281
+    est = ex["setup_s"] + ex["cycles"] * ex["cycle_s"] + ex["steps"] * ex["orth_s_at_k_avg"] + ex["final_s"]
+    assert abs(10 / est - line["value"]) <= 1e-9 * line["value"]
+    assert abs(line["ms_per_step"] - 1000 * ex["cycle_s"]) <= 1e-9 * line["ms_per_step"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]

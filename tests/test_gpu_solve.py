@@ -208,6 +208,64 @@ def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
 
 
 @pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+@pytest.mark.parametrize("shape,n_src", [((20, 24, 40), 1), ((32, 48, 32), 2)])
+def test_fused_3d_levels_agree_bitwise(precision, shape, n_src):
+    """The 3D z-march kernels (four half sweeps, residual and restriction, or
+    interpolation and four half sweeps, per launch) repeat the per-level
+    kernels' operations in the same order: the same bits for every tile shape
+    and z-chunk, including ragged tiles (40 x 24 cells in x-y against 16 x 16
+    and 32 x 16 tiles) and ragged chunks (20 planes in chunks of 6 or 8), a
+    level that is not coarsened in z (10 x 6 x 5 below 20 x 12 x 10) and the
+    host-driven loop."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=5, periods=(5.0, 3600.0), n_p=3, seed=37, n_src=n_src, m_max=60)
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, 0)
+    a = s.solve(precision=precision, inner_tol=1e-10)
+    fks.fks_op_set_fusion(s.op, precision, -1)
+    nl = len(fks.fks_op_zchunks(s.op, precision))
+    for t16, t8 in ((0, 0), (-1, 0), (-1, -1)):        # 32 x 16, 16 x 16, 8 x 8 tiles
+        fks.fks_op_set_tiles(s.op, precision, t16)
+        fks.fks_op_set_tiles8(s.op, precision, t8)
+        for zc in (2, 6, 8, 0):
+            for lv in range(nl):
+                fks.fks_op_set_zchunk(s.op, precision, lv, zc)
+            d = s.solve(precision=precision, inner_tol=1e-10)
+            assert np.array_equal(a.X, d.X), (t16, t8, zc)
+            assert np.array_equal(a.inner_cycles, d.inner_cycles) and np.array_equal(a.m_j, d.m_j)
+    h = s.solve(precision=precision, inner_tol=1e-10, launch_mode=1)
+    assert np.array_equal(a.X, h.X)
+    fks.fks_op_autotune(s.op, precision, pr.tau_bar[1])
+    c = s.solve(precision=precision, inner_tol=1e-10)
+    assert np.array_equal(a.X, c.X), (fks.fks_op_tiling(s.op, precision), fks.fks_op_zchunks(s.op, precision))
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_fused_3d_replay_parity(precision):
+    """Replay parity with the oracle on a 3D grid whose levels all run in the
+    z-march kernels (chunks of 4 planes, 8 x 8 tiles), every x_j to 1e-8
+    (complex128) or 1e-6 (complex64 cycles)."""
+    need_gpu()
+    pr = synth.make_problem((24, 16, 32), n_f=6, periods=(5.0, 3600.0), n_p=3, seed=39, m_max=80,
+                            corr_frac=(0.2, 0.2, 0.05), ss_var=0.25)
+    eps = 1e-10
+    op, ref = oracle_run(pr, eps)
+    rc, mj = replay_arrays(pr, [ref])
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, -1)
+    fks.fks_op_set_tiles8(s.op, precision, -1)
+    for lv in range(len(fks.fks_op_zchunks(s.op, precision))):
+        fks.fks_op_set_zchunk(s.op, precision, lv, 4)
+    out = s.solve(inner_tol=eps, precision=precision, replay_cycles=rc, replay_mj=mj)
+    assert np.array_equal(out.m_j[0], ref.m_j)
+    tol = 1e-8 if precision == fks.FKS_PREC_FP64 else 1e-6
+    for j in range(len(pr.sigma)):
+        assert rel_err(out.X[0, j], ref.x[:, j]) <= tol, j
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
 @pytest.mark.parametrize("shape,n_src", [((64, 80), 1), ((256, 256), 3)])
 def test_cluster_vcycle_agrees_bitwise(precision, shape, n_src):
     """The cluster kernel (lower levels as bands of rows in the shared memory of
