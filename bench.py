@@ -62,7 +62,7 @@ WORKLOAD_STEPS = {1: 36, 2: 36, 3: 40, 4: 40}
 ORACLE_CYCLES = {(2, 0.003): 307}
 # The same for the 3D 128^3 workload (3) at l = 0.003: (Arnoldi steps, inner
 # cycles) of the oracle's complete solve of its source.
-ORACLE_SOLVE = {(1, 0.003): (37, 281), (2, 0.003): (36, 307)}
+ORACLE_SOLVE = {(1, 0.003): (37, 281), (2, 0.003): (36, 307), (3, 0.003): (31, 327)}
 JAC_SENSORS = 8   # sensors of the Jacobian workload (6)
 FP64_PEAK_TFLOPS = 1.25    # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 
@@ -88,7 +88,11 @@ def parse():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain (complex128, fixed tolerance) and mixed relaxed variants")
     ap.add_argument("--single", action="store_true",
-                    help="one untimed solve and exit (a small command for ncu captures)")
+                    help="one untimed solve (after autotuning) and exit (a short command for ncu launch lists)")
+    ap.add_argument("--precond-cycles", type=int, default=0,
+                    help="run this many inner cycles of one fks_precond_apply on the workload's operator (after "
+                         "autotuning) and exit: the inner-solve kernels at full size with a small device footprint, "
+                         "for ncu captures")
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "host"],
                     help="graph: the step loop as one CUDA graph; host: the same kernels launched one by one")
     ap.add_argument("--inner-relax", type=float, default=0.003,
@@ -997,6 +1001,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def set_thresholds(fks, op, prec, args):
+    """The multigrid launch thresholds given on the command line (instead of the
+    autotuner's, e.g. for an ncu capture whose timings would mislead it)."""
+    fks.fks_op_set_fusion(op, prec, args.fuse_max)
+    if args.tile16_max is not None:
+        fks.fks_op_set_tiles(op, prec, args.tile16_max)
+    if args.tail_max is not None:
+        fks.fks_op_set_tail(op, prec, args.tail_max)
+    if args.cluster_max is not None:
+        fks.fks_op_set_cluster(op, prec, args.cluster_max)
+    if args.tile8_max is not None:
+        fks.fks_op_set_tiles8(op, prec, args.tile8_max)
+
+
 def batched_sample(args, local, dist, world):
     """The batched workload (3D 96^3, 64 well sources x 100 shifts, complex64
     cycles with complex128 outer work, relaxed inner tolerance): the sources
@@ -1093,6 +1111,23 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
     n, n_f, n_rhs = pr.n, len(pr.sigma), len(pr.src_cells)
+    if args.precond_cycles > 0:
+        # the inner-solve kernels of this workload's operator, tuned as the
+        # solve is (or with the thresholds given), on v = b / ||b|| (no basis,
+        # no outputs on the device)
+        if args.fuse_max is not None:
+            set_thresholds(fks, solver.op, prec, args)
+        else:
+            fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+        v = torch.from_numpy(pr.rhs()[:, 0] / np.linalg.norm(pr.rhs()[:, 0])).to(dev)
+        z = torch.zeros_like(v)
+        st, cyc, pn = fks.fks_precond_apply(solver.op, complex(pr.tau_bar[len(pr.tau_bar) // 2]), v, z, INNER_EPS,
+                                            cycles=args.precond_cycles, precision=prec, stream=sh)
+        torch.cuda.synchronize()
+        print(json.dumps({"precond_cycles": cyc, "pnorm": pn, "tiling": list(fks.fks_op_tiling(solver.op, prec))}),
+              flush=True)
+        solver.close()
+        return
     b_d = torch.from_numpy(pr.rhs().T.copy()).to(dev)
     sig_d = torch.from_numpy(pr.sigma.astype(np.complex128)).to(dev)
     tau_d = torch.from_numpy(pr.tau_bar.astype(np.complex128)).to(dev)
@@ -1117,25 +1152,18 @@ def main():
     barrier, max_over_ranks, sum_over_ranks = replicas.barrier, replicas.max, replicas.sum
 
     if args.fuse_max is not None:
-        fks.fks_op_set_fusion(solver.op, prec, args.fuse_max)
-        if args.tile16_max is not None:
-            fks.fks_op_set_tiles(solver.op, prec, args.tile16_max)
-        if args.tail_max is not None:
-            fks.fks_op_set_tail(solver.op, prec, args.tail_max)
-        if args.cluster_max is not None:
-            fks.fks_op_set_cluster(solver.op, prec, args.cluster_max)
-        if args.tile8_max is not None:
-            fks.fks_op_set_tiles8(solver.op, prec, args.tile8_max)
-    if args.single:
-        st = step(b_d, X_d)
-        torch.cuda.synchronize()
-        print(json.dumps({"single_solve_status": st, "converged": int(np.sum(tru <= TOL))}), flush=True)
-        solver.close()
-        return
+        set_thresholds(fks, solver.op, prec, args)
     if args.fuse_max is not None:
         tuned = args.fuse_max
     else:
         tuned = fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
+    if args.single:
+        st = step(b_d, X_d)
+        torch.cuda.synchronize()
+        print(json.dumps({"single_solve_status": st, "converged": int(np.sum(tru <= TOL)),
+                          "tiling": list(fks.fks_op_tiling(solver.op, prec))}), flush=True)
+        solver.close()
+        return
     for _ in range(args.warmup):
         step(b_d, X_d)
     # kernel-class survey (stderr only) and choice of the dominant class

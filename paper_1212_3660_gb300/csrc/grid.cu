@@ -5,6 +5,8 @@
 //
 // Every vector kernel takes a batch of sources ("slots") on gridDim.y; vector
 // arguments point at slot 0 and consecutive slots are `vs` elements apart.
+#include <algorithm>
+
 #include "grid.cuh"
 #include "stencil.cuh"
 
@@ -184,16 +186,27 @@ __global__ void k_apply(LevelView<T> L, z64 s_fixed, const SlotState* st, const 
 // One red-black Gauss-Seidel half sweep on the cells of `color`
 // (color 0 = red: i + j + k even): z_c = (f_c + sum_nb t z_nb) / (K_cc + tau M_cc).
 // `zero_start`: the other colour is taken as zero (first sweep from z = 0).
+// Multiple sources (SpMM form): a block holds G sources of the batch as
+// threadIdx.z over the same cells (blockDim = (32, 8 / G, G)), so a cell's
+// faces and inverse diagonal are fetched from memory once and served to the
+// other sources' warps from the SM's L1 (sources in lockstep share tau_k);
+// sources whose inner solve has finished return at once. Every source's update
+// is the single-source one.
 template <typename T>
 __global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
-                     const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs, int color, int zero_start) {
-  int slot = blockIdx.z;
-  if (!slot_running(st, slot)) return;
-  Cell p;
-  int c;
-  if (!grid_color_cell(L.nx, L.ny, L.nz, color, &p, &c)) return;
-  cx<T> id = invd[(int64_t)st[slot].tau * L.n + c];
-  z[slot * vs + c] = gs_value(L, p, c, id, f + slot * vs, z + slot * vs, zero_start);
+                     const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs, int color, int zero_start,
+                     int nslot) {
+  const int slot = blockIdx.z * blockDim.z + threadIdx.z;
+  if (slot >= nslot || !slot_running(st, slot)) return;
+  const int ii = blockIdx.x * GX + threadIdx.x;
+  const int row = blockIdx.y * blockDim.y + threadIdx.y;
+  if (row >= L.ny * L.nz) return;
+  const int k = row / L.ny, j = row - k * L.ny;
+  const int i = 2 * ii + ((j + k + color) & 1);
+  if (i >= L.nx) return;
+  const int c = row * L.nx + i;
+  const cx<T> id = invd[(int64_t)st[slot].tau * L.n + c];
+  z[slot * vs + c] = gs_value(L, Cell{i, j, k}, c, id, f + slot * vs, z + slot * vs, zero_start);
 }
 
 // The last half sweep of the finest level's post-smoothing fused with the
@@ -201,15 +214,15 @@ __global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restric
 // updates the one of colour `color` as k_gs does, and adds both final values
 // e to column k - 1 of the outer iterates (z_k = e on the first cycle, z_k + e
 // after), the update of k_correct. z itself is not written: nothing reads the
-// finest level's correction after this.
+// finest level's correction after this. Sources as in k_gs.
 template <typename T>
 __global__ void k_gs_correct(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
                              const cx<T>* __restrict__ f, const cx<T>* __restrict__ z, int64_t vs, int color,
-                             z64* __restrict__ Zk, int64_t vsZk, int64_t zcol) {
-  const int slot = blockIdx.z;
-  if (!slot_running(st, slot)) return;
+                             z64* __restrict__ Zk, int64_t vsZk, int64_t zcol, int nslot) {
+  const int slot = blockIdx.z * blockDim.z + threadIdx.z;
+  if (slot >= nslot || !slot_running(st, slot)) return;
   const int ii = blockIdx.x * GX + threadIdx.x;
-  const int row = blockIdx.y * GY + threadIdx.y;
+  const int row = blockIdx.y * blockDim.y + threadIdx.y;
   if (row >= L.ny * L.nz || 2 * ii >= L.nx) return;
   const int k = row / L.ny, j = row - k * L.ny;
   const cx<T>* zs = z + slot * vs;
@@ -233,18 +246,21 @@ __global__ void k_gs_correct(LevelView<T> L, const SlotState* st, const cx<T>* _
 
 // --------------------------------------------------------------------- transfer
 // Coarse right-hand side = sum over the children of the fine residual f - A z.
+// Sources as in k_gs (threadIdx.z), so the children's coefficients come from
+// memory once per block.
 template <typename T>
 __global__ void k_residual_restrict(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz,
                                     const SlotState* st, const z64* taus, const cx<T>* __restrict__ f,
-                                    const cx<T>* __restrict__ z, int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
-  int slot = blockIdx.z;
-  if (!slot_running(st, slot)) return;
-  Cell pc;
-  int C;
-  if (!grid_cell(cnx, cny, cnz, &pc, &C)) return;
-  int I = pc.i, J = pc.j, K = pc.k;
-  cx<T> s = cvt<T>(taus[st[slot].tau]);
-  fc[slot * vsc + C] = restrict_value(F, rx, ry, rz, I, J, K, s, f + slot * vs, z + slot * vs);
+                                    const cx<T>* __restrict__ z, int64_t vs, cx<T>* __restrict__ fc, int64_t vsc,
+                                    int nslot) {
+  const int slot = blockIdx.z * blockDim.z + threadIdx.z;
+  if (slot >= nslot || !slot_running(st, slot)) return;
+  const int I = blockIdx.x * GX + threadIdx.x;
+  const int row = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= cnx || row >= cny * cnz) return;
+  const int K = row / cny, J = row - K * cny;
+  const cx<T> s = cvt<T>(taus[st[slot].tau]);
+  fc[slot * vsc + (int64_t)row * cnx + I] = restrict_value(F, rx, ry, rz, I, J, K, s, f + slot * vs, z + slot * vs);
 }
 
 // z_fine += P z_coarse
@@ -259,6 +275,44 @@ __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, i
   if (!grid_cell(F.nx, F.ny, F.nz, &p, &c)) return;
   cx<T>* zs = z + slot * vs;
   zs[c] = zs[c] + prolong_value(p, rx, ry, rz, cnx, cny, cnz, mask, zc + slot * vsc);
+}
+
+// z_fine += P z_coarse on a 3D level coarsened by 2 in every axis: a block
+// updates 32 x 8 cells of one plane and first stages the 18 x 6 x 2 coarse
+// values they interpolate from (their parents' plane and the neighbouring
+// coarse plane on the child's side) in shared memory, so each coarse value is
+// read once per block instead of once per fine cell; the interpolation itself
+// is prolong_value_at's, on those values.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add3(LevelView<T> F, int cnx, int cny, int cnz, uint32_t mask,
+                                                      const SlotState* st, const cx<T>* __restrict__ zc,
+                                                      int64_t vsc, cx<T>* __restrict__ z, int64_t vs) {
+  constexpr int SX = GX / 2 + 2, SY = GY / 2 + 2;
+  __shared__ cx<T> sc[2][SY][SX];
+  const int slot = blockIdx.z;
+  if (!slot_running(st, slot)) return;
+  const int nby = (F.ny + GY - 1) / GY;
+  const int k = blockIdx.y / nby, by = blockIdx.y - k * nby;
+  const int x0 = blockIdx.x * GX, y0 = by * GY;
+  const int X0 = x0 / 2 - 1, Y0 = y0 / 2 - 1;
+  const int K = k >> 1, K2 = (k & 1) ? K + 1 : K - 1;
+  const cx<T>* zcs = zc + slot * vsc;
+  const int t = threadIdx.y * GX + threadIdx.x;
+  if (t < 2 * SY * SX) {
+    const int q = t / (SY * SX), rem = t - q * (SY * SX);
+    const int yy = rem / SX, xx = rem - yy * SX;
+    const int X = X0 + xx, Y = Y0 + yy, Z = q == 0 ? K : K2;
+    const bool in = X >= 0 && X < cnx && Y >= 0 && Y < cny && Z >= 0 && Z < cnz;
+    sc[q][yy][xx] = in ? zcs[((int64_t)Z * cny + Y) * cnx + X] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+  if (i >= F.nx || j >= F.ny) return;
+  const int64_t c = ((int64_t)k * F.ny + j) * F.nx + i;
+  cx<T>* zs = z + slot * vs;
+  zs[c] = zs[c] + prolong_value_at<T>(Cell{i, j, k}, 2, 2, 2, cnx, cny, cnz, mask, [&](int X, int Y, int Z) {
+            return sc[Z == K ? 0 : 1][Y - Y0][X - X0];
+          });
 }
 
 // --------------------------------------------------------------------- fused 2D level kernels
@@ -1139,29 +1193,44 @@ void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* 
   k_apply<T><<<grid2(L.nx, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), sfix, st, taus, x, y, vs);
 }
 
+// Sources per block of the multi-source smoother and restriction: a power of
+// two up to 8 (blockDim = (32, 8 / G, G)).
+static int spmm_group(int nslot) {
+  int g = 1;
+  while (g < 8 && 2 * g <= nslot) g *= 2;
+  return g;
+}
+
 template <typename T>
 void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
                int nslot, int color, int zero_start, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
+  const int G = spmm_group(nslot), rb = GY / G;
+  const dim3 blk(GX, rb, G), grd(nb((L.nx + 1) / 2, GX), nb((int64_t)L.ny * L.nz, rb), nb(nslot, G));
   if (Zk) {
-    k_gs_correct<T><<<grid2((L.nx + 1) / 2, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), st, invd, f, z, vs,
-                                                                                    color, Zk, vsZk, zcol);
+    k_gs_correct<T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, Zk, vsZk, zcol, nslot);
     return;
   }
-  k_gs<T><<<grid2((L.nx + 1) / 2, (int64_t)L.ny * L.nz, nslot), B2, 0, s>>>(view<T>(L), st, invd, f, z, vs, color,
-                                                                          zero_start);
+  k_gs<T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, zero_start, nslot);
 }
 
 template <typename T>
 void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
                               const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
                               cudaStream_t s) {
-  k_residual_restrict<T><<<grid2(C.nx, (int64_t)C.ny * C.nz, nslot), B2, 0, s>>>(
-      view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc, vsc);
+  const int G = spmm_group(nslot), rb = GY / G;
+  const dim3 blk(GX, rb, G), grd(nb(C.nx, GX), nb((int64_t)C.ny * C.nz, rb), nb(nslot, G));
+  k_residual_restrict<T><<<grd, blk, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
+                                             vsc, nslot);
 }
 
 template <typename T>
 void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* zc,
                         int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s) {
+  if (F.nz > 1 && F.rx == 2 && F.ry == 2 && F.rz == 2 && (int64_t)nb(F.ny, GY) * F.nz <= 65535) {
+    const dim3 g(nb(F.nx, GX), nb(F.ny, GY) * F.nz, nslot);
+    k_prolong_add3<T><<<g, B2, 0, s>>>(view<T>(F), C.nx, C.ny, C.nz, mask, st, zc, vsc, z, vs);
+    return;
+  }
   k_prolong_add<T><<<grid2(F.nx, (int64_t)F.ny * F.nz, nslot), B2, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny,
                                                                             C.nz, mask, st, zc, vsc, z, vs);
 }

@@ -385,3 +385,25 @@ def test_relaxed_inner_tolerance_replay_parity():
     for j in range(len(pr.sigma)):
         assert rel_err(out.X[0, j], ref.x[:, j]) <= 1e-8, j
     s.close()
+
+
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_replay_parity_beyond_64_steps(precision):
+    """A solve of 82 Arnoldi steps (tolerance 1e-10, one tau at the geometric
+    mean of a 1 s to 10 h period range): the source takes more steps than the
+    tensor-core assembly's exactness bound allows (64), so its x_j = Z y_j come
+    from the FP64 assembly kernel; every x_j to 1e-8 (complex128 cycles) or
+    1e-6 (complex64 cycles) of the oracle's."""
+    need_gpu()
+    pr = synth.make_problem((32, 32), n_f=12, periods=(1.0, 36000.0), n_p=1, seed=51, m_max=100, tol=1e-10)
+    eps = 1e-12
+    op, ref = oracle_run(pr, eps)
+    assert ref.steps > 64
+    rc, mj = replay_arrays(pr, [ref])
+    s = Solver(pr)
+    out = s.solve(inner_tol=eps, precision=precision, replay_cycles=rc, replay_mj=mj)
+    assert np.array_equal(out.m_j[0], ref.m_j) and int(out.steps[0]) == ref.steps
+    tol = 1e-8 if precision == fks.FKS_PREC_FP64 else 1e-6
+    for j in range(len(pr.sigma)):
+        assert rel_err(out.X[0, j], ref.x[:, j]) <= tol, j
+    s.close()
