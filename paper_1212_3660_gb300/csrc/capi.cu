@@ -324,6 +324,7 @@ struct Solve {
   SlotState* st;
   SlotState* st_host;  // pinned mirror
   z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
+  z32* V32 = nullptr;  // complex64 copy of the basis (mixed precision), or null
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
   double* alpha;   // Prop. 3's alpha per (source, shift) at its freeze step
   double* tolv;    // per-shift tolerances of a restart cycle (used when tolv_on)
@@ -882,8 +883,12 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
   // CGS2: two projections; pass p writes its coefficients to h12[slot][p]
   for (int pass = 0; pass < 2; ++pass) {
     z64* hp = S.h12 + pass * MAX_M;
-    PROF(FKS_K_MDOT, -1, ns * 16 * nn * (kk + 1), ns * 8 * nn * kk,
-         launch_mdot(S.st, S.V, vsV, S.w, n, S.mdpart, kmax, n_rhs, S.s));
+    if (pass == 0 && S.V32)
+      PROF(FKS_K_MDOT, -1, ns * (8 * nn * kk + 16 * nn), ns * 8 * nn * kk,
+           launch_mdot32(S.st, S.V32, vsV, S.w, n, S.mdpart, kmax, n_rhs, S.s));
+    else
+      PROF(FKS_K_MDOT, -1, ns * 16 * nn * (kk + 1), ns * 8 * nn * kk,
+           launch_mdot(S.st, S.V, vsV, S.w, n, S.mdpart, kmax, n_rhs, S.s));
     PROF(-1, -1, 0, 0, launch_hreduce(S.st, S.mdpart, n, hp, 2 * MAX_M, n_rhs, S.s));
     PROF(FKS_K_MAXPY, -1, ns * 16 * nn * (kk + 2), ns * 8 * nn * kk,
          launch_maxpy(S.st, S.V, vsV, hp, 2 * MAX_M, S.w, n, n_rhs, S.s));
@@ -892,7 +897,7 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
   PROF(-1, -1, 0, 0,
        launch_arnoldi_finish(S.st, n_rhs, S.h12, S.wpart, S.mpart, norm_blocks(n), S.H, m, S.pn, S.cyc,
                              BREAKDOWN_RTOL, S.s));
-  PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, S.s));
+  PROF(-1, -1, 0, 0, launch_new_v(S.st, S.w, n, S.H, m, S.V, vsV, n_rhs, S.s, S.V32));
   PROF(FKS_K_GIVENS, -1, ns * n_f * 48.0 * kk, ns * n_f * 26.0 * kk,
        launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant, S.replay ? S.rep_mj : nullptr,
                      S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, S.alpha, n_rhs, S.s,
@@ -1053,6 +1058,8 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.rep_cyc = A.take<int32_t>((size_t)ns * m);
   S.rep_mj = A.take<int32_t>((size_t)ns * nf);
   S.V = A.take<z64>((size_t)ns * (m + 1) * n);
+  // complex64 copy of the basis for the first CGS projection (mixed precision)
+  S.V32 = S.precision == FKS_PREC_MIXED ? A.take<z32>((size_t)ns * (m + 1) * n) : nullptr;
   S.Z = A.take<z64>((size_t)ns * m * n);
   S.w = A.take<z64>((size_t)ns * n);
   S.ndef = defect_partials(S.op);
@@ -1210,7 +1217,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   int nbn = norm_blocks(n);
   PROF(-1, -1, 0, 0, launch_norm2_partial(S.st, 0, S.b, n, n, S.npart, n_rhs, s));
   PROF(-1, -1, 0, 0, launch_start(S.st, n_rhs, S.npart, nbn, n_f, s));
-  PROF(-1, -1, 0, 0, launch_init_v1(S.st, S.b, n, S.V, (m + 1) * n, n_rhs, s));
+  PROF(-1, -1, 0, 0, launch_init_v1(S.st, S.b, n, S.V, (m + 1) * n, n_rhs, s, S.V32));
   PROF(-1, -1, 0, 0, launch_init_shifts(S.st, n_f, m, S.sst, S.mj, S.est, S.bnd, S.Y, S.alpha, n_rhs, s));
   CK(cudaMemsetAsync(S.pn, 0, sizeof(double) * m * n_rhs, s));
   CK(cudaMemsetAsync(S.cyc, 0, sizeof(int32_t) * m * n_rhs, s));
@@ -1615,6 +1622,7 @@ static fks_status solve_chunked(fks_op* op, Lane* lane, const fks_c128* b, int n
     S.n_tau = n_tau;
     S.m = o->m_max;
     S.sched_len = o->sched_len;
+    S.precision = o->precision;
     S.n = op->n;
     Arena probe;
     carve<VT>(S, probe, !x_dev);
@@ -2813,6 +2821,7 @@ static size_t request_bytes(const fks_request& r, int n_rhs) {
   S.n_tau = r.n_tau;
   S.m = r.opt.m_max;
   S.sched_len = r.opt.sched_len;
+  S.precision = r.opt.precision;
   S.n = r.op->n;
   Arena probe;
   carve<VT>(S, probe, true);

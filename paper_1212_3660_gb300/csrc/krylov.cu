@@ -65,13 +65,14 @@ __global__ void k_start(SlotState* st, int nslot, const double* __restrict__ par
 
 // v_1 = b / beta; shift bookkeeping reset (status LIVE, g_1 = beta, Y = 0).
 __global__ void k_init_v1(const SlotState* st, const z64* __restrict__ b, int64_t n, z64* __restrict__ V,
-                          int64_t vsV) {
+                          int64_t vsV, z32* __restrict__ V32) {
   int slot = blockIdx.y;
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= n) return;
   double beta = st[slot].beta;
   z64 v = beta > 0.0 ? (1.0 / beta) * b[slot * n + c] : mk(0.0, 0.0);
   V[slot * vsV + c] = v;
+  if (V32) V32[slot * vsV + c] = cvt<float>(v);
 }
 
 __global__ void k_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_t* mj, double* est,
@@ -173,6 +174,58 @@ __global__ void __launch_bounds__(MD_THREADS) k_mdot(const SlotState* st, const 
   }
 }
 
+// The first CGS projection of the mixed-precision solve: the partial sums of
+// h_i = v_i^* w as k_mdot forms them, from the complex64 copy of the basis and
+// w rounded to complex64, accumulated in fp32 (written as complex128 partials,
+// summed by k_hreduce). Its error (about 1e-7 ||w||) is removed by the second,
+// complex128 projection; both updates w -= V h stay complex128, so the Arnoldi
+// relation M z_k = V_{k+1} h holds to complex128 rounding with h = h1 + h2.
+__global__ void __launch_bounds__(MD_THREADS) k_mdot32(const SlotState* st, const z32* __restrict__ V, int64_t vsV,
+                                                       const z64* __restrict__ w, int64_t n,
+                                                       z64* __restrict__ partial) {
+  int slot = blockIdx.y;
+  if (!st[slot].active) return;
+  int k = st[slot].k;
+  int c0 = blockIdx.z * MD_COLS;
+  if (c0 >= k) return;
+  int c1 = min(k, c0 + MD_COLS);
+  __shared__ z32 red[MD_THREADS / 32][MD_COLS];
+  int64_t row0 = (int64_t)blockIdx.x * MD_THREADS * MD_ROWS + threadIdx.x;
+  z32 wr[MD_ROWS];
+#pragma unroll
+  for (int r = 0; r < MD_ROWS; ++r) {
+    int64_t row = row0 + (int64_t)r * MD_THREADS;
+    wr[r] = row < n ? cvt<float>(w[slot * n + row]) : mk(0.f, 0.f);
+  }
+  const z32* Vs = V + slot * vsV;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = c0; c < c1; ++c) {
+    const z32* col = Vs + (int64_t)c * n;
+    z32 acc = mk(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < MD_ROWS; ++r) {
+      int64_t row = row0 + (int64_t)r * MD_THREADS;
+      if (row < n) {
+        const z32 a = col[row], b = wr[r];
+        acc.re = fmaT(a.re, b.re, fmaT(a.im, b.im, acc.re));
+        acc.im = fmaT(a.re, b.im, fmaT(-a.im, b.re, acc.im));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_down_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) red[warp][c - c0] = acc;
+  }
+  __syncthreads();
+  int t = threadIdx.x;
+  if (t < c1 - c0) {
+    z32 s = mk(0.f, 0.f);
+    for (int q = 0; q < MD_THREADS / 32; ++q) s = s + red[q][t];
+    partial[((int64_t)slot * gridDim.x + blockIdx.x) * MAX_M + c0 + t] = cvt<double>(s);
+  }
+}
+
 // h[i] = sum over row blocks of the partials (fixed order), i < k.
 __global__ void k_hreduce(const SlotState* st, const z64* __restrict__ partial, int nblocks, z64* __restrict__ h,
                           int64_t hstride) {
@@ -241,8 +294,10 @@ __global__ void k_arnoldi_finish(SlotState* st, int nslot, const z64* __restrict
 }
 
 // v_{k+1} = w / h_{k+1,k}
+// v_{k+1} = w / h_{k+1,k}; with V32 also its complex64 copy (the first CGS
+// projection of the mixed-precision solve reads it)
 __global__ void k_new_v(const SlotState* st, const z64* __restrict__ w, int64_t n, const z64* __restrict__ H, int m,
-                        z64* __restrict__ V, int64_t vsV) {
+                        z64* __restrict__ V, int64_t vsV, z32* __restrict__ V32) {
   int slot = blockIdx.y;
   const SlotState& s = st[slot];
   if (!s.active || s.breakdown) return;
@@ -250,7 +305,9 @@ __global__ void k_new_v(const SlotState* st, const z64* __restrict__ w, int64_t 
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= n) return;
   double hn = H[(int64_t)slot * (m + 1) * m + (int64_t)(k - 1) * (m + 1) + k].re;
-  V[slot * vsV + (int64_t)k * n + c] = (1.0 / hn) * w[slot * n + c];
+  const z64 v = (1.0 / hn) * w[slot * n + c];
+  V[slot * vsV + (int64_t)k * n + c] = v;
+  if (V32) V32[slot * vsV + (int64_t)k * n + c] = cvt<float>(v);
 }
 
 __device__ __forceinline__ z64 cdiv(z64 a, z64 b) {
@@ -531,9 +588,10 @@ void launch_norm2_partial(const SlotState* st, int need_active, const z64* x, in
 void launch_start(SlotState* st, int nslot, const double* partial, int nblocks, int nf, cudaStream_t s) {
   k_start<<<nslot, 512, 0, s>>>(st, nslot, partial, nblocks, nf);
 }
-void launch_init_v1(const SlotState* st, const z64* b, int64_t n, z64* V, int64_t vsV, int nslot, cudaStream_t s) {
+void launch_init_v1(const SlotState* st, const z64* b, int64_t n, z64* V, int64_t vsV, int nslot, cudaStream_t s,
+                    z32* V32) {
   dim3 g(nbk(n, 256), nslot);
-  k_init_v1<<<g, 256, 0, s>>>(st, b, n, V, vsV);
+  k_init_v1<<<g, 256, 0, s>>>(st, b, n, V, vsV, V32);
 }
 void launch_init_shifts(const SlotState* st, int nf, int m, int32_t* sst, int32_t* mj, double* est, double* bnd,
                         z64* Y, double* alpha, int nslot, cudaStream_t s) {
@@ -555,6 +613,11 @@ void launch_mdot(const SlotState* st, const z64* V, int64_t vsV, const z64* w, i
   dim3 g(mdot_blocks(n), nslot, nbk(kmax, MD_COLS));
   k_mdot<<<g, MD_THREADS, 0, s>>>(st, V, vsV, w, n, partial);
 }
+void launch_mdot32(const SlotState* st, const z32* V, int64_t vsV, const z64* w, int64_t n, z64* partial, int kmax,
+                   int nslot, cudaStream_t s) {
+  dim3 g(mdot_blocks(n), nslot, nbk(kmax, MD_COLS));
+  k_mdot32<<<g, MD_THREADS, 0, s>>>(st, V, vsV, w, n, partial);
+}
 void launch_hreduce(const SlotState* st, const z64* partial, int64_t n, z64* h, int64_t hstride, int nslot,
                     cudaStream_t s) {
   k_hreduce<<<nslot, 1024, 0, s>>>(st, partial, mdot_blocks(n), h, hstride);
@@ -569,9 +632,9 @@ void launch_arnoldi_finish(SlotState* st, int nslot, const z64* h12, const doubl
   k_arnoldi_finish<<<nslot, 512, 0, s>>>(st, nslot, h12, wpart, mpart, nblocks, H, m, pn, cyc, rtol);
 }
 void launch_new_v(const SlotState* st, const z64* w, int64_t n, const z64* H, int m, z64* V, int64_t vsV, int nslot,
-                  cudaStream_t s) {
+                  cudaStream_t s, z32* V32) {
   dim3 g(nbk(n, 256), nslot);
-  k_new_v<<<g, 256, 0, s>>>(st, w, n, H, m, V, vsV);
+  k_new_v<<<g, 256, 0, s>>>(st, w, n, H, m, V, vsV, V32);
 }
 void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H, const z64* taus_k, const double* pn,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
