@@ -319,15 +319,24 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
                              double* out_pnorm, void* stream);
 
 /*
- * Serving (no counterpart in the paper): a request loop over fks_solve.
- * Worker threads, each with its own stream and workspace ("lane"), admit queued
- * requests while the device-memory budget allows; requests that share the
- * operator, the shifts and the options are merged into one batch whose slots
- * are their sources; batches on different lanes overlap on the device. Each
- * request's result equals what fks_solve gives it alone. All request arrays are
- * HOST memory owned by the caller and must stay valid until the request is done;
- * options' tau_schedule is copied at submit. Replay mode is not accepted.
- * The server is thread-safe.
+ * Serving (no counterpart in the paper): a request loop over the solver with
+ * continuous (iteration-level) batching. One driver thread issues all of the
+ * server's CUDA calls; each lane (own stream, workspace and step-loop graph)
+ * runs a batch started for the first queued request that fits the
+ * device-memory budget, with spare slots (one slot per source)
+ * for later requests that share its operator, shifts, taus and options. The
+ * batch's step loop runs one Arnoldi step per launch; between launches the
+ * worker admits queued compatible requests into free slots (their sources
+ * start at step 1 while the others go on), stops cancelled or timed-out
+ * requests, and delivers every source that has finished (assembly, true
+ * residual, copies into the request's arrays) as soon as it finishes.
+ * Batches on different lanes overlap on the device. Each request's result
+ * equals what fks_solve gives it alone. All request arrays are HOST memory
+ * owned by the caller and must stay valid until the request is done; X may be
+ * NULL (the residuals and statuses are still delivered); options'
+ * tau_schedule is copied at submit. Replay mode is not accepted. The server is
+ * thread-safe. A workspace that cannot be allocated ends the requests of that
+ * batch with FKS_ERR_OOM and releases their slots and budget.
  */
 typedef struct fks_server fks_server;
 typedef struct {
@@ -340,6 +349,8 @@ typedef struct {
   double* res_est; double* res_bound;    /* [n_f * n_rhs] out                                   */
   double* res_true;                      /* [n_f * n_rhs] out or NULL                           */
   int32_t* m_j; int32_t* shift_status;   /* [n_f * n_rhs] out                                   */
+  double timeout_s;                      /* > 0: stop with FKS_ERR_TIMEOUT once the request has run
+                                            this long (checked between Arnoldi steps); 0: none      */
 } fks_request;
 /* lanes: concurrent batches (1..64); mem_budget_bytes: device memory the
  * admitted batches' workspaces may use together (one oversized request still
@@ -351,12 +362,21 @@ fks_status fks_server_submit(fks_server* srv, const fks_request* req, uint64_t* 
 /* done = 1 when finished or cancelled; result = the request's status. */
 fks_status fks_server_poll(fks_server* srv, uint64_t ticket, int* done, fks_status* result);
 fks_status fks_server_wait(fks_server* srv, uint64_t ticket, fks_status* result);
-/* Cancels a request that has not started (FKS_ERR_ARG otherwise); its result is FKS_ERR_CANCELLED. */
+/* Cancels a request: a queued one at once, a running one at its batch's next
+ * Arnoldi-step boundary (its sources take no further step and deliver nothing).
+ * Its result is FKS_ERR_CANCELLED. FKS_ERR_ARG if it already finished. */
 fks_status fks_server_cancel(fks_server* srv, uint64_t ticket);
 /* Host wall-clock seconds (steady clock) of submit, start and end of a request. */
 fks_status fks_server_times(fks_server* srv, uint64_t ticket, double* submit_s, double* start_s, double* end_s);
 /* Kernel launches made by the server's lanes since it was created. */
 fks_status fks_server_launches(fks_server* srv, int64_t* launches);
+/*
+ * Test hook (no counterpart in the paper): the next `count` workspace
+ * reservations of any solve or server batch fail as cudaMalloc does when the
+ * device is out of memory (FKS_ERR_OOM), so that failure handling can be tested
+ * without exhausting a GPU. count = 0 clears it.
+ */
+void fks_debug_fail_allocs(int count);
 /* Stops the workers after their current batches; queued requests are dropped. */
 void fks_server_destroy(fks_server* srv);
 

@@ -6,6 +6,7 @@
 // correction in complex128. All per-step state lives in device memory; the
 // host only enqueues kernels and reads small flags to decide when a loop ends.
 #include <algorithm>
+#include <atomic>
 #include <limits>
 #include <complex>
 #include <climits>
@@ -39,7 +40,6 @@ static thread_local std::string g_err;
 // across threads (the server builds graphs from several worker threads).
 static std::mutex g_build_mu;
 // Serialises the host-side CUDA calls of concurrent server batches.
-static std::mutex g_api_mu;
 void set_error(const std::string& msg) { g_err = msg; }
 const char* get_error() { return g_err.c_str(); }
 
@@ -51,6 +51,10 @@ struct CudaError {
   cudaError_t e;
   const char* where;
 };
+
+// Test hook (fks_debug_fail_allocs): the next this-many workspace reservations
+// fail as cudaMalloc would when the device is out of memory.
+static std::atomic<int> g_fail_allocs{0};
 
 #define CK(x)                                            \
   do {                                                   \
@@ -66,6 +70,8 @@ struct Arena {
   cudaStream_t astream = nullptr;  // stream-ordered allocation on this stream when set
   void reserve(size_t bytes) {
     if (bytes <= cap) return;
+    if (g_fail_allocs.load() > 0 && g_fail_allocs.fetch_sub(1) > 0)
+      throw CudaError{cudaErrorMemoryAllocation, "cudaMalloc(workspace) (injected failure)"};
     if (base) {
       if (astream) cudaFreeAsync(base, astream); else cudaFree(base);
     }
@@ -325,6 +331,12 @@ struct Solve {
   SlotState* st_host;  // pinned mirror
   z64 *b, *sigma, *taus, *V, *Z, *w, *H, *taus_k, *h12, *mdpart, *g, *rs, *R, *Y, *X;
   z32* V32 = nullptr;  // complex64 copy of the basis (mixed precision), or null
+  // continuous batching (server): steps left in a launch of the step loop, and
+  // per-slot stop flags; null for fks_solve
+  bool batching = false;
+  int32_t* budget = nullptr;
+  int32_t* stopv = nullptr;
+  int32_t* tcerr = nullptr;  // the tensor-core assembly's error flag of a server batch
   double *pn, *rc, *est, *bnd, *dpart, *npart, *mpart, *wpart, *tpart, *tres;
   double* alpha;   // Prop. 3's alpha per (source, shift) at its freeze step
   double* tolv;    // per-shift tolerances of a restart cycle (used when tolv_on)
@@ -902,7 +914,7 @@ static void sec_step_end(Solve& S, int step, int use_cond, cudaGraphConditionalH
        launch_givens(S.st, n_f, m, S.sigma, S.H, S.taus_k, S.pn, S.tol, S.variant, S.replay ? S.rep_mj : nullptr,
                      S.g, S.rc, S.rs, S.R, S.Y, S.sst, S.mj, S.est, S.bnd, S.alpha, n_rhs, S.s,
                      S.tolv_on ? S.tolv : nullptr, S.tolv_on ? S.rcoef : nullptr));
-  PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, use_cond, hout, S.s));
+  PROF(-1, -1, 0, 0, launch_step_end(S.st, n_rhs, m, use_cond, hout, S.s, S.budget));
 }
 
 // The loop over Arnoldi steps as one graph: outer WHILE (some source active) {
@@ -1136,6 +1148,9 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.tpart = A.take<double>((size_t)ns * nf * (S.op->csr ? csr_blocks(n) : tres_blocks(Ls[0])));
   S.tres = A.take<double>((size_t)ns * nf);
   S.X = x_internal ? A.take<z64>((size_t)ns * nf * n) : nullptr;
+  S.budget = S.batching ? A.take<int32_t>(1) : nullptr;
+  S.stopv = S.batching ? A.take<int32_t>(ns) : nullptr;
+  S.tcerr = S.batching ? A.take<int32_t>(1) : nullptr;
 }
 
 // Outputs of a run of consecutive slots [r0, r0 + nr) that belong to one
@@ -1236,7 +1251,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)op->tile16_max[1], S.relax, (double)op->tail_max[0],
                                  (double)op->tail_max[1], (double)op->cluster_max[0], (double)op->cluster_max[1],
                                  (double)op->tile8_max[0], (double)op->tile8_max[1], (double)S.tolv_on,
-                                 (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L};
+                                 (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L, (double)S.batching};
       for (int pz = 0; pz < 2; ++pz)
         for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
       if (!lane->graph || lane->graph_key != key) {
@@ -2770,6 +2785,8 @@ struct Request {
   fks_status result = FKS_OK;
   double t_submit = 0, t_start = 0, t_end = 0;
   size_t est = 0;
+  bool cancel = false;   // fks_server_cancel while running: stop at the next step boundary
+  int sources_left = 0;  // sources not yet delivered
 };
 
 static double now_s() {
@@ -2799,6 +2816,9 @@ struct fks_server {
   fks_ctx* ctx = nullptr;
   size_t budget = 0, in_use = 0;
   int max_batch = 64;
+  int join_slots = 16;           // spare slots a batch reserves for requests that join it later
+  int steps_per_launch = 1;      // Arnoldi steps between admissions
+  std::atomic<int64_t> launches{0};
   std::mutex mu;
   std::condition_variable cv, done_cv;
   std::deque<std::shared_ptr<fks::Request>> queue;
@@ -2823,116 +2843,435 @@ static size_t request_bytes(const fks_request& r, int n_rhs) {
   S.sched_len = r.opt.sched_len;
   S.precision = r.opt.precision;
   S.n = r.op->n;
+  S.batching = true;
   Arena probe;
   carve<VT>(S, probe, true);
-  return probe.off + 4096;
+  // the tensor-core assembly's slices of one source (delivered one at a time)
+  const int kmax = std::min(r.opt.m_max, TC_MAX_KP / 2);
+  const size_t tc = r.opt.assembly == 0 && tc_supported(kmax, S.n) ? tc_ws_bytes(tc_layout(S.n, r.n_f, kmax, 1)) : 0;
+  return probe.off + tc + 4096;
 }
 
-static void run_batch(fks_server* sv, int lane_id, std::vector<std::shared_ptr<Request>>& batch) {
-  Lane* lane = sv->lanes[lane_id].get();
-  cudaStream_t s = sv->streams[lane_id];
-  const fks_request& r0 = batch[0]->req;
-  int64_t n = r0.op->n;
-  int n_total = 0;
-  for (auto& q : batch) n_total += q->req.n_rhs;
-  std::vector<fks_c128> bcat((size_t)n * n_total);
-  std::vector<OutGroup> groups;
-  int at = 0;
-  for (auto& q : batch) {
-    std::memcpy(bcat.data() + (size_t)at * n, q->req.b, sizeof(fks_c128) * n * q->req.n_rhs);
-    groups.push_back(OutGroup{at, q->req.n_rhs, q->req.X, q->req.res_est, q->req.res_bound, q->req.res_true,
-                              q->req.m_j, q->req.shift_status});
-    at += q->req.n_rhs;
+// Free run of `cnt` consecutive slots in `use`, or -1.
+struct SlotUse {
+  std::shared_ptr<Request> q;
+  int r = 0;          // the request's source in this slot
+  bool done = false;  // delivered
+};
+
+static int free_run(const std::vector<SlotUse>& use, int cnt) {
+  int run = 0;
+  for (int i = 0; i < (int)use.size(); ++i) {
+    run = use[i].q ? 0 : run + 1;
+    if (run == cnt) return i - cnt + 1;
   }
-  fks_options o = r0.opt;
-  o.tau_schedule = batch[0]->sched.data();
-  o.launch_mode = 0;
-  fks_status st;
-  std::unique_lock<std::mutex> api(g_api_mu);
-  try {
-    CK(cudaSetDevice(sv->ctx->device));
-    if (o.precision == FKS_PREC_FP64)
-      st = solve_impl<double>(r0.op, lane, bcat.data(), n_total, batch[0]->sigma.data(), r0.n_f,
-                              batch[0]->tau.data(), r0.n_tau, &o, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                              nullptr, s, &groups, &api);
-    else
-      st = solve_impl<float>(r0.op, lane, bcat.data(), n_total, batch[0]->sigma.data(), r0.n_f,
-                             batch[0]->tau.data(), r0.n_tau, &o, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, s, &groups, &api);
-  } catch (CudaError& e) {
-    set_error(std::string("fks_server: ") + e.where + ": " + cudaGetErrorString(e.e));
-    st = e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA;
-  }
-  // per-request status from its own shifts
-  for (auto& q : batch) {
-    if (st < 0) {
-      q->result = st;
-      continue;
-    }
-    fks_status rs = FKS_OK;
-    for (int j = 0; j < q->req.n_f * q->req.n_rhs; ++j) {
-      int32_t v = q->req.shift_status[j];
-      if (v == 1 || v == -1) rs = FKS_NOT_CONVERGED;
-      else if (v == 2 && rs == FKS_OK) rs = FKS_BREAKDOWN_EXACT;
-    }
-    q->result = rs;
-  }
+  return -1;
 }
 
-static void worker_loop(fks_server* sv, int lane_id) {
-  cudaSetDevice(sv->ctx->device);
-  while (true) {
-    std::vector<std::shared_ptr<Request>> batch;
-    size_t est = 0;
+// One slot's outputs: x_j = Z y_j (tensor cores, or FP64 beyond their bound),
+// the true residuals, and the copies into the request's own arrays for its
+// source u.r. Each source is assembled and checked alone, exactly as fks_solve
+// does it (its own step count decides the kernel), so its results do not depend
+// on the batch it ran in.
+template <typename VT>
+static void deliver_slot(Solve& S, Lane* lane, int sl, const SlotUse& u, cudaStream_t s, int* tc_err) {
+  const int64_t n = S.n;
+  const int nf = S.n_f, m = S.m;
+  const int k = S.st_host[sl].k;
+  const int64_t vsZ = (int64_t)m * n;
+  z64* Xs = S.X + (size_t)sl * nf * n;
+  const fks_request& R = u.q->req;
+  if (R.opt.assembly == 0 && k >= 1 && tc_supported(k, n)) {
+    TcLayout T = tc_layout(n, nf, k, 1);
+    const size_t need = tc_ws_bytes(T);
+    lane->tcws.reserve(need + 256);
     {
-      std::unique_lock<std::mutex> lk(sv->mu);
-      while (true) {
-        if (sv->stop) return;
-        // first queued request that fits the free budget (a request larger than
-        // the whole budget runs when nothing else is in flight)
+      std::lock_guard<std::mutex> build_lock(g_build_mu);
+      tc_prepare();
+    }
+    lane->prof.all_launches += launch_tc_assemble(T, S.st + sl, S.Z + (size_t)sl * vsZ, vsZ, S.Y + (size_t)sl * nf * m,
+                                                  S.mj + (size_t)sl * nf, nf, m, Xs, n, 1, lane->tcws.base, tc_err, s);
+  } else {
+    launch_assemble(S.Z + (size_t)sl * vsZ, vsZ, S.Y + (size_t)sl * nf * m, S.mj + (size_t)sl * nf, nf, m, Xs, n, 1, s);
+    lane->prof.all_launches += 1;
+  }
+  const fks_op* op = S.op;
+  const int nb = op->csr ? csr_blocks(n) : tres_blocks(op->levels[0]);
+  if (op->csr)
+    launch_csr_true_residual(op->cd.view<double>(n), S.sigma, nf, S.b + (size_t)sl * n, Xs,
+                             S.tpart + (size_t)sl * nf * nb, S.st + sl, S.tres + (size_t)sl * nf, 1, s);
+  else
+    launch_true_residual(op->levels[0], S.sigma, nf, S.b + (size_t)sl * n, Xs, S.tpart + (size_t)sl * nf * nb,
+                         S.st + sl, S.tres + (size_t)sl * nf, 1, s);
+  lane->prof.all_launches += 2;
+  const size_t o = (size_t)u.r * nf, so = (size_t)sl * nf;
+  if (R.X) copy_out(R.X + o * n, Xs, sizeof(z64) * n * nf, s);
+  copy_out(R.res_est + o, S.est + so, sizeof(double) * nf, s);
+  copy_out(R.res_bound + o, S.bnd + so, sizeof(double) * nf, s);
+  if (R.res_true) copy_out(R.res_true + o, S.tres + so, sizeof(double) * nf, s);
+  copy_out(R.m_j + o, S.mj + so, sizeof(int32_t) * nf, s);
+  copy_out(R.shift_status + o, S.sst + so, sizeof(int32_t) * nf, s);
+}
+
+// Request status from its delivered shifts (after the copies completed).
+static fks_status request_status(const Request& q) {
+  fks_status rs = FKS_OK;
+  for (int j = 0; j < q.req.n_f * q.req.n_rhs; ++j) {
+    const int32_t v = q.req.shift_status[j];
+    if (v == 1 || v == -1) rs = FKS_NOT_CONVERGED;
+    else if (v == 2 && rs == FKS_OK) rs = FKS_BREAKDOWN_EXACT;
+  }
+  return rs;
+}
+
+static void finish_request(fks_server* sv, Request& q, fks_status st, int state = 2) {
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    q.result = st;
+    q.state = state;
+    q.t_end = now_s();
+  }
+  sv->done_cv.notify_all();
+}
+
+// A lane's continuous batch (iteration-level batching): `cap` slots, one
+// source each, for requests compatible with `first` (same operator, shifts,
+// taus and options). The step loop runs `steps_per_launch` Arnoldi steps per
+// launch of its graph; after each launch the server's driver thread
+//  - delivers every source that finished (assembly, true residual, copies into
+//    the request's arrays: per-source output delivery) and frees its slot,
+//  - stops the slots of cancelled or timed-out requests (k_stop_slots),
+//  - admits queued compatible requests into free slots (their sources start at
+//    step 1 while the others go on: every kernel works per slot, with its own
+//    step, tau and inner-solve state),
+// and launches the loop again. The batch ends when no slot is busy and no
+// compatible request is queued.
+struct BatchBase {
+  virtual ~BatchBase() {}
+  // setup, first launch; false if the batch already ended (its requests failed)
+  virtual bool start() = 0;
+  // after the last launch completed: deliveries, stops, admissions, next
+  // launch; false when the batch has ended
+  virtual bool step_done() = 0;
+  cudaEvent_t ev = nullptr;
+  size_t est = 0;
+  int lane_id = 0;
+};
+
+template <typename VT>
+struct Batch : BatchBase {
+  fks_server* sv;
+  Lane* lane;
+  cudaStream_t s;
+  std::shared_ptr<Request> first;
+  int cap;
+  Solve S{};
+  fks_options o{};
+  std::vector<SlotUse> use;
+  std::vector<SlotState> sth;
+  std::vector<int32_t> stop_h, cyc_h;
+  std::vector<std::pair<int, std::shared_ptr<Request>>> admit;
+
+  Batch(fks_server* sv_, int lane_, std::shared_ptr<Request> first_, int cap_)
+      : sv(sv_), lane(sv_->lanes[lane_].get()), s(sv_->streams[lane_]), first(std::move(first_)), cap(cap_) {
+    lane_id = lane_;
+    use.resize(cap);
+    sth.resize(cap);
+    stop_h.assign(cap, 0);
+  }
+  ~Batch() override {
+    if (ev) cudaEventDestroy(ev);
+  }
+
+  // every request still holding (or about to take) a slot ends with `st`
+  void fail_all(fks_status st) {
+    std::vector<std::shared_ptr<Request>> qs;
+    for (auto& u : use)
+      if (u.q && std::find(qs.begin(), qs.end(), u.q) == qs.end()) qs.push_back(u.q);
+    for (auto& a : admit)
+      if (std::find(qs.begin(), qs.end(), a.second) == qs.end()) qs.push_back(a.second);
+    for (auto& q : qs) finish_request(sv, *q, st);
+    for (auto& u : use) u = SlotUse{};
+    admit.clear();
+  }
+  void fail(const CudaError& e) {
+    set_error(std::string("fks_server: ") + e.where + ": " + cudaGetErrorString(e.e));
+    cudaGetLastError();
+    fail_all(e.e == cudaErrorMemoryAllocation ? FKS_ERR_OOM : FKS_ERR_CUDA);
+  }
+
+  bool start() override {
+    const fks_request& r0 = first->req;
+    fks_op* op = r0.op;
+    const int64_t n = op->n;
+    o = r0.opt;
+    o.tau_schedule = first->sched.data();
+    S.op = op;
+    S.lane = lane;
+    S.s = s;
+    S.nslot = cap;
+    S.n_f = r0.n_f;
+    S.n_tau = r0.n_tau;
+    S.m = o.m_max;
+    S.sched_len = o.sched_len;
+    S.precision = o.precision;
+    S.variant = o.variant;
+    S.n = n;
+    S.tol = o.tol;
+    S.eps = o.inner_tol > 0 ? o.inner_tol : std::min(1e-6, o.tol / 100.0);
+    S.max_cycles = o.inner_max_cycles > 0 ? o.inner_max_cycles : 50;
+    S.replay = false;
+    S.inner_steps = o.inner_steps > 0 ? o.inner_steps : (op->csr && op->amg.on ? 4 : 8);
+    S.relax = o.inner_relax > 0 ? o.inner_relax : 0.0;
+    S.batching = true;
+    S.st_host = sth.data();
+    for (int i = 0; i < r0.n_rhs; ++i) use[i] = SlotUse{first, i, false};
+    first->sources_left = r0.n_rhs;
+    admit = {{0, first}};
+    try {
+      std::string err = amg_prepare<VT>(S, first->tau.data());
+      if (!err.empty()) {
+        set_error("fks_server: " + err);
+        fail_all(FKS_ERR_ARG);
+        return false;
+      }
+      Arena probe;
+      carve<VT>(S, probe, true);
+      lane->ws.reserve(probe.off + 4096);
+      carve<VT>(S, lane->ws, true);
+      if (S.amg) CK(cudaMemcpyAsync(S.amg_tab, S.amg_table.data(), S.amg_table.size(), cudaMemcpyHostToDevice, s));
+      copy_in(S.sigma, first->sigma.data(), sizeof(z64) * S.n_f, s);
+      copy_in(S.taus, first->tau.data(), sizeof(z64) * S.n_tau, s);
+      CK(cudaMemcpyAsync(S.sched, o.tau_schedule, sizeof(int32_t) * o.sched_len, cudaMemcpyHostToDevice, s));
+      setup_levels<VT>(S);
+      CK(cudaMemsetAsync(S.st, 0, sizeof(SlotState) * cap, s));  // every slot idle
+      std::vector<double> key = {(double)(uintptr_t)lane->ws.base, (double)cap, (double)S.n_f, (double)S.n_tau,
+                                 (double)S.m, (double)S.sched_len, (double)S.precision, (double)S.variant, 0.0, S.eps,
+                                 S.tol, (double)S.max_cycles, (double)op->fuse_max[0], (double)op->fuse_max[1],
+                                 (double)S.inner_steps, (double)op->tile16_max[0], (double)op->tile16_max[1], S.relax,
+                                 (double)op->tail_max[0], (double)op->tail_max[1], (double)op->cluster_max[0],
+                                 (double)op->cluster_max[1], (double)op->tile8_max[0], (double)op->tile8_max[1], 0.0,
+                                 (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L, 1.0};
+      for (int pz = 0; pz < 2; ++pz)
+        for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
+      if (!lane->graph || lane->graph_key != key) {
+        if (lane->graph) cudaGraphExecDestroy(lane->graph);
+        lane->graph = nullptr;
+        build_graph<VT>(S, &lane->graph, &lane->graph_outer, &lane->graph_inner);
+        lane->graph_key = key;
+      }
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      launch();
+      return true;
+    } catch (CudaError& e) {
+      fail(e);
+      return false;
+    }
+  }
+
+  // sources of newly admitted requests start (beta, v_1, shift bookkeeping),
+  // then a few Arnoldi steps of every busy slot; `ev` marks the end
+  void launch() {
+    const int64_t n = S.n;
+    const int n_f = S.n_f, m = S.m;
+    const int nbn = norm_blocks(n);
+    const int64_t vsV = (int64_t)(m + 1) * n;
+    for (auto& a : admit) {
+      const int a0 = a.first, nr = a.second->req.n_rhs;
+      copy_in(S.b + (size_t)a0 * n, a.second->req.b, sizeof(z64) * n * nr, s);
+      launch_norm2_partial(S.st + a0, 0, S.b + (size_t)a0 * n, n, n, S.npart + (size_t)a0 * nbn, nr, s);
+      launch_start(S.st + a0, nr, S.npart + (size_t)a0 * nbn, nbn, n_f, s);
+      launch_init_v1(S.st + a0, S.b + (size_t)a0 * n, n, S.V + (size_t)a0 * vsV, vsV, nr, s,
+                     S.V32 ? S.V32 + (size_t)a0 * vsV : nullptr);
+      launch_init_shifts(S.st + a0, n_f, m, S.sst + (size_t)a0 * n_f, S.mj + (size_t)a0 * n_f,
+                         S.est + (size_t)a0 * n_f, S.bnd + (size_t)a0 * n_f, S.Y + (size_t)a0 * n_f * m,
+                         S.alpha + (size_t)a0 * n_f, nr, s);
+      CK(cudaMemsetAsync(S.pn + (size_t)a0 * m, 0, sizeof(double) * m * nr, s));
+      CK(cudaMemsetAsync(S.cyc + (size_t)a0 * m, 0, sizeof(int32_t) * m * nr, s));
+      CK(cudaMemsetAsync(S.H + (size_t)a0 * (m + 1) * m, 0, sizeof(z64) * (m + 1) * m * nr, s));
+      CK(cudaMemsetAsync(S.taus_k + (size_t)a0 * m, 0, sizeof(z64) * m * nr, s));
+      lane->prof.all_launches += 4;
+    }
+    admit.clear();
+    const int32_t steps = sv->steps_per_launch;
+    CK(cudaMemcpyAsync(S.budget, &steps, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaGraphLaunch(lane->graph, s));
+    CK(cudaEventRecord(ev, s));
+  }
+
+  bool step_done() override {
+    try {
+      const int m = S.m;
+      CK(cudaMemcpyAsync(S.st_host, S.st, sizeof(SlotState) * cap, cudaMemcpyDeviceToHost, s));
+      cyc_h.resize((size_t)cap * m);
+      CK(cudaMemcpyAsync(cyc_h.data(), S.cyc, sizeof(int32_t) * cap * m, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      // launches: per step the outer section, per inner iteration (the most
+      // cycles any busy slot ran in its step) the inner section
+      int mx = 0;
+      for (int i = 0; i < cap; ++i)
+        if (use[i].q && !use[i].done && S.st_host[i].k >= 1)
+          mx = std::max(mx, cyc_h[(size_t)i * m + S.st_host[i].k - 1]);
+      lane->prof.all_launches += (int64_t)lane->graph_outer + (int64_t)mx * lane->graph_inner;
+      // deliver finished sources
+      std::vector<std::shared_ptr<Request>> completed;
+      CK(cudaMemsetAsync(S.tcerr, 0, sizeof(int), s));
+      for (int i = 0; i < cap; ++i) {
+        SlotUse& u = use[i];
+        if (!u.q || u.done || S.st_host[i].active) continue;
+        deliver_slot<VT>(S, lane, i, u, s, S.tcerr);
+        u.done = true;
+        if (--u.q->sources_left == 0) completed.push_back(u.q);
+      }
+      int tc_h = 0;
+      CK(cudaMemcpyAsync(&tc_h, S.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (tc_h) throw CudaError{cudaErrorLaunchFailure, "tensor-core assembly: a wait gave up after two seconds"};
+      for (auto& q : completed) {
+        for (auto& u : use)
+          if (u.q == q) u = SlotUse{};
+        finish_request(sv, *q, request_status(*q));
+      }
+      // cancellations and timeouts, then admissions
+      std::vector<std::pair<std::shared_ptr<Request>, fks_status>> stopping;
+      bool busy = false;
+      {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        const double t = now_s();
+        for (auto& u : use) {
+          if (!u.q) continue;
+          Request& q = *u.q;
+          const bool late = q.req.timeout_s > 0 && t - q.t_start > q.req.timeout_s;
+          if ((q.cancel || late) &&
+              std::find_if(stopping.begin(), stopping.end(), [&](auto& p) { return p.first == u.q; }) == stopping.end())
+            stopping.push_back({u.q, q.cancel ? FKS_ERR_CANCELLED : FKS_ERR_TIMEOUT});
+        }
+        for (auto& sp : stopping)
+          for (int i = 0; i < cap; ++i)
+            if (use[i].q == sp.first) {
+              stop_h[i] = 1;
+              use[i] = SlotUse{};
+            }
+        if (!sv->stop)
+          for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+            const int nr = (*it)->req.n_rhs;
+            const int a0 = compatible(*first, **it) ? free_run(use, nr) : -1;
+            if (a0 < 0) {
+              ++it;
+              continue;
+            }
+            for (int i = 0; i < nr; ++i) use[a0 + i] = SlotUse{*it, i, false};
+            (*it)->state = 1;
+            (*it)->t_start = t;
+            (*it)->sources_left = nr;
+            admit.push_back({a0, *it});
+            it = sv->queue.erase(it);
+          }
+        for (auto& u : use) busy = busy || u.q != nullptr;
+      }
+      if (!stopping.empty()) {
+        CK(cudaMemcpyAsync(S.stopv, stop_h.data(), sizeof(int32_t) * cap, cudaMemcpyHostToDevice, s));
+        launch_stop_slots(S.st, S.stopv, cap, s);
+        CK(cudaStreamSynchronize(s));
+        std::fill(stop_h.begin(), stop_h.end(), 0);
+        for (auto& sp : stopping) finish_request(sv, *sp.first, sp.second, sp.second == FKS_ERR_CANCELLED ? 3 : 2);
+      }
+      if (!busy) return false;
+      launch();
+      return true;
+    } catch (CudaError& e) {
+      fail(e);
+      return false;
+    }
+  }
+};
+
+// Slots of a new batch: the first request's sources plus up to join_slots spare
+// ones for requests that join later, within max_batch and the free budget.
+template <typename VT>
+static int batch_slots(fks_server* sv, const Request& q, size_t* bytes) {
+  const int nr = q.req.n_rhs;
+  int cap = std::min(std::max(nr, nr + sv->join_slots), std::max(nr, sv->max_batch));
+  const size_t fixed = request_bytes<VT>(q.req, nr);
+  const size_t per = std::max<size_t>(1, request_bytes<VT>(q.req, nr + 1) - fixed);
+  const size_t avail = sv->budget > sv->in_use ? sv->budget - sv->in_use : 0;
+  while (cap > nr && fixed + (size_t)(cap - nr) * per > avail) --cap;
+  *bytes = request_bytes<VT>(q.req, cap);
+  return cap;
+}
+
+// The server's driver: one host thread issues every CUDA call of the server
+// (no two threads ever call the runtime for it), and the lanes overlap on the
+// device through their own streams and graphs. It polls the lanes' launches,
+// runs each finished launch's host work, and starts a batch on an idle lane
+// for the first queued request that fits the budget (a request larger than the
+// whole budget runs when nothing else holds any of it).
+static void driver_loop(fks_server* sv) {
+  cudaSetDevice(sv->ctx->device);
+  const int nl = (int)sv->lanes.size();
+  std::vector<std::unique_ptr<BatchBase>> run(nl);
+  auto end_batch = [&](int i) {
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->in_use -= run[i]->est;
+    }
+    run[i].reset();
+    sv->done_cv.notify_all();
+  };
+  while (true) {
+    bool progress = false, running = false;
+    for (int i = 0; i < nl; ++i) {
+      if (!run[i]) continue;
+      const cudaError_t q = cudaEventQuery(run[i]->ev);
+      if (q == cudaErrorNotReady) {
+        running = true;
+        continue;
+      }
+      progress = true;
+      const int64_t l0 = sv->lanes[i]->prof.all_launches;
+      bool more = false;
+      // (a failed launch makes step_done's first call fail, which ends the batch's requests)
+      more = run[i]->step_done();
+      sv->launches += sv->lanes[i]->prof.all_launches - l0;
+      if (more) running = true;
+      else end_batch(i);
+    }
+    for (int i = 0; i < nl; ++i) {
+      if (run[i]) continue;
+      std::shared_ptr<Request> first;
+      size_t est = 0;
+      int cap = 0;
+      {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stop) break;
         auto it = sv->queue.begin();
         for (; it != sv->queue.end(); ++it)
           if ((*it)->est + sv->in_use <= sv->budget || sv->in_use == 0) break;
-        if (it != sv->queue.end()) {
-          batch.push_back(*it);
-          est = (*it)->est;
-          sv->queue.erase(it);
-          int slots = batch[0]->req.n_rhs;
-          for (auto jt = sv->queue.begin(); jt != sv->queue.end();) {
-            size_t add = (*jt)->est;
-            if (slots + (*jt)->req.n_rhs <= sv->max_batch && compatible(*batch[0], **jt) &&
-                est + add + sv->in_use <= std::max(sv->budget, est)) {
-              slots += (*jt)->req.n_rhs;
-              est += add;
-              batch.push_back(*jt);
-              jt = sv->queue.erase(jt);
-            } else {
-              ++jt;
-            }
-          }
-          sv->in_use += est;
-          double t = now_s();
-          for (auto& q : batch) {
-            q->state = 1;
-            q->t_start = t;
-          }
-          break;
-        }
-        sv->cv.wait(lk);
+        if (it == sv->queue.end()) break;
+        first = *it;
+        sv->queue.erase(it);
+        cap = first->req.opt.precision == FKS_PREC_FP64 ? batch_slots<double>(sv, *first, &est)
+                                                        : batch_slots<float>(sv, *first, &est);
+        sv->in_use += est;
+        first->state = 1;
+        first->t_start = now_s();
       }
+      progress = true;
+      if (first->req.opt.precision == FKS_PREC_FP64) run[i].reset(new Batch<double>(sv, i, first, cap));
+      else run[i].reset(new Batch<float>(sv, i, first, cap));
+      run[i]->est = est;
+      const int64_t l0 = sv->lanes[i]->prof.all_launches;
+      const bool ok = run[i]->start();
+      sv->launches += sv->lanes[i]->prof.all_launches - l0;
+      if (ok) running = true;
+      else end_batch(i);
     }
-    run_batch(sv, lane_id, batch);
-    {
-      std::lock_guard<std::mutex> lk(sv->mu);
-      sv->in_use -= est;
-      double t = now_s();
-      for (auto& q : batch) {
-        q->state = 2;
-        q->t_end = t;
-      }
+    std::unique_lock<std::mutex> lk(sv->mu);
+    if (sv->stop && !running) return;
+    if (!progress) {
+      if (running) sv->cv.wait_for(lk, std::chrono::microseconds(50));
+      else sv->cv.wait(lk, [&] { return sv->stop || !sv->queue.empty(); });
     }
-    sv->cv.notify_all();
-    sv->done_cv.notify_all();
   }
 }
 
@@ -2963,7 +3302,7 @@ extern "C" fks_status fks_server_create(fks_ctx* ctx, size_t mem_budget_bytes, i
     set_error(std::string("fks_server_create: ") + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
   }
-  for (int i = 0; i < lanes; ++i) sv->workers.emplace_back(worker_loop, sv, i);
+  sv->workers.emplace_back(driver_loop, sv);
   *out = sv;
   return FKS_OK;
 }
@@ -2971,7 +3310,7 @@ extern "C" fks_status fks_server_create(fks_ctx* ctx, size_t mem_budget_bytes, i
 extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, uint64_t* ticket) {
   if (!sv || !r || !ticket) { set_error("fks_server_submit: NULL argument"); return FKS_ERR_ARG; }
   const fks_options& o = r->opt;
-  if (!r->op || !r->b || !r->sigma || !r->tau || !r->X || !r->res_est || !r->res_bound || !r->m_j ||
+  if (!r->op || !r->b || !r->sigma || !r->tau || !r->res_est || !r->res_bound || !r->m_j ||
       !r->shift_status || r->n_rhs < 1 || r->n_f < 1 || r->n_tau < 1 || r->n_tau > MAX_TAU ||
       o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
       (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
@@ -2982,7 +3321,8 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
   }
   for (int i = 0; i < o.sched_len; ++i)
     if (o.tau_schedule[i] < 0 || o.tau_schedule[i] >= r->n_tau) { set_error("fks_server_submit: bad schedule"); return FKS_ERR_ARG; }
-  if (is_device_ptr(r->b) || is_device_ptr(r->X)) { set_error("fks_server_submit: request arrays must be host memory"); return FKS_ERR_ARG; }
+  if (is_device_ptr(r->b) || (r->X && is_device_ptr(r->X))) { set_error("fks_server_submit: request arrays must be host memory"); return FKS_ERR_ARG; }
+  if (!(r->timeout_s >= 0.0)) { set_error("fks_server_submit: timeout_s must be >= 0"); return FKS_ERR_ARG; }
   auto q = std::make_shared<Request>();
   q->req = *r;
   q->sched.assign(o.tau_schedule, o.tau_schedule + o.sched_len);
@@ -3011,6 +3351,7 @@ extern "C" fks_status fks_server_poll(fks_server* sv, uint64_t ticket, int* done
   if (it == sv->all.end()) { set_error("fks_server_poll: unknown ticket"); return FKS_ERR_ARG; }
   *done = it->second->state >= 2;
   if (result) *result = it->second->state == 3 ? FKS_ERR_CANCELLED : it->second->result;
+  if (result && !*done) *result = FKS_OK;
   return FKS_OK;
 }
 
@@ -3032,7 +3373,12 @@ extern "C" fks_status fks_server_cancel(fks_server* sv, uint64_t ticket) {
     auto it = sv->all.find(ticket);
     if (it == sv->all.end()) { set_error("fks_server_cancel: unknown ticket"); return FKS_ERR_ARG; }
     auto q = it->second;
-    if (q->state != 0) { set_error("fks_server_cancel: the request already started"); return FKS_ERR_ARG; }
+    if (q->state >= 2) { set_error("fks_server_cancel: the request already finished"); return FKS_ERR_ARG; }
+    if (q->state == 1) {
+      // running: its worker stops its sources at the next step boundary
+      q->cancel = true;
+      return FKS_OK;
+    }
     for (auto jt = sv->queue.begin(); jt != sv->queue.end(); ++jt)
       if (*jt == q) {
         sv->queue.erase(jt);
@@ -3059,13 +3405,12 @@ extern "C" fks_status fks_server_times(fks_server* sv, uint64_t ticket, double* 
 
 extern "C" fks_status fks_server_launches(fks_server* sv, int64_t* launches) {
   if (!sv || !launches) { set_error("fks_server_launches: NULL argument"); return FKS_ERR_ARG; }
-  // the lanes' counters are updated by batches holding this lock
-  std::lock_guard<std::mutex> lk(g_api_mu);
-  int64_t t = 0;
-  for (auto& l : sv->lanes) t += l->prof.all_launches;
-  *launches = t;
+  // the workers add each finished batch's launches
+  *launches = sv->launches.load();
   return FKS_OK;
 }
+
+extern "C" void fks_debug_fail_allocs(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
 extern "C" void fks_server_destroy(fks_server* sv) {
   if (!sv) return;

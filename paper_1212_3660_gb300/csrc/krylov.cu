@@ -475,7 +475,12 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
 // End of a step: a slot stops when every shift is frozen, at breakdown or at
 // m_max. One block; with `use_cond` it sets the graph's outer loop condition
 // to "some slot still active".
-__global__ void k_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond) {
+// End of a step: sources with no live shift, a breakdown or m steps stop. With
+// `budget` (steps left in this launch of the step loop, set by the host) the
+// loop also stops when it runs out, so that the host can admit new sources
+// into free slots between launches (continuous batching).
+__global__ void k_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond,
+                           int* budget) {
   int any = 0;
   for (int slot = threadIdx.x; slot < nslot; slot += blockDim.x) {
     SlotState& s = st[slot];
@@ -486,7 +491,21 @@ __global__ void k_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGr
     any |= s.active;
   }
   any = __syncthreads_or(any);
-  if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, any ? 1u : 0u);
+  if (threadIdx.x == 0) {
+    if (budget) {
+      const int left = *budget - 1;
+      *budget = left;
+      if (left <= 0) any = 0;
+    }
+    if (use_cond) cudaGraphSetConditional(cond, any ? 1u : 0u);
+  }
+}
+
+// Stop every source whose flag is set (stop[slot] != 0): it takes no further
+// step (the server's cancellation and timeouts, between launches of the loop).
+__global__ void k_stop_slots(SlotState* st, const int* __restrict__ stop, int nslot) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot < nslot && stop[slot]) st[slot].active = 0;
 }
 
 // X[:, j] = Z Y[:, j] for a tile of AS_J shifts (Y is zero beyond m_j).
@@ -644,8 +663,12 @@ void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H,
   k_givens<<<gr, GV_WARPS * 32, 0, s>>>(st, nf, m, sigma, H, taus_k, pn, tol, variant, replay_mj, g, rc, rs, R, Y, sst,
                                         mj, est, bnd, alpha, tol_shift, coef);
 }
-void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s) {
-  k_step_end<<<1, 256, 0, s>>>(st, nslot, m, use_cond, cond);
+void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s,
+                     int* budget) {
+  k_step_end<<<1, 256, 0, s>>>(st, nslot, m, use_cond, cond, budget);
+}
+void launch_stop_slots(SlotState* st, const int* stop, int nslot, cudaStream_t s) {
+  k_stop_slots<<<nbk(nslot, 64), 64, 0, s>>>(st, stop, nslot);
 }
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
                      int nslot, cudaStream_t s, const SlotState* st, int skip_k_le) {

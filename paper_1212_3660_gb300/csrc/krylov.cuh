@@ -44,7 +44,11 @@ void launch_givens(SlotState* st, int nf, int m, const z64* sigma, const z64* H,
                    double tol, int variant, const int32_t* replay_mj, z64* g, double* rc, z64* rs, z64* R, z64* Y,
                    int32_t* sst, int32_t* mj, double* est, double* bnd, double* alpha, int nslot, cudaStream_t s,
                    const double* tol_shift = nullptr, z64* coef = nullptr);
-void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s);
+// budget (optional, device): steps left in this launch of the step loop
+void launch_step_end(SlotState* st, int nslot, int m, int use_cond, cudaGraphConditionalHandle cond, cudaStream_t s,
+                     int* budget = nullptr);
+// st[slot].active = 0 where stop[slot] != 0
+void launch_stop_slots(SlotState* st, const int* stop, int nslot, cudaStream_t s);
 // x_j = Z y_j in FP64; with st given, sources with st[slot].k <= skip_k_le are skipped
 void launch_assemble(const z64* Z, int64_t vsZ, const z64* Y, const int32_t* mj, int nf, int m, z64* X, int64_t n,
                      int nslot, cudaStream_t s, const SlotState* st = nullptr, int skip_k_le = -1);

@@ -50,7 +50,7 @@ class fks_request(C.Structure):
     _fields_ = [("op", C.c_void_p), ("b", C.c_void_p), ("n_rhs", C.c_int), ("sigma", C.c_void_p), ("n_f", C.c_int),
                 ("tau", C.c_void_p), ("n_tau", C.c_int), ("opt", fks_options), ("X", C.c_void_p),
                 ("res_est", C.c_void_p), ("res_bound", C.c_void_p), ("res_true", C.c_void_p), ("m_j", C.c_void_p),
-                ("shift_status", C.c_void_p)]
+                ("shift_status", C.c_void_p), ("timeout_s", C.c_double)]
 
 
 class FksError(RuntimeError):
@@ -121,6 +121,8 @@ def lib():
     L.fks_server_launches.argtypes = [vp, C.POINTER(C.c_int64)]
     L.fks_server_destroy.argtypes = [vp]
     L.fks_server_destroy.restype = None
+    L.fks_debug_fail_allocs.argtypes = [C.c_int]
+    L.fks_debug_fail_allocs.restype = None
     L.fks_profile_select.argtypes = [vp, C.c_int, C.c_int]
     L.fks_profile_read.argtypes = [vp, C.POINTER(C.c_int64), f64p, f64p, f64p, C.POINTER(C.c_int64)]
     for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_op_amg", "fks_op_amg_setup", "fks_op_amg_info", "fks_amg_host_shape", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
@@ -472,16 +474,18 @@ def fks_server_destroy(srv):
 
 
 class ServerRequest:
-    """A request and the host arrays it points to (kept alive until done)."""
+    """A request and the host arrays it points to (kept alive until done).
+    with_x=False submits X = NULL (residuals and statuses only); timeout_s > 0
+    stops the request with FKS_ERR_TIMEOUT once it has run that long."""
 
-    def __init__(self, op, b, sigma, tau, options, keep, n):
+    def __init__(self, op, b, sigma, tau, options, keep, n, with_x=True, timeout_s=0.0):
         b = np.ascontiguousarray(b, dtype=np.complex128)
         self.n_rhs = b.shape[0] if b.ndim == 2 else 1
         self.b = b.reshape(self.n_rhs, n)
         self.sigma = np.ascontiguousarray(sigma, dtype=np.complex128)
         self.tau = np.ascontiguousarray(tau, dtype=np.complex128)
         n_f = len(self.sigma)
-        self.X = np.zeros((self.n_rhs, n_f, n), np.complex128)
+        self.X = np.zeros((self.n_rhs, n_f, n), np.complex128) if with_x else None
         self.res_est = np.zeros((self.n_rhs, n_f))
         self.res_bound = np.zeros((self.n_rhs, n_f))
         self.res_true = np.zeros((self.n_rhs, n_f))
@@ -490,8 +494,9 @@ class ServerRequest:
         self.keep = keep
         self.c = fks_request(op.value if hasattr(op, "value") else op, self.b.ctypes.data, self.n_rhs,
                              self.sigma.ctypes.data, n_f, self.tau.ctypes.data, len(self.tau), options,
-                             self.X.ctypes.data, self.res_est.ctypes.data, self.res_bound.ctypes.data,
-                             self.res_true.ctypes.data, self.m_j.ctypes.data, self.shift_status.ctypes.data)
+                             self.X.ctypes.data if with_x else None, self.res_est.ctypes.data,
+                             self.res_bound.ctypes.data, self.res_true.ctypes.data, self.m_j.ctypes.data,
+                             self.shift_status.ctypes.data, float(timeout_s))
         self.ticket = None
 
 
@@ -518,6 +523,11 @@ def fks_server_wait(srv, ticket):
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
     return r.value
+
+
+def fks_debug_fail_allocs(count):
+    """Test hook: the next `count` workspace reservations fail as out of memory."""
+    lib().fks_debug_fail_allocs(int(count))
 
 
 def fks_server_cancel(srv, ticket):
