@@ -98,7 +98,9 @@ def parse():
     ap.add_argument("--inner-relax", type=float, default=0.003,
                     help="relaxed inner tolerance constant l (eps_k = min(1e-3, max(eps, l tol / R_k-1))); "
                          "0: the fixed eps of every step")
-    ap.add_argument("--requests", type=int, default=64, help="workload 5: requests in the stream")
+    ap.add_argument("--requests", type=int, default=1000, help="workload 5: requests in the stream")
+    ap.add_argument("--latency-requests", type=int, default=150,
+                    help="workload 5: requests of each Poisson latency run")
     ap.add_argument("--lanes", type=int, default=3, help="workload 5: concurrent server lanes")
     ap.add_argument("--fuse-max", type=int, default=None,
                     help="fused 2D levels up to this many cells (-1: all) instead of autotuning")
@@ -171,18 +173,21 @@ def recorded_traffic(workload, precision, kclass, level):
     return None, None
 
 
-# Serving stream (workload 5): request sizes are bounded so that every
-# request's host output (n x n_f x sources x 16 B) stays below 3.4 GB.
-SERVE_MAX_CELLS = 512 * 512
-SERVE_MAX_SOURCES = 4
+# Serving stream (workload 5): x_j are delivered to the client for requests
+# whose outputs (n x n_f x sources x 16 B) take at most this many bytes; larger
+# ones deliver their residual certificates and statuses only (X = NULL).
+SERVE_MAX_X_BYTES = 1 << 30
+SERVE_WINDOW = 32          # outstanding requests of the closed-loop client
 
 
 def serve_bench(args, rank, world, local, dist):
-    """Request loop over the server: a seeded Poisson stream of requests with
-    their own grids, fields, shift counts and sources, admitted by a device
-    memory budget onto concurrent lanes. Capacity is measured with every request
-    submitted at once; latency (submit to results in host memory) at Poisson
-    arrivals of 0.7x and 0.9x that capacity."""
+    """Request loop over the server on the serving workload: a pool of aquifers
+    (2D and 3D, 64^2 to 160^3 cells) and a seeded Poisson stream of requests,
+    each on one aquifer with 10-200 shifts and 1-16 sources, admitted by a
+    device-memory budget onto concurrent lanes with continuous batching.
+    Capacity: a closed-loop client keeps SERVE_WINDOW requests outstanding;
+    latency (submit to results in host memory) at Poisson arrivals of 0.7x and
+    0.9x that capacity."""
     import threading
 
     import torch
@@ -190,72 +195,95 @@ def serve_bench(args, rank, world, local, dist):
     from paper_1212_3660_gb300 import fks, synth
     prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
     count = args.requests
-    stream = synth.make_request_stream(count, seed=3000 + rank, max_cells=SERVE_MAX_CELLS,
-                                       max_sources=SERVE_MAX_SOURCES)
-    probs = [synth.make_problem(m_max=100, **p) for _, p in stream]
-    arrival_unit = np.array([t for t, _ in stream])        # arrival times at 1 request/s
+    aquifers, stream = synth.make_serving_stream(count, seed=3000 + rank)
     ctx = fks.fks_create(local)
     t0 = time.perf_counter()
-    ops = []
-    for p in probs:
+    probs, ops = [], []
+    for a in aquifers:
+        p = synth.make_problem(m_max=100, **a)
         d = p.dim
-        ops.append(fks.fks_op_grid(ctx, d, [p.shape[d - 1 - a] for a in range(d)], p.h, p.cond, p.ss,
+        probs.append(p)
+        ops.append(fks.fks_op_grid(ctx, d, [p.shape[d - 1 - q] for q in range(d)], p.h, p.cond, p.ss,
                                    p.dirichlet_mask))
     setup_ms = 1000 * (time.perf_counter() - t0)
+    for p, op in zip(probs, ops):   # tiles and chunks per aquifer, as a deployment would do once
+        fks.fks_op_autotune(op, prec, complex(p.tau_bar[len(p.tau_bar) // 2]))
     free, _ = torch.cuda.mem_get_info(local)
-    budget = int(free * 0.6)
+    budget = int(free * 0.7)
     srv = fks.fks_server_create(ctx, budget, lanes=args.lanes)
+    sigma_of = {}
 
     def make_req(i):
-        p = probs[i]
+        q = stream[i]
+        p = probs[q["aquifer"]]
+        key = (q["aquifer"], q["n_f"])
+        if key not in sigma_of:
+            sigma_of[key] = 1j * synth.log_spaced_omegas(5.0, 3600.0, q["n_f"])
+        src = synth.well_cells(p.shape, q["n_rhs"], np.random.default_rng(q["src_seed"]))
+        b = np.zeros((q["n_rhs"], p.n), np.complex128)
+        b[np.arange(q["n_rhs"]), src] = 1.0
         opts, keep = fks.make_options(tol=TOL, m_max=p.m_max, precision=prec, inner_tol=INNER_EPS,
                                       schedule=p.schedule, inner_relax=args.inner_relax)
-        return fks.ServerRequest(ops[i], p.rhs().T.copy(), p.sigma, p.tau_bar, opts, keep, p.n)
+        with_x = p.n * q["n_f"] * q["n_rhs"] * 16 <= SERVE_MAX_X_BYTES
+        return fks.ServerRequest(ops[q["aquifer"]], b, sigma_of[key], p.tau_bar, opts, keep, p.n, with_x=with_x)
 
-    def run(idx, arrivals=None):
-        reqs = [None] * len(idx)
-        t_start = time.perf_counter()
+    def run(idx, arrivals=None, window=None):
+        out = {}
         err = []
+        t_start = time.perf_counter()
+        sem = threading.Semaphore(window) if window else None
 
         def submitter():
             try:
                 for q, i in enumerate(idx):
+                    if sem is not None:
+                        sem.acquire()
                     if arrivals is not None:
                         dt = t_start + arrivals[q] - time.perf_counter()
                         if dt > 0:
                             time.sleep(dt)
                     r = make_req(i)
                     fks.fks_server_submit(srv, r)
-                    reqs[q] = r
+                    out[q] = r
             except Exception as e:  # noqa: BLE001
                 err.append(e)
 
         th = threading.Thread(target=submitter)
         th.start()
-        th.join()
-        if err:
-            raise err[0]
         lat, conv, total, ends, starts, statuses = [], 0, 0, [], [], []
         h2d = d2h = 0
-        for r in reqs:
-            statuses.append(fks.fks_server_wait(srv, r.ticket))
+        for q in range(len(idx)):
+            while q not in out and not err:
+                time.sleep(0.0005)
+            if err:
+                break
+            r = out[q]
+            st_r = fks.fks_server_wait(srv, r.ticket)
+            statuses.append(st_r)
+            if sem is not None:
+                sem.release()
             ts, _, te = fks.fks_server_times(srv, r.ticket)
             lat.append(1000 * (te - ts))
             starts.append(ts)
             ends.append(te)
-            conv += int(np.sum(r.res_true <= TOL))
+            if st_r >= 0:   # failed requests deliver nothing
+                conv += int(np.sum(r.res_true <= TOL))
             total += r.res_true.size
             h2d += r.b.nbytes + r.sigma.nbytes + r.tau.nbytes
-            d2h += r.X.nbytes + r.res_true.size * (8 * 3 + 4 * 2)
+            d2h += (r.X.nbytes if r.X is not None else 0) + r.res_true.size * (8 * 3 + 4 * 2)
+            out[q] = None   # the client drops the delivered arrays
+        th.join()
+        if err:
+            raise err[0]
         wall = max(ends) - min(starts)
         return {"wall_s": wall, "converged": conv, "solves": total, "solves_per_s": conv / wall,
                 "requests_per_s": len(idx) / wall, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "h2d": h2d, "d2h": d2h,
-                "statuses": sorted(set(int(x) for x in statuses))}
+                "statuses": {str(k): int(v) for k, v in zip(*np.unique(np.array(statuses), return_counts=True))}}
 
-    # warm-up: the first few requests once (graph capture, workspaces)
+    # warm-up: a few requests once (graph capture, workspaces)
     for _ in range(max(args.warmup, 1)):
-        run(list(range(min(4, count))))
+        run(list(range(min(4, count))), window=4)
     gpu_index = local
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
     if cvd:
@@ -264,14 +292,16 @@ def serve_bench(args, rank, world, local, dist):
         except ValueError:
             pass
     l0 = fks.fks_server_launches(srv)
+    n_lat = min(count, args.latency_requests)
+    arrival_unit = np.array([q["arrival"] for q in stream[:n_lat]])
     with ClockSampler(gpu_index) as clk:
         if world > 1:
             dist.barrier()
-        cap = run(list(range(count)))
+        cap = run(list(range(count)), window=SERVE_WINDOW)
         loads = {}
         for f in (0.7, 0.9):
             lam = f * cap["requests_per_s"]
-            loads[f"{f:.1f}"] = run(list(range(count)), arrivals=arrival_unit / lam)
+            loads[f"{f:.1f}"] = run(list(range(n_lat)), arrivals=arrival_unit / lam)
         if world > 1:
             dist.barrier()
     launches = fks.fks_server_launches(srv) - l0
@@ -281,38 +311,45 @@ def serve_bench(args, rank, world, local, dist):
     value = replicas.throughput(cap["converged"], cap["wall_s"])
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        p0 = probs[0]
+        # the oracle on the stream's first request (first source), its own steps
         r0 = make_req(0)
         fks.fks_server_submit(srv, r0)
         fks.fks_server_wait(srv, r0.ticket)
+        p0 = probs[stream[0]["aquifer"]]
         ws = int(r0.m_j.max())
-        v, dt, desc = cpu_oracle_sample(p0, min(args.cpu_sample_steps, ws), ws, INNER_EPS, args.inner_relax)
+        pr0 = synth.make_problem(m_max=100, **{**aquifers[stream[0]["aquifer"]], "n_f": stream[0]["n_f"]})
+        v, dt, desc = cpu_oracle_sample(pr0, min(args.cpu_sample_steps, ws), ws, INNER_EPS, args.inner_relax)
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"request 0 ({'x'.join(map(str, p0.shape[::-1]))}, {len(p0.sigma)} shifts, "
-                         f"{len(p0.src_cells)} sources; first source): " + desc}
+               "sample": f"request 0 ({'x'.join(map(str, p0.shape[::-1]))}, {stream[0]['n_f']} shifts; "
+                         f"first source): " + desc}
     fks.fks_server_destroy(srv)
     for op in ops:
         fks.fks_op_destroy(op)
     fks.fks_destroy(ctx)
     if rank == 0:
         shapes = {}
-        for p in probs:
-            k = "x".join(map(str, p.shape[::-1]))
+        for q in stream:
+            k = "x".join(map(str, probs[q["aquifer"]].shape[::-1]))
             shapes[k] = shapes.get(k, 0) + 1
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
                 "warmup": max(args.warmup, 1), "ms_per_step": 1000 * wall, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer", "data": "synthetic",
-                "config": {"workload": "serving-stream", "requests": count, "grids": shapes,
-                           "max_cells": SERVE_MAX_CELLS, "max_sources": SERVE_MAX_SOURCES,
+                "config": {"workload": "serving-stream", "requests": count, "aquifers": len(aquifers),
+                           "requests_per_grid": shapes, "shifts": "10..200 (multiples of 10)", "sources": "1..16",
                            "shifted_solves": cap["solves"], "lanes": args.lanes, "mem_budget_bytes": budget,
                            "precision": args.precision, "parallelism": f"replicas{world}",
-                           "step": "one pass over the stream with every request submitted at once",
-                           "op_setup_ms_all_requests": setup_ms,
-                           "l2": "requests up to 512^2 / 64^3 cells; bases and outputs exceed L2"},
+                           "batching": "continuous: sources join running batches at Arnoldi-step boundaries",
+                           "client": f"closed loop, {SERVE_WINDOW} requests outstanding",
+                           "x_delivery": f"x_j delivered for requests with at most {SERVE_MAX_X_BYTES >> 20} MiB "
+                                         "of outputs, residuals and statuses for all",
+                           "step": "one pass over the stream",
+                           "op_setup_ms_all_aquifers": setup_ms,
+                           "l2": "aquifers up to 160^3 cells; bases and outputs exceed L2"},
                 "latency_ms": {"closed_loop": {"p50": cap["p50_ms"], "p99": cap["p99_ms"]},
                                **{f"poisson_{k}x_capacity": {"p50": v_["p50_ms"], "p99": v_["p99_ms"],
                                                              "solves_per_s": v_["solves_per_s"],
+                                                             "requests": n_lat,
                                                              "offered_requests_per_s": float(k) * cap["requests_per_s"]}
                                   for k, v_ in loads.items()}},
                 "converged_per_step": cap["converged"], "request_statuses": cap["statuses"],
@@ -977,8 +1014,9 @@ def run_reference(args):
         return
     if args.workload == 5:
         # the stream's first request stands for the stream
-        _, p0 = synth.make_request_stream(1, seed=3000, max_cells=SERVE_MAX_CELLS, max_sources=SERVE_MAX_SOURCES)[0]
-        pr = synth.make_problem(m_max=100, **p0)
+        # the stream's first request (its aquifer and shift count) stands for the stream
+        aq, rq = synth.make_serving_stream(1, seed=3000)
+        pr = synth.make_problem(m_max=100, **{**aq[rq[0]["aquifer"]], "n_f": rq[0]["n_f"]})
         pr.name = "serving-stream"
     else:
         pr = synth.workload(args.workload, m_max=100)

@@ -158,6 +158,7 @@ struct Prof {
 struct Lane {
   Arena ws;
   Arena tcws;  // slices of the tensor-core assembly
+  Arena xws;   // server lanes: one source's x_j, assembled there and delivered
   Prof prof;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
@@ -167,6 +168,7 @@ struct Lane {
     graph = nullptr;
     ws.release();
     tcws.release();
+    xws.release();
     prof.release();
   }
 };
@@ -2787,6 +2789,7 @@ struct Request {
   size_t est = 0;
   bool cancel = false;   // fks_server_cancel while running: stop at the next step boundary
   int sources_left = 0;  // sources not yet delivered
+  int next_src = 0;      // sources admitted so far (a request's sources are admitted in order as slots free up)
 };
 
 static double now_s() {
@@ -2845,11 +2848,12 @@ static size_t request_bytes(const fks_request& r, int n_rhs) {
   S.n = r.op->n;
   S.batching = true;
   Arena probe;
-  carve<VT>(S, probe, true);
-  // the tensor-core assembly's slices of one source (delivered one at a time)
+  carve<VT>(S, probe, false);
+  // one source's x_j and the tensor-core assembly's slices of one source
+  // (sources are delivered one at a time)
   const int kmax = std::min(r.opt.m_max, TC_MAX_KP / 2);
   const size_t tc = r.opt.assembly == 0 && tc_supported(kmax, S.n) ? tc_ws_bytes(tc_layout(S.n, r.n_f, kmax, 1)) : 0;
-  return probe.off + tc + 4096;
+  return probe.off + tc + sizeof(z64) * (size_t)S.n * r.n_f + 4096;
 }
 
 // Free run of `cnt` consecutive slots in `use`, or -1.
@@ -2879,7 +2883,7 @@ static void deliver_slot(Solve& S, Lane* lane, int sl, const SlotUse& u, cudaStr
   const int nf = S.n_f, m = S.m;
   const int k = S.st_host[sl].k;
   const int64_t vsZ = (int64_t)m * n;
-  z64* Xs = S.X + (size_t)sl * nf * n;
+  z64* Xs = S.X;  // the lane's one-source delivery buffer
   const fks_request& R = u.q->req;
   if (R.opt.assembly == 0 && k >= 1 && tc_supported(k, n)) {
     TcLayout T = tc_layout(n, nf, k, 1);
@@ -2970,7 +2974,24 @@ struct Batch : BatchBase {
   std::vector<SlotUse> use;
   std::vector<SlotState> sth;
   std::vector<int32_t> stop_h, cyc_h;
-  std::vector<std::pair<int, std::shared_ptr<Request>>> admit;
+  struct Admit {
+    int slot;
+    std::shared_ptr<Request> q;
+    int r;
+  };
+  std::vector<Admit> admit;
+
+  // the request's next sources into free slots (in order); false if some stay
+  // pending. Caller holds sv->mu or runs before the batch is visible.
+  bool admit_sources(const std::shared_ptr<Request>& q) {
+    for (int i = 0; i < cap && q->next_src < q->req.n_rhs; ++i) {
+      if (use[i].q) continue;
+      use[i] = SlotUse{q, q->next_src, false};
+      admit.push_back({i, q, q->next_src});
+      ++q->next_src;
+    }
+    return q->next_src >= q->req.n_rhs;
+  }
 
   Batch(fks_server* sv_, int lane_, std::shared_ptr<Request> first_, int cap_)
       : sv(sv_), lane(sv_->lanes[lane_].get()), s(sv_->streams[lane_]), first(std::move(first_)), cap(cap_) {
@@ -2989,7 +3010,18 @@ struct Batch : BatchBase {
     for (auto& u : use)
       if (u.q && std::find(qs.begin(), qs.end(), u.q) == qs.end()) qs.push_back(u.q);
     for (auto& a : admit)
-      if (std::find(qs.begin(), qs.end(), a.second) == qs.end()) qs.push_back(a.second);
+      if (std::find(qs.begin(), qs.end(), a.q) == qs.end()) qs.push_back(a.q);
+    if (first && first->next_src < first->req.n_rhs &&
+        std::find(qs.begin(), qs.end(), first) == qs.end())
+      qs.push_back(first);
+    {
+      // sources of these requests still queued are dropped with them
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (auto& q : qs) {
+        auto it = std::find(sv->queue.begin(), sv->queue.end(), q);
+        if (it != sv->queue.end()) sv->queue.erase(it);
+      }
+    }
     for (auto& q : qs) finish_request(sv, *q, st);
     for (auto& u : use) u = SlotUse{};
     admit.clear();
@@ -3025,9 +3057,7 @@ struct Batch : BatchBase {
     S.relax = o.inner_relax > 0 ? o.inner_relax : 0.0;
     S.batching = true;
     S.st_host = sth.data();
-    for (int i = 0; i < r0.n_rhs; ++i) use[i] = SlotUse{first, i, false};
-    first->sources_left = r0.n_rhs;
-    admit = {{0, first}};
+    admit_sources(first);
     try {
       std::string err = amg_prepare<VT>(S, first->tau.data());
       if (!err.empty()) {
@@ -3036,9 +3066,11 @@ struct Batch : BatchBase {
         return false;
       }
       Arena probe;
-      carve<VT>(S, probe, true);
+      carve<VT>(S, probe, false);
       lane->ws.reserve(probe.off + 4096);
-      carve<VT>(S, lane->ws, true);
+      carve<VT>(S, lane->ws, false);
+      lane->xws.reserve(sizeof(z64) * (size_t)n * S.n_f + 256);
+      S.X = (z64*)lane->xws.base;
       if (S.amg) CK(cudaMemcpyAsync(S.amg_tab, S.amg_table.data(), S.amg_table.size(), cudaMemcpyHostToDevice, s));
       copy_in(S.sigma, first->sigma.data(), sizeof(z64) * S.n_f, s);
       copy_in(S.taus, first->tau.data(), sizeof(z64) * S.n_tau, s);
@@ -3077,8 +3109,8 @@ struct Batch : BatchBase {
     const int nbn = norm_blocks(n);
     const int64_t vsV = (int64_t)(m + 1) * n;
     for (auto& a : admit) {
-      const int a0 = a.first, nr = a.second->req.n_rhs;
-      copy_in(S.b + (size_t)a0 * n, a.second->req.b, sizeof(z64) * n * nr, s);
+      const int a0 = a.slot, nr = 1;
+      copy_in(S.b + (size_t)a0 * n, a.q->req.b + (size_t)a.r * n, sizeof(z64) * n, s);
       launch_norm2_partial(S.st + a0, 0, S.b + (size_t)a0 * n, n, n, S.npart + (size_t)a0 * nbn, nr, s);
       launch_start(S.st + a0, nr, S.npart + (size_t)a0 * nbn, nbn, n_f, s);
       launch_init_v1(S.st + a0, S.b + (size_t)a0 * n, n, S.V + (size_t)a0 * vsV, vsV, nr, s,
@@ -3110,7 +3142,7 @@ struct Batch : BatchBase {
       // cycles any busy slot ran in its step) the inner section
       int mx = 0;
       for (int i = 0; i < cap; ++i)
-        if (use[i].q && !use[i].done && S.st_host[i].k >= 1)
+        if (use[i].q && S.st_host[i].k >= 1)
           mx = std::max(mx, cyc_h[(size_t)i * m + S.st_host[i].k - 1]);
       lane->prof.all_launches += (int64_t)lane->graph_outer + (int64_t)mx * lane->graph_inner;
       // deliver finished sources
@@ -3118,20 +3150,16 @@ struct Batch : BatchBase {
       CK(cudaMemsetAsync(S.tcerr, 0, sizeof(int), s));
       for (int i = 0; i < cap; ++i) {
         SlotUse& u = use[i];
-        if (!u.q || u.done || S.st_host[i].active) continue;
+        if (!u.q || S.st_host[i].active) continue;
         deliver_slot<VT>(S, lane, i, u, s, S.tcerr);
-        u.done = true;
         if (--u.q->sources_left == 0) completed.push_back(u.q);
+        u = SlotUse{};  // the slot is free for the next source at once
       }
       int tc_h = 0;
       CK(cudaMemcpyAsync(&tc_h, S.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (tc_h) throw CudaError{cudaErrorLaunchFailure, "tensor-core assembly: a wait gave up after two seconds"};
-      for (auto& q : completed) {
-        for (auto& u : use)
-          if (u.q == q) u = SlotUse{};
-        finish_request(sv, *q, request_status(*q));
-      }
+      for (auto& q : completed) finish_request(sv, *q, request_status(*q));
       // cancellations and timeouts, then admissions
       std::vector<std::pair<std::shared_ptr<Request>, fks_status>> stopping;
       bool busy = false;
@@ -3146,26 +3174,29 @@ struct Batch : BatchBase {
               std::find_if(stopping.begin(), stopping.end(), [&](auto& p) { return p.first == u.q; }) == stopping.end())
             stopping.push_back({u.q, q.cancel ? FKS_ERR_CANCELLED : FKS_ERR_TIMEOUT});
         }
-        for (auto& sp : stopping)
+        for (auto& sp : stopping) {
           for (int i = 0; i < cap; ++i)
             if (use[i].q == sp.first) {
               stop_h[i] = 1;
               use[i] = SlotUse{};
             }
+          auto qi = std::find(sv->queue.begin(), sv->queue.end(), sp.first);  // its sources not yet admitted
+          if (qi != sv->queue.end()) sv->queue.erase(qi);
+        }
         if (!sv->stop)
           for (auto it = sv->queue.begin(); it != sv->queue.end();) {
-            const int nr = (*it)->req.n_rhs;
-            const int a0 = compatible(*first, **it) ? free_run(use, nr) : -1;
-            if (a0 < 0) {
+            if (!compatible(*first, **it) || free_run(use, 1) < 0) {
               ++it;
               continue;
             }
-            for (int i = 0; i < nr; ++i) use[a0 + i] = SlotUse{*it, i, false};
-            (*it)->state = 1;
-            (*it)->t_start = t;
-            (*it)->sources_left = nr;
-            admit.push_back({a0, *it});
-            it = sv->queue.erase(it);
+            std::shared_ptr<Request> q = *it;
+            if (q->state == 0) {
+              q->state = 1;
+              q->t_start = t;
+              q->sources_left = q->req.n_rhs;
+            }
+            if (admit_sources(q)) it = sv->queue.erase(it);
+            else ++it;
           }
         for (auto& u : use) busy = busy || u.q != nullptr;
       }
@@ -3186,16 +3217,17 @@ struct Batch : BatchBase {
   }
 };
 
-// Slots of a new batch: the first request's sources plus up to join_slots spare
-// ones for requests that join later, within max_batch and the free budget.
+// Slots of a new batch: the first request's sources plus join_slots spare
+// ones, within max_batch and the free budget; at least one (a request with
+// more sources than fit runs them in turn as slots free up).
 template <typename VT>
 static int batch_slots(fks_server* sv, const Request& q, size_t* bytes) {
   const int nr = q.req.n_rhs;
-  int cap = std::min(std::max(nr, nr + sv->join_slots), std::max(nr, sv->max_batch));
-  const size_t fixed = request_bytes<VT>(q.req, nr);
-  const size_t per = std::max<size_t>(1, request_bytes<VT>(q.req, nr + 1) - fixed);
+  int cap = std::max(1, std::min(nr + sv->join_slots, sv->max_batch));
+  const size_t one = request_bytes<VT>(q.req, 1);
+  const size_t per = std::max<size_t>(1, request_bytes<VT>(q.req, 2) - one);
   const size_t avail = sv->budget > sv->in_use ? sv->budget - sv->in_use : 0;
-  while (cap > nr && fixed + (size_t)(cap - nr) * per > avail) --cap;
+  while (cap > 1 && one + (size_t)(cap - 1) * per > avail) --cap;
   *bytes = request_bytes<VT>(q.req, cap);
   return cap;
 }
@@ -3211,6 +3243,15 @@ static void driver_loop(fks_server* sv) {
   const int nl = (int)sv->lanes.size();
   std::vector<std::unique_ptr<BatchBase>> run(nl);
   auto end_batch = [&](int i) {
+    // the lane's workspaces go back to the stream-ordered pool, so that the
+    // budget accounts for all the memory the server holds
+    Lane* lane = sv->lanes[i].get();
+    if (lane->graph) cudaGraphExecDestroy(lane->graph);
+    lane->graph = nullptr;
+    lane->graph_key.clear();
+    lane->ws.release();
+    lane->tcws.release();
+    lane->xws.release();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->in_use -= run[i]->est;
@@ -3249,16 +3290,20 @@ static void driver_loop(fks_server* sv) {
           if ((*it)->est + sv->in_use <= sv->budget || sv->in_use == 0) break;
         if (it == sv->queue.end()) break;
         first = *it;
-        sv->queue.erase(it);
         cap = first->req.opt.precision == FKS_PREC_FP64 ? batch_slots<double>(sv, *first, &est)
                                                         : batch_slots<float>(sv, *first, &est);
         sv->in_use += est;
-        first->state = 1;
-        first->t_start = now_s();
+        if (first->state == 0) {
+          first->state = 1;
+          first->t_start = now_s();
+          first->sources_left = first->req.n_rhs;
+        }
+        // the request leaves the queue once all its sources have slots
+        if (first->req.n_rhs - first->next_src <= cap) sv->queue.erase(it);
+        if (first->req.opt.precision == FKS_PREC_FP64) run[i].reset(new Batch<double>(sv, i, first, cap));
+        else run[i].reset(new Batch<float>(sv, i, first, cap));
       }
       progress = true;
-      if (first->req.opt.precision == FKS_PREC_FP64) run[i].reset(new Batch<double>(sv, i, first, cap));
-      else run[i].reset(new Batch<float>(sv, i, first, cap));
       run[i]->est = est;
       const int64_t l0 = sv->lanes[i]->prof.all_launches;
       const bool ok = run[i]->start();
@@ -3295,6 +3340,8 @@ extern "C" fks_status fks_server_create(fks_ctx* ctx, size_t mem_budget_bytes, i
       sv->streams.push_back(st);
       sv->lanes.emplace_back(new Lane);
       sv->lanes.back()->ws.astream = st;
+      sv->lanes.back()->tcws.astream = st;
+      sv->lanes.back()->xws.astream = st;
     }
   } catch (CudaError& e) {
     for (auto st : sv->streams) cudaStreamDestroy(st);
@@ -3331,7 +3378,8 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
   for (auto& z : q->sigma) if (!finite_c(z)) { set_error("fks_server_submit: sigma has NaN/Inf"); return FKS_ERR_ARG; }
   for (auto& z : q->tau) if (!finite_c(z)) { set_error("fks_server_submit: tau has NaN/Inf"); return FKS_ERR_ARG; }
   if (!csr_diag_ok(r->op, q->tau.data(), r->n_tau)) { set_error("fks_server_submit: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
-  q->est = o.precision == FKS_PREC_FP64 ? request_bytes<double>(*r, r->n_rhs) : request_bytes<float>(*r, r->n_rhs);
+  // the least a batch for it needs: one source's slot (more sources run as slots free up)
+  q->est = o.precision == FKS_PREC_FP64 ? request_bytes<double>(*r, 1) : request_bytes<float>(*r, 1);
   q->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(sv->mu);

@@ -8,6 +8,7 @@ loading fails loudly otherwise.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 import re
@@ -461,16 +462,31 @@ def fks_profile_read(op):
 
 
 # ---------------------------------------------------------------- serving
+# servers not yet destroyed: stopped at interpreter exit, so that the server's
+# driver thread never outlives the process's CUDA state
+_live_servers = {}
+
+
+def _destroy_live_servers():
+    for key in list(_live_servers):
+        lib().fks_server_destroy(_live_servers.pop(key))
+
+
+atexit.register(_destroy_live_servers)
+
+
 def fks_server_create(ctx, mem_budget_bytes, lanes=2):
     out = C.c_void_p()
     st = lib().fks_server_create(ctx, int(mem_budget_bytes), int(lanes), C.byref(out))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
+    _live_servers[out.value] = out
     return out
 
 
 def fks_server_destroy(srv):
-    lib().fks_server_destroy(srv)
+    if _live_servers.pop(srv.value, None) is not None:
+        lib().fks_server_destroy(srv)
 
 
 class ServerRequest:

@@ -167,3 +167,19 @@ def test_injected_allocation_failure_fails_the_batch_and_leaks_nothing():
     assert done and res == fks.FKS_OK
     fks.fks_server_destroy(srv)
     s.close()
+
+
+def test_request_larger_than_the_budget_runs_source_by_source():
+    """With room for one source at a time (a one-byte budget: a batch gets one
+    slot), a request's sources are admitted in turn as slots free up; each is
+    delivered as it finishes and the results equal the solve alone."""
+    need_gpu()
+    p = synth.make_problem((80, 64), n_f=12, periods=(5.0, 3600.0), n_p=3, seed=46, m_max=60)
+    s = Solver(p)
+    srv = fks.fks_server_create(s.ctx, 1, lanes=2)
+    r = _request(p, s, [10, 2000, 4000])
+    fks.fks_server_submit(srv, r)
+    assert fks.fks_server_wait(srv, r.ticket) == fks.FKS_OK
+    _alone_equal(s, r, fks.FKS_PREC_MIXED, p.tol, 1e-12)
+    fks.fks_server_destroy(srv)
+    s.close()
