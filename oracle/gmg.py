@@ -9,9 +9,15 @@ this build's own (the paper gives none); the GPU path implements the same
 specification independently:
 
   levels   coarsen grid axis a by 2 while n_a is even and n_a > 4 (per axis);
-           stop when no axis coarsens.
+           stop when no axis coarsens. If the coarsest level so formed has more
+           than MAX_COARSE cells (too large for the exact solve), the hierarchy
+           is formed again with "ragged" halving: while a level has more than
+           MAX_COARSE cells, an odd axis with n_a > 4 also coarsens, to
+           (n_a + 1) / 2 cells, children 2I and 2I + 1 except the last coarse
+           cell, whose only child is the last fine cell.
   coarse   face transmissibility = (sum of the fine faces on the coarse face) / r_a,
-           boundary faces alike; coarse storage = sum of the children.
+           boundary faces alike (a ragged axis: the last coarse cell's high face
+           is its lone child's high face); coarse storage = sum of the children.
   R        restriction = sum of the children.
   P        prolongation = cell-centred (bi/tri)linear interpolation, weights 3/4
            and 1/4 per coarsened axis; beyond a zero-head face the coarse ghost
@@ -39,15 +45,30 @@ from .operator import matrix_from_faces
 
 NU1 = 2
 NU2 = 2
+MAX_COARSE = 1024   # largest coarsest level (cells) solved exactly
 
 
-def _ratios(shape):
-    # numpy axis order; grid axis a = d-1-q
-    return tuple(2 if (s % 2 == 0 and s > 4) else 1 for s in shape)
+def _ratios(shape, ragged=False):
+    # numpy axis order; grid axis a = d-1-q. Ragged: odd axes > 4 also halve
+    # (rounding up) while the level has more than MAX_COARSE cells.
+    big = ragged and int(np.prod(shape)) > MAX_COARSE
+    return tuple(2 if (s > 4 and (s % 2 == 0 or big)) else 1 for s in shape)
 
 
 def _coarsen_sum(arr, r, sel_q=None, sel_off=None):
+    """Sum over the children of each coarse cell (children 2I, 2I + 1 per
+    coarsened axis; an odd axis's last coarse cell has the one child 2I). With
+    sel_q, only the child at offset sel_off along numpy axis sel_q is taken: 0
+    is the first child, r - 1 the last one (the lone child of a ragged cell)."""
     d = arr.ndim
+    for q in range(d):
+        if r[q] == 2 and arr.shape[q] % 2 == 1:
+            # pad the odd axis to even: with zeros (no second child), or, where
+            # the last child is selected, with a copy of the lone child
+            pad = [(0, 0)] * d
+            pad[q] = (0, 1)
+            mode = "edge" if (q == sel_q and sel_off == r[q] - 1) else "constant"
+            arr = np.pad(arr, pad, mode=mode)
     new = []
     for n, rq in zip(arr.shape, r):
         new += [n // rq, rq]
@@ -57,10 +78,9 @@ def _coarsen_sum(arr, r, sel_q=None, sel_off=None):
     return x.sum(axis=tuple(2 * q + 1 for q in range(d)))
 
 
-def _prolong_1d(n_c, r, dirichlet_lo, dirichlet_hi):
+def _prolong_1d(n_f, n_c, r, dirichlet_lo, dirichlet_hi):
     if r == 1:
         return sp.identity(n_c, format="csr")
-    n_f = 2 * n_c
     rows, cols, vals = [], [], []
     for i in range(n_f):
         parent = i // 2
@@ -74,12 +94,11 @@ def _prolong_1d(n_c, r, dirichlet_lo, dirichlet_hi):
     return sp.csr_matrix((vals, (rows, cols)), shape=(n_f, n_c))
 
 
-def _restrict_1d(n_c, r):
+def _restrict_1d(n_f, n_c, r):
     if r == 1:
         return sp.identity(n_c, format="csr")
-    rows = np.repeat(np.arange(n_c), 2)
-    cols = np.arange(2 * n_c)
-    return sp.csr_matrix((np.ones(2 * n_c), (rows, cols)), shape=(n_c, 2 * n_c))
+    cols = np.arange(n_f)
+    return sp.csr_matrix((np.ones(n_f), (cols // 2, cols)), shape=(n_c, n_f))
 
 
 def _kron_all(mats):
@@ -115,14 +134,23 @@ class Hierarchy:
     """Multigrid levels of K, M and, per distinct tau, the shifted matrices."""
 
     def __init__(self, op, taus, max_coarse=None):
+        self._build(op, ragged=False)
+        if self.levels[-1].n > MAX_COARSE:
+            self._build(op, ragged=True)
+        self.taus = np.asarray(taus, dtype=np.complex128)
+        self.A = [[(L.K + t * L.M).tocsr() for L in self.levels] for t in self.taus]
+        self.D = [[A.diagonal() for A in As] for As in self.A]
+        self.coarse_lu = [sla.lu_factor(As[-1].toarray()) for As in self.A]
+
+    def _build(self, op, ragged):
         d = len(op.shape)
         lev = Level(op.shape, op.h, op.t_lo, op.t_hi, op.m_diag, op.dirichlet_mask)
         self.levels = [lev]
         while True:
-            r = _ratios(lev.shape)
+            r = _ratios(lev.shape, ragged)
             if all(x == 1 for x in r):
                 break
-            cshape = tuple(s // x for s, x in zip(lev.shape, r))
+            cshape = tuple((s + x - 1) // x for s, x in zip(lev.shape, r))
             ch = tuple(lev.h[a] * r[d - 1 - a] for a in range(d))
             t_lo, t_hi = [], []
             for a in range(d):
@@ -135,17 +163,13 @@ class Hierarchy:
             r1 = []
             for q in range(d):
                 a = d - 1 - q
-                p1.append(_prolong_1d(cshape[q], r[q], op.dirichlet_mask >> (2 * a) & 1,
+                p1.append(_prolong_1d(lev.shape[q], cshape[q], r[q], op.dirichlet_mask >> (2 * a) & 1,
                                       op.dirichlet_mask >> (2 * a + 1) & 1))
-                r1.append(_restrict_1d(cshape[q], r[q]))
+                r1.append(_restrict_1d(lev.shape[q], cshape[q], r[q]))
             lev.P = _kron_all(p1)
             lev.R = _kron_all(r1)
             self.levels.append(clev)
             lev = clev
-        self.taus = np.asarray(taus, dtype=np.complex128)
-        self.A = [[(L.K + t * L.M).tocsr() for L in self.levels] for t in self.taus]
-        self.D = [[A.diagonal() for A in As] for As in self.A]
-        self.coarse_lu = [sla.lu_factor(As[-1].toarray()) for As in self.A]
 
     def vcycle(self, p, f, lev=0):
         """One V-cycle for (K + tau_p M) e = f on level `lev`, zero initial guess."""

@@ -25,6 +25,95 @@ def test_level_shapes(shape, expect):
     assert [L.shape for L in hier.levels] == expect
 
 
+@pytest.mark.parametrize("shape,expect", [
+    # even halving would stop at 125^2, 25^3 and 35 x 45 (> 1024 cells): odd
+    # sides then halve too, rounding up, while a level has more than 1024 cells
+    ((250, 250), [(250, 250), (125, 125), (63, 63), (32, 32), (16, 16), (8, 8), (4, 4)]),
+    ((100, 100, 100), [(100, 100, 100), (50, 50, 50), (25, 25, 25), (13, 13, 13), (7, 7, 7)]),
+    ((70, 90), [(70, 90), (35, 45), (18, 23), (9, 23)]),
+    # an even-halving hierarchy that ends at <= 1024 cells is kept as it is
+    ((2048, 5), [(2048, 5), (1024, 5), (512, 5), (256, 5), (128, 5), (64, 5), (32, 5), (16, 5), (8, 5), (4, 5)]),
+])
+def test_level_shapes_ragged(shape, expect):
+    op = oracle.assemble(shape, (1.0,) * len(shape), np.ones(shape), np.ones(shape), (1 << (2 * len(shape))) - 1)
+    hier = Hierarchy(op, [1j])
+    assert [L.shape for L in hier.levels] == expect
+    assert hier.levels[-1].n <= 1024
+
+
+@pytest.mark.parametrize("shape", [(70, 90), (30, 50, 50)])
+def test_ragged_levels_homogeneous_geometry(shape):
+    """Coarse levels of a homogeneous medium on ragged hierarchies. A coarse
+    cell covers w_q fine cells along axis q (1D: children summed, the one-child
+    cell of an odd axis covering one fewer); against the uniform
+    re-discretisation with spacing W_q = h_q(level) / h_q(0) fine cells, every
+    face along axis q has area prod_{q' != q} w_q' / W_q' times the uniform one
+    and every storage prod_q w_q / W_q. R sums each fine cell into exactly one
+    coarse cell, and with no-flow faces every row of P sums to 1."""
+    d = len(shape)
+    h = (2.0, 1.0, 0.5)[:d]
+    for mask in (0, (1 << 2 * d) - 1):
+        op = oracle.assemble(shape, h, np.full(shape, 2e-4), np.full(shape, 3e-5), mask)
+        hier = Hierarchy(op, [0.1j])
+        widths = [np.ones(n) for n in shape]   # per numpy axis, in level-0 cells
+        ragged_seen = False
+        for F, L in zip(hier.levels[:-1], hier.levels[1:]):
+            for q in range(d):
+                if L.shape[q] < F.shape[q]:
+                    w = widths[q]
+                    ragged_seen |= len(w) % 2 == 1
+                    widths[q] = np.array([w[2 * I:2 * I + 2].sum() for I in range(L.shape[q])])
+            ref = oracle.assemble(L.shape, L.h, np.full(L.shape, 2e-4), np.full(L.shape, 3e-5), mask)
+            frac = []
+            for q in range(d):
+                a = d - 1 - q
+                W = L.h[a] / h[a]
+                shp = [1] * d
+                shp[q] = L.shape[q]
+                frac.append((widths[q] / W).reshape(shp))
+            for a in range(d):
+                q = d - 1 - a
+                scale = np.ones(L.shape)
+                for q2 in range(d):
+                    if q2 != q:
+                        scale = scale * frac[q2]
+                assert np.allclose(L.t_lo[a], ref.t_lo[a] * scale, rtol=1e-14, atol=0)
+                assert np.allclose(L.t_hi[a], ref.t_hi[a] * scale, rtol=1e-14, atol=0)
+            mscale = np.ones(L.shape)
+            for q in range(d):
+                mscale = mscale * frac[q]
+            assert np.allclose(L.m.reshape(L.shape), ref.m_diag.reshape(L.shape) * mscale, rtol=1e-14)
+            assert np.array_equal(np.asarray(F.R.sum(axis=0)).ravel(), np.ones(F.n))
+            if mask == 0:
+                assert np.allclose(np.asarray(F.P.sum(axis=1)).ravel(), 1.0, rtol=0, atol=1e-15)
+        assert ragged_seen
+
+
+@pytest.mark.parametrize("shape", [(66, 70), (18, 22, 26)])
+def test_ragged_hierarchy_contracts_and_solves(shape):
+    """Measured V-cycle contraction on ragged hierarchies (a wrong child, face or
+    weight at the one-child slabs shows as a slow or divergent cycle), and the
+    solve against sparse LU within ||A^-1|| ||p||."""
+    d = len(shape)
+    op = oracle.assemble(shape, (500.0 / shape[-1],) * d, np.full(shape, 1e-4), np.full(shape, 1e-5),
+                         (1 << 2 * d) - 1)
+    tau = 2j * np.pi / 100
+    hier = Hierarchy(op, [tau])
+    v = np.random.default_rng(1).standard_normal(op.n) + 0j
+    _, _, p1 = hier.solve(v, 0, 0.0, cycles=2)
+    _, _, p2 = hier.solve(v, 0, 0.0, cycles=6)
+    assert (p2 / p1) ** 0.25 <= 0.25
+    v /= np.linalg.norm(v)
+    z, c, pn = hier.solve(v, 0, 1e-10)
+    assert pn <= 1e-10
+    A = op.shifted(tau).tocsc()
+    assert [L.n for L in hier.levels][-1] <= 1024 and any(
+        F.shape[q] % 2 == 1 and L.shape[q] < F.shape[q]
+        for F, L in zip(hier.levels[:-1], hier.levels[1:]) for q in range(d))
+    z_lu = spla.spsolve(A, v)
+    assert np.linalg.norm(z - z_lu) <= 1e-6 * np.linalg.norm(z_lu)
+
+
 @pytest.mark.parametrize("shape,mask", [((16, 24), 0b1111), ((8, 8, 12), 0b111111), ((16, 16), 0b1001)])
 def test_coarse_operator_is_rediscretisation_for_homogeneous_media(shape, mask):
     h = (2.0, 1.0, 0.5)[:len(shape)]
