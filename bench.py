@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
     ap.add_argument("--workload", type=int, default=3)
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "bf16"],
                     help="default: fp64 for workloads 1, 2 and 6 (complex128 throughout), mixed for 3-5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6,
@@ -193,7 +193,7 @@ def serve_bench(args, rank, world, local, dist):
     import torch
 
     from paper_1212_3660_gb300 import fks, synth
-    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    prec = prec_of(args.precision, fks)
     count = args.requests
     aquifers, stream = synth.make_serving_stream(count, seed=3000 + rank)
     ctx = fks.fks_create(local)
@@ -334,7 +334,7 @@ def serve_bench(args, rank, world, local, dist):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
                 "warmup": max(args.warmup, 1), "ms_per_step": 1000 * wall, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer", "data": "synthetic",
+                "dtype": dtype_of(prec, fks), "data": "synthetic",
                 "config": {"workload": "serving-stream", "requests": count, "aquifers": len(aquifers),
                            "requests_per_grid": shapes, "shifts": "10..200 (multiples of 10)", "sources": "1..16",
                            "shifted_solves": cap["solves"], "lanes": args.lanes, "mem_budget_bytes": budget,
@@ -376,7 +376,7 @@ def jacobian_bench(args, rank, world, local, dist):
 
     from paper_1212_3660_gb300 import fks, synth
     from paper_1212_3660_gb300.solver import Solver
-    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    prec = prec_of(args.precision, fks)
     pr = synth.workload(2, m_max=100)
     pr.sigma = pr.sigma[::max(1, args.shift_stride)].copy()
     ns = args.sensors
@@ -478,7 +478,7 @@ def jacobian_bench(args, rank, world, local, dist):
         line = {"metric": "Jacobian rows/s at 1e-8 residual", "value": value, "unit": "rows/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": replicas.max(ms),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer", "data": "synthetic",
+                "dtype": dtype_of(prec, fks), "data": "synthetic",
                 "config": {"workload": name, "grid": "x".join(map(str, pr.shape[::-1])), "n": n, "n_f": n_f,
                            "sensors": ns, "parameters": ["ln K", "ln S_s"], "precision": args.precision,
                            "inner_relax": args.inner_relax, "parallelism": f"replicas{world}",
@@ -505,7 +505,7 @@ def csr_bench(args, rank, world, local, dist):
 
     from paper_1212_3660_gb300 import fks, synth
     from paper_1212_3660_gb300.solver import Solver
-    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    prec = prec_of(args.precision, fks)
     pr = synth.fe_workload()
     amg = args.precond == "amg"
     solver = Solver(pr, device=local, csr=pr.csr_arrays(), amg=amg)
@@ -619,21 +619,10 @@ def csr_bench(args, rank, world, local, dist):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, _, desc = csr_cpu_sample(pr, args, amg, int(main_info["inner_cycles"][:pr.m_max].sum()))
         cpu = {"value": v, "unit": UNIT, "cores": blas_threads(), "kind": "oracle", "sample": desc}
-    tiling = fks.fks_op_tiling(solver.op, prec)
-    zchunks = fks.fks_op_zchunks(solver.op, prec) if len(pr.shape) == 3 else None
-    # ---- the batched workload (3D 96^3, 64 well sources) beside the 128^3 line
-    batched = None
-    if args.workload == 3 and not args.no_compare and not args.no_batched:
-        del X_d, b_d
-        solver.close()
-        torch.cuda.empty_cache()
-        batched = batched_sample(args, local, dist, world)
-    else:
-        solver.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": replicas.max(ms), "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer",
+                "vs_baseline": None, "dtype": dtype_of(prec, fks),
                 "data": "synthetic",
                 "config": {"workload": pr.name, "n": n, "nnz_K": int(pr.K.nnz), "n_f": n_f,
                            "n_p": len(pr.tau_bar), "schedule": "cycled", "sources_per_gpu": n_rhs,
@@ -1041,6 +1030,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def prec_of(name, fks):
+    """fks precision of a --precision name."""
+    return {"fp64": fks.FKS_PREC_FP64, "mixed": fks.FKS_PREC_MIXED, "bf16": fks.FKS_PREC_MIXED_BF16}[name]
+
+
+def dtype_of(prec, fks):
+    return {fks.FKS_PREC_FP64: "c128", fks.FKS_PREC_MIXED: "c64-inner/c128-outer",
+            fks.FKS_PREC_MIXED_BF16: "c64-inner(bf16 coefficients)/c128-outer"}[prec]
+
+
 def set_thresholds(fks, op, prec, args):
     """The multigrid launch thresholds given on the command line (instead of the
     autotuner's, e.g. for an ncu capture whose timings would mislead it)."""
@@ -1143,7 +1142,7 @@ def main():
             dist.destroy_process_group()
         return
     pr = synth.workload(args.workload, m_max=100)
-    prec = fks.FKS_PREC_FP64 if args.precision == "fp64" else fks.FKS_PREC_MIXED
+    prec = prec_of(args.precision, fks)
     t_setup0 = time.perf_counter()
     solver = Solver(pr, device=local)
     setup_ms = 1000 * (time.perf_counter() - t_setup0)
@@ -1359,14 +1358,16 @@ def main():
         torch.cuda.synchronize()
         ms_v = max_over_ranks(v0.elapsed_time(v1) / reps)
         return {"value": sum_over_ranks(conv_v / reps) / (ms_v / 1000.0), "ms_per_step": ms_v,
-                "precision": "fp64" if v_prec == fks.FKS_PREC_FP64 else "mixed", "inner_relax": v_relax,
+                "precision": {0: "fp64", 1: "mixed", 2: "bf16"}[v_prec], "inner_relax": v_relax,
                 "inner_cycles_total": int(info_arr["inner_cycles"].sum()), "steps_timed": reps}
     comparison = None
     if args.workload in (1, 2, 3, 4) and not args.no_compare:
         comparison = {"this_line": {"value": value, "precision": args.precision, "inner_relax": args.inner_relax},
                       "plain_fp64_fixed_eps": variant(fks.FKS_PREC_FP64, 0.0),
                       "fp64_relaxed": variant(fks.FKS_PREC_FP64, args.inner_relax if args.inner_relax > 0 else 0.003),
-                      "mixed_relaxed": variant(fks.FKS_PREC_MIXED, args.inner_relax if args.inner_relax > 0 else 0.003)}
+                      "mixed_relaxed": variant(fks.FKS_PREC_MIXED, args.inner_relax if args.inner_relax > 0 else 0.003),
+                      "bf16_smoother_relaxed": variant(fks.FKS_PREC_MIXED_BF16,
+                                                       args.inner_relax if args.inner_relax > 0 else 0.003)}
         # restore this line's tuning for what follows
         fks.fks_op_autotune(solver.op, prec, complex(pr.tau_bar[len(pr.tau_bar) // 2]), sh)
 
@@ -1409,7 +1410,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c128" if prec == fks.FKS_PREC_FP64 else "c64-inner/c128-outer",
+                "vs_baseline": None, "dtype": dtype_of(prec, fks),
                 "data": "synthetic",
                 "config": {"workload": pr.name, "grid": "x".join(map(str, pr.shape[::-1])), "n": n, "n_f": n_f,
                            "n_p": len(pr.tau_bar), "schedule": "cycled", "sources_per_gpu": n_rhs,

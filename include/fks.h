@@ -164,7 +164,7 @@ void fks_op_destroy(fks_op* op);
 int64_t fks_op_size(const fks_op* op);
 
 enum { FKS_FGMRES = 0, FKS_FFOM = 1 };
-enum { FKS_PREC_FP64 = 0, FKS_PREC_MIXED = 1 };
+enum { FKS_PREC_FP64 = 0, FKS_PREC_MIXED = 1, FKS_PREC_MIXED_BF16 = 2 };
 
 typedef struct {
   double tol;            /* relative tolerance on ||b - (K + sigma_j M) x_j|| / ||b||, > 0     */
@@ -172,7 +172,11 @@ typedef struct {
   int variant;           /* FKS_FGMRES (least squares) or FKS_FFOM (square solve)             */
   int precision;         /* FKS_PREC_FP64: complex128 throughout; FKS_PREC_MIXED: inner
                             multigrid cycles in complex64, defect correction and everything
-                            else in complex128                                                */
+                            else in complex128; FKS_PREC_MIXED_BF16 (grid operators): as
+                            FKS_PREC_MIXED with the multigrid coefficients (faces, storage)
+                            rounded to bf16 and stored so for the per-level smoother and
+                            restriction kernels (fp32 arithmetic; the complex128 defect
+                            correction uses the exact operator)                               */
   double inner_tol;      /* eps: stop the inner solve when ||p_k|| <= eps ||v_k||; <= 0 means
                             min(1e-6, tol / 100)                                              */
   int inner_max_cycles;  /* cap on multigrid cycles per inner solve (<= 0 means 50)           */

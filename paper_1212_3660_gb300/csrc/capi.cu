@@ -185,7 +185,8 @@ struct fks_ctx {
 // values per entry (fp64 and fp32), diagonals for the Jacobi preconditioner.
 struct CsrDev {
   int64_t nnz = 0;
-  int64_t* rowptr = nullptr;
+  int64_t* sell = nullptr;  // sliced ELL layout of the union pattern (CsrView)
+  int32_t* len = nullptr;
   int32_t* col = nullptr;
   double *kv = nullptr, *mv = nullptr, *dk = nullptr, *dm = nullptr;
   float *kv32 = nullptr, *mv32 = nullptr;
@@ -198,7 +199,8 @@ struct CsrDev {
   fks::CsrView<T> view(int64_t n) const {
     fks::CsrView<T> v;
     v.n = n;
-    v.rowptr = rowptr;
+    v.sell = sell;
+    v.len = len;
     v.col = col;
     if constexpr (sizeof(T) == 8) { v.kv = kv; v.mv = mv; } else { v.kv = kv32; v.mv = mv32; }
     return v;
@@ -247,6 +249,7 @@ struct fks_op {
   uint32_t mask;
   double* cond_d = nullptr;  // grid operators: cell conductivity (device), for the sensitivities
   std::vector<LevelHost> levels;
+  std::vector<LevelHost> levels_bf;  // the same levels with fp32 coefficients replaced by their bf16 roundings
   Lane lane0;  // workspace, graph and instrumentation of fks_solve / fks_precond_apply
   // 2D levels with at most this many cells use the fused tile kernels
   // ([0] complex128 cycles, [1] complex64 cycles); set by fks_op_autotune
@@ -266,6 +269,8 @@ struct fks_op {
 };
 
 namespace fks {
+
+static bool prec_ok(int p) { return p == FKS_PREC_FP64 || p == FKS_PREC_MIXED || p == FKS_PREC_MIXED_BF16; }
 
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -375,6 +380,13 @@ struct Solve {
   // only while they wait for their step-loop graph to finish
   std::unique_lock<std::mutex>* api_lock = nullptr;
 };
+
+// The bf16-smoother option: the V-cycle runs on op->levels_bf (coefficients
+// rounded to bf16; bf16 storage for the per-level smoother and restriction).
+static bool bf16_of(const Solve& S) { return S.precision == FKS_PREC_MIXED_BF16 && !S.op->csr; }
+static const std::vector<LevelHost>& cycle_levels(const Solve& S) {
+  return bf16_of(S) ? S.op->levels_bf : S.op->levels;
+}
 
 template <typename VT>
 static BcgVecs<VT> bcg_vecs(Solve& S) {
@@ -508,7 +520,8 @@ static size_t tail_blob_bytes(const std::vector<LevelHost>& Ls, int64_t tmax, in
 // column k - 1 of Zk (given with its strides; Zk null: never).
 template <typename VT>
 static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zcol = 0) {
-  auto& Ls = S.op->levels;
+  const auto& Ls = cycle_levels(S);
+  const int bf = bf16_of(S) ? 1 : 0;
   int nl = (int)Ls.size();
   ClusterParams<VT> CP{};
   size_t csmem = 0;
@@ -549,13 +562,13 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
     for (int r = 0; r < NU1; ++r) {
       int zs = r == 0 ? 1 : 0;
       PROF(FKS_K_SMOOTH, l, smooth_b(L, zs), smooth_f(L, zs),
-           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, zs, s));
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, zs, s, nullptr, 0, 0, bf));
       PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
-           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s));
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s, nullptr, 0, 0, bf));
     }
     PROF(FKS_K_RESTRICT, l, ns * (L.n * (2 * cv + (d + 1) * rv) + cv * Ls[l + 1].n), ns * L.n * (8 * d + 10),
          launch_residual_restrict<VT>(L, Ls[l + 1], S.st, S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
-                                      s));
+                                      s, bf));
   }
   if (lc >= 0) {
     // levels lc .. coarsest in one cluster per slot
@@ -640,10 +653,10 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
     const bool add_to_zk = l == 0 && Zk;
     for (int r = 0; r < NU2; ++r) {
       PROF(FKS_K_SMOOTH, l, smooth_b(L, 0), smooth_f(L, 0),
-           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s));
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 1, 0, s, nullptr, 0, 0, bf));
       const bool last = add_to_zk && r == NU2 - 1;
       PROF(FKS_K_SMOOTH, l, smooth_b(L, 0) + (last ? ns * L.n * 32.0 : 0.0), smooth_f(L, 0) + (last ? ns * L.n * 2.0 : 0.0),
-           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, 0, s, last ? Zk : nullptr, vsZk, zcol));
+           launch_gs<VT>(L, S.st, I(l), F(l), Zl(l), L.n, S.nslot, 0, 0, s, last ? Zk : nullptr, vsZk, zcol, bf));
     }
     zfin = add_to_zk ? nullptr : Zl(l);
   }
@@ -1002,7 +1015,8 @@ static void setup_levels(Solve& S) {
     S.lane->prof.all_launches += 2;
     return;
   }
-  auto& Ls = S.op->levels;
+  const auto& Ls = cycle_levels(S);
+  const int bf = bf16_of(S) ? 1 : 0;
   {
     std::lock_guard<std::mutex> build_lock(g_build_mu);
     tail_prepare<VT>(tail_launch_smem<VT>(Ls, tail_level<VT>(Ls, tail_max_of<VT>(S.op))));
@@ -1012,7 +1026,7 @@ static void setup_levels(Solve& S) {
     if (cluster_level<VT>(S.op, nullptr, &csm) >= 0) cluster_prepare<VT>(csm);
   }
   for (size_t l = 0; l < Ls.size(); ++l)
-    PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s));
+    PROF(-1, -1, 0, 0, launch_invd<VT>(Ls[l], S.taus, S.n_tau, (cx<VT>*)S.invd[l], S.s, bf));
   PROF(-1, -1, 0, 0, launch_diag64(Ls[0], S.taus, S.n_tau, S.diag64, S.s));
   if (S.tblob) {
     // the tail's coefficients per tau, laid out as in its shared memory
@@ -1042,7 +1056,7 @@ static void setup_levels(Solve& S) {
   CK(cudaMemsetAsync(S.counter, 0, sizeof(int), S.s));
   CK(cudaMemsetAsync(S.bcount, 0, sizeof(int) * S.nslot, S.s));
   S.lane->prof.all_launches += 3;
-  launch_coarse_inverse(C, S.taus, S.n_tau, S.cwork, S.cinv64, S.singular, S.s);
+  launch_coarse_inverse(C, S.taus, S.n_tau, S.cwork, S.cinv64, S.singular, S.s, bf);
   if constexpr (sizeof(VT) == 8) {
     CK(cudaMemcpyAsync(S.cinv, S.cinv64, sizeof(z64) * S.n_tau * nc * nc, cudaMemcpyDeviceToDevice, S.s));
   } else {
@@ -1073,7 +1087,7 @@ static void carve(Solve& S, Arena& A, bool x_internal) {
   S.rep_mj = A.take<int32_t>((size_t)ns * nf);
   S.V = A.take<z64>((size_t)ns * (m + 1) * n);
   // complex64 copy of the basis for the first CGS projection (mixed precision)
-  S.V32 = S.precision == FKS_PREC_MIXED ? A.take<z32>((size_t)ns * (m + 1) * n) : nullptr;
+  S.V32 = S.precision != FKS_PREC_FP64 ? A.take<z32>((size_t)ns * (m + 1) * n) : nullptr;
   S.Z = A.take<z64>((size_t)ns * m * n);
   S.w = A.take<z64>((size_t)ns * n);
   S.ndef = defect_partials(S.op);
@@ -1774,6 +1788,8 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
         int64_t cnt = a < 3 ? (a == 2 && L.nz == 1 ? 1 : face_count(L, a)) : L.n;
         CK(cudaMalloc(&L.d64[a], sizeof(double) * cnt));
         CK(cudaMalloc(&L.d32[a], sizeof(float) * cnt));
+        CK(cudaMalloc(&L.d16[a], sizeof(__nv_bfloat16) * cnt));
+        CK(cudaMalloc(&L.d32b[a], sizeof(float) * cnt));
       }
     }
     op->levels = Ls;
@@ -1789,7 +1805,14 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
       for (int a = 0; a < 4; ++a) {
         int64_t cnt = a < 3 ? (a == 2 && L.nz == 1 ? 1 : face_count(L, a)) : L.n;
         launch_to_f32(L.d64[a], L.d32[a], cnt, s);
+        launch_round_bf16(L.d64[a], L.d16[a], L.d32b[a], cnt, s);
       }
+    // the bf16-smoother option's view of the hierarchy: the kernels that read
+    // fp32 coefficients get the bf16-rounded values, so every kernel of its
+    // V-cycle works with the same coefficients
+    op->levels_bf = op->levels;
+    for (auto& L : op->levels_bf)
+      for (int a = 0; a < 4; ++a) L.d32[a] = L.d32b[a];
     CK(cudaDeviceSynchronize());
     CK(cudaGetLastError());
     op->cond_d = cond_d;
@@ -1869,24 +1892,45 @@ fks_status fks_op_csr(fks_ctx* ctx, int64_t n, const int64_t* k_rowptr, const in
   C.nnz = nnz;
   try {
     CK(cudaSetDevice(ctx->device));
-    std::vector<float> kf(kv.begin(), kv.end()), mf(mv.begin(), mv.end());
-    size_t z = (size_t)std::max<int64_t>(nnz, 1);
-    CK(cudaMalloc(&C.rowptr, sizeof(int64_t) * (n + 1)));
-    CK(cudaMalloc(&C.col, sizeof(int32_t) * z));
-    CK(cudaMalloc(&C.kv, sizeof(double) * z));
-    CK(cudaMalloc(&C.mv, sizeof(double) * z));
-    CK(cudaMalloc(&C.kv32, sizeof(float) * z));
-    CK(cudaMalloc(&C.mv32, sizeof(float) * z));
+    // sliced ELL: each slice of CSR_SLICE rows padded to its longest row
+    const int64_t nsl = (n + CSR_SLICE - 1) / CSR_SLICE;
+    std::vector<int64_t> sell(nsl + 1, 0);
+    std::vector<int32_t> len(n);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+      int64_t w = 0;
+      for (int64_t r = sl * CSR_SLICE; r < std::min(n, (sl + 1) * CSR_SLICE); ++r) {
+        len[r] = (int32_t)(rowptr[r + 1] - rowptr[r]);
+        w = std::max<int64_t>(w, len[r]);
+      }
+      sell[sl + 1] = sell[sl] + w * CSR_SLICE;
+    }
+    const size_t se = (size_t)std::max<int64_t>(sell[nsl], 1);
+    std::vector<int32_t> scol(se, 0);
+    std::vector<double> skv(se, 0.0), smv(se, 0.0);
+    for (int64_t r = 0; r < n; ++r)
+      for (int64_t q = 0; q < len[r]; ++q) {
+        const int64_t e = sell[r / CSR_SLICE] + q * CSR_SLICE + (r % CSR_SLICE), src = rowptr[r] + q;
+        scol[e] = col[src];
+        skv[e] = kv[src];
+        smv[e] = mv[src];
+      }
+    std::vector<float> kf(skv.begin(), skv.end()), mf(smv.begin(), smv.end());
+    CK(cudaMalloc(&C.sell, sizeof(int64_t) * (nsl + 1)));
+    CK(cudaMalloc(&C.len, sizeof(int32_t) * n));
+    CK(cudaMalloc(&C.col, sizeof(int32_t) * se));
+    CK(cudaMalloc(&C.kv, sizeof(double) * se));
+    CK(cudaMalloc(&C.mv, sizeof(double) * se));
+    CK(cudaMalloc(&C.kv32, sizeof(float) * se));
+    CK(cudaMalloc(&C.mv32, sizeof(float) * se));
     CK(cudaMalloc(&C.dk, sizeof(double) * n));
     CK(cudaMalloc(&C.dm, sizeof(double) * n));
-    CK(cudaMemcpy(C.rowptr, rowptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
-    if (nnz > 0) {
-      CK(cudaMemcpy(C.col, col.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(C.kv, kv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(C.mv, mv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(C.kv32, kf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(C.mv32, mf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
-    }
+    CK(cudaMemcpy(C.sell, sell.data(), sizeof(int64_t) * (nsl + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.len, len.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.col, scol.data(), sizeof(int32_t) * se, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.kv, skv.data(), sizeof(double) * se, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.mv, smv.data(), sizeof(double) * se, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.kv32, kf.data(), sizeof(float) * se, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(C.mv32, mf.data(), sizeof(float) * se, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(C.dk, dk.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(C.dm, dm.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
   } catch (CudaError& e) {
@@ -1908,7 +1952,7 @@ void fks_op_destroy(fks_op* op) {
   if (!op) return;
   {
     CsrDev& C = op->cd;
-    void* ps[8] = {C.rowptr, C.col, C.kv, C.mv, C.kv32, C.mv32, C.dk, C.dm};
+    void* ps[9] = {C.sell, C.len, C.col, C.kv, C.mv, C.kv32, C.mv32, C.dk, C.dm};
     for (void* q : ps)
       if (q) cudaFree(q);
   }
@@ -1916,6 +1960,8 @@ void fks_op_destroy(fks_op* op) {
     for (int a = 0; a < 4; ++a) {
       if (L.d64[a]) cudaFree(L.d64[a]);
       if (L.d32[a]) cudaFree(L.d32[a]);
+      if (L.d16[a]) cudaFree(L.d16[a]);
+      if (L.d32b[a]) cudaFree(L.d32b[a]);
     }
     if (L.kd64) cudaFree(L.kd64);
   }
@@ -1939,7 +1985,8 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
   if (o->m_max < 1 || o->m_max > MAX_M) { set_error("fks_solve: m_max must be in 1..128"); return FKS_ERR_ARG; }
   if (!(o->tol > 0) || !std::isfinite(o->tol)) { set_error("fks_solve: tol must be positive"); return FKS_ERR_ARG; }
   if (o->variant != FKS_FGMRES && o->variant != FKS_FFOM) { set_error("fks_solve: bad variant"); return FKS_ERR_ARG; }
-  if (o->precision != FKS_PREC_FP64 && o->precision != FKS_PREC_MIXED) { set_error("fks_solve: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(o->precision)) { set_error("fks_solve: bad precision"); return FKS_ERR_ARG; }
+  if (op->csr && o->precision == FKS_PREC_MIXED_BF16) { set_error("fks_solve: the bf16 smoother option is for grid operators"); return FKS_ERR_ARG; }
   if (o->sched_len < 1 || !o->tau_schedule) { set_error("fks_solve: empty tau schedule"); return FKS_ERR_ARG; }
   for (int i = 0; i < o->sched_len; ++i)
     if (o->tau_schedule[i] < 0 || o->tau_schedule[i] >= n_tau) { set_error("fks_solve: schedule index out of range"); return FKS_ERR_ARG; }
@@ -1994,7 +2041,7 @@ fks_status fks_solve(fks_op* op, const fks_c128* b, int n_rhs, const fks_c128* s
 fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_fusion: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_fusion: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_fusion: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_fusion: bad precision"); return FKS_ERR_ARG; }
   op->fuse_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
   return FKS_OK;
 }
@@ -2002,7 +2049,7 @@ fks_status fks_op_set_fusion(fks_op* op, int precision, int64_t max_cells) {
 fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_tiles: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_tiles: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_tiles: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_tiles: bad precision"); return FKS_ERR_ARG; }
   op->tile16_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
   return FKS_OK;
 }
@@ -2010,7 +2057,7 @@ fks_status fks_op_set_tiles(fks_op* op, int precision, int64_t max_cells) {
 fks_status fks_op_set_tiles8(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_tiles8: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_tiles8: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_tiles8: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_tiles8: bad precision"); return FKS_ERR_ARG; }
   op->tile8_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells < 0 ? INT64_MAX : max_cells;
   return FKS_OK;
 }
@@ -2018,7 +2065,7 @@ fks_status fks_op_set_tiles8(fks_op* op, int precision, int64_t max_cells) {
 fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_tail: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_tail: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_tail: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_tail: bad precision"); return FKS_ERR_ARG; }
   if (max_cells < 1) { set_error("fks_op_set_tail: max_cells must be >= 1"); return FKS_ERR_ARG; }
   int lt;
   size_t smem;
@@ -2037,7 +2084,7 @@ fks_status fks_op_set_tail(fks_op* op, int precision, int64_t max_cells) {
 fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
   if (!op) { set_error("fks_op_set_cluster: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_cluster: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_cluster: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_cluster: bad precision"); return FKS_ERR_ARG; }
   const int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   if (max_cells <= 0) {
     op->cluster_max[pi] = 0;
@@ -2075,7 +2122,7 @@ fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
 fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes) {
   if (!op) { set_error("fks_op_set_zchunk: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_set_zchunk: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_set_zchunk: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_zchunk: bad precision"); return FKS_ERR_ARG; }
   if (level < 0 || level >= (int)op->levels.size()) { set_error("fks_op_set_zchunk: no such level"); return FKS_ERR_ARG; }
   op->zchunk[precision == FKS_PREC_FP64 ? 0 : 1][level] = planes <= 0 ? 0 : std::max(2, planes & ~1);
   return FKS_OK;
@@ -2083,7 +2130,7 @@ fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes) {
 
 fks_status fks_op_zchunks(const fks_op* op, int precision, int32_t* planes, int cap, int* levels) {
   if (!op) { set_error("fks_op_zchunks: NULL operator"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_zchunks: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_zchunks: bad precision"); return FKS_ERR_ARG; }
   const int nl = (int)op->levels.size();
   if (levels) *levels = nl;
   for (int l = 0; l < nl && l < cap && planes; ++l) planes[l] = op->zchunk[precision == FKS_PREC_FP64 ? 0 : 1][l];
@@ -2093,7 +2140,7 @@ fks_status fks_op_zchunks(const fks_op* op, int precision, int32_t* planes, int 
 fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int64_t* tile16_max,
                          int64_t* tail_max, int64_t* cluster_max, int64_t* tile8_max) {
   if (!op) { set_error("fks_op_tiling: NULL operator"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_tiling: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_tiling: bad precision"); return FKS_ERR_ARG; }
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   if (fuse_max) *fuse_max = op->fuse_max[pi];
   if (tile16_max) *tile16_max = op->tile16_max[pi];
@@ -2106,7 +2153,7 @@ fks_status fks_op_tiling(const fks_op* op, int precision, int64_t* fuse_max, int
 fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream, int64_t* chosen) {
   if (!op) { set_error("fks_op_autotune: NULL operator"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_op_autotune: grid operators only"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_autotune: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_autotune: bad precision"); return FKS_ERR_ARG; }
   if (!finite_c(tau)) { set_error("fks_op_autotune: tau has NaN/Inf"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
@@ -2376,7 +2423,7 @@ fks_status fks_op_amg(fks_op* op, int enable, int max_levels, int64_t max_coarse
 fks_status fks_op_amg_setup(fks_op* op, const fks_c128* tau, int n_tau, int precision, double* setup_ms) {
   if (!op || !tau || !op->csr || !op->amg.on) { set_error("fks_op_amg_setup: needs a CSR operator with AMG on"); return FKS_ERR_ARG; }
   if (n_tau < 1 || n_tau > MAX_TAU) { set_error("fks_op_amg_setup: n_tau must be in 1..16"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_amg_setup: bad precision"); return FKS_ERR_ARG; }
+  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_op_amg_setup: bad precision (the bf16 option is for grid operators)"); return FKS_ERR_ARG; }
   for (int q = 0; q < n_tau; ++q)
     if (!finite_c(tau[q])) { set_error("fks_op_amg_setup: tau has NaN/Inf"); return FKS_ERR_ARG; }
   if (!csr_diag_ok(op, tau, n_tau)) { set_error("fks_op_amg_setup: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
@@ -2571,7 +2618,7 @@ fks_status fks_precond_apply(fks_op* op, fks_c128 tau, const fks_c128* v, fks_c1
                              int cycles, int precision, int32_t* out_cycles, double* out_pnorm, void* stream) {
   if (!op || !v || !z) { set_error("fks_precond_apply: NULL argument"); return FKS_ERR_ARG; }
   if (!finite_c(tau)) { set_error("fks_precond_apply: tau has NaN/Inf"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) { set_error("fks_precond_apply: bad precision"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_precond_apply: bad precision"); return FKS_ERR_ARG; }
   if (cycles < 0 && !(eps > 0)) { set_error("fks_precond_apply: eps must be positive"); return FKS_ERR_ARG; }
   if (!csr_diag_ok(op, &tau, 1)) { set_error("fks_precond_apply: K + tau M has a zero diagonal entry"); return FKS_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
@@ -2682,7 +2729,7 @@ extern "C" fks_status fks_precond_apply_noalloc(fks_op* op, fks_c128 tau, const 
   if (!op || !v || !z) { set_error("fks_precond_apply_noalloc: NULL argument"); return FKS_ERR_ARG; }
   if (op->csr) { set_error("fks_precond_apply_noalloc: grid operators only"); return FKS_ERR_ARG; }
   if (!finite_c(tau)) { set_error("fks_precond_apply_noalloc: tau has NaN/Inf"); return FKS_ERR_ARG; }
-  if (precision != FKS_PREC_FP64 && precision != FKS_PREC_MIXED) {
+  if (!prec_ok(precision)) {
     set_error("fks_precond_apply_noalloc: bad precision");
     return FKS_ERR_ARG;
   }
@@ -3360,7 +3407,7 @@ extern "C" fks_status fks_server_submit(fks_server* sv, const fks_request* r, ui
   if (!r->op || !r->b || !r->sigma || !r->tau || !r->res_est || !r->res_bound || !r->m_j ||
       !r->shift_status || r->n_rhs < 1 || r->n_f < 1 || r->n_tau < 1 || r->n_tau > MAX_TAU ||
       o.m_max < 1 || o.m_max > MAX_M || !(o.tol > 0) || o.sched_len < 1 || !o.tau_schedule || o.replay_mode ||
-      (o.precision != FKS_PREC_FP64 && o.precision != FKS_PREC_MIXED) ||
+      !prec_ok(o.precision) || (r->op && r->op->csr && o.precision == FKS_PREC_MIXED_BF16) ||
       (o.variant != FKS_FGMRES && o.variant != FKS_FFOM) || o.inner_steps > 64 ||
       (o.assembly != 0 && o.assembly != 1) || !std::isfinite(o.inner_relax) || o.restart_len != 0) {
     set_error("fks_server_submit: bad request (restarted solves go through fks_solve)");

@@ -1,6 +1,7 @@
 // Internal types shared by the kernels and the host engine.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,16 +75,25 @@ typedef cx<float> z32;
 // boundary faces: 2 K A / h on a zero-head face, 0 on a no-flow face); likewise
 // fy with (ny+1) rows per plane and fz with (nz+1) planes. mm is the diagonal of M.
 // The diagonal of K at a cell is the sum of its 2d faces.
-template <typename T>
+// C is the storage type of the coefficients (T itself, or bf16 / float
+// copies read into T arithmetic); kd is always T.
+template <typename T, typename C = T>
 struct LevelView {
   int nx, ny, nz;
   int64_t n;
-  const T* fx;
-  const T* fy;
-  const T* fz;  // unused when nz == 1
-  const T* mm;
+  const C* fx;
+  const C* fy;
+  const C* fz;  // unused when nz == 1
+  const C* mm;
   const T* kd;  // diagonal of K (sum of the cell's faces), when precomputed; else null
 };
+
+// coefficient i of a C array in arithmetic type T
+template <typename T, typename C>
+__host__ __device__ __forceinline__ T ldc(const C* p, int64_t i) {
+  if constexpr (sizeof(C) == 2) return (T)__bfloat162float(p[i]);
+  else return (T)p[i];
+}
 
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_COARSE = 1024;
@@ -98,7 +108,26 @@ struct LevelHost {
   double* d64[4];     // fx, fy, fz, mm (device)
   float* d32[4];      // fp32 copies (device)
   double* kd64;       // diagonal of K in fp64 (finest level only; else null)
+  // the bf16-smoother option: the coefficients rounded to bf16 (d16), and the
+  // same rounded values as fp32 (d32b) for the kernels that read fp32
+  __nv_bfloat16* d16[4];
+  float* d32b[4];
 };
+
+// A view of the level's coefficients stored as C (double: d64, float: d32,
+// bf16: d16), read in arithmetic type T; no precomputed diagonal.
+template <typename T, typename C>
+inline LevelView<T, C> view_as(const LevelHost& L) {
+  LevelView<T, C> v;
+  v.nx = L.nx; v.ny = L.ny; v.nz = L.nz; v.n = L.n;
+  C* const* a;
+  if constexpr (sizeof(C) == 8) a = (C* const*)L.d64;
+  else if constexpr (sizeof(C) == 4) a = (C* const*)L.d32;
+  else a = (C* const*)L.d16;
+  v.fx = a[0]; v.fy = a[1]; v.fz = a[2]; v.mm = a[3];
+  v.kd = nullptr;
+  return v;
+}
 
 template <typename T>
 inline LevelView<T> view(const LevelHost& L) {

@@ -22,9 +22,11 @@ __device__ __forceinline__ bool csr_running(const SlotState* st, int slot) {
 template <typename T>
 __device__ __forceinline__ cx<T> csr_row(const CsrView<T>& A, int64_t row, cx<T> s, const cx<T>* __restrict__ x) {
   cx<T> acc = mk(T(0), T(0));
-  for (int64_t q = A.rowptr[row]; q < A.rowptr[row + 1]; ++q) {
-    cx<T> a = mk(fmaT(s.re, A.mv[q], A.kv[q]), mulT(s.im, A.mv[q]));
-    acc = acc + a * x[A.col[q]];
+  const int nq = A.len[row];
+  for (int q = 0; q < nq; ++q) {
+    const int64_t e = csr_at(A, row, q);
+    cx<T> a = mk(fmaT(s.re, A.mv[e], A.kv[e]), mulT(s.im, A.mv[e]));
+    acc = acc + a * x[A.col[e]];
   }
   return acc;
 }
@@ -75,7 +77,10 @@ __global__ void k_csr_mass(CsrView<double> A, const SlotState* st, const z64* __
   double a = 0.0;
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < A.n; row += (int64_t)gridDim.x * blockDim.x) {
     z64 acc = mk(0.0, 0.0);
-    for (int64_t q = A.rowptr[row]; q < A.rowptr[row + 1]; ++q) acc = axpy(A.mv[q], z[A.col[q]], acc);
+    for (int q = 0; q < A.len[row]; ++q) {
+      const int64_t e = csr_at(A, row, q);
+      acc = axpy(A.mv[e], z[A.col[e]], acc);
+    }
     w[slot * A.n + row] = acc;
     a += abs2(acc);
   }
@@ -292,9 +297,11 @@ __device__ __forceinline__ cx<T> ldcg_cx(const cx<T>* p) {
 template <typename T>
 __device__ __forceinline__ cx<T> csr_row_cg(const CsrView<T>& A, int64_t row, cx<T> s, const cx<T>* x) {
   cx<T> acc = mk(T(0), T(0));
-  for (int64_t q = A.rowptr[row]; q < A.rowptr[row + 1]; ++q) {
-    cx<T> a = mk(fmaT(s.re, A.mv[q], A.kv[q]), mulT(s.im, A.mv[q]));
-    acc = acc + a * ldcg_cx(x + A.col[q]);
+  const int nq = A.len[row];
+  for (int q = 0; q < nq; ++q) {
+    const int64_t e = csr_at(A, row, q);
+    cx<T> a = mk(fmaT(s.re, A.mv[e], A.kv[e]), mulT(s.im, A.mv[e]));
+    acc = acc + a * ldcg_cx(x + A.col[e]);
   }
   return acc;
 }

@@ -10,15 +10,28 @@ struct AmgRun;
 namespace fks {
 
 // K + s M on the union pattern of K and M: one column index and a K and an M
-// value per stored entry (zero where a matrix has no entry).
+// value per stored entry (zero where a matrix has no entry), in sliced ELL
+// order: the rows are cut into slices of CSR_SLICE consecutive rows, and
+// entry q of row r sits at sell[r / CSR_SLICE] + q * CSR_SLICE + r % CSR_SLICE
+// (q < len[r], a row's entries in ascending column order). Threads that own
+// consecutive rows then read consecutive addresses for each q.
+constexpr int CSR_SLICE = 32;
+
 template <typename T>
 struct CsrView {
   int64_t n;
-  const int64_t* rowptr;
+  const int64_t* sell;  // [n / CSR_SLICE + 1] start of each slice
+  const int32_t* len;   // [n] entries of each row
   const int32_t* col;
   const T* kv;
   const T* mv;
 };
+
+// position of entry q of row `row`
+template <typename T>
+__device__ __forceinline__ int64_t csr_at(const CsrView<T>& A, int64_t row, int q) {
+  return A.sell[row / CSR_SLICE] + (int64_t)q * CSR_SLICE + (row % CSR_SLICE);
+}
 
 // BiCGSTAB work vectors of the sources, each [nslot][n] in the cycle precision.
 template <typename T>

@@ -131,14 +131,27 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
   if (t < n) b[t] = (float)a[t];
 }
 
+// The bf16-smoother option's coefficients: a rounded to bf16 (nearest) and the
+// same value as fp32 (exact).
+__global__ void k_round_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, float* __restrict__ r,
+                             int64_t n) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const __nv_bfloat16 v = __double2bfloat16(a[t]);
+  b[t] = v;
+  r[t] = __bfloat162float(v);
+}
+
 // 1 / (K_cc + tau M_cc) per cell for every distinct tau, computed in fp64.
-template <typename T>
-__global__ void k_invd(LevelView<double> L, const z64* __restrict__ taus, int ntau, cx<T>* __restrict__ out) {
+// (C: the coefficients' storage; the bf16-smoother option computes from the
+// bf16-rounded values held as fp32)
+template <typename T, typename C>
+__global__ void k_invd(LevelView<double, C> L, const z64* __restrict__ taus, int ntau, cx<T>* __restrict__ out) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   Cell p = cell_of(c, L.nx, L.ny);
   Faces<double> f = faces_at(L, p);
-  double d = fsum(f), m = L.mm[c];
+  double d = fsum(f), m = ldc<double>(L.mm, c);
   for (int q = 0; q < ntau; ++q) {
     z64 D = mk(d + taus[q].re * m, taus[q].im * m);
     double den = abs2(D);
@@ -147,12 +160,13 @@ __global__ void k_invd(LevelView<double> L, const z64* __restrict__ taus, int nt
 }
 
 // Dense coarsest-level matrix K + tau M (row-major, n x n) for every tau.
-__global__ void k_coarse_dense(LevelView<double> L, const z64* __restrict__ taus, int ntau, z64* __restrict__ A) {
+template <typename C>
+__global__ void k_coarse_dense(LevelView<double, C> L, const z64* __restrict__ taus, int ntau, z64* __restrict__ A) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   Cell p = cell_of(c, L.nx, L.ny);
   Faces<double> f = faces_at(L, p);
-  double d = fsum(f), m = L.mm[c];
+  double d = fsum(f), m = ldc<double>(L.mm, c);
   int64_t n = L.n, sxy = (int64_t)L.nx * L.ny;
   for (int q = 0; q < ntau; ++q) {
     z64* row = A + (int64_t)q * n * n + c * n;
@@ -192,8 +206,8 @@ __global__ void k_apply(LevelView<T> L, z64 s_fixed, const SlotState* st, const 
 // other sources' warps from the SM's L1 (sources in lockstep share tau_k);
 // sources whose inner solve has finished return at once. Every source's update
 // is the single-source one.
-template <typename T>
-__global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+template <typename T, typename C>
+__global__ void k_gs(LevelView<T, C> L, const SlotState* st, const cx<T>* __restrict__ invd,
                      const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs, int color, int zero_start,
                      int nslot) {
   const int slot = blockIdx.z * blockDim.z + threadIdx.z;
@@ -215,8 +229,8 @@ __global__ void k_gs(LevelView<T> L, const SlotState* st, const cx<T>* __restric
 // e to column k - 1 of the outer iterates (z_k = e on the first cycle, z_k + e
 // after), the update of k_correct. z itself is not written: nothing reads the
 // finest level's correction after this. Sources as in k_gs.
-template <typename T>
-__global__ void k_gs_correct(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
+template <typename T, typename C>
+__global__ void k_gs_correct(LevelView<T, C> L, const SlotState* st, const cx<T>* __restrict__ invd,
                              const cx<T>* __restrict__ f, const cx<T>* __restrict__ z, int64_t vs, int color,
                              z64* __restrict__ Zk, int64_t vsZk, int64_t zcol, int nslot) {
   const int slot = blockIdx.z * blockDim.z + threadIdx.z;
@@ -248,8 +262,8 @@ __global__ void k_gs_correct(LevelView<T> L, const SlotState* st, const cx<T>* _
 // Coarse right-hand side = sum over the children of the fine residual f - A z.
 // Sources as in k_gs (threadIdx.z), so the children's coefficients come from
 // memory once per block.
-template <typename T>
-__global__ void k_residual_restrict(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz,
+template <typename T, typename C>
+__global__ void k_residual_restrict(LevelView<T, C> F, int rx, int ry, int rz, int cnx, int cny, int cnz,
                                     const SlotState* st, const z64* taus, const cx<T>* __restrict__ f,
                                     const cx<T>* __restrict__ z, int64_t vs, cx<T>* __restrict__ fc, int64_t vsc,
                                     int nslot) {
@@ -1172,14 +1186,20 @@ void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_invd(const LevelHost& L, const z64* taus, int ntau, cx<T>* out, cudaStream_t s) {
-  k_invd<T><<<nb(L.n, 256), 256, 0, s>>>(view<double>(L), taus, ntau, out);
+void launch_invd(const LevelHost& L, const z64* taus, int ntau, cx<T>* out, cudaStream_t s, int from_f32) {
+  if (from_f32) k_invd<T, float><<<nb(L.n, 256), 256, 0, s>>>(view_as<double, float>(L), taus, ntau, out);
+  else k_invd<T, double><<<nb(L.n, 256), 256, 0, s>>>(view<double>(L), taus, ntau, out);
 }
 
 void launch_coarse_inverse(const LevelHost& L, const z64* taus, int ntau, z64* work, z64* inv, int* singular,
-                           cudaStream_t s) {
-  k_coarse_dense<<<nb(L.n, 128), 128, 0, s>>>(view<double>(L), taus, ntau, work);
+                           cudaStream_t s, int from_f32) {
+  if (from_f32) k_coarse_dense<float><<<nb(L.n, 128), 128, 0, s>>>(view_as<double, float>(L), taus, ntau, work);
+  else k_coarse_dense<double><<<nb(L.n, 128), 128, 0, s>>>(view<double>(L), taus, ntau, work);
   k_gauss_jordan<<<ntau, 1024, 0, s>>>(work, inv, (int)L.n, singular);
+}
+
+void launch_round_bf16(const double* a, __nv_bfloat16* b, float* r, int64_t n, cudaStream_t s) {
+  k_round_bf16<<<nb(n, 256), 256, 0, s>>>(a, b, r, n);
 }
 
 template <typename T>
@@ -1203,24 +1223,42 @@ static int spmm_group(int nslot) {
 
 template <typename T>
 void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
-               int nslot, int color, int zero_start, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
+               int nslot, int color, int zero_start, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol, int bf16) {
   const int G = spmm_group(nslot), rb = GY / G;
   const dim3 blk(GX, rb, G), grd(nb((L.nx + 1) / 2, GX), nb((int64_t)L.ny * L.nz, rb), nb(nslot, G));
+  if constexpr (sizeof(T) == 4) {
+    if (bf16) {
+      if (Zk)
+        k_gs_correct<T, __nv_bfloat16><<<grd, blk, 0, s>>>(view_as<T, __nv_bfloat16>(L), st, invd, f, z, vs, color,
+                                                           Zk, vsZk, zcol, nslot);
+      else
+        k_gs<T, __nv_bfloat16><<<grd, blk, 0, s>>>(view_as<T, __nv_bfloat16>(L), st, invd, f, z, vs, color,
+                                                   zero_start, nslot);
+      return;
+    }
+  }
   if (Zk) {
-    k_gs_correct<T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, Zk, vsZk, zcol, nslot);
+    k_gs_correct<T, T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, Zk, vsZk, zcol, nslot);
     return;
   }
-  k_gs<T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, zero_start, nslot);
+  k_gs<T, T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, zero_start, nslot);
 }
 
 template <typename T>
 void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
                               const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
-                              cudaStream_t s) {
+                              cudaStream_t s, int bf16) {
   const int G = spmm_group(nslot), rb = GY / G;
   const dim3 blk(GX, rb, G), grd(nb(C.nx, GX), nb((int64_t)C.ny * C.nz, rb), nb(nslot, G));
-  k_residual_restrict<T><<<grd, blk, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
-                                             vsc, nslot);
+  if constexpr (sizeof(T) == 4) {
+    if (bf16) {
+      k_residual_restrict<T, __nv_bfloat16><<<grd, blk, 0, s>>>(view_as<T, __nv_bfloat16>(F), F.rx, F.ry, F.rz, C.nx,
+                                                                C.ny, C.nz, st, taus, f, z, vs, fc, vsc, nslot);
+      return;
+    }
+  }
+  k_residual_restrict<T, T><<<grd, blk, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
+                                                vsc, nslot);
 }
 
 template <typename T>
@@ -1369,15 +1407,15 @@ void launch_inner_decide(SlotState* st, int nslot, const double* partial, int nb
                                  cudaStream_t, z64*, int64_t, int64_t);                                           \
   template void tail_prepare<T>(size_t);                                                                          \
   template void launch_tail<T>(const TailParams<T>&, size_t, const SlotState*, int, cudaStream_t);                \
-  template void launch_invd<T>(const LevelHost&, const z64*, int, cx<T>*, cudaStream_t);                          \
+  template void launch_invd<T>(const LevelHost&, const z64*, int, cx<T>*, cudaStream_t, int);                     \
   template void launch_to_prec<T>(const z64*, cx<T>*, int64_t, cudaStream_t);                                     \
   template void launch_apply<T>(const LevelHost&, z64, const SlotState*, const z64*, const cx<T>*, cx<T>*, int64_t, \
                                 int, cudaStream_t);                                                               \
   template void launch_gs<T>(const LevelHost&, const SlotState*, const cx<T>*, const cx<T>*, cx<T>*, int64_t, int,  \
-                             int, int, cudaStream_t, z64*, int64_t, int64_t);                                     \
+                             int, int, cudaStream_t, z64*, int64_t, int64_t, int);                                \
   template void launch_residual_restrict<T>(const LevelHost&, const LevelHost&, const SlotState*, const z64*,      \
                                             const cx<T>*, const cx<T>*, int64_t, cx<T>*, int64_t, int,           \
-                                            cudaStream_t);                                                        \
+                                            cudaStream_t, int);                                                   \
   template void launch_prolong_add<T>(const LevelHost&, const LevelHost&, uint32_t, const SlotState*,             \
                                       const cx<T>*, int64_t, cx<T>*, int64_t, int, cudaStream_t);                 \
   template void launch_coarse_solve<T>(const cx<T>*, int, const SlotState*, const cx<T>*, cx<T>*, int64_t, int,    \

@@ -77,10 +77,14 @@ bool tail2d_ok(const std::vector<LevelHost>& Ls, int lt);
 void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond, cudaStream_t s);
 void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s);
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+// from_f32: from the level's fp32 coefficients (the bf16-smoother option's
+// rounded values) instead of its fp64 ones
 template <typename T>
-void launch_invd(const LevelHost& L, const z64* taus, int ntau, cx<T>* out, cudaStream_t s);
+void launch_invd(const LevelHost& L, const z64* taus, int ntau, cx<T>* out, cudaStream_t s, int from_f32 = 0);
 void launch_coarse_inverse(const LevelHost& L, const z64* taus, int ntau, z64* work, z64* inv, int* singular,
-                           cudaStream_t s);
+                           cudaStream_t s, int from_f32 = 0);
+// b = a rounded to bf16, r = the same value as fp32
+void launch_round_bf16(const double* a, __nv_bfloat16* b, float* r, int64_t n, cudaStream_t s);
 template <typename T>
 void launch_to_prec(const z64* a, cx<T>* b, int64_t n, cudaStream_t s);
 template <typename T>
@@ -92,11 +96,11 @@ void launch_apply(const LevelHost& L, z64 sfix, const SlotState* st, const z64* 
 template <typename T>
 void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const cx<T>* f, cx<T>* z, int64_t vs,
                int nslot, int color, int zero_start, cudaStream_t s, z64* Zk = nullptr, int64_t vsZk = 0,
-               int64_t zcol = 0);
+               int64_t zcol = 0, int bf16 = 0);
 template <typename T>
 void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const SlotState* st, const z64* taus,
                               const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
-                              cudaStream_t s);
+                              cudaStream_t s, int bf16 = 0);
 template <typename T>
 void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* zc,
                         int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s);

@@ -57,19 +57,19 @@ struct Faces {
   T xl, xh, yl, yh, zl, zh;
 };
 
-template <typename T>
-__device__ __forceinline__ Faces<T> faces_at(const LevelView<T>& L, Cell p) {
+template <typename T, typename C>
+__device__ __forceinline__ Faces<T> faces_at(const LevelView<T, C>& L, Cell p) {
   Faces<T> f;
   int64_t rx = ((int64_t)p.k * L.ny + p.j) * (L.nx + 1) + p.i;
-  f.xl = L.fx[rx];
-  f.xh = L.fx[rx + 1];
+  f.xl = ldc<T>(L.fx, rx);
+  f.xh = ldc<T>(L.fx, rx + 1);
   int64_t ry = ((int64_t)p.k * (L.ny + 1) + p.j) * L.nx + p.i;
-  f.yl = L.fy[ry];
-  f.yh = L.fy[ry + L.nx];
+  f.yl = ldc<T>(L.fy, ry);
+  f.yh = ldc<T>(L.fy, ry + L.nx);
   if (L.nz > 1) {
     int64_t rz = ((int64_t)p.k * L.ny + p.j) * L.nx + p.i;
-    f.zl = L.fz[rz];
-    f.zh = L.fz[rz + (int64_t)L.nx * L.ny];
+    f.zl = ldc<T>(L.fz, rz);
+    f.zh = ldc<T>(L.fz, rz + (int64_t)L.nx * L.ny);
   } else {
     f.zl = T(0);
     f.zh = T(0);
@@ -83,8 +83,8 @@ __device__ __forceinline__ T fsum(const Faces<T>& f) {
 }
 
 // s0 + sum over existing neighbours of t_face * x_nb (accumulated in this order)
-template <typename T>
-__device__ __forceinline__ cx<T> nb_sum(const LevelView<T>& L, const Faces<T>& f, Cell p, int64_t c,
+template <typename T, typename C>
+__device__ __forceinline__ cx<T> nb_sum(const LevelView<T, C>& L, const Faces<T>& f, Cell p, int64_t c,
                                         const cx<T>* __restrict__ x, cx<T> s0 = cx<T>{T(0), T(0)}) {
   cx<T> s = s0;
   int64_t sxy = (int64_t)L.nx * L.ny;
@@ -99,12 +99,12 @@ __device__ __forceinline__ cx<T> nb_sum(const LevelView<T>& L, const Faces<T>& f
   return s;
 }
 
-template <typename T>
-__device__ __forceinline__ cx<T> apply_at(const LevelView<T>& L, Cell p, int64_t c, cx<T> s,
+template <typename T, typename C>
+__device__ __forceinline__ cx<T> apply_at(const LevelView<T, C>& L, Cell p, int64_t c, cx<T> s,
                                           const cx<T>* __restrict__ x) {
   Faces<T> f = faces_at(L, p);
   T d = L.kd ? L.kd[c] : fsum(f);  // same sum either way
-  T m = L.mm[c];
+  T m = ldc<T>(L.mm, c);
   cx<T> diag = mk(fmaT(s.re, m, d), mulT(s.im, m));
   return diag * x[c] - nb_sum(L, f, p, c, x);
 }
@@ -112,8 +112,8 @@ __device__ __forceinline__ cx<T> apply_at(const LevelView<T>& L, Cell p, int64_t
 // v_c - ((K + tau M) x)_c with diag = K_cc + tau M_cc given: the neighbour
 // terms accumulate onto v, then diag * x_c is subtracted with fused
 // multiply-adds (fewer FP64 operations than v - apply_at).
-template <typename T>
-__device__ __forceinline__ cx<T> defect_at(const LevelView<T>& L, Cell p, int64_t c, cx<T> diag, cx<T> v,
+template <typename T, typename C>
+__device__ __forceinline__ cx<T> defect_at(const LevelView<T, C>& L, Cell p, int64_t c, cx<T> diag, cx<T> v,
                                            const cx<T>* __restrict__ x) {
   Faces<T> f = faces_at(L, p);
   cx<T> acc = nb_sum(L, f, p, c, x, v);
@@ -125,8 +125,8 @@ __device__ __forceinline__ cx<T> defect_at(const LevelView<T>& L, Cell p, int64_
 
 // Red-black Gauss-Seidel update of cell c: (f_c + sum_nb t z_nb) / (K_cc + tau M_cc),
 // the neighbours taken as zero when `zero_start`.
-template <typename T>
-__device__ __forceinline__ cx<T> gs_value(const LevelView<T>& L, Cell p, int64_t c, cx<T> id, const cx<T>* f,
+template <typename T, typename C>
+__device__ __forceinline__ cx<T> gs_value(const LevelView<T, C>& L, Cell p, int64_t c, cx<T> id, const cx<T>* f,
                                           const cx<T>* z, int zero_start) {
   cx<T> rhs = f[c];
   if (!zero_start) {
@@ -152,8 +152,8 @@ __device__ __forceinline__ bool color_cell(int nx, int ny, int nz, int color, in
 }
 
 // Sum over the children of coarse cell (I,J,K) of the fine residual f - (K + s M) z.
-template <typename T>
-__device__ __forceinline__ cx<T> restrict_value(const LevelView<T>& F, int rx, int ry, int rz, int I, int J, int K,
+template <typename T, typename C>
+__device__ __forceinline__ cx<T> restrict_value(const LevelView<T, C>& F, int rx, int ry, int rz, int I, int J, int K,
                                                 cx<T> s, const cx<T>* f, const cx<T>* z) {
   cx<T> acc = mk(T(0), T(0));
   for (int c = 0; c < rz; ++c)

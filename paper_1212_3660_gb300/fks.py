@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fks.h")
 FKS_OK, FKS_NOT_CONVERGED, FKS_BREAKDOWN_EXACT, FKS_INNER_NOT_CONVERGED = 0, 1, 2, 3
 FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1, -2, -3, -4, -5
 FKS_FGMRES, FKS_FFOM = 0, 1
-FKS_PREC_FP64, FKS_PREC_MIXED = 0, 1
+FKS_PREC_FP64, FKS_PREC_MIXED, FKS_PREC_MIXED_BF16 = 0, 1, 2
 KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
                   "assemble", "tres", "tail", "pre2d", "post2d", "bicgstab", "cluster", "pre3d", "post3d"]
 

@@ -174,7 +174,7 @@ def test_graph_and_host_driven_loops_agree_bitwise(precision):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED, fks.FKS_PREC_MIXED_BF16])
 def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
     """Fused 2D tile kernels and per-half-sweep kernels perform the same
     operations in the same order; the autotuner's choice cannot change results."""
@@ -207,7 +207,7 @@ def test_fused_and_per_sweep_kernels_agree_bitwise(precision):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED, fks.FKS_PREC_MIXED_BF16])
 @pytest.mark.parametrize("shape,n_src", [((20, 24, 40), 1), ((32, 48, 32), 2)])
 def test_fused_3d_levels_agree_bitwise(precision, shape, n_src):
     """The 3D z-march kernels (four half sweeps, residual and restriction, or
@@ -406,4 +406,27 @@ def test_replay_parity_beyond_64_steps(precision):
     tol = 1e-8 if precision == fks.FKS_PREC_FP64 else 1e-6
     for j in range(len(pr.sigma)):
         assert rel_err(out.X[0, j], ref.x[:, j]) <= tol, j
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(128, 96), (24, 32, 40)])
+def test_bf16_smoother_option_certifies_every_shift(shape):
+    """The bf16-smoother option (multigrid coefficients rounded to bf16 inside
+    the complex64 cycle, complex128 defect correction with the exact operator):
+    free-running solves reach the 1e-8 true residual for every shift, checked
+    with the oracle's own operator, and x_j agree with the complex128 solve
+    within what the tolerance allows."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=12, periods=(5.0, 3600.0), n_p=3, seed=48, m_max=100,
+                            corr_frac=(0.2, 0.2, 0.05) if len(shape) == 3 else (0.2, 0.2, 0.2))
+    s = Solver(pr)
+    out = s.solve(precision=fks.FKS_PREC_MIXED_BF16, inner_tol=1e-10, inner_relax=0.003)
+    assert out.status == fks.FKS_OK
+    op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+    tr = oracle.true_residuals(op, pr.rhs()[:, 0], pr.sigma, out.X[0].T)
+    assert np.all(tr <= pr.tol * 1.0001), tr.max()
+    assert np.allclose(tr, out.res_true[0], rtol=1e-6, atol=1e-15)
+    ref = s.solve(precision=fks.FKS_PREC_FP64, inner_tol=1e-10)
+    for j in range(len(pr.sigma)):
+        assert rel_err(out.X[0, j], ref.X[0, j]) <= 1e-5, j
     s.close()
