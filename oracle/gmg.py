@@ -15,9 +15,15 @@ specification independently:
            MAX_COARSE cells, an odd axis with n_a > 4 also coarsens, to
            (n_a + 1) / 2 cells, children 2I and 2I + 1 except the last coarse
            cell, whose only child is the last fine cell.
-  coarse   face transmissibility = (sum of the fine faces on the coarse face) / r_a,
-           boundary faces alike (a ragged axis: the last coarse cell's high face
-           is its lone child's high face); coarse storage = sum of the children.
+  coarse   face transmissibility = (sum of the fine faces on the coarse face)
+           x (fine centre distance across it) / (coarse centre distance), the
+           distances from the cell widths in fine cells (a zero-head boundary face:
+           the half widths); on evenly halved axes this is the sum / r_a. A ragged
+           axis's last coarse cell keeps its lone child's width, so its faces are
+           those of a two-point flux discretisation on the non-uniform coarse
+           cells (a plain / r_a there made V-cycles diverge on grids like 289^2,
+           whose one-cell-wide edge cells persist through several levels).
+           Coarse storage = sum of the children.
   R        restriction = sum of the children.
   P        prolongation = cell-centred (bi/tri)linear interpolation, weights 3/4
            and 1/4 per coarsened axis; beyond a zero-head face the coarse ghost
@@ -76,6 +82,24 @@ def _coarsen_sum(arr, r, sel_q=None, sel_off=None):
     if sel_q is not None:
         x = np.take(x, [sel_off], axis=2 * sel_q + 1)
     return x.sum(axis=tuple(2 * q + 1 for q in range(d)))
+
+
+def _face_factors(w, r):
+    """Per coarse cell along one axis, the factors of its low and high faces
+    (fine centre distance / coarse centre distance, or half widths at the
+    boundary), and the coarse widths; w = fine cell widths in finest cells."""
+    n = len(w)
+    if r == 1:
+        return np.ones(n), np.ones(n), w.copy()
+    nc = (n + 1) // 2
+    W = np.array([w[2 * I:2 * I + 2].sum() for I in range(nc)])
+    lo = np.empty(nc)
+    hi = np.empty(nc)
+    for I in range(nc):
+        first, last = 2 * I, min(2 * I + 1, n - 1)
+        lo[I] = w[first] / W[I] if I == 0 else (w[first - 1] + w[first]) / (W[I - 1] + W[I])
+        hi[I] = w[last] / W[I] if I == nc - 1 else (w[last] + w[last + 1]) / (W[I] + W[I + 1])
+    return lo, hi, W
 
 
 def _prolong_1d(n_f, n_c, r, dirichlet_lo, dirichlet_hi):
@@ -146,17 +170,22 @@ class Hierarchy:
         d = len(op.shape)
         lev = Level(op.shape, op.h, op.t_lo, op.t_hi, op.m_diag, op.dirichlet_mask)
         self.levels = [lev]
+        widths = [np.ones(s) for s in op.shape]   # per numpy axis, in finest cells
         while True:
             r = _ratios(lev.shape, ragged)
             if all(x == 1 for x in r):
                 break
             cshape = tuple((s + x - 1) // x for s, x in zip(lev.shape, r))
             ch = tuple(lev.h[a] * r[d - 1 - a] for a in range(d))
+            facs = [_face_factors(widths[q], r[q]) for q in range(d)]
+            widths = [f[2] for f in facs]
             t_lo, t_hi = [], []
             for a in range(d):
                 q = d - 1 - a
-                t_lo.append(_coarsen_sum(lev.t_lo[a], r, q, 0) / r[q])
-                t_hi.append(_coarsen_sum(lev.t_hi[a], r, q, r[q] - 1) / r[q])
+                shp = [1] * d
+                shp[q] = cshape[q]
+                t_lo.append(_coarsen_sum(lev.t_lo[a], r, q, 0) * facs[q][0].reshape(shp))
+                t_hi.append(_coarsen_sum(lev.t_hi[a], r, q, r[q] - 1) * facs[q][1].reshape(shp))
             cm = _coarsen_sum(lev.m.reshape(lev.shape), r)
             clev = Level(cshape, ch, t_lo, t_hi, cm, op.dirichlet_mask)
             p1 = []

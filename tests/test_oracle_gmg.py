@@ -41,21 +41,23 @@ def test_level_shapes_ragged(shape, expect):
     assert hier.levels[-1].n <= 1024
 
 
-@pytest.mark.parametrize("shape", [(70, 90), (30, 50, 50)])
+@pytest.mark.parametrize("shape", [(70, 90), (30, 50, 50), (289, 40)])
 def test_ragged_levels_homogeneous_geometry(shape):
-    """Coarse levels of a homogeneous medium on ragged hierarchies. A coarse
-    cell covers w_q fine cells along axis q (1D: children summed, the one-child
-    cell of an odd axis covering one fewer); against the uniform
-    re-discretisation with spacing W_q = h_q(level) / h_q(0) fine cells, every
-    face along axis q has area prod_{q' != q} w_q' / W_q' times the uniform one
-    and every storage prod_q w_q / W_q. R sums each fine cell into exactly one
-    coarse cell, and with no-flow faces every row of P sums to 1."""
+    """Coarse levels of a homogeneous medium on ragged hierarchies are the
+    two-point flux discretisation on the coarse cells, whose widths are the
+    numbers of finest cells they cover (1D: children summed; the one-child cell
+    of an odd axis keeps its child's width): a face along axis q joins cells of
+    widths W1, W2 over the distance (W1 + W2) h_q / 2 and has the area of the
+    other axes' widths; a zero-head face sits half a width away; storage is
+    S_s times the cell volume. R sums each fine cell into exactly one coarse
+    cell, and with no-flow faces every row of P sums to 1."""
     d = len(shape)
-    h = (2.0, 1.0, 0.5)[:d]
+    h = (2.0, 1.0, 0.5)[:d]          # per grid axis a (x first)
+    K0, S0 = 2e-4, 3e-5
     for mask in (0, (1 << 2 * d) - 1):
-        op = oracle.assemble(shape, h, np.full(shape, 2e-4), np.full(shape, 3e-5), mask)
+        op = oracle.assemble(shape, h, np.full(shape, K0), np.full(shape, S0), mask)
         hier = Hierarchy(op, [0.1j])
-        widths = [np.ones(n) for n in shape]   # per numpy axis, in level-0 cells
+        widths = [np.ones(n) for n in shape]   # per numpy axis q, in finest cells
         ragged_seen = False
         for F, L in zip(hier.levels[:-1], hier.levels[1:]):
             for q in range(d):
@@ -63,46 +65,52 @@ def test_ragged_levels_homogeneous_geometry(shape):
                     w = widths[q]
                     ragged_seen |= len(w) % 2 == 1
                     widths[q] = np.array([w[2 * I:2 * I + 2].sum() for I in range(L.shape[q])])
-            ref = oracle.assemble(L.shape, L.h, np.full(L.shape, 2e-4), np.full(L.shape, 3e-5), mask)
-            frac = []
-            for q in range(d):
-                a = d - 1 - q
-                W = L.h[a] / h[a]
-                shp = [1] * d
-                shp[q] = L.shape[q]
-                frac.append((widths[q] / W).reshape(shp))
+            hq = [h[d - 1 - q] for q in range(d)]     # spacing of numpy axis q
+            grids = np.meshgrid(*[widths[q] * hq[q] for q in range(d)], indexing="ij")
+            vol = np.prod(grids, axis=0)
             for a in range(d):
                 q = d - 1 - a
-                scale = np.ones(L.shape)
-                for q2 in range(d):
-                    if q2 != q:
-                        scale = scale * frac[q2]
-                assert np.allclose(L.t_lo[a], ref.t_lo[a] * scale, rtol=1e-14, atol=0)
-                assert np.allclose(L.t_hi[a], ref.t_hi[a] * scale, rtol=1e-14, atol=0)
-            mscale = np.ones(L.shape)
-            for q in range(d):
-                mscale = mscale * frac[q]
-            assert np.allclose(L.m.reshape(L.shape), ref.m_diag.reshape(L.shape) * mscale, rtol=1e-14)
+                area = vol / grids[q]
+                W = widths[q] * hq[q]
+                shp = [1] * d
+                shp[q] = L.shape[q]
+                Wl = np.concatenate([[np.nan], W[:-1]]).reshape(shp)   # low neighbour's width
+                Wh = np.concatenate([W[1:], [np.nan]]).reshape(shp)    # high neighbour's width
+                Wc = W.reshape(shp)
+                lo = K0 * area / ((Wl + Wc) / 2)
+                hi = K0 * area / ((Wc + Wh) / 2)
+                first = [slice(None)] * d
+                first[q] = 0
+                last = [slice(None)] * d
+                last[q] = L.shape[q] - 1
+                lo[tuple(first)] = (K0 * area / (Wc / 2))[tuple(first)] if (mask >> (2 * a)) & 1 else 0.0
+                hi[tuple(last)] = (K0 * area / (Wc / 2))[tuple(last)] if (mask >> (2 * a + 1)) & 1 else 0.0
+                assert np.allclose(L.t_lo[a], lo, rtol=1e-13, atol=0), (L.shape, a)
+                assert np.allclose(L.t_hi[a], hi, rtol=1e-13, atol=0), (L.shape, a)
+            assert np.allclose(L.m.reshape(L.shape), S0 * vol, rtol=1e-13)
             assert np.array_equal(np.asarray(F.R.sum(axis=0)).ravel(), np.ones(F.n))
             if mask == 0:
                 assert np.allclose(np.asarray(F.P.sum(axis=1)).ravel(), 1.0, rtol=0, atol=1e-15)
         assert ragged_seen
 
 
-@pytest.mark.parametrize("shape", [(66, 70), (18, 22, 26)])
+@pytest.mark.parametrize("shape", [(66, 70), (18, 22, 26), (289, 289)])
 def test_ragged_hierarchy_contracts_and_solves(shape):
-    """Measured V-cycle contraction on ragged hierarchies (a wrong child, face or
-    weight at the one-child slabs shows as a slow or divergent cycle), and the
-    solve against sparse LU within ||A^-1|| ||p||."""
+    """Measured V-cycle contraction on ragged hierarchies for every tau of a
+    synthetic log-normal aquifer (a wrong child, face or weight at the one-child
+    cells shows as a slow or divergent cycle; 289^2 keeps one-cell-wide edge
+    cells through four levels), and the solve against sparse LU."""
+    from paper_1212_3660_gb300 import synth
     d = len(shape)
-    op = oracle.assemble(shape, (500.0 / shape[-1],) * d, np.full(shape, 1e-4), np.full(shape, 1e-5),
-                         (1 << 2 * d) - 1)
-    tau = 2j * np.pi / 100
-    hier = Hierarchy(op, [tau])
+    pr = synth.make_problem(shape, n_f=10, periods=(5.0, 3600.0), n_p=3, seed=20000)
+    op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+    hier = Hierarchy(op, pr.tau_bar)
     v = np.random.default_rng(1).standard_normal(op.n) + 0j
-    _, _, p1 = hier.solve(v, 0, 0.0, cycles=2)
-    _, _, p2 = hier.solve(v, 0, 0.0, cycles=6)
-    assert (p2 / p1) ** 0.25 <= 0.25
+    for p in range(len(pr.tau_bar)):
+        _, _, p1 = hier.solve(v, p, 0.0, cycles=2)
+        _, _, p2 = hier.solve(v, p, 0.0, cycles=6)
+        assert (p2 / p1) ** 0.25 <= 0.25, p
+    tau = pr.tau_bar[0]
     v /= np.linalg.norm(v)
     z, c, pn = hier.solve(v, 0, 1e-10)
     assert pn <= 1e-10
