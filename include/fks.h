@@ -78,7 +78,10 @@ const char* fks_version(void);
  *  dirichlet_mask bit 2a: low face of axis a is zero-head; bit 2a+1: high face
  *  out            receives the operator (owned by the library; free with fks_op_destroy)
  * The multigrid hierarchy is built here: axis a is halved while n_a is even and
- * n_a > 4; the coarsest level must hold at most 1024 cells (else FKS_ERR_ARG).
+ * n_a > 4. If that hierarchy ends above 1024 cells (the largest coarsest level
+ * solved exactly), it is built again with odd axes > 4 also halved, to
+ * (n_a + 1) / 2 cells (the last coarse cell having one child), while a level
+ * has more than 1024 cells. FKS_ERR_ARG only if that needs more than 16 levels.
  */
 fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const double h[3],
                        const double* cond, const double* ss, uint32_t dirichlet_mask,
@@ -449,6 +452,17 @@ fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells);
  * depend on it. Grid operators only.
  */
 fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes);
+/*
+ * Launch overlap (no counterpart in the paper): the multigrid and defect
+ * kernels are launched with programmatic dependent launch, so that each one's
+ * blocks are scheduled while its predecessor finishes (they wait for the
+ * predecessor's results before reading memory). on = 1 (the default) or 0 sets
+ * it for the whole process; a negative value only queries. Returns the previous
+ * setting. Results are the same bits either way; graphs built before a change
+ * are rebuilt at their next use. If a graph capture refuses the overlap, the
+ * library switches it off by itself.
+ */
+int fks_set_pdl(int on);
 /* The z-chunk of every multigrid level of `precision` (planes[0 .. levels-1],
  * as fks_op_set_zchunk stores them); *levels receives the level count. */
 fks_status fks_op_zchunks(const fks_op* op, int precision, int32_t* planes, int cap, int* levels);

@@ -5,9 +5,11 @@
 // k_tc_gemm: one CTA per (32-column tile, 128-row tile, source); one thread
 // streams 16-wide k' slabs of all slices into shared memory with bulk async
 // copies (two stages, mbarrier transaction counts) and issues the 36
-// tcgen05.mma per slab into eight TMEM accumulators; then four warps read the
-// accumulators with tcgen05.ld and write x_j. Every wait on an mbarrier gives
-// up after two seconds, sets the error flag and still releases TMEM.
+// tcgen05.mma per slab into eight TMEM accumulators; after each chunk of at
+// most 8 slabs four warps read the accumulators with tcgen05.ld into 64-bit
+// totals (the copies of the next chunk's first slab already in flight), and
+// after the last chunk write x_j. Every wait on an mbarrier gives up after two
+// seconds, sets the error flag and still releases TMEM.
 #include <algorithm>
 
 #include "assemble_tc.cuh"
@@ -135,6 +137,43 @@ __device__ __forceinline__ void digits7(double v, int e, int (&d)[TC_SLICES]) {
   for (int s = 0; s < TC_SLICES; ++s) d[s] = sg * (int)((X >> (49 - 7 * s)) & 127ull);
 }
 
+// (hi + lo 2^-28) 2^E rounded to the nearest double (ties to even), with integer
+// instructions only: N = hi 2^28 + lo is exact in 128 bits (|hi| < 2^47), its
+// leading 53 bits are rounded by the bits below them, and the exponent is set
+// directly. Equal to scalbn(fma((double)lo, 0x1p-28, (double)hi), E) whenever
+// the result is a normal double; returns false otherwise (the caller then takes
+// that FP64 form).
+__device__ __forceinline__ bool int_to_double(long long hi, long long lo, int E, double* out) {
+  const __int128 N = ((__int128)hi << 28) + (__int128)lo;
+  if (N == 0) {
+    *out = 0.0;
+    return true;
+  }
+  const unsigned long long sign = N < 0 ? 1ull : 0ull;
+  const unsigned __int128 u = N < 0 ? (unsigned __int128)(-N) : (unsigned __int128)N;
+  const unsigned long long uh = (unsigned long long)(u >> 64), ul = (unsigned long long)u;
+  const int p = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);  // leading bit
+  unsigned long long m;
+  int ex = p;
+  if (p <= 52) {
+    m = ul << (52 - p);
+  } else {
+    const int sh = p - 52;  // 1 .. 75
+    const unsigned __int128 q = u >> sh;
+    const unsigned __int128 rem = u - (q << sh), half = (unsigned __int128)1 << (sh - 1);
+    m = (unsigned long long)q;
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      ++ex;
+    }
+  }
+  const int be = ex + E - 28 + 1023;
+  if (be < 1 || be > 2046) return false;
+  *out = __longlong_as_double((long long)((sign << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
+  return true;
+}
+
 // bf16 bits of a small integer (exact: at most 8 significant bits)
 __device__ __forceinline__ uint32_t bf16_of(int d) { return __float_as_uint((float)d) >> 16; }
 
@@ -257,64 +296,78 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const SlotState* __restrict_
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp == 0 && lane == 0) {
-    const unsigned char* asrc = As + (size_t)(slot * nrt + rt) * nslab * TC_A_SLAB;
-    const unsigned char* bsrc = Bs + (size_t)(slot * nct + ct) * nslab * TC_B_SLAB;
-    constexpr uint32_t idesc = mma_idesc();
-    bool ok = true;
-    int loaded = 1, consumed = 0;
+  const unsigned char* asrc = As + (size_t)(slot * nrt + rt) * nslab * TC_A_SLAB;
+  const unsigned char* bsrc = Bs + (size_t)(slot * nct + ct) * nslab * TC_B_SLAB;
+  const bool issuer = warp == 0 && lane == 0;
+  // issuer state across chunks: slabs whose copies were started / consumed
+  bool ok = true;
+  int loaded = 0, consumed = 0;
+  if (issuer) {
     mbar_expect_tx(full0, STAGE_BYTES);
     bulk_g2s(sbase, asrc, TC_A_SLAB, full0);
     bulk_g2s(sbase + TC_A_SLAB, bsrc, TC_B_SLAB, full0);
-    uint32_t started = 0;  // accumulators already written
-    for (int q = 0; q < nslab; ++q) {
-      const int st = q & 1;
-      if (q + 1 < nslab) {
-        const int ns = (q + 1) & 1;
-        // the stage is free once the MMAs of slab q - 1 completed
-        if (q + 1 >= 2 && !mbar_wait(free0 + 8 * ns, ((q + 1) / 2 - 1) & 1)) { ok = false; break; }
-        const uint32_t dst = sbase + ns * STAGE_BYTES, fb = full0 + 8 * ns;
-        mbar_expect_tx(fb, STAGE_BYTES);
-        bulk_g2s(dst, asrc + (size_t)(q + 1) * TC_A_SLAB, TC_A_SLAB, fb);
-        bulk_g2s(dst + TC_A_SLAB, bsrc + (size_t)(q + 1) * TC_B_SLAB, TC_B_SLAB, fb);
-        ++loaded;
-      }
-      if (!mbar_wait(full0 + 8 * st, (q / 2) & 1)) { ok = false; break; }
-      ++consumed;
-      tc_fence_after();
-      const uint32_t a0 = sbase + st * STAGE_BYTES, b0 = a0 + TC_A_SLAB;
+    loaded = 1;
+  }
+  constexpr int SPC = TC_CHUNK_KP / TC_KSLAB;  // slabs per chunk
+  const int nchunk = (nslab + SPC - 1) / SPC;
+  // 64-bit totals of this thread's row: levels 0-3 (hi) and 4-7 (lo), 32 columns
+  long long thi[2][16], tlo[2][16];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) thi[h][c] = tlo[h][c] = 0;
+  const int r = warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-      for (int s = 0; s < TC_SLICES; ++s)
-#pragma unroll 1
-        for (int t = 0; s + t < TC_SLICES; ++t) {
-          const int lev = s + t;
-          mma_bf16(tmem + (uint32_t)(lev * TC_N), smem_desc(a0 + s * (TC_A_SLAB / TC_SLICES), 128, 256),
-                   smem_desc(b0 + t * (TC_B_SLAB / TC_SLICES), 128, 256), idesc, (started >> lev) & 1u);
-          started |= 1u << lev;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    if (issuer && ok) {
+      constexpr uint32_t idesc = mma_idesc();
+      const int q1 = min(nslab, (ch + 1) * SPC);
+      uint32_t started = 0;  // accumulators already written in this chunk
+      for (int q = ch * SPC; q < q1; ++q) {
+        const int sg = q & 1;
+        if (q + 1 < nslab) {
+          const int ns = (q + 1) & 1;
+          // the stage is free once the MMAs of slab q - 1 completed
+          if (q + 1 >= 2 && !mbar_wait(free0 + 8 * ns, ((q + 1) / 2 - 1) & 1)) { ok = false; break; }
+          const uint32_t dst = sbase + ns * STAGE_BYTES, fb = full0 + 8 * ns;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          bulk_g2s(dst, asrc + (size_t)(q + 1) * TC_A_SLAB, TC_A_SLAB, fb);
+          bulk_g2s(dst + TC_A_SLAB, bsrc + (size_t)(q + 1) * TC_B_SLAB, TC_B_SLAB, fb);
+          ++loaded;
         }
-      mma_commit(free0 + 8 * st);
-    }
-    mma_commit(done);
-    if (!ok) {
-      atomicExch(err, 1);
-      *sfail = 1;
-      // let copies still in flight land before the CTA exits
-      for (int q = consumed; q < loaded; ++q) mbar_wait(full0 + 8 * (q & 1), (q / 2) & 1);
-    }
-  }
-  if (warp == 0) __syncwarp();  // the other lanes of the issuing warp wait here, not in a spin
-  if (!mbar_wait(done, 0)) {
-    atomicExch(err, 2);
-    *sfail = 1;
-  }
-  __syncthreads();
-  tc_fence_after();
-  if (*sfail == 0) {  // uniform over the CTA: tcgen05.ld is executed by whole warps
-    const int r = warp * 32 + lane;
-    const int64_t i = (int64_t)rt * TC_M + r;
-    const int e = erow[((int64_t)slot * nrt + rt) * TC_M + r];
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        if (!mbar_wait(full0 + 8 * sg, (q / 2) & 1)) { ok = false; break; }
+        ++consumed;
+        tc_fence_after();
+        const uint32_t a0 = sbase + sg * STAGE_BYTES, b0 = a0 + TC_A_SLAB;
 #pragma unroll 1
+        for (int s = 0; s < TC_SLICES; ++s)
+#pragma unroll 1
+          for (int t = 0; s + t < TC_SLICES; ++t) {
+            const int lev = s + t;
+            mma_bf16(tmem + (uint32_t)(lev * TC_N), smem_desc(a0 + s * (TC_A_SLAB / TC_SLICES), 128, 256),
+                     smem_desc(b0 + t * (TC_B_SLAB / TC_SLICES), 128, 256), idesc, (started >> lev) & 1u);
+            started |= 1u << lev;
+          }
+        mma_commit(free0 + 8 * sg);
+      }
+      if (!ok) {
+        atomicExch(err, 1);
+        *sfail = 1;
+        // let copies still in flight land before the CTA exits
+        for (int q = consumed; q < loaded; ++q) mbar_wait(full0 + 8 * (q & 1), (q / 2) & 1);
+      }
+      mma_commit(done);  // arrives once every MMA issued so far has completed
+    }
+    if (warp == 0) __syncwarp();  // the other lanes of the issuing warp wait here, not in a spin
+    if (!mbar_wait(done, ch & 1)) {
+      atomicExch(err, 2);
+      *sfail = 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (*sfail != 0) break;  // uniform over the CTA: tcgen05.ld is executed by whole warps
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       long long hi[16], lo[16];
 #pragma unroll
@@ -330,21 +383,35 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const SlotState* __restrict_
           else lo[c] = lo[c] * 128 + a;
         }
       }
-      if (i < n) {
 #pragma unroll
-        for (int c = 0; c < 16; c += 2) {
-          const int jp = ct * TC_N + h * 16 + c;
-          const int j = jp >> 1;
-          if (j >= nf) break;
+      for (int c = 0; c < 16; ++c) {
+        thi[h][c] += hi[c];
+        tlo[h][c] += lo[c];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // the accumulators are read: the next chunk may overwrite them
+  }
+  const int64_t i = (int64_t)rt * TC_M + r;
+  if (*sfail == 0 && i < n) {
+    const int e = erow[((int64_t)slot * nrt + rt) * TC_M + r];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) {
+        const int jp = ct * TC_N + h * 16 + c;
+        const int j = jp >> 1;
+        if (j < nf) {
           const int f0 = ecol[((int64_t)slot * nct + ct) * TC_N + h * 16 + c];
           const int f1 = ecol[((int64_t)slot * nct + ct) * TC_N + h * 16 + c + 1];
           z64 x;
-          x.re = scalbn(fma((double)lo[c], 0x1p-28, (double)hi[c]), e + f0 - 35);
-          x.im = scalbn(fma((double)lo[c + 1], 0x1p-28, (double)hi[c + 1]), e + f1 - 35);
+          if (!int_to_double(thi[h][c], tlo[h][c], e + f0 - 35, &x.re))
+            x.re = scalbn(fma((double)tlo[h][c], 0x1p-28, (double)thi[h][c]), e + f0 - 35);
+          if (!int_to_double(thi[h][c + 1], tlo[h][c + 1], e + f1 - 35, &x.im))
+            x.im = scalbn(fma((double)tlo[h][c + 1], 0x1p-28, (double)thi[h][c + 1]), e + f1 - 35);
           X[((int64_t)slot * nf + j) * n + i] = x;
         }
       }
-    }
   }
   tc_fence_before();
   __syncthreads();

@@ -293,20 +293,26 @@ static void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 }
 
 // Shapes of the multigrid levels: axis a halves while n_a is even and > 4.
-static std::vector<LevelHost> level_shapes(int nx, int ny, int nz, const double h[3]) {
+// Multigrid levels: an axis halves while its cell count is even and > 4. With
+// `ragged`, an odd axis > 4 also halves (to (n + 1) / 2 cells, the last coarse
+// cell having one child) while the level has more than MAX_COARSE cells; the
+// operator takes the ragged hierarchy only when the even one ends above
+// MAX_COARSE cells (the largest coarsest level solved exactly).
+static std::vector<LevelHost> level_shapes(int nx, int ny, int nz, const double h[3], bool ragged) {
   std::vector<LevelHost> L;
   LevelHost l{};
   l.nx = nx; l.ny = ny; l.nz = nz;
   l.h[0] = h[0]; l.h[1] = h[1]; l.h[2] = h[2];
   while (true) {
     l.n = (int64_t)l.nx * l.ny * l.nz;
-    l.rx = (l.nx % 2 == 0 && l.nx > 4) ? 2 : 1;
-    l.ry = (l.ny % 2 == 0 && l.ny > 4) ? 2 : 1;
-    l.rz = (l.nz % 2 == 0 && l.nz > 4) ? 2 : 1;
+    const bool big = ragged && l.n > MAX_COARSE;
+    l.rx = (l.nx > 4 && (l.nx % 2 == 0 || big)) ? 2 : 1;
+    l.ry = (l.ny > 4 && (l.ny % 2 == 0 || big)) ? 2 : 1;
+    l.rz = (l.nz > 4 && (l.nz % 2 == 0 || big)) ? 2 : 1;
     L.push_back(l);
     if (l.rx == 1 && l.ry == 1 && l.rz == 1) break;
     LevelHost c{};
-    c.nx = l.nx / l.rx; c.ny = l.ny / l.ry; c.nz = l.nz / l.rz;
+    c.nx = (l.nx + l.rx - 1) / l.rx; c.ny = (l.ny + l.ry - 1) / l.ry; c.nz = (l.nz + l.rz - 1) / l.rz;
     c.h[0] = l.h[0] * l.rx; c.h[1] = l.h[1] * l.ry; c.h[2] = l.h[2] * l.rz;
     l = c;
     if ((int)L.size() >= MAX_LEVELS) break;
@@ -1005,6 +1011,20 @@ static void build_graph(Solve& S, cudaGraphExec_t* exec, int* outer_kernels, int
   cudaStreamDestroy(cs);
 }
 
+// build_graph with programmatic dependent launches; if the capture or the
+// instantiation refuses them, the process switches them off and builds again.
+template <typename VT>
+static void build_graph_any(Solve& S, Lane* lane) {
+  try {
+    build_graph<VT>(S, &lane->graph, &lane->graph_outer, &lane->graph_inner);
+  } catch (const CudaError&) {
+    if (!pdl_flag()) throw;
+    cudaGetLastError();
+    pdl_flag() = 0;
+    build_graph<VT>(S, &lane->graph, &lane->graph_outer, &lane->graph_inner);
+  }
+}
+
 template <typename VT>
 static void setup_levels(Solve& S) {
   if (S.op->csr) {
@@ -1270,10 +1290,12 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L, (double)S.batching};
       for (int pz = 0; pz < 2; ++pz)
         for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
+      key.push_back((double)pdl_flag());
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
-        build_graph<VT>(S, &lane->graph, &lane->graph_outer, &lane->graph_inner);
+        build_graph_any<VT>(S, lane);
+        key.back() = (double)pdl_flag();
         lane->graph_key = key;
       }
       CK(cudaGraphLaunch(lane->graph, s));
@@ -1769,9 +1791,10 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
   double vol = hh[0] * hh[1] * hh[2];
   std::vector<double> mass(n);
   for (int64_t c = 0; c < n; ++c) mass[c] = ss[c] * vol;
-  std::vector<LevelHost> Ls = level_shapes((int)nx, (int)ny, (int)nz, hh);
+  std::vector<LevelHost> Ls = level_shapes((int)nx, (int)ny, (int)nz, hh, false);
+  if (Ls.back().n > MAX_COARSE) Ls = level_shapes((int)nx, (int)ny, (int)nz, hh, true);
   if (Ls.back().n > MAX_COARSE) {
-    set_error("fks_op_grid: coarsest multigrid level has more than 1024 cells (halve sides while even and > 4)");
+    set_error("fks_op_grid: coarsest multigrid level has more than 1024 cells (more than 16 levels needed)");
     return FKS_ERR_ARG;
   }
   fks_op* op = new fks_op;
@@ -1798,7 +1821,37 @@ fks_status fks_op_grid(fks_ctx* ctx, int dim, const int64_t ncell[3], const doub
     CK(cudaMemcpy(cond_d, cond, sizeof(double) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(op->levels[0].d64[3], mass.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     launch_faces_from_cond(op->levels[0], hh, mask, cond_d, s);
-    for (size_t l = 0; l + 1 < op->levels.size(); ++l) launch_coarsen(op->levels[l], op->levels[l + 1], s);
+    {
+      // coarse-face factors of every coarsening from the cells' widths (in
+      // finest cells) along each axis, uploaded at once
+      std::vector<double> w[3] = {std::vector<double>(nx, 1.0), std::vector<double>(ny, 1.0),
+                                  std::vector<double>(nz, 1.0)};
+      std::vector<double> all;
+      std::vector<size_t> at;
+      for (size_t l = 0; l + 1 < op->levels.size(); ++l) {
+        const LevelHost& F = op->levels[l];
+        const int r[3] = {F.rx, F.ry, F.rz};
+        for (int a = 0; a < 3; ++a) {
+          std::vector<double> W;
+          std::vector<double> f = coarse_face_factors(w[a], r[a], &W);
+          at.push_back(all.size());
+          all.insert(all.end(), f.begin(), f.end());
+          w[a] = W;
+        }
+      }
+      double* fac_d = nullptr;
+      if (!all.empty()) {
+        CK(cudaMalloc(&fac_d, sizeof(double) * all.size()));
+        CK(cudaMemcpy(fac_d, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice));
+      }
+      for (size_t l = 0; l + 1 < op->levels.size(); ++l)
+        launch_coarsen(op->levels[l], op->levels[l + 1], fac_d + at[3 * l], fac_d + at[3 * l + 1],
+                       fac_d + at[3 * l + 2], s);
+      if (fac_d) {
+        CK(cudaStreamSynchronize(s));
+        CK(cudaFree(fac_d));
+      }
+    }
     CK(cudaMalloc(&op->levels[0].kd64, sizeof(double) * n));
     launch_kdiag(op->levels[0], op->levels[0].kd64, s);
     for (auto& L : op->levels)
@@ -2117,6 +2170,12 @@ fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
   }
   op->cluster_max[pi] = max_cells;
   return FKS_OK;
+}
+
+int fks_set_pdl(int on) {
+  const int prev = fks::pdl_flag();
+  if (on >= 0) fks::pdl_flag() = on ? 1 : 0;
+  return prev;
 }
 
 fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes) {
@@ -3133,10 +3192,12 @@ struct Batch : BatchBase {
                                  (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L, 1.0};
       for (int pz = 0; pz < 2; ++pz)
         for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
+      key.push_back((double)pdl_flag());
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
         lane->graph = nullptr;
-        build_graph<VT>(S, &lane->graph, &lane->graph_outer, &lane->graph_inner);
+        build_graph_any<VT>(S, lane);
+        key.back() = (double)pdl_flag();
         lane->graph_key = key;
       }
       CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));

@@ -35,7 +35,7 @@ bool cluster_layout(const std::vector<LevelHost>& Ls, int l0, ClusterParams<T>* 
   Q.nlev = nlev;
   for (int l = l0; l < L - 1; ++l) {
     const LevelHost& A = Ls[l];
-    if (A.nz != 1 || A.rx != 2 || A.ry != 2 || A.rz != 1) return false;
+    if (A.nz != 1 || A.rx != 2 || A.ry != 2 || A.rz != 1 || A.nx % 2 || A.ny % 2) return false;
     if (A.ny % CL_SIZE != 0) return false;
     const int R = A.ny / CL_SIZE;
     // a banded coarser level must take exactly the two fine rows of each coarse row

@@ -95,6 +95,38 @@ __host__ __device__ __forceinline__ T ldc(const C* p, int64_t i) {
   else return (T)p[i];
 }
 
+// ---------------------------------------------------------------- launch overlap
+// Programmatic dependent launch: a kernel launched by launch_pdl may be
+// scheduled while its predecessor in the stream is still running. It waits in
+// pdl_enter for the predecessor's completion (and the visibility of its
+// writes) before it touches global memory, then lets its own successor begin
+// launching. Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// process-wide switch (on by default; fks_set_pdl)
+inline int& pdl_flag() {
+  static int on = 1;
+  return on;
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_flag() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_COARSE = 1024;
 constexpr int MAX_TAU = 16;

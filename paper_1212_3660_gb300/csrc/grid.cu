@@ -66,10 +66,15 @@ __global__ void k_faces_from_cond(int nx, int ny, int nz, double hx, double hy, 
   }
 }
 
-// Coarse faces: (sum of the fine faces on the coarse face) / r_a; coarse mass:
-// sum of the children. One thread per coarse face / cell.
+// Coarse faces: (sum of the fine faces on the coarse face) x the face's factor
+// (fine over coarse centre distance across it: 1/2 on evenly halved axes, 1 on
+// axes not coarsened; fac_x/y/z, one per coarse face index along the axis);
+// coarse mass: sum of the children. One thread per coarse face / cell. On an
+// odd (ragged) axis the last coarse cell has one child: its high face is that
+// child's, and the sums skip children past the fine grid.
 __global__ void k_coarsen(LevelView<double> F, int rx, int ry, int rz, int cx_, int cy, int cz, double* fx,
-                          double* fy, double* fz, double* mm) {
+                          double* fy, double* fz, double* mm, const double* __restrict__ fac_x,
+                          const double* __restrict__ fac_y, const double* __restrict__ fac_z) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t nfx = (int64_t)(cx_ + 1) * cy * cz, nfy = (int64_t)cx_ * (cy + 1) * cz;
   int64_t nfz = cz > 1 || F.nz > 1 ? (int64_t)cx_ * cy * (cz + 1) : 0;
@@ -79,12 +84,14 @@ __global__ void k_coarsen(LevelView<double> F, int rx, int ry, int rz, int cx_, 
     int64_t q = t / (cx_ + 1);
     int J = (int)(q % cy), K = (int)(q / cy);
     double s = 0.0;
+    const int64_t fi = min(rx * I, F.nx);
     for (int c = 0; c < rz; ++c)
       for (int b = 0; b < ry; ++b) {
+        if (rz * K + c >= F.nz || ry * J + b >= F.ny) continue;
         int64_t row = (int64_t)(rz * K + c) * F.ny + (ry * J + b);
-        s += F.fx[row * (F.nx + 1) + (int64_t)rx * I];
+        s += F.fx[row * (F.nx + 1) + fi];
       }
-    fx[t] = s / rx;
+    fx[t] = s * fac_x[I];
     return;
   }
   t -= nfx;
@@ -93,10 +100,13 @@ __global__ void k_coarsen(LevelView<double> F, int rx, int ry, int rz, int cx_, 
     int64_t q = t / cx_;
     int J = (int)(q % (cy + 1)), K = (int)(q / (cy + 1));
     double s = 0.0;
+    const int64_t fj = min(ry * J, F.ny);
     for (int c = 0; c < rz; ++c)
-      for (int a = 0; a < rx; ++a)
-        s += F.fy[((int64_t)(rz * K + c) * (F.ny + 1) + (int64_t)ry * J) * F.nx + (rx * I + a)];
-    fy[t] = s / ry;
+      for (int a = 0; a < rx; ++a) {
+        if (rz * K + c >= F.nz || rx * I + a >= F.nx) continue;
+        s += F.fy[((int64_t)(rz * K + c) * (F.ny + 1) + fj) * F.nx + (rx * I + a)];
+      }
+    fy[t] = s * fac_y[J];
     return;
   }
   t -= nfy;
@@ -106,10 +116,13 @@ __global__ void k_coarsen(LevelView<double> F, int rx, int ry, int rz, int cx_, 
     int K = (int)(t / sxy);
     int I = (int)(ij % cx_), J = (int)(ij / cx_);
     double s = 0.0;
+    const int64_t fk = min(rz * K, F.nz);
     for (int b = 0; b < ry; ++b)
-      for (int a = 0; a < rx; ++a)
-        s += F.fz[((int64_t)rz * K * F.ny + (ry * J + b)) * F.nx + (rx * I + a)];
-    fz[t] = s / rz;
+      for (int a = 0; a < rx; ++a) {
+        if (ry * J + b >= F.ny || rx * I + a >= F.nx) continue;
+        s += F.fz[(fk * F.ny + (ry * J + b)) * F.nx + (rx * I + a)];
+      }
+    fz[t] = s * fac_z[K];
     return;
   }
   t -= nfz;
@@ -120,8 +133,10 @@ __global__ void k_coarsen(LevelView<double> F, int rx, int ry, int rz, int cx_, 
     double s = 0.0;
     for (int c = 0; c < rz; ++c)
       for (int b = 0; b < ry; ++b)
-        for (int a = 0; a < rx; ++a)
+        for (int a = 0; a < rx; ++a) {
+          if (rz * K + c >= F.nz || ry * J + b >= F.ny || rx * I + a >= F.nx) continue;
           s += F.mm[((int64_t)(rz * K + c) * F.ny + (ry * J + b)) * F.nx + (rx * I + a)];
+        }
     mm[t] = s;
   }
 }
@@ -210,6 +225,7 @@ template <typename T, typename C>
 __global__ void k_gs(LevelView<T, C> L, const SlotState* st, const cx<T>* __restrict__ invd,
                      const cx<T>* __restrict__ f, cx<T>* __restrict__ z, int64_t vs, int color, int zero_start,
                      int nslot) {
+  pdl_enter();
   const int slot = blockIdx.z * blockDim.z + threadIdx.z;
   if (slot >= nslot || !slot_running(st, slot)) return;
   const int ii = blockIdx.x * GX + threadIdx.x;
@@ -233,6 +249,7 @@ template <typename T, typename C>
 __global__ void k_gs_correct(LevelView<T, C> L, const SlotState* st, const cx<T>* __restrict__ invd,
                              const cx<T>* __restrict__ f, const cx<T>* __restrict__ z, int64_t vs, int color,
                              z64* __restrict__ Zk, int64_t vsZk, int64_t zcol, int nslot) {
+  pdl_enter();
   const int slot = blockIdx.z * blockDim.z + threadIdx.z;
   if (slot >= nslot || !slot_running(st, slot)) return;
   const int ii = blockIdx.x * GX + threadIdx.x;
@@ -267,6 +284,7 @@ __global__ void k_residual_restrict(LevelView<T, C> F, int rx, int ry, int rz, i
                                     const SlotState* st, const z64* taus, const cx<T>* __restrict__ f,
                                     const cx<T>* __restrict__ z, int64_t vs, cx<T>* __restrict__ fc, int64_t vsc,
                                     int nslot) {
+  pdl_enter();
   const int slot = blockIdx.z * blockDim.z + threadIdx.z;
   if (slot >= nslot || !slot_running(st, slot)) return;
   const int I = blockIdx.x * GX + threadIdx.x;
@@ -282,6 +300,7 @@ template <typename T>
 __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz, uint32_t mask,
                               const SlotState* st, const cx<T>* __restrict__ zc, int64_t vsc,
                               cx<T>* __restrict__ z, int64_t vs) {
+  pdl_enter();
   int slot = blockIdx.z;
   if (!slot_running(st, slot)) return;
   Cell p;
@@ -301,6 +320,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add3(LevelView<T> F, int cnx, int cny, int cnz, uint32_t mask,
                                                       const SlotState* st, const cx<T>* __restrict__ zc,
                                                       int64_t vsc, cx<T>* __restrict__ z, int64_t vs) {
+  pdl_enter();
   constexpr int SX = GX / 2 + 2, SY = GY / 2 + 2;
   __shared__ cx<T> sc[2][SY][SX];
   const int slot = blockIdx.z;
@@ -513,6 +533,7 @@ __global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, c
 // the per-level kernels.
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail_vcycle(TailParams<T> P, const SlotState* st) {
+  pdl_enter();
   int slot = blockIdx.x;
   if (!slot_running(st, slot)) return;
   extern __shared__ __align__(16) unsigned char tail_smem[];
@@ -855,7 +876,7 @@ bool tail2d_ok(const std::vector<LevelHost>& Ls, int lt) {
   if (Ls[nl - 1].nz != 1) return false;
   for (int l = lt; l + 1 < nl; ++l) {
     const LevelHost& A = Ls[l];
-    if (A.nz != 1 || A.rx != 2 || A.ry != 2 || A.n > 2 * TAIL_THREADS) return false;
+    if (A.nz != 1 || A.rx != 2 || A.ry != 2 || A.nx % 2 || A.ny % 2 || A.n > 2 * TAIL_THREADS) return false;
   }
   return true;
 }
@@ -1037,6 +1058,7 @@ __global__ void k_defect(LevelView<double> L, SlotState* st, const z64* taus, co
                          const z64* __restrict__ v, int64_t vsv, const z64* __restrict__ z, int64_t vsz, int64_t col,
                          int zero_z, cx<T>* __restrict__ f0, int64_t vsf, double* __restrict__ partial, int with_v,
                          DecideArgs D) {
+  pdl_enter();
   int slot = blockIdx.z;
   __shared__ double red[2][GX * GY / 32];
   __shared__ int last_blk;
@@ -1175,10 +1197,27 @@ void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask
                                                   L.d64[1], L.d64[2]);
 }
 
-void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s) {
+void launch_coarsen(const LevelHost& F, const LevelHost& C, const double* fac_x, const double* fac_y,
+                    const double* fac_z, cudaStream_t s) {
   int64_t tot = face_count(C, 0) + face_count(C, 1) + (C.nz > 1 || F.nz > 1 ? face_count(C, 2) : 0) + C.n;
   k_coarsen<<<nb(tot, 256), 256, 0, s>>>(view<double>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, C.d64[0], C.d64[1],
-                                          C.d64[2], C.d64[3]);
+                                          C.d64[2], C.d64[3], fac_x, fac_y, fac_z);
+}
+
+std::vector<double> coarse_face_factors(const std::vector<double>& w, int r, std::vector<double>* W) {
+  const int n = (int)w.size();
+  if (r == 1) {
+    *W = w;
+    return std::vector<double>(n + 1, 1.0);
+  }
+  const int nc = (n + 1) / 2;
+  W->assign(nc, 0.0);
+  for (int I = 0; I < nc; ++I) (*W)[I] = w[2 * I] + (2 * I + 1 < n ? w[2 * I + 1] : 0.0);
+  std::vector<double> f(nc + 1);
+  f[0] = w[0] / (*W)[0];
+  for (int I = 1; I < nc; ++I) f[I] = (w[2 * I - 1] + w[2 * I]) / ((*W)[I - 1] + (*W)[I]);
+  f[nc] = w[n - 1] / (*W)[nc - 1];
+  return f;
 }
 
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
@@ -1229,19 +1268,19 @@ void launch_gs(const LevelHost& L, const SlotState* st, const cx<T>* invd, const
   if constexpr (sizeof(T) == 4) {
     if (bf16) {
       if (Zk)
-        k_gs_correct<T, __nv_bfloat16><<<grd, blk, 0, s>>>(view_as<T, __nv_bfloat16>(L), st, invd, f, z, vs, color,
+        launch_pdl(k_gs_correct<T, __nv_bfloat16>, grd, blk, 0, s, view_as<T, __nv_bfloat16>(L), st, invd, f, z, vs, color,
                                                            Zk, vsZk, zcol, nslot);
       else
-        k_gs<T, __nv_bfloat16><<<grd, blk, 0, s>>>(view_as<T, __nv_bfloat16>(L), st, invd, f, z, vs, color,
+        launch_pdl(k_gs<T, __nv_bfloat16>, grd, blk, 0, s, view_as<T, __nv_bfloat16>(L), st, invd, f, z, vs, color,
                                                    zero_start, nslot);
       return;
     }
   }
   if (Zk) {
-    k_gs_correct<T, T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, Zk, vsZk, zcol, nslot);
+    launch_pdl(k_gs_correct<T, T>, grd, blk, 0, s, view<T>(L), st, invd, f, z, vs, color, Zk, vsZk, zcol, nslot);
     return;
   }
-  k_gs<T, T><<<grd, blk, 0, s>>>(view<T>(L), st, invd, f, z, vs, color, zero_start, nslot);
+  launch_pdl(k_gs<T, T>, grd, blk, 0, s, view<T>(L), st, invd, f, z, vs, color, zero_start, nslot);
 }
 
 template <typename T>
@@ -1252,12 +1291,12 @@ void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const Slot
   const dim3 blk(GX, rb, G), grd(nb(C.nx, GX), nb((int64_t)C.ny * C.nz, rb), nb(nslot, G));
   if constexpr (sizeof(T) == 4) {
     if (bf16) {
-      k_residual_restrict<T, __nv_bfloat16><<<grd, blk, 0, s>>>(view_as<T, __nv_bfloat16>(F), F.rx, F.ry, F.rz, C.nx,
+      launch_pdl(k_residual_restrict<T, __nv_bfloat16>, grd, blk, 0, s, view_as<T, __nv_bfloat16>(F), F.rx, F.ry, F.rz, C.nx,
                                                                 C.ny, C.nz, st, taus, f, z, vs, fc, vsc, nslot);
       return;
     }
   }
-  k_residual_restrict<T, T><<<grd, blk, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
+  launch_pdl(k_residual_restrict<T, T>, grd, blk, 0, s, view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny, C.nz, st, taus, f, z, vs, fc,
                                                 vsc, nslot);
 }
 
@@ -1266,10 +1305,10 @@ void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, c
                         int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s) {
   if (F.nz > 1 && F.rx == 2 && F.ry == 2 && F.rz == 2 && (int64_t)nb(F.ny, GY) * F.nz <= 65535) {
     const dim3 g(nb(F.nx, GX), nb(F.ny, GY) * F.nz, nslot);
-    k_prolong_add3<T><<<g, B2, 0, s>>>(view<T>(F), C.nx, C.ny, C.nz, mask, st, zc, vsc, z, vs);
+    launch_pdl(k_prolong_add3<T>, g, B2, 0, s, view<T>(F), C.nx, C.ny, C.nz, mask, st, zc, vsc, z, vs);
     return;
   }
-  k_prolong_add<T><<<grid2(F.nx, (int64_t)F.ny * F.nz, nslot), B2, 0, s>>>(view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny,
+  launch_pdl(k_prolong_add<T>, grid2(F.nx, (int64_t)F.ny * F.nz, nslot), B2, 0, s, view<T>(F), F.rx, F.ry, F.rz, C.nx, C.ny,
                                                                             C.nz, mask, st, zc, vsc, z, vs);
 }
 
@@ -1280,7 +1319,9 @@ static size_t fused_smem() {
   return 2 * (size_t)(TX + 2 * FH) * (TY + 2 * FH) * sizeof(cx<T>);
 }
 
-bool fused_level_ok(const LevelHost& L) { return L.nz == 1 && L.rx == 2 && L.ry == 2 && L.rz == 1; }
+bool fused_level_ok(const LevelHost& L) {
+  return L.nz == 1 && L.rx == 2 && L.ry == 2 && L.rz == 1 && L.nx % 2 == 0 && L.ny % 2 == 0;
+}
 
 template <typename T>
 void fused_prepare() {
@@ -1336,7 +1377,7 @@ void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st,
   if (P.pairs)
     k_tail2d<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
   else
-    k_tail_vcycle<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
+    launch_pdl(k_tail_vcycle<T>, nslot, TAIL_THREADS, smem_bytes, s, P, st);
 }
 
 template <typename T>
@@ -1367,7 +1408,7 @@ void launch_defect(const LevelHost& L, const SlotState* st, const z64* taus, con
                    int64_t vsz, int64_t col, int zero_z, cx<T>* f0, int64_t vsf, double* partial, int with_v,
                    int nslot, cudaStream_t s) {
   DecideArgs D{};
-  k_defect<T><<<defect_grid(L, nslot), B2, 0, s>>>(view<double>(L), const_cast<SlotState*>(st), taus, nullptr, v, vsv,
+  launch_pdl(k_defect<T>, defect_grid(L, nslot), B2, 0, s, view<double>(L), const_cast<SlotState*>(st), taus, nullptr, v, vsv,
                                                    z, vsz, col, zero_z, f0, vsf, partial, with_v, D);
 }
 
@@ -1378,7 +1419,7 @@ void launch_defect_decide(const LevelHost& L, SlotState* st, const z64* taus, co
                           int use_cond, cudaGraphConditionalHandle cond, int* flags, int* counter, int* bcount,
                           int nslot, double relax, double tol, cudaStream_t s) {
   DecideArgs D{1, eps, max_cycles, replay_cycles, m_max, use_cond, cond, flags, counter, bcount, nslot, relax, tol};
-  k_defect<T><<<defect_grid(L, nslot), B2, 0, s>>>(view<double>(L), st, taus, diag64, v, vsv, z, vsz, col, zero_z,
+  launch_pdl(k_defect<T>, defect_grid(L, nslot), B2, 0, s, view<double>(L), st, taus, diag64, v, vsv, z, vsz, col, zero_z,
                                                    f0, vsf, partial, zero_z, D);
 }
 

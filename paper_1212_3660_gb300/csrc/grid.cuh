@@ -75,7 +75,14 @@ void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st,
 bool tail2d_ok(const std::vector<LevelHost>& Ls, int lt);
 
 void launch_faces_from_cond(const LevelHost& L, const double h[3], uint32_t mask, const double* cond, cudaStream_t s);
-void launch_coarsen(const LevelHost& F, const LevelHost& C, cudaStream_t s);
+void launch_coarsen(const LevelHost& F, const LevelHost& C, const double* fac_x, const double* fac_y,
+                    const double* fac_z, cudaStream_t s);
+// Factors of the coarse faces along one axis (index 0..nc: the face below
+// coarse cell I; nc: the high boundary): fine centre distance across the face
+// over the coarse one, from the fine cells' widths w in finest cells (half
+// widths at the boundary); 1/2 everywhere on evenly halved axes, 1 where r = 1.
+// W receives the coarse widths.
+std::vector<double> coarse_face_factors(const std::vector<double>& w, int r, std::vector<double>* W);
 void launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 // from_f32: from the level's fp32 coefficients (the bf16-smoother option's
 // rounded values) instead of its fp64 ones

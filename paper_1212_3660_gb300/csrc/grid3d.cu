@@ -358,7 +358,9 @@ static size_t fused3_smem(bool pre) {
   return (size_t)(R3Z + R3F) * Tile3<TX, TY>::P * sizeof(cx<T>) + (pre ? (size_t)(TX / 2) * (TY / 2) * sizeof(cx<T>) : 0);
 }
 
-bool fused3d_level_ok(const LevelHost& L) { return L.nz > 1 && L.rx == 2 && L.ry == 2 && L.rz == 2; }
+bool fused3d_level_ok(const LevelHost& L) {
+  return L.nz > 1 && L.rx == 2 && L.ry == 2 && L.rz == 2 && L.nx % 2 == 0 && L.ny % 2 == 0 && L.nz % 2 == 0;
+}
 
 template <typename T>
 void fused3d_prepare() {

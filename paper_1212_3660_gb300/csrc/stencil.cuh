@@ -151,7 +151,8 @@ __device__ __forceinline__ bool color_cell(int nx, int ny, int nz, int color, in
   return true;
 }
 
-// Sum over the children of coarse cell (I,J,K) of the fine residual f - (K + s M) z.
+// Sum over the children of coarse cell (I,J,K) of the fine residual f - (K + s M) z
+// (on an odd axis the last coarse cell has one child).
 template <typename T, typename C>
 __device__ __forceinline__ cx<T> restrict_value(const LevelView<T, C>& F, int rx, int ry, int rz, int I, int J, int K,
                                                 cx<T> s, const cx<T>* f, const cx<T>* z) {
@@ -160,6 +161,7 @@ __device__ __forceinline__ cx<T> restrict_value(const LevelView<T, C>& F, int rx
     for (int b = 0; b < ry; ++b)
       for (int a = 0; a < rx; ++a) {
         Cell p{rx * I + a, ry * J + b, rz * K + c};
+        if (p.i >= F.nx || p.j >= F.ny || p.k >= F.nz) continue;
         int64_t cc = ((int64_t)p.k * F.ny + p.j) * F.nx + p.i;
         acc = acc + (f[cc] - apply_at(F, p, cc, s, z));
       }

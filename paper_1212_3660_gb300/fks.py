@@ -112,6 +112,8 @@ def lib():
     L.fks_op_tiling.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.fks_op_set_zchunk.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    L.fks_set_pdl.argtypes = [C.c_int]
+    L.fks_set_pdl.restype = C.c_int
     L.fks_op_zchunks.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_int)]
     L.fks_server_create.argtypes = [vp, C.c_size_t, C.c_int, C.POINTER(vp)]
     L.fks_server_submit.argtypes = [vp, C.POINTER(fks_request), C.POINTER(C.c_uint64)]
@@ -396,6 +398,12 @@ def fks_op_set_tiles8(op, precision, max_cells):
     st = lib().fks_op_set_tiles8(op, int(precision), int(max_cells))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
+
+
+def fks_set_pdl(on):
+    """Programmatic dependent launch of the multigrid and defect kernels for the
+    process (1 on, 0 off, -1 query); returns the previous setting."""
+    return int(lib().fks_set_pdl(int(on)))
 
 
 def fks_op_set_zchunk(op, precision, level, planes):

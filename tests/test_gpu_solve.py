@@ -24,6 +24,9 @@ CASES = [
     dict(shape=(12, 20, 10), n_f=5, periods=(5.0, 3600.0), n_p=4, seed=10, corr_frac=(0.2, 0.2, 0.05),
          ss_var=0.25),                                                               # aniso + lognormal S_s
     dict(shape=(30, 18), n_f=4, periods=(10.0, 1000.0), n_p=2, seed=12, dirichlet_mask=0b0011),  # no-flow y
+    # even halving would end at 33 x 35 and 9 x 11 x 13 (> 1024 cells): ragged halving of odd sides
+    dict(shape=(66, 70), n_f=5, periods=(5.0, 3600.0), n_p=2, seed=14),
+    dict(shape=(18, 22, 26), n_f=4, periods=(5.0, 3600.0), n_p=2, seed=15),
 ]
 
 
@@ -327,6 +330,81 @@ def test_tail_kernels_agree_bitwise(precision, shape, n_src):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
+def test_ragged_hierarchy_paths_agree_bitwise(precision):
+    """126 x 130 halves to 63 x 65, which even halving cannot coarsen further, so
+    odd sides halve too: 32 x 33, 16 x 17, 8 x 17, 4 x 17. The fused tile kernels
+    and the 2D tail keep to levels with two children per coarse cell; every
+    choice of fusion and tail (the general tail over the ragged levels included)
+    and the autotuner's give the bits of the per-level kernels."""
+    need_gpu()
+    pr = synth.make_problem((126, 130), n_f=5, periods=(5.0, 3600.0), n_p=3, seed=34, n_src=2, m_max=60)
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, 0)
+    fks.fks_op_set_tail(s.op, precision, 1)
+    a = s.solve(precision=precision, inner_tol=1e-10)
+    assert a.status == fks.FKS_OK
+    for fuse in (0, -1):
+        fks.fks_op_set_fusion(s.op, precision, fuse)
+        for tail in (64, 320, 1100, 4096):
+            fks.fks_op_set_tail(s.op, precision, tail)
+            d = s.solve(precision=precision, inner_tol=1e-10)
+            assert np.array_equal(a.X, d.X), (fuse, tail)
+    fks.fks_op_autotune(s.op, precision, pr.tau_bar[1])
+    d = s.solve(precision=precision, inner_tol=1e-10)
+    assert np.array_equal(a.X, d.X), fks.fks_op_tiling(s.op, precision)
+    op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+    for r in range(2):
+        tr = oracle.true_residuals(op, pr.rhs()[:, r], pr.sigma, a.X[r].T)
+        assert (tr <= pr.tol).all()
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(289, 289), (45, 45, 45)])
+def test_odd_aquifers_certify_every_shift(shape):
+    """Odd-sided aquifers whose hierarchies are ragged from the finest level
+    (289^2 keeps one-cell-wide edge cells through four levels): free-running
+    mixed-precision solves certify every shift, and the GPU's true residuals
+    equal the oracle's recomputation."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=8, periods=(5.0, 3600.0), n_p=3, seed=20000, m_max=80)
+    s = Solver(pr)
+    out = s.solve(precision=fks.FKS_PREC_MIXED, inner_tol=1e-10, inner_relax=0.003)
+    assert out.status == fks.FKS_OK
+    assert int(out.inner_cycles.max()) < 50
+    op = oracle.assemble(pr.shape, pr.h, pr.cond, pr.ss, pr.dirichlet_mask)
+    tr = oracle.true_residuals(op, pr.rhs()[:, 0], pr.sigma, out.X[0].T)
+    assert (tr <= pr.tol).all()
+    assert np.allclose(out.res_true[0], tr, rtol=1e-6, atol=1e-15)
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (96, 80)])
+def test_launch_overlap_changes_no_bits(shape):
+    """Programmatic dependent launch of the multigrid and defect kernels (the
+    default) and plain launches, each in the graph and host-driven loops, give
+    the same bits; the graph capture keeps the overlap on."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=6, periods=(5.0, 3600.0), n_p=3, seed=36, n_src=2, m_max=60)
+    s = Solver(pr)
+    prev = fks.fks_set_pdl(1)
+    try:
+        outs = []
+        for on in (1, 0):
+            fks.fks_set_pdl(on)
+            for mode in (0, 1):
+                outs.append(s.solve(precision=fks.FKS_PREC_MIXED, inner_tol=1e-10, launch_mode=mode))
+                if on:
+                    assert fks.fks_set_pdl(-1) == 1
+        assert outs[0].status == fks.FKS_OK
+        for o in outs[1:]:
+            assert np.array_equal(outs[0].X, o.X)
+            assert np.array_equal(outs[0].inner_cycles, o.inner_cycles)
+    finally:
+        fks.fks_set_pdl(prev)
+        s.close()
+
+
 def test_cluster_vcycle_rejects_inapplicable_levels():
     """48 x 48 coarsens to 24 x 24 (3 rows per band, followed by a 12-row level
     that does not split into 8 bands): no starting level qualifies."""
@@ -390,10 +468,11 @@ def test_relaxed_inner_tolerance_replay_parity():
 @pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED])
 def test_replay_parity_beyond_64_steps(precision):
     """A solve of 82 Arnoldi steps (tolerance 1e-10, one tau at the geometric
-    mean of a 1 s to 10 h period range): the source takes more steps than the
-    tensor-core assembly's exactness bound allows (64), so its x_j = Z y_j come
-    from the FP64 assembly kernel; every x_j to 1e-8 (complex128 cycles) or
-    1e-6 (complex64 cycles) of the oracle's."""
+    mean of a 1 s to 10 h period range): more steps than one exact tensor-core
+    accumulation covers (64), so the tensor-core assembly runs two chunks and
+    adds them in 64-bit integers. Every x_j to 1e-8 (complex128 cycles) or 1e-6
+    (complex64 cycles) of the oracle's, from the tensor cores and from the FP64
+    assembly kernel, and the two within 1e-12 of each other."""
     need_gpu()
     pr = synth.make_problem((32, 32), n_f=12, periods=(1.0, 36000.0), n_p=1, seed=51, m_max=100, tol=1e-10)
     eps = 1e-12
@@ -401,11 +480,16 @@ def test_replay_parity_beyond_64_steps(precision):
     assert ref.steps > 64
     rc, mj = replay_arrays(pr, [ref])
     s = Solver(pr)
-    out = s.solve(inner_tol=eps, precision=precision, replay_cycles=rc, replay_mj=mj)
-    assert np.array_equal(out.m_j[0], ref.m_j) and int(out.steps[0]) == ref.steps
     tol = 1e-8 if precision == fks.FKS_PREC_FP64 else 1e-6
+    outs = []
+    for assembly in (0, 1):
+        out = s.solve(inner_tol=eps, precision=precision, replay_cycles=rc, replay_mj=mj, assembly=assembly)
+        assert np.array_equal(out.m_j[0], ref.m_j) and int(out.steps[0]) == ref.steps
+        for j in range(len(pr.sigma)):
+            assert rel_err(out.X[0, j], ref.x[:, j]) <= tol, (assembly, j)
+        outs.append(out)
     for j in range(len(pr.sigma)):
-        assert rel_err(out.X[0, j], ref.x[:, j]) <= tol, j
+        assert rel_err(outs[0].X[0, j], outs[1].X[0, j]) <= 1e-12, j
     s.close()
 
 
