@@ -19,8 +19,6 @@ namespace fks {
 namespace {
 
 constexpr int STAGE_BYTES = TC_A_SLAB + TC_B_SLAB;
-constexpr int GEMM_SMEM = 2 * STAGE_BYTES + 64;
-constexpr uint32_t TMEM_COLS = 256;  // 8 levels x 32 columns
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -82,12 +80,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;                // base offset 0, relative lbo, layout type 0 (no swizzle)
 }
 
-// Instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D, M = 128, N = 32.
-__host__ __device__ constexpr uint32_t mma_idesc() {
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D, M = 128,
+// N columns (a multiple of 16, at most 256).
+__host__ __device__ constexpr uint32_t mma_idesc(uint32_t N) {
   return (1u << 4)                        // D format: f32
          | (1u << 7)                      // A format: bf16
          | (1u << 10)                     // B format: bf16
-         | ((uint32_t)(TC_N >> 3) << 17)  // N / 8
+         | ((N >> 3) << 17)               // N / 8
          | ((uint32_t)(TC_M >> 4) << 24); // M / 16
 }
 
@@ -120,19 +119,32 @@ __host__ __device__ __forceinline__ bool tc_slot(int K) {
   return K >= 0 && ((2 * K + TC_KSLAB - 1) / TC_KSLAB) * TC_KSLAB <= TC_MAX_KP;
 }
 
-// Exponent e with max |row| < 2^e (0 for a zero row).
+// Exponent e with max |row| < 2^e (0 for a zero row): for a normal amax, its
+// biased exponent - 1022 (as frexp gives), read from the bits.
 __device__ __forceinline__ int pow2_above(double amax) {
   if (amax == 0.0) return 0;
+  const int be = (int)((__double_as_longlong(amax) >> 52) & 0x7FF);
+  if (be != 0) return be - 1022;
   int e;
-  frexp(amax, &e);
+  frexp(amax, &e);  // subnormal
   return e;
 }
 
 // Eight signed 7-bit digits of v / 2^e (|v| < 2^e): v = 2^e sum_s d_s 2^{-7(s+1)}
-// up to the truncated bits below 2^{e-56}.
+// up to the truncated bits below 2^{e-56}. X = trunc(|v| 2^(56-e)) is the
+// significand shifted by the exponent difference (integer instructions only).
 __device__ __forceinline__ void digits7(double v, int e, int (&d)[TC_SLICES]) {
-  const unsigned long long X = (unsigned long long)__double2ull_rz(scalbn(fabs(v), 56 - e));
-  const int sg = v < 0.0 ? -1 : 1;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int be = (int)((bits >> 52) & 0x7FF);
+  unsigned long long X;
+  if (be == 0) {
+    X = (unsigned long long)__double2ull_rz(scalbn(fabs(v), 56 - e));  // zero or subnormal
+  } else {
+    const unsigned long long M = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = be - 1019 - e;  // |v| = M 2^(be - 1075)
+    X = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+  }
+  const int sg = (bits >> 63) ? -1 : 1;
 #pragma unroll
   for (int s = 0; s < TC_SLICES; ++s) d[s] = sg * (int)((X >> (49 - 7 * s)) & 127ull);
 }
@@ -261,162 +273,229 @@ __global__ void __launch_bounds__(TC_N) k_tc_slice_b(const SlotState* __restrict
   }
 }
 
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const SlotState* __restrict__ st,
-                                                     const unsigned char* __restrict__ As,
-                                                     const unsigned char* __restrict__ Bs,
-                                                     const int* __restrict__ erow, const int* __restrict__ ecol,
-                                                     int nslab, int nrt, int nct, int64_t n, int nf,
-                                                     z64* __restrict__ X, int* __restrict__ err) {
+// Persistent form: one CTA per SM takes (source, 128-row tile) items in turn and
+// runs every 32-column tile of an item. Warp P_EPI + 1 (one lane) issues the
+// MMAs of a tile (per chunk of at most 8 slabs) into one of two TMEM
+// accumulator sets, warp P_EPI (one lane) streams the slabs through a ring of
+// PS stages, and the epilogue warps drain the other set into 64-bit totals and
+// write x_j, so a tile's epilogue overlaps the next tile's MMAs: warp w reads
+// TMEM lanes 32 (w mod 4) .. + 31 (one row per thread) and the 16 columns of
+// half w / 4 of the tile, two warps per SM sub-partition to hide the latency
+// of the integer epilogue. Barriers: full/empty per stage, tfull/tempty per
+// accumulator set.
+constexpr int PS = 4;
+constexpr int P_EPI = 8;                   // epilogue warps
+constexpr int P_THREADS = 32 * (P_EPI + 2);
+constexpr uint32_t P_TMEM_COLS = 512;      // two sets of 8 levels x 32 columns
+
+struct PBars {
+  uint64_t full[PS], empty[PS], tfull[2], tempty[2], fin;
+  uint32_t tslot;
+  int abort;
+};
+
+constexpr int P_SMEM = PS * STAGE_BYTES + (int)sizeof(PBars) + 64;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool p_aborted(const PBars* B) { return *(volatile const int*)&B->abort != 0; }
+
+__device__ __forceinline__ void p_fail(PBars* B, int* err, int code) {
+  atomicExch(err, code);
+  atomicExch(&B->abort, 1);
+}
+
+__global__ void __launch_bounds__(P_THREADS, 1) k_tc_gemm(const SlotState* __restrict__ st,
+                                                           const unsigned char* __restrict__ As,
+                                                           const unsigned char* __restrict__ Bs,
+                                                           const int* __restrict__ erow, const int* __restrict__ ecol,
+                                                           int nslab, int nrt, int nct, int64_t n, int nf, int nslot,
+                                                           z64* __restrict__ X, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * STAGE_BYTES);  // full[2], free[2], done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
-  int* sfail = reinterpret_cast<int*>(tslot + 1);
-  const int ct = blockIdx.x, rt = blockIdx.y, slot = blockIdx.z;
-  if (!tc_slot(st[slot].k)) return;  // this source is assembled by the FP64 kernel
+  PBars* B = reinterpret_cast<PBars*>(sm + PS * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t sbase = smem_u32(sm);
-  const uint32_t full0 = smem_u32(&bars[0]), free0 = smem_u32(&bars[2]), done = smem_u32(&bars[4]);
   if (threadIdx.x == 0) {
-    mbar_init(full0, 1);
-    mbar_init(full0 + 8, 1);
-    mbar_init(free0, 1);
-    mbar_init(free0 + 8, 1);
-    mbar_init(done, 1);
-    *sfail = 0;
+    for (int q = 0; q < PS; ++q) {
+      mbar_init(smem_u32(&B->full[q]), 1);
+      mbar_init(smem_u32(&B->empty[q]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&B->tfull[a]), 1);
+      mbar_init(smem_u32(&B->tempty[a]), P_EPI);
+    }
+    mbar_init(smem_u32(&B->fin), 1);
+    B->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(TMEM_COLS)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&B->tslot)),
+                 "r"(P_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-
-  const unsigned char* asrc = As + (size_t)(slot * nrt + rt) * nslab * TC_A_SLAB;
-  const unsigned char* bsrc = Bs + (size_t)(slot * nct + ct) * nslab * TC_B_SLAB;
-  const bool issuer = warp == 0 && lane == 0;
-  // issuer state across chunks: slabs whose copies were started / consumed
-  bool ok = true;
-  int loaded = 0, consumed = 0;
-  if (issuer) {
-    mbar_expect_tx(full0, STAGE_BYTES);
-    bulk_g2s(sbase, asrc, TC_A_SLAB, full0);
-    bulk_g2s(sbase + TC_A_SLAB, bsrc, TC_B_SLAB, full0);
-    loaded = 1;
-  }
+  const uint32_t tmem = B->tslot;
   constexpr int SPC = TC_CHUNK_KP / TC_KSLAB;  // slabs per chunk
   const int nchunk = (nslab + SPC - 1) / SPC;
-  // 64-bit totals of this thread's row: levels 0-3 (hi) and 4-7 (lo), 32 columns
-  long long thi[2][16], tlo[2][16];
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int c = 0; c < 16; ++c) thi[h][c] = tlo[h][c] = 0;
-  const int r = warp * 32 + lane;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-  for (int ch = 0; ch < nchunk; ++ch) {
-    if (issuer && ok) {
-      constexpr uint32_t idesc = mma_idesc();
-      const int q1 = min(nslab, (ch + 1) * SPC);
-      uint32_t started = 0;  // accumulators already written in this chunk
-      for (int q = ch * SPC; q < q1; ++q) {
-        const int sg = q & 1;
-        if (q + 1 < nslab) {
-          const int ns = (q + 1) & 1;
-          // the stage is free once the MMAs of slab q - 1 completed
-          if (q + 1 >= 2 && !mbar_wait(free0 + 8 * ns, ((q + 1) / 2 - 1) & 1)) { ok = false; break; }
-          const uint32_t dst = sbase + ns * STAGE_BYTES, fb = full0 + 8 * ns;
-          mbar_expect_tx(fb, STAGE_BYTES);
-          bulk_g2s(dst, asrc + (size_t)(q + 1) * TC_A_SLAB, TC_A_SLAB, fb);
-          bulk_g2s(dst + TC_A_SLAB, bsrc + (size_t)(q + 1) * TC_B_SLAB, TC_B_SLAB, fb);
-          ++loaded;
-        }
-        if (!mbar_wait(full0 + 8 * sg, (q / 2) & 1)) { ok = false; break; }
-        ++consumed;
-        tc_fence_after();
-        const uint32_t a0 = sbase + sg * STAGE_BYTES, b0 = a0 + TC_A_SLAB;
-#pragma unroll 1
-        for (int s = 0; s < TC_SLICES; ++s)
-#pragma unroll 1
-          for (int t = 0; s + t < TC_SLICES; ++t) {
-            const int lev = s + t;
-            mma_bf16(tmem + (uint32_t)(lev * TC_N), smem_desc(a0 + s * (TC_A_SLAB / TC_SLICES), 128, 256),
-                     smem_desc(b0 + t * (TC_B_SLAB / TC_SLICES), 128, 256), idesc, (started >> lev) & 1u);
-            started |= 1u << lev;
+  const int nitems = nslot * nrt;
+
+  if (warp == P_EPI) {
+    // ---- producer: slabs of every tile of every item, in order, through the ring
+    if (lane == 0) {
+      long long g = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < nitems; item += gridDim.x) {
+        const int slot = item / nrt, rt = item - slot * nrt;
+        if (!tc_slot(st[slot].k)) continue;
+        const unsigned char* asrc = As + (size_t)(slot * nrt + rt) * nslab * TC_A_SLAB;
+        for (int ct = 0; ok && ct < nct; ++ct) {
+          const unsigned char* bsrc = Bs + (size_t)(slot * nct + ct) * nslab * TC_B_SLAB;
+          for (int q = 0; q < nslab; ++q, ++g) {
+            const int sg = (int)(g % PS);
+            if (g >= PS && !mbar_wait(smem_u32(&B->empty[sg]), (uint32_t)((g / PS - 1) & 1))) {
+              p_fail(B, err, 1);
+              ok = false;
+              break;
+            }
+            if (p_aborted(B)) { ok = false; break; }
+            const uint32_t dst = sbase + sg * STAGE_BYTES, fb = smem_u32(&B->full[sg]);
+            mbar_expect_tx(fb, STAGE_BYTES);
+            bulk_g2s(dst, asrc + (size_t)q * TC_A_SLAB, TC_A_SLAB, fb);
+            bulk_g2s(dst + TC_A_SLAB, bsrc + (size_t)q * TC_B_SLAB, TC_B_SLAB, fb);
           }
-        mma_commit(free0 + 8 * sg);
+        }
       }
-      if (!ok) {
-        atomicExch(err, 1);
-        *sfail = 1;
-        // let copies still in flight land before the CTA exits
-        for (int q = consumed; q < loaded; ++q) mbar_wait(full0 + 8 * (q & 1), (q / 2) & 1);
-      }
-      mma_commit(done);  // arrives once every MMA issued so far has completed
+      // the copies of the last slabs must have landed before the CTA exits
+      for (long long h = g - 1; h >= 0 && h >= g - PS; --h)
+        mbar_wait(smem_u32(&B->full[h % PS]), (uint32_t)((h / PS) & 1));
     }
-    if (warp == 0) __syncwarp();  // the other lanes of the issuing warp wait here, not in a spin
-    if (!mbar_wait(done, ch & 1)) {
-      atomicExch(err, 2);
-      *sfail = 1;
-    }
-    __syncthreads();
-    tc_fence_after();
-    if (*sfail != 0) break;  // uniform over the CTA: tcgen05.ld is executed by whole warps
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      long long hi[16], lo[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+  } else if (warp == P_EPI + 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      long long g = 0;
+      int u = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < nitems; item += gridDim.x) {
+        const int slot = item / nrt;
+        if (!tc_slot(st[slot].k)) continue;
+        for (int ct = 0; ok && ct < nct; ++ct)
+          for (int ch = 0; ok && ch < nchunk; ++ch, ++u) {
+            const int acc = u & 1;
+            if (u >= 2 && !mbar_wait(smem_u32(&B->tempty[acc]), (uint32_t)(((u >> 1) - 1) & 1))) {
+              p_fail(B, err, 2);
+              ok = false;
+              break;
+            }
+            if (p_aborted(B)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t dacc = tmem + (uint32_t)(acc * 8 * TC_N);
+            const int q1 = min(nslab, (ch + 1) * SPC);
+            for (int q = ch * SPC; q < q1; ++q, ++g) {
+              const int sg = (int)(g % PS);
+              if (!mbar_wait(smem_u32(&B->full[sg]), (uint32_t)((g / PS) & 1))) {
+                p_fail(B, err, 3);
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a0 = sbase + sg * STAGE_BYTES, b0 = a0 + TC_A_SLAB;
+              // slice s of A times B slices t = 0 .. 7 - s in one MMA: the B
+              // slices lie one after another in shared memory with the same
+              // stride between 8-column groups, so they form one operand of
+              // 32 (8 - s) columns, whose block t lands on the accumulator of
+              // level s + t. The first MMA of a chunk (s = 0) covers all eight
+              // levels and starts them; every other one accumulates.
 #pragma unroll 1
-      for (int lev = 0; lev < TC_SLICES; ++lev) {
-        uint32_t v[16];
-        tmem_ld16(trow + (uint32_t)(lev * TC_N + h * 16), v);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const long long a = (long long)__float2int_rn(__uint_as_float(v[c]));
-          if (lev < 4) hi[c] = hi[c] * 128 + a;
-          else lo[c] = lo[c] * 128 + a;
-        }
+              for (int s = 0; s < TC_SLICES; ++s)
+                mma_bf16(dacc + (uint32_t)(s * TC_N), smem_desc(a0 + s * (TC_A_SLAB / TC_SLICES), 128, 256),
+                         smem_desc(b0, 128, 256), mma_idesc((uint32_t)(TC_N * (TC_SLICES - s))),
+                         (q == ch * SPC && s == 0) ? 0u : 1u);
+              mma_commit(smem_u32(&B->empty[sg]));
+            }
+            mma_commit(smem_u32(&B->tfull[acc]));  // arrives once this chunk's MMAs completed
+          }
       }
+      // every MMA issued has completed before TMEM is released (also after an abort)
+      mma_commit(smem_u32(&B->fin));
+      if (!mbar_wait(smem_u32(&B->fin), 0)) p_fail(B, err, 5);
+    }
+  } else {
+    // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (rows of the
+    // tile), columns 16 (w / 4) .. + 15
+    const int quarter = warp & 3, h = warp >> 2;
+    const int r = quarter * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * 16);
+    int u = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < nitems; item += gridDim.x) {
+      const int slot = item / nrt, rt = item - slot * nrt;
+      if (!tc_slot(st[slot].k)) continue;
+      const int64_t i = (int64_t)rt * TC_M + r;
+      const int e = erow[((int64_t)slot * nrt + rt) * TC_M + r];
+      for (int ct = 0; ok && ct < nct; ++ct) {
+        long long thi[16], tlo[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        thi[h][c] += hi[c];
-        tlo[h][c] += lo[c];
+        for (int c = 0; c < 16; ++c) thi[c] = tlo[c] = 0;
+        for (int ch = 0; ch < nchunk; ++ch, ++u) {
+          const int acc = u & 1;
+          bool got = mbar_wait(smem_u32(&B->tfull[acc]), (uint32_t)((u >> 1) & 1));
+          got = __all_sync(0xffffffffu, got) && !__any_sync(0xffffffffu, p_aborted(B));
+          if (!got) {
+            if (lane == 0) p_fail(B, err, 4);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          long long hi[16], lo[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+#pragma unroll 1
+          for (int lev = 0; lev < TC_SLICES; ++lev) {
+            uint32_t v[16];
+            tmem_ld16(trow + (uint32_t)(acc * 8 * TC_N + lev * TC_N), v);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const long long a = (long long)__float2int_rn(__uint_as_float(v[c]));
+              if (lev < 4) hi[c] = hi[c] * 128 + a;
+              else lo[c] = lo[c] * 128 + a;
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&B->tempty[acc]));  // this set may take the next chunk
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            thi[c] += hi[c];
+            tlo[c] += lo[c];
+          }
+        }
+        if (!ok || i >= n) continue;
+        const int* ec = ecol + ((int64_t)slot * nct + ct) * TC_N + h * 16;
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+          const int j = (ct * TC_N + h * 16 + c) >> 1;
+          if (j < nf) {
+            const int f0 = ec[c], f1 = ec[c + 1];
+            z64 x;
+            if (!int_to_double(thi[c], tlo[c], e + f0 - 35, &x.re))
+              x.re = scalbn(fma((double)tlo[c], 0x1p-28, (double)thi[c]), e + f0 - 35);
+            if (!int_to_double(thi[c + 1], tlo[c + 1], e + f1 - 35, &x.im))
+              x.im = scalbn(fma((double)tlo[c + 1], 0x1p-28, (double)thi[c + 1]), e + f1 - 35);
+            X[((int64_t)slot * nf + j) * n + i] = x;
+          }
+        }
       }
     }
-    tc_fence_before();
-    __syncthreads();  // the accumulators are read: the next chunk may overwrite them
-  }
-  const int64_t i = (int64_t)rt * TC_M + r;
-  if (*sfail == 0 && i < n) {
-    const int e = erow[((int64_t)slot * nrt + rt) * TC_M + r];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int c = 0; c < 16; c += 2) {
-        const int jp = ct * TC_N + h * 16 + c;
-        const int j = jp >> 1;
-        if (j < nf) {
-          const int f0 = ecol[((int64_t)slot * nct + ct) * TC_N + h * 16 + c];
-          const int f1 = ecol[((int64_t)slot * nct + ct) * TC_N + h * 16 + c + 1];
-          z64 x;
-          if (!int_to_double(thi[h][c], tlo[h][c], e + f0 - 35, &x.re))
-            x.re = scalbn(fma((double)tlo[h][c], 0x1p-28, (double)thi[h][c]), e + f0 - 35);
-          if (!int_to_double(thi[h][c + 1], tlo[h][c + 1], e + f1 - 35, &x.im))
-            x.im = scalbn(fma((double)tlo[h][c + 1], 0x1p-28, (double)thi[h][c + 1]), e + f1 - 35);
-          X[((int64_t)slot * nf + j) * n + i] = x;
-        }
-      }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P_TMEM_COLS) : "memory");
 }
 
 // ------------------------------------------------------------------ host
@@ -449,7 +528,7 @@ int tc_group_size(int64_t n, int nf, int K, int nslot) {
 }
 
 void tc_prepare() {
-  cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+  cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM);
 }
 
 static inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -467,8 +546,12 @@ int launch_tc_assemble(const TcLayout& T, const SlotState* st, const z64* Z, int
   int* ecol = (int*)w;
   k_tc_slice_a<<<dim3(T.nrt, nslot), TC_M, 0, s>>>(st, Z, vsZ, n, T.nslab, T.nrt, As, erow);
   k_tc_slice_b<<<dim3(T.nct, nslot), TC_N, 0, s>>>(st, Y, mj, nf, m, T.nslab, T.nct, Bs, ecol);
-  k_tc_gemm<<<dim3(T.nct, T.nrt, nslot), 128, GEMM_SMEM, s>>>(st, (const unsigned char*)As, (const unsigned char*)Bs,
-                                                                erow, ecol, T.nslab, T.nrt, T.nct, n, nf, X, err);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = nslot * T.nrt;
+  k_tc_gemm<<<std::max(1, std::min(items, sms)), P_THREADS, P_SMEM, s>>>(
+      st, (const unsigned char*)As, (const unsigned char*)Bs, erow, ecol, T.nslab, T.nrt, T.nct, n, nf, nslot, X, err);
   return 3;
 }
 

@@ -163,9 +163,25 @@ struct Lane {
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
   int graph_outer = 0, graph_inner = 0;
+  // a second stream that copies x_j to host memory while the true residuals run
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_x = nullptr, ev_copied = nullptr;
+  void side_init() {
+    if (side) return;
+    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ev_x, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_copied, cudaEventDisableTiming));
+  }
   void release() {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+      cudaEventDestroy(ev_x);
+      cudaEventDestroy(ev_copied);
+      side = nullptr;
+    }
     ws.release();
     tcws.release();
     xws.release();
@@ -1242,6 +1258,7 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
   if (S.amg)
     CK(cudaMemcpyAsync(S.amg_tab, S.amg_table.data(), S.amg_table.size(), cudaMemcpyHostToDevice, s));
   z64* Xd = x_dev ? (z64*)X : S.X;
+  bool x_early = false;  // host x_j already being copied on the lane's side stream
   std::vector<SlotState> st_host(n_rhs);
   S.st_host = st_host.data();
   int64_t n = S.n;
@@ -1379,6 +1396,15 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
       PROF(FKS_K_ASSEMBLE, -1, ns * 16 * nn * (ks + n_f), ns * 8 * nn * ks * n_f,
            launch_assemble(S.Z, vsZ, S.Y, S.mj, n_f, m, Xd, n, n_rhs, s, use_tc ? S.st : nullptr, skip));
     }
+    if (!groups && !x_dev && X && res_true) {
+      // host x_j: copy them on the side stream while the true residuals run
+      lane->side_init();
+      CK(cudaEventRecord(lane->ev_x, s));
+      CK(cudaStreamWaitEvent(lane->side, lane->ev_x, 0));
+      copy_out(X, Xd, sizeof(z64) * n * n_f * n_rhs, lane->side);
+      CK(cudaEventRecord(lane->ev_copied, lane->side));
+      x_early = true;
+    }
     if (res_true && op->csr)
       PROF(FKS_K_TRES, -1, ns * (nn * (16.0 * n_f + 16) + n_f * op->cd.nnz * 36.0), ns * n_f * op->cd.nnz * 10.0,
            launch_csr_true_residual(op->cd.view<double>(n), S.sigma, n_f, S.b, Xd, S.tpart, S.st, S.tres, n_rhs, s));
@@ -1402,7 +1428,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
       copy_out(g.sst, S.sst + o0, sizeof(int32_t) * cnt, s);
     }
   } else {
-    if (!x_dev) copy_out(X, Xd, sizeof(z64) * n * n_f * n_rhs, s);
+    if (!x_dev && !x_early) copy_out(X, Xd, sizeof(z64) * n * n_f * n_rhs, s);
+    if (x_early) CK(cudaStreamWaitEvent(s, lane->ev_copied, 0));
     copy_out(res_est, S.est, sizeof(double) * n_f * n_rhs, s);
     copy_out(res_bound, S.bnd, sizeof(double) * n_f * n_rhs, s);
     if (res_true) copy_out(res_true, S.tres, sizeof(double) * n_f * n_rhs, s);

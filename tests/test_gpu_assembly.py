@@ -19,6 +19,9 @@ CASES = [
     dict(shape=(40, 24), n_f=7, periods=(5.0, 3600.0), n_p=3, seed=8),                  # ragged rows, odd n_f
     dict(shape=(64, 64), n_f=40, periods=(5.0, 3600.0), n_p=3, seed=5, n_src=3),        # 3 column tiles, 3 sources
     dict(shape=(12, 20, 10), n_f=17, periods=(5.0, 3600.0), n_p=2, seed=10, ss_var=0.25),  # 3D
+    # 424 row tiles x 2 sources: more (source, row tile) items than CTAs, so
+    # each persistent CTA runs several items through its ring and both TMEM sets
+    dict(shape=(256, 212), n_f=23, periods=(5.0, 3600.0), n_p=3, seed=6, n_src=2),
 ]
 
 
