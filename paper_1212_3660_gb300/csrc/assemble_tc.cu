@@ -104,6 +104,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -279,12 +286,13 @@ __global__ void __launch_bounds__(TC_N) k_tc_slice_b(const SlotState* __restrict
 // accumulator sets, warp P_EPI (one lane) streams the slabs through a ring of
 // PS stages, and the epilogue warps drain the other set into 64-bit totals and
 // write x_j, so a tile's epilogue overlaps the next tile's MMAs: warp w reads
-// TMEM lanes 32 (w mod 4) .. + 31 (one row per thread) and the 16 columns of
-// half w / 4 of the tile, two warps per SM sub-partition to hide the latency
-// of the integer epilogue. Barriers: full/empty per stage, tfull/tempty per
-// accumulator set.
+// TMEM lanes 32 (w mod 4) .. + 31 (one row per thread) and the EPI_COLS columns
+// of group w / 4 of the tile, four warps per SM sub-partition to hide the
+// latency of the integer epilogue. Barriers: full/empty per stage,
+// tfull/tempty per accumulator set.
 constexpr int PS = 4;
-constexpr int P_EPI = 8;                   // epilogue warps
+constexpr int P_EPI = 16;                  // epilogue warps
+constexpr int EPI_COLS = TC_N * 4 / P_EPI; // columns of a tile per epilogue warp (8)
 constexpr int P_THREADS = 32 * (P_EPI + 2);
 constexpr uint32_t P_TMEM_COLS = 512;      // two sets of 8 levels x 32 columns
 
@@ -426,10 +434,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_gemm(const SlotState* __res
     }
   } else {
     // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (rows of the
-    // tile), columns 16 (w / 4) .. + 15
-    const int quarter = warp & 3, h = warp >> 2;
+    // tile), columns EPI_COLS (w / 4) .. + EPI_COLS - 1
+    const int quarter = warp & 3, cg = warp >> 2;
     const int r = quarter * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * 16);
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cg * EPI_COLS);
     int u = 0;
     bool ok = true;
     for (int item = blockIdx.x; ok && item < nitems; item += gridDim.x) {
@@ -438,9 +446,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_gemm(const SlotState* __res
       const int64_t i = (int64_t)rt * TC_M + r;
       const int e = erow[((int64_t)slot * nrt + rt) * TC_M + r];
       for (int ct = 0; ok && ct < nct; ++ct) {
-        long long thi[16], tlo[16];
+        long long thi[EPI_COLS], tlo[EPI_COLS];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) thi[c] = tlo[c] = 0;
+        for (int c = 0; c < EPI_COLS; ++c) thi[c] = tlo[c] = 0;
         for (int ch = 0; ch < nchunk; ++ch, ++u) {
           const int acc = u & 1;
           bool got = mbar_wait(smem_u32(&B->tfull[acc]), (uint32_t)((u >> 1) & 1));
@@ -451,15 +459,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_gemm(const SlotState* __res
             break;
           }
           tc_fence_after();
-          long long hi[16], lo[16];
+          long long hi[EPI_COLS], lo[EPI_COLS];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+          for (int c = 0; c < EPI_COLS; ++c) hi[c] = lo[c] = 0;
 #pragma unroll 1
           for (int lev = 0; lev < TC_SLICES; ++lev) {
-            uint32_t v[16];
-            tmem_ld16(trow + (uint32_t)(acc * 8 * TC_N + lev * TC_N), v);
+            uint32_t v[EPI_COLS];
+            tmem_ld8(trow + (uint32_t)(acc * 8 * TC_N + lev * TC_N), v);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < EPI_COLS; ++c) {
               const long long a = (long long)__float2int_rn(__uint_as_float(v[c]));
               if (lev < 4) hi[c] = hi[c] * 128 + a;
               else lo[c] = lo[c] * 128 + a;
@@ -469,16 +477,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_gemm(const SlotState* __res
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&B->tempty[acc]));  // this set may take the next chunk
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
+          for (int c = 0; c < EPI_COLS; ++c) {
             thi[c] += hi[c];
             tlo[c] += lo[c];
           }
         }
         if (!ok || i >= n) continue;
-        const int* ec = ecol + ((int64_t)slot * nct + ct) * TC_N + h * 16;
+        const int* ec = ecol + ((int64_t)slot * nct + ct) * TC_N + cg * EPI_COLS;
 #pragma unroll
-        for (int c = 0; c < 16; c += 2) {
-          const int j = (ct * TC_N + h * 16 + c) >> 1;
+        for (int c = 0; c < EPI_COLS; c += 2) {
+          const int j = (ct * TC_N + cg * EPI_COLS + c) >> 1;
           if (j < nf) {
             const int f0 = ec[c], f1 = ec[c + 1];
             z64 x;
