@@ -378,6 +378,7 @@ template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (TX == 32 ? 6 : 8) : 4) k_pre2d(LevelView<T> L, const SlotState* st, const cx<T>* __restrict__ invd,
                                                const z64* taus, const cx<T>* __restrict__ f, cx<T>* __restrict__ z,
                                                int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
+  pdl_enter();
   constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
   extern __shared__ __align__(16) unsigned char pre_smem[];
   cx<T>* sF = (cx<T>*)pre_smem;
@@ -456,6 +457,7 @@ __global__ void __launch_bounds__(256) k_post2d(LevelView<T> L, uint32_t mask, c
                                                 const cx<T>* __restrict__ z, cx<T>* __restrict__ zout, int64_t vs,
                                                 const cx<T>* __restrict__ zc, int64_t vsc, z64* __restrict__ Zk,
                                                 int64_t vsZk, int64_t zcol) {
+  pdl_enter();
   constexpr int RX = TX + 2 * FH, RY = TY + 2 * FH;
   extern __shared__ __align__(16) unsigned char post_smem[];
   cx<T>* sF = (cx<T>*)post_smem;
@@ -768,6 +770,7 @@ __device__ __forceinline__ void tail2d_residual(const TailPair<T>& q, int nx, in
 
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS, 1) k_tail2d(TailParams<T> P, const SlotState* st) {
+  pdl_enter();
   const int slot = blockIdx.x;
   if (!slot_running(st, slot)) return;
   extern __shared__ __align__(16) unsigned char t2_smem[];
@@ -1335,13 +1338,13 @@ void launch_pre2d(const LevelHost& F, const LevelHost& C, const SlotState* st, c
                   const cx<T>* f, cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot, int tile, cudaStream_t s) {
   if (tile == 8) {
     dim3 g(nb(F.nx, 8), nb(F.ny, 8), nslot);
-    k_pre2d<T, 8, 8><<<g, 256, fused_smem<T, 8, 8>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+    launch_pdl(k_pre2d<T, 8, 8>, g, 256, fused_smem<T, 8, 8>(), s, view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
   } else if (tile == 16) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
-    k_pre2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+    launch_pdl(k_pre2d<T, 16, 16>, g, 256, fused_smem<T, 16, 16>(), s, view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
   } else {
     dim3 g(nb(F.nx, 32), nb(F.ny, 32), nslot);
-    k_pre2d<T, 32, 32><<<g, 256, fused_smem<T, 32, 32>(), s>>>(view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
+    launch_pdl(k_pre2d<T, 32, 32>, g, 256, fused_smem<T, 32, 32>(), s, view<T>(F), st, invd, taus, f, z, vs, fc, vsc);
   }
   (void)C;
 }
@@ -1352,15 +1355,15 @@ void launch_post2d(const LevelHost& F, const LevelHost& C, uint32_t mask, const 
                    int tile, cudaStream_t s, z64* Zk, int64_t vsZk, int64_t zcol) {
   if (tile == 8) {
     dim3 g(nb(F.nx, 8), nb(F.ny, 8), nslot);
-    k_post2d<T, 8, 8><<<g, 256, fused_smem<T, 8, 8>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc, Zk,
+    launch_pdl(k_post2d<T, 8, 8>, g, 256, fused_smem<T, 8, 8>(), s, view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc, Zk,
                                                              vsZk, zcol);
   } else if (tile == 16) {
     dim3 g(nb(F.nx, 16), nb(F.ny, 16), nslot);
-    k_post2d<T, 16, 16><<<g, 256, fused_smem<T, 16, 16>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
+    launch_pdl(k_post2d<T, 16, 16>, g, 256, fused_smem<T, 16, 16>(), s, view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
                                                                  Zk, vsZk, zcol);
   } else {
     dim3 g(nb(F.nx, 32), nb(F.ny, 32), nslot);
-    k_post2d<T, 32, 32><<<g, 256, fused_smem<T, 32, 32>(), s>>>(view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
+    launch_pdl(k_post2d<T, 32, 32>, g, 256, fused_smem<T, 32, 32>(), s, view<T>(F), mask, st, invd, f, z, zout, vs, zc, vsc,
                                                                  Zk, vsZk, zcol);
   }
   (void)C;
@@ -1375,7 +1378,7 @@ void tail_prepare(size_t smem_bytes) {
 template <typename T>
 void launch_tail(const TailParams<T>& P, size_t smem_bytes, const SlotState* st, int nslot, cudaStream_t s) {
   if (P.pairs)
-    k_tail2d<T><<<nslot, TAIL_THREADS, smem_bytes, s>>>(P, st);
+    launch_pdl(k_tail2d<T>, nslot, TAIL_THREADS, smem_bytes, s, P, st);
   else
     launch_pdl(k_tail_vcycle<T>, nslot, TAIL_THREADS, smem_bytes, s, P, st);
 }
