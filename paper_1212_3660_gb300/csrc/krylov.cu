@@ -310,11 +310,6 @@ __global__ void k_new_v(const SlotState* st, const z64* __restrict__ w, int64_t 
   if (V32) V32[slot * vsV + (int64_t)k * n + c] = cvt<float>(v);
 }
 
-__device__ __forceinline__ z64 cdiv(z64 a, z64 b) {
-  double d = abs2(b);
-  return mk((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
-}
-
 __device__ __forceinline__ double cabs(z64 a) { return hypot(a.re, a.im); }
 
 // Per-shift least-squares update, one warp per (slot, shift).
@@ -328,7 +323,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   __shared__ z64 col[GV_WARPS][MAX_M + 1];
   __shared__ z64 yv[GV_WARPS][MAX_M];
   __shared__ z64 rhs[GV_WARPS][MAX_M];
-  __shared__ z64 dg[GV_WARPS][MAX_M];      // diagonal of R (or of the square factor)
+  __shared__ z64 dg[GV_WARPS][MAX_M];      // reciprocals of the diagonal of R (or of the square factor)
   __shared__ double rcs[GV_WARPS][MAX_M];  // this shift's stored rotations, staged
   __shared__ z64 rss[GV_WARPS][MAX_M];
   __shared__ z64 sc[GV_WARPS][2];   // pre (diagonal before the new rotation), g_k before it
@@ -416,9 +411,14 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
   // back substitution: R y = g (FGMRES) or the square factor (FFOM). The
   // diagonal is staged first and every column of R is loaded one step ahead,
   // so the dependent chain over i waits on arithmetic, not on memory.
+  // the reciprocals of the diagonal are formed here, by all lanes at once, so
+  // that the dependent chain below multiplies instead of dividing (an FP64
+  // division is a long dependent sequence on this GPU)
   for (int i = lane; i < k; i += 32) {
     rhs[warp][i] = gj[i];
-    dg[warp][i] = (variant == 1 && i == k - 1) ? sc[warp][0] : Rj[(int64_t)i * m + i];
+    const z64 d = (variant == 1 && i == k - 1) ? sc[warp][0] : Rj[(int64_t)i * m + i];
+    const double t = 1.0 / abs2(d);
+    dg[warp][i] = mk(d.re * t, -d.im * t);
   }
   __syncwarp();
   if (variant == 1 && lane == 0) rhs[warp][k - 1] = sc[warp][1];
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32) k_givens(SlotState* st, int nf,
       const int l = lane + 32 * q;
       nextv[q] = (i > 0 && l < i - 1) ? Rj[(int64_t)(i - 1) * m + l] : mk(0.0, 0.0);
     }
-    if (lane == 0) yv[warp][i] = cdiv(rhs[warp][i], dg[warp][i]);
+    if (lane == 0) yv[warp][i] = rhs[warp][i] * dg[warp][i];
     __syncwarp();
     z64 yi = yv[warp][i];
 #pragma unroll

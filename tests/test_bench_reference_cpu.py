@@ -52,3 +52,18 @@ def test_reference_arm_grid_workload_line(monkeypatch):
     assert abs(10 / est - line["value"]) <= 1e-9 * line["value"]
     assert abs(line["ms_per_step"] - 1000 * ex["cycle_s"]) <= 1e-9 * line["ms_per_step"]
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+
+
+def test_all_cores_oracle_baseline_runs_one_solve_per_core():
+    """The all-cores CPU baseline: spawned processes (one BLAS thread each) each
+    time the oracle model of one solve; the value is their sum and never below
+    the best single process."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1212_3660_gb300 import synth
+    pr = synth.make_problem((12, 12, 12), n_f=6, periods=(5.0, 3600.0), n_p=2, seed=3, m_max=30)
+    value, cores, seconds, desc = bench.oracle_model_all_cores(pr, 10, 40, 1e-10, reps=1)
+    assert cores >= 1 and seconds > 0 and value > 0
+    assert f"{cores} concurrent processes" in desc
+    single, _, _ = bench.oracle_model_sample(pr, 1, 10, 40, 1e-10)
+    assert value >= 0.5 * single   # the sum over processes is at least about one process's rate
