@@ -115,6 +115,9 @@ def parse():
     ap.add_argument("--cluster-max", type=int, default=None,
                     help="with --fuse-max: from the first level of at most this many cells down, the cluster "
                          "V-cycle kernel (0: off)")
+    ap.add_argument("--coop-max", type=int, default=None,
+                    help="with --fuse-max: the cooperative lower cycle from the first level of at most this many "
+                         "cells (default 0: off)")
     ap.add_argument("--variant", default="fgmres", choices=["fgmres", "ffom"])
     ap.add_argument("--precond", default="amg", choices=["amg", "jacobi"],
                     help="workload 7: preconditioner of the BiCGSTAB inner cycles")
@@ -1097,6 +1100,7 @@ def set_thresholds(fks, op, prec, args):
         fks.fks_op_set_cluster(op, prec, args.cluster_max)
     if args.tile8_max is not None:
         fks.fks_op_set_tiles8(op, prec, args.tile8_max)
+    fks.fks_op_set_coop(op, prec, args.coop_max or 0)
 
 
 def batched_sample(args, local, dist, world):
@@ -1149,6 +1153,7 @@ def batched_sample(args, local, dist, world):
            "converged_per_step": conv / reps, "solves_per_step": n_f * n_rhs,
            "arnoldi_steps_max": int(info_arr["steps"].max()), "inner_cycles_total": int(info_arr["inner_cycles"].sum()),
            "steps_timed": reps, "tiling": list(fks.fks_op_tiling(solver.op, prec)),
+           "coop_levels_max_cells": fks.fks_op_coop_max(solver.op, prec),
            "zchunks": fks.fks_op_zchunks(solver.op, prec)}
     del X_d
     solver.close()
@@ -1450,6 +1455,7 @@ def main():
             else ("stale: kernels changed since the ncu capture" if traffic_src else "no ncu capture recorded")
     tiling = fks.fks_op_tiling(solver.op, prec)
     zchunks = fks.fks_op_zchunks(solver.op, prec) if len(pr.shape) == 3 else None
+    coop_max = fks.fks_op_coop_max(solver.op, prec)
     # ---- the batched workload (3D 96^3, 64 well sources) beside the 128^3 line
     batched = None
     if args.workload == 3 and not args.no_compare and not args.no_batched:
@@ -1477,6 +1483,7 @@ def main():
                            "tile16_levels_max_cells": tiling[1], "tail_levels_max_cells": tiling[2],
                            "cluster_levels_max_cells": tiling[3], "tile8_levels_max_cells": tiling[4],
                            "zchunk_planes_per_level": zchunks,
+                           "coop_levels_max_cells": coop_max,
                            "launch_mode": args.launch_mode, "variant": args.variant,
                            "restart_len": args.restart,
                            "basis_bytes_per_source": (2 * (args.restart or pr.m_max) + 1) * n * 16},

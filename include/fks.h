@@ -463,6 +463,17 @@ fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes);
  * library switches it off by itself.
  */
 int fks_set_pdl(int on);
+/*
+ * Cooperative lower cycle (no counterpart in the paper): from the first
+ * multigrid level with at most max_cells cells (not the finest, above the tail
+ * kernel's levels) down to the coarsest, the V-cycle's phases run in one
+ * cooperative launch with grid-wide barriers between them, on the levels'
+ * vectors in device memory, instead of one launch per phase; 0 switches it off
+ * (the default). Results are bitwise those of the separate kernels.
+ * fks_op_autotune tries it. fks_op_coop_max reads the setting.
+ */
+fks_status fks_op_set_coop(fks_op* op, int precision, int64_t max_cells);
+fks_status fks_op_coop_max(fks_op* op, int precision, int64_t* max_cells);
 /* The z-chunk of every multigrid level of `precision` (planes[0 .. levels-1],
  * as fks_op_set_zchunk stores them); *levels receives the level count. */
 fks_status fks_op_zchunks(const fks_op* op, int precision, int32_t* planes, int cap, int* levels);
@@ -523,7 +534,8 @@ enum {
   FKS_K_CLUSTER = 15,  /* the V-cycle of the lower 2D levels in one 8-CTA cluster per source */
   FKS_K_PRE3D = 16,    /* 3D level: four pre-smoothing half sweeps + residual + restriction (z-march) */
   FKS_K_POST3D = 17,   /* 3D level: prolongation + four post-smoothing half sweeps (z-march) */
-  FKS_K_COUNT = 18
+  FKS_K_COOP = 18,     /* the lower levels' V-cycle in one cooperative launch */
+  FKS_K_COUNT = 19
 };
 /*
  * Time every launch of kernel class `kclass` (on level `level`, or every level

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libfks.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["capi.cu", "grid.cu", "grid3d.cu", "krylov.cu", "csr.cu", "assemble_tc.cu", "cluster.cu", "sensitivity.cu", "monitors.cu", "amg.cu"]
+SOURCES = ["capi.cu", "grid.cu", "grid3d.cu", "krylov.cu", "csr.cu", "assemble_tc.cu", "cluster.cu", "coop.cu", "sensitivity.cu", "monitors.cu", "amg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-g", "--expt-relaxed-constexpr"]
 

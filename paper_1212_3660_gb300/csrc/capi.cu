@@ -29,6 +29,7 @@
 #include "csr.cuh"
 #include "assemble_tc.cuh"
 #include "cluster.cuh"
+#include "coop.cuh"
 #include "sensitivity.cuh"
 #include "monitors.cuh"
 #include "amg.cuh"
@@ -279,6 +280,7 @@ struct fks_op {
   // from the first level with at most this many cells (and a cluster layout)
   // down, the V-cycle runs in the cluster kernel instead of the tail (0: off)
   int64_t cluster_max[2] = {0, 0};
+  int64_t coop_max[2] = {0, 0};       // cooperative lower cycle from the first level <= this (0: off)
   // planes per block of the fused 3D level kernels, per level (0: the whole level)
   int zchunk[2][MAX_LEVELS] = {{16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16},
                                {16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16}};
@@ -550,6 +552,18 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
   const int lc = cluster_level<VT>(S.op, &CP, &csmem);
   // first level of the single-launch lower part: the cluster kernel's, else the tail's
   int lt = lc >= 0 ? lc : tail_level<VT>(Ls, tail_max_of<VT>(S.op));
+  // or the cooperative lower cycle's, when it is on and starts above the tail
+  int lco = -1;
+  const int64_t cmx = S.op->coop_max[sizeof(VT) == 8 ? 0 : 1];
+  if (lc < 0 && cmx > 0) {
+    for (int l = 1; l < lt; ++l)
+      if (Ls[l].n <= cmx) {
+        lco = l;
+        break;
+      }
+    if (lco >= 0 && coop_capacity_vcycle<VT>() <= 0) lco = -1;
+  }
+  const int lp = lco >= 0 ? lco : lt;
   cudaStream_t s = S.s;
   auto F = [&](int l) { return (cx<VT>*)S.f[l]; };
   auto Zl = [&](int l) { return (cx<VT>*)S.z[l]; };
@@ -565,7 +579,7 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
   const int64_t t8 = S.op->tile8_max[sizeof(VT) == 8 ? 0 : 1];
   auto tile_of = [&](const LevelHost& L) { return L.n <= t8 ? 8 : (L.n <= t16 ? 16 : 32); };
   const int pix = sizeof(VT) == 8 ? 0 : 1;
-  for (int l = 0; l < lt; ++l) {
+  for (int l = 0; l < lp; ++l) {
     const LevelHost& L = Ls[l];
     if (fused_level_ok(L) && L.n <= fmax) {
       PROF(FKS_K_PRE2D, l, ns * (L.n * (3 * cv + (d + 1) * rv) + cv * Ls[l + 1].n),
@@ -592,7 +606,36 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
          launch_residual_restrict<VT>(L, Ls[l + 1], S.st, S.taus, F(l), Zl(l), L.n, F(l + 1), Ls[l + 1].n, S.nslot,
                                       s, bf));
   }
-  if (lc >= 0) {
+  if (lco >= 0) {
+    // levels lco .. coarsest in one cooperative launch
+    CoopParams<VT> P{};
+    P.nlev = nl - lco;
+    double tb = 0, tf = 0;
+    int64_t most = 0;
+    for (int l = lco; l < nl; ++l) {
+      const int i = l - lco;
+      P.L[i] = view<VT>(Ls[l]);
+      P.invd[i] = I(l);
+      P.f[i] = F(l);
+      P.z[i] = Zl(l);
+      P.rx[i] = Ls[l].rx; P.ry[i] = Ls[l].ry; P.rz[i] = Ls[l].rz;
+      tb += Ls[l].n * (8 * cv + d * rv);
+      tf += Ls[l].n * (8 * d + 6) * 4;
+      most = std::max<int64_t>(most, Ls[l].n);
+    }
+    const LevelHost& C = Ls[nl - 1];
+    P.Ainv = (const cx<VT>*)S.cinv;
+    P.nc = (int)C.n;
+    P.mask = S.op->mask;
+    P.taus = S.taus;
+    P.nslot = S.nslot;
+    tb += cv * C.n * C.n;
+    tf += 8.0 * C.n * C.n;
+    const int blocks = (int)std::min<int64_t>((most * S.nslot + 255) / 256, INT_MAX);
+    bool ok = false;
+    PROF(FKS_K_COOP, lco, ns * tb, ns * tf, ok = launch_coop_vcycle<VT>(P, S.st, blocks, s));
+    if (!ok) throw CudaError{cudaErrorLaunchFailure, "cooperative lower V-cycle launch"};
+  } else if (lc >= 0) {
     // levels lc .. coarsest in one cluster per slot
     CP.mask = S.op->mask;
     CP.f_in = F(lc);
@@ -646,8 +689,8 @@ static cx<VT>* vcycle(Solve& S, z64* Zk = nullptr, int64_t vsZk = 0, int64_t zco
     if (!P.blob) P.pairs = 0;
     PROF(FKS_K_TAIL, lt, ns * tb, ns * tf, launch_tail<VT>(P, tsm, S.st, S.nslot, s));
   }
-  cx<VT>* zfin = Zl(lt);  // final correction of the level below
-  for (int l = lt - 1; l >= 0; --l) {
+  cx<VT>* zfin = Zl(lp);  // final correction of the level below
+  for (int l = lp - 1; l >= 0; --l) {
     const LevelHost& L = Ls[l];
     if (fused_level_ok(L) && L.n <= fmax) {
       cx<VT>* out = (cx<VT>*)S.z2[l];
@@ -1307,6 +1350,8 @@ static fks_status solve_impl(fks_op* op, Lane* lane, const fks_c128* b, int n_rh
                                  (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L, (double)S.batching};
       for (int pz = 0; pz < 2; ++pz)
         for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
+      key.push_back((double)op->coop_max[0]);
+      key.push_back((double)op->coop_max[1]);
       key.push_back((double)pdl_flag());
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);
@@ -2199,6 +2244,21 @@ fks_status fks_op_set_cluster(fks_op* op, int precision, int64_t max_cells) {
   return FKS_OK;
 }
 
+fks_status fks_op_set_coop(fks_op* op, int precision, int64_t max_cells) {
+  if (!op) { set_error("fks_op_set_coop: NULL operator"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_set_coop: bad precision"); return FKS_ERR_ARG; }
+  if (max_cells < 0) { set_error("fks_op_set_coop: max_cells must be >= 0"); return FKS_ERR_ARG; }
+  op->coop_max[precision == FKS_PREC_FP64 ? 0 : 1] = max_cells;
+  return FKS_OK;
+}
+
+fks_status fks_op_coop_max(fks_op* op, int precision, int64_t* max_cells) {
+  if (!op || !max_cells) { set_error("fks_op_coop_max: NULL argument"); return FKS_ERR_ARG; }
+  if (!prec_ok(precision)) { set_error("fks_op_coop_max: bad precision"); return FKS_ERR_ARG; }
+  *max_cells = op->coop_max[precision == FKS_PREC_FP64 ? 0 : 1];
+  return FKS_OK;
+}
+
 int fks_set_pdl(int on) {
   const int prev = fks::pdl_flag();
   if (on >= 0) fks::pdl_flag() = on ? 1 : 0;
@@ -2244,7 +2304,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   int pi = precision == FKS_PREC_FP64 ? 0 : 1;
   int64_t saved = op->fuse_max[pi], saved16 = op->tile16_max[pi], savedt = op->tail_max[pi];
-  int64_t savedc = op->cluster_max[pi], saved8 = op->tile8_max[pi];
+  int64_t savedc = op->cluster_max[pi], saved8 = op->tile8_max[pi], savedco = op->coop_max[pi];
   int savedz[MAX_LEVELS];
   std::memcpy(savedz, op->zchunk[pi], sizeof(savedz));
   try {
@@ -2291,6 +2351,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
       CK(cudaEventCreate(&e1));
       double best = 1e30;
       int64_t pick = saved, pick16 = saved16, pickt = savedt, pickc = savedc, pick8 = 0;
+      op->coop_max[pi] = 0;  // the other choices are timed without the cooperative lower cycle
       struct Choice { int64_t fuse, t16, tail, cl, t8; };
       std::vector<Choice> choices;
       // fusion choices for the levels above the single-launch lower part
@@ -2403,6 +2464,23 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
           op->zchunk[pi][l] = bestz;
         }
       }
+      // then the cooperative lower cycle from each level above the pick's tail
+      {
+        const Choice ch{pick, pick16, pickt, pickc, pick8};
+        int64_t pickco = 0;
+        if (pickc == 0 && coop_capacity_vcycle<VT>() > 0) {
+          const int lt = tail_level<VT>(op->levels, pickt);
+          for (int l = 1; l < lt; ++l) {
+            op->coop_max[pi] = op->levels[l].n;
+            const float ms = measure(ch);
+            if (ms < best) {
+              best = ms;
+              pickco = op->levels[l].n;
+            }
+          }
+        }
+        op->coop_max[pi] = pickco;
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       cudaStreamDestroy(cs);
@@ -2420,6 +2498,7 @@ fks_status fks_op_autotune(fks_op* op, int precision, fks_c128 tau, void* stream
     op->tail_max[pi] = savedt;
     op->cluster_max[pi] = savedc;
     op->tile8_max[pi] = saved8;
+    op->coop_max[pi] = savedco;
     std::memcpy(op->zchunk[pi], savedz, sizeof(savedz));
     set_error(std::string("fks_op_autotune: ") + e.where + ": " + cudaGetErrorString(e.e));
     return FKS_ERR_CUDA;
@@ -3219,6 +3298,8 @@ struct Batch : BatchBase {
                                  (double)(S.amg ? op->amg.gen : -1), (double)S.amg_L, 1.0};
       for (int pz = 0; pz < 2; ++pz)
         for (int l = 0; l < MAX_LEVELS; ++l) key.push_back((double)op->zchunk[pz][l]);
+      key.push_back((double)op->coop_max[0]);
+      key.push_back((double)op->coop_max[1]);
       key.push_back((double)pdl_flag());
       if (!lane->graph || lane->graph_key != key) {
         if (lane->graph) cudaGraphExecDestroy(lane->graph);

@@ -24,7 +24,7 @@ FKS_ERR_ARG, FKS_ERR_OOM, FKS_ERR_CUDA, FKS_ERR_TIMEOUT, FKS_ERR_CANCELLED = -1,
 FKS_FGMRES, FKS_FFOM = 0, 1
 FKS_PREC_FP64, FKS_PREC_MIXED, FKS_PREC_MIXED_BF16 = 0, 1, 2
 KERNEL_CLASSES = ["smooth", "restrict", "prolong", "coarse", "defect", "correct", "mdot", "maxpy", "givens",
-                  "assemble", "tres", "tail", "pre2d", "post2d", "bicgstab", "cluster", "pre3d", "post3d"]
+                  "assemble", "tres", "tail", "pre2d", "post2d", "bicgstab", "cluster", "pre3d", "post3d", "coop"]
 
 
 class fks_c128(C.Structure):
@@ -113,6 +113,8 @@ def lib():
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.fks_op_set_zchunk.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.fks_set_pdl.argtypes = [C.c_int]
+    L.fks_op_set_coop.argtypes = [vp, C.c_int, C.c_int64]
+    L.fks_op_coop_max.argtypes = [vp, C.c_int, C.POINTER(C.c_int64)]
     L.fks_set_pdl.restype = C.c_int
     L.fks_op_zchunks.argtypes = [vp, C.c_int, C.POINTER(C.c_int32), C.c_int, C.POINTER(C.c_int)]
     L.fks_server_create.argtypes = [vp, C.c_size_t, C.c_int, C.POINTER(vp)]
@@ -131,7 +133,7 @@ def lib():
     for name in ("fks_create", "fks_op_grid", "fks_op_csr", "fks_op_amg", "fks_op_amg_setup", "fks_op_amg_info", "fks_amg_host_shape", "fks_solve", "fks_op_apply", "fks_sensitivity", "fks_ritz", "fks_precond_apply", "fks_profile_select",
                  "fks_profile_read", "fks_precond_apply_noalloc", "fks_op_autotune",
                  "fks_op_set_fusion", "fks_op_set_tiles", "fks_op_set_tail", "fks_op_set_cluster", "fks_op_set_tiles8", "fks_op_tiling",
-                 "fks_op_set_zchunk", "fks_op_zchunks",
+                 "fks_op_set_zchunk", "fks_op_zchunks", "fks_op_set_coop", "fks_op_coop_max",
                  "fks_server_create",
                  "fks_server_submit", "fks_server_poll", "fks_server_wait",
                  "fks_server_cancel", "fks_server_times", "fks_server_launches"):
@@ -398,6 +400,21 @@ def fks_op_set_tiles8(op, precision, max_cells):
     st = lib().fks_op_set_tiles8(op, int(precision), int(max_cells))
     if st != FKS_OK:
         raise FksError(st, fks_last_error())
+
+
+def fks_op_set_coop(op, precision, max_cells):
+    """Cooperative lower cycle from the first level of at most max_cells cells (0: off)."""
+    st = lib().fks_op_set_coop(op, int(precision), int(max_cells))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+
+
+def fks_op_coop_max(op, precision):
+    v = C.c_int64(0)
+    st = lib().fks_op_coop_max(op, int(precision), C.byref(v))
+    if st != FKS_OK:
+        raise FksError(st, fks_last_error())
+    return int(v.value)
 
 
 def fks_set_pdl(on):

@@ -405,6 +405,40 @@ def test_launch_overlap_changes_no_bits(shape):
         s.close()
 
 
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED, fks.FKS_PREC_MIXED_BF16])
+@pytest.mark.parametrize("shape,n_src", [((32, 48, 40), 2), ((160, 128), 1), ((45, 45, 45), 1)])
+def test_cooperative_lower_cycle_agrees_bitwise(precision, shape, n_src):
+    """The lower levels' V-cycle in one cooperative launch (from every level
+    above the tail, down to the coarsest, on even and ragged hierarchies, in
+    the graph and host-driven loops) gives the bits of the separate kernels."""
+    need_gpu()
+    pr = synth.make_problem(shape, n_f=5, periods=(5.0, 3600.0), n_p=3, seed=37, n_src=n_src, m_max=60)
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, 0)
+    fks.fks_op_set_tail(s.op, precision, 64)
+    fks.fks_op_set_coop(s.op, precision, 0)
+    a = s.solve(precision=precision, inner_tol=1e-10)
+    assert a.status == fks.FKS_OK
+    sizes = sorted({int(np.prod(L)) for L in _level_shapes(shape)[1:] if int(np.prod(L)) > 64}, reverse=True)
+    assert sizes
+    for cm in sizes:
+        fks.fks_op_set_coop(s.op, precision, cm)
+        assert fks.fks_op_coop_max(s.op, precision) == cm
+        for mode in (0, 1):
+            d = s.solve(precision=precision, inner_tol=1e-10, launch_mode=mode)
+            assert np.array_equal(a.X, d.X), (cm, mode)
+            assert np.array_equal(a.inner_cycles, d.inner_cycles), (cm, mode)
+    fks.fks_op_set_coop(s.op, precision, 0)
+    s.close()
+
+
+def _level_shapes(shape):
+    """The multigrid level shapes of a grid (numpy axis order), as the oracle forms them."""
+    op = oracle.assemble(shape, (1.0,) * len(shape), np.ones(shape), np.ones(shape), (1 << (2 * len(shape))) - 1)
+    from oracle.gmg import Hierarchy
+    return [L.shape for L in Hierarchy(op, [1j]).levels]
+
+
 def test_cluster_vcycle_rejects_inapplicable_levels():
     """48 x 48 coarsens to 24 x 24 (3 rows per band, followed by a 12-row level
     that does not split into 8 bands): no starting level qualifies."""
