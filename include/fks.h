@@ -457,8 +457,8 @@ fks_status fks_op_set_zchunk(fks_op* op, int precision, int level, int planes);
  * kernels are launched with programmatic dependent launch, so that each one's
  * blocks are scheduled while its predecessor finishes (they wait for the
  * predecessor's results before reading memory). on = 1 (the default) or 0 sets
- * it for the whole process; a negative value only queries. Returns the previous
- * setting. Results are the same bits either way; graphs built before a change
+ * it for the whole process (call it while no solve or server is running); a
+ * negative value only queries. Returns the previous setting. Results are the same bits either way; graphs built before a change
  * are rebuilt at their next use. If a graph capture refuses the overlap, the
  * library switches it off by itself.
  */
