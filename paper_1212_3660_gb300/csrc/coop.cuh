@@ -1,7 +1,8 @@
-// Cooperative V-cycle of the lower multigrid levels: one grid-synchronised
-// launch runs every phase of levels lc .. coarsest (half sweeps, residual and
-// restriction, the coarsest dense solve, interpolation) on the levels' global
-// vectors, with the per-cell arithmetic of the per-level kernels.
+// Cooperative V-cycle of the lower multigrid levels: one launch runs every
+// phase of levels lc .. coarsest (half sweeps, residual and restriction, the
+// coarsest dense solve, interpolation) on the levels' global vectors, with the
+// per-cell arithmetic of the per-level kernels, as one thread-block cluster
+// per source (levels of at most 65536 cells) or one cooperative grid.
 #pragma once
 #include "common.cuh"
 
@@ -22,13 +23,13 @@ struct CoopParams {
   int nslot;
 };
 
-// Blocks of 256 threads that can be resident together for this kernel on the
-// current device (0: no cooperative launch).
+// Positive when either form can be launched on the current device (0: neither).
 template <typename T>
 int coop_capacity_vcycle();
 
-// Launches the cooperative V-cycle with `blocks` blocks (at most the capacity);
-// false when the launch was refused (the caller then runs the separate kernels).
+// Launches the lower V-cycle: one cluster per source, or a cooperative grid of
+// `blocks` blocks (at most what can be resident); false when the launch was
+// refused.
 template <typename T>
 bool launch_coop_vcycle(const CoopParams<T>& P, const SlotState* st, int blocks, cudaStream_t s);
 
