@@ -194,9 +194,10 @@ typedef struct {
   int inner_steps;       /* CSR operators: BiCGSTAB steps per inner cycle (<= 0 means 8, or 4
                             with AMG; at most 64); ignored by grid operators                  */
   int assembly;          /* x_j = Z y_j (Algorithm 4): 0 = tensor cores (Z and Y cut into eight
-                            7-bit bf16 slices, exact fp32 accumulation of the slice products,
-                            error at the level of an FP64 GEMM; used when 2 * steps <= 128,
-                            else the FP64 kernel); 1 = FP64 FMA kernel                         */
+                            7-bit bf16 slices, exact fp32 accumulation of the slice products
+                            over chunks of at most 64 steps, the chunks added in 64-bit
+                            integers; error at the level of an FP64 GEMM; any step count up
+                            to 128); 1 = FP64 FMA kernel                                       */
   double inner_relax;    /* l > 0: relaxed inner tolerance, step k uses
                             min(1e-3, max(eps, l * tol / R_{k-1})) with R_{k-1} the largest
                             ||beta e_1 - H_bar(sigma_j) y|| / beta of the shifts still iterating

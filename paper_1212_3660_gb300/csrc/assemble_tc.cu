@@ -104,22 +104,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+// eight columns of the warp's 32 TMEM lanes; the values may be used only after tmem_wait
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Sources whose step count keeps the padded 2K within the exactness bound.
 __host__ __device__ __forceinline__ bool tc_slot(int K) {
@@ -462,15 +454,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_tc_gemm(const SlotState* __res
           long long hi[EPI_COLS], lo[EPI_COLS];
 #pragma unroll
           for (int c = 0; c < EPI_COLS; ++c) hi[c] = lo[c] = 0;
+          // two levels per wait: the second load is in flight with the first
 #pragma unroll 1
-          for (int lev = 0; lev < TC_SLICES; ++lev) {
-            uint32_t v[EPI_COLS];
-            tmem_ld8(trow + (uint32_t)(acc * 8 * TC_N + lev * TC_N), v);
+          for (int lev = 0; lev < TC_SLICES; lev += 2) {
+            uint32_t v0[EPI_COLS], v1[EPI_COLS];
+            tmem_ld8_async(trow + (uint32_t)(acc * 8 * TC_N + lev * TC_N), v0);
+            tmem_ld8_async(trow + (uint32_t)(acc * 8 * TC_N + (lev + 1) * TC_N), v1);
+            tmem_wait();
 #pragma unroll
             for (int c = 0; c < EPI_COLS; ++c) {
-              const long long a = (long long)__float2int_rn(__uint_as_float(v[c]));
-              if (lev < 4) hi[c] = hi[c] * 128 + a;
-              else lo[c] = lo[c] * 128 + a;
+              const long long a0 = (long long)__float2int_rn(__uint_as_float(v0[c]));
+              const long long a1 = (long long)__float2int_rn(__uint_as_float(v1[c]));
+              if (lev < 4) hi[c] = (hi[c] * 128 + a0) * 128 + a1;
+              else lo[c] = (lo[c] * 128 + a0) * 128 + a1;
             }
           }
           tc_fence_before();
