@@ -295,6 +295,57 @@ __global__ void k_residual_restrict(LevelView<T, C> F, int rx, int ry, int rz, i
   fc[slot * vsc + (int64_t)row * cnx + I] = restrict_value(F, rx, ry, rz, I, J, K, s, f + slot * vs, z + slot * vs);
 }
 
+// Coarse right-hand side on a 3D level coarsened by 2 in every axis, one
+// source per block. The per-coarse-cell loop of k_residual_restrict computes
+// its eight children one after another; here the block's 256 threads first
+// compute the fine residuals f - A z of a 32 x 8 x 2 tile, one (i, j) column
+// of two planes each, into shared memory, then one thread per coarse cell
+// adds its children in restrict_value's order (z, then y, then x child),
+// skipping those past the fine grid, so the sum is bitwise the same.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) k_residual_restrict3(LevelView<T, C> F, int cnx, int cny, int cnz,
+                                                            const SlotState* st, const z64* taus,
+                                                            const cx<T>* __restrict__ f, const cx<T>* __restrict__ z,
+                                                            int64_t vs, cx<T>* __restrict__ fc, int64_t vsc) {
+  pdl_enter();
+  __shared__ cx<T> sr[2][GY][GX];
+  const int slot = blockIdx.z;
+  if (!slot_running(st, slot)) return;
+  const int nby = (F.ny + GY - 1) / GY;
+  const int K = blockIdx.y / nby, by = blockIdx.y - K * nby;
+  const int i = blockIdx.x * GX + threadIdx.x, j = by * GY + threadIdx.y;
+  const cx<T> s = cvt<T>(taus[st[slot].tau]);
+  const cx<T>* fs = f + slot * vs;
+  const cx<T>* zs = z + slot * vs;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int k = 2 * K + q;
+    cx<T> r = mk(T(0), T(0));
+    if (i < F.nx && j < F.ny && k < F.nz) {
+      const int64_t cc = ((int64_t)k * F.ny + j) * F.nx + i;
+      r = fs[cc] - apply_at(F, Cell{i, j, k}, cc, s, zs);
+    }
+    sr[q][threadIdx.y][threadIdx.x] = r;
+  }
+  __syncthreads();
+  const int t = threadIdx.y * GX + threadIdx.x;
+  if (t >= (GX / 2) * (GY / 2)) return;
+  const int ti = t % (GX / 2), tj = t / (GX / 2);
+  const int I = blockIdx.x * (GX / 2) + ti, J = by * (GY / 2) + tj;
+  if (I >= cnx || J >= cny) return;
+  cx<T> acc = mk(T(0), T(0));
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        if (2 * I + a >= F.nx || 2 * J + b >= F.ny || 2 * K + c >= F.nz) continue;
+        acc = acc + sr[c][2 * tj + b][2 * ti + a];
+      }
+  fc[slot * vsc + ((int64_t)K * cny + J) * cnx + I] = acc;
+}
+
 // z_fine += P z_coarse
 template <typename T>
 __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, int cny, int cnz, uint32_t mask,
@@ -331,6 +382,13 @@ __global__ void __launch_bounds__(256) k_prolong_add3(LevelView<T> F, int cnx, i
   const int X0 = x0 / 2 - 1, Y0 = y0 / 2 - 1;
   const int K = k >> 1, K2 = (k & 1) ? K + 1 : K - 1;
   const cx<T>* zcs = zc + slot * vsc;
+  // the cell's own value is loaded before the staging barrier, so its latency
+  // overlaps that of the coarse values
+  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+  const bool own = i < F.nx && j < F.ny;
+  const int64_t c = ((int64_t)k * F.ny + j) * F.nx + i;
+  cx<T>* zs = z + slot * vs;
+  const cx<T> z0 = own ? zs[c] : mk(T(0), T(0));
   const int t = threadIdx.y * GX + threadIdx.x;
   if (t < 2 * SY * SX) {
     const int q = t / (SY * SX), rem = t - q * (SY * SX);
@@ -340,11 +398,8 @@ __global__ void __launch_bounds__(256) k_prolong_add3(LevelView<T> F, int cnx, i
     sc[q][yy][xx] = in ? zcs[((int64_t)Z * cny + Y) * cnx + X] : mk(T(0), T(0));
   }
   __syncthreads();
-  const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
-  if (i >= F.nx || j >= F.ny) return;
-  const int64_t c = ((int64_t)k * F.ny + j) * F.nx + i;
-  cx<T>* zs = z + slot * vs;
-  zs[c] = zs[c] + prolong_value_at<T>(Cell{i, j, k}, 2, 2, 2, cnx, cny, cnz, mask, [&](int X, int Y, int Z) {
+  if (!own) return;
+  zs[c] = z0 + prolong_value_at<T>(Cell{i, j, k}, 2, 2, 2, cnx, cny, cnz, mask, [&](int X, int Y, int Z) {
             return sc[Z == K ? 0 : 1][Y - Y0][X - X0];
           });
 }
@@ -1291,6 +1346,20 @@ void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const Slot
                               const cx<T>* f, const cx<T>* z, int64_t vs, cx<T>* fc, int64_t vsc, int nslot,
                               cudaStream_t s, int bf16) {
   const int G = spmm_group(nslot), rb = GY / G;
+  if (G == 1 && F.nz > 1 && F.rx == 2 && F.ry == 2 && F.rz == 2 && (int64_t)nb(F.ny, GY) * C.nz <= 65535) {
+    // one source: the tile form (with several, the per-coarse-cell form reads
+    // each coefficient once for the block's sources)
+    const dim3 g3(nb(F.nx, GX), nb(F.ny, GY) * C.nz, nslot);
+    if constexpr (sizeof(T) == 4) {
+      if (bf16) {
+        launch_pdl(k_residual_restrict3<T, __nv_bfloat16>, g3, B2, 0, s, view_as<T, __nv_bfloat16>(F), C.nx, C.ny,
+                   C.nz, st, taus, f, z, vs, fc, vsc);
+        return;
+      }
+    }
+    launch_pdl(k_residual_restrict3<T, T>, g3, B2, 0, s, view<T>(F), C.nx, C.ny, C.nz, st, taus, f, z, vs, fc, vsc);
+    return;
+  }
   const dim3 blk(GX, rb, G), grd(nb(C.nx, GX), nb((int64_t)C.ny * C.nz, rb), nb(nslot, G));
   if constexpr (sizeof(T) == 4) {
     if (bf16) {

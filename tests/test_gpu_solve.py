@@ -360,6 +360,27 @@ def test_ragged_hierarchy_paths_agree_bitwise(precision):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [fks.FKS_PREC_FP64, fks.FKS_PREC_MIXED, fks.FKS_PREC_MIXED_BF16])
+def test_one_source_restriction_agrees_with_batched_form(precision):
+    """A lone source restricts 3D levels in 32 x 8 x 2 tiles (fine residuals
+    first, then the sum over children); a batch of sources uses one thread per
+    coarse cell for all of its sources. On 18 x 22 x 26, whose hierarchy
+    continues ragged below 9 x 11 x 13 (children past the odd sides skipped),
+    each source alone gives the bits it gets inside the batch."""
+    need_gpu()
+    pr = synth.make_problem((18, 22, 26), n_f=5, periods=(5.0, 3600.0), n_p=3, seed=41, n_src=2, m_max=60)
+    s = Solver(pr)
+    fks.fks_op_set_fusion(s.op, precision, 0)
+    fks.fks_op_set_tail(s.op, precision, 1)
+    both = s.solve(precision=precision, inner_tol=1e-10)
+    assert both.status == fks.FKS_OK
+    for r in range(2):
+        alone = s.solve(b=pr.rhs().T[r:r + 1].copy(), precision=precision, inner_tol=1e-10)
+        assert np.array_equal(alone.X[0], both.X[r]), r
+        assert np.array_equal(alone.inner_cycles[0], both.inner_cycles[r]), r
+    s.close()
+
+
 @pytest.mark.parametrize("shape", [(289, 289), (45, 45, 45)])
 def test_odd_aquifers_certify_every_shift(shape):
     """Odd-sided aquifers whose hierarchies are ragged from the finest level
