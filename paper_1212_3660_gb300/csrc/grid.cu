@@ -362,46 +362,53 @@ __global__ void k_prolong_add(LevelView<T> F, int rx, int ry, int rz, int cnx, i
 }
 
 // z_fine += P z_coarse on a 3D level coarsened by 2 in every axis: a block
-// updates 32 x 8 cells of one plane and first stages the 18 x 6 x 2 coarse
-// values they interpolate from (their parents' plane and the neighbouring
-// coarse plane on the child's side) in shared memory, so each coarse value is
-// read once per block instead of once per fine cell; the interpolation itself
-// is prolong_value_at's, on those values.
+// updates 32 x 8 cells in each of the two fine planes of coarse plane K and
+// first stages the 18 x 6 x 3 coarse values they interpolate from (planes K -
+// 1, K and K + 1) in shared memory, so each coarse value is read once per
+// block instead of once per fine cell; the interpolation itself is
+// prolong_value_at's, on those values.
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add3(LevelView<T> F, int cnx, int cny, int cnz, uint32_t mask,
                                                       const SlotState* st, const cx<T>* __restrict__ zc,
                                                       int64_t vsc, cx<T>* __restrict__ z, int64_t vs) {
   pdl_enter();
   constexpr int SX = GX / 2 + 2, SY = GY / 2 + 2;
-  __shared__ cx<T> sc[2][SY][SX];
+  __shared__ cx<T> sc[3][SY][SX];
   const int slot = blockIdx.z;
   if (!slot_running(st, slot)) return;
   const int nby = (F.ny + GY - 1) / GY;
-  const int k = blockIdx.y / nby, by = blockIdx.y - k * nby;
+  const int K = blockIdx.y / nby, by = blockIdx.y - K * nby;
   const int x0 = blockIdx.x * GX, y0 = by * GY;
   const int X0 = x0 / 2 - 1, Y0 = y0 / 2 - 1;
-  const int K = k >> 1, K2 = (k & 1) ? K + 1 : K - 1;
   const cx<T>* zcs = zc + slot * vsc;
-  // the cell's own value is loaded before the staging barrier, so its latency
-  // overlaps that of the coarse values
+  // the cells' own values are loaded before the staging barrier, so their
+  // latency overlaps that of the coarse values
   const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
-  const bool own = i < F.nx && j < F.ny;
-  const int64_t c = ((int64_t)k * F.ny + j) * F.nx + i;
   cx<T>* zs = z + slot * vs;
-  const cx<T> z0 = own ? zs[c] : mk(T(0), T(0));
-  const int t = threadIdx.y * GX + threadIdx.x;
-  if (t < 2 * SY * SX) {
+  bool own[2];
+  int64_t c[2];
+  cx<T> z0[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int k = 2 * K + q;
+    own[q] = i < F.nx && j < F.ny && k < F.nz;
+    c[q] = ((int64_t)k * F.ny + j) * F.nx + i;
+    z0[q] = own[q] ? zs[c[q]] : mk(T(0), T(0));
+  }
+  for (int t = threadIdx.y * GX + threadIdx.x; t < 3 * SY * SX; t += GX * GY) {
     const int q = t / (SY * SX), rem = t - q * (SY * SX);
     const int yy = rem / SX, xx = rem - yy * SX;
-    const int X = X0 + xx, Y = Y0 + yy, Z = q == 0 ? K : K2;
+    const int X = X0 + xx, Y = Y0 + yy, Z = K - 1 + q;
     const bool in = X >= 0 && X < cnx && Y >= 0 && Y < cny && Z >= 0 && Z < cnz;
     sc[q][yy][xx] = in ? zcs[((int64_t)Z * cny + Y) * cnx + X] : mk(T(0), T(0));
   }
   __syncthreads();
-  if (!own) return;
-  zs[c] = z0 + prolong_value_at<T>(Cell{i, j, k}, 2, 2, 2, cnx, cny, cnz, mask, [&](int X, int Y, int Z) {
-            return sc[Z == K ? 0 : 1][Y - Y0][X - X0];
-          });
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!own[q]) continue;
+    zs[c[q]] = z0[q] + prolong_value_at<T>(Cell{i, j, 2 * K + q}, 2, 2, 2, cnx, cny, cnz, mask,
+                                            [&](int X, int Y, int Z) { return sc[Z - K + 1][Y - Y0][X - X0]; });
+  }
 }
 
 // --------------------------------------------------------------------- fused 2D level kernels
@@ -1375,8 +1382,8 @@ void launch_residual_restrict(const LevelHost& F, const LevelHost& C, const Slot
 template <typename T>
 void launch_prolong_add(const LevelHost& F, const LevelHost& C, uint32_t mask, const SlotState* st, const cx<T>* zc,
                         int64_t vsc, cx<T>* z, int64_t vs, int nslot, cudaStream_t s) {
-  if (F.nz > 1 && F.rx == 2 && F.ry == 2 && F.rz == 2 && (int64_t)nb(F.ny, GY) * F.nz <= 65535) {
-    const dim3 g(nb(F.nx, GX), nb(F.ny, GY) * F.nz, nslot);
+  if (F.nz > 1 && F.rx == 2 && F.ry == 2 && F.rz == 2 && (int64_t)nb(F.ny, GY) * C.nz <= 65535) {
+    const dim3 g(nb(F.nx, GX), nb(F.ny, GY) * C.nz, nslot);
     launch_pdl(k_prolong_add3<T>, g, B2, 0, s, view<T>(F), C.nx, C.ny, C.nz, mask, st, zc, vsc, z, vs);
     return;
   }
