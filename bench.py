@@ -15,13 +15,15 @@ outer Arnoldi / least squares / assembly / true residual ("mixed"). Its
 the batched workload 4 (3D 96^3, 64 well sources, 100 shifts).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-                  [--workload 1|2|3|4|5|6|7] [--precision fp64|mixed]
+                  [--workload 1|2|3|4|5|6|7|8] [--precision fp64|mixed]
 
 Workload 5 is the serving stream (request loop); workload 6 the sensitivity
 matrix of workload 2's aquifer (Algorithm 6: forward solve, adjoint solves of 8
 sensors, adjoint-state inner products for ln K and ln S_s), in Jacobian rows/s;
 workload 7 a general sparse operator through the CSR path (K and M as CSR
-arrays, BiCGSTAB inner cycles).
+arrays, BiCGSTAB inner cycles); workload 8 the mixed 2D batch (32 aquifers of
+128^2 to 384^2 cells, one source each, 100 shifts) through the server's
+concurrent lanes.
 
 Under torchrun every rank solves its own copy of the workload (replicas, weak
 scaling; no data-path collective). Prints one JSON line on rank 0.
@@ -104,6 +106,7 @@ def parse():
     ap.add_argument("--latency-requests", type=int, default=150,
                     help="workload 5: requests of each Poisson latency run")
     ap.add_argument("--lanes", type=int, default=3, help="workload 5: concurrent server lanes")
+    ap.add_argument("--mix-lanes", type=int, default=8, help="workload 8: concurrent server lanes")
     ap.add_argument("--fuse-max", type=int, default=None,
                     help="fused 2D levels up to this many cells (-1: all) instead of autotuning")
     ap.add_argument("--tile16-max", type=int, default=None,
@@ -373,6 +376,137 @@ def serve_bench(args, rank, world, local, dist):
                                  "workload 1-4 lines",
                 "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
         print(json.dumps(line), flush=True)
+
+
+def mix2d_bench(args, rank, world, local, dist):
+    """The mixed 2D batch: 32 aquifers of 128^2 to 384^2 cells, one centre
+    source each, 100 shifts, 4 taus cycled. A step submits one request per
+    aquifer to the server, whose lanes run the different operators
+    concurrently, and ends when the last request's x_j are in host memory
+    (page-locked output arrays, allocated once and reused, as a client would).
+    Beside it, the same step on a one-lane server: one operator at a time."""
+    import torch
+
+    from paper_1212_3660_gb300 import fks, synth
+    prec = prec_of(args.precision, fks)
+    grids = synth.mix2d_grids()
+    ctx = fks.fks_create(local)
+    t0 = time.perf_counter()
+    probs = [synth.make_problem(m_max=100, **g) for g in grids]
+    ops = [fks.fks_op_grid(ctx, 2, [p.shape[1], p.shape[0]], p.h, p.cond, p.ss, p.dirichlet_mask) for p in probs]
+    setup_ms = 1000 * (time.perf_counter() - t0)
+    for p, op in zip(probs, ops):
+        fks.fks_op_autotune(op, prec, complex(p.tau_bar[len(p.tau_bar) // 2]))
+    outs_t = [torch.empty((1, len(p.sigma), p.n), dtype=torch.complex128, pin_memory=True) for p in probs]
+    outs = [t.numpy() for t in outs_t]   # views of the page-locked tensors (kept alive in outs_t)
+    rhs = [p.rhs().T.copy() for p in probs]
+    free, _ = torch.cuda.mem_get_info(local)
+    budget = int(free * 0.7)
+
+    def one_pass(srv):
+        t_start = time.perf_counter()
+        reqs = []
+        for g, p in enumerate(probs):
+            opts, keep = fks.make_options(tol=TOL, m_max=p.m_max, precision=prec, inner_tol=INNER_EPS,
+                                          schedule=p.schedule, inner_relax=args.inner_relax)
+            r = fks.ServerRequest(ops[g], rhs[g], p.sigma, p.tau_bar, opts, keep, p.n, out=outs[g])
+            fks.fks_server_submit(srv, r)
+            reqs.append(r)
+        conv = total = h2d = d2h = 0
+        statuses = []
+        for r in reqs:
+            st_r = fks.fks_server_wait(srv, r.ticket)
+            statuses.append(st_r)
+            if st_r >= 0:
+                conv += int(np.sum(r.res_true <= TOL))
+            total += r.res_true.size
+            h2d += r.b.nbytes + r.sigma.nbytes + r.tau.nbytes
+            d2h += r.X.nbytes + r.res_true.size * (8 * 3 + 4 * 2)
+        return {"wall_s": time.perf_counter() - t_start, "converged": conv, "solves": total, "h2d": h2d,
+                "d2h": d2h, "steps_max": int(max(int(r.m_j.max()) for r in reqs)),
+                "statuses": {str(k): int(v) for k, v in zip(*np.unique(np.array(statuses), return_counts=True))}}
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local])
+        except ValueError:
+            pass
+    replicas = Replicas(dist, world, torch.device("cuda", local))
+    srv = fks.fks_server_create(ctx, budget, lanes=args.mix_lanes)
+    for _ in range(max(args.warmup, 1)):
+        one_pass(srv)
+    l0 = fks.fks_server_launches(srv)
+    passes = []
+    with ClockSampler(gpu_index) as clk:
+        replicas.barrier()
+        for _ in range(args.steps):
+            passes.append(one_pass(srv))
+        replicas.barrier()
+    launches = fks.fks_server_launches(srv) - l0
+    fks.fks_server_destroy(srv)
+    wall = sum(q["wall_s"] for q in passes)
+    conv = sum(q["converged"] for q in passes)
+    value = replicas.throughput(conv / args.steps, wall / args.steps)
+    ms = 1000 * replicas.max(wall / args.steps)
+    one_lane = None
+    if not args.no_compare:
+        srv1 = fks.fks_server_create(ctx, budget, lanes=1)
+        one_pass(srv1)
+        q1 = one_pass(srv1)
+        fks.fks_server_destroy(srv1)
+        one_lane = {"value": q1["converged"] / q1["wall_s"], "ms_per_step": 1000 * q1["wall_s"], "lanes": 1,
+                    "steps_timed": 1}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = mix2d_cpu_sample(probs, args, passes[0]["steps_max"])
+    for op in ops:
+        fks.fks_op_destroy(op)
+    fks.fks_destroy(ctx)
+    if rank == 0:
+        sides = {}
+        for p in probs:
+            k = f"{p.shape[1]}x{p.shape[0]}"
+            sides[k] = sides.get(k, 0) + 1
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 1), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dtype_of(prec, fks), "data": "synthetic",
+                "config": {"workload": "2d-mix-32x(128..384)^2-f100-p4", "aquifers": len(probs), "grids": sides,
+                           "cells_total": int(sum(p.n for p in probs)), "n_f": len(probs[0].sigma), "n_p": 4,
+                           "sources_per_aquifer": 1, "precision": args.precision, "lanes": args.mix_lanes,
+                           "parallelism": f"replicas{world}",
+                           "step": "one request per aquifer through the server, until the last x_j is in host "
+                                   "memory", "op_setup_ms_all_aquifers": setup_ms,
+                           "arnoldi_steps_max": passes[0]["steps_max"],
+                           "l2": "bases and outputs of the 32 solves (GBs) exceed L2"},
+                "solves_per_step": passes[0]["solves"], "converged_per_step": conv / args.steps,
+                "request_statuses": passes[-1]["statuses"],
+                "comparison": {"one_lane": one_lane},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": passes[0]["h2d"],
+                        "d2h_bytes_per_step": passes[0]["d2h"],
+                        "note": "the server API takes host buffers: every request's copies are inside the timed "
+                                "region"},
+                "roofline": None,
+                "roofline_note": "per-kernel event timing runs on fks_solve's lane; the kernels are those of the "
+                                 "workload 1-2 lines",
+                "cpu_baseline": cpu, "clocks": clk.summary(), "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+
+
+def mix2d_cpu_sample(probs, args, steps):
+    """The oracle on the mixed 2D batch: a bounded sample of its first aquifer
+    (cpu_oracle_sample, scaled to `steps` Arnoldi steps), scaled to the batch by
+    cell count (the oracle's time per shifted solve grows with n)."""
+    p0 = probs[0]
+    v, dt, desc = cpu_oracle_sample(p0, max(1, args.cpu_sample_steps // 3), max(steps, 1), INNER_EPS,
+                                    args.inner_relax)
+    cells = sum(p.n for p in probs)
+    t_batch = len(p0.sigma) / v * cells / p0.n
+    value = sum(len(p.sigma) for p in probs) / t_batch
+    return {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": f"aquifer 0 ({p0.shape[1]}x{p0.shape[0]}, {len(p0.sigma)} shifts): {desc}; scaled to the "
+                      f"32 aquifers by cell count ({cells} cells)"}
 
 
 def jacobian_bench(args, rank, world, local, dist):
@@ -1049,6 +1183,25 @@ def run_reference(args):
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
+    if args.workload == 8:
+        probs = [synth.make_problem(m_max=100, **g) for g in synth.mix2d_grids()]
+        vals = []
+        cpu = None
+        for i in range(args.warmup + args.steps):
+            cpu = mix2d_cpu_sample(probs, args, WORKLOAD_STEPS[2])
+            if i >= args.warmup:
+                vals.append(cpu["value"])
+        value = statistics.median(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * sum(len(p.sigma) for p in probs) / value, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+                "config": {"workload": "2d-mix-32x(128..384)^2-f100-p4", "aquifers": len(probs),
+                           "cells_total": int(sum(p.n for p in probs)), "n_f": len(probs[0].sigma)},
+                "cpu_baseline": {**cpu, "value": value},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == 5:
         # the stream's first request stands for the stream
         # the stream's first request (its aquifer and shift count) stands for the stream
@@ -1190,6 +1343,11 @@ def main():
         return
     if args.workload == 7:
         csr_bench(args, rank, world, local, dist)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.workload == 8:
+        mix2d_bench(args, rank, world, local, dist)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -516,17 +516,26 @@ def fks_server_destroy(srv):
 
 class ServerRequest:
     """A request and the host arrays it points to (kept alive until done).
-    with_x=False submits X = NULL (residuals and statuses only); timeout_s > 0
-    stops the request with FKS_ERR_TIMEOUT once it has run that long."""
+    with_x=False submits X = NULL (residuals and statuses only); `out`, if
+    given, is the caller's array for X (complex128, C-contiguous, n_rhs x n_f x
+    n; for instance a view of page-locked memory reused across requests);
+    timeout_s > 0 stops the request with FKS_ERR_TIMEOUT once it has run that
+    long."""
 
-    def __init__(self, op, b, sigma, tau, options, keep, n, with_x=True, timeout_s=0.0):
+    def __init__(self, op, b, sigma, tau, options, keep, n, with_x=True, timeout_s=0.0, out=None):
         b = np.ascontiguousarray(b, dtype=np.complex128)
         self.n_rhs = b.shape[0] if b.ndim == 2 else 1
         self.b = b.reshape(self.n_rhs, n)
         self.sigma = np.ascontiguousarray(sigma, dtype=np.complex128)
         self.tau = np.ascontiguousarray(tau, dtype=np.complex128)
         n_f = len(self.sigma)
-        self.X = np.zeros((self.n_rhs, n_f, n), np.complex128) if with_x else None
+        if out is not None:
+            if (out.dtype != np.complex128 or out.shape != (self.n_rhs, n_f, n)
+                    or not out.flags["C_CONTIGUOUS"] or not out.flags["WRITEABLE"]):
+                raise ValueError(f"out: a writeable C-contiguous complex128 array of shape {(self.n_rhs, n_f, n)} "
+                                 f"expected, got {out.dtype} {out.shape}")
+            with_x = True
+        self.X = (out if out is not None else np.zeros((self.n_rhs, n_f, n), np.complex128)) if with_x else None
         self.res_est = np.zeros((self.n_rhs, n_f))
         self.res_bound = np.zeros((self.n_rhs, n_f))
         self.res_true = np.zeros((self.n_rhs, n_f))

@@ -54,6 +54,31 @@ def test_reference_arm_grid_workload_line(monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
 
 
+def test_reference_arm_mixed_2d_batch_line(monkeypatch):
+    """The reference arm of the mixed 2D batch: a bounded oracle sample of the
+    first aquifer, scaled to the 32 aquifers by cell count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1212_3660_gb300 import synth
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "8", "--steps", "1",
+                                      "--warmup", "0", "--cpu-sample-steps", "3"])
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.main()
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    grids = synth.mix2d_grids()
+    cells = sum(g["shape"][0] ** 2 for g in grids)
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["workload"] == "2d-mix-32x(128..384)^2-f100-p4"
+    assert line["config"]["aquifers"] == 32 and line["config"]["cells_total"] == cells
+    assert abs(line["ms_per_step"] - 1000.0 * 3200 / line["value"]) <= 1e-9 * line["ms_per_step"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert f"by cell count ({cells} cells)" in line["cpu_baseline"]["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
 def test_all_cores_oracle_baseline_runs_one_solve_per_core():
     """The all-cores CPU baseline: spawned processes (one BLAS thread each) each
     time the oracle model of one solve; the value is their sum and never below
