@@ -67,6 +67,36 @@ def test_results_alone_and_in_the_mix_are_identical():
         s.close()
 
 
+def test_page_locked_output_arrays_reused_across_requests():
+    """Requests on two operators whose x_j go into the caller's page-locked
+    arrays (out=), submitted twice with the same arrays, as the mixed 2D batch
+    of the bench does: both rounds give the bits of each request alone."""
+    need_gpu()
+    import torch
+    probs = [synth.make_problem((64, 64), n_f=6, periods=(5.0, 3600.0), n_p=3, seed=46, m_max=60),
+             synth.make_problem((96, 96), n_f=5, periods=(5.0, 3600.0), n_p=4, seed=47, m_max=60)]
+    solvers = [Solver(p) for p in probs]
+    keep_t = [torch.empty((1, len(p.sigma), p.n), dtype=torch.complex128, pin_memory=True) for p in probs]
+    outs = [t.numpy() for t in keep_t]
+    srv = fks.fks_server_create(solvers[0].ctx, 2 << 30, lanes=2)
+    for rnd in range(2):
+        reqs = []
+        for p, s, out in zip(probs, solvers, outs):
+            out.fill(np.nan)
+            opts, keep = fks.make_options(tol=p.tol, m_max=p.m_max, precision=fks.FKS_PREC_MIXED, inner_tol=1e-10,
+                                          schedule=p.schedule)
+            r = fks.ServerRequest(s.op, p.rhs().T.copy(), p.sigma, p.tau_bar, opts, keep, p.n, out=out)
+            fks.fks_server_submit(srv, r)
+            reqs.append(r)
+        for g, (p, s, r) in enumerate(zip(probs, solvers, reqs)):
+            assert fks.fks_server_wait(srv, r.ticket) == fks.FKS_OK, rnd
+            assert r.X is outs[g]
+            _alone_equal(s, r, fks.FKS_PREC_MIXED, p.tol)
+    fks.fks_server_destroy(srv)
+    for s in solvers:
+        s.close()
+
+
 def _long_problem():
     # 256^2, 200 shifts, tolerance 1e-10: tens of Arnoldi steps
     return synth.make_problem((256, 256), n_f=200, periods=(5.0, 3600.0), n_p=3, seed=44, m_max=100, tol=1e-10)
